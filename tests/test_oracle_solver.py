@@ -1,0 +1,199 @@
+"""Pins of the oracle's linear algebra and LM loop.
+
+The Schur complement (Sec. 4.2) and back substitution (Eq. backsub_sc) are
+checked against a brute-force dense solve of the full damped problem of
+Eq. linearized_residual (all pose and landmark unknowns at once) and a
+least-squares solve of the stacked augmented Jacobian; the per-landmark SC
+against the nullspace identity of Eq. red_H / red_b computed with numpy's QR;
+the PCG against the dense solve and the large-damping closed form; the LM
+loop against monotonicity, the chi-square level of the optimum and the
+noise-free optimum.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_01843_gb300.synth import make_scene
+
+
+def _full_jacobian(s, cams=None, pts=None):
+    cams = s.cams if cams is None else cams
+    pts = s.pts if pts is None else pts
+    n_p, n_l = 9 * s.n_cam, 3 * s.n_pt
+    J = np.zeros((2 * s.n_obs, n_p + n_l))
+    r = np.zeros(2 * s.n_obs)
+    for o in range(s.n_obs):
+        c, j = s.obs_cam[o], s.obs_pt[o]
+        ro, Jp, Jl = oracle.residual(cams[c], pts[j], s.obs_xy[o])
+        r[2 * o:2 * o + 2] = ro
+        J[2 * o:2 * o + 2, 9 * c:9 * c + 9] = Jp
+        J[2 * o:2 * o + 2, n_p + 3 * j:n_p + 3 * j + 3] = Jl
+    return J, r
+
+
+@pytest.fixture(scope="module")
+def small():
+    # few landmarks so that the full (9 n_cam + 3 n_pt)^2 system is cheap
+    return make_scene("small", 4, n_cam=8, n_pt=60, p=0.4, cap=8)
+
+
+def test_damping_diagonal_is_clamped_column_norm(small):
+    J, _ = _full_jacobian(small)
+    d = np.clip((J * J).sum(0), 1e-6, 1e32)
+    Dp2, Dl2 = oracle.damping_diag(small)
+    np.testing.assert_allclose(Dp2.ravel(), d[: 9 * small.n_cam], rtol=1e-12)
+    np.testing.assert_allclose(Dl2.ravel(), d[9 * small.n_cam:], rtol=1e-12)
+
+
+@pytest.mark.parametrize("lam", [1e-6, 1e-4, 1.0])
+def test_sc_step_equals_brute_force_full_solve(small, lam):
+    s = small
+    J, r = _full_jacobian(s)
+    D2 = np.clip((J * J).sum(0), 1e-6, 1e32)
+    H = J.T @ J + lam * np.diag(D2)
+    full = np.linalg.solve(H, -J.T @ r)
+    st = oracle.linear_step(s, lam, dense=True)
+    n_p = 9 * s.n_cam
+    scale = np.abs(full).max()
+    np.testing.assert_allclose(st["dp"].ravel(), full[:n_p], atol=1e-7 * scale)
+    np.testing.assert_allclose(st["dl"].ravel(), full[n_p:], atol=1e-7 * scale)
+    # also the minimiser of the stacked least-squares problem (QR-based lstsq)
+    if lam > 0:
+        A = np.vstack([J, np.sqrt(lam) * np.diag(np.sqrt(D2))])
+        b = -np.concatenate([r, np.zeros(J.shape[1])])
+        ls = np.linalg.lstsq(A, b, rcond=None)[0]
+        np.testing.assert_allclose(full, ls, atol=1e-7 * scale)
+    # model cost L = ||r + J dx||^2
+    dx = np.concatenate([st["dp"].ravel(), st["dl"].ravel()])
+    np.testing.assert_allclose(st["model_cost"], np.sum((r + J @ dx) ** 2), rtol=1e-9)
+    np.testing.assert_allclose(st["cost"], np.sum(r * r), rtol=1e-12)
+
+
+def test_rcs_is_symmetric_positive_definite_and_consistent(small):
+    H, bt = oracle.rcs_dense(small, 1e-4)
+    np.testing.assert_allclose(H, H.T, atol=1e-9 * np.abs(H).max())
+    assert np.linalg.eigvalsh(H).min() > 0
+    M, bt2 = oracle.rcs_diag(small, 1e-4)
+    for i in range(small.n_cam):
+        np.testing.assert_allclose(M[i], H[9 * i:9 * i + 9, 9 * i:9 * i + 9], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(bt2.ravel(), bt, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("lam", [0.0, 1e-3, 10.0])
+def test_landmark_sc_equals_nullspace_projection(small, lam):
+    """Eq. red_H / red_b: per landmark, S_j = (Q2^T J_p)^T (Q2^T J_p) and
+    b~_j = (Q2^T J_p)^T Q2^T r, with Q from a QR of the (damped) J_l."""
+    s = small
+    Dp2, Dl2 = oracle.damping_diag(s)
+    for j in range(0, s.n_pt, 7):
+        obs = np.nonzero(s.obs_pt == j)[0]
+        obs = obs[np.argsort(s.obs_cam[obs])]
+        k = obs.size
+        Jp = np.zeros((2 * k + 3, 9 * k))
+        Jl = np.zeros((2 * k + 3, 3))
+        r = np.zeros(2 * k + 3)
+        for t, o in enumerate(obs):
+            ro, P, L = oracle.residual(s.cams[s.obs_cam[o]], s.pts[j], s.obs_xy[o])
+            Jp[2 * t:2 * t + 2, 9 * t:9 * t + 9] = P
+            Jl[2 * t:2 * t + 2] = L
+            r[2 * t:2 * t + 2] = ro
+        Jl[2 * k:] = np.sqrt(lam) * np.diag(np.sqrt(Dl2[j]))
+        Q, _ = np.linalg.qr(Jl, mode="complete")
+        Q2 = Q[:, 3:]
+        A, c = Q2.T @ Jp, Q2.T @ r
+        S, bts, Hll, cc = oracle.landmark_sc(s, lam, j)
+        sc = np.abs(A.T @ A).max()
+        np.testing.assert_allclose(S, A.T @ A, atol=1e-9 * sc)
+        np.testing.assert_allclose(bts, A.T @ c, atol=1e-9 * max(np.abs(A.T @ c).max(), 1e-9))
+        np.testing.assert_allclose(Hll, Jl.T @ Jl, rtol=1e-12)
+        np.testing.assert_allclose(cc, c @ c, rtol=1e-8, atol=1e-12)
+
+
+def test_pcg_tight_equals_dense(small):
+    d = oracle.linear_step(small, 1e-3, dense=True)
+    p = oracle.linear_step(small, 1e-3, dense=False, max_cg=2000, cg_eta=1e-14)
+    scale = np.abs(d["dp"]).max()
+    np.testing.assert_allclose(p["dp"], d["dp"], atol=1e-6 * scale)
+    np.testing.assert_allclose(p["dl"], d["dl"], atol=1e-6 * np.abs(d["dl"]).max())
+    assert 1 <= p["cg_iters"] <= 2000
+
+
+def test_pcg_large_damping_is_scaled_gradient_step(small):
+    # with lambda -> inf, H~ -> lambda D_p^2: dp -> -b~ / (lambda D_p^2), one iteration
+    lam = 1e10
+    Dp2, _ = oracle.damping_diag(small)
+    _, bt = oracle.rcs_diag(small, lam)
+    st = oracle.linear_step(small, lam, dense=False)
+    np.testing.assert_allclose(st["dp"], -bt / (lam * Dp2), rtol=1e-4)
+    assert st["cg_iters"] == 1
+
+
+def test_pcg_iterations_fall_as_eta_grows(small):
+    its = [oracle.linear_step(small, 1e-4, dense=False, cg_eta=e)["cg_iters"]
+           for e in (1e-8, 1e-4, 1e-2, 0.1, 0.5)]
+    assert all(a >= b for a, b in zip(its, its[1:])), its
+
+
+def _check_lm_log(log, lambda0=1e-4):
+    lam, nu = lambda0, 2.0
+    last = None
+    for e in log:
+        assert e["lam"] == pytest.approx(lam, rel=1e-12)
+        if last is not None:
+            assert e["cost"] == pytest.approx(last, rel=1e-12)
+        if e["accepted"]:
+            assert e["new_cost"] <= e["cost"]
+            lam *= max(1 / 3, 1 - (2 * e["rho"] - 1) ** 3)
+            lam = max(lam, 1e-16)
+            nu = 2.0
+            last = e["new_cost"]
+        else:
+            lam *= nu
+            nu *= 2
+            last = e["cost"]
+
+
+@pytest.mark.parametrize("dense", [True, False])
+def test_lm_monotone_and_nielsen(tiny_scene, dense):
+    _, _, log = oracle.lm(tiny_scene, max_iters=20, dense=dense)
+    _check_lm_log(log)
+    assert log[-1]["accepted"]
+
+
+def test_lm_optimum_is_at_chi_square_level():
+    # residual dof = 2 n_obs - (9 n_cam + 3 n_pt) + 7 (similarity gauge)
+    for seed in (0, 1, 2):
+        s = make_scene("tiny", seed)
+        _, _, log = oracle.lm(s, max_iters=50, dense=True)
+        final = [e["new_cost"] for e in log if e["accepted"]][-1]
+        dof = 2 * s.n_obs - 9 * s.n_cam - 3 * s.n_pt + 7
+        assert abs(final - dof) < 5 * np.sqrt(2 * dof), (seed, final, dof)
+        # the optimum is at or below the cost at the ground truth
+        assert final <= oracle.cost(s, s.cams_gt, s.pts_gt)
+
+
+def test_lm_noise_free_reaches_zero():
+    s = make_scene("tiny", 1, noise_px=0.0)
+    e0 = oracle.cost(s)
+    c, p, log = oracle.lm(s, max_iters=50, dense=True, func_tol=0.0)
+    assert oracle.cost(s, c, p) < 1e-12 * e0
+
+
+def test_lm_dense_and_pcg_agree(tiny_scene):
+    _, _, ld = oracle.lm(tiny_scene, max_iters=20, dense=True)
+    _, _, lp = oracle.lm(tiny_scene, max_iters=20, dense=False)
+    fd = [e["new_cost"] for e in ld if e["accepted"]][-1]
+    fp = [e["new_cost"] for e in lp if e["accepted"]][-1]
+    assert abs(fd - fp) / fd < 1e-5
+
+
+def test_gauss_newton_model_matches_energy_to_second_order(small):
+    """E(x (+) t dx) - L(t dx) = O(t^2): pins the Jacobians and the update."""
+    st = oracle.linear_step(small, 1e-4, dense=True)
+    J, r = _full_jacobian(small)
+    dx = np.concatenate([st["dp"].ravel(), st["dl"].ravel()])
+    gaps = []
+    for t in (1e-2, 5e-3):
+        c, p = oracle.apply_update(small.cams, t * st["dp"], small.pts, t * st["dl"])
+        gaps.append(abs(oracle.cost(small, c, p) - np.sum((r + t * J @ dx) ** 2)))
+    assert 3.0 < gaps[0] / gaps[1] < 5.0, gaps
