@@ -26,7 +26,8 @@
  *     the composed rotation is stored back as axis-angle via unit quaternions.
  *   D^2 = clamp(diag(J^T J), 1e-6, 1e32) of the unscaled Jacobian (equivalent
  *     to unit column scaling with D = I in exact arithmetic).
- *   lambda update: Nielsen's rule; accept iff rho > 1e-3 with finite cost.
+ *   lambda update: Nielsen's rule; accept iff rho > 1e-3, the model decrease
+ *     E - L is positive and the new cost is finite.
  *     rho = (E - E_new) / (E - L), L = ||r + J dx||^2 (undamped model).
  *   CG stop: Nash-Sofer truncated-Newton test i (Q_i - Q_{i-1}) / Q_i < eta with
  *     Q(x) = 1/2 x^T H x - g^T x evaluated as -1/2 x^T (g + r); or ||r|| <= 1e-10 ||g||;
@@ -721,6 +722,34 @@ int orc_landmark_sc(int32_t n_cam, const double* cams, int32_t n_pt, const doubl
     return rc;
 }
 
+/* y = H~ v with the damped Schur complement assembled block-sparse. */
+int orc_rcs_matvec(int32_t n_cam, const double* cams, int32_t n_pt, const double* pts,
+                   int64_t n_obs, const int32_t* obs_cam, const int32_t* obs_pt,
+                   const double* obs_xy, double lambda, int32_t nv, const double* v, double* y) {
+    orc_lin L;
+    int rc = lin_setup(&L, n_cam, cams, n_pt, pts, n_obs, obs_cam, obs_pt, obs_xy);
+    if (!rc) rc = lin_build_rcs(&L, lambda);
+    for (int32_t m = 0; !rc && m < nv; ++m)
+        rcs_matvec(&L, v + 9 * (int64_t)n_cam * m, y + 9 * (int64_t)n_cam * m);
+    lin_free(&L);
+    return rc;
+}
+
+/* Landmark back substitution (Eq. backsub_sc, damped) for a given pose
+ * step dp, and the model cost L(dx) = ||r + J dx||^2 of the full step. */
+int orc_backsub_given(int32_t n_cam, const double* cams, int32_t n_pt, const double* pts,
+                      int64_t n_obs, const int32_t* obs_cam, const int32_t* obs_pt,
+                      const double* obs_xy, double lambda, const double* dp, double* dl,
+                      double* model_cost) {
+    orc_lin L;
+    int rc = lin_setup(&L, n_cam, cams, n_pt, pts, n_obs, obs_cam, obs_pt, obs_xy);
+    L.lambda = lambda;
+    if (!rc) rc = lin_backsub(&L, dp, dl);
+    if (!rc) *model_cost = lin_model_cost(&L, dp, dl);
+    lin_free(&L);
+    return rc;
+}
+
 typedef struct {
     double lambda0;   /* 1e-4 */
     int32_t max_iters; /* 50 */
@@ -800,7 +829,7 @@ int orc_lm(int32_t n_cam, double* cams, int32_t n_pt, double* pts, int64_t n_obs
         orc_apply_update(n_cam, cams, dp, n_pt, pts, dl, cn, pn);
         double En = orc_cost(n_cam, cn, n_pt, pn, n_obs, obs_cam, obs_pt, obs_xy);
         double rho = (E - En) / (E - model);
-        int acc = isfinite(En) && isfinite(rho) && rho > 1e-3;
+        int acc = isfinite(En) && isfinite(rho) && (E - model) > 0 && rho > 1e-3;
         orc_iter* lg = log + (*n_log)++;
         lg->cost = E; lg->new_cost = En; lg->model_cost = model; lg->lambda = lambda;
         lg->rho = rho; lg->cg_iters = cg; lg->accepted = acc;
