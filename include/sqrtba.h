@@ -1,0 +1,263 @@
+/*
+ * sqrtba.h - C ABI of the GB300 (sm_103a) square root bundle adjustment
+ * library (Demmel, Sommer, Cremers, Usenko: "Square Root Bundle Adjustment
+ * for Large-Scale Reconstruction", CVPR 2021).
+ *
+ * The problem (Sec. 4): minimise E = sum_ij ||r_ij||^2 (Eq. ba_energy) over
+ * n_cam cameras with d_p = 9 parameters each and n_pt 3-D landmarks, by
+ * Levenberg-Marquardt on the damped linearised problem of
+ * Eq. linearized_residual.  Landmarks are eliminated by nullspace
+ * marginalisation (Sec. 4.3): every landmark's dense block [J_p | J_l | r]
+ * (Sec. 5.1, Fig. 2) is QR-factored in place by three Householder
+ * reflections (Sec. 5.2), landmark damping is folded in by six stored Givens
+ * rotations (Sec. 5.3, Fig. 3), and the reduced camera system is solved by
+ * block-Jacobi preconditioned CG on the normal equations through the stored
+ * Q2^T J_p blocks (Sec. 5.4, Eq. cg_mult); landmarks are then recovered by
+ * back substitution (Eq. backsub_nm).  All marginalisation and PCG arithmetic
+ * is FP32 (Sec. 6.1, "sqrt BA-32"); the global cost sum, the model cost and
+ * the LM gain ratio are accumulated in FP64.
+ *
+ * Conventions for every call
+ *   - Camera layout (BAL, Sec. 6.2): 9 doubles per camera, row-major:
+ *     axis-angle w[3], translation t[3], focal length f, radial k1, k2.
+ *     P = R(w) X + t; points in front have P_z < 0; p = -P_xy / P_z;
+ *     pixel = f (1 + k1 |p|^2 + k2 |p|^4) p; residual = pixel - observation.
+ *   - Landmarks: 3 doubles each.  Observations: obs_cam[o], obs_pt[o] index
+ *     the camera and landmark of observation o, obs_xy[2 o + 0/1] its pixel.
+ *   - Host pointers are read during the call only; the library copies what
+ *     it needs.  The library owns all device memory of a problem.
+ *   - Work is issued in stream order on the CUDA stream given to ba_create
+ *     (NULL = the library creates its own); a call that returns a scalar
+ *     synchronises that stream.
+ *   - Every call returns a ba_status; nothing throws across the ABI.  After a
+ *     failure, ba_last_error() describes it.  A handle is used by one host
+ *     thread at a time.
+ */
+#ifndef SQRTBA_H
+#define SQRTBA_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SQRTBA_API __attribute__((visibility("default")))
+#else
+#define SQRTBA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ba_problem ba_problem; /* opaque */
+
+typedef enum {
+    BA_OK = 0,
+    BA_ERR_INVALID_ARG = 1, /* bad index, non-finite value, landmark with < 2 observations,
+                               duplicate (camera, landmark) pair, null pointer */
+    BA_ERR_OOM = 2,         /* device allocation failed */
+    BA_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    BA_ERR_STATE = 4,       /* calls out of order (e.g. PCG before marginalisation) */
+    BA_ERR_NUMERIC = 5,     /* non-finite cost / a preconditioner block not positive definite */
+    BA_ERR_TIMEOUT = 6      /* a bounded device-side wait gave up */
+} ba_status;
+
+/* Solver settings (Sec. 6.1 gives lambda0, the iteration limits and the
+ * function tolerance). */
+typedef struct {
+    double lambda0;       /* initial LM damping, default 1e-4 */
+    int32_t max_lm_iters; /* default 50; every linear solve counts as one iteration */
+    double func_tol;      /* relative cost-change stop on an accepted step, default 1e-6 */
+    int32_t max_cg_iters; /* default 500 */
+    double cg_eta;        /* Nash-Sofer forcing tolerance, default 0.1 */
+    int32_t use_graph;    /* 1 (default): PCG iterations replayed from a CUDA graph */
+    int32_t reserved[7];  /* zero */
+} ba_options;
+
+/* Fills *opt with the defaults above. */
+SQRTBA_API void ba_default_options(ba_options* opt);
+
+typedef struct {
+    int32_t iterations;   /* CG iterations performed */
+    int32_t stop_reason;  /* 0 forcing test, 1 residual, 2 iteration limit, 3 breakdown, 4 zero rhs */
+    double residual_norm; /* ||g - H~ x|| by the CG recursion */
+    double rhs_norm;      /* ||g|| */
+} ba_pcg_report;
+
+typedef struct {
+    int32_t iteration;    /* 0-based index of this LM iteration */
+    int32_t accepted;     /* 1 if the candidate replaced the state */
+    int32_t relinearized; /* 1 if this iteration linearised (K1) */
+    int32_t cg_iters;
+    int32_t stop;         /* 1: LM terminated on this iteration (tolerance, lambda overflow) */
+    int32_t pcg_stop_reason;
+    double cost;          /* E at the state the iteration started from */
+    double new_cost;      /* E at the candidate x (+) dx */
+    double model_cost;    /* ||r + J dx||^2, undamped Gauss-Newton model */
+    double lambda;        /* damping used */
+    double rho;           /* (cost - new_cost) / (cost - model_cost) */
+} ba_lm_report;
+
+/* Creates a problem from host FP64 arrays (layouts above).  Observations are
+ * validated and grouped by landmark on the device (Sec. 5.1).
+ * Errors: BA_ERR_INVALID_ARG for n_cam < 1, n_pt < 1, n_obs < 2, an index out
+ * of range, a non-finite value, a landmark with fewer than two observations
+ * or a duplicate (camera, landmark) pair; BA_ERR_OOM; BA_ERR_CUDA.
+ * cuda_stream: a cudaStream_t (e.g. a PyTorch stream) or NULL.
+ * On success *out owns the problem; release it with ba_destroy. */
+SQRTBA_API ba_status ba_create(const double* cams, int32_t n_cam, const double* pts, int32_t n_pt,
+                    const int32_t* obs_cam, const int32_t* obs_pt, const double* obs_xy,
+                    int64_t n_obs, const ba_options* opt, void* cuda_stream,
+                    ba_problem** out);
+
+/* Releases all device and host memory of a problem.  NULL is a no-op. */
+SQRTBA_API ba_status ba_destroy(ba_problem* h);
+
+/* Linearises at the current state (Sec. 4.1) and marginalises every landmark
+ * (Sec. 4.3, 5.2): residuals and analytic Jacobians, D^2 = clamp(diag(J^T J),
+ * 1e-6, 1e32), three Householder reflections per landmark block applied to
+ * [J_p | r]; stores R1, Q1^T J_p, Q1^T r, Q2^T J_p, Q2^T r.  Leaves the blocks
+ * undamped.  Also evaluates the cost at the current state. */
+SQRTBA_API ba_status ba_linearize(ba_problem* h);
+
+/* Applies landmark damping sqrt(lambda) D_l with six Givens rotations per
+ * landmark block (Sec. 5.3, Fig. 3 a-b), first undoing the previous damping
+ * with the stored rotations if the blocks are damped (Fig. 3 c).
+ * Errors: BA_ERR_STATE if not linearised; BA_ERR_INVALID_ARG if lambda <= 0
+ * or not finite. */
+SQRTBA_API ba_status ba_marginalize_qr(ba_problem* h, double lambda);
+
+/* Solves the damped reduced camera system H~ dx_p = -b~ with block-Jacobi
+ * PCG (Sec. 5.4, Eq. cg_mult; Sec. 6.1): builds the per-camera 9x9 blocks of
+ * H~ from the landmark blocks, then iterates the matvec
+ * (Q2^T J_p)^T (Q2^T J_p v) + lambda D_p^2 v.  Stops by the Nash-Sofer test
+ * with cg_eta, ||r|| <= 1e-10 ||g||, or max_cg_iters.  report may be NULL.
+ * Errors: BA_ERR_STATE if not marginalised. */
+SQRTBA_API ba_status ba_pcg_solve(ba_problem* h, ba_pcg_report* report);
+
+/* Back substitution dx_l = -R1^-1 (Q1^T r + Q1^T J_p dx_p) per landmark
+ * (Eq. backsub_nm, damped), then *model_cost = ||r + J dx||^2 (FP64 sum).
+ * Errors: BA_ERR_STATE if no PCG solution is present. */
+SQRTBA_API ba_status ba_backsubstitute(ba_problem* h, double* model_cost);
+
+/* *cost = E (Eq. ba_energy, FP64 sum of FP32 residuals) at the current state
+ * (candidate = 0) or at the candidate x (+) dx (candidate = 1; rotation
+ * updated as Exp(dw) R, everything else additively).
+ * Errors: BA_ERR_STATE for candidate = 1 without a back-substituted step. */
+SQRTBA_API ba_status ba_eval_cost(ba_problem* h, int32_t candidate, double* cost);
+
+/* One Levenberg-Marquardt iteration (Sec. 6.1): linearise if needed,
+ * marginalise with the current lambda, PCG, back substitution, candidate
+ * cost, FP64 gain ratio, accept or reject and update lambda (Nielsen).  A
+ * rejected step keeps the linearisation, so the next call only re-damps.
+ * report may be NULL.  Returns BA_ERR_STATE once the LM has stopped. */
+SQRTBA_API ba_status ba_lm_step(ba_problem* h, ba_lm_report* report);
+
+/* Runs ba_lm_step until stop or max_lm_iters.  reports (may be NULL) has
+ * room for max_reports entries; *n_reports (may be NULL) gets the count. */
+SQRTBA_API ba_status ba_solve(ba_problem* h, ba_lm_report* reports, int32_t max_reports,
+                   int32_t* n_reports);
+
+/* Copies the current state to host FP64 arrays (cams: 9 n_cam, pts: 3 n_pt);
+ * either pointer may be NULL. */
+SQRTBA_API ba_status ba_get_params(ba_problem* h, double* cams, double* pts);
+
+/* Replaces the state (host FP64 arrays, same layout), resets lambda to
+ * lambda0 and the LM iteration counter, and marks the linearisation stale. */
+SQRTBA_API ba_status ba_set_params(ba_problem* h, const double* cams, const double* pts);
+
+/* Checkpoint of the LM state besides the parameters. */
+typedef struct {
+    double lambda;
+    double nu;
+    int32_t iteration;
+    int32_t stopped;
+} ba_lm_state;
+SQRTBA_API ba_status ba_get_state(ba_problem* h, ba_lm_state* state);
+SQRTBA_API ba_status ba_set_state(ba_problem* h, const ba_lm_state* state);
+
+/* Sizes: n_cam, n_pt, n_obs, the number of FP32 values in the stored
+ * Q2^T J_p blocks (sum over landmarks of 2k x 9k, each block padded to a
+ * multiple of 4) and the total device bytes the problem holds. */
+typedef struct {
+    int32_t n_cam;
+    int32_t n_pt;
+    int64_t n_obs;
+    int64_t a_pool_floats;
+    int64_t sum_k2;
+    int32_t k_max;
+    int32_t reserved;
+    int64_t device_bytes;
+} ba_info;
+SQRTBA_API ba_status ba_get_info(ba_problem* h, ba_info* info);
+
+/* Timing of the phases of the hot path with CUDA events on the problem's
+ * stream, and transfer / launch counters.  Slots of ms[] and count[]:
+ *   0 linearisation + Householder QR (K1, with the D_p^2 kernel)
+ *   1 landmark damping (K2)   2 preconditioner + right-hand side (K3)
+ *   3 PCG matvec, one entry per launch (K4)   4 unused
+ *   5 back substitution + model cost (K6)   6 cost evaluations (K7)
+ * ms[i] is the summed duration, count[i] the number of timed intervals.
+ * kernel_launches counts every kernel the library launched (a replayed
+ * graph counts its kernels); h2d_bytes / d2h_bytes count the bytes copied
+ * between host and device.  All counters restart at ba_set_profiling. */
+typedef struct {
+    double ms[8];
+    int64_t count[8];
+    int64_t kernel_launches;
+    int64_t h2d_bytes;
+    int64_t d2h_bytes;
+} ba_profile;
+
+/* enable != 0 turns event timing on (adds event records around the phases,
+ * including event nodes inside the PCG graph); resets all counters. */
+SQRTBA_API ba_status ba_set_profiling(ba_problem* h, int32_t enable);
+SQRTBA_API ba_status ba_get_profile(ba_problem* h, ba_profile* out);
+
+/* Human-readable description of the last failure on this handle (never
+ * NULL; "" when none).  With h = NULL: the last failure of ba_create. */
+SQRTBA_API const char* ba_last_error(const ba_problem* h);
+
+/* ---------------------------------------------------------------------- */
+/* Inspection exports for tests (copy device state to host buffers).       */
+/* ---------------------------------------------------------------------- */
+
+/* Grouping by landmark (Sec. 5.1): perm[n_obs] = input observation index in
+ * (landmark, camera) order; pt_off[n_pt + 1] = landmark j owns sorted
+ * positions pt_off[j] .. pt_off[j+1]-1; cam_off[n_cam + 1], cam_list[n_obs] =
+ * camera i's sorted positions in increasing order.  Any pointer may be NULL. */
+SQRTBA_API ba_status ba_debug_export_order(ba_problem* h, int32_t* perm, int64_t* pt_off,
+                                int64_t* cam_off, int32_t* cam_list);
+
+/* Landmark block j in its current (damped or undamped) state.  With k its
+ * observation count and cameras in increasing index order:
+ *   top[3 * (9k + 4)]  rows of Q^T [J_p | J_l | r] belonging to R1:
+ *                      [Q1^T J_p (9k) | R1 row (3) | Q1^T r (1)] per row
+ *   a[2k * 9k]         Q2^T J_p row-major (last 3 rows: the damping rows)
+ *   c[2k]              Q2^T r
+ *   rot[12]            the six Givens (cos, sin) pairs of the current damping
+ * *k_out receives k; buffers must hold k_cap-sized data. */
+SQRTBA_API ba_status ba_debug_export_landmark(ba_problem* h, int32_t j, int32_t k_cap, float* top,
+                                   float* a, float* c, float* rot, int32_t* k_out);
+
+/* D_p^2 (9 n_cam) and D_l^2 (3 n_pt) of the current linearisation. */
+SQRTBA_API ba_status ba_debug_export_damping(ba_problem* h, float* dp2, float* dl2);
+
+/* Per sorted observation s: residual r (2), J_p (18, row-major 2x9) and J_l
+ * (6, row-major 2x3) at the current state.  Any pointer may be NULL. */
+SQRTBA_API ba_status ba_debug_export_jacobians(ba_problem* h, float* r, float* jp, float* jl);
+
+/* The block-Jacobi blocks M_i = sum_j A_ji^T A_ji + lambda D_p,i^2
+ * (n_cam x 81) and g = -b~ (9 n_cam) of the last PCG solve. */
+SQRTBA_API ba_status ba_debug_export_rcs_diag(ba_problem* h, float* m, float* g);
+
+/* y = H~ v for a host vector v (9 n_cam) with the current blocks and lambda. */
+SQRTBA_API ba_status ba_debug_matvec(ba_problem* h, const float* v, float* y);
+
+/* The last step: dx_p (9 n_cam) and dx_l (3 n_pt). */
+SQRTBA_API ba_status ba_debug_export_step(ba_problem* h, float* dp, float* dl);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SQRTBA_H */

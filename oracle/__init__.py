@@ -15,6 +15,8 @@ Functions and the passages of the paper they follow:
   landmark_sc    : one landmark's contribution to H~ and b~ (Eq. red_H, red_b)
   linear_step    : dense or block-Jacobi PCG solve of the RCS (Sec. 5.4, 6.1)
                    and back substitution (Eq. backsub_sc)
+  rcs_matvec     : products with H~ (block-sparse assembly)
+  backsub_given  : back substitution and model cost for a given pose step
   lm             : the Levenberg-Marquardt loop of Sec. 6.1
 """
 from __future__ import annotations
@@ -200,6 +202,31 @@ def landmark_sc(s, lam, j, k_cap=256, cams=None, pts=None):
                                  _p(Hll, _d), _p(cc, _d), _p(k, _i32)), "landmark_sc")
     n = 9 * int(k[0])
     return S[: n * n].reshape(n, n), bts[:n], Hll.reshape(3, 3), float(cc[0])
+
+
+def rcs_matvec(s, lam, V, cams=None, pts=None):
+    """Rows of H~ V^T: y_m = H~ v_m for each row v_m of V (m, 9 n_cam)."""
+    c, p, oc, op, xy = _problem(s)
+    c = c if cams is None else _f64(cams)
+    p = p if pts is None else _f64(pts)
+    V = np.atleast_2d(_f64(V))
+    Y = np.zeros_like(V)
+    _check(lib().orc_rcs_matvec(*_args(c, p, oc, op, xy), ctypes.c_double(lam), ctypes.c_int32(V.shape[0]),
+                                _p(V, _d), _p(Y, _d)), "rcs_matvec")
+    return Y
+
+
+def backsub_given(s, lam, dp, cams=None, pts=None):
+    """Landmark step for a given pose step dp (Eq. backsub_sc) and L(dx)."""
+    c, p, oc, op, xy = _problem(s)
+    c = c if cams is None else _f64(cams)
+    p = p if pts is None else _f64(pts)
+    dp = _f64(dp).ravel()
+    dl = np.zeros(3 * p.shape[0])
+    m = ctypes.c_double()
+    _check(lib().orc_backsub_given(*_args(c, p, oc, op, xy), ctypes.c_double(lam), _p(dp, _d),
+                                   _p(dl, _d), ctypes.byref(m)), "backsub_given")
+    return dl.reshape(-1, 3), m.value
 
 
 def options(lambda0=1e-4, max_iters=50, func_tol=1e-6, max_cg=500, cg_eta=0.1, dense=False):

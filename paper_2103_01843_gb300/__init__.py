@@ -1,0 +1,330 @@
+"""Python binding of the sqrtba C ABI (include/sqrtba.h).
+
+Square root bundle adjustment (Demmel et al., CVPR 2021) on GB300: the
+binding only marshals arguments; every step of the solver runs in the CUDA
+kernels of libsqrtba.so.  There is no CPU fallback: if the library has not
+been built, importing works but any call raises BAError.
+
+    from paper_2103_01843_gb300 import Problem
+    with Problem(cams, pts, obs_cam, obs_pt, obs_xy) as p:
+        reports = p.solve()
+        cams, pts = p.get_params()
+
+Function names follow the C ABI (ba_create -> Problem(), ba_linearize ->
+Problem.linearize, ...).  PyTorch, when used, only supplies the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libsqrtba.so")
+
+BA_OK = 0
+STATUS_NAMES = {0: "BA_OK", 1: "BA_ERR_INVALID_ARG", 2: "BA_ERR_OOM", 3: "BA_ERR_CUDA",
+                4: "BA_ERR_STATE", 5: "BA_ERR_NUMERIC", 6: "BA_ERR_TIMEOUT"}
+
+
+class BAError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("lambda0", ctypes.c_double), ("max_lm_iters", ctypes.c_int32),
+                ("func_tol", ctypes.c_double), ("max_cg_iters", ctypes.c_int32),
+                ("cg_eta", ctypes.c_double), ("use_graph", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
+
+
+class PcgReport(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("stop_reason", ctypes.c_int32),
+                ("residual_norm", ctypes.c_double), ("rhs_norm", ctypes.c_double)]
+
+
+class LmReport(ctypes.Structure):
+    _fields_ = [("iteration", ctypes.c_int32), ("accepted", ctypes.c_int32),
+                ("relinearized", ctypes.c_int32), ("cg_iters", ctypes.c_int32),
+                ("stop", ctypes.c_int32), ("pcg_stop_reason", ctypes.c_int32),
+                ("cost", ctypes.c_double), ("new_cost", ctypes.c_double),
+                ("model_cost", ctypes.c_double), ("lambda_", ctypes.c_double),
+                ("rho", ctypes.c_double)]
+
+
+class LmState(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("nu", ctypes.c_double),
+                ("iteration", ctypes.c_int32), ("stopped", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_cam", ctypes.c_int32), ("n_pt", ctypes.c_int32), ("n_obs", ctypes.c_int64),
+                ("a_pool_floats", ctypes.c_int64), ("sum_k2", ctypes.c_int64),
+                ("k_max", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 8), ("count", ctypes.c_int64 * 8),
+                ("kernel_launches", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64),
+                ("d2h_bytes", ctypes.c_int64)]
+
+
+PROFILE_SLOTS = ("linearize", "damp", "precond", "matvec", "unused", "backsub", "cost")
+
+
+def _struct_dict(s):
+    return {name.rstrip("_"): getattr(s, name) for name, _ in s._fields_ if name != "reserved"}
+
+
+_lib = None
+_lock = threading.Lock()
+
+_P = ctypes.c_void_p
+_d = ctypes.POINTER(ctypes.c_double)
+_f = ctypes.POINTER(ctypes.c_float)
+_i32 = ctypes.POINTER(ctypes.c_int32)
+_i64 = ctypes.POINTER(ctypes.c_int64)
+
+# name -> argtypes (restype ba_status = int unless noted)
+_SIGS = {
+    "ba_create": [_d, ctypes.c_int32, _d, ctypes.c_int32, _i32, _i32, _d, ctypes.c_int64,
+                  ctypes.POINTER(Options), _P, ctypes.POINTER(_P)],
+    "ba_destroy": [_P],
+    "ba_linearize": [_P],
+    "ba_marginalize_qr": [_P, ctypes.c_double],
+    "ba_pcg_solve": [_P, ctypes.POINTER(PcgReport)],
+    "ba_backsubstitute": [_P, _d],
+    "ba_eval_cost": [_P, ctypes.c_int32, _d],
+    "ba_lm_step": [_P, ctypes.POINTER(LmReport)],
+    "ba_solve": [_P, ctypes.POINTER(LmReport), ctypes.c_int32, _i32],
+    "ba_get_params": [_P, _d, _d],
+    "ba_set_params": [_P, _d, _d],
+    "ba_get_state": [_P, ctypes.POINTER(LmState)],
+    "ba_set_state": [_P, ctypes.POINTER(LmState)],
+    "ba_get_info": [_P, ctypes.POINTER(Info)],
+    "ba_set_profiling": [_P, ctypes.c_int32],
+    "ba_get_profile": [_P, ctypes.POINTER(Profile)],
+    "ba_debug_export_order": [_P, _i32, _i64, _i64, _i32],
+    "ba_debug_export_landmark": [_P, ctypes.c_int32, ctypes.c_int32, _f, _f, _f, _f, _i32],
+    "ba_debug_export_damping": [_P, _f, _f],
+    "ba_debug_export_jacobians": [_P, _f, _f, _f],
+    "ba_debug_export_rcs_diag": [_P, _f, _f],
+    "ba_debug_matvec": [_P, _f, _f],
+    "ba_debug_export_step": [_P, _f, _f],
+}
+
+
+def lib():
+    """The loaded libsqrtba.so; raises BAError if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise BAError(3, f"{LIB_PATH} is missing: build it with "
+                                 "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, args in _SIGS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+            L.ba_default_options.argtypes = [ctypes.POINTER(Options)]
+            L.ba_default_options.restype = None
+            L.ba_last_error.argtypes = [_P]
+            L.ba_last_error.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+def exported_symbols():
+    """Names the binding expects the library to export."""
+    return sorted(list(_SIGS) + ["ba_default_options", "ba_last_error"])
+
+
+def default_options(**kw):
+    o = Options()
+    lib().ba_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(t)
+
+
+class Problem:
+    """One bundle-adjustment problem resident on the GPU (ba_create)."""
+
+    def __init__(self, cams, pts, obs_cam, obs_pt, obs_xy, options=None, stream=None, **kw):
+        L = lib()
+        self._cams = np.ascontiguousarray(cams, np.float64)
+        self._pts = np.ascontiguousarray(pts, np.float64)
+        oc = np.ascontiguousarray(obs_cam, np.int32)
+        op = np.ascontiguousarray(obs_pt, np.int32)
+        xy = np.ascontiguousarray(obs_xy, np.float64)
+        self.n_cam, self.n_pt, self.n_obs = self._cams.shape[0], self._pts.shape[0], oc.shape[0]
+        opt = options if options is not None else default_options(**kw)
+        h = _P()
+        st = _P(stream) if stream else None
+        rc = L.ba_create(_ptr(self._cams, _d), self.n_cam, _ptr(self._pts, _d), self.n_pt,
+                         _ptr(oc, _i32), _ptr(op, _i32), _ptr(xy, _d), self.n_obs,
+                         ctypes.byref(opt), st, ctypes.byref(h))
+        if rc != BA_OK:
+            raise BAError(rc, L.ba_last_error(None).decode())
+        self.h = h
+        self.options = opt
+
+    @classmethod
+    def from_scene(cls, scene, **kw):
+        return cls(scene.cams, scene.pts, scene.obs_cam, scene.obs_pt, scene.obs_xy, **kw)
+
+    # --- lifetime -------------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ba_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != BA_OK:
+            raise BAError(rc, lib().ba_last_error(self.h).decode())
+
+    # --- the hot path -----------------------------------------------------------
+    def linearize(self):
+        self._check(lib().ba_linearize(self.h))
+
+    def marginalize_qr(self, lam):
+        self._check(lib().ba_marginalize_qr(self.h, float(lam)))
+
+    def pcg_solve(self):
+        r = PcgReport()
+        self._check(lib().ba_pcg_solve(self.h, ctypes.byref(r)))
+        return _struct_dict(r)
+
+    def backsubstitute(self):
+        m = ctypes.c_double()
+        self._check(lib().ba_backsubstitute(self.h, ctypes.byref(m)))
+        return m.value
+
+    def eval_cost(self, candidate=False):
+        c = ctypes.c_double()
+        self._check(lib().ba_eval_cost(self.h, 1 if candidate else 0, ctypes.byref(c)))
+        return c.value
+
+    def lm_step(self):
+        r = LmReport()
+        self._check(lib().ba_lm_step(self.h, ctypes.byref(r)))
+        return _struct_dict(r)
+
+    def solve(self, max_reports=1000):
+        reps = (LmReport * max_reports)()
+        n = ctypes.c_int32()
+        self._check(lib().ba_solve(self.h, reps, max_reports, ctypes.byref(n)))
+        return [_struct_dict(r) for r in reps[: min(n.value, max_reports)]]
+
+    # --- state ------------------------------------------------------------------
+    def get_params(self):
+        c = np.zeros((self.n_cam, 9))
+        p = np.zeros((self.n_pt, 3))
+        self._check(lib().ba_get_params(self.h, _ptr(c, _d), _ptr(p, _d)))
+        return c, p
+
+    def set_params(self, cams, pts):
+        c = np.ascontiguousarray(cams, np.float64)
+        p = np.ascontiguousarray(pts, np.float64)
+        assert c.shape == (self.n_cam, 9) and p.shape == (self.n_pt, 3)
+        self._check(lib().ba_set_params(self.h, _ptr(c, _d), _ptr(p, _d)))
+
+    def get_state(self):
+        s = LmState()
+        self._check(lib().ba_get_state(self.h, ctypes.byref(s)))
+        return _struct_dict(s)
+
+    def set_state(self, lam, nu, iteration, stopped=False):
+        s = LmState(lam, nu, iteration, 1 if stopped else 0)
+        self._check(lib().ba_set_state(self.h, ctypes.byref(s)))
+
+    def info(self):
+        i = Info()
+        self._check(lib().ba_get_info(self.h, ctypes.byref(i)))
+        return _struct_dict(i)
+
+    def set_profiling(self, enable=True):
+        self._check(lib().ba_set_profiling(self.h, 1 if enable else 0))
+
+    def profile(self):
+        pr = Profile()
+        self._check(lib().ba_get_profile(self.h, ctypes.byref(pr)))
+        out = {name: dict(ms=pr.ms[i], count=pr.count[i]) for i, name in enumerate(PROFILE_SLOTS)}
+        out.update(kernel_launches=pr.kernel_launches, h2d_bytes=pr.h2d_bytes, d2h_bytes=pr.d2h_bytes)
+        return out
+
+    # --- inspection exports -------------------------------------------------------
+    def export_order(self):
+        perm = np.zeros(self.n_obs, np.int32)
+        pt_off = np.zeros(self.n_pt + 1, np.int64)
+        cam_off = np.zeros(self.n_cam + 1, np.int64)
+        cam_list = np.zeros(self.n_obs, np.int32)
+        self._check(lib().ba_debug_export_order(self.h, _ptr(perm, _i32), _ptr(pt_off, _i64),
+                                                _ptr(cam_off, _i64), _ptr(cam_list, _i32)))
+        return perm, pt_off, cam_off, cam_list
+
+    def export_landmark(self, j, k_cap=256):
+        top = np.zeros(3 * (9 * k_cap + 4), np.float32)
+        a = np.zeros(2 * k_cap * 9 * k_cap, np.float32)
+        c = np.zeros(2 * k_cap, np.float32)
+        rot = np.zeros(12, np.float32)
+        k = ctypes.c_int32()
+        self._check(lib().ba_debug_export_landmark(self.h, int(j), int(k_cap), _ptr(top, _f), _ptr(a, _f),
+                                                   _ptr(c, _f), _ptr(rot, _f), ctypes.byref(k)))
+        k = k.value
+        n = 9 * k
+        return dict(k=k, top=top[: 3 * (n + 4)].reshape(3, n + 4), a=a[: 2 * k * n].reshape(2 * k, n),
+                    c=c[: 2 * k], rot=rot.reshape(6, 2))
+
+    def export_damping(self):
+        dp2 = np.zeros(9 * self.n_cam, np.float32)
+        dl2 = np.zeros(3 * self.n_pt, np.float32)
+        self._check(lib().ba_debug_export_damping(self.h, _ptr(dp2, _f), _ptr(dl2, _f)))
+        return dp2.reshape(-1, 9), dl2.reshape(-1, 3)
+
+    def export_jacobians(self):
+        r = np.zeros(2 * self.n_obs, np.float32)
+        jp = np.zeros(18 * self.n_obs, np.float32)
+        jl = np.zeros(6 * self.n_obs, np.float32)
+        self._check(lib().ba_debug_export_jacobians(self.h, _ptr(r, _f), _ptr(jp, _f), _ptr(jl, _f)))
+        return r.reshape(-1, 2), jp.reshape(-1, 2, 9), jl.reshape(-1, 2, 3)
+
+    def export_rcs_diag(self):
+        m = np.zeros(81 * self.n_cam, np.float32)
+        g = np.zeros(9 * self.n_cam, np.float32)
+        self._check(lib().ba_debug_export_rcs_diag(self.h, _ptr(m, _f), _ptr(g, _f)))
+        return m.reshape(-1, 9, 9), g.reshape(-1, 9)
+
+    def matvec(self, v):
+        v = np.ascontiguousarray(v, np.float32).ravel()
+        y = np.zeros_like(v)
+        self._check(lib().ba_debug_matvec(self.h, _ptr(v, _f), _ptr(y, _f)))
+        return y
+
+    def export_step(self):
+        dp = np.zeros(9 * self.n_cam, np.float32)
+        dl = np.zeros(3 * self.n_pt, np.float32)
+        self._check(lib().ba_debug_export_step(self.h, _ptr(dp, _f), _ptr(dl, _f)))
+        return dp.reshape(-1, 9), dl.reshape(-1, 3)

@@ -1,0 +1,159 @@
+// K6: landmark back substitution (Eq. backsub_nm, damped form of Sec. 5.3):
+//     dx_l = -R1^-1 (Q1^T r + Q1^T J_p dx_p)
+// from the three top rows of each landmark block, followed by the
+// Gauss-Newton model cost L(dx) = ||r + J_p dx_p + J_l dx_l||^2 (undamped)
+// evaluated per observation from the camera model and summed in FP64.
+//
+// K7 (same file): candidate state x (+) dx (rotation Exp(dw) R, everything
+// else additive) and the energy E = sum ||r||^2 (Eq. ba_energy) with FP32
+// residuals accumulated in FP64.  All FP64 sums are deterministic: fixed
+// per-block partials reduced in a fixed order.
+#include <algorithm>
+
+#include "camera.cuh"
+#include "problem.cuh"
+
+namespace sqrtba {
+
+namespace {
+
+constexpr int BS_WARPS = 4;
+
+__global__ void __launch_bounds__(32 * BS_WARPS)
+k_backsub(int n_pt, const int32_t* __restrict__ pt_off, const int32_t* __restrict__ obs_cam_s,
+          const float2* __restrict__ obs_xy_s, const float* __restrict__ tpool,
+          const float* __restrict__ cams, const float* __restrict__ pts, const float* __restrict__ dp,
+          float* __restrict__ dl, double* __restrict__ partials) {
+    __shared__ double wsum[BS_WARPS];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int j = blockIdx.x * BS_WARPS + w;
+    double msum = 0.0;
+    if (j < n_pt) {
+        const int s0 = pt_off[j], k = pt_off[j + 1] - s0, ncol = 9 * k;
+        const float* top = tpool + top_offset(s0, j);
+        float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+        for (int col = lane; col < ncol; col += 32) {
+            const int s = col / 9;
+            const float d = dp[9 * obs_cam_s[s0 + s] + (col - 9 * s)];
+            t0 += top[col] * d;
+            t1 += top[(ncol + 4) + col] * d;
+            t2 += top[2 * (ncol + 4) + col] * d;
+        }
+        t0 = warp_sum(t0);
+        t1 = warp_sum(t1);
+        t2 = warp_sum(t2);
+        const float* R0 = top + ncol;
+        const float* R1 = top + (ncol + 4) + ncol;
+        const float* R2 = top + 2 * (ncol + 4) + ncol;
+        t0 += R0[3];
+        t1 += R1[3];
+        t2 += R2[3];
+        const float l2 = -t2 / R2[2];
+        const float l1 = (-t1 - R1[2] * l2) / R1[1];
+        const float l0 = (-t0 - R0[1] * l1 - R0[2] * l2) / R0[0];
+        if (lane == 0) {
+            dl[3 * j] = l0;
+            dl[3 * j + 1] = l1;
+            dl[3 * j + 2] = l2;
+        }
+        const float X0 = pts[3 * j], X1 = pts[3 * j + 1], X2 = pts[3 * j + 2];
+        for (int s = lane; s < k; s += 32) {
+            const int cam = obs_cam_s[s0 + s];
+            const float2 z = obs_xy_s[s0 + s];
+            float r[2], Jp[18], Jl[6];
+            project_jacobians(cams + 9 * cam, X0, X1, X2, z.x, z.y, r, Jp, Jl);
+            const float* d = dp + 9 * cam;
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                float e = r[i] + Jl[3 * i] * l0 + Jl[3 * i + 1] * l1 + Jl[3 * i + 2] * l2;
+#pragma unroll
+                for (int c = 0; c < 9; ++c) e += Jp[9 * i + c] * d[c];
+                msum += (double)e * (double)e;
+            }
+        }
+        msum = warp_sum_d(msum);
+    }
+    if (lane == 0) wsum[w] = msum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int m = 0; m < BS_WARPS; ++m) s += wsum[m];
+        partials[blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_cost(int64_t n_obs, const float* __restrict__ cams, const float* __restrict__ pts,
+       const int32_t* __restrict__ obs_cam_s, const int32_t* __restrict__ obs_pt_s,
+       const float2* __restrict__ obs_xy_s, double* __restrict__ partials) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_obs;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int j = obs_pt_s[s];
+        const float2 z = obs_xy_s[s];
+        float r0, r1;
+        project_residual(cams + 9 * obs_cam_s[s], pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], z.x, z.y, r0, r1);
+        acc += (double)r0 * (double)r0 + (double)r1 * (double)r1;
+    }
+    acc = block_sum_d(acc, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(1024)
+k_sum_partials(const double* __restrict__ partials, int n, double* out) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partials[i];
+    acc = block_sum_d(acc, red);
+    if (threadIdx.x == 0) *out = acc;
+}
+
+__global__ void k_candidate(int n_cam, const float* __restrict__ cams, const float* __restrict__ dp,
+                            float* __restrict__ cand_cams, int n_pt, const float* __restrict__ pts,
+                            const float* __restrict__ dl, float* __restrict__ cand_pts) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_cam) {
+        const float* c = cams + 9 * i;
+        const float* d = dp + 9 * i;
+        float w[3];
+        compose_rotation(d, c, w);
+        float* o = cand_cams + 9 * i;
+        o[0] = w[0];
+        o[1] = w[1];
+        o[2] = w[2];
+#pragma unroll
+        for (int m = 3; m < 9; ++m) o[m] = c[m] + d[m];
+    }
+    if (i < 3 * n_pt) cand_pts[i] = pts[i] + dl[i];
+}
+
+}  // namespace
+
+void launch_backsub(Problem& p) {
+    count_launches(p, 2);
+    const int nb = ceil_div(p.n_pt, BS_WARPS);
+    k_backsub<<<nb, 32 * BS_WARPS, 0, p.stream>>>(p.n_pt, p.pt_off, p.obs_cam_s, p.obs_xy_s, p.tpool, p.cams,
+                                                  p.pts, p.x, p.dl, p.partials);
+    k_sum_partials<<<1, 1024, 0, p.stream>>>(p.partials, nb, p.dsum + 1);
+    BA_LAUNCH_CHECK();
+}
+
+void launch_candidate(Problem& p) {
+    count_launches(p, 1);
+    const int n = std::max(p.n_cam, 3 * p.n_pt);
+    k_candidate<<<ceil_div(n, 256), 256, 0, p.stream>>>(p.n_cam, p.cams, p.x, p.cand_cams, p.n_pt, p.pts, p.dl,
+                                                       p.cand_pts);
+    BA_LAUNCH_CHECK();
+}
+
+void launch_cost(Problem& p, bool candidate) {
+    count_launches(p, 2);
+    k_cost<<<p.red_grid, 256, 0, p.stream>>>(p.n_obs, candidate ? p.cand_cams : p.cams,
+                                             candidate ? p.cand_pts : p.pts, p.obs_cam_s, p.obs_pt_s,
+                                             p.obs_xy_s, p.partials);
+    k_sum_partials<<<1, 1024, 0, p.stream>>>(p.partials, p.red_grid, p.dsum + 0);
+    BA_LAUNCH_CHECK();
+}
+
+}  // namespace sqrtba

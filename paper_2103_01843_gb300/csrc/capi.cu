@@ -1,0 +1,756 @@
+// C ABI of the library and the host side of the Levenberg-Marquardt loop
+// (Sec. 6.1): lambda0, the iteration limit, the relative function tolerance
+// and the accept/reject rule with Nielsen's damping update.  The host only
+// reads back a few scalars per LM iteration (the PCG scalars, the FP64 model
+// cost and the FP64 candidate cost); everything else stays on the device.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "problem.cuh"
+
+namespace sqrtba {
+int linearize_k_limit();
+int matvec_ctas_per_sm();
+}  // namespace sqrtba
+
+using namespace sqrtba;
+
+struct ba_problem {
+    Problem p;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+constexpr int PCG_CHUNK = 8;
+
+void set_error(ba_problem* h, const std::string& m) {
+    if (h) h->p.last_error = m;
+    else g_create_error = m;
+}
+
+#define API_TRY try {
+#define API_CATCH(h)                                                      \
+    }                                                                     \
+    catch (const Error& e) {                                              \
+        set_error(h, e.msg);                                              \
+        return e.code;                                                    \
+    }                                                                     \
+    catch (const std::bad_alloc&) {                                       \
+        set_error(h, "host allocation failed");                           \
+        return BA_ERR_OOM;                                                \
+    }                                                                     \
+    catch (...) {                                                         \
+        set_error(h, "unexpected exception");                             \
+        return BA_ERR_CUDA;                                               \
+    }
+
+void require(bool cond, ba_status code, const char* msg) {
+    if (!cond) throw Error{code, msg};
+}
+
+template <typename T>
+void h2d(Problem& p, T* dst, const T* src, int64_t n) {
+    BA_CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(T) * n, cudaMemcpyHostToDevice, p.stream));
+    p.h2d_bytes += (int64_t)sizeof(T) * n;
+}
+template <typename T>
+void d2h(Problem& p, T* dst, const T* src, int64_t n) {
+    BA_CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(T) * n, cudaMemcpyDeviceToHost, p.stream));
+    p.d2h_bytes += (int64_t)sizeof(T) * n;
+}
+
+// --- optional phase timing (CUDA events, resolved at synchronisation points) --
+cudaEvent_t prof_event(Problem& p) {
+    Profiler& f = p.prof;
+    if (f.next == f.events.size()) {
+        cudaEvent_t e;
+        BA_CUDA_TRY(cudaEventCreate(&e));
+        f.events.push_back(e);
+    }
+    return f.events[f.next++];
+}
+
+struct PhaseTimer {
+    Problem& p;
+    int slot;
+    cudaEvent_t a = nullptr, b = nullptr;
+    PhaseTimer(Problem& pp, int s) : p(pp), slot(s) {
+        if (!p.prof.on) return;
+        a = prof_event(p);
+        b = prof_event(p);
+        BA_CUDA_TRY(cudaEventRecord(a, p.stream));
+    }
+    void end() {
+        if (!a) return;
+        BA_CUDA_TRY(cudaEventRecord(b, p.stream));
+        p.prof.pending.push_back({a, b, slot});
+        a = nullptr;
+    }
+};
+
+void prof_resolve(Problem& p) {
+    Profiler& f = p.prof;
+    for (auto& e : f.pending) {
+        float ms = 0.f;
+        BA_CUDA_TRY(cudaEventElapsedTime(&ms, e.a, e.b));
+        f.ms[e.slot] += ms;
+        f.count[e.slot] += 1;
+    }
+    f.pending.clear();
+    f.next = 0;
+}
+
+void sync(Problem& p) {
+    BA_CUDA_TRY(cudaStreamSynchronize(p.stream));
+    if (p.prof.on) prof_resolve(p);
+}
+
+void destroy_graph(Problem& p) {
+    if (p.pcg_graph) cudaGraphExecDestroy(p.pcg_graph);
+    p.pcg_graph = nullptr;
+}
+
+void free_all(Problem& p) {
+    destroy_graph(p);
+    for (cudaEvent_t e : p.prof.events) cudaEventDestroy(e);
+    for (cudaEvent_t e : p.mv_events) cudaEventDestroy(e);
+    p.prof.events.clear();
+    p.mv_events.clear();
+    for (void* a : p.allocations) cudaFree(a);
+    p.allocations.clear();
+    if (p.pcg_host) cudaFreeHost(p.pcg_host);
+    if (p.dsum_host) cudaFreeHost(p.dsum_host);
+    p.pcg_host = nullptr;
+    p.dsum_host = nullptr;
+    if (p.own_stream && p.stream) cudaStreamDestroy(p.stream);
+    p.stream = nullptr;
+}
+
+// --- the steps of the hot path ------------------------------------------------
+void do_linearize(Problem& p) {
+    PhaseTimer t(p, PROF_LINEARIZE);
+    launch_camera_diag(p);
+    launch_linearize(p);
+    t.end();
+    PhaseTimer tc(p, PROF_COST);
+    launch_cost(p, false);
+    tc.end();
+    d2h(p, p.dsum_host, p.dsum, 1);
+    sync(p);
+    p.cost = p.dsum_host[0];
+    p.linearized = true;
+    p.damped = false;
+    p.solved = false;
+    p.backsubbed = false;
+}
+
+void do_marginalize(Problem& p, double lambda) {
+    require(p.linearized, BA_ERR_STATE, "ba_marginalize_qr: problem is not linearised");
+    require(std::isfinite(lambda) && lambda > 0.0, BA_ERR_INVALID_ARG, "lambda must be positive and finite");
+    PhaseTimer t(p, PROF_DAMP);
+    launch_damp(p, p.damped, (float)lambda);
+    t.end();
+    p.damped = true;
+    p.lambda_damped = lambda;
+    p.solved = false;
+    p.backsubbed = false;
+}
+
+cudaEvent_t mv_event(Problem& p, int i) {
+    return p.prof.on ? p.mv_events[i] : nullptr;
+}
+
+void capture_pcg_graph(Problem& p) {
+    cudaGraph_t graph = nullptr;
+    BA_CUDA_TRY(cudaStreamBeginCapture(p.stream, cudaStreamCaptureModeThreadLocal));
+    p.capturing = true;
+    try {
+        for (int i = 0; i < PCG_CHUNK; ++i) launch_pcg_iteration(p, mv_event(p, 2 * i), mv_event(p, 2 * i + 1));
+    } catch (...) {
+        p.capturing = false;
+        cudaStreamEndCapture(p.stream, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        throw;
+    }
+    p.capturing = false;
+    BA_CUDA_TRY(cudaStreamEndCapture(p.stream, &graph));
+    cudaError_t e = cudaGraphInstantiate(&p.pcg_graph, graph, 0);
+    cudaGraphDestroy(graph);
+    BA_CUDA_TRY(e);
+    p.pcg_graph_iters = PCG_CHUNK;
+}
+
+void do_pcg(Problem& p, ba_pcg_report* rep) {
+    require(p.damped, BA_ERR_STATE, "ba_pcg_solve: blocks are not marginalised (call ba_marginalize_qr)");
+    PhaseTimer t(p, PROF_PRECOND);
+    launch_precond_rhs(p);
+    launch_pcg_init(p);
+    t.end();
+    if (p.opt.use_graph && !p.pcg_graph) capture_pcg_graph(p);
+    int launched = 0, it_before = 0;
+    for (;;) {
+        if (p.opt.use_graph) {
+            BA_CUDA_TRY(cudaGraphLaunch(p.pcg_graph, p.stream));
+            count_launches(p, 2 * p.pcg_graph_iters);
+        } else {
+            for (int i = 0; i < PCG_CHUNK; ++i) launch_pcg_iteration(p, mv_event(p, 2 * i), mv_event(p, 2 * i + 1));
+        }
+        launched += PCG_CHUNK;
+        d2h(p, p.pcg_host, p.pcg, 1);
+        sync(p);
+        if (p.prof.on) {
+            const int real = std::min(PCG_CHUNK, p.pcg_host->it - it_before);
+            for (int i = 0; i < real; ++i) {
+                float ms = 0.f;
+                BA_CUDA_TRY(cudaEventElapsedTime(&ms, p.mv_events[2 * i], p.mv_events[2 * i + 1]));
+                p.prof.ms[PROF_MATVEC] += ms;
+                p.prof.count[PROF_MATVEC] += 1;
+            }
+        }
+        it_before = p.pcg_host->it;
+        if (p.pcg_host->done || launched >= p.opt.max_cg_iters + PCG_CHUNK) break;
+    }
+    p.solved = true;
+    p.backsubbed = false;
+    if (rep) {
+        rep->iterations = p.pcg_host->it;
+        rep->stop_reason = p.pcg_host->stop;
+        rep->residual_norm = p.pcg_host->rnorm;
+        rep->rhs_norm = p.pcg_host->gnorm;
+    }
+}
+
+double do_backsub(Problem& p) {
+    require(p.solved, BA_ERR_STATE, "ba_backsubstitute: no PCG solution");
+    PhaseTimer t(p, PROF_BACKSUB);
+    launch_backsub(p);
+    t.end();
+    d2h(p, p.dsum_host + 1, p.dsum + 1, 1);
+    sync(p);
+    p.backsubbed = true;
+    return p.dsum_host[1];
+}
+
+double do_eval_cost(Problem& p, bool candidate) {
+    if (candidate) {
+        require(p.backsubbed, BA_ERR_STATE, "ba_eval_cost: no back-substituted step");
+    }
+    PhaseTimer t(p, PROF_COST);
+    if (candidate) launch_candidate(p);
+    launch_cost(p, candidate);
+    t.end();
+    d2h(p, p.dsum_host, p.dsum, 1);
+    sync(p);
+    return p.dsum_host[0];
+}
+
+void do_lm_step(Problem& p, ba_lm_report* rep) {
+    require(!p.stopped, BA_ERR_STATE, "ba_lm_step: the LM loop has stopped");
+    ba_lm_report r{};
+    r.iteration = p.iteration;
+    if (!p.linearized) {
+        do_linearize(p);
+        r.relinearized = 1;
+    }
+    const double E = p.cost;
+    const double lam = p.lambda;
+    do_marginalize(p, lam);
+    ba_pcg_report pr{};
+    do_pcg(p, &pr);
+    const double L = do_backsub(p);
+    const double En = do_eval_cost(p, true);
+    // a step is accepted only if the model predicts a decrease (E - L > 0);
+    // near convergence both differences sink below the FP32 evaluation noise
+    // and their ratio alone would accept noise
+    const double rho = (E - En) / (E - L);
+    const bool acc = std::isfinite(En) && std::isfinite(rho) && (E - L) > 0.0 && rho > 1e-3;
+    r.cost = E;
+    r.new_cost = En;
+    r.model_cost = L;
+    r.lambda = lam;
+    r.rho = rho;
+    r.cg_iters = pr.iterations;
+    r.pcg_stop_reason = pr.stop_reason;
+    r.accepted = acc ? 1 : 0;
+    if (acc) {
+        std::swap(p.cams, p.cand_cams);
+        std::swap(p.pts, p.cand_pts);
+        p.cost = En;
+        p.linearized = false;
+        p.damped = false;
+        p.solved = false;
+        p.backsubbed = false;
+        const double t = 2.0 * rho - 1.0;
+        p.lambda *= std::max(1.0 / 3.0, 1.0 - t * t * t);
+        p.lambda = std::max(p.lambda, 1e-16);
+        p.nu = 2.0;
+        if (std::fabs(E - En) / E < p.opt.func_tol) p.stopped = true;
+    } else {
+        p.lambda *= p.nu;
+        p.nu *= 2.0;
+        if (p.lambda >= 1e32) {
+            p.lambda = 1e32;
+            p.stopped = true;
+        }
+    }
+    p.iteration += 1;
+    if (p.iteration >= p.opt.max_lm_iters) p.stopped = true;
+    r.stop = p.stopped ? 1 : 0;
+    if (rep) *rep = r;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ba_default_options(ba_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->lambda0 = 1e-4;
+    o->max_lm_iters = 50;
+    o->func_tol = 1e-6;
+    o->max_cg_iters = 500;
+    o->cg_eta = 0.1;
+    o->use_graph = 1;
+}
+
+ba_status ba_create(const double* cams, int32_t n_cam, const double* pts, int32_t n_pt, const int32_t* obs_cam,
+                    const int32_t* obs_pt, const double* obs_xy, int64_t n_obs, const ba_options* opt,
+                    void* cuda_stream, ba_problem** out) {
+    ba_problem* h = nullptr;
+    g_create_error.clear();
+    try {
+        require(out != nullptr, BA_ERR_INVALID_ARG, "out is NULL");
+        *out = nullptr;
+        require(cams && pts && obs_cam && obs_pt && obs_xy, BA_ERR_INVALID_ARG, "null input pointer");
+        require(n_cam >= 1 && n_pt >= 1 && n_obs >= 2, BA_ERR_INVALID_ARG, "empty problem");
+        require(n_obs < ((int64_t)1 << 31) - 1, BA_ERR_INVALID_ARG, "too many observations (limit 2^31 - 2)");
+        h = new ba_problem();
+        Problem& p = h->p;
+        ba_default_options(&p.opt);
+        if (opt) p.opt = *opt;
+        require(p.opt.lambda0 > 0 && p.opt.max_lm_iters >= 1 && p.opt.max_cg_iters >= 1 && p.opt.cg_eta > 0,
+                BA_ERR_INVALID_ARG, "invalid options");
+        p.n_cam = n_cam;
+        p.n_pt = n_pt;
+        p.n_obs = n_obs;
+        p.lambda = p.opt.lambda0;
+        p.nu = 2.0;
+        if (cuda_stream) {
+            p.stream = (cudaStream_t)cuda_stream;
+        } else {
+            BA_CUDA_TRY(cudaStreamCreateWithFlags(&p.stream, cudaStreamNonBlocking));
+            p.own_stream = true;
+        }
+        int dev = 0;
+        BA_CUDA_TRY(cudaGetDevice(&dev));
+        BA_CUDA_TRY(cudaDeviceGetAttribute(&p.sm_count, cudaDevAttrMultiProcessorCount, dev));
+        p.mv_grid = p.sm_count * matvec_ctas_per_sm();
+        p.red_grid = p.sm_count * 4;
+
+        p.cams = dalloc<float>(p, 9 * (int64_t)n_cam);
+        p.cand_cams = dalloc<float>(p, 9 * (int64_t)n_cam);
+        p.pts = dalloc<float>(p, 3 * (int64_t)n_pt);
+        p.cand_pts = dalloc<float>(p, 3 * (int64_t)n_pt);
+        p.obs_cam_s = dalloc<int32_t>(p, n_obs);
+        p.obs_pt_s = dalloc<int32_t>(p, n_obs);
+        p.perm = dalloc<int32_t>(p, n_obs);
+        p.obs_xy_s = dalloc<float2>(p, n_obs);
+        p.pt_off = dalloc<int32_t>(p, n_pt + 1);
+        p.cam_off = dalloc<int32_t>(p, n_cam + 1);
+        p.cam_list = dalloc<int32_t>(p, n_obs);
+        p.a_off = dalloc<int64_t>(p, n_pt + 1);
+        p.lm_by_k = dalloc<int32_t>(p, n_pt);
+        p.mv_begin = dalloc<int32_t>(p, p.mv_grid + 1);
+        p.err = dalloc<uint32_t>(p, 4);
+        p.dsum = dalloc<double>(p, 4);
+        p.pcg = dalloc<PcgScalars>(p, 1);
+        BA_CUDA_TRY(cudaMallocHost(&p.pcg_host, sizeof(PcgScalars)));
+        BA_CUDA_TRY(cudaMallocHost(&p.dsum_host, 4 * sizeof(double)));
+        std::memset(p.pcg_host, 0, sizeof(PcgScalars));
+
+        // stage the FP64 inputs on the device for validation and grouping
+        double *d_cams = nullptr, *d_pts = nullptr, *d_xy = nullptr;
+        int32_t *d_oc = nullptr, *d_op = nullptr;
+        BA_CUDA_TRY(cudaMallocAsync(&d_cams, sizeof(double) * 9 * n_cam, p.stream));
+        BA_CUDA_TRY(cudaMallocAsync(&d_pts, sizeof(double) * 3 * n_pt, p.stream));
+        BA_CUDA_TRY(cudaMallocAsync(&d_xy, sizeof(double) * 2 * n_obs, p.stream));
+        BA_CUDA_TRY(cudaMallocAsync(&d_oc, sizeof(int32_t) * n_obs, p.stream));
+        BA_CUDA_TRY(cudaMallocAsync(&d_op, sizeof(int32_t) * n_obs, p.stream));
+        struct StageGuard {
+            Problem& p;
+            void* b[5];
+            ~StageGuard() {
+                for (void* x : b)
+                    if (x) cudaFreeAsync(x, p.stream);
+            }
+        } sg{p, {d_cams, d_pts, d_xy, d_oc, d_op}};
+        h2d(p, d_cams, cams, 9 * (int64_t)n_cam);
+        h2d(p, d_pts, pts, 3 * (int64_t)n_pt);
+        h2d(p, d_xy, obs_xy, 2 * n_obs);
+        h2d(p, d_oc, obs_cam, n_obs);
+        h2d(p, d_op, obs_pt, n_obs);
+        build_index(p, d_oc, d_op, d_xy, d_cams, d_pts);
+        require(p.k_max <= linearize_k_limit(), BA_ERR_INVALID_ARG,
+                "a landmark has more observations than the supported maximum (900)");
+
+        p.apool = dalloc<float>(p, p.a_floats);
+        p.t_floats = 3 * (9 * n_obs + 4 * (int64_t)n_pt);
+        p.tpool = dalloc<float>(p, p.t_floats);
+        p.cpool = dalloc<float>(p, 2 * n_obs);
+        p.rot = dalloc<float>(p, 12 * (int64_t)n_pt);
+        p.dp2 = dalloc<float>(p, 9 * (int64_t)n_cam);
+        p.dl2 = dalloc<float>(p, 3 * (int64_t)n_pt);
+        const int64_t nv = 9 * (int64_t)n_cam;
+        p.g = dalloc<float>(p, nv);
+        p.x = dalloc<float>(p, nv);
+        p.r = dalloc<float>(p, nv);
+        p.z = dalloc<float>(p, nv);
+        p.p = dalloc<float>(p, nv);
+        p.q = dalloc<float>(p, nv);
+        p.minv = dalloc<float>(p, 81 * (int64_t)n_cam);
+        p.mdiag = dalloc<float>(p, 81 * (int64_t)n_cam);
+        p.dl = dalloc<float>(p, 3 * (int64_t)n_pt);
+        p.partials = dalloc<double>(p, std::max<int64_t>((n_pt + 3) / 4 + 1, p.red_grid + 1));
+        BA_CUDA_TRY(cudaMemsetAsync(p.x, 0, sizeof(float) * nv, p.stream));
+        BA_CUDA_TRY(cudaMemsetAsync(p.dl, 0, sizeof(float) * 3 * n_pt, p.stream));
+        configure_linearize(p);
+        configure_matvec(p);
+        sync(p);
+        *out = h;
+        return BA_OK;
+    } catch (const Error& e) {
+        g_create_error = e.msg;
+        if (h) {
+            free_all(h->p);
+            delete h;
+        }
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        g_create_error = "host allocation failed";
+        if (h) {
+            free_all(h->p);
+            delete h;
+        }
+        return BA_ERR_OOM;
+    }
+}
+
+ba_status ba_destroy(ba_problem* h) {
+    if (!h) return BA_OK;
+    if (h->p.stream) cudaStreamSynchronize(h->p.stream);
+    free_all(h->p);
+    delete h;
+    return BA_OK;
+}
+
+ba_status ba_linearize(ba_problem* h) {
+    if (!h) return BA_ERR_INVALID_ARG;
+    API_TRY
+    do_linearize(h->p);
+    return BA_OK;
+    API_CATCH(h)
+}
+
+ba_status ba_marginalize_qr(ba_problem* h, double lambda) {
+    if (!h) return BA_ERR_INVALID_ARG;
+    API_TRY
+    do_marginalize(h->p, lambda);
+    return BA_OK;
+    API_CATCH(h)
+}
+
+ba_status ba_pcg_solve(ba_problem* h, ba_pcg_report* rep) {
+    if (!h) return BA_ERR_INVALID_ARG;
+    API_TRY
+    do_pcg(h->p, rep);
+    return BA_OK;
+    API_CATCH(h)
+}
+
+ba_status ba_backsubstitute(ba_problem* h, double* model_cost) {
+    if (!h) return BA_ERR_INVALID_ARG;
+    API_TRY
+    const double m = do_backsub(h->p);
+    if (model_cost) *model_cost = m;
+    return BA_OK;
+    API_CATCH(h)
+}
+
+ba_status ba_eval_cost(ba_problem* h, int32_t candidate, double* cost) {
+    if (!h || !cost) return BA_ERR_INVALID_ARG;
+    API_TRY
+    *cost = do_eval_cost(h->p, candidate != 0);
+    return BA_OK;
+    API_CATCH(h)
+}
+
+ba_status ba_lm_step(ba_problem* h, ba_lm_report* rep) {
+    if (!h) return BA_ERR_INVALID_ARG;
+    API_TRY
+    do_lm_step(h->p, rep);
+    return BA_OK;
+    API_CATCH(h)
+}
+
+ba_status ba_solve(ba_problem* h, ba_lm_report* reps, int32_t max_reports, int32_t* n_reports) {
+    if (!h) return BA_ERR_INVALID_ARG;
+    API_TRY
+    int32_t n = 0;
+    while (!h->p.stopped) {
+        ba_lm_report r;
+        do_lm_step(h->p, &r);
+        if (reps && n < max_reports) reps[n] = r;
+        ++n;
+    }
+    if (n_reports) *n_reports = n;
+    return BA_OK;
+    API_CATCH(h)
+}
+
+ba_status ba_get_params(ba_problem* h, double* cams, double* pts) {
+    if (!h) return BA_ERR_INVALID_ARG;
+    API_TRY
+    Problem& p = h->p;
+    std::vector<float> c(9 * (size_t)p.n_cam), x(3 * (size_t)p.n_pt);
+    if (cams) d2h(p, c.data(), p.cams, (int64_t)c.size());
+    if (pts) d2h(p, x.data(), p.pts, (int64_t)x.size());
+    sync(p);
+    if (cams)
+        for (size_t i = 0; i < c.size(); ++i) cams[i] = c[i];
+    if (pts)
+        for (size_t i = 0; i < x.size(); ++i) pts[i] = x[i];
+    return BA_OK;
+    API_CATCH(h)
+}
+
+ba_status ba_set_params(ba_problem* h, const double* cams, const double* pts) {
+    if (!h || !cams || !pts) return BA_ERR_INVALID_ARG;
+    API_TRY
+    Problem& p = h->p;
+    std::vector<float> c(9 * (size_t)p.n_cam), x(3 * (size_t)p.n_pt);
+    for (size_t i = 0; i < c.size(); ++i) {
+        require(std::isfinite(cams[i]), BA_ERR_INVALID_ARG, "non-finite camera value");
+        c[i] = (float)cams[i];
+    }
+    for (size_t i = 0; i < x.size(); ++i) {
+        require(std::isfinite(pts[i]), BA_ERR_INVALID_ARG, "non-finite point value");
+        x[i] = (float)pts[i];
+    }
+    h2d(p, p.cams, c.data(), (int64_t)c.size());
+    h2d(p, p.pts, x.data(), (int64_t)x.size());
+    sync(p);
+    p.linearized = p.damped = p.solved = p.backsubbed = false;
+    p.lambda = p.opt.lambda0;
+    p.nu = 2.0;
+    p.iteration = 0;
+    p.stopped = false;
+    return BA_OK;
+    API_CATCH(h)
+}
+
+ba_status ba_get_state(ba_problem* h, ba_lm_state* s) {
+    if (!h || !s) return BA_ERR_INVALID_ARG;
+    s->lambda = h->p.lambda;
+    s->nu = h->p.nu;
+    s->iteration = h->p.iteration;
+    s->stopped = h->p.stopped ? 1 : 0;
+    return BA_OK;
+}
+
+ba_status ba_set_state(ba_problem* h, const ba_lm_state* s) {
+    if (!h || !s) return BA_ERR_INVALID_ARG;
+    if (!(s->lambda > 0) || !(s->nu >= 1) || s->iteration < 0) {
+        set_error(h, "invalid LM state");
+        return BA_ERR_INVALID_ARG;
+    }
+    h->p.lambda = s->lambda;
+    h->p.nu = s->nu;
+    h->p.iteration = s->iteration;
+    h->p.stopped = s->stopped != 0;
+    return BA_OK;
+}
+
+ba_status ba_get_info(ba_problem* h, ba_info* info) {
+    if (!h || !info) return BA_ERR_INVALID_ARG;
+    std::memset(info, 0, sizeof(*info));
+    info->n_cam = h->p.n_cam;
+    info->n_pt = h->p.n_pt;
+    info->n_obs = h->p.n_obs;
+    info->a_pool_floats = h->p.a_floats;
+    info->sum_k2 = h->p.sum_k2;
+    info->k_max = h->p.k_max;
+    info->device_bytes = h->p.device_bytes;
+    return BA_OK;
+}
+
+ba_status ba_set_profiling(ba_problem* h, int32_t enable) {
+    if (!h) return BA_ERR_INVALID_ARG;
+    API_TRY
+    Problem& p = h->p;
+    sync(p);
+    p.prof.on = false;
+    p.prof.pending.clear();
+    p.prof.next = 0;
+    for (int i = 0; i < PROF_NSLOT; ++i) {
+        p.prof.ms[i] = 0.0;
+        p.prof.count[i] = 0;
+    }
+    p.launches = 0;
+    p.h2d_bytes = p.d2h_bytes = 0;
+    if (enable && p.mv_events.empty()) {
+        p.mv_events.resize(2 * PCG_CHUNK);
+        for (auto& e : p.mv_events) BA_CUDA_TRY(cudaEventCreate(&e));
+    }
+    destroy_graph(p);  // recaptured on the next solve, with event nodes only when profiling
+    p.prof.on = enable != 0;
+    return BA_OK;
+    API_CATCH(h)
+}
+
+ba_status ba_get_profile(ba_problem* h, ba_profile* out) {
+    if (!h || !out) return BA_ERR_INVALID_ARG;
+    API_TRY
+    Problem& p = h->p;
+    sync(p);
+    std::memset(out, 0, sizeof(*out));
+    for (int i = 0; i < PROF_NSLOT; ++i) {
+        out->ms[i] = p.prof.ms[i];
+        out->count[i] = p.prof.count[i];
+    }
+    out->kernel_launches = p.launches;
+    out->h2d_bytes = p.h2d_bytes;
+    out->d2h_bytes = p.d2h_bytes;
+    return BA_OK;
+    API_CATCH(h)
+}
+
+const char* ba_last_error(const ba_problem* h) {
+    return h ? h->p.last_error.c_str() : g_create_error.c_str();
+}
+
+// --- inspection exports ---------------------------------------------------------
+ba_status ba_debug_export_order(ba_problem* h, int32_t* perm, int64_t* pt_off, int64_t* cam_off,
+                                int32_t* cam_list) {
+    if (!h) return BA_ERR_INVALID_ARG;
+    API_TRY
+    Problem& p = h->p;
+    std::vector<int32_t> po(p.n_pt + 1), co(p.n_cam + 1);
+    if (perm) d2h(p, perm, p.perm, p.n_obs);
+    if (cam_list) d2h(p, cam_list, p.cam_list, p.n_obs);
+    d2h(p, po.data(), p.pt_off, p.n_pt + 1);
+    d2h(p, co.data(), p.cam_off, p.n_cam + 1);
+    sync(p);
+    if (pt_off)
+        for (int i = 0; i <= p.n_pt; ++i) pt_off[i] = po[i];
+    if (cam_off)
+        for (int i = 0; i <= p.n_cam; ++i) cam_off[i] = co[i];
+    return BA_OK;
+    API_CATCH(h)
+}
+
+ba_status ba_debug_export_landmark(ba_problem* h, int32_t j, int32_t k_cap, float* top, float* a, float* c,
+                                   float* rot, int32_t* k_out) {
+    if (!h) return BA_ERR_INVALID_ARG;
+    API_TRY
+    Problem& p = h->p;
+    require(j >= 0 && j < p.n_pt, BA_ERR_INVALID_ARG, "landmark index out of range");
+    require(p.linearized, BA_ERR_STATE, "not linearised");
+    int32_t off[2];
+    int64_t aoff = 0;
+    d2h(p, off, p.pt_off + j, 2);
+    d2h(p, &aoff, p.a_off + j, 1);
+    sync(p);
+    const int k = off[1] - off[0];
+    if (k_out) *k_out = k;
+    require(k <= k_cap, BA_ERR_INVALID_ARG, "k exceeds k_cap");
+    const int64_t ncol = 9 * (int64_t)k;
+    if (top) d2h(p, top, p.tpool + top_offset(off[0], j), 3 * (ncol + 4));
+    if (a) d2h(p, a, p.apool + aoff, 2 * (int64_t)k * ncol);
+    if (c) d2h(p, c, p.cpool + 2 * (int64_t)off[0], 2 * (int64_t)k);
+    if (rot) d2h(p, rot, p.rot + 12 * (int64_t)j, 12);
+    sync(p);
+    return BA_OK;
+    API_CATCH(h)
+}
+
+ba_status ba_debug_export_damping(ba_problem* h, float* dp2, float* dl2) {
+    if (!h) return BA_ERR_INVALID_ARG;
+    API_TRY
+    Problem& p = h->p;
+    if (dp2) d2h(p, dp2, p.dp2, 9 * (int64_t)p.n_cam);
+    if (dl2) d2h(p, dl2, p.dl2, 3 * (int64_t)p.n_pt);
+    sync(p);
+    return BA_OK;
+    API_CATCH(h)
+}
+
+ba_status ba_debug_export_jacobians(ba_problem* h, float* r, float* jp, float* jl) {
+    if (!h) return BA_ERR_INVALID_ARG;
+    API_TRY
+    Problem& p = h->p;
+    float *dr = nullptr, *djp = nullptr, *djl = nullptr;
+    BA_CUDA_TRY(cudaMallocAsync(&dr, sizeof(float) * 2 * p.n_obs, p.stream));
+    BA_CUDA_TRY(cudaMallocAsync(&djp, sizeof(float) * 18 * p.n_obs, p.stream));
+    BA_CUDA_TRY(cudaMallocAsync(&djl, sizeof(float) * 6 * p.n_obs, p.stream));
+    launch_export_jacobians(p, dr, djp, djl);
+    if (r) d2h(p, r, dr, 2 * p.n_obs);
+    if (jp) d2h(p, jp, djp, 18 * p.n_obs);
+    if (jl) d2h(p, jl, djl, 6 * p.n_obs);
+    cudaFreeAsync(dr, p.stream);
+    cudaFreeAsync(djp, p.stream);
+    cudaFreeAsync(djl, p.stream);
+    sync(p);
+    return BA_OK;
+    API_CATCH(h)
+}
+
+ba_status ba_debug_export_rcs_diag(ba_problem* h, float* m, float* g) {
+    if (!h) return BA_ERR_INVALID_ARG;
+    API_TRY
+    Problem& p = h->p;
+    require(p.solved, BA_ERR_STATE, "no PCG solve yet");
+    if (m) d2h(p, m, p.mdiag, 81 * (int64_t)p.n_cam);
+    if (g) d2h(p, g, p.g, 9 * (int64_t)p.n_cam);
+    sync(p);
+    return BA_OK;
+    API_CATCH(h)
+}
+
+ba_status ba_debug_matvec(ba_problem* h, const float* v, float* y) {
+    if (!h || !v || !y) return BA_ERR_INVALID_ARG;
+    API_TRY
+    Problem& p = h->p;
+    require(p.damped, BA_ERR_STATE, "blocks are not marginalised");
+    const int64_t n = 9 * (int64_t)p.n_cam;
+    float *dv = nullptr, *dy = nullptr;
+    BA_CUDA_TRY(cudaMallocAsync(&dv, sizeof(float) * n, p.stream));
+    BA_CUDA_TRY(cudaMallocAsync(&dy, sizeof(float) * n, p.stream));
+    h2d(p, dv, v, n);
+    launch_matvec(p, dv, dy, true);
+    d2h(p, y, dy, n);
+    cudaFreeAsync(dv, p.stream);
+    cudaFreeAsync(dy, p.stream);
+    sync(p);
+    return BA_OK;
+    API_CATCH(h)
+}
+
+ba_status ba_debug_export_step(ba_problem* h, float* dp, float* dl) {
+    if (!h) return BA_ERR_INVALID_ARG;
+    API_TRY
+    Problem& p = h->p;
+    if (dp) d2h(p, dp, p.x, 9 * (int64_t)p.n_cam);
+    if (dl) d2h(p, dl, p.dl, 3 * (int64_t)p.n_pt);
+    sync(p);
+    return BA_OK;
+    API_CATCH(h)
+}
+
+}  // extern "C"

@@ -1,0 +1,379 @@
+// K0: input validation and grouping of the observations by landmark
+// (Sec. 5.1: "we group the residuals by landmarks"), plus the camera-side
+// index and the landmark-block offsets.  Integer work; the result is unique
+// (observations sorted by (landmark, camera), camera lists in increasing
+// sorted position), so it is bit-exact whatever the thread schedule.
+#include <algorithm>
+#include <vector>
+
+#include "problem.cuh"
+
+namespace sqrtba {
+
+namespace {
+
+constexpr int SCAN_T = 256;
+constexpr int SCAN_PER = 16;
+constexpr int SCAN_B = SCAN_T * SCAN_PER;
+
+__device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t* sh, int64_t& total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) sh[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t w = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+        int64_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        sh[32 + lane] = wi - w;  // exclusive warp offsets
+        if (lane == 31) sh[64] = wi;
+    }
+    __syncthreads();
+    total = sh[64];
+    int64_t res = sh[32 + wid] + inc - v;
+    __syncthreads();
+    return res;
+}
+
+template <typename TIn>
+__global__ void k_scan_blocksum(const TIn* __restrict__ in, int64_t n, int64_t* __restrict__ bsum) {
+    __shared__ int64_t sh[65];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_B + (int64_t)threadIdx.x * SCAN_PER;
+    int64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_PER; ++i)
+        if (base + i < n) s += (int64_t)in[base + i];
+    int64_t total;
+    block_exclusive_scan(s, sh, total);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+__global__ void k_scan_bsums(int64_t* bsum, int nb) {
+    __shared__ int64_t sh[65];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < nb; c0 += blockDim.x) {
+        const int i = c0 + threadIdx.x;
+        int64_t v = i < nb ? bsum[i] : 0;
+        int64_t total;
+        int64_t ex = block_exclusive_scan(v, sh, total);
+        if (i < nb) bsum[i] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += total;
+        __syncthreads();
+    }
+}
+
+template <typename TIn, typename TOut>
+__global__ void k_scan_final(const TIn* __restrict__ in, int64_t n, const int64_t* __restrict__ bex,
+                             TOut* __restrict__ out) {
+    __shared__ int64_t sh[65];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_B + (int64_t)threadIdx.x * SCAN_PER;
+    int64_t vals[SCAN_PER];
+    int64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_PER; ++i) {
+        vals[i] = base + i < n ? (int64_t)in[base + i] : 0;
+        s += vals[i];
+    }
+    int64_t total;
+    int64_t run = bex[blockIdx.x] + block_exclusive_scan(s, sh, total);
+#pragma unroll
+    for (int i = 0; i < SCAN_PER; ++i) {
+        if (base + i < n) out[base + i] = (TOut)run;
+        if (base + i == n - 1) out[n] = (TOut)(run + vals[i]);
+        run += vals[i];
+    }
+}
+
+// exclusive scan of n values into out[0..n]; tmp holds >= ceil(n / SCAN_B) int64
+template <typename TIn, typename TOut>
+void exclusive_scan(const TIn* in, int64_t n, TOut* out, int64_t* tmp, cudaStream_t st) {
+    if (n <= 0) {
+        BA_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(TOut), st));
+        return;
+    }
+    const int nb = ceil_div(n, SCAN_B);
+    k_scan_blocksum<TIn><<<nb, SCAN_T, 0, st>>>(in, n, tmp);
+    k_scan_bsums<<<1, 1024, 0, st>>>(tmp, nb);
+    k_scan_final<TIn, TOut><<<nb, SCAN_T, 0, st>>>(in, n, tmp, out);
+    BA_LAUNCH_CHECK();
+}
+
+__global__ void k_convert_params(const double* __restrict__ in, int64_t n, float* __restrict__ out,
+                                 uint32_t* err) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = in[i];
+        if (!isfinite(v)) atomicOr(err, ERRBIT_NONFINITE);
+        out[i] = (float)v;
+    }
+}
+
+__global__ void k_validate_count(const int32_t* __restrict__ oc, const int32_t* __restrict__ op,
+                                 const double* __restrict__ xy, int64_t n, int n_cam, int n_pt,
+                                 int32_t* cnt_pt, int32_t* cnt_cam, uint32_t* err) {
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        const int c = oc[o], j = op[o];
+        if (c < 0 || c >= n_cam || j < 0 || j >= n_pt) {
+            atomicOr(err, ERRBIT_INDEX);
+            continue;
+        }
+        if (!isfinite(xy[2 * o]) || !isfinite(xy[2 * o + 1])) atomicOr(err, ERRBIT_NONFINITE);
+        atomicAdd(&cnt_pt[j], 1);
+        atomicAdd(&cnt_cam[c], 1);
+    }
+}
+
+__global__ void k_scatter_pt(const int32_t* __restrict__ op, int64_t n,
+                             const int32_t* __restrict__ pt_off, int32_t* cursor,
+                             int32_t* __restrict__ tmp) {
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        const int j = op[o];
+        const int pos = pt_off[j] + atomicAdd(&cursor[j], 1);
+        tmp[pos] = (int32_t)o;
+    }
+}
+
+// One thread per landmark: order its observations by camera (insertion
+// sort; the keys are unique for valid input), reject k < 2 and duplicates,
+// and write the sorted observation arrays.
+__global__ void k_sort_segments(int n_pt, const int32_t* __restrict__ pt_off, int32_t* tmp,
+                                const int32_t* __restrict__ oc, const double* __restrict__ xy,
+                                int32_t* __restrict__ perm, int32_t* __restrict__ obs_cam_s,
+                                int32_t* __restrict__ obs_pt_s, float2* __restrict__ obs_xy_s,
+                                int32_t* __restrict__ kcount, int32_t* kmax, int32_t* nbig,
+                                uint32_t* err) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_pt) return;
+    const int a = pt_off[j], b = pt_off[j + 1], k = b - a;
+    kcount[j] = k;
+    atomicMax(kmax, k);
+    if (k > 32) atomicAdd(nbig, 1);
+    if (k < 2) atomicOr(err, ERRBIT_FEWOBS);
+    for (int i = a + 1; i < b; ++i) {
+        const int v = tmp[i];
+        const int key = oc[v];
+        int m = i - 1;
+        while (m >= a && oc[tmp[m]] > key) {
+            tmp[m + 1] = tmp[m];
+            --m;
+        }
+        tmp[m + 1] = v;
+    }
+    int prev = -1;
+    for (int i = a; i < b; ++i) {
+        const int o = tmp[i];
+        const int c = oc[o];
+        if (c == prev) atomicOr(err, ERRBIT_DUPLICATE);
+        prev = c;
+        perm[i] = o;
+        obs_cam_s[i] = c;
+        obs_pt_s[i] = j;
+        obs_xy_s[i] = make_float2((float)xy[2 * o], (float)xy[2 * o + 1]);
+    }
+}
+
+// --- camera lists: a stable counting sort by camera over tiles --------------
+__global__ void k_tile_hist(const int32_t* __restrict__ cam_s, int64_t n, int n_cam, int tile,
+                            int32_t* hist) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&hist[(s / tile) * n_cam + cam_s[s]], 1);
+}
+
+__global__ void k_tile_base(int32_t* hist, int n_tiles, int n_cam, const int32_t* __restrict__ cam_off) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_cam) return;
+    int run = cam_off[c];
+    for (int t = 0; t < n_tiles; ++t) {
+        const int64_t i = (int64_t)t * n_cam + c;
+        const int h = hist[i];
+        hist[i] = run;  // becomes the tile's running base for this camera
+        run += h;
+    }
+}
+
+// one warp per tile, 32 observations at a time in increasing order
+__global__ void k_tile_place(const int32_t* __restrict__ cam_s, int64_t n, int n_cam, int tile,
+                             int n_tiles, int32_t* base, int32_t* __restrict__ cam_list) {
+    const int lane = threadIdx.x & 31;
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= n_tiles) return;
+    const int64_t s_end = min((int64_t)(t + 1) * tile, n);
+    for (int64_t c0 = (int64_t)t * tile; c0 < s_end; c0 += 32) {
+        const int64_t s = c0 + lane;
+        const bool valid = s < s_end;
+        const int cam = valid ? cam_s[s] : -1;
+        const unsigned grp = __match_any_sync(0xffffffffu, cam);
+        const int leader = __ffs(grp) - 1;
+        const int rank = __popc(grp & ((1u << lane) - 1u));
+        int b = 0;
+        if (valid && lane == leader) b = base[(int64_t)t * n_cam + cam];
+        b = __shfl_sync(0xffffffffu, b, leader);
+        if (valid) cam_list[b + rank] = (int32_t)s;
+        if (valid && lane == leader) base[(int64_t)t * n_cam + cam] = b + __popc(grp);
+        __syncwarp();
+    }
+}
+
+// --- block sizes and work lists ---------------------------------------------
+__global__ void k_block_sizes(int n_pt, const int32_t* __restrict__ kcount, int64_t* __restrict__ asz,
+                              int64_t* __restrict__ k2) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_pt) return;
+    const int64_t k = kcount[j];
+    asz[j] = pad4(18 * k * k);
+    k2[j] = k * k;
+}
+
+__global__ void k_khist(int n_pt, const int32_t* __restrict__ kcount, int kmax, int32_t* hist) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_pt) return;
+    atomicAdd(&hist[kmax - kcount[j]], 1);  // decreasing k
+}
+
+__global__ void k_kscatter(int n_pt, const int32_t* __restrict__ kcount, int kmax,
+                           const int32_t* __restrict__ koff, int32_t* cursor, int32_t* out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_pt) return;
+    const int b = kmax - kcount[j];
+    out[koff[b] + atomicAdd(&cursor[b], 1)] = j;
+}
+
+// first landmark of each matvec CTA: balanced by A-pool floats
+__global__ void k_partition(int n_pt, const int64_t* __restrict__ a_off, int grid,
+                            int32_t* __restrict__ begin) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > grid) return;
+    if (b == grid) {
+        begin[b] = n_pt;
+        return;
+    }
+    const int64_t target = (a_off[n_pt] * (int64_t)b) / grid;
+    int lo = 0, hi = n_pt;  // first j with a_off[j] >= target
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a_off[mid] < target) lo = mid + 1; else hi = mid;
+    }
+    begin[b] = lo;
+}
+
+}  // namespace
+
+void build_index(Problem& p, const int32_t* d_oc, const int32_t* d_op, const double* d_xy,
+                 const double* d_cams, const double* d_pts) {
+    cudaStream_t st = p.stream;
+    const int64_t n = p.n_obs;
+    const int TPB = 256;
+    const int gsz = std::max(1, std::min(ceil_div(n, TPB), p.sm_count * 8));
+
+    // temporaries, freed at the end of this call
+    std::vector<void*> tmps;
+    auto tmp_alloc = [&](size_t bytes) {
+        void* ptr = nullptr;
+        BA_CUDA_TRY(cudaMallocAsync(&ptr, bytes ? bytes : 1, st));
+        tmps.push_back(ptr);
+        return ptr;
+    };
+    struct Guard {
+        std::vector<void*>* v;
+        cudaStream_t st;
+        ~Guard() {
+            for (void* q : *v) cudaFreeAsync(q, st);
+        }
+    } guard{&tmps, st};
+
+    int32_t* cnt_pt = (int32_t*)tmp_alloc(sizeof(int32_t) * (p.n_pt + 1));
+    int32_t* cnt_cam = (int32_t*)tmp_alloc(sizeof(int32_t) * (p.n_cam + 1));
+    int64_t* scan_tmp = (int64_t*)tmp_alloc(sizeof(int64_t) * (ceil_div(n + p.n_pt + p.n_cam + 1, SCAN_B) + 2));
+    BA_CUDA_TRY(cudaMemsetAsync(cnt_pt, 0, sizeof(int32_t) * (p.n_pt + 1), st));
+    BA_CUDA_TRY(cudaMemsetAsync(cnt_cam, 0, sizeof(int32_t) * (p.n_cam + 1), st));
+    BA_CUDA_TRY(cudaMemsetAsync(p.err, 0, sizeof(uint32_t), st));
+
+    k_convert_params<<<gsz, TPB, 0, st>>>(d_cams, 9 * (int64_t)p.n_cam, p.cams, p.err);
+    k_convert_params<<<gsz, TPB, 0, st>>>(d_pts, 3 * (int64_t)p.n_pt, p.pts, p.err);
+    k_validate_count<<<gsz, TPB, 0, st>>>(d_oc, d_op, d_xy, n, p.n_cam, p.n_pt, cnt_pt, cnt_cam, p.err);
+    BA_LAUNCH_CHECK();
+    uint32_t herr = 0;
+    BA_CUDA_TRY(cudaMemcpyAsync(&herr, p.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    BA_CUDA_TRY(cudaStreamSynchronize(st));
+    if (herr & ERRBIT_INDEX) throw Error{BA_ERR_INVALID_ARG, "observation index out of range"};
+    if (herr & ERRBIT_NONFINITE) throw Error{BA_ERR_INVALID_ARG, "non-finite camera, point or observation value"};
+
+    exclusive_scan(cnt_pt, p.n_pt, p.pt_off, scan_tmp, st);
+    exclusive_scan(cnt_cam, p.n_cam, p.cam_off, scan_tmp, st);
+
+    int32_t* cursor = cnt_pt;  // reuse as scatter cursors
+    BA_CUDA_TRY(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (p.n_pt + 1), st));
+    int32_t* tmp_idx = (int32_t*)tmp_alloc(sizeof(int32_t) * n);
+    k_scatter_pt<<<gsz, TPB, 0, st>>>(d_op, n, p.pt_off, cursor, tmp_idx);
+    int32_t* kcount = (int32_t*)tmp_alloc(sizeof(int32_t) * (p.n_pt + 1));
+    int32_t* kmax_d = (int32_t*)tmp_alloc(2 * sizeof(int32_t));
+    BA_CUDA_TRY(cudaMemsetAsync(kmax_d, 0, 2 * sizeof(int32_t), st));
+    k_sort_segments<<<ceil_div(p.n_pt, 128), 128, 0, st>>>(p.n_pt, p.pt_off, tmp_idx, d_oc, d_xy, p.perm,
+                                                           p.obs_cam_s, p.obs_pt_s, p.obs_xy_s, kcount,
+                                                           kmax_d, kmax_d + 1, p.err);
+    BA_LAUNCH_CHECK();
+
+    // camera lists
+    int64_t n_tiles = std::max<int64_t>(1, std::min<int64_t>((n + 2047) / 2048, ((int64_t)1 << 25) / p.n_cam));
+    int64_t tile = ((n + n_tiles - 1) / n_tiles + 31) / 32 * 32;
+    n_tiles = std::max<int64_t>(1, (n + tile - 1) / tile);
+    int32_t* hist = (int32_t*)tmp_alloc(sizeof(int32_t) * n_tiles * p.n_cam);
+    BA_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(int32_t) * n_tiles * p.n_cam, st));
+    k_tile_hist<<<gsz, TPB, 0, st>>>(p.obs_cam_s, n, p.n_cam, (int)tile, hist);
+    k_tile_base<<<ceil_div(p.n_cam, 128), 128, 0, st>>>(hist, (int)n_tiles, p.n_cam, p.cam_off);
+    k_tile_place<<<ceil_div(n_tiles * 32, 128), 128, 0, st>>>(p.obs_cam_s, n, p.n_cam, (int)tile,
+                                                              (int)n_tiles, hist, p.cam_list);
+    BA_LAUNCH_CHECK();
+
+    // block offsets
+    int64_t* asz = (int64_t*)tmp_alloc(sizeof(int64_t) * (p.n_pt + 1));
+    int64_t* k2 = (int64_t*)tmp_alloc(sizeof(int64_t) * (p.n_pt + 1));
+    int64_t* k2off = (int64_t*)tmp_alloc(sizeof(int64_t) * (p.n_pt + 1));
+    k_block_sizes<<<ceil_div(p.n_pt, 256), 256, 0, st>>>(p.n_pt, kcount, asz, k2);
+    exclusive_scan(asz, p.n_pt, p.a_off, scan_tmp, st);
+    exclusive_scan(k2, p.n_pt, k2off, scan_tmp, st);
+
+    int32_t kinfo[2] = {0, 0};
+    int64_t totals[2] = {0, 0};
+    BA_CUDA_TRY(cudaMemcpyAsync(&herr, p.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    BA_CUDA_TRY(cudaMemcpyAsync(kinfo, kmax_d, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    BA_CUDA_TRY(cudaMemcpyAsync(&totals[0], p.a_off + p.n_pt, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    BA_CUDA_TRY(cudaMemcpyAsync(&totals[1], k2off + p.n_pt, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    BA_CUDA_TRY(cudaStreamSynchronize(st));
+    if (herr & ERRBIT_FEWOBS) throw Error{BA_ERR_INVALID_ARG, "a landmark has fewer than two observations"};
+    if (herr & ERRBIT_DUPLICATE) throw Error{BA_ERR_INVALID_ARG, "duplicate (camera, landmark) observation"};
+    const int32_t kmax = kinfo[0];
+    p.k_max = kmax;
+    p.n_big = kinfo[1];
+    p.a_floats = totals[0];
+    p.sum_k2 = totals[1];
+
+    // landmarks by decreasing k (work order for the per-landmark kernels)
+    int32_t* kh = (int32_t*)tmp_alloc(sizeof(int32_t) * (kmax + 2));
+    int32_t* ko = (int32_t*)tmp_alloc(sizeof(int32_t) * (kmax + 2));
+    BA_CUDA_TRY(cudaMemsetAsync(kh, 0, sizeof(int32_t) * (kmax + 2), st));
+    k_khist<<<ceil_div(p.n_pt, 256), 256, 0, st>>>(p.n_pt, kcount, kmax, kh);
+    exclusive_scan(kh, kmax + 1, ko, scan_tmp, st);
+    BA_CUDA_TRY(cudaMemsetAsync(kh, 0, sizeof(int32_t) * (kmax + 2), st));
+    k_kscatter<<<ceil_div(p.n_pt, 256), 256, 0, st>>>(p.n_pt, kcount, kmax, ko, kh, p.lm_by_k);
+    k_partition<<<ceil_div(p.mv_grid + 1, 256), 256, 0, st>>>(p.n_pt, p.a_off, p.mv_grid, p.mv_begin);
+    BA_LAUNCH_CHECK();
+    BA_CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+}  // namespace sqrtba

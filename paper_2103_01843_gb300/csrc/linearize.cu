@@ -1,0 +1,375 @@
+// K1: per-landmark linearisation and in-place nullspace marginalisation.
+//
+// For landmark j with k observations the dense landmark block of Sec. 5.1
+// (Fig. 2b) is [J_p | J_l | r] with 2k rows.  Three Householder reflections
+// H_a = I - tau_a v_a v_a^T (Sec. 5.2: "three Householder reflections per
+// landmark block") reduce J_l to R1; Q^T = H_3 H_2 H_1 is applied to the pose
+// columns and the residual in compact WY form, Q^T = I - V T^T V^T, so that
+// each output element costs three FMAs plus the one non-zero of the sparse
+// J_p column:   out[i][col] = M[i][col] - sum_a V[i][a] W[a][col],
+// W = T^T (V^T M) with M = [J_p | r].  Rows 0..2 are the R1 rows
+// (Q1^T J_p, R1, Q1^T r, used by back substitution, Eq. backsub_nm); rows
+// 3..2k-1 are Q2^T J_p and Q2^T r (Eq. reduced).  Q is never stored.
+//
+// One warp handles a landmark with k <= 32 (2k rows fit one row per lane for
+// the reductions); a 256-thread CTA handles larger k.  Work is taken from
+// the landmark list ordered by decreasing k, so long blocks start first.
+#include <algorithm>
+
+#include "camera.cuh"
+#include "problem.cuh"
+
+namespace sqrtba {
+
+namespace {
+
+constexpr int K_WARP = 32;     // largest k handled by one warp
+constexpr int LIN_WARPS = 4;   // warps per CTA in the warp kernel
+constexpr int BIG_TEAM = 256;  // threads per CTA for k > K_WARP
+
+__host__ __device__ constexpr int lin_smem_floats(int k) { return 59 * k + 24; }
+
+template <int TEAM>
+struct Team;
+
+template <>
+struct Team<32> {
+    __device__ static int rank() { return threadIdx.x & 31; }
+    __device__ static void sync() { __syncwarp(); }
+    __device__ static void sum3(float& a, float& b, float& c, float*) {
+        a = warp_sum(a);
+        b = warp_sum(b);
+        c = warp_sum(c);
+    }
+};
+
+template <>
+struct Team<BIG_TEAM> {
+    __device__ static int rank() { return threadIdx.x; }
+    __device__ static void sync() { __syncthreads(); }
+    // red: >= 3 * (BIG_TEAM / 32) floats of shared memory
+    __device__ static void sum3(float& a, float& b, float& c, float* red) {
+        constexpr int NW = BIG_TEAM / 32;
+        a = warp_sum(a);
+        b = warp_sum(b);
+        c = warp_sum(c);
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        if (lane == 0) {
+            red[3 * w] = a;
+            red[3 * w + 1] = b;
+            red[3 * w + 2] = c;
+        }
+        __syncthreads();
+        a = b = c = 0.0f;
+#pragma unroll
+        for (int m = 0; m < NW; ++m) {
+            a += red[3 * m];
+            b += red[3 * m + 1];
+            c += red[3 * m + 2];
+        }
+        __syncthreads();
+    }
+};
+
+struct LinArgs {
+    const float* cams;
+    const float* pts;
+    const int32_t* obs_cam_s;
+    const float2* obs_xy_s;
+    const int32_t* pt_off;
+    const int64_t* a_off;
+    float* apool;
+    float* tpool;
+    float* cpool;
+    float* dl2;
+};
+
+// Linearise and marginalise landmark j; sm holds lin_smem_floats(k) floats.
+template <int TEAM>
+__device__ void marginalize_landmark(const LinArgs& A, int j, float* sm, float* red) {
+    using T = Team<TEAM>;
+    const int rank = T::rank();
+    const int s0 = A.pt_off[j];
+    const int k = A.pt_off[j + 1] - s0;
+    const int nr = 2 * k;        // rows
+    const int ncol = 9 * k;      // pose columns
+    float* L = sm;               // nr x 3   (J_l -> R1 and reflector tails)
+    float* JP = L + 3 * nr;      // nr x 9   (pose Jacobian rows, block-sparse)
+    float* RV = JP + 9 * nr;     // nr       (residuals)
+    float* V = RV + nr;          // nr x 3   (Householder vectors, v_a[a] = 1)
+    float* W = V + 3 * nr;       // 3 x (ncol + 1)
+    float* misc = W + 3 * (ncol + 1);  // tau[3], beta, v0, Tm[9], vr[3]
+
+    // 1. residuals and Jacobians of every observation (Sec. 6.1: analytic)
+    const float X0 = A.pts[3 * j], X1 = A.pts[3 * j + 1], X2 = A.pts[3 * j + 2];
+    for (int s = rank; s < k; s += TEAM) {
+        const float2 z = A.obs_xy_s[s0 + s];
+        float r[2], Jp[18], Jl[6];
+        project_jacobians(A.cams + 9 * A.obs_cam_s[s0 + s], X0, X1, X2, z.x, z.y, r, Jp, Jl);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            RV[2 * s + i] = r[i];
+#pragma unroll
+            for (int c = 0; c < 9; ++c) JP[(2 * s + i) * 9 + c] = Jp[9 * i + c];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) L[(2 * s + i) * 3 + c] = Jl[3 * i + c];
+        }
+    }
+    T::sync();
+
+    // D_l^2 = clamp(diag(J_l^T J_l), 1e-6, 1e32)
+    {
+        float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+        for (int i = rank; i < nr; i += TEAM) {
+            d0 += L[3 * i] * L[3 * i];
+            d1 += L[3 * i + 1] * L[3 * i + 1];
+            d2 += L[3 * i + 2] * L[3 * i + 2];
+        }
+        T::sum3(d0, d1, d2, red);
+        if (rank == 0) {
+            A.dl2[3 * j] = fminf(fmaxf(d0, 1e-6f), 1e32f);
+            A.dl2[3 * j + 1] = fminf(fmaxf(d1, 1e-6f), 1e32f);
+            A.dl2[3 * j + 2] = fminf(fmaxf(d2, 1e-6f), 1e32f);
+        }
+    }
+
+    // 2. Householder QR of J_l (2k x 3), reflector a acts on rows a..2k-1
+    for (int a = 0; a < 3; ++a) {
+        float sg = 0.f, u1 = 0.f, u2 = 0.f;
+        for (int i = a + 1 + rank; i < nr; i += TEAM) sg += L[3 * i + a] * L[3 * i + a];
+        T::sum3(sg, u1, u2, red);
+        if (rank == 0) {
+            const float alpha = L[3 * a + a];
+            float tau = 0.f, beta = alpha, v0 = 1.f;
+            if (sg > 0.f) {
+                const float mu = sqrtf(alpha * alpha + sg);
+                beta = alpha > 0.f ? -mu : mu;
+                v0 = alpha - beta;
+                tau = (beta - alpha) / beta;
+            }
+            misc[a] = tau;
+            misc[3] = beta;
+            misc[4] = v0;
+        }
+        T::sync();
+        const float tau = misc[a], inv_v0 = 1.0f / misc[4];
+        for (int i = rank; i < nr; i += TEAM)
+            V[3 * i + a] = i < a ? 0.f : (i == a ? 1.f : (tau == 0.f ? 0.f : L[3 * i + a] * inv_v0));
+        T::sync();
+        // apply H_a to the remaining landmark columns
+        float w1 = 0.f, w2 = 0.f, w0 = 0.f;
+        for (int i = a + rank; i < nr; i += TEAM) {
+            if (a + 1 < 3) w1 += V[3 * i + a] * L[3 * i + a + 1];
+            if (a + 2 < 3) w2 += V[3 * i + a] * L[3 * i + a + 2];
+        }
+        T::sum3(w1, w2, w0, red);
+        for (int i = a + rank; i < nr; i += TEAM) {
+            const float va = V[3 * i + a];
+            if (a + 1 < 3) L[3 * i + a + 1] -= tau * w1 * va;
+            if (a + 2 < 3) L[3 * i + a + 2] -= tau * w2 * va;
+        }
+        T::sync();
+        if (rank == 0) L[3 * a + a] = misc[3];
+        T::sync();
+    }
+
+    // 3. compact WY: H_1 H_2 H_3 = I - V Tm V^T, Tm upper triangular
+    {
+        float d01 = 0.f, d02 = 0.f, d12 = 0.f;
+        for (int i = rank; i < nr; i += TEAM) {
+            d01 += V[3 * i] * V[3 * i + 1];
+            d02 += V[3 * i] * V[3 * i + 2];
+            d12 += V[3 * i + 1] * V[3 * i + 2];
+        }
+        T::sum3(d01, d02, d12, red);
+        float r0 = 0.f, r1 = 0.f, r2 = 0.f;  // V^T r
+        for (int i = rank; i < nr; i += TEAM) {
+            r0 += V[3 * i] * RV[i];
+            r1 += V[3 * i + 1] * RV[i];
+            r2 += V[3 * i + 2] * RV[i];
+        }
+        T::sum3(r0, r1, r2, red);
+        if (rank == 0) {
+            const float t0 = misc[0], t1 = misc[1], t2 = misc[2];
+            float* Tm = misc + 5;
+            Tm[0] = t0;
+            Tm[4] = t1;
+            Tm[8] = t2;
+            Tm[3] = Tm[6] = Tm[7] = 0.f;
+            Tm[1] = -t0 * t1 * d01;
+            Tm[5] = -t2 * (t1 * d12);
+            Tm[2] = -t2 * (t0 * d02 + Tm[1] * d12);
+            // W column of the residual: Tm^T (V^T r)
+            float* vr = misc + 14;
+            vr[0] = Tm[0] * r0;
+            vr[1] = Tm[1] * r0 + Tm[4] * r1;
+            vr[2] = Tm[2] * r0 + Tm[5] * r1 + Tm[8] * r2;
+        }
+        T::sync();
+    }
+
+    // 4. W = Tm^T (V^T J_p) for the pose columns (two non-zero rows each)
+    {
+        const float* Tm = misc + 5;
+        const float T00 = Tm[0], T01 = Tm[1], T02 = Tm[2], T11 = Tm[4], T12 = Tm[5], T22 = Tm[8];
+        for (int col = rank; col < ncol; col += TEAM) {
+            const int s = col / 9, c = col - 9 * s;
+            const float ja = JP[(2 * s) * 9 + c], jb = JP[(2 * s + 1) * 9 + c];
+            const float m0 = V[3 * (2 * s)] * ja + V[3 * (2 * s + 1)] * jb;
+            const float m1 = V[3 * (2 * s) + 1] * ja + V[3 * (2 * s + 1) + 1] * jb;
+            const float m2 = V[3 * (2 * s) + 2] * ja + V[3 * (2 * s + 1) + 2] * jb;
+            W[col] = T00 * m0;
+            W[(ncol + 1) + col] = T01 * m0 + T11 * m1;
+            W[2 * (ncol + 1) + col] = T02 * m0 + T12 * m1 + T22 * m2;
+        }
+        if (rank == 0) {
+            W[ncol] = misc[14];
+            W[(ncol + 1) + ncol] = misc[15];
+            W[2 * (ncol + 1) + ncol] = misc[16];
+        }
+        T::sync();
+    }
+
+    // 5. write Q^T [J_p | r]: rows 0..2 to the top block, rows 3.. to A_j / c_j
+    const int64_t toff = top_offset(s0, j);
+    float* __restrict__ top = A.tpool + toff;
+    float* __restrict__ Aj = A.apool + A.a_off[j];
+    const int64_t total = (int64_t)nr * ncol;
+    int e = rank;
+    int i = e / ncol, col = e - i * ncol;
+    for (; e < total; e += TEAM) {
+        const int s = col / 9;
+        const float mval = (s == (i >> 1)) ? JP[i * 9 + (col - 9 * s)] : 0.f;
+        const float out = mval - (V[3 * i] * W[col] + V[3 * i + 1] * W[(ncol + 1) + col] +
+                                  V[3 * i + 2] * W[2 * (ncol + 1) + col]);
+        if (i < 3) top[i * (ncol + 4) + col] = out;
+        else if (i < nr) Aj[e - 3 * ncol] = out;
+        col += TEAM;
+        while (col >= ncol) {
+            col -= ncol;
+            ++i;
+        }
+    }
+    // residual column and R1
+    for (int ii = rank; ii < nr; ii += TEAM) {
+        const float out = RV[ii] - (V[3 * ii] * W[ncol] + V[3 * ii + 1] * W[(ncol + 1) + ncol] +
+                                    V[3 * ii + 2] * W[2 * (ncol + 1) + ncol]);
+        if (ii < 3) {
+            float* row = top + ii * (ncol + 4) + ncol;
+            row[0] = ii <= 0 ? L[3 * ii] : 0.f;
+            row[1] = ii <= 1 ? L[3 * ii + 1] : 0.f;
+            row[2] = L[3 * ii + 2];
+            row[3] = out;
+        } else {
+            A.cpool[2 * (int64_t)s0 + (ii - 3)] = out;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(32 * LIN_WARPS)
+k_linearize_warp(LinArgs A, const int32_t* __restrict__ order, int first, int count) {
+    extern __shared__ float smem[];
+    const int w = threadIdx.x >> 5;
+    const int idx = blockIdx.x * LIN_WARPS + w;
+    if (idx >= count) return;
+    float* sm = smem + w * lin_smem_floats(K_WARP);
+    marginalize_landmark<32>(A, order[first + idx], sm, nullptr);
+}
+
+__global__ void __launch_bounds__(BIG_TEAM)
+k_linearize_block(LinArgs A, const int32_t* __restrict__ order, int count) {
+    extern __shared__ float smem[];
+    __shared__ float red[3 * (BIG_TEAM / 32)];
+    if ((int)blockIdx.x >= count) return;
+    marginalize_landmark<BIG_TEAM>(A, order[blockIdx.x], smem, red);
+}
+
+// D_p^2 = clamp(diag(J_p^T J_p), 1e-6, 1e32) per camera, one warp per
+// camera summing over its observations in a fixed order (deterministic).
+__global__ void k_camera_diag(int n_cam, const float* __restrict__ cams, const float* __restrict__ pts,
+                              const int32_t* __restrict__ obs_pt_s, const float2* __restrict__ obs_xy_s,
+                              const int32_t* __restrict__ cam_off, const int32_t* __restrict__ cam_list,
+                              float* __restrict__ dp2) {
+    const int cam = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (cam >= n_cam) return;
+    float acc[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) acc[c] = 0.f;
+    for (int e = cam_off[cam] + lane; e < cam_off[cam + 1]; e += 32) {
+        const int s = cam_list[e];
+        const int j = obs_pt_s[s];
+        const float2 z = obs_xy_s[s];
+        float r[2], Jp[18], Jl[6];
+        project_jacobians(cams + 9 * cam, pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], z.x, z.y, r, Jp, Jl);
+#pragma unroll
+        for (int c = 0; c < 9; ++c) acc[c] += Jp[c] * Jp[c] + Jp[9 + c] * Jp[9 + c];
+    }
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+        const float v = warp_sum(acc[c]);
+        if (lane == 0) dp2[9 * cam + c] = fminf(fmaxf(v, 1e-6f), 1e32f);
+    }
+}
+
+__global__ void k_export_jacobians(int64_t n_obs, const float* __restrict__ cams, const float* __restrict__ pts,
+                                   const int32_t* __restrict__ obs_cam_s, const int32_t* __restrict__ obs_pt_s,
+                                   const float2* __restrict__ obs_xy_s, float* r_out, float* jp_out,
+                                   float* jl_out) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_obs;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int j = obs_pt_s[s];
+        const float2 z = obs_xy_s[s];
+        float r[2], Jp[18], Jl[6];
+        project_jacobians(cams + 9 * obs_cam_s[s], pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], z.x, z.y, r,
+                          Jp, Jl);
+        for (int i = 0; i < 2; ++i) r_out[2 * s + i] = r[i];
+        for (int i = 0; i < 18; ++i) jp_out[18 * s + i] = Jp[i];
+        for (int i = 0; i < 6; ++i) jl_out[6 * s + i] = Jl[i];
+    }
+}
+
+}  // namespace
+
+int linearize_k_limit() { return 900; }
+
+void configure_linearize(Problem& p) {
+    const int sb = (int)(sizeof(float) * lin_smem_floats(std::max(p.k_max, K_WARP)));
+    BA_CUDA_TRY(cudaFuncSetAttribute(k_linearize_block, cudaFuncAttributeMaxDynamicSharedMemorySize, sb));
+    const int sw = (int)(sizeof(float) * lin_smem_floats(K_WARP) * LIN_WARPS);
+    BA_CUDA_TRY(cudaFuncSetAttribute(k_linearize_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, sw));
+}
+
+void launch_camera_diag(Problem& p) {
+    count_launches(p, 1);
+    k_camera_diag<<<ceil_div((int64_t)p.n_cam * 32, 128), 128, 0, p.stream>>>(
+        p.n_cam, p.cams, p.pts, p.obs_pt_s, p.obs_xy_s, p.cam_off, p.cam_list, p.dp2);
+    BA_LAUNCH_CHECK();
+}
+
+void launch_linearize(Problem& p) {
+    count_launches(p, (p.n_big > 0) + (p.n_pt - p.n_big > 0));
+    LinArgs A{p.cams, p.pts, p.obs_cam_s, p.obs_xy_s, p.pt_off, p.a_off,
+              p.apool, p.tpool, p.cpool, p.dl2};
+    const int n_big = p.n_big;
+    if (n_big > 0) {
+        const size_t sm = sizeof(float) * lin_smem_floats(p.k_max);
+        k_linearize_block<<<n_big, BIG_TEAM, sm, p.stream>>>(A, p.lm_by_k, n_big);
+        BA_LAUNCH_CHECK();
+    }
+    const int n_small = p.n_pt - n_big;
+    if (n_small > 0) {
+        const size_t sm = sizeof(float) * lin_smem_floats(K_WARP) * LIN_WARPS;
+        k_linearize_warp<<<ceil_div(n_small, LIN_WARPS), 32 * LIN_WARPS, sm, p.stream>>>(A, p.lm_by_k, n_big,
+                                                                                          n_small);
+        BA_LAUNCH_CHECK();
+    }
+}
+
+void launch_export_jacobians(Problem& p, float* r, float* jp, float* jl) {
+    k_export_jacobians<<<p.sm_count * 4, 256, 0, p.stream>>>(p.n_obs, p.cams, p.pts, p.obs_cam_s, p.obs_pt_s,
+                                                             p.obs_xy_s, r, jp, jl);
+    BA_LAUNCH_CHECK();
+}
+
+}  // namespace sqrtba

@@ -1,0 +1,167 @@
+// Device-resident state of one bundle-adjustment problem and the launchers
+// of every kernel of the hot path.
+//
+// Data layout in HBM (FP32 unless noted; k_j = observations of landmark j):
+//   cams[9 n_cam], pts[3 n_pt]          current state; cand_* the candidate
+//   obs_cam_s, obs_pt_s, obs_xy_s       observations sorted by (landmark, camera)
+//   pt_off[n_pt + 1] (int32)            landmark j owns sorted obs pt_off[j] ..
+//   cam_off[n_cam + 1], cam_list[n_obs] camera -> sorted positions (increasing)
+//   a_off[n_pt + 1] (int64)             float offset of A_j in apool
+//   apool                               A_j = Q^T J_p rows below R1, 2k x 9k row-major,
+//                                       the last 3 rows are the landmark damping rows
+//                                       (Sec. 5.3); blocks padded to 16 bytes
+//   tpool                               top_j: 3 x (9k + 4) rows [Q1^T J_p | R1 | Q1^T r],
+//                                       at float offset 3 (9 pt_off[j] + 4 j)
+//   cpool                               c_j = Q2^T r (2k), at float offset 2 pt_off[j]
+//   rot[12 n_pt]                        six Givens (cos, sin) of the current damping
+//   dp2[9 n_cam], dl2[3 n_pt]           D^2 = clamp(diag(J^T J), 1e-6, 1e32)
+//   PCG vectors (9 n_cam each) and the per-camera 9x9 preconditioner blocks
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace sqrtba {
+
+// Scalars of the PCG recursion, kept on the device so that a whole solve
+// can run without host round trips.
+struct PcgScalars {
+    float rho;        // r^T z
+    float q_prev;     // Q_{i-1} of the Nash-Sofer test
+    float gnorm;      // ||g||
+    float rnorm;      // ||r_i||
+    float lambda;     // LM damping of the current blocks
+    float eta;        // forcing tolerance
+    int32_t it;       // iterations done
+    int32_t max_it;
+    int32_t done;     // 1 once a stop rule fired
+    int32_t stop;     // reason (ba_pcg_report.stop_reason)
+};
+
+// Optional timing of the phases of the hot path with CUDA events.
+enum ProfSlot { PROF_LINEARIZE = 0, PROF_DAMP, PROF_PRECOND, PROF_MATVEC, PROF_PCG_UPDATE,
+                PROF_BACKSUB, PROF_COST, PROF_NSLOT };
+
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> events;   // pairs handed out by begin()
+    size_t next = 0;
+    struct Pending {
+        cudaEvent_t a, b;
+        int slot;
+    };
+    std::vector<Pending> pending;
+    double ms[8] = {};
+    int64_t count[8] = {};
+};
+
+struct Problem {
+    int32_t n_cam = 0, n_pt = 0;
+    int64_t n_obs = 0;
+    int32_t k_max = 0;
+    int32_t n_big = 0;               // landmarks with k > 32 (CTA-per-landmark K1)
+    int64_t sum_k2 = 0;
+    int64_t a_floats = 0, t_floats = 0;
+    ba_options opt{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int sm_count = 0;
+
+    // parameters
+    float *cams = nullptr, *pts = nullptr, *cand_cams = nullptr, *cand_pts = nullptr;
+    // sorted observations and index
+    int32_t *obs_cam_s = nullptr, *obs_pt_s = nullptr, *perm = nullptr;
+    float2* obs_xy_s = nullptr;
+    int32_t *pt_off = nullptr, *cam_off = nullptr, *cam_list = nullptr;
+    int64_t* a_off = nullptr;
+    int32_t* lm_by_k = nullptr;      // landmarks by decreasing k
+    int32_t* mv_begin = nullptr;     // matvec: first landmark of each CTA (grid + 1)
+    int mv_grid = 0;
+    // blocks
+    float *apool = nullptr, *tpool = nullptr, *cpool = nullptr, *rot = nullptr;
+    float *dp2 = nullptr, *dl2 = nullptr;
+    // PCG
+    float *g = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+    float *minv = nullptr, *mdiag = nullptr;
+    PcgScalars* pcg = nullptr;
+    PcgScalars* pcg_host = nullptr;  // pinned mirror
+    // step
+    float* dl = nullptr;
+    // reductions
+    double* partials = nullptr;      // per-block FP64 partial sums
+    double* dsum = nullptr;          // [0] cost, [1] model cost
+    double* dsum_host = nullptr;     // pinned mirror
+    uint32_t* err = nullptr;         // kernel error bits
+    int red_grid = 0;
+
+    // CUDA graph of a chunk of PCG iterations
+    cudaGraphExec_t pcg_graph = nullptr;
+    int pcg_graph_iters = 0;
+    bool capturing = false;
+    std::vector<cudaEvent_t> mv_events;  // 2 per captured PCG iteration (profiling)
+
+    // counters
+    Profiler prof;
+    int64_t launches = 0;      // kernels launched by the library
+    int64_t h2d_bytes = 0, d2h_bytes = 0;
+
+    // host-side LM state
+    bool linearized = false, damped = false, solved = false, backsubbed = false;
+    double lambda_damped = 0.0;
+    double lambda = 1e-4, nu = 2.0;
+    int32_t iteration = 0;
+    bool stopped = false;
+    double cost = 0.0;               // E at the current state (valid when linearized)
+    int64_t device_bytes = 0;
+    std::vector<void*> allocations;
+    std::string last_error;
+};
+
+// ---------------------------------------------------------------------------
+// launchers (each enqueues on p.stream; none synchronises)
+// ---------------------------------------------------------------------------
+// K0: validation and grouping (index.cu)
+void build_index(Problem& p, const int32_t* d_obs_cam, const int32_t* d_obs_pt,
+                 const double* d_obs_xy, const double* d_cams, const double* d_pts);
+// K1: damping diagonals, linearisation + Householder QR (linearize.cu)
+void launch_camera_diag(Problem& p);
+void launch_linearize(Problem& p);
+void launch_export_jacobians(Problem& p, float* r, float* jp, float* jl);
+// cost and state update (cost.cu)
+void launch_cost(Problem& p, bool candidate);
+void launch_candidate(Problem& p);
+// K2: landmark damping with Givens rotations (damp.cu)
+void launch_damp(Problem& p, bool undo_old, float lambda);
+// K3-K5: preconditioner, matvec, PCG (pcg.cu)
+void launch_precond_rhs(Problem& p);
+void launch_pcg_init(Problem& p);
+void launch_pcg_iteration(Problem& p, cudaEvent_t mv_begin = nullptr, cudaEvent_t mv_end = nullptr);
+void launch_matvec(Problem& p, const float* v, float* y, bool add_damping);
+// K6: back substitution + model cost (backsub.cu)
+void launch_backsub(Problem& p);
+// one-time kernel attributes (dynamic shared memory limits)
+void configure_linearize(Problem& p);
+void configure_matvec(Problem& p);
+
+// kernel launch counter (not counted while a graph is being captured)
+inline void count_launches(Problem& p, int n) {
+    if (!p.capturing) p.launches += n;
+}
+
+// device allocation helper that records the pointer for ba_destroy
+template <typename T>
+T* dalloc(Problem& p, int64_t n) {
+    void* ptr = nullptr;
+    size_t bytes = sizeof(T) * (size_t)(n > 0 ? n : 1);
+    BA_CUDA_TRY(cudaMalloc(&ptr, bytes));
+    p.allocations.push_back(ptr);
+    p.device_bytes += (int64_t)bytes;
+    return static_cast<T*>(ptr);
+}
+
+}  // namespace sqrtba
