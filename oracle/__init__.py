@@ -42,7 +42,8 @@ _i64 = ctypes.POINTER(ctypes.c_int64)
 class Options(ctypes.Structure):
     _fields_ = [("lambda0", ctypes.c_double), ("max_iters", ctypes.c_int32),
                 ("func_tol", ctypes.c_double), ("max_cg", ctypes.c_int32),
-                ("cg_eta", ctypes.c_double), ("dense", ctypes.c_int32)]
+                ("cg_eta", ctypes.c_double), ("dense", ctypes.c_int32),
+                ("target_cost", ctypes.c_double)]
 
 
 class Iter(ctypes.Structure):
@@ -229,8 +230,9 @@ def backsub_given(s, lam, dp, cams=None, pts=None):
     return dl.reshape(-1, 3), m.value
 
 
-def options(lambda0=1e-4, max_iters=50, func_tol=1e-6, max_cg=500, cg_eta=0.1, dense=False):
-    return Options(lambda0, max_iters, func_tol, max_cg, cg_eta, 1 if dense else 0)
+def options(lambda0=1e-4, max_iters=50, func_tol=1e-6, max_cg=500, cg_eta=0.1, dense=False,
+            target_cost=0.0):
+    return Options(lambda0, max_iters, func_tol, max_cg, cg_eta, 1 if dense else 0, target_cost)
 
 
 def linear_step(s, lam, dense=True, max_cg=500, cg_eta=0.1, cams=None, pts=None):

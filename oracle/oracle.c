@@ -757,6 +757,7 @@ typedef struct {
     int32_t max_cg;   /* 500 */
     double cg_eta;    /* 0.1 */
     int32_t dense;    /* 1: dense Cholesky RCS solve, 0: block-Jacobi PCG */
+    double target_cost; /* > 0: also stop at the first accepted cost <= target (timing hook) */
 } orc_options;
 
 /* One damped linear step at the given state: dp (9 n_cam), dl (3 n_pt),
@@ -842,6 +843,7 @@ int orc_lm(int32_t n_cam, double* cams, int32_t n_pt, double* pts, int64_t n_obs
             nu = 2.0;
             if (lambda < 1e-16) lambda = 1e-16;
             if (fabs(E - En) / E < opt->func_tol) break;
+            if (opt->target_cost > 0 && En <= opt->target_cost) break;
         } else {
             lambda *= nu;
             nu *= 2.0;

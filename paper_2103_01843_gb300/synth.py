@@ -12,10 +12,13 @@ code with it.  Axis-angle conversion goes through scipy.
 Recipe (the paper's preprocessing, Sec. 6.2, applied to synthetic data):
   1. ground truth in metres (cameras, points), per-config geometry below;
   2. observations = projection of ground truth + N(0, sigma_px^2) pixel noise;
-     a camera observes a point only if the point is in front of it and
-     projects inside the 1000 x 1000 px image (|u|, |v| < 500);
+     a camera observes a point only if the point is in front of it (depth >
+     0.5 m), projects inside the 1000 x 1000 px image (|u|, |v| < 500) and
+     lies inside the field of view (|P_x / P_z|, |P_y / P_z| < 1.2);
   3. initial state = ground truth perturbed (rotation Exp(N(0, 0.01^2 I)) R,
-     translation + N(0, 0.05^2), points + N(0, 0.1^2));
+     translation + N(0, 0.05^2), points + N(0, 0.1^2)); observations whose
+     point has depth < 1 m or |P_xy / P_z| >= 1.5 in the perturbed state are
+     removed, then landmarks with fewer than two observations (Sec. 6.2);
   4. gauge normalisation of the initial state: points centred at their
      per-axis median and scaled so that the median L1 deviation is 100;
      cameras transformed consistently (pixels are unchanged by this
@@ -76,13 +79,27 @@ def _project_mat(Rm, t, f, k1, k2, X):
 
     Returns (pixels (..., 2), depth (...,)) where depth = -P_z (> 0 in front).
     """
+    pix, depth, _ = _project_mat_p(Rm, t, f, k1, k2, X)
+    return pix, depth
+
+
+def _project_mat_p(Rm, t, f, k1, k2, X):
     P = np.einsum("...ij,...j->...i", Rm, X) + t
     depth = -P[..., 2]
     with np.errstate(divide="ignore", invalid="ignore"):
         p = P[..., :2] / depth[..., None]
     r2 = (p * p).sum(-1)
     d = 1.0 + k1 * r2 + k2 * r2 * r2
-    return (f * d)[..., None] * p, depth
+    return (f * d)[..., None] * p, depth, p
+
+
+def _visible(Rm, t, f, k1, k2, X):
+    """In front (depth > 0.5 m), inside the image, and inside the field of
+    view in normalised coordinates (|p| < 1.2), so that radial distortion
+    cannot fold a point far outside the view back into the image."""
+    pix, depth, p = _project_mat_p(Rm, t, f, k1, k2, X)
+    with np.errstate(invalid="ignore"):
+        return (depth > 0.5) & (np.abs(pix) < IMAGE_HALF).all(-1) & (np.abs(p) < 1.2).all(-1)
 
 
 def _look_at(center, target, up=np.array([0.0, 0.0, 1.0])):
@@ -164,9 +181,7 @@ def _gt_ring(rng, n_cam, n_pt, radius, box_half, k_sampler, window=None,
             sel = _choose_subsets(rng, np.ones((m, win), bool), kt)
             rows, cols = np.nonzero(sel)
             cams = (start[rows] + cols) % n_cam
-            pix, depth = _project_mat(R[cams], t[cams], f[cams], k1[cams],
-                                      k2[cams], X[idx[rows]])
-            ok_pair = (depth > 0.5) & (np.abs(pix) < IMAGE_HALF).all(-1)
+            ok_pair = _visible(R[cams], t[cams], f[cams], k1[cams], k2[cams], X[idx[rows]])
             ok = np.ones(m, bool)
             ok[rows[~ok_pair]] = False
             keep = ok[rows]
@@ -206,9 +221,8 @@ def _gt_walk(rng, n_cam, n_pt, k_sampler, window=80):
             cand = anchor[:, None] + np.arange(-window, window + 1)[None, :]
             inr = (cand >= 0) & (cand < n_cam)
             cand = np.clip(cand, 0, n_cam - 1)
-            pix, dep = _project_mat(R[cand], t[cand], f[cand], k1[cand],
-                                    k2[cand], X[idx][:, None, :])
-            valid = inr & (dep > 0.5) & (np.abs(pix) < IMAGE_HALF).all(-1)
+            valid = inr & _visible(R[cand], t[cand], f[cand], k1[cand], k2[cand],
+                                   X[idx][:, None, :])
             sel = _choose_subsets(rng, valid, k_sampler(rng, m))
             ok = sel.sum(1) >= 2
             rows, cols = np.nonzero(sel & ok[:, None])
@@ -257,6 +271,23 @@ def _finish(rng, name, seed, R, t, f, k1, k2, X, obs_cam, obs_pt,
         X0 = X + rng.normal(0.0, 0.1, X.shape)
     else:
         R0, t0, X0 = R.copy(), t.copy(), X.copy()
+
+    # Sec. 6.2: drop observations with small or negative z in the camera frame
+    # of the perturbed state (read as depth < 1 m or |P_xy / P_z| >= 1.5), then
+    # landmarks left with fewer than two observations (points re-indexed)
+    _, dep0, p0 = _project_mat_p(R0[obs_cam], t0[obs_cam], f[obs_cam], k1[obs_cam],
+                                 k2[obs_cam], X0[obs_pt])
+    with np.errstate(invalid="ignore"):
+        keep = (dep0 > 1.0) & (np.abs(p0) < 1.5).all(-1)
+    cnt = np.bincount(obs_pt[keep], minlength=X.shape[0])
+    keep &= cnt[obs_pt] >= 2
+    if not keep.all():
+        obs_cam, obs_pt, obs_xy = obs_cam[keep], obs_pt[keep], obs_xy[keep]
+        used = np.unique(obs_pt)
+        remap = np.full(X.shape[0], -1, np.int64)
+        remap[used] = np.arange(used.size)
+        obs_pt = remap[obs_pt].astype(np.int32)
+        X, X0 = X[used], X0[used]
 
     # gauge normalisation from the initial state
     center = np.median(X0, axis=0)
