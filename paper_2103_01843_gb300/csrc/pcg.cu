@@ -60,7 +60,7 @@ k_precond_rhs(int n_cam, const int32_t* __restrict__ cam_off, const int32_t* __r
               const int32_t* __restrict__ obs_pt_s, const int32_t* __restrict__ pt_off,
               const int64_t* __restrict__ a_off, const float* __restrict__ apool,
               const float* __restrict__ cpool, const float* __restrict__ dp2,
-              const PcgScalars* __restrict__ S, float* __restrict__ mdiag, float* __restrict__ minv,
+              const float lam, float* __restrict__ mdiag, float* __restrict__ minv,
               float* __restrict__ g, uint32_t* err) {
     __shared__ float part[PC_WARPS][54];
     __shared__ float tot[54];
@@ -110,7 +110,6 @@ k_precond_rhs(int n_cam, const int32_t* __restrict__ cam_off, const int32_t* __r
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const float lam = S->lambda;
         float M[81], Mi[81];
         int t = 0;
         for (int u = 0; u < 9; ++u)
@@ -392,7 +391,7 @@ void configure_matvec(Problem& p) {
 void launch_precond_rhs(Problem& p) {
     count_launches(p, 1);
     k_precond_rhs<<<p.n_cam, 32 * PC_WARPS, 0, p.stream>>>(p.n_cam, p.cam_off, p.cam_list, p.obs_pt_s, p.pt_off,
-                                                          p.a_off, p.apool, p.cpool, p.dp2, p.pcg, p.mdiag,
+                                                          p.a_off, p.apool, p.cpool, p.dp2, (float)p.lambda_damped, p.mdiag,
                                                           p.minv, p.g, p.err);
     BA_LAUNCH_CHECK();
 }
