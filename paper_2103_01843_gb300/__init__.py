@@ -109,6 +109,7 @@ _SIGS = {
     "ba_get_info": [_P, ctypes.POINTER(Info)],
     "ba_set_profiling": [_P, ctypes.c_int32],
     "ba_get_profile": [_P, ctypes.POINTER(Profile)],
+    "ba_eval_cost_noalloc": [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P, _P, ctypes.c_int64, _P, _P],
     "ba_debug_export_order": [_P, _i32, _i64, _i64, _i32],
     "ba_debug_export_landmark": [_P, ctypes.c_int32, ctypes.c_int32, _f, _f, _f, _f, _i32],
     "ba_debug_export_damping": [_P, _f, _f],
@@ -155,6 +156,26 @@ def default_options(**kw):
 
 def _ptr(a, t):
     return a.ctypes.data_as(t)
+
+
+def _devptr(x):
+    """Device address of a tensor-like object (data_ptr()) or an int."""
+    return int(x.data_ptr()) if hasattr(x, "data_ptr") else int(x)
+
+
+def eval_cost_noalloc(cams, pts, obs_cam, obs_pt, obs_xy, out, n_cam=None, n_pt=None, n_obs=None, stream=None):
+    """ba_eval_cost_noalloc: E of device-resident FP32 data written to the
+    device double `out`, with no device allocation.  Arguments are CUDA
+    tensors (or raw device addresses with explicit sizes); enqueued on
+    `stream` without synchronising."""
+    n_cam = n_cam if n_cam is not None else cams.shape[0]
+    n_pt = n_pt if n_pt is not None else pts.shape[0]
+    n_obs = n_obs if n_obs is not None else obs_cam.shape[0]
+    rc = lib().ba_eval_cost_noalloc(_devptr(cams), int(n_cam), _devptr(pts), int(n_pt), _devptr(obs_cam),
+                                    _devptr(obs_pt), _devptr(obs_xy), int(n_obs), _devptr(out),
+                                    _P(stream) if stream else None)
+    if rc != BA_OK:
+        raise BAError(rc, lib().ba_last_error(None).decode())
 
 
 class Problem:

@@ -307,6 +307,11 @@ void do_lm_step(Problem& p, ba_lm_report* rep) {
 
 }  // namespace
 
+namespace sqrtba {
+// failure text of calls without a handle, read back by ba_last_error(NULL)
+void set_create_error(const std::string& m) { g_create_error = m; }
+}  // namespace sqrtba
+
 extern "C" {
 
 void ba_default_options(ba_options* o) {
