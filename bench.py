@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="solve", choices=["solve", "matvec"],
+                    help="matvec: only repeat the PCG matvec on a linearised, damped problem "
+                         "(a short run for kernel profiling; prints no bench line)")
     return ap.parse_args()
 
 
@@ -357,8 +360,27 @@ def run_ours(args):
     return 0
 
 
+def run_matvec_only(args):
+    """Linearise and damp once, then `steps` PCG matvecs (kernel profiling)."""
+    import numpy as np
+    import torch
+    import paper_2103_01843_gb300 as sq
+    from paper_2103_01843_gb300.synth import make_scene
+    torch.cuda.set_device(0)
+    scene = make_scene(args.config, args.seed)
+    with sq.Problem.from_scene(scene, stream=torch.cuda.current_stream().cuda_stream) as p:
+        p.linearize()
+        p.marginalize_qr(1e-4)
+        v = np.random.default_rng(0).normal(size=9 * scene.n_cam).astype(np.float32)
+        for _ in range(args.warmup + args.steps):
+            p.matvec(v)
+    return 0
+
+
 def main():
     args = parse()
+    if args.mode == "matvec":
+        return run_matvec_only(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -15,7 +15,6 @@
 
 namespace sqrtba {
 int linearize_k_limit();
-int matvec_ctas_per_sm();
 }  // namespace sqrtba
 
 using namespace sqrtba;
@@ -372,7 +371,9 @@ ba_status ba_create(const double* cams, int32_t n_cam, const double* pts, int32_
         p.cam_list = dalloc<int32_t>(p, n_obs);
         p.a_off = dalloc<int64_t>(p, n_pt + 1);
         p.lm_by_k = dalloc<int32_t>(p, n_pt);
-        p.mv_begin = dalloc<int32_t>(p, p.mv_grid + 1);
+        p.mv_cam = dalloc<int32_t>(p, n_obs + 8);
+        p.c_off = dalloc<int32_t>(p, n_pt + 1);
+        p.cam_list_st = dalloc<int32_t>(p, n_obs);
         p.err = dalloc<uint32_t>(p, 4);
         p.dsum = dalloc<double>(p, 4);
         p.pcg = dalloc<PcgScalars>(p, 1);
@@ -404,11 +405,12 @@ ba_status ba_create(const double* cams, int32_t n_cam, const double* pts, int32_
         build_index(p, d_oc, d_op, d_xy, d_cams, d_pts);
         require(p.k_max <= linearize_k_limit(), BA_ERR_INVALID_ARG,
                 "a landmark has more observations than the supported maximum (900)");
+        plan_matvec(p);
 
         p.apool = dalloc<float>(p, p.a_floats);
         p.t_floats = 3 * (9 * n_obs + 4 * (int64_t)n_pt);
         p.tpool = dalloc<float>(p, p.t_floats);
-        p.cpool = dalloc<float>(p, 2 * n_obs);
+        p.cpool = dalloc<float>(p, 2 * n_obs + 8);
         p.rot = dalloc<float>(p, 12 * (int64_t)n_pt);
         p.dp2 = dalloc<float>(p, 9 * (int64_t)n_cam);
         p.dl2 = dalloc<float>(p, 3 * (int64_t)n_pt);
@@ -421,6 +423,7 @@ ba_status ba_create(const double* cams, int32_t n_cam, const double* pts, int32_
         p.q = dalloc<float>(p, nv);
         p.minv = dalloc<float>(p, 81 * (int64_t)n_cam);
         p.mdiag = dalloc<float>(p, 81 * (int64_t)n_cam);
+        p.prec = dalloc<float>(p, 54 * n_obs);
         p.dl = dalloc<float>(p, 3 * (int64_t)n_pt);
         p.partials = dalloc<double>(p, std::max<int64_t>((n_pt + 3) / 4 + 1, p.red_grid + 1));
         BA_CUDA_TRY(cudaMemsetAsync(p.x, 0, sizeof(float) * nv, p.stream));
@@ -667,10 +670,11 @@ ba_status ba_debug_export_landmark(ba_problem* h, int32_t j, int32_t k_cap, floa
     Problem& p = h->p;
     require(j >= 0 && j < p.n_pt, BA_ERR_INVALID_ARG, "landmark index out of range");
     require(p.linearized, BA_ERR_STATE, "not linearised");
-    int32_t off[2];
+    int32_t off[2], coff = 0;
     int64_t aoff = 0;
     d2h(p, off, p.pt_off + j, 2);
     d2h(p, &aoff, p.a_off + j, 1);
+    d2h(p, &coff, p.c_off + j, 1);
     sync(p);
     const int k = off[1] - off[0];
     if (k_out) *k_out = k;
@@ -678,7 +682,7 @@ ba_status ba_debug_export_landmark(ba_problem* h, int32_t j, int32_t k_cap, floa
     const int64_t ncol = 9 * (int64_t)k;
     if (top) d2h(p, top, p.tpool + top_offset(off[0], j), 3 * (ncol + 4));
     if (a) d2h(p, a, p.apool + aoff, 2 * (int64_t)k * ncol);
-    if (c) d2h(p, c, p.cpool + 2 * (int64_t)off[0], 2 * (int64_t)k);
+    if (c) d2h(p, c, p.cpool + coff, 2 * (int64_t)k);
     if (rot) d2h(p, rot, p.rot + 12 * (int64_t)j, 12);
     sync(p);
     return BA_OK;

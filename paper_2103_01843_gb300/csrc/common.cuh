@@ -43,6 +43,7 @@ enum : uint32_t {
     ERRBIT_FEWOBS = 1u << 2,     // landmark with < 2 observations
     ERRBIT_DUPLICATE = 1u << 3,  // duplicate (landmark, camera) pair
     ERRBIT_PRECOND = 1u << 4,    // a preconditioner block was not positive definite
+    ERRBIT_TIMEOUT = 1u << 5,    // a bounded device-side wait gave up
 };
 
 // ---------------------------------------------------------------------------

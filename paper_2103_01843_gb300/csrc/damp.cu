@@ -23,6 +23,7 @@ __constant__ int kRotD[6] = {0, 0, 0, 1, 1, 2};
 __global__ void __launch_bounds__(128)
 k_damp(int n_pt, const int32_t* __restrict__ pt_off, const int64_t* __restrict__ a_off,
        float* __restrict__ tpool, float* __restrict__ apool, float* __restrict__ cpool,
+       const int32_t* __restrict__ c_off,
        const float* __restrict__ dl2, float* __restrict__ rot, float sqrt_lambda, int undo) {
     __shared__ float sh_rot[4][24];  // per warp: old (12) and new (12) rotations
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -32,7 +33,7 @@ k_damp(int n_pt, const int32_t* __restrict__ pt_off, const int64_t* __restrict__
     const int ncol = 9 * k, nr = 2 * k;
     float* top = tpool + top_offset(s0, j);
     float* damp = apool + a_off[j] + (int64_t)(nr - 3) * ncol;  // damping rows of A_j
-    float* cd = cpool + 2 * (int64_t)s0 + (nr - 3);              // their residual entries
+    float* cd = cpool + c_off[j] + (nr - 3);                     // their residual entries
     float* rs = sh_rot[w];
 
     if (lane == 0) {
@@ -134,7 +135,8 @@ k_damp(int n_pt, const int32_t* __restrict__ pt_off, const int64_t* __restrict__
 void launch_damp(Problem& p, bool undo_old, float lambda) {
     count_launches(p, 1);
     k_damp<<<ceil_div((int64_t)p.n_pt * 32, 128), 128, 0, p.stream>>>(
-        p.n_pt, p.pt_off, p.a_off, p.tpool, p.apool, p.cpool, p.dl2, p.rot, sqrtf(lambda), undo_old ? 1 : 0);
+        p.n_pt, p.pt_off, p.a_off, p.tpool, p.apool, p.cpool, p.c_off, p.dl2, p.rot, sqrtf(lambda),
+        undo_old ? 1 : 0);
     BA_LAUNCH_CHECK();
 }
 

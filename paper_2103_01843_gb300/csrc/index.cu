@@ -230,12 +230,10 @@ __global__ void k_tile_place(const int32_t* __restrict__ cam_s, int64_t n, int n
 }
 
 // --- block sizes and work lists ---------------------------------------------
-__global__ void k_block_sizes(int n_pt, const int32_t* __restrict__ kcount, int64_t* __restrict__ asz,
-                              int64_t* __restrict__ k2) {
+__global__ void k_ksq(int n_pt, const int32_t* __restrict__ kcount, int64_t* __restrict__ k2) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_pt) return;
     const int64_t k = kcount[j];
-    asz[j] = pad4(18 * k * k);
     k2[j] = k * k;
 }
 
@@ -253,22 +251,34 @@ __global__ void k_kscatter(int n_pt, const int32_t* __restrict__ kcount, int kma
     out[koff[b] + atomicAdd(&cursor[b], 1)] = j;
 }
 
-// first landmark of each matvec CTA: balanced by A-pool floats
-__global__ void k_partition(int n_pt, const int64_t* __restrict__ a_off, int grid,
-                            int32_t* __restrict__ begin) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b > grid) return;
-    if (b == grid) {
-        begin[b] = n_pt;
-        return;
+// Block offsets in storage order (decreasing k, then the order of lm_by_k)
+// and the cameras of every observation in that order (the matvec's stream).
+__global__ void k_storage(int n_pt, const int32_t* __restrict__ order, const int32_t* __restrict__ kcount,
+                          int kmax, const int32_t* __restrict__ ko, const int64_t* __restrict__ run_off,
+                          const int64_t* __restrict__ run_co, const int32_t* __restrict__ pt_off,
+                          const int32_t* __restrict__ obs_cam_s, int64_t* __restrict__ a_off,
+                          int32_t* __restrict__ mv_cam, int32_t* __restrict__ c_off,
+                          int32_t* __restrict__ obs_store) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_pt) return;
+    const int j = order[i];
+    const int64_t k = kcount[j];
+    const int b = kmax - (int)k;
+    const int64_t idx = i - ko[b];
+    a_off[j] = run_off[b] + idx * pad4(18 * k * k);
+    const int64_t co = run_co[b] + idx * k;
+    const int s0 = pt_off[j];
+    c_off[j] = (int32_t)(2 * co);
+    for (int s = 0; s < k; ++s) {
+        mv_cam[co + s] = obs_cam_s[s0 + s];
+        obs_store[s0 + s] = (int32_t)(co + s);
     }
-    const int64_t target = (a_off[n_pt] * (int64_t)b) / grid;
-    int lo = 0, hi = n_pt;  // first j with a_off[j] >= target
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (a_off[mid] < target) lo = mid + 1; else hi = mid;
-    }
-    begin[b] = lo;
+}
+
+__global__ void k_map_list(int64_t n, const int32_t* __restrict__ list, const int32_t* __restrict__ map,
+                           int32_t* __restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = map[list[e]];
 }
 
 }  // namespace
@@ -340,39 +350,62 @@ void build_index(Problem& p, const int32_t* d_oc, const int32_t* d_op, const dou
                                                               (int)n_tiles, hist, p.cam_list);
     BA_LAUNCH_CHECK();
 
-    // block offsets
-    int64_t* asz = (int64_t*)tmp_alloc(sizeof(int64_t) * (p.n_pt + 1));
+    // sum of k^2 (reported), error checks and k_max
     int64_t* k2 = (int64_t*)tmp_alloc(sizeof(int64_t) * (p.n_pt + 1));
     int64_t* k2off = (int64_t*)tmp_alloc(sizeof(int64_t) * (p.n_pt + 1));
-    k_block_sizes<<<ceil_div(p.n_pt, 256), 256, 0, st>>>(p.n_pt, kcount, asz, k2);
-    exclusive_scan(asz, p.n_pt, p.a_off, scan_tmp, st);
+    k_ksq<<<ceil_div(p.n_pt, 256), 256, 0, st>>>(p.n_pt, kcount, k2);
     exclusive_scan(k2, p.n_pt, k2off, scan_tmp, st);
 
     int32_t kinfo[2] = {0, 0};
-    int64_t totals[2] = {0, 0};
+    int64_t sumk2 = 0;
     BA_CUDA_TRY(cudaMemcpyAsync(&herr, p.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     BA_CUDA_TRY(cudaMemcpyAsync(kinfo, kmax_d, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    BA_CUDA_TRY(cudaMemcpyAsync(&totals[0], p.a_off + p.n_pt, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    BA_CUDA_TRY(cudaMemcpyAsync(&totals[1], k2off + p.n_pt, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    BA_CUDA_TRY(cudaMemcpyAsync(&sumk2, k2off + p.n_pt, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     BA_CUDA_TRY(cudaStreamSynchronize(st));
     if (herr & ERRBIT_FEWOBS) throw Error{BA_ERR_INVALID_ARG, "a landmark has fewer than two observations"};
     if (herr & ERRBIT_DUPLICATE) throw Error{BA_ERR_INVALID_ARG, "duplicate (camera, landmark) observation"};
     const int32_t kmax = kinfo[0];
     p.k_max = kmax;
     p.n_big = kinfo[1];
-    p.a_floats = totals[0];
-    p.sum_k2 = totals[1];
+    p.sum_k2 = sumk2;
 
-    // landmarks by decreasing k (work order for the per-landmark kernels)
+    // landmarks by decreasing k; the work order of the per-landmark kernels
+    // and the storage order of the landmark blocks (equal-k blocks adjacent)
     int32_t* kh = (int32_t*)tmp_alloc(sizeof(int32_t) * (kmax + 2));
     int32_t* ko = (int32_t*)tmp_alloc(sizeof(int32_t) * (kmax + 2));
     BA_CUDA_TRY(cudaMemsetAsync(kh, 0, sizeof(int32_t) * (kmax + 2), st));
     k_khist<<<ceil_div(p.n_pt, 256), 256, 0, st>>>(p.n_pt, kcount, kmax, kh);
     exclusive_scan(kh, kmax + 1, ko, scan_tmp, st);
+    p.k_run_count.assign(kmax + 1, 0);
+    BA_CUDA_TRY(cudaMemcpyAsync(p.k_run_count.data(), kh, sizeof(int32_t) * (kmax + 1), cudaMemcpyDeviceToHost, st));
     BA_CUDA_TRY(cudaMemsetAsync(kh, 0, sizeof(int32_t) * (kmax + 2), st));
     k_kscatter<<<ceil_div(p.n_pt, 256), 256, 0, st>>>(p.n_pt, kcount, kmax, ko, kh, p.lm_by_k);
-    k_partition<<<ceil_div(p.mv_grid + 1, 256), 256, 0, st>>>(p.n_pt, p.a_off, p.mv_grid, p.mv_begin);
     BA_LAUNCH_CHECK();
+    BA_CUDA_TRY(cudaStreamSynchronize(st));
+
+    // run b holds the landmarks with k = kmax - b: block offsets (floats) and
+    // offsets into the camera stream of the matvec (one int per observation)
+    p.run_off.assign(kmax + 2, 0);
+    p.run_co.assign(kmax + 2, 0);
+    for (int b = 0; b <= kmax; ++b) {
+        const int64_t k = kmax - b, cnt = p.k_run_count[b];
+        p.run_off[b + 1] = p.run_off[b] + cnt * pad4(18 * k * k);
+        p.run_co[b + 1] = p.run_co[b] + cnt * k;
+    }
+    p.a_floats = p.run_off[kmax + 1];
+    int64_t* d_run = (int64_t*)tmp_alloc(sizeof(int64_t) * 2 * (kmax + 2));
+    BA_CUDA_TRY(cudaMemcpyAsync(d_run, p.run_off.data(), sizeof(int64_t) * (kmax + 2), cudaMemcpyHostToDevice, st));
+    BA_CUDA_TRY(cudaMemcpyAsync(d_run + kmax + 2, p.run_co.data(), sizeof(int64_t) * (kmax + 2),
+                                cudaMemcpyHostToDevice, st));
+    BA_CUDA_TRY(cudaMemcpyAsync(p.a_off + p.n_pt, &p.run_off[kmax + 1], sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    int32_t* obs_store = (int32_t*)tmp_alloc(sizeof(int32_t) * n);
+    k_storage<<<ceil_div(p.n_pt, 256), 256, 0, st>>>(p.n_pt, p.lm_by_k, kcount, kmax, ko, d_run, d_run + kmax + 2,
+                                                     p.pt_off, p.obs_cam_s, p.a_off, p.mv_cam, p.c_off, obs_store);
+    k_map_list<<<gsz, TPB, 0, st>>>(n, p.cam_list, obs_store, p.cam_list_st);
+    BA_LAUNCH_CHECK();
+    // observations of landmarks with k > 21 (they come first in storage order)
+    p.n_obs_direct_big = 0;
+    for (int b = 0; b <= kmax && kmax - b > 21; ++b) p.n_obs_direct_big = p.run_co[b + 1];
     BA_CUDA_TRY(cudaStreamSynchronize(st));
 }
 

@@ -29,8 +29,26 @@ constexpr int BIG_TEAM = 256;  // threads per CTA for k > K_WARP
 
 __host__ __device__ constexpr int lin_smem_floats(int k) { return 59 * k + 24; }
 
+// A team of TEAM threads factors one landmark block.  TEAM = 8 or 16: a
+// sub-warp team (segmented shuffles), several landmarks per warp; 32: a warp;
+// BIG_TEAM: a CTA.  Every team of a warp runs the same sequence of shuffles
+// and syncs whatever its k, so teams of one warp may hold different k.
 template <int TEAM>
-struct Team;
+struct Team {
+    static_assert(TEAM == 8 || TEAM == 16, "sub-warp team width");
+    __device__ static int rank() { return threadIdx.x & (TEAM - 1); }
+    __device__ static void sync() { __syncwarp(); }
+    __device__ static float tsum(float v) {
+#pragma unroll
+        for (int o = TEAM / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        return v;
+    }
+    __device__ static void sum3(float& a, float& b, float& c, float*) {
+        a = tsum(a);
+        b = tsum(b);
+        c = tsum(c);
+    }
+};
 
 template <>
 struct Team<32> {
@@ -81,12 +99,14 @@ struct LinArgs {
     float* apool;
     float* tpool;
     float* cpool;
+    const int32_t* c_off;
     float* dl2;
 };
 
 // Linearise and marginalise landmark j; sm holds lin_smem_floats(k) floats.
+// write = false runs the same steps without storing (an idle team of a warp).
 template <int TEAM>
-__device__ void marginalize_landmark(const LinArgs& A, int j, float* sm, float* red) {
+__device__ void marginalize_landmark(const LinArgs& A, int j, float* sm, float* red, bool write = true) {
     using T = Team<TEAM>;
     const int rank = T::rank();
     const int s0 = A.pt_off[j];
@@ -126,7 +146,7 @@ __device__ void marginalize_landmark(const LinArgs& A, int j, float* sm, float* 
             d2 += L[3 * i + 2] * L[3 * i + 2];
         }
         T::sum3(d0, d1, d2, red);
-        if (rank == 0) {
+        if (rank == 0 && write) {
             A.dl2[3 * j] = fminf(fmaxf(d0, 1e-6f), 1e32f);
             A.dl2[3 * j + 1] = fminf(fmaxf(d1, 1e-6f), 1e32f);
             A.dl2[3 * j + 2] = fminf(fmaxf(d2, 1e-6f), 1e32f);
@@ -237,7 +257,7 @@ __device__ void marginalize_landmark(const LinArgs& A, int j, float* sm, float* 
     const int64_t total = (int64_t)nr * ncol;
     int e = rank;
     int i = e / ncol, col = e - i * ncol;
-    for (; e < total; e += TEAM) {
+    for (; write && e < total; e += TEAM) {
         const int s = col / 9;
         const float mval = (s == (i >> 1)) ? JP[i * 9 + (col - 9 * s)] : 0.f;
         const float out = mval - (V[3 * i] * W[col] + V[3 * i + 1] * W[(ncol + 1) + col] +
@@ -251,7 +271,7 @@ __device__ void marginalize_landmark(const LinArgs& A, int j, float* sm, float* 
         }
     }
     // residual column and R1
-    for (int ii = rank; ii < nr; ii += TEAM) {
+    for (int ii = rank; write && ii < nr; ii += TEAM) {
         const float out = RV[ii] - (V[3 * ii] * W[ncol] + V[3 * ii + 1] * W[(ncol + 1) + ncol] +
                                     V[3 * ii + 2] * W[2 * (ncol + 1) + ncol]);
         if (ii < 3) {
@@ -261,19 +281,24 @@ __device__ void marginalize_landmark(const LinArgs& A, int j, float* sm, float* 
             row[2] = L[3 * ii + 2];
             row[3] = out;
         } else {
-            A.cpool[2 * (int64_t)s0 + (ii - 3)] = out;
+            A.cpool[A.c_off[j] + (ii - 3)] = out;
         }
     }
 }
 
+// landmarks order[first .. first + count) with k <= KMAX, one team of W lanes each
+template <int W, int KMAX>
 __global__ void __launch_bounds__(32 * LIN_WARPS)
-k_linearize_warp(LinArgs A, const int32_t* __restrict__ order, int first, int count) {
+k_linearize_team(LinArgs A, const int32_t* __restrict__ order, int first, int count) {
     extern __shared__ float smem[];
-    const int w = threadIdx.x >> 5;
-    const int idx = blockIdx.x * LIN_WARPS + w;
-    if (idx >= count) return;
-    float* sm = smem + w * lin_smem_floats(K_WARP);
-    marginalize_landmark<32>(A, order[first + idx], sm, nullptr);
+    constexpr int TPW = 32 / W;
+    const int w = threadIdx.x >> 5, tm = (threadIdx.x & 31) / W;
+    const int idx0 = (blockIdx.x * LIN_WARPS + w) * TPW;
+    if (idx0 >= count) return;  // whole warp
+    const int idx = idx0 + tm;
+    const bool active = idx < count;
+    float* sm = smem + (w * TPW + tm) * lin_smem_floats(KMAX);
+    marginalize_landmark<W>(A, order[first + (active ? idx : idx0)], sm, nullptr, active);
 }
 
 __global__ void __launch_bounds__(BIG_TEAM)
@@ -333,11 +358,28 @@ __global__ void k_export_jacobians(int64_t n_obs, const float* __restrict__ cams
 
 int linearize_k_limit() { return 900; }
 
+// landmark counts with k in (lo, hi] (lm_by_k is ordered by decreasing k)
+int count_k(const Problem& p, int lo, int hi) {
+    int n = 0;
+    for (int b = 0; b <= p.k_max; ++b) {
+        const int k = p.k_max - b;
+        if (k > lo && k <= hi) n += p.k_run_count[b];
+    }
+    return n;
+}
+
+template <int W, int KMAX>
+constexpr int team_smem_bytes() { return (int)sizeof(float) * lin_smem_floats(KMAX) * LIN_WARPS * (32 / W); }
+
 void configure_linearize(Problem& p) {
     const int sb = (int)(sizeof(float) * lin_smem_floats(std::max(p.k_max, K_WARP)));
     BA_CUDA_TRY(cudaFuncSetAttribute(k_linearize_block, cudaFuncAttributeMaxDynamicSharedMemorySize, sb));
-    const int sw = (int)(sizeof(float) * lin_smem_floats(K_WARP) * LIN_WARPS);
-    BA_CUDA_TRY(cudaFuncSetAttribute(k_linearize_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, sw));
+    BA_CUDA_TRY(cudaFuncSetAttribute(k_linearize_team<32, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     team_smem_bytes<32, 32>()));
+    BA_CUDA_TRY(cudaFuncSetAttribute(k_linearize_team<16, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     team_smem_bytes<16, 8>()));
+    BA_CUDA_TRY(cudaFuncSetAttribute(k_linearize_team<8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     team_smem_bytes<8, 4>()));
 }
 
 void launch_camera_diag(Problem& p) {
@@ -348,22 +390,35 @@ void launch_camera_diag(Problem& p) {
 }
 
 void launch_linearize(Problem& p) {
-    count_launches(p, (p.n_big > 0) + (p.n_pt - p.n_big > 0));
     LinArgs A{p.cams, p.pts, p.obs_cam_s, p.obs_xy_s, p.pt_off, p.a_off,
-              p.apool, p.tpool, p.cpool, p.dl2};
-    const int n_big = p.n_big;
+              p.apool, p.tpool, p.cpool, p.c_off, p.dl2};
+    // segments of lm_by_k: k > 32 | 9..32 | 5..8 | 2..4
+    const int n_big = p.n_big, n32 = count_k(p, 8, 32), n16 = count_k(p, 4, 8), n8 = count_k(p, 1, 4);
+    int first = 0;
     if (n_big > 0) {
         const size_t sm = sizeof(float) * lin_smem_floats(p.k_max);
         k_linearize_block<<<n_big, BIG_TEAM, sm, p.stream>>>(A, p.lm_by_k, n_big);
-        BA_LAUNCH_CHECK();
+        count_launches(p, 1);
     }
-    const int n_small = p.n_pt - n_big;
-    if (n_small > 0) {
-        const size_t sm = sizeof(float) * lin_smem_floats(K_WARP) * LIN_WARPS;
-        k_linearize_warp<<<ceil_div(n_small, LIN_WARPS), 32 * LIN_WARPS, sm, p.stream>>>(A, p.lm_by_k, n_big,
-                                                                                          n_small);
-        BA_LAUNCH_CHECK();
+    first += n_big;
+    if (n32 > 0) {
+        k_linearize_team<32, 32><<<ceil_div(n32, LIN_WARPS), 32 * LIN_WARPS, team_smem_bytes<32, 32>(), p.stream>>>(
+            A, p.lm_by_k, first, n32);
+        count_launches(p, 1);
     }
+    first += n32;
+    if (n16 > 0) {
+        k_linearize_team<16, 8><<<ceil_div(n16, 2 * LIN_WARPS), 32 * LIN_WARPS, team_smem_bytes<16, 8>(), p.stream>>>(
+            A, p.lm_by_k, first, n16);
+        count_launches(p, 1);
+    }
+    first += n16;
+    if (n8 > 0) {
+        k_linearize_team<8, 4><<<ceil_div(n8, 4 * LIN_WARPS), 32 * LIN_WARPS, team_smem_bytes<8, 4>(), p.stream>>>(
+            A, p.lm_by_k, first, n8);
+        count_launches(p, 1);
+    }
+    BA_LAUNCH_CHECK();
 }
 
 void launch_export_jacobians(Problem& p, float* r, float* jp, float* jl) {

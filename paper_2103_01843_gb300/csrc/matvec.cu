@@ -1,0 +1,630 @@
+// K4: the PCG matvec of Eq. cg_mult without forming H~:
+//     y += sum_j P_j^T A_j^T (A_j P_j v)
+// where A_j = Q^T J_p below R1 (2k x 9k, FP32, stored in the landmark block,
+// Sec. 5.1-5.3) and P_j gathers the landmark's k camera sub-vectors.
+//
+// HBM-bound: every block is read once per launch (72 k^2 bytes per landmark).
+// Blocks are stored by decreasing k, so equal-k blocks are adjacent.  The
+// host plans tiles of the block pool (runs of equal-k blocks up to 32 KB, or
+// 4-row-aligned row ranges of one block when a block is larger); each CTA
+// (one per SM) streams its contiguous range of tiles through a 4-stage ring
+// in shared memory with bulk asynchronous copies (cp.async.bulk + mbarrier),
+// one producer thread and 15 consumer warps.  A tile rarely needs every
+// consumer warp, so successive tiles are handed to successive groups of warps.
+//   small tiles (k <= 21): teams of 8/16/32 lanes, one block per team, code
+//     specialised per k; per row u_r = A_j[r,:] v_j (team shuffle reduction)
+//     and y_j += u_r A_j[r,:] (single pass over the block);
+//   big tiles (21 < k <= 222): u for the tile's rows, then column sums;
+//   k > 222: read directly from global memory (two passes).
+// y accumulates in a per-CTA shared copy flushed once per CTA (one atomic per
+// touched entry).  Every wait is bounded (2 s by %globaltimer); on a timeout
+// the kernel raises ERRBIT_TIMEOUT, waits for its own copies and returns.
+#include <algorithm>
+#include <vector>
+
+#include "problem.cuh"
+
+namespace sqrtba {
+
+namespace {
+
+constexpr int MV_STAGES = 4;
+constexpr int MV_STAGE_A = 32768;   // bytes of blocks per stage
+constexpr int MV_STAGE_C = 1024;    // bytes of camera indices per stage
+// Registers are split over the SM's four sub-partitions (16K each) and the
+// CTA's 16 warps spread four to a sub-partition: 128 registers per thread.
+constexpr int MV_CONSUMERS = 15;    // consumer warps per CTA
+constexpr int MV_THREADS = 32 * (MV_CONSUMERS + 1);
+constexpr int MV_KSMALL = 21;       // whole blocks, specialised per k
+constexpr int MV_KBIG = 222;        // row ranges of 4 rows (36k * 4 <= 32 KB)
+constexpr int MV_UMAX = 45;         // rows of one big tile (multiple of MV_CONSUMERS)
+constexpr uint64_t MV_WAIT_NS = 2000000000ull;
+
+constexpr int MV_STAGE_R = 2048;    // bytes of c_j values per stage (preconditioner mode)
+constexpr int SM_STAGE_C_OFF = MV_STAGES * MV_STAGE_A;
+constexpr int SM_STAGE_R_OFF = SM_STAGE_C_OFF + MV_STAGES * MV_STAGE_C;
+constexpr int SM_U_OFF = SM_STAGE_R_OFF + MV_STAGES * MV_STAGE_R;
+constexpr int SM_BAR_OFF = SM_U_OFF + MV_STAGES * MV_UMAX * 4;
+constexpr int SM_DESC_OFF = SM_BAR_OFF + 2 * MV_STAGES * 8;  // tile record of each stage
+constexpr int SM_FLAG_OFF = SM_DESC_OFF + MV_STAGES * 32;
+constexpr int SM_Y_OFF = SM_FLAG_OFF + 16;
+
+enum : int16_t { TILE_SMALL = 0, TILE_BIG = 1, TILE_GLOBAL = 2 };
+
+struct MvTile {
+    int64_t a_off;    // float offset of the tile's first A float
+    int32_t cam_off;  // offset into mv_cam of its first landmark's cameras
+    int32_t bytes;    // A bytes to copy (multiple of 16; 0 for TILE_GLOBAL)
+    int16_t k;
+    int16_t kind;
+    int32_t count;    // small: landmarks; big: rows; global: 1
+    int32_t r0;       // big: first row
+    int32_t first;    // global: storage position of the landmark
+};
+static_assert(sizeof(MvTile) == 32, "tile record size");
+
+enum : int { MODE_MATVEC = 0, MODE_PRECOND = 1 };
+constexpr int REC = 54;  // per-observation record: 45 entries of A_s^T A_s (upper, row-major) + A_s^T c
+
+struct MvArgs {
+    const MvTile* tiles;
+    const int32_t* tile_begin;
+    const float* apool;
+    const int32_t* mv_cam;
+    const int32_t* lm_by_k;
+    const int32_t* pt_off;
+    const int32_t* obs_cam_s;
+    const int64_t* a_off;
+    const float* v;
+    float* y;
+    int n_cam;
+    const PcgScalars* S;
+    uint32_t* err;
+    const float* cpool;  // preconditioner mode: c_j in storage order
+    float* rec;          // preconditioner mode: REC floats per observation (storage order)
+};
+
+// --- PTX wrappers ---------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for the phase of `parity`; false after MV_WAIT_NS or when another
+// warp has aborted (honour_abort).
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint32_t* err,
+                          bool honour_abort = true) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (honour_abort && *abort_flag) return false;
+        if (global_ns() - t0 > MV_WAIT_NS) {
+            *abort_flag = 1;
+            atomicOr(err, ERRBIT_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+// --- consumers ---------------------------------------------------------------------
+template <int K>
+struct SmallShape {
+    static constexpr int NC = 9 * K, NR = 2 * K;
+    static constexpr int W = NC <= 32 ? 8 : (NC <= 64 ? 16 : 32);  // team width (<= 4 columns a lane below k = 8)
+    static constexpr int NM = (NC + W - 1) / W;
+    static constexpr int BF = (18 * K * K + 3) & ~3;  // block floats (padded to 16 bytes)
+};
+
+// One tile of `count` blocks with k = K; consumer warp cw of MV_CONSUMERS.
+template <int K>
+__device__ __forceinline__ void small_tile(const float* __restrict__ sa, const int32_t* __restrict__ sc, int count,
+                                           const float* __restrict__ v, float* __restrict__ yt, int cw, int lane) {
+    using S = SmallShape<K>;
+    constexpr int TPW = 32 / S::W;
+    constexpr int T = MV_CONSUMERS * TPW;
+    const int t = lane % S::W;
+    for (int base = cw * TPW; base < count; base += T) {
+        const int l = base + lane / S::W;
+        const bool active = l < count;
+        const float* blk = sa + (active ? l : 0) * S::BF;
+        const int32_t* cams = sc + (active ? l : 0) * K;
+        float vr[S::NM], yr[S::NM];
+        int yi[S::NM];
+#pragma unroll
+        for (int m = 0; m < S::NM; ++m) {
+            const int col = t + S::W * m;
+            const bool ok = active && col < S::NC;
+            const int s = col / 9;
+            yi[m] = ok ? 9 * cams[s] + (col - 9 * s) : 0;
+            vr[m] = ok ? __ldg(v + yi[m]) : 0.f;
+            yr[m] = 0.f;
+        }
+#pragma unroll 4
+        for (int r = 0; r < S::NR; ++r) {
+            float a[S::NM];
+            float part = 0.f;
+#pragma unroll
+            for (int m = 0; m < S::NM; ++m) {
+                const int col = t + S::W * m;
+                a[m] = (active && col < S::NC) ? blk[r * S::NC + col] : 0.f;
+                part += a[m] * vr[m];
+            }
+#pragma unroll
+            for (int o = S::W / 2; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+#pragma unroll
+            for (int m = 0; m < S::NM; ++m) yr[m] += part * a[m];
+        }
+#pragma unroll
+        for (int m = 0; m < S::NM; ++m) {
+            const int col = t + S::W * m;
+            if (active && col < S::NC) atomicAdd(yt + yi[m], yr[m]);
+        }
+    }
+}
+
+// --- preconditioner mode: per-observation records -----------------------------------
+// One thread per observation slot s of a block: over the block's rows r,
+// acc += a a^T (upper triangle) and accg += a c_r with a = A_j[r, 9s .. 9s+8].
+__device__ __forceinline__ void slot_accumulate(const float* __restrict__ blk, const float* __restrict__ cvals,
+                                                int nc, int r0, int r1, int s, float acc[REC]) {
+    for (int r = r0; r < r1; ++r) {
+        float a[9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) a[c] = blk[r * nc + 9 * s + c];
+        const float cv = cvals[r];
+        int t = 0;
+#pragma unroll
+        for (int u = 0; u < 9; ++u) {
+            acc[45 + u] += a[u] * cv;
+#pragma unroll
+            for (int v = u; v < 9; ++v) acc[t++] += a[u] * a[v];
+        }
+    }
+}
+
+__device__ __forceinline__ void rec_store(float* __restrict__ rec, const float acc[REC]) {
+#pragma unroll
+    for (int m = 0; m < REC; ++m) rec[m] = acc[m];
+}
+
+__device__ __forceinline__ void rec_add(float* __restrict__ rec, const float acc[REC]) {
+#pragma unroll
+    for (int m = 0; m < REC; ++m) atomicAdd(rec + m, acc[m]);
+}
+
+// whole staged blocks, one slot per thread
+__device__ __forceinline__ void precond_blocks(const MvArgs& a, const MvTile& tile, const float* __restrict__ blocks,
+                                               const float* __restrict__ cvals, int tid) {
+    const int k = tile.k, nc = 9 * k, nr = 2 * k;
+    const int64_t bf = pad4(18LL * k * k);
+    for (int q = tid; q < tile.count * k; q += MV_CONSUMERS * 32) {
+        const int l = q / k, s = q - l * k;
+        float acc[REC];
+#pragma unroll
+        for (int m = 0; m < REC; ++m) acc[m] = 0.f;
+        slot_accumulate(blocks + l * bf, cvals + l * nr, nc, 0, nr, s, acc);
+        rec_store(a.rec + (int64_t)(tile.cam_off + q) * REC, acc);
+    }
+}
+
+// rows [r0, r0 + nrows) of one block (staged): partial records added atomically
+__device__ __forceinline__ void precond_rows(const MvArgs& a, const MvTile& tile, const float* __restrict__ sa,
+                                             const float* __restrict__ cvals, int tid) {
+    const int k = tile.k, nc = 9 * k;
+    for (int s = tid; s < k; s += MV_CONSUMERS * 32) {
+        float acc[REC];
+#pragma unroll
+        for (int m = 0; m < REC; ++m) acc[m] = 0.f;
+        slot_accumulate(sa, cvals, nc, 0, tile.count, s, acc);
+        rec_add(a.rec + (int64_t)(tile.cam_off + s) * REC, acc);
+    }
+}
+
+// a block read from global memory (k > MV_KBIG)
+__device__ void precond_global(const MvArgs& a, const MvTile& tile, int tid) {
+    const int j = a.lm_by_k[tile.first];
+    const int k = a.pt_off[j + 1] - a.pt_off[j], nc = 9 * k, nr = 2 * k;
+    const float* Aj = a.apool + a.a_off[j];
+    const float* cj = a.cpool + 2LL * tile.cam_off;
+    for (int s = tid; s < k; s += MV_CONSUMERS * 32) {
+        float acc[REC];
+#pragma unroll
+        for (int m = 0; m < REC; ++m) acc[m] = 0.f;
+        slot_accumulate(Aj, cj, nc, 0, nr, s, acc);
+        rec_store(a.rec + (int64_t)(tile.cam_off + s) * REC, acc);
+    }
+}
+
+__device__ __forceinline__ void small_dispatch(int k, const float* sa, const int32_t* sc, int count,
+                                               const float* __restrict__ v, float* yt, int cw, int lane) {
+    switch (k) {
+#define MV_CASE(KK) \
+    case KK: small_tile<KK>(sa, sc, count, v, yt, cw, lane); break;
+        MV_CASE(2) MV_CASE(3) MV_CASE(4) MV_CASE(5) MV_CASE(6) MV_CASE(7) MV_CASE(8) MV_CASE(9) MV_CASE(10)
+        MV_CASE(11) MV_CASE(12) MV_CASE(13) MV_CASE(14) MV_CASE(15) MV_CASE(16) MV_CASE(17) MV_CASE(18)
+        MV_CASE(19) MV_CASE(20) MV_CASE(21)
+#undef MV_CASE
+        default: break;
+    }
+}
+
+// Rows [r0, r0 + nrows) of one block with k > MV_KSMALL, staged in sa.  Each
+// consumer warp takes rows cw, cw + 8, ...: u_r by a warp reduction, then its
+// rows' contribution to y_j column by column (no cross-warp barrier).
+__device__ __forceinline__ void big_tile(const float* __restrict__ sa, const int32_t* __restrict__ sc, int k,
+                                         int nrows, float* __restrict__ ub, const float* __restrict__ v,
+                                         float* __restrict__ yt, int cw, int lane) {
+    const int nc = 9 * k;
+    if (cw >= nrows) return;
+    // rows of warp cw: cw, cw + MV_CONSUMERS, ... (nrows <= MV_UMAX, so at most
+    // MV_UMAX / MV_CONSUMERS of them)
+    static_assert(MV_UMAX % MV_CONSUMERS == 0, "u slice per warp");
+    float* u = ub + cw * (MV_UMAX / MV_CONSUMERS);
+    int nmine = 0;
+    for (int rr = cw; rr < nrows; rr += MV_CONSUMERS, ++nmine) {
+        const float* row = sa + rr * nc;
+        float part = 0.f;
+        for (int col = lane; col < nc; col += 32) {
+            const int s = col / 9;
+            part += row[col] * __ldg(v + 9 * sc[s] + (col - 9 * s));
+        }
+        part = warp_sum(part);
+        if (lane == 0) u[nmine] = part;
+    }
+    __syncwarp();
+    for (int col = lane; col < nc; col += 32) {
+        float acc = 0.f;
+        int q = 0;
+        for (int rr = cw; rr < nrows; rr += MV_CONSUMERS, ++q) acc += sa[rr * nc + col] * u[q];
+        const int s = col / 9;
+        atomicAdd(yt + 9 * sc[s] + (col - 9 * s), acc);
+    }
+    __syncwarp();
+}
+
+// A block read straight from global memory (k > MV_KBIG), one warp, two passes.
+__device__ void global_block(const MvArgs& a, int pos, float* __restrict__ ub, float* __restrict__ yt, int lane) {
+    const int j = a.lm_by_k[pos];
+    const int s0 = a.pt_off[j], k = a.pt_off[j + 1] - s0, nc = 9 * k, nr = 2 * k;
+    const float* Aj = a.apool + a.a_off[j];
+    for (int r0 = 0; r0 < nr; r0 += MV_UMAX) {
+        const int rn = min(MV_UMAX, nr - r0);
+        for (int r = 0; r < rn; ++r) {
+            float part = 0.f;
+            for (int col = lane; col < nc; col += 32) {
+                const int s = col / 9;
+                part += Aj[(int64_t)(r0 + r) * nc + col] * __ldg(a.v + 9 * a.obs_cam_s[s0 + s] + (col - 9 * s));
+            }
+            part = warp_sum(part);
+            if (lane == 0) ub[r] = part;
+        }
+        __syncwarp();
+        for (int col = lane; col < nc; col += 32) {
+            float acc = 0.f;
+            for (int r = 0; r < rn; ++r) acc += Aj[(int64_t)(r0 + r) * nc + col] * ub[r];
+            const int s = col / 9;
+            atomicAdd(yt + 9 * a.obs_cam_s[s0 + s] + (col - 9 * s), acc);
+        }
+        __syncwarp();
+    }
+}
+
+// consumer warps a tile keeps busy (at most MV_CONSUMERS)
+__device__ __forceinline__ int tile_warps(const MvTile& t, int mode) {
+    int w;
+    if (mode == MODE_MATVEC) {
+        if (t.kind == TILE_SMALL) {
+            const int nc = 9 * t.k;
+            const int tpw = nc <= 32 ? 4 : (nc <= 64 ? 2 : 1);
+            w = (t.count + tpw - 1) / tpw;
+        } else if (t.kind == TILE_BIG) {
+            w = t.count;
+        } else {
+            w = 1;
+        }
+    } else {
+        const int slots = t.kind == TILE_SMALL ? t.count * t.k : t.k;
+        w = (slots + 31) / 32;
+    }
+    return w < 1 ? 1 : (w > MV_CONSUMERS ? MV_CONSUMERS : w);
+}
+
+template <int MODE, bool SMEM_Y>
+__global__ void __launch_bounds__(MV_THREADS, 1) k_matvec_tiles(MvArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (a.S != nullptr && a.S->done) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* ys = reinterpret_cast<float*>(smem + SM_Y_OFF);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + SM_FLAG_OFF);
+    const uint32_t bar0 = smem_u32(smem + SM_BAR_OFF);
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (MV_STAGES + s); };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < MV_STAGES; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), MV_CONSUMERS);
+        }
+        *abort_flag = 0;
+        mbar_fence_init();
+    }
+    if (MODE == MODE_MATVEC && SMEM_Y)
+        for (int i = threadIdx.x; i < 9 * a.n_cam; i += MV_THREADS) ys[i] = 0.f;
+    __syncthreads();
+    float* yt = SMEM_Y ? ys : a.y;
+
+    const int tb = a.tile_begin[blockIdx.x], te = a.tile_begin[blockIdx.x + 1];
+    if (warp == 0) {
+        // producer warp: tile records are fetched 32 at a time (one coalesced
+        // load, lane l holds record base + l), lane 0 publishes each record in
+        // the stage's descriptor slot and issues the bulk copies
+        MvTile* desc = reinterpret_cast<MvTile*>(smem + SM_DESC_OFF);
+        int issued = 0;
+        bool stop = false;
+        for (int base = tb; base < te && !stop; base += 32) {
+            MvTile mine{};
+            if (base + lane < te) mine = a.tiles[base + lane];
+            const int n = min(32, te - base);
+            for (int q = 0; q < n; ++q) {
+                MvTile tile;
+                tile.a_off = __shfl_sync(0xffffffffu, mine.a_off, q);
+                tile.cam_off = __shfl_sync(0xffffffffu, mine.cam_off, q);
+                tile.bytes = __shfl_sync(0xffffffffu, mine.bytes, q);
+                tile.k = (int16_t)__shfl_sync(0xffffffffu, (int)mine.k, q);
+                tile.kind = (int16_t)__shfl_sync(0xffffffffu, (int)mine.kind, q);
+                tile.count = __shfl_sync(0xffffffffu, mine.count, q);
+                tile.r0 = __shfl_sync(0xffffffffu, mine.r0, q);
+                tile.first = __shfl_sync(0xffffffffu, mine.first, q);
+                int ok = 1;
+                if (lane == 0) {
+                    const int i = base + q - tb, s = i % MV_STAGES;
+                    if (i >= MV_STAGES && !mbar_wait(empty_bar(s), ((i / MV_STAGES) - 1) & 1, abort_flag, a.err)) {
+                        ok = 0;
+                    } else {
+                        desc[s] = tile;
+                        if (tile.kind == TILE_GLOBAL) {
+                            mbar_arrive(full_bar(s));
+                        } else {
+                            const int nc = tile.kind == TILE_SMALL ? tile.count * tile.k : tile.k;
+                            const int c4 = tile.cam_off & ~3;
+                            const uint32_t cbytes = (uint32_t)(((tile.cam_off - c4 + nc) * 4 + 15) & ~15);
+                            // preconditioner mode: c_j values (2k per block, or the tile's rows)
+                            const int64_t r_first = 2LL * tile.cam_off + (tile.kind == TILE_BIG ? tile.r0 : 0);
+                            const int r_n = tile.kind == TILE_SMALL ? 2 * tile.k * tile.count : tile.count;
+                            const int64_t r4 = r_first & ~3LL;
+                            const uint32_t rbytes =
+                                MODE == MODE_PRECOND ? (uint32_t)(((r_first - r4 + r_n) * 4 + 15) & ~15) : 0u;
+                            mbar_expect_tx(full_bar(s), (uint32_t)tile.bytes + cbytes + rbytes);
+                            bulk_g2s(smem_u32(smem + s * MV_STAGE_A), a.apool + tile.a_off, (uint32_t)tile.bytes,
+                                     full_bar(s));
+                            bulk_g2s(smem_u32(smem + SM_STAGE_C_OFF + s * MV_STAGE_C), a.mv_cam + c4, cbytes,
+                                     full_bar(s));
+                            if (MODE == MODE_PRECOND)
+                                bulk_g2s(smem_u32(smem + SM_STAGE_R_OFF + s * MV_STAGE_R), a.cpool + r4, rbytes,
+                                         full_bar(s));
+                        }
+                        ++issued;
+                    }
+                }
+                if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                    stop = true;
+                    break;
+                }
+            }
+        }
+        if (lane == 0 && *abort_flag) {
+            // let the copies already issued land before the CTA exits
+            for (int i = max(0, issued - MV_STAGES); i < issued; ++i)
+                mbar_wait(full_bar(i % MV_STAGES), (i / MV_STAGES) & 1, abort_flag, a.err, false);
+        }
+    } else {
+        const int cw = warp - 1;
+        for (int t = tb; t < te; ++t) {
+            const int i = t - tb, s = i % MV_STAGES;
+            if (!mbar_wait(full_bar(s), (i / MV_STAGES) & 1, abort_flag, a.err)) break;
+            const MvTile tile = reinterpret_cast<const MvTile*>(smem + SM_DESC_OFF)[s];
+            const float* sa = reinterpret_cast<const float*>(smem + s * MV_STAGE_A);
+            const int32_t* sc = reinterpret_cast<const int32_t*>(smem + SM_STAGE_C_OFF + s * MV_STAGE_C) +
+                                (tile.cam_off & 3);
+            float* ub = reinterpret_cast<float*>(smem + SM_U_OFF) + s * MV_UMAX;
+            // A tile rarely needs all consumer warps; successive tiles start at
+            // successive groups of warps (rotation by the warps the tile needs),
+            // so that the tiles in flight are worked on by disjoint warps.
+            const int need = tile_warps(tile, MODE);
+            const int vcw = (cw + MV_CONSUMERS - (i * need) % MV_CONSUMERS) % MV_CONSUMERS;
+            if (MODE == MODE_MATVEC) {
+                if (tile.kind == TILE_SMALL) small_dispatch(tile.k, sa, sc, tile.count, a.v, yt, vcw, lane);
+                else if (tile.kind == TILE_BIG) big_tile(sa, sc, tile.k, tile.count, ub, a.v, yt, vcw, lane);
+                else if (vcw == 0) global_block(a, tile.first, ub, yt, lane);
+            } else {
+                const int tid = vcw * 32 + lane;
+                const int64_t r_first = 2LL * tile.cam_off + (tile.kind == TILE_BIG ? tile.r0 : 0);
+                const float* sr = reinterpret_cast<const float*>(smem + SM_STAGE_R_OFF + s * MV_STAGE_R) + (r_first & 3);
+                if (tile.kind == TILE_SMALL) precond_blocks(a, tile, sa, sr, tid);
+                else if (tile.kind == TILE_BIG) precond_rows(a, tile, sa, sr, tid);
+                else precond_global(a, tile, tid);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty_bar(s));
+        }
+    }
+    __syncthreads();
+    if (MODE == MODE_MATVEC && SMEM_Y) {
+        for (int i = threadIdx.x; i < 9 * a.n_cam; i += MV_THREADS) {
+            const float val = ys[i];
+            if (val != 0.f) atomicAdd(a.y + i, val);
+        }
+    }
+}
+
+__global__ void k_add_damping(int n, const float* __restrict__ dp2, float lam, const float* __restrict__ v,
+                              float* __restrict__ y) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] += lam * dp2[i] * v[i];
+}
+
+bool smem_y(const Problem& p) { return SM_Y_OFF + 36 * (int64_t)p.n_cam <= 227 * 1024; }
+size_t smem_bytes(const Problem& p) { return SM_Y_OFF + (smem_y(p) ? 36 * (size_t)p.n_cam : 0); }
+
+MvArgs make_args(Problem& p, const float* v, float* y, const PcgScalars* S) {
+    return MvArgs{static_cast<const MvTile*>(p.mv_tiles), p.mv_tile_begin, p.apool, p.mv_cam, p.lm_by_k, p.pt_off,
+                  p.obs_cam_s, p.a_off, v, y, p.n_cam, S, p.err, p.cpool, p.prec};
+}
+
+}  // namespace
+
+// Host planning of the tiles: runs of equal-k blocks in storage order
+// (decreasing k), cut into stage-sized tiles, then contiguous tile ranges per
+// CTA balanced by bytes.
+void plan_matvec(Problem& p) {
+    std::vector<MvTile> tiles;
+    const int kmax = p.k_max;
+    for (int b = 0; b <= kmax; ++b) {
+        const int k = kmax - b;
+        const int64_t cnt = p.k_run_count[b];
+        if (cnt == 0 || k < 2) continue;
+        const int64_t bf = pad4(18LL * k * k);
+        const int64_t pos0 = [&] {
+            int64_t q = 0;
+            for (int bb = 0; bb < b; ++bb) q += p.k_run_count[bb];
+            return q;
+        }();
+        if (k <= MV_KSMALL) {
+            const int64_t per = std::max<int64_t>(1, MV_STAGE_A / (4 * bf));
+            for (int64_t l = 0; l < cnt; l += per) {
+                MvTile t{};
+                const int64_t n = std::min(per, cnt - l);
+                t.a_off = p.run_off[b] + l * bf;
+                t.cam_off = (int32_t)(p.run_co[b] + l * k);
+                t.bytes = (int32_t)(4 * n * bf);
+                t.k = (int16_t)k;
+                t.kind = TILE_SMALL;
+                t.count = (int32_t)n;
+                t.first = (int32_t)(pos0 + l);
+                tiles.push_back(t);
+            }
+        } else if (k <= MV_KBIG) {
+            const int nc = 9 * k, nr = 2 * k;
+            const int rows = std::min(MV_UMAX & ~3, (MV_STAGE_A / (4 * nc)) & ~3);
+            for (int64_t l = 0; l < cnt; ++l) {
+                for (int r0 = 0; r0 < nr; r0 += rows) {
+                    MvTile t{};
+                    const int n = std::min(rows, nr - r0);
+                    t.a_off = p.run_off[b] + l * bf + (int64_t)r0 * nc;
+                    t.cam_off = (int32_t)(p.run_co[b] + l * k);
+                    t.bytes = (int32_t)((4LL * n * nc + 15) & ~15LL);
+                    t.k = (int16_t)k;
+                    t.kind = TILE_BIG;
+                    t.count = n;
+                    t.r0 = r0;
+                    t.first = (int32_t)(pos0 + l);
+                    tiles.push_back(t);
+                }
+            }
+        } else {
+            for (int64_t l = 0; l < cnt; ++l) {
+                MvTile t{};
+                t.k = (int16_t)std::min(k, 32767);
+                t.kind = TILE_GLOBAL;
+                t.count = 1;
+                t.first = (int32_t)(pos0 + l);
+                t.bytes = 0;
+                tiles.push_back(t);
+            }
+        }
+    }
+    // CTA b takes tiles b, b + G, b + 2G, ... of the k-sorted list, so every
+    // SM gets the same mix of block sizes (work per byte differs strongly with
+    // k); stored as contiguous ranges of a permuted list
+    const int grid = p.mv_grid;
+    std::vector<MvTile> perm;
+    perm.reserve(tiles.size());
+    std::vector<int32_t> begin(grid + 1, 0);
+    for (int c = 0; c < grid; ++c) {
+        begin[c] = (int32_t)perm.size();
+        for (size_t i = c; i < tiles.size(); i += grid) perm.push_back(tiles[i]);
+    }
+    begin[grid] = (int32_t)perm.size();
+    tiles.swap(perm);
+    p.n_mv_tiles = (int)tiles.size();
+    p.mv_tiles = dalloc<MvTile>(p, std::max<int64_t>(1, (int64_t)tiles.size()));
+    p.mv_tile_begin = dalloc<int32_t>(p, grid + 1);
+    if (!tiles.empty())
+        BA_CUDA_TRY(cudaMemcpyAsync(p.mv_tiles, tiles.data(), sizeof(MvTile) * tiles.size(), cudaMemcpyHostToDevice,
+                                    p.stream));
+    BA_CUDA_TRY(cudaMemcpyAsync(p.mv_tile_begin, begin.data(), sizeof(int32_t) * (grid + 1), cudaMemcpyHostToDevice,
+                                p.stream));
+    BA_CUDA_TRY(cudaStreamSynchronize(p.stream));
+}
+
+int matvec_ctas_per_sm() { return 1; }
+
+void configure_matvec(Problem& p) {
+    const int sm = (int)smem_bytes(p);
+    BA_CUDA_TRY(cudaFuncSetAttribute(k_matvec_tiles<MODE_MATVEC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    BA_CUDA_TRY(cudaFuncSetAttribute(k_matvec_tiles<MODE_MATVEC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    BA_CUDA_TRY(cudaFuncSetAttribute(k_matvec_tiles<MODE_PRECOND, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)SM_Y_OFF));
+}
+
+void launch_matvec_raw(Problem& p, const float* v, float* y, const PcgScalars* S) {
+    const MvArgs a = make_args(p, v, y, S);
+    if (smem_y(p)) k_matvec_tiles<MODE_MATVEC, true><<<p.mv_grid, MV_THREADS, smem_bytes(p), p.stream>>>(a);
+    else k_matvec_tiles<MODE_MATVEC, false><<<p.mv_grid, MV_THREADS, smem_bytes(p), p.stream>>>(a);
+    BA_LAUNCH_CHECK();
+}
+
+// K3, first half: per-observation records of the block-Jacobi blocks and the
+// right-hand side, streamed through the same tile pipeline
+void launch_precond_records(Problem& p) {
+    if (p.n_obs_direct_big > 0)
+        BA_CUDA_TRY(cudaMemsetAsync(p.prec, 0, sizeof(float) * REC * p.n_obs_direct_big, p.stream));
+    const MvArgs a = make_args(p, nullptr, nullptr, nullptr);
+    k_matvec_tiles<MODE_PRECOND, false><<<p.mv_grid, MV_THREADS, SM_Y_OFF, p.stream>>>(a);
+    BA_LAUNCH_CHECK();
+}
+
+void launch_matvec(Problem& p, const float* v, float* y, bool add_damping) {
+    count_launches(p, 1 + (add_damping ? 1 : 0));
+    BA_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(float) * 9 * p.n_cam, p.stream));
+    launch_matvec_raw(p, v, y, nullptr);
+    if (add_damping) {
+        k_add_damping<<<ceil_div(9 * (int64_t)p.n_cam, 256), 256, 0, p.stream>>>(9 * p.n_cam, p.dp2,
+                                                                                 (float)p.lambda_damped, v, y);
+        BA_LAUNCH_CHECK();
+    }
+}
+
+}  // namespace sqrtba

@@ -4,9 +4,11 @@
 // landmark-damping rows) and c_j = Q2^T r.
 //
 //   K3  M_i = sum_j A_ji^T A_ji + lambda D_p,i^2,  g_i = -sum_j A_ji^T c_j,
-//       Cholesky-inverted per camera (the block diagonal of H~, Sec. 6.1)
-//   K4  y = sum_j P_j^T A_j^T (A_j P_j v) + lambda D_p^2 v  (Eq. cg_mult; pose
-//       damping added only in the product, Sec. 5.3)
+//       Cholesky-inverted per camera (the block diagonal of H~, Sec. 6.1):
+//       per-observation records from the tile pipeline (matvec.cu), summed
+//       here per camera in a fixed order
+//   K4  y = sum_j P_j^T A_j^T (A_j P_j v) (matvec.cu) + lambda D_p^2 v, the pose
+//       damping added only in the product (Sec. 5.3), inside K5
 //   K5  the CG recursion with the Nash-Sofer stop
 //       i (Q_i - Q_{i-1}) / Q_i < eta, Q(x) = 1/2 x^T H~ x - g^T x = -1/2 x^T (g + r).
 #include <algorithm>
@@ -55,52 +57,29 @@ __device__ int cholesky_inverse9(const float* M, float* Minv) {
     return 0;
 }
 
+// Second half of K3: per camera, the records of its observations (written by
+// the tile pipeline, 54 floats each: upper triangle of A_s^T A_s and A_s^T c)
+// are summed in a fixed order, lambda D_p^2 is added and the block inverted.
 __global__ void __launch_bounds__(32 * PC_WARPS)
-k_precond_rhs(int n_cam, const int32_t* __restrict__ cam_off, const int32_t* __restrict__ cam_list,
-              const int32_t* __restrict__ obs_pt_s, const int32_t* __restrict__ pt_off,
-              const int64_t* __restrict__ a_off, const float* __restrict__ apool,
-              const float* __restrict__ cpool, const float* __restrict__ dp2,
-              const float lam, float* __restrict__ mdiag, float* __restrict__ minv,
-              float* __restrict__ g, uint32_t* err) {
+k_precond_reduce(int n_cam, const int32_t* __restrict__ cam_off, const int32_t* __restrict__ cam_list_st,
+                 const float* __restrict__ rec, const float* __restrict__ dp2, const float lam,
+                 float* __restrict__ mdiag, float* __restrict__ minv, float* __restrict__ g, uint32_t* err) {
     __shared__ float part[PC_WARPS][54];
     __shared__ float tot[54];
     const int cam = blockIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    float acc[45], accg[9];
+    float acc[54];
 #pragma unroll
-    for (int i = 0; i < 45; ++i) acc[i] = 0.f;
+    for (int i = 0; i < 54; ++i) acc[i] = 0.f;
+    for (int e = cam_off[cam] + threadIdx.x; e < cam_off[cam + 1]; e += 32 * PC_WARPS) {
+        const float* r = rec + (int64_t)cam_list_st[e] * 54;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) accg[i] = 0.f;
-    for (int e = cam_off[cam] + w; e < cam_off[cam + 1]; e += PC_WARPS) {
-        const int s = cam_list[e];
-        const int j = obs_pt_s[s];
-        const int s0 = pt_off[j], k = pt_off[j + 1] - s0;
-        const int ncol = 9 * k;
-        const float* Ab = apool + a_off[j] + 9 * (s - s0);
-        const float* cj = cpool + 2 * (int64_t)s0;
-        for (int row = lane; row < 2 * k; row += 32) {
-            float a[9];
-#pragma unroll
-            for (int c = 0; c < 9; ++c) a[c] = __ldg(Ab + (int64_t)row * ncol + c);
-            const float cv = __ldg(cj + row);
-            int t = 0;
-#pragma unroll
-            for (int u = 0; u < 9; ++u) {
-                accg[u] += a[u] * cv;
-#pragma unroll
-                for (int v = u; v < 9; ++v) acc[t++] += a[u] * a[v];
-            }
-        }
+        for (int i = 0; i < 54; ++i) acc[i] += __ldg(r + i);
     }
 #pragma unroll
-    for (int i = 0; i < 45; ++i) {
+    for (int i = 0; i < 54; ++i) {
         const float v = warp_sum(acc[i]);
         if (lane == 0) part[w][i] = v;
-    }
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const float v = warp_sum(accg[i]);
-        if (lane == 0) part[w][45 + i] = v;
     }
     __syncthreads();
     if (threadIdx.x < 54) {
@@ -128,109 +107,6 @@ k_precond_rhs(int n_cam, const int32_t* __restrict__ cam_off, const int32_t* __r
         }
         for (int i = 0; i < 81; ++i) minv[81 * (int64_t)cam + i] = Mi[i];
         for (int u = 0; u < 9; ++u) g[9 * cam + u] = -tot[45 + u];
-    }
-}
-
-// ---------------------------------------------------------------------------
-// K4: y += sum_j A_j^T (A_j v_j)   (v_j = the landmark's camera sub-vector)
-// One warp per landmark.  Row-wise single pass over A_j: u_r = A_j[r,:] v_j
-// (warp reduction), then y_j += u_r A_j[r,:]; the 9k-entry y_j stays in
-// registers (k <= MV_KREG) and is added into a per-CTA copy of y in shared
-// memory, which is flushed to global memory once per CTA.  Larger k use two
-// passes with u_j in shared memory.
-// ---------------------------------------------------------------------------
-constexpr int MV_WARPS = 8;
-constexpr int MV_KREG = 64;              // 9k <= 576 -> 18 columns per lane
-constexpr int MV_NM = (9 * MV_KREG + 31) / 32;
-constexpr int MV_UCAP = 2 * 1024;        // shared u_j capacity per warp (k <= 1024)
-
-template <bool SMEM_Y>
-__global__ void __launch_bounds__(32 * MV_WARPS)
-k_matvec(int n_cam, const int32_t* __restrict__ begin, const int32_t* __restrict__ pt_off,
-         const int32_t* __restrict__ obs_cam_s, const int64_t* __restrict__ a_off,
-         const float* __restrict__ apool, const float* __restrict__ v, float* __restrict__ y,
-         const PcgScalars* __restrict__ S) {
-    extern __shared__ float smem[];
-    if (S != nullptr && S->done) return;
-    float* ys = smem;                                    // 9 n_cam (SMEM_Y)
-    float* ubuf = smem + (SMEM_Y ? 9 * n_cam : 0);       // per-warp u for big k
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (SMEM_Y) {
-        for (int i = threadIdx.x; i < 9 * n_cam; i += blockDim.x) ys[i] = 0.f;
-        __syncthreads();
-    }
-    const int jb = begin[blockIdx.x], je = begin[blockIdx.x + 1];
-    for (int j = jb + w; j < je; j += MV_WARPS) {
-        const int s0 = pt_off[j], k = pt_off[j + 1] - s0;
-        const int ncol = 9 * k, nr = 2 * k;
-        const float* __restrict__ Aj = apool + a_off[j];
-        if (k <= MV_KREG) {
-            float vr[MV_NM], yr[MV_NM];
-            int yi[MV_NM];
-#pragma unroll
-            for (int m = 0; m < MV_NM; ++m) {
-                const int col = lane + 32 * m;
-                vr[m] = 0.f;
-                yr[m] = 0.f;
-                yi[m] = 0;
-                if (col < ncol) {
-                    const int s = col / 9;
-                    yi[m] = 9 * obs_cam_s[s0 + s] + (col - 9 * s);
-                    vr[m] = __ldg(v + yi[m]);
-                }
-            }
-            for (int r = 0; r < nr; ++r) {
-                const float* row = Aj + (int64_t)r * ncol;
-                float a[MV_NM];
-                float part = 0.f;
-#pragma unroll
-                for (int m = 0; m < MV_NM; ++m) {
-                    const int col = lane + 32 * m;
-                    a[m] = col < ncol ? __ldcs(row + col) : 0.f;
-                    part += a[m] * vr[m];
-                }
-                const float u = warp_sum(part);
-#pragma unroll
-                for (int m = 0; m < MV_NM; ++m) yr[m] += u * a[m];
-            }
-#pragma unroll
-            for (int m = 0; m < MV_NM; ++m) {
-                const int col = lane + 32 * m;
-                if (col < ncol) {
-                    if (SMEM_Y) atomicAdd(ys + yi[m], yr[m]);
-                    else atomicAdd(y + yi[m], yr[m]);
-                }
-            }
-        } else {
-            float* u = ubuf + w * MV_UCAP;
-            for (int r = 0; r < nr; ++r) {
-                const float* row = Aj + (int64_t)r * ncol;
-                float part = 0.f;
-                for (int col = lane; col < ncol; col += 32) {
-                    const int s = col / 9;
-                    part += row[col] * __ldg(v + 9 * obs_cam_s[s0 + s] + (col - 9 * s));
-                }
-                part = warp_sum(part);
-                if (lane == 0) u[r] = part;
-            }
-            __syncwarp();
-            for (int col = lane; col < ncol; col += 32) {
-                float acc = 0.f;
-                for (int r = 0; r < nr; ++r) acc += Aj[(int64_t)r * ncol + col] * u[r];
-                const int s = col / 9;
-                const int yi = 9 * obs_cam_s[s0 + s] + (col - 9 * s);
-                if (SMEM_Y) atomicAdd(ys + yi, acc);
-                else atomicAdd(y + yi, acc);
-            }
-            __syncwarp();
-        }
-    }
-    if (SMEM_Y) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < 9 * n_cam; i += blockDim.x) {
-            const float val = ys[i];
-            if (val != 0.f) atomicAdd(y + i, val);
-        }
     }
 }
 
@@ -353,46 +229,13 @@ k_pcg_update(int n_cam, const float* __restrict__ g, const float* __restrict__ d
     if (threadIdx.x == 0) S->rho = rz;
 }
 
-__global__ void k_add_damping(int n, const float* __restrict__ dp2, float lam, const float* __restrict__ v,
-                              float* __restrict__ y) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[i] += lam * dp2[i] * v[i];
-}
-
-bool matvec_smem_y(const Problem& p) { return 9 * (int64_t)p.n_cam * 4 <= 96 * 1024; }
-
-size_t matvec_smem(const Problem& p) {
-    return (matvec_smem_y(p) ? 9 * (size_t)p.n_cam * 4 : 0) +
-           (p.k_max > MV_KREG ? (size_t)MV_WARPS * MV_UCAP * 4 : 0);
-}
-
-void matvec_raw(Problem& p, const float* v, float* y, const PcgScalars* S) {
-    const size_t sm = matvec_smem(p);
-    if (matvec_smem_y(p)) {
-        k_matvec<true><<<p.mv_grid, 32 * MV_WARPS, sm, p.stream>>>(p.n_cam, p.mv_begin, p.pt_off, p.obs_cam_s,
-                                                                   p.a_off, p.apool, v, y, S);
-    } else {
-        k_matvec<false><<<p.mv_grid, 32 * MV_WARPS, sm, p.stream>>>(p.n_cam, p.mv_begin, p.pt_off,
-                                                                    p.obs_cam_s, p.a_off, p.apool, v, y, S);
-    }
-    BA_LAUNCH_CHECK();
-}
-
 }  // namespace
 
-int matvec_ctas_per_sm() { return 2; }
-
-void configure_matvec(Problem& p) {
-    const int sm = (int)matvec_smem(p);
-    BA_CUDA_TRY(cudaFuncSetAttribute(k_matvec<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    BA_CUDA_TRY(cudaFuncSetAttribute(k_matvec<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-}
-
 void launch_precond_rhs(Problem& p) {
-    count_launches(p, 1);
-    k_precond_rhs<<<p.n_cam, 32 * PC_WARPS, 0, p.stream>>>(p.n_cam, p.cam_off, p.cam_list, p.obs_pt_s, p.pt_off,
-                                                          p.a_off, p.apool, p.cpool, p.dp2, (float)p.lambda_damped, p.mdiag,
-                                                          p.minv, p.g, p.err);
+    count_launches(p, 2 + (p.n_obs_direct_big > 0 ? 1 : 0));
+    launch_precond_records(p);
+    k_precond_reduce<<<p.n_cam, 32 * PC_WARPS, 0, p.stream>>>(p.n_cam, p.cam_off, p.cam_list_st, p.prec, p.dp2,
+                                                             (float)p.lambda_damped, p.mdiag, p.minv, p.g, p.err);
     BA_LAUNCH_CHECK();
 }
 
@@ -411,21 +254,10 @@ void launch_pcg_iteration(Problem& p, cudaEvent_t mv_begin, cudaEvent_t mv_end) 
         else BA_CUDA_TRY(cudaEventRecord(ev, p.stream));
     };
     record(mv_begin);
-    matvec_raw(p, p.p, p.q, p.pcg);
+    launch_matvec_raw(p, p.p, p.q, p.pcg);
     record(mv_end);
     k_pcg_update<<<1, PCG_T, 0, p.stream>>>(p.n_cam, p.g, p.dp2, p.minv, p.x, p.r, p.z, p.p, p.q, p.pcg);
     BA_LAUNCH_CHECK();
-}
-
-void launch_matvec(Problem& p, const float* v, float* y, bool add_damping) {
-    count_launches(p, 1 + (add_damping ? 1 : 0));
-    BA_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(float) * 9 * p.n_cam, p.stream));
-    matvec_raw(p, v, y, nullptr);
-    if (add_damping) {
-        k_add_damping<<<ceil_div(9 * (int64_t)p.n_cam, 256), 256, 0, p.stream>>>(9 * p.n_cam, p.dp2,
-                                                                                 (float)p.lambda_damped, v, y);
-        BA_LAUNCH_CHECK();
-    }
 }
 
 }  // namespace sqrtba

@@ -6,13 +6,14 @@
 //   obs_cam_s, obs_pt_s, obs_xy_s       observations sorted by (landmark, camera)
 //   pt_off[n_pt + 1] (int32)            landmark j owns sorted obs pt_off[j] ..
 //   cam_off[n_cam + 1], cam_list[n_obs] camera -> sorted positions (increasing)
-//   a_off[n_pt + 1] (int64)             float offset of A_j in apool
+//   a_off[n_pt + 1] (int64)             float offset of A_j in apool (blocks stored by
+//                                       decreasing k: lm_by_k order)
 //   apool                               A_j = Q^T J_p rows below R1, 2k x 9k row-major,
 //                                       the last 3 rows are the landmark damping rows
 //                                       (Sec. 5.3); blocks padded to 16 bytes
 //   tpool                               top_j: 3 x (9k + 4) rows [Q1^T J_p | R1 | Q1^T r],
 //                                       at float offset 3 (9 pt_off[j] + 4 j)
-//   cpool                               c_j = Q2^T r (2k), at float offset 2 pt_off[j]
+//   cpool                               c_j = Q2^T r (2k), at float offset c_off[j] (storage order)
 //   rot[12 n_pt]                        six Givens (cos, sin) of the current damping
 //   dp2[9 n_cam], dl2[3 n_pt]           D^2 = clamp(diag(J^T J), 1e-6, 1e32)
 //   PCG vectors (9 n_cam each) and the per-camera 9x9 preconditioner blocks
@@ -79,8 +80,17 @@ struct Problem {
     float2* obs_xy_s = nullptr;
     int32_t *pt_off = nullptr, *cam_off = nullptr, *cam_list = nullptr;
     int64_t* a_off = nullptr;
-    int32_t* lm_by_k = nullptr;      // landmarks by decreasing k
-    int32_t* mv_begin = nullptr;     // matvec: first landmark of each CTA (grid + 1)
+    int32_t* lm_by_k = nullptr;      // landmarks by decreasing k (storage order of the blocks)
+    int32_t* mv_cam = nullptr;       // camera of every observation in storage order
+    int32_t* c_off = nullptr;        // float offset of c_j = Q2^T r (storage order, 2k per landmark)
+    int32_t* cam_list_st = nullptr;  // camera lists as storage-order observation indices
+    int64_t n_obs_direct_big = 0;    // observations of landmarks with k > 21 (first in storage order)
+    std::vector<int32_t> k_run_count;  // host: landmarks with k = k_max - b
+    std::vector<int64_t> run_off, run_co;  // host: float / observation offset of run b
+    // matvec work plan: tiles of the block pool streamed through shared memory
+    void* mv_tiles = nullptr;        // MvTile[n_mv_tiles]
+    int32_t* mv_tile_begin = nullptr;  // first tile of each CTA (grid + 1)
+    int n_mv_tiles = 0;
     int mv_grid = 0;
     // blocks
     float *apool = nullptr, *tpool = nullptr, *cpool = nullptr, *rot = nullptr;
@@ -88,6 +98,7 @@ struct Problem {
     // PCG
     float *g = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
     float *minv = nullptr, *mdiag = nullptr;
+    float* prec = nullptr;           // 54 floats per observation: A_s^T A_s (upper) and A_s^T c
     PcgScalars* pcg = nullptr;
     PcgScalars* pcg_host = nullptr;  // pinned mirror
     // step
@@ -137,16 +148,21 @@ void launch_cost(Problem& p, bool candidate);
 void launch_candidate(Problem& p);
 // K2: landmark damping with Givens rotations (damp.cu)
 void launch_damp(Problem& p, bool undo_old, float lambda);
-// K3-K5: preconditioner, matvec, PCG (pcg.cu)
+// K3, K5: preconditioner and PCG (pcg.cu); K4: matvec (matvec.cu)
 void launch_precond_rhs(Problem& p);
 void launch_pcg_init(Problem& p);
 void launch_pcg_iteration(Problem& p, cudaEvent_t mv_begin = nullptr, cudaEvent_t mv_end = nullptr);
 void launch_matvec(Problem& p, const float* v, float* y, bool add_damping);
+void launch_matvec_raw(Problem& p, const float* v, float* y, const PcgScalars* S);
+void launch_precond_records(Problem& p);
+int matvec_ctas_per_sm();
 // K6: back substitution + model cost (backsub.cu)
 void launch_backsub(Problem& p);
 // one-time kernel attributes (dynamic shared memory limits)
 void configure_linearize(Problem& p);
 void configure_matvec(Problem& p);
+// matvec tile plan (host planning + upload), after build_index
+void plan_matvec(Problem& p);
 
 // kernel launch counter (not counted while a graph is being captured)
 inline void count_launches(Problem& p, int n) {
