@@ -403,9 +403,7 @@ void build_index(Problem& p, const int32_t* d_oc, const int32_t* d_op, const dou
                                                      p.pt_off, p.obs_cam_s, p.a_off, p.mv_cam, p.c_off, obs_store);
     k_map_list<<<gsz, TPB, 0, st>>>(n, p.cam_list, obs_store, p.cam_list_st);
     BA_LAUNCH_CHECK();
-    // observations of landmarks with k > 21 (they come first in storage order)
-    p.n_obs_direct_big = 0;
-    for (int b = 0; b <= kmax && kmax - b > 21; ++b) p.n_obs_direct_big = p.run_co[b + 1];
+
     BA_CUDA_TRY(cudaStreamSynchronize(st));
 }
 

@@ -35,8 +35,8 @@ constexpr int MV_STAGE_C = 1024;    // bytes of camera indices per stage
 // CTA's 16 warps spread four to a sub-partition: 128 registers per thread.
 constexpr int MV_CONSUMERS = 15;    // consumer warps per CTA
 constexpr int MV_THREADS = 32 * (MV_CONSUMERS + 1);
-constexpr int MV_KSMALL = 21;       // whole blocks, specialised per k
-constexpr int MV_KBIG = 222;        // row ranges of 4 rows (36k * 4 <= 32 KB)
+constexpr int MV_KSMALL = 13;       // whole blocks, specialised per k (>= 2 per tile)
+constexpr int MV_KBIG = 222;        // row ranges, multiples of 4 rows (36k * 4 <= 32 KB)
 constexpr int MV_UMAX = 45;         // rows of one big tile (multiple of MV_CONSUMERS)
 constexpr uint64_t MV_WAIT_NS = 2000000000ull;
 
@@ -281,37 +281,58 @@ __device__ __forceinline__ void small_dispatch(int k, const float* sa, const int
 }
 
 // Rows [r0, r0 + nrows) of one block with k > MV_KSMALL, staged in sa.  Each
-// consumer warp takes rows cw, cw + 8, ...: u_r by a warp reduction, then its
-// rows' contribution to y_j column by column (no cross-warp barrier).
+// warp owns BIG_RPW consecutive rows (no cross-warp dependency): u_r for its
+// rows over all columns, with v gathered once per column chunk for all of
+// its rows, then its rows' contribution A[r, col] u_r to every column.  A
+// tile keeps ceil(nrows / BIG_RPW) warps busy; tiles rotate over the warps.
+constexpr int BIG_RPW = 4;   // rows per warp
+constexpr int BIG_CH = 4;    // columns per lane per chunk
 __device__ __forceinline__ void big_tile(const float* __restrict__ sa, const int32_t* __restrict__ sc, int k,
-                                         int nrows, float* __restrict__ ub, const float* __restrict__ v,
-                                         float* __restrict__ yt, int cw, int lane) {
+                                         int nrows, const float* __restrict__ v, float* __restrict__ yt, int vcw,
+                                         int lane) {
     const int nc = 9 * k;
-    if (cw >= nrows) return;
-    // rows of warp cw: cw, cw + MV_CONSUMERS, ... (nrows <= MV_UMAX, so at most
-    // MV_UMAX / MV_CONSUMERS of them)
-    static_assert(MV_UMAX % MV_CONSUMERS == 0, "u slice per warp");
-    float* u = ub + cw * (MV_UMAX / MV_CONSUMERS);
-    int nmine = 0;
-    for (int rr = cw; rr < nrows; rr += MV_CONSUMERS, ++nmine) {
-        const float* row = sa + rr * nc;
-        float part = 0.f;
-        for (int col = lane; col < nc; col += 32) {
+    const int ra = vcw * BIG_RPW;
+    if (ra >= nrows) return;
+    const int nr = min(BIG_RPW, nrows - ra);
+    const float* rows = sa + ra * nc;
+    float part[BIG_RPW];
+#pragma unroll
+    for (int q = 0; q < BIG_RPW; ++q) part[q] = 0.f;
+    for (int c0 = 0; c0 < nc; c0 += 32 * BIG_CH) {
+        float vc[BIG_CH];
+#pragma unroll
+        for (int m = 0; m < BIG_CH; ++m) {
+            const int col = c0 + lane + 32 * m;
             const int s = col / 9;
-            part += row[col] * __ldg(v + 9 * sc[s] + (col - 9 * s));
+            vc[m] = col < nc ? __ldg(v + 9 * sc[s] + (col - 9 * s)) : 0.f;
         }
-        part = warp_sum(part);
-        if (lane == 0) u[nmine] = part;
+#pragma unroll
+        for (int q = 0; q < BIG_RPW; ++q) {
+            if (q < nr) {
+#pragma unroll
+                for (int m = 0; m < BIG_CH; ++m) {
+                    const int col = c0 + lane + 32 * m;
+                    if (col < nc) part[q] += rows[q * nc + col] * vc[m];
+                }
+            }
+        }
     }
-    __syncwarp();
-    for (int col = lane; col < nc; col += 32) {
-        float acc = 0.f;
-        int q = 0;
-        for (int rr = cw; rr < nrows; rr += MV_CONSUMERS, ++q) acc += sa[rr * nc + col] * u[q];
-        const int s = col / 9;
-        atomicAdd(yt + 9 * sc[s] + (col - 9 * s), acc);
+#pragma unroll
+    for (int q = 0; q < BIG_RPW; ++q) part[q] = warp_sum(part[q]);
+    for (int c0 = 0; c0 < nc; c0 += 32 * BIG_CH) {
+#pragma unroll
+        for (int m = 0; m < BIG_CH; ++m) {
+            const int col = c0 + lane + 32 * m;
+            if (col < nc) {
+                float acc = 0.f;
+#pragma unroll
+                for (int q = 0; q < BIG_RPW; ++q)
+                    if (q < nr) acc += rows[q * nc + col] * part[q];
+                const int s = col / 9;
+                atomicAdd(yt + 9 * sc[s] + (col - 9 * s), acc);
+            }
+        }
     }
-    __syncwarp();
 }
 
 // A block read straight from global memory (k > MV_KBIG), one warp, two passes.
@@ -350,7 +371,7 @@ __device__ __forceinline__ int tile_warps(const MvTile& t, int mode) {
             const int tpw = nc <= 32 ? 4 : (nc <= 64 ? 2 : 1);
             w = (t.count + tpw - 1) / tpw;
         } else if (t.kind == TILE_BIG) {
-            w = t.count;
+            w = (t.count + BIG_RPW - 1) / BIG_RPW;
         } else {
             w = 1;
         }
@@ -466,7 +487,7 @@ __global__ void __launch_bounds__(MV_THREADS, 1) k_matvec_tiles(MvArgs a) {
             const int vcw = (cw + MV_CONSUMERS - (i * need) % MV_CONSUMERS) % MV_CONSUMERS;
             if (MODE == MODE_MATVEC) {
                 if (tile.kind == TILE_SMALL) small_dispatch(tile.k, sa, sc, tile.count, a.v, yt, vcw, lane);
-                else if (tile.kind == TILE_BIG) big_tile(sa, sc, tile.k, tile.count, ub, a.v, yt, vcw, lane);
+                else if (tile.kind == TILE_BIG) big_tile(sa, sc, tile.k, tile.count, a.v, yt, vcw, lane);
                 else if (vcw == 0) global_block(a, tile.first, ub, yt, lane);
             } else {
                 const int tid = vcw * 32 + lane;
@@ -511,6 +532,11 @@ MvArgs make_args(Problem& p, const float* v, float* y, const PcgScalars* S) {
 void plan_matvec(Problem& p) {
     std::vector<MvTile> tiles;
     const int kmax = p.k_max;
+    // records of blocks that are split into row tiles are accumulated
+    // atomically: the observations of all landmarks with k > MV_KSMALL, which
+    // come first in storage order, are zeroed before each preconditioner pass
+    p.n_obs_direct_big = 0;
+    for (int b = 0; b <= kmax && kmax - b > MV_KSMALL; ++b) p.n_obs_direct_big = p.run_co[b + 1];
     for (int b = 0; b <= kmax; ++b) {
         const int k = kmax - b;
         const int64_t cnt = p.k_run_count[b];

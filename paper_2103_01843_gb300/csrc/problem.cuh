@@ -84,7 +84,7 @@ struct Problem {
     int32_t* mv_cam = nullptr;       // camera of every observation in storage order
     int32_t* c_off = nullptr;        // float offset of c_j = Q2^T r (storage order, 2k per landmark)
     int32_t* cam_list_st = nullptr;  // camera lists as storage-order observation indices
-    int64_t n_obs_direct_big = 0;    // observations of landmarks with k > 21 (first in storage order)
+    int64_t n_obs_direct_big = 0;    // observations of blocks split into row tiles (first in storage order)
     std::vector<int32_t> k_run_count;  // host: landmarks with k = k_max - b
     std::vector<int64_t> run_off, run_co;  // host: float / observation offset of run b
     // matvec work plan: tiles of the block pool streamed through shared memory

@@ -283,6 +283,21 @@ def test_heavy_reduced_system_and_matvec(pkg, heavy):
     assert rel_fro(M, Mref) < 1e-4
 
 
+def test_repeated_solves_keep_preconditioner_exact(pkg, heavy):
+    """Re-damping and re-solving with a new lambda rebuilds the block-Jacobi
+    blocks from scratch: no state of an earlier pass may leak into them."""
+    s = Rounded(heavy)
+    with pkg.Problem.from_scene(heavy) as p:
+        p.linearize()
+        for lam in (1e-3, 1e-1, 1e-2, 1e-1):
+            p.marginalize_qr(lam)
+            p.pcg_solve()
+            M, g = p.export_rcs_diag()
+            Mref, bt = oracle.rcs_diag(s, lam)
+            assert rel_fro(M, Mref) < 1e-4, (lam, rel_fro(M, Mref))
+            assert rel_fro(g, -bt) < 1e-4
+
+
 def test_pcg_solution_and_back_substitution(pkg, tiny):
     s = Rounded(tiny)
     lam = 1e-3
