@@ -309,19 +309,22 @@ k_linearize_block(LinArgs A, const int32_t* __restrict__ order, int count) {
     marginalize_landmark<BIG_TEAM>(A, order[blockIdx.x], smem, red);
 }
 
-// D_p^2 = clamp(diag(J_p^T J_p), 1e-6, 1e32) per camera, one warp per
-// camera summing over its observations in a fixed order (deterministic).
-__global__ void k_camera_diag(int n_cam, const float* __restrict__ cams, const float* __restrict__ pts,
-                              const int32_t* __restrict__ obs_pt_s, const float2* __restrict__ obs_xy_s,
-                              const int32_t* __restrict__ cam_off, const int32_t* __restrict__ cam_list,
-                              float* __restrict__ dp2) {
-    const int cam = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (cam >= n_cam) return;
+// D_p^2 = clamp(diag(J_p^T J_p), 1e-6, 1e32) per camera: one CTA per camera,
+// threads strided over its observations, then a fixed-order block reduction
+// (deterministic).
+constexpr int CD_THREADS = 256;
+__global__ void __launch_bounds__(CD_THREADS)
+k_camera_diag(int n_cam, const float* __restrict__ cams, const float* __restrict__ pts,
+              const int32_t* __restrict__ obs_pt_s, const float2* __restrict__ obs_xy_s,
+              const int32_t* __restrict__ cam_off, const int32_t* __restrict__ cam_list,
+              float* __restrict__ dp2) {
+    __shared__ float part[CD_THREADS / 32][9];
+    const int cam = blockIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float acc[9];
 #pragma unroll
     for (int c = 0; c < 9; ++c) acc[c] = 0.f;
-    for (int e = cam_off[cam] + lane; e < cam_off[cam + 1]; e += 32) {
+    for (int e = cam_off[cam] + threadIdx.x; e < cam_off[cam + 1]; e += CD_THREADS) {
         const int s = cam_list[e];
         const int j = obs_pt_s[s];
         const float2 z = obs_xy_s[s];
@@ -333,7 +336,13 @@ __global__ void k_camera_diag(int n_cam, const float* __restrict__ cams, const f
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
         const float v = warp_sum(acc[c]);
-        if (lane == 0) dp2[9 * cam + c] = fminf(fmaxf(v, 1e-6f), 1e32f);
+        if (lane == 0) part[w][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 9) {
+        float v = 0.f;
+        for (int q = 0; q < CD_THREADS / 32; ++q) v += part[q][threadIdx.x];
+        dp2[9 * cam + threadIdx.x] = fminf(fmaxf(v, 1e-6f), 1e32f);
     }
 }
 
@@ -384,8 +393,8 @@ void configure_linearize(Problem& p) {
 
 void launch_camera_diag(Problem& p) {
     count_launches(p, 1);
-    k_camera_diag<<<ceil_div((int64_t)p.n_cam * 32, 128), 128, 0, p.stream>>>(
-        p.n_cam, p.cams, p.pts, p.obs_pt_s, p.obs_xy_s, p.cam_off, p.cam_list, p.dp2);
+    k_camera_diag<<<p.n_cam, CD_THREADS, 0, p.stream>>>(p.n_cam, p.cams, p.pts, p.obs_pt_s, p.obs_xy_s, p.cam_off,
+                                                       p.cam_list, p.dp2);
     BA_LAUNCH_CHECK();
 }
 

@@ -41,13 +41,20 @@ constexpr int MV_UMAX = 45;         // rows of one big tile (multiple of MV_CONS
 constexpr uint64_t MV_WAIT_NS = 2000000000ull;
 
 constexpr int MV_STAGE_R = 2048;    // bytes of c_j values per stage (preconditioner mode)
-constexpr int SM_STAGE_C_OFF = MV_STAGES * MV_STAGE_A;
-constexpr int SM_STAGE_R_OFF = SM_STAGE_C_OFF + MV_STAGES * MV_STAGE_C;
-constexpr int SM_U_OFF = SM_STAGE_R_OFF + MV_STAGES * MV_STAGE_R;
-constexpr int SM_BAR_OFF = SM_U_OFF + MV_STAGES * MV_UMAX * 4;
-constexpr int SM_DESC_OFF = SM_BAR_OFF + 2 * MV_STAGES * 8;  // tile record of each stage
-constexpr int SM_FLAG_OFF = SM_DESC_OFF + MV_STAGES * 32;
-constexpr int SM_Y_OFF = SM_FLAG_OFF + 16;
+// Shared-memory layout for NS stages; ACC_OFF starts the per-CTA
+// accumulators (y in matvec mode, the camera blocks in preconditioner mode).
+template <int NS>
+struct Layout {
+    static constexpr int STAGE_C_OFF = NS * MV_STAGE_A;
+    static constexpr int STAGE_R_OFF = STAGE_C_OFF + NS * MV_STAGE_C;
+    static constexpr int U_OFF = STAGE_R_OFF + NS * MV_STAGE_R;
+    static constexpr int BAR_OFF = (U_OFF + NS * MV_UMAX * 4 + 7) & ~7;
+    static constexpr int DESC_OFF = BAR_OFF + 2 * NS * 8;  // tile record of each stage
+    static constexpr int FLAG_OFF = DESC_OFF + NS * 32;
+    static constexpr int ACC_OFF = FLAG_OFF + 16;
+};
+constexpr int SMEM_LIMIT = 227 * 1024;
+constexpr int PC_STAGES = 3;  // preconditioner mode with camera blocks in shared memory
 
 enum : int16_t { TILE_SMALL = 0, TILE_BIG = 1, TILE_GLOBAL = 2 };
 
@@ -82,6 +89,7 @@ struct MvArgs {
     uint32_t* err;
     const float* cpool;  // preconditioner mode: c_j in storage order
     float* rec;          // preconditioner mode: REC floats per observation (storage order)
+    float* mpart;        // preconditioner mode, camera blocks in smem: REC * n_cam per CTA
 };
 
 // --- PTX wrappers ---------------------------------------------------------------
@@ -224,9 +232,26 @@ __device__ __forceinline__ void rec_add(float* __restrict__ rec, const float acc
     for (int m = 0; m < REC; ++m) atomicAdd(rec + m, acc[m]);
 }
 
+// A slot's record either goes to its camera's block in the CTA's shared
+// accumulator (macc != nullptr) or to the observation's record in global
+// memory (stored, or added when a block is split over several tiles).
+__device__ __forceinline__ void rec_out(const MvArgs& a, float* macc, int cam, int64_t obs, bool add,
+                                        const float acc[REC]) {
+    if (macc) {
+        float* m = macc + cam * REC;
+#pragma unroll
+        for (int q = 0; q < REC; ++q) atomicAdd(m + q, acc[q]);
+    } else if (add) {
+        rec_add(a.rec + obs * REC, acc);
+    } else {
+        rec_store(a.rec + obs * REC, acc);
+    }
+}
+
 // whole staged blocks, one slot per thread
 __device__ __forceinline__ void precond_blocks(const MvArgs& a, const MvTile& tile, const float* __restrict__ blocks,
-                                               const float* __restrict__ cvals, int tid) {
+                                               const int32_t* __restrict__ sc, const float* __restrict__ cvals,
+                                               int tid, float* macc) {
     const int k = tile.k, nc = 9 * k, nr = 2 * k;
     const int64_t bf = pad4(18LL * k * k);
     for (int q = tid; q < tile.count * k; q += MV_CONSUMERS * 32) {
@@ -235,25 +260,26 @@ __device__ __forceinline__ void precond_blocks(const MvArgs& a, const MvTile& ti
 #pragma unroll
         for (int m = 0; m < REC; ++m) acc[m] = 0.f;
         slot_accumulate(blocks + l * bf, cvals + l * nr, nc, 0, nr, s, acc);
-        rec_store(a.rec + (int64_t)(tile.cam_off + q) * REC, acc);
+        rec_out(a, macc, sc[q], tile.cam_off + q, false, acc);
     }
 }
 
-// rows [r0, r0 + nrows) of one block (staged): partial records added atomically
+// rows [r0, r0 + nrows) of one block (staged): partial records
 __device__ __forceinline__ void precond_rows(const MvArgs& a, const MvTile& tile, const float* __restrict__ sa,
-                                             const float* __restrict__ cvals, int tid) {
+                                             const int32_t* __restrict__ sc, const float* __restrict__ cvals,
+                                             int tid, float* macc) {
     const int k = tile.k, nc = 9 * k;
     for (int s = tid; s < k; s += MV_CONSUMERS * 32) {
         float acc[REC];
 #pragma unroll
         for (int m = 0; m < REC; ++m) acc[m] = 0.f;
         slot_accumulate(sa, cvals, nc, 0, tile.count, s, acc);
-        rec_add(a.rec + (int64_t)(tile.cam_off + s) * REC, acc);
+        rec_out(a, macc, sc[s], tile.cam_off + s, true, acc);
     }
 }
 
 // a block read from global memory (k > MV_KBIG)
-__device__ void precond_global(const MvArgs& a, const MvTile& tile, int tid) {
+__device__ void precond_global(const MvArgs& a, const MvTile& tile, int tid, float* macc) {
     const int j = a.lm_by_k[tile.first];
     const int k = a.pt_off[j + 1] - a.pt_off[j], nc = 9 * k, nr = 2 * k;
     const float* Aj = a.apool + a.a_off[j];
@@ -263,7 +289,7 @@ __device__ void precond_global(const MvArgs& a, const MvTile& tile, int tid) {
 #pragma unroll
         for (int m = 0; m < REC; ++m) acc[m] = 0.f;
         slot_accumulate(Aj, cj, nc, 0, nr, s, acc);
-        rec_store(a.rec + (int64_t)(tile.cam_off + s) * REC, acc);
+        rec_out(a, macc, a.mv_cam[tile.cam_off + s], tile.cam_off + s, false, acc);
     }
 }
 
@@ -382,14 +408,21 @@ __device__ __forceinline__ int tile_warps(const MvTile& t, int mode) {
     return w < 1 ? 1 : (w > MV_CONSUMERS ? MV_CONSUMERS : w);
 }
 
-template <int MODE, bool SMEM_Y>
+// MODE_MATVEC: y (SMEM_ACC: per-CTA copy of y in shared memory);
+// MODE_PRECOND: per-observation records, or (SMEM_ACC) the camera blocks
+// accumulated per CTA in shared memory and written as one partial per CTA.
+template <int MODE, bool SMEM_ACC, int NS>
 __global__ void __launch_bounds__(MV_THREADS, 1) k_matvec_tiles(MvArgs a) {
+    using L = Layout<NS>;
+    constexpr int MV_STAGES = NS;
     extern __shared__ __align__(128) unsigned char smem[];
     if (a.S != nullptr && a.S->done) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float* ys = reinterpret_cast<float*>(smem + SM_Y_OFF);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + SM_FLAG_OFF);
-    const uint32_t bar0 = smem_u32(smem + SM_BAR_OFF);
+    float* ys = reinterpret_cast<float*>(smem + L::ACC_OFF);
+    const int acc_n = MODE == MODE_MATVEC ? 9 * a.n_cam : REC * a.n_cam;
+    float* macc = (MODE == MODE_PRECOND && SMEM_ACC) ? ys : nullptr;
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L::FLAG_OFF);
+    const uint32_t bar0 = smem_u32(smem + L::BAR_OFF);
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
     auto empty_bar = [&](int s) { return bar0 + 8u * (MV_STAGES + s); };
 
@@ -401,17 +434,17 @@ __global__ void __launch_bounds__(MV_THREADS, 1) k_matvec_tiles(MvArgs a) {
         *abort_flag = 0;
         mbar_fence_init();
     }
-    if (MODE == MODE_MATVEC && SMEM_Y)
-        for (int i = threadIdx.x; i < 9 * a.n_cam; i += MV_THREADS) ys[i] = 0.f;
+    if (SMEM_ACC)
+        for (int i = threadIdx.x; i < acc_n; i += MV_THREADS) ys[i] = 0.f;
     __syncthreads();
-    float* yt = SMEM_Y ? ys : a.y;
+    float* yt = SMEM_ACC ? ys : a.y;
 
     const int tb = a.tile_begin[blockIdx.x], te = a.tile_begin[blockIdx.x + 1];
     if (warp == 0) {
         // producer warp: tile records are fetched 32 at a time (one coalesced
         // load, lane l holds record base + l), lane 0 publishes each record in
         // the stage's descriptor slot and issues the bulk copies
-        MvTile* desc = reinterpret_cast<MvTile*>(smem + SM_DESC_OFF);
+        MvTile* desc = reinterpret_cast<MvTile*>(smem + L::DESC_OFF);
         int issued = 0;
         bool stop = false;
         for (int base = tb; base < te && !stop; base += 32) {
@@ -450,10 +483,10 @@ __global__ void __launch_bounds__(MV_THREADS, 1) k_matvec_tiles(MvArgs a) {
                             mbar_expect_tx(full_bar(s), (uint32_t)tile.bytes + cbytes + rbytes);
                             bulk_g2s(smem_u32(smem + s * MV_STAGE_A), a.apool + tile.a_off, (uint32_t)tile.bytes,
                                      full_bar(s));
-                            bulk_g2s(smem_u32(smem + SM_STAGE_C_OFF + s * MV_STAGE_C), a.mv_cam + c4, cbytes,
+                            bulk_g2s(smem_u32(smem + L::STAGE_C_OFF + s * MV_STAGE_C), a.mv_cam + c4, cbytes,
                                      full_bar(s));
                             if (MODE == MODE_PRECOND)
-                                bulk_g2s(smem_u32(smem + SM_STAGE_R_OFF + s * MV_STAGE_R), a.cpool + r4, rbytes,
+                                bulk_g2s(smem_u32(smem + L::STAGE_R_OFF + s * MV_STAGE_R), a.cpool + r4, rbytes,
                                          full_bar(s));
                         }
                         ++issued;
@@ -475,11 +508,11 @@ __global__ void __launch_bounds__(MV_THREADS, 1) k_matvec_tiles(MvArgs a) {
         for (int t = tb; t < te; ++t) {
             const int i = t - tb, s = i % MV_STAGES;
             if (!mbar_wait(full_bar(s), (i / MV_STAGES) & 1, abort_flag, a.err)) break;
-            const MvTile tile = reinterpret_cast<const MvTile*>(smem + SM_DESC_OFF)[s];
+            const MvTile tile = reinterpret_cast<const MvTile*>(smem + L::DESC_OFF)[s];
             const float* sa = reinterpret_cast<const float*>(smem + s * MV_STAGE_A);
-            const int32_t* sc = reinterpret_cast<const int32_t*>(smem + SM_STAGE_C_OFF + s * MV_STAGE_C) +
+            const int32_t* sc = reinterpret_cast<const int32_t*>(smem + L::STAGE_C_OFF + s * MV_STAGE_C) +
                                 (tile.cam_off & 3);
-            float* ub = reinterpret_cast<float*>(smem + SM_U_OFF) + s * MV_UMAX;
+            float* ub = reinterpret_cast<float*>(smem + L::U_OFF) + s * MV_UMAX;
             // A tile rarely needs all consumer warps; successive tiles start at
             // successive groups of warps (rotation by the warps the tile needs),
             // so that the tiles in flight are worked on by disjoint warps.
@@ -492,21 +525,25 @@ __global__ void __launch_bounds__(MV_THREADS, 1) k_matvec_tiles(MvArgs a) {
             } else {
                 const int tid = vcw * 32 + lane;
                 const int64_t r_first = 2LL * tile.cam_off + (tile.kind == TILE_BIG ? tile.r0 : 0);
-                const float* sr = reinterpret_cast<const float*>(smem + SM_STAGE_R_OFF + s * MV_STAGE_R) + (r_first & 3);
-                if (tile.kind == TILE_SMALL) precond_blocks(a, tile, sa, sr, tid);
-                else if (tile.kind == TILE_BIG) precond_rows(a, tile, sa, sr, tid);
-                else precond_global(a, tile, tid);
+                const float* sr = reinterpret_cast<const float*>(smem + L::STAGE_R_OFF + s * MV_STAGE_R) + (r_first & 3);
+                if (tile.kind == TILE_SMALL) precond_blocks(a, tile, sa, sc, sr, tid, macc);
+                else if (tile.kind == TILE_BIG) precond_rows(a, tile, sa, sc, sr, tid, macc);
+                else precond_global(a, tile, tid, macc);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(empty_bar(s));
         }
     }
     __syncthreads();
-    if (MODE == MODE_MATVEC && SMEM_Y) {
-        for (int i = threadIdx.x; i < 9 * a.n_cam; i += MV_THREADS) {
+    if (MODE == MODE_MATVEC && SMEM_ACC) {
+        for (int i = threadIdx.x; i < acc_n; i += MV_THREADS) {
             const float val = ys[i];
             if (val != 0.f) atomicAdd(a.y + i, val);
         }
+    }
+    if (MODE == MODE_PRECOND && SMEM_ACC) {
+        float* dst = a.mpart + (int64_t)blockIdx.x * acc_n;
+        for (int i = threadIdx.x; i < acc_n; i += MV_THREADS) dst[i] = ys[i];
     }
 }
 
@@ -516,12 +553,13 @@ __global__ void k_add_damping(int n, const float* __restrict__ dp2, float lam, c
     if (i < n) y[i] += lam * dp2[i] * v[i];
 }
 
-bool smem_y(const Problem& p) { return SM_Y_OFF + 36 * (int64_t)p.n_cam <= 227 * 1024; }
-size_t smem_bytes(const Problem& p) { return SM_Y_OFF + (smem_y(p) ? 36 * (size_t)p.n_cam : 0); }
+bool smem_y(const Problem& p) { return Layout<MV_STAGES>::ACC_OFF + 36 * (int64_t)p.n_cam <= SMEM_LIMIT; }
+size_t smem_bytes(const Problem& p) { return Layout<MV_STAGES>::ACC_OFF + (smem_y(p) ? 36 * (size_t)p.n_cam : 0); }
+size_t precond_smem_bytes(const Problem& p) { return Layout<PC_STAGES>::ACC_OFF + 4 * (size_t)REC * p.n_cam; }
 
 MvArgs make_args(Problem& p, const float* v, float* y, const PcgScalars* S) {
     return MvArgs{static_cast<const MvTile*>(p.mv_tiles), p.mv_tile_begin, p.apool, p.mv_cam, p.lm_by_k, p.pt_off,
-                  p.obs_cam_s, p.a_off, v, y, p.n_cam, S, p.err, p.cpool, p.prec};
+                  p.obs_cam_s, p.a_off, v, y, p.n_cam, S, p.err, p.cpool, p.prec, p.mpart};
 }
 
 }  // namespace
@@ -619,28 +657,43 @@ int matvec_ctas_per_sm() { return 1; }
 
 void configure_matvec(Problem& p) {
     const int sm = (int)smem_bytes(p);
-    BA_CUDA_TRY(cudaFuncSetAttribute(k_matvec_tiles<MODE_MATVEC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    BA_CUDA_TRY(cudaFuncSetAttribute(k_matvec_tiles<MODE_MATVEC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    BA_CUDA_TRY(cudaFuncSetAttribute(k_matvec_tiles<MODE_PRECOND, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)SM_Y_OFF));
+    BA_CUDA_TRY(cudaFuncSetAttribute(k_matvec_tiles<MODE_MATVEC, true, MV_STAGES>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    BA_CUDA_TRY(cudaFuncSetAttribute(k_matvec_tiles<MODE_MATVEC, false, MV_STAGES>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    BA_CUDA_TRY(cudaFuncSetAttribute(k_matvec_tiles<MODE_PRECOND, false, MV_STAGES>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Layout<MV_STAGES>::ACC_OFF));
+    if (precond_smem_bytes(p) <= SMEM_LIMIT)
+        BA_CUDA_TRY(cudaFuncSetAttribute(k_matvec_tiles<MODE_PRECOND, true, PC_STAGES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)precond_smem_bytes(p)));
 }
 
 void launch_matvec_raw(Problem& p, const float* v, float* y, const PcgScalars* S) {
     const MvArgs a = make_args(p, v, y, S);
-    if (smem_y(p)) k_matvec_tiles<MODE_MATVEC, true><<<p.mv_grid, MV_THREADS, smem_bytes(p), p.stream>>>(a);
-    else k_matvec_tiles<MODE_MATVEC, false><<<p.mv_grid, MV_THREADS, smem_bytes(p), p.stream>>>(a);
+    if (smem_y(p)) k_matvec_tiles<MODE_MATVEC, true, MV_STAGES><<<p.mv_grid, MV_THREADS, smem_bytes(p), p.stream>>>(a);
+    else k_matvec_tiles<MODE_MATVEC, false, MV_STAGES><<<p.mv_grid, MV_THREADS, smem_bytes(p), p.stream>>>(a);
     BA_LAUNCH_CHECK();
 }
 
-// K3, first half: per-observation records of the block-Jacobi blocks and the
-// right-hand side, streamed through the same tile pipeline
-void launch_precond_records(Problem& p) {
+// K3, first half, streamed through the same tile pipeline: the camera
+// blocks accumulated per CTA in shared memory (written as one partial per
+// CTA) when they fit, else per-observation records.  Returns true for the
+// partials form.
+bool launch_precond_records(Problem& p) {
+    const MvArgs a = make_args(p, nullptr, nullptr, nullptr);
+    if (precond_smem_bytes(p) <= SMEM_LIMIT) {
+        k_matvec_tiles<MODE_PRECOND, true, PC_STAGES><<<p.mv_grid, MV_THREADS, precond_smem_bytes(p), p.stream>>>(a);
+        BA_LAUNCH_CHECK();
+        return true;
+    }
     if (p.n_obs_direct_big > 0)
         BA_CUDA_TRY(cudaMemsetAsync(p.prec, 0, sizeof(float) * REC * p.n_obs_direct_big, p.stream));
-    const MvArgs a = make_args(p, nullptr, nullptr, nullptr);
-    k_matvec_tiles<MODE_PRECOND, false><<<p.mv_grid, MV_THREADS, SM_Y_OFF, p.stream>>>(a);
+    k_matvec_tiles<MODE_PRECOND, false, MV_STAGES><<<p.mv_grid, MV_THREADS, Layout<MV_STAGES>::ACC_OFF, p.stream>>>(a);
     BA_LAUNCH_CHECK();
+    return false;
 }
+
+bool precond_uses_partials(const Problem& p) { return precond_smem_bytes(p) <= SMEM_LIMIT; }
 
 void launch_matvec(Problem& p, const float* v, float* y, bool add_damping) {
     count_launches(p, 1 + (add_damping ? 1 : 0));

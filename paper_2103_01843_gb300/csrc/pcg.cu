@@ -57,57 +57,79 @@ __device__ int cholesky_inverse9(const float* M, float* Minv) {
     return 0;
 }
 
-// Second half of K3: per camera, the records of its observations (written by
-// the tile pipeline, 54 floats each: upper triangle of A_s^T A_s and A_s^T c)
-// are summed in a fixed order, lambda D_p^2 is added and the block inverted.
+// Second half of K3: per camera, the 54 sums (upper triangle of
+// sum_j A_ji^T A_ji and sum_j A_ji^T c_j) are formed in a fixed order, lambda
+// D_p^2 is added and the 9x9 block inverted by Cholesky.
+__device__ void finish_block(int cam, const float* tot, const float* __restrict__ dp2, float lam,
+                             float* __restrict__ mdiag, float* __restrict__ minv, float* __restrict__ g,
+                             uint32_t* err) {
+    float M[81], Mi[81];
+    int t = 0;
+    for (int u = 0; u < 9; ++u)
+        for (int v = u; v < 9; ++v) {
+            M[u * 9 + v] = tot[t];
+            M[v * 9 + u] = tot[t];
+            ++t;
+        }
+    for (int u = 0; u < 9; ++u) M[u * 9 + u] += lam * dp2[9 * cam + u];
+    for (int i = 0; i < 81; ++i) mdiag[81 * (int64_t)cam + i] = M[i];
+    if (cholesky_inverse9(M, Mi) != 0) {
+        // not positive definite in FP32: fall back to the diagonal (Jacobi)
+        atomicOr(err, ERRBIT_PRECOND);
+        for (int i = 0; i < 81; ++i) Mi[i] = 0.f;
+        for (int u = 0; u < 9; ++u) Mi[u * 9 + u] = M[u * 9 + u] > 0.f ? 1.f / M[u * 9 + u] : 0.f;
+    }
+    for (int i = 0; i < 81; ++i) minv[81 * (int64_t)cam + i] = Mi[i];
+    for (int u = 0; u < 9; ++u) g[9 * cam + u] = -tot[45 + u];
+}
+
+// from per-observation records: one warp reads one record (27 float2 lanes)
 __global__ void __launch_bounds__(32 * PC_WARPS)
 k_precond_reduce(int n_cam, const int32_t* __restrict__ cam_off, const int32_t* __restrict__ cam_list_st,
                  const float* __restrict__ rec, const float* __restrict__ dp2, const float lam,
                  float* __restrict__ mdiag, float* __restrict__ minv, float* __restrict__ g, uint32_t* err) {
-    __shared__ float part[PC_WARPS][54];
+    __shared__ float2 part[PC_WARPS][27];
     __shared__ float tot[54];
     const int cam = blockIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    float acc[54];
-#pragma unroll
-    for (int i = 0; i < 54; ++i) acc[i] = 0.f;
-    for (int e = cam_off[cam] + threadIdx.x; e < cam_off[cam + 1]; e += 32 * PC_WARPS) {
-        const float* r = rec + (int64_t)cam_list_st[e] * 54;
-#pragma unroll
-        for (int i = 0; i < 54; ++i) acc[i] += __ldg(r + i);
-    }
-#pragma unroll
-    for (int i = 0; i < 54; ++i) {
-        const float v = warp_sum(acc[i]);
-        if (lane == 0) part[w][i] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 54) {
-        float s = 0.f;
-        for (int m = 0; m < PC_WARPS; ++m) s += part[m][threadIdx.x];
-        tot[threadIdx.x] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float M[81], Mi[81];
-        int t = 0;
-        for (int u = 0; u < 9; ++u)
-            for (int v = u; v < 9; ++v) {
-                M[u * 9 + v] = tot[t];
-                M[v * 9 + u] = tot[t];
-                ++t;
-            }
-        for (int u = 0; u < 9; ++u) M[u * 9 + u] += lam * dp2[9 * cam + u];
-        for (int i = 0; i < 81; ++i) mdiag[81 * (int64_t)cam + i] = M[i];
-        if (cholesky_inverse9(M, Mi) != 0) {
-            // not positive definite in FP32: fall back to the diagonal (Jacobi)
-            atomicOr(err, ERRBIT_PRECOND);
-            for (int i = 0; i < 81; ++i) Mi[i] = 0.f;
-            for (int u = 0; u < 9; ++u) Mi[u * 9 + u] = M[u * 9 + u] > 0.f ? 1.f / M[u * 9 + u] : 0.f;
+    float2 acc = make_float2(0.f, 0.f);
+    if (lane < 27) {
+        for (int e = cam_off[cam] + w; e < cam_off[cam + 1]; e += PC_WARPS) {
+            const float2 r = __ldg(reinterpret_cast<const float2*>(rec + (int64_t)cam_list_st[e] * 54) + lane);
+            acc.x += r.x;
+            acc.y += r.y;
         }
-        for (int i = 0; i < 81; ++i) minv[81 * (int64_t)cam + i] = Mi[i];
-        for (int u = 0; u < 9; ++u) g[9 * cam + u] = -tot[45 + u];
+        part[w][lane] = acc;
     }
+    __syncthreads();
+    if (threadIdx.x < 27) {
+        float2 s2 = make_float2(0.f, 0.f);
+        for (int m = 0; m < PC_WARPS; ++m) {
+            s2.x += part[m][threadIdx.x].x;
+            s2.y += part[m][threadIdx.x].y;
+        }
+        tot[2 * threadIdx.x] = s2.x;
+        tot[2 * threadIdx.x + 1] = s2.y;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) finish_block(cam, tot, dp2, lam, mdiag, minv, g, err);
+}
+
+// from per-CTA partial blocks (grid x 54 n_cam), summed in CTA order
+__global__ void __launch_bounds__(64)
+k_precond_reduce_partials(int n_cam, int grid, const float* __restrict__ mpart, const float* __restrict__ dp2,
+                          const float lam, float* __restrict__ mdiag, float* __restrict__ minv,
+                          float* __restrict__ g, uint32_t* err) {
+    __shared__ float tot[54];
+    const int cam = blockIdx.x;
+    if (threadIdx.x < 54) {
+        float acc = 0.f;
+        const float* src = mpart + (int64_t)cam * 54 + threadIdx.x;
+        for (int b = 0; b < grid; ++b) acc += __ldg(src + (int64_t)b * 54 * n_cam);
+        tot[threadIdx.x] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) finish_block(cam, tot, dp2, lam, mdiag, minv, g, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -232,10 +254,15 @@ k_pcg_update(int n_cam, const float* __restrict__ g, const float* __restrict__ d
 }  // namespace
 
 void launch_precond_rhs(Problem& p) {
-    count_launches(p, 2 + (p.n_obs_direct_big > 0 ? 1 : 0));
-    launch_precond_records(p);
-    k_precond_reduce<<<p.n_cam, 32 * PC_WARPS, 0, p.stream>>>(p.n_cam, p.cam_off, p.cam_list_st, p.prec, p.dp2,
-                                                             (float)p.lambda_damped, p.mdiag, p.minv, p.g, p.err);
+    if (launch_precond_records(p)) {
+        count_launches(p, 2);
+        k_precond_reduce_partials<<<p.n_cam, 64, 0, p.stream>>>(p.n_cam, p.mv_grid, p.mpart, p.dp2,
+                                                                (float)p.lambda_damped, p.mdiag, p.minv, p.g, p.err);
+    } else {
+        count_launches(p, 2 + (p.n_obs_direct_big > 0 ? 1 : 0));
+        k_precond_reduce<<<p.n_cam, 32 * PC_WARPS, 0, p.stream>>>(p.n_cam, p.cam_off, p.cam_list_st, p.prec, p.dp2,
+                                                                 (float)p.lambda_damped, p.mdiag, p.minv, p.g, p.err);
+    }
     BA_LAUNCH_CHECK();
 }
 

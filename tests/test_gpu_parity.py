@@ -298,6 +298,26 @@ def test_repeated_solves_keep_preconditioner_exact(pkg, heavy):
             assert rel_fro(g, -bt) < 1e-4
 
 
+def test_many_cameras_records_path(pkg):
+    """With many cameras the per-camera blocks do not fit the matvec CTA's
+    shared memory: the preconditioner goes through per-observation records."""
+    sc = make_scene("small", 9, n_cam=700, n_pt=2500, p=0.25, cap=40)
+    s = Rounded(sc)
+    lam = 1e-3
+    with pkg.Problem.from_scene(sc) as p:
+        p.linearize()
+        for lam in (1e-3, 1e-1):
+            p.marginalize_qr(lam)
+            p.pcg_solve()
+            M, g = p.export_rcs_diag()
+            Mref, bt = oracle.rcs_diag(s, lam)
+            assert rel_fro(M, Mref) < 1e-4
+            assert rel_fro(g, -bt) < 1e-4
+        V = np.random.default_rng(2).normal(size=(2, 9 * s.n_cam)).astype(np.float32)
+        Y = np.stack([p.matvec(v) for v in V])
+    assert rel_fro(Y, oracle.rcs_matvec(s, lam, V)) < 1e-4
+
+
 def test_pcg_solution_and_back_substitution(pkg, tiny):
     s = Rounded(tiny)
     lam = 1e-3
