@@ -423,8 +423,7 @@ ba_status ba_create(const double* cams, int32_t n_cam, const double* pts, int32_
         p.q = dalloc<float>(p, nv);
         p.minv = dalloc<float>(p, 81 * (int64_t)n_cam);
         p.mdiag = dalloc<float>(p, 81 * (int64_t)n_cam);
-        if (precond_uses_partials(p)) p.mpart = dalloc<float>(p, 54LL * n_cam * p.mv_grid);
-        else p.prec = dalloc<float>(p, 54 * n_obs);
+        p.prec = dalloc<float>(p, 56 * n_obs);
         p.dl = dalloc<float>(p, 3 * (int64_t)n_pt);
         p.partials = dalloc<double>(p, std::max<int64_t>((n_pt + 3) / 4 + 1, p.red_grid + 1));
         BA_CUDA_TRY(cudaMemsetAsync(p.x, 0, sizeof(float) * nv, p.stream));

@@ -54,7 +54,6 @@ struct Layout {
     static constexpr int ACC_OFF = FLAG_OFF + 16;
 };
 constexpr int SMEM_LIMIT = 227 * 1024;
-constexpr int PC_STAGES = 3;  // preconditioner mode with camera blocks in shared memory
 
 enum : int16_t { TILE_SMALL = 0, TILE_BIG = 1, TILE_GLOBAL = 2 };
 
@@ -72,6 +71,7 @@ static_assert(sizeof(MvTile) == 32, "tile record size");
 
 enum : int { MODE_MATVEC = 0, MODE_PRECOND = 1 };
 constexpr int REC = 54;  // per-observation record: 45 entries of A_s^T A_s (upper, row-major) + A_s^T c
+constexpr int REC_STRIDE = 56;  // floats between records in global memory (16-byte aligned, 2 pad floats)
 
 struct MvArgs {
     const MvTile* tiles;
@@ -89,7 +89,6 @@ struct MvArgs {
     uint32_t* err;
     const float* cpool;  // preconditioner mode: c_j in storage order
     float* rec;          // preconditioner mode: REC floats per observation (storage order)
-    float* mpart;        // preconditioner mode, camera blocks in smem: REC * n_cam per CTA
 };
 
 // --- PTX wrappers ---------------------------------------------------------------
@@ -223,35 +222,31 @@ __device__ __forceinline__ void slot_accumulate(const float* __restrict__ blk, c
 }
 
 __device__ __forceinline__ void rec_store(float* __restrict__ rec, const float acc[REC]) {
+    float4* r4 = reinterpret_cast<float4*>(rec);
 #pragma unroll
-    for (int m = 0; m < REC; ++m) rec[m] = acc[m];
+    for (int m = 0; m < REC / 4; ++m) r4[m] = make_float4(acc[4 * m], acc[4 * m + 1], acc[4 * m + 2], acc[4 * m + 3]);
+    r4[REC / 4] = make_float4(acc[REC - 2], acc[REC - 1], 0.f, 0.f);
 }
 
 __device__ __forceinline__ void rec_add(float* __restrict__ rec, const float acc[REC]) {
+    float4* r4 = reinterpret_cast<float4*>(rec);
 #pragma unroll
-    for (int m = 0; m < REC; ++m) atomicAdd(rec + m, acc[m]);
+    for (int m = 0; m < REC / 4; ++m)
+        atomicAdd(r4 + m, make_float4(acc[4 * m], acc[4 * m + 1], acc[4 * m + 2], acc[4 * m + 3]));
+    atomicAdd(r4 + REC / 4, make_float4(acc[REC - 2], acc[REC - 1], 0.f, 0.f));
 }
 
-// A slot's record either goes to its camera's block in the CTA's shared
-// accumulator (macc != nullptr) or to the observation's record in global
-// memory (stored, or added when a block is split over several tiles).
-__device__ __forceinline__ void rec_out(const MvArgs& a, float* macc, int cam, int64_t obs, bool add,
-                                        const float acc[REC]) {
-    if (macc) {
-        float* m = macc + cam * REC;
-#pragma unroll
-        for (int q = 0; q < REC; ++q) atomicAdd(m + q, acc[q]);
-    } else if (add) {
-        rec_add(a.rec + obs * REC, acc);
-    } else {
-        rec_store(a.rec + obs * REC, acc);
-    }
+// A slot's record is stored in the observation's record in global memory,
+// or added there when its block is split over several row tiles.
+__device__ __forceinline__ void rec_out(const MvArgs& a, int64_t obs, bool add, const float acc[REC]) {
+    if (add) rec_add(a.rec + obs * REC_STRIDE, acc);
+    else rec_store(a.rec + obs * REC_STRIDE, acc);
 }
 
 // whole staged blocks, one slot per thread
 __device__ __forceinline__ void precond_blocks(const MvArgs& a, const MvTile& tile, const float* __restrict__ blocks,
                                                const int32_t* __restrict__ sc, const float* __restrict__ cvals,
-                                               int tid, float* macc) {
+                                               int tid) {
     const int k = tile.k, nc = 9 * k, nr = 2 * k;
     const int64_t bf = pad4(18LL * k * k);
     for (int q = tid; q < tile.count * k; q += MV_CONSUMERS * 32) {
@@ -260,26 +255,26 @@ __device__ __forceinline__ void precond_blocks(const MvArgs& a, const MvTile& ti
 #pragma unroll
         for (int m = 0; m < REC; ++m) acc[m] = 0.f;
         slot_accumulate(blocks + l * bf, cvals + l * nr, nc, 0, nr, s, acc);
-        rec_out(a, macc, sc[q], tile.cam_off + q, false, acc);
+        rec_out(a, tile.cam_off + q, false, acc);
     }
 }
 
 // rows [r0, r0 + nrows) of one block (staged): partial records
 __device__ __forceinline__ void precond_rows(const MvArgs& a, const MvTile& tile, const float* __restrict__ sa,
                                              const int32_t* __restrict__ sc, const float* __restrict__ cvals,
-                                             int tid, float* macc) {
+                                             int tid) {
     const int k = tile.k, nc = 9 * k;
     for (int s = tid; s < k; s += MV_CONSUMERS * 32) {
         float acc[REC];
 #pragma unroll
         for (int m = 0; m < REC; ++m) acc[m] = 0.f;
         slot_accumulate(sa, cvals, nc, 0, tile.count, s, acc);
-        rec_out(a, macc, sc[s], tile.cam_off + s, true, acc);
+        rec_out(a, tile.cam_off + s, tile.count < 2 * k, acc);
     }
 }
 
 // a block read from global memory (k > MV_KBIG)
-__device__ void precond_global(const MvArgs& a, const MvTile& tile, int tid, float* macc) {
+__device__ void precond_global(const MvArgs& a, const MvTile& tile, int tid) {
     const int j = a.lm_by_k[tile.first];
     const int k = a.pt_off[j + 1] - a.pt_off[j], nc = 9 * k, nr = 2 * k;
     const float* Aj = a.apool + a.a_off[j];
@@ -289,7 +284,7 @@ __device__ void precond_global(const MvArgs& a, const MvTile& tile, int tid, flo
 #pragma unroll
         for (int m = 0; m < REC; ++m) acc[m] = 0.f;
         slot_accumulate(Aj, cj, nc, 0, nr, s, acc);
-        rec_out(a, macc, a.mv_cam[tile.cam_off + s], tile.cam_off + s, false, acc);
+        rec_out(a, tile.cam_off + s, false, acc);
     }
 }
 
@@ -409,8 +404,7 @@ __device__ __forceinline__ int tile_warps(const MvTile& t, int mode) {
 }
 
 // MODE_MATVEC: y (SMEM_ACC: per-CTA copy of y in shared memory);
-// MODE_PRECOND: per-observation records, or (SMEM_ACC) the camera blocks
-// accumulated per CTA in shared memory and written as one partial per CTA.
+// MODE_PRECOND: per-observation records (SMEM_ACC false).
 template <int MODE, bool SMEM_ACC, int NS>
 __global__ void __launch_bounds__(MV_THREADS, 1) k_matvec_tiles(MvArgs a) {
     using L = Layout<NS>;
@@ -419,8 +413,8 @@ __global__ void __launch_bounds__(MV_THREADS, 1) k_matvec_tiles(MvArgs a) {
     if (a.S != nullptr && a.S->done) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* ys = reinterpret_cast<float*>(smem + L::ACC_OFF);
-    const int acc_n = MODE == MODE_MATVEC ? 9 * a.n_cam : REC * a.n_cam;
-    float* macc = (MODE == MODE_PRECOND && SMEM_ACC) ? ys : nullptr;
+    static_assert(MODE == MODE_MATVEC || !SMEM_ACC, "records are written to global memory");
+    const int acc_n = 9 * a.n_cam;
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L::FLAG_OFF);
     const uint32_t bar0 = smem_u32(smem + L::BAR_OFF);
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
@@ -526,9 +520,9 @@ __global__ void __launch_bounds__(MV_THREADS, 1) k_matvec_tiles(MvArgs a) {
                 const int tid = vcw * 32 + lane;
                 const int64_t r_first = 2LL * tile.cam_off + (tile.kind == TILE_BIG ? tile.r0 : 0);
                 const float* sr = reinterpret_cast<const float*>(smem + L::STAGE_R_OFF + s * MV_STAGE_R) + (r_first & 3);
-                if (tile.kind == TILE_SMALL) precond_blocks(a, tile, sa, sc, sr, tid, macc);
-                else if (tile.kind == TILE_BIG) precond_rows(a, tile, sa, sc, sr, tid, macc);
-                else precond_global(a, tile, tid, macc);
+                if (tile.kind == TILE_SMALL) precond_blocks(a, tile, sa, sc, sr, tid);
+                else if (tile.kind == TILE_BIG) precond_rows(a, tile, sa, sc, sr, tid);
+                else precond_global(a, tile, tid);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(empty_bar(s));
@@ -541,10 +535,6 @@ __global__ void __launch_bounds__(MV_THREADS, 1) k_matvec_tiles(MvArgs a) {
             if (val != 0.f) atomicAdd(a.y + i, val);
         }
     }
-    if (MODE == MODE_PRECOND && SMEM_ACC) {
-        float* dst = a.mpart + (int64_t)blockIdx.x * acc_n;
-        for (int i = threadIdx.x; i < acc_n; i += MV_THREADS) dst[i] = ys[i];
-    }
 }
 
 __global__ void k_add_damping(int n, const float* __restrict__ dp2, float lam, const float* __restrict__ v,
@@ -555,14 +545,16 @@ __global__ void k_add_damping(int n, const float* __restrict__ dp2, float lam, c
 
 bool smem_y(const Problem& p) { return Layout<MV_STAGES>::ACC_OFF + 36 * (int64_t)p.n_cam <= SMEM_LIMIT; }
 size_t smem_bytes(const Problem& p) { return Layout<MV_STAGES>::ACC_OFF + (smem_y(p) ? 36 * (size_t)p.n_cam : 0); }
-size_t precond_smem_bytes(const Problem& p) { return Layout<PC_STAGES>::ACC_OFF + 4 * (size_t)REC * p.n_cam; }
 
 MvArgs make_args(Problem& p, const float* v, float* y, const PcgScalars* S) {
     return MvArgs{static_cast<const MvTile*>(p.mv_tiles), p.mv_tile_begin, p.apool, p.mv_cam, p.lm_by_k, p.pt_off,
-                  p.obs_cam_s, p.a_off, v, y, p.n_cam, S, p.err, p.cpool, p.prec, p.mpart};
+                  p.obs_cam_s, p.a_off, v, y, p.n_cam, S, p.err, p.cpool, p.prec};
 }
 
 }  // namespace
+
+// rows of one big tile of a k-block (a multiple of 4)
+int big_tile_rows(int k) { return std::min(MV_UMAX & ~3, (MV_STAGE_A / (36 * k)) & ~3); }
 
 // Host planning of the tiles: runs of equal-k blocks in storage order
 // (decreasing k), cut into stage-sized tiles, then contiguous tile ranges per
@@ -571,10 +563,12 @@ void plan_matvec(Problem& p) {
     std::vector<MvTile> tiles;
     const int kmax = p.k_max;
     // records of blocks that are split into row tiles are accumulated
-    // atomically: the observations of all landmarks with k > MV_KSMALL, which
-    // come first in storage order, are zeroed before each preconditioner pass
+    // atomically: the observations of the landmarks with k above the
+    // smallest split k, which come first in storage order, are zeroed before
+    // each preconditioner pass (the records of unsplit blocks are stored)
     p.n_obs_direct_big = 0;
-    for (int b = 0; b <= kmax && kmax - b > MV_KSMALL; ++b) p.n_obs_direct_big = p.run_co[b + 1];
+    for (int b = 0; b <= kmax && kmax - b > MV_KSMALL; ++b)
+        if (big_tile_rows(kmax - b) < 2 * (kmax - b)) p.n_obs_direct_big = p.run_co[b + 1];
     for (int b = 0; b <= kmax; ++b) {
         const int k = kmax - b;
         const int64_t cnt = p.k_run_count[b];
@@ -601,7 +595,7 @@ void plan_matvec(Problem& p) {
             }
         } else if (k <= MV_KBIG) {
             const int nc = 9 * k, nr = 2 * k;
-            const int rows = std::min(MV_UMAX & ~3, (MV_STAGE_A / (4 * nc)) & ~3);
+            const int rows = big_tile_rows(k);
             for (int64_t l = 0; l < cnt; ++l) {
                 for (int r0 = 0; r0 < nr; r0 += rows) {
                     MvTile t{};
@@ -663,9 +657,6 @@ void configure_matvec(Problem& p) {
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
     BA_CUDA_TRY(cudaFuncSetAttribute(k_matvec_tiles<MODE_PRECOND, false, MV_STAGES>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Layout<MV_STAGES>::ACC_OFF));
-    if (precond_smem_bytes(p) <= SMEM_LIMIT)
-        BA_CUDA_TRY(cudaFuncSetAttribute(k_matvec_tiles<MODE_PRECOND, true, PC_STAGES>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)precond_smem_bytes(p)));
 }
 
 void launch_matvec_raw(Problem& p, const float* v, float* y, const PcgScalars* S) {
@@ -675,25 +666,17 @@ void launch_matvec_raw(Problem& p, const float* v, float* y, const PcgScalars* S
     BA_LAUNCH_CHECK();
 }
 
-// K3, first half, streamed through the same tile pipeline: the camera
-// blocks accumulated per CTA in shared memory (written as one partial per
-// CTA) when they fit, else per-observation records.  Returns true for the
-// partials form.
-bool launch_precond_records(Problem& p) {
+// K3, first half, streamed through the same tile pipeline: one record of
+// REC floats per observation (A_s^T A_s upper triangle and A_s^T c_j), in
+// storage order.  Records of blocks split over row tiles are accumulated, so
+// their prefix is zeroed first.
+void launch_precond_records(Problem& p) {
     const MvArgs a = make_args(p, nullptr, nullptr, nullptr);
-    if (precond_smem_bytes(p) <= SMEM_LIMIT) {
-        k_matvec_tiles<MODE_PRECOND, true, PC_STAGES><<<p.mv_grid, MV_THREADS, precond_smem_bytes(p), p.stream>>>(a);
-        BA_LAUNCH_CHECK();
-        return true;
-    }
     if (p.n_obs_direct_big > 0)
-        BA_CUDA_TRY(cudaMemsetAsync(p.prec, 0, sizeof(float) * REC * p.n_obs_direct_big, p.stream));
+        BA_CUDA_TRY(cudaMemsetAsync(p.prec, 0, sizeof(float) * REC_STRIDE * p.n_obs_direct_big, p.stream));
     k_matvec_tiles<MODE_PRECOND, false, MV_STAGES><<<p.mv_grid, MV_THREADS, Layout<MV_STAGES>::ACC_OFF, p.stream>>>(a);
     BA_LAUNCH_CHECK();
-    return false;
 }
-
-bool precond_uses_partials(const Problem& p) { return precond_smem_bytes(p) <= SMEM_LIMIT; }
 
 void launch_matvec(Problem& p, const float* v, float* y, bool add_damping) {
     count_launches(p, 1 + (add_damping ? 1 : 0));

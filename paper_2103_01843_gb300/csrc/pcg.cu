@@ -19,117 +19,140 @@ namespace sqrtba {
 
 namespace {
 
-constexpr int PC_WARPS = 8;
+constexpr int PC_WARPS = 16;
 
 // ---------------------------------------------------------------------------
 // K3: per-camera preconditioner block and right-hand side
 // ---------------------------------------------------------------------------
-__device__ int cholesky_inverse9(const float* M, float* Minv) {
-    float L[81];
-    for (int i = 0; i < 81; ++i) L[i] = 0.f;
-    for (int jj = 0; jj < 9; ++jj) {
-        float s = M[jj * 9 + jj];
-        for (int m = 0; m < jj; ++m) s -= L[jj * 9 + m] * L[jj * 9 + m];
-        if (!(s > 0.f)) return -1;
-        const float l = sqrtf(s);
-        L[jj * 9 + jj] = l;
-        for (int i = jj + 1; i < 9; ++i) {
-            float t = M[i * 9 + jj];
-            for (int m = 0; m < jj; ++m) t -= L[i * 9 + m] * L[jj * 9 + m];
-            L[i * 9 + jj] = t / l;
-        }
+// Second half of K3, one warp per camera: the 54 sums (upper triangle of
+// sum_j A_ji^T A_ji and sum_j A_ji^T c_j) are expanded, lambda D_p^2 is added,
+// the 9x9 block is factored by Cholesky (lanes over the rows below the
+// pivot) and inverted column by column (lane c solves L L^T x = e_c).
+// sM, sL: 81 floats of shared memory each.
+__device__ void finish_block_warp(int cam, const float* tot, const float* __restrict__ dp2, float lam,
+                                  float* __restrict__ mdiag, float* __restrict__ minv, float* __restrict__ g,
+                                  uint32_t* err, float* sM, float* sL, int lane) {
+    for (int i = lane; i < 81; i += 32) {
+        const int u = i / 9, v = i - 9 * u;
+        const int lo = u < v ? u : v, hi = u < v ? v : u;
+        float m = tot[9 * lo - lo * (lo - 1) / 2 + (hi - lo)];
+        if (u == v) m += lam * dp2[9 * cam + u];
+        sM[i] = m;
+        sL[i] = 0.f;
+        mdiag[81 * (int64_t)cam + i] = m;
     }
-    // columns of M^-1: solve L L^T x = e_c
-    for (int c = 0; c < 9; ++c) {
-        float y[9];
-        for (int i = 0; i < 9; ++i) {
-            float s = i == c ? 1.f : 0.f;
-            for (int m = 0; m < i; ++m) s -= L[i * 9 + m] * y[m];
-            y[i] = s / L[i * 9 + i];
+    __syncwarp();
+    bool ok = true;
+    for (int j = 0; j < 9; ++j) {
+        float s = sM[j * 9 + j];
+        for (int m = 0; m < j; ++m) s -= sL[j * 9 + m] * sL[j * 9 + m];
+        ok = ok && s > 0.f;
+        const float l = s > 0.f ? sqrtf(s) : 1.f;
+        if (lane > j && lane < 9) {
+            float t = sM[lane * 9 + j];
+            for (int m = 0; m < j; ++m) t -= sL[lane * 9 + m] * sL[j * 9 + m];
+            sL[lane * 9 + j] = t / l;
         }
-        for (int i = 8; i >= 0; --i) {
-            float s = y[i];
-            for (int m = i + 1; m < 9; ++m) s -= L[m * 9 + i] * y[m];
-            y[i] = s / L[i * 9 + i];
-        }
-        for (int i = 0; i < 9; ++i) Minv[i * 9 + c] = y[i];
+        if (lane == 0) sL[j * 9 + j] = l;
+        __syncwarp();
     }
-    return 0;
+    if (lane < 9) {
+        const int c = lane;
+        float x[9];
+        if (ok) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                float t = i == c ? 1.f : 0.f;
+#pragma unroll
+                for (int m = 0; m < i; ++m) t -= sL[i * 9 + m] * x[m];
+                x[i] = t / sL[i * 9 + i];
+            }
+#pragma unroll
+            for (int i = 8; i >= 0; --i) {
+                float t = x[i];
+#pragma unroll
+                for (int m = i + 1; m < 9; ++m) t -= sL[m * 9 + i] * x[m];
+                x[i] = t / sL[i * 9 + i];
+            }
+        } else {
+            // not positive definite in FP32: fall back to the diagonal (Jacobi)
+#pragma unroll
+            for (int i = 0; i < 9; ++i) x[i] = 0.f;
+            const float d = sM[c * 9 + c];
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+                if (i == c) x[i] = d > 0.f ? 1.f / d : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) minv[81 * (int64_t)cam + i * 9 + c] = x[i];
+        g[9 * cam + c] = -tot[45 + c];
+    }
+    if (!ok && lane == 0) atomicOr(err, ERRBIT_PRECOND);
 }
 
-// Second half of K3: per camera, the 54 sums (upper triangle of
-// sum_j A_ji^T A_ji and sum_j A_ji^T c_j) are formed in a fixed order, lambda
-// D_p^2 is added and the 9x9 block inverted by Cholesky.
-__device__ void finish_block(int cam, const float* tot, const float* __restrict__ dp2, float lam,
-                             float* __restrict__ mdiag, float* __restrict__ minv, float* __restrict__ g,
-                             uint32_t* err) {
-    float M[81], Mi[81];
-    int t = 0;
-    for (int u = 0; u < 9; ++u)
-        for (int v = u; v < 9; ++v) {
-            M[u * 9 + v] = tot[t];
-            M[v * 9 + u] = tot[t];
-            ++t;
-        }
-    for (int u = 0; u < 9; ++u) M[u * 9 + u] += lam * dp2[9 * cam + u];
-    for (int i = 0; i < 81; ++i) mdiag[81 * (int64_t)cam + i] = M[i];
-    if (cholesky_inverse9(M, Mi) != 0) {
-        // not positive definite in FP32: fall back to the diagonal (Jacobi)
-        atomicOr(err, ERRBIT_PRECOND);
-        for (int i = 0; i < 81; ++i) Mi[i] = 0.f;
-        for (int u = 0; u < 9; ++u) Mi[u * 9 + u] = M[u * 9 + u] > 0.f ? 1.f / M[u * 9 + u] : 0.f;
-    }
-    for (int i = 0; i < 81; ++i) minv[81 * (int64_t)cam + i] = Mi[i];
-    for (int u = 0; u < 9; ++u) g[9 * cam + u] = -tot[45 + u];
-}
-
-// from per-observation records: one warp reads one record (27 float2 lanes)
+// from per-observation records (56 floats apart): a warp reads two records
+// at a time, lanes 0-13 and 16-29 one float4 each, four record pairs in
+// flight per warp; the camera's records are summed in a fixed order
 __global__ void __launch_bounds__(32 * PC_WARPS)
 k_precond_reduce(int n_cam, const int32_t* __restrict__ cam_off, const int32_t* __restrict__ cam_list_st,
                  const float* __restrict__ rec, const float* __restrict__ dp2, const float lam,
                  float* __restrict__ mdiag, float* __restrict__ minv, float* __restrict__ g, uint32_t* err) {
-    __shared__ float2 part[PC_WARPS][27];
-    __shared__ float tot[54];
+    constexpr int U = 4;
+    __shared__ float4 part[2 * PC_WARPS][14];
+    __shared__ float tot[56], sM[81], sL[81];
     const int cam = blockIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    float2 acc = make_float2(0.f, 0.f);
-    if (lane < 27) {
-        for (int e = cam_off[cam] + w; e < cam_off[cam + 1]; e += PC_WARPS) {
-            const float2 r = __ldg(reinterpret_cast<const float2*>(rec + (int64_t)cam_list_st[e] * 54) + lane);
-            acc.x += r.x;
-            acc.y += r.y;
+    const int half = lane >> 4, q = lane & 15;
+    float4 acc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (q < 14) {
+        const int e0 = cam_off[cam], e1 = cam_off[cam + 1];
+        const float4* r4 = reinterpret_cast<const float4*>(rec) + q;
+        for (int e = e0 + 2 * w + half; e < e1; e += 2 * PC_WARPS * U) {
+            int st[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int eu = e + 2 * PC_WARPS * u;
+                st[u] = eu < e1 ? __ldg(cam_list_st + eu) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (st[u] >= 0) {
+                    const float4 r = __ldg(r4 + (int64_t)st[u] * 14);
+                    acc[u].x += r.x;
+                    acc[u].y += r.y;
+                    acc[u].z += r.z;
+                    acc[u].w += r.w;
+                }
+            }
         }
-        part[w][lane] = acc;
-    }
-    __syncthreads();
-    if (threadIdx.x < 27) {
-        float2 s2 = make_float2(0.f, 0.f);
-        for (int m = 0; m < PC_WARPS; ++m) {
-            s2.x += part[m][threadIdx.x].x;
-            s2.y += part[m][threadIdx.x].y;
+#pragma unroll
+        for (int u = 1; u < U; ++u) {
+            acc[0].x += acc[u].x;
+            acc[0].y += acc[u].y;
+            acc[0].z += acc[u].z;
+            acc[0].w += acc[u].w;
         }
-        tot[2 * threadIdx.x] = s2.x;
-        tot[2 * threadIdx.x + 1] = s2.y;
+        part[2 * w + half][q] = acc[0];
     }
     __syncthreads();
-    if (threadIdx.x == 0) finish_block(cam, tot, dp2, lam, mdiag, minv, g, err);
-}
-
-// from per-CTA partial blocks (grid x 54 n_cam), summed in CTA order
-__global__ void __launch_bounds__(64)
-k_precond_reduce_partials(int n_cam, int grid, const float* __restrict__ mpart, const float* __restrict__ dp2,
-                          const float lam, float* __restrict__ mdiag, float* __restrict__ minv,
-                          float* __restrict__ g, uint32_t* err) {
-    __shared__ float tot[54];
-    const int cam = blockIdx.x;
-    if (threadIdx.x < 54) {
-        float acc = 0.f;
-        const float* src = mpart + (int64_t)cam * 54 + threadIdx.x;
-        for (int b = 0; b < grid; ++b) acc += __ldg(src + (int64_t)b * 54 * n_cam);
-        tot[threadIdx.x] = acc;
+    if (threadIdx.x < 14) {
+        float4 s4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int m = 0; m < 2 * PC_WARPS; ++m) {
+            const float4 t = part[m][threadIdx.x];
+            s4.x += t.x;
+            s4.y += t.y;
+            s4.z += t.z;
+            s4.w += t.w;
+        }
+        tot[4 * threadIdx.x] = s4.x;
+        tot[4 * threadIdx.x + 1] = s4.y;
+        tot[4 * threadIdx.x + 2] = s4.z;
+        tot[4 * threadIdx.x + 3] = s4.w;
     }
     __syncthreads();
-    if (threadIdx.x == 0) finish_block(cam, tot, dp2, lam, mdiag, minv, g, err);
+    if (w == 0) finish_block_warp(cam, tot, dp2, lam, mdiag, minv, g, err, sM, sL, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -254,15 +277,10 @@ k_pcg_update(int n_cam, const float* __restrict__ g, const float* __restrict__ d
 }  // namespace
 
 void launch_precond_rhs(Problem& p) {
-    if (launch_precond_records(p)) {
-        count_launches(p, 2);
-        k_precond_reduce_partials<<<p.n_cam, 64, 0, p.stream>>>(p.n_cam, p.mv_grid, p.mpart, p.dp2,
-                                                                (float)p.lambda_damped, p.mdiag, p.minv, p.g, p.err);
-    } else {
-        count_launches(p, 2 + (p.n_obs_direct_big > 0 ? 1 : 0));
-        k_precond_reduce<<<p.n_cam, 32 * PC_WARPS, 0, p.stream>>>(p.n_cam, p.cam_off, p.cam_list_st, p.prec, p.dp2,
-                                                                 (float)p.lambda_damped, p.mdiag, p.minv, p.g, p.err);
-    }
+    launch_precond_records(p);
+    count_launches(p, 2 + (p.n_obs_direct_big > 0 ? 1 : 0));
+    k_precond_reduce<<<p.n_cam, 32 * PC_WARPS, 0, p.stream>>>(p.n_cam, p.cam_off, p.cam_list_st, p.prec, p.dp2,
+                                                             (float)p.lambda_damped, p.mdiag, p.minv, p.g, p.err);
     BA_LAUNCH_CHECK();
 }
 

@@ -98,8 +98,7 @@ struct Problem {
     // PCG
     float *g = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
     float *minv = nullptr, *mdiag = nullptr;
-    float* prec = nullptr;           // 54 floats per observation: A_s^T A_s (upper) and A_s^T c
-    float* mpart = nullptr;          // or 54 floats per camera per matvec CTA (camera blocks per CTA)
+    float* prec = nullptr;           // 56 floats per observation: A_s^T A_s (upper), A_s^T c, 2 pad
     PcgScalars* pcg = nullptr;
     PcgScalars* pcg_host = nullptr;  // pinned mirror
     // step
@@ -155,8 +154,7 @@ void launch_pcg_init(Problem& p);
 void launch_pcg_iteration(Problem& p, cudaEvent_t mv_begin = nullptr, cudaEvent_t mv_end = nullptr);
 void launch_matvec(Problem& p, const float* v, float* y, bool add_damping);
 void launch_matvec_raw(Problem& p, const float* v, float* y, const PcgScalars* S);
-bool launch_precond_records(Problem& p);
-bool precond_uses_partials(const Problem& p);
+void launch_precond_records(Problem& p);
 int matvec_ctas_per_sm();
 // K6: back substitution + model cost (backsub.cu)
 void launch_backsub(Problem& p);
