@@ -70,7 +70,9 @@ typedef struct {
     int32_t max_cg_iters; /* default 500 */
     double cg_eta;        /* Nash-Sofer forcing tolerance, default 0.1 */
     int32_t use_graph;    /* 1 (default): PCG iterations replayed from a CUDA graph */
-    int32_t reserved[7];  /* zero */
+    int32_t autotune;     /* 1: the first PCG solve first runs the matvec autotuner
+                             (ba_autotune); default 0 */
+    int32_t reserved[6];  /* zero */
 } ba_options;
 
 /* Fills *opt with the defaults above. */
@@ -242,6 +244,101 @@ SQRTBA_API ba_status ba_eval_cost_noalloc(const float* d_cams, int32_t n_cam, co
                                           int32_t n_pt, const int32_t* d_obs_cam,
                                           const int32_t* d_obs_pt, const float* d_obs_xy,
                                           int64_t n_obs, double* d_cost, void* cuda_stream);
+
+/* ---------------------------------------------------------------------- */
+/* Autotuner of the K4 matvec work plan.                                   */
+/* ---------------------------------------------------------------------- */
+
+/* The matvec streams the landmark blocks, stored by decreasing k, as tiles:
+ * blocks with k <= ksmall are grouped into tiles of up to small_bytes
+ * (specialised code per k), larger blocks are cut into row tiles.  The
+ * tuner times the matvec on the current damped blocks for ksmall in
+ * {8, 13, 21} and small_bytes in {8192, 16384, 32768} (median of five
+ * launches each, CUDA events on the problem's stream), keeps the fastest
+ * plan and reports it.  The paper parallelises over landmarks with a
+ * parallel-for (Sec. 6.1) and has no tuner.
+ * Errors: BA_ERR_STATE if the blocks are not marginalised. */
+typedef struct {
+    int32_t ksmall;       /* chosen bucket limit */
+    int32_t small_bytes;  /* chosen tile size of the small-block buckets */
+    double matvec_ms;     /* its matvec time */
+    double default_ms;    /* matvec time of the default plan (13, 32768) */
+    double tune_ms;       /* wall time of the tuning */
+} ba_tune_report;
+SQRTBA_API ba_status ba_autotune(ba_problem* h, ba_tune_report* report);
+
+/* ---------------------------------------------------------------------- */
+/* Batches of independent problems.                                        */
+/* ---------------------------------------------------------------------- */
+
+/* Many small problems of uneven size are solved together: their cameras,
+ * landmarks and observations are concatenated into one index space, so
+ * each phase (K1 linearise + QR, K2 damping, K3 preconditioner, K4 matvec,
+ * K6 back substitution, K7 cost) is one launch over the whole batch, and
+ * the PCG iterations run from one CUDA graph.  Each problem keeps its own LM
+ * damping, CG scalars and stop rules, FP64 cost sums and accept / reject
+ * decision (the rules of ba_lm_step); the decision runs on the device.  The
+ * paper solves one problem at a time; this interface has no counterpart
+ * there.  Every problem is relinearised in every batch iteration (a
+ * rejected problem recomputes the same blocks). */
+typedef struct ba_batch ba_batch; /* opaque */
+
+/* One problem: the arrays and layouts of ba_create, indices local to it. */
+typedef struct {
+    const double* cams;
+    int32_t n_cam;
+    const double* pts;
+    int32_t n_pt;
+    const int32_t* obs_cam;
+    const int32_t* obs_pt;
+    const double* obs_xy;
+    int64_t n_obs;
+} ba_problem_desc;
+
+/* Per-problem outcome of ba_batch_solve. */
+typedef struct {
+    int32_t iterations;   /* LM iterations (linear solves) */
+    int32_t accepted;     /* accepted steps */
+    int32_t cg_iters;     /* PCG iterations summed over its LM iterations */
+    int32_t stop;         /* 1 function tolerance, 2 iteration limit, 3 lambda limit */
+    double initial_cost;  /* E at the initial state */
+    double final_cost;    /* E at the final state */
+    double lambda;        /* final damping */
+    double solve_ms;      /* from the start of ba_batch_solve to the end of the batch
+                             iteration in which this problem stopped (CUDA events) */
+} ba_batch_report;
+
+typedef struct {
+    int32_t n_problems;
+    int32_t lm_iterations;  /* batch iterations until every problem stopped */
+    int32_t tuned_ksmall;   /* matvec plan in use (see ba_autotune) */
+    int32_t tuned_small_bytes;
+    double total_ms;        /* device time of the whole solve (CUDA events) */
+    double tune_ms;         /* autotuner wall time (0 if it did not run) */
+    int64_t kernel_launches;
+} ba_batch_summary;
+
+/* Creates a batch of n >= 1 problems (each validated as by ba_create; an
+ * index out of its own problem's range is BA_ERR_INVALID_ARG).  opt applies
+ * to every problem; opt->autotune = 1 runs the matvec autotuner in the first
+ * ba_batch_solve.  On success *out owns the batch (ba_batch_destroy). */
+SQRTBA_API ba_status ba_batch_create(const ba_problem_desc* descs, int32_t n, const ba_options* opt,
+                                     void* cuda_stream, ba_batch** out);
+SQRTBA_API ba_status ba_batch_destroy(ba_batch* b);
+
+/* Solves every problem from its current state until its LM stops.
+ * reports (may be NULL) has room for n entries; summary may be NULL. */
+SQRTBA_API ba_status ba_batch_solve(ba_batch* b, ba_batch_report* reports, ba_batch_summary* summary);
+
+/* Restores every problem's initial state (the parameters given to
+ * ba_batch_create), for repeated solves. */
+SQRTBA_API ba_status ba_batch_restart(ba_batch* b);
+
+/* Copies problem i's current state to host FP64 arrays (either may be NULL). */
+SQRTBA_API ba_status ba_batch_get_params(ba_batch* b, int32_t i, double* cams, double* pts);
+
+/* Like ba_last_error for a batch (b = NULL: the last ba_batch_create failure). */
+SQRTBA_API const char* ba_batch_last_error(const ba_batch* b);
 
 /* ---------------------------------------------------------------------- */
 /* Inspection exports for tests (copy device state to host buffers).       */

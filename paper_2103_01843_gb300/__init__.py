@@ -39,7 +39,7 @@ class Options(ctypes.Structure):
     _fields_ = [("lambda0", ctypes.c_double), ("max_lm_iters", ctypes.c_int32),
                 ("func_tol", ctypes.c_double), ("max_cg_iters", ctypes.c_int32),
                 ("cg_eta", ctypes.c_double), ("use_graph", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class PcgReport(ctypes.Structure):
@@ -72,6 +72,33 @@ class Profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 8), ("count", ctypes.c_int64 * 8),
                 ("kernel_launches", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64),
                 ("d2h_bytes", ctypes.c_int64)]
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("ksmall", ctypes.c_int32), ("small_bytes", ctypes.c_int32),
+                ("matvec_ms", ctypes.c_double), ("default_ms", ctypes.c_double),
+                ("tune_ms", ctypes.c_double)]
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [("cams", ctypes.POINTER(ctypes.c_double)), ("n_cam", ctypes.c_int32),
+                ("pts", ctypes.POINTER(ctypes.c_double)), ("n_pt", ctypes.c_int32),
+                ("obs_cam", ctypes.POINTER(ctypes.c_int32)), ("obs_pt", ctypes.POINTER(ctypes.c_int32)),
+                ("obs_xy", ctypes.POINTER(ctypes.c_double)), ("n_obs", ctypes.c_int64)]
+
+
+class BatchReport(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("accepted", ctypes.c_int32),
+                ("cg_iters", ctypes.c_int32), ("stop", ctypes.c_int32),
+                ("initial_cost", ctypes.c_double), ("final_cost", ctypes.c_double),
+                ("lambda_", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+
+
+class BatchSummary(ctypes.Structure):
+    _fields_ = [("n_problems", ctypes.c_int32), ("lm_iterations", ctypes.c_int32),
+                ("tuned_ksmall", ctypes.c_int32), ("tuned_small_bytes", ctypes.c_int32),
+                ("total_ms", ctypes.c_double), ("tune_ms", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64)]
 
 
 PROFILE_SLOTS = ("linearize", "damp", "precond", "matvec", "unused", "backsub", "cost")
@@ -110,6 +137,13 @@ _SIGS = {
     "ba_set_profiling": [_P, ctypes.c_int32],
     "ba_get_profile": [_P, ctypes.POINTER(Profile)],
     "ba_eval_cost_noalloc": [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P, _P, ctypes.c_int64, _P, _P],
+    "ba_autotune": [_P, ctypes.POINTER(TuneReport)],
+    "ba_batch_create": [ctypes.POINTER(ProblemDesc), ctypes.c_int32, ctypes.POINTER(Options), _P,
+                        ctypes.POINTER(_P)],
+    "ba_batch_destroy": [_P],
+    "ba_batch_solve": [_P, ctypes.POINTER(BatchReport), ctypes.POINTER(BatchSummary)],
+    "ba_batch_restart": [_P],
+    "ba_batch_get_params": [_P, ctypes.c_int32, _d, _d],
     "ba_debug_export_order": [_P, _i32, _i64, _i64, _i32],
     "ba_debug_export_landmark": [_P, ctypes.c_int32, ctypes.c_int32, _f, _f, _f, _f, _i32],
     "ba_debug_export_damping": [_P, _f, _f],
@@ -137,13 +171,15 @@ def lib():
             L.ba_default_options.restype = None
             L.ba_last_error.argtypes = [_P]
             L.ba_last_error.restype = ctypes.c_char_p
+            L.ba_batch_last_error.argtypes = [_P]
+            L.ba_batch_last_error.restype = ctypes.c_char_p
             _lib = L
     return _lib
 
 
 def exported_symbols():
     """Names the binding expects the library to export."""
-    return sorted(list(_SIGS) + ["ba_default_options", "ba_last_error"])
+    return sorted(list(_SIGS) + ["ba_default_options", "ba_last_error", "ba_batch_last_error"])
 
 
 def default_options(**kw):
@@ -286,6 +322,11 @@ class Problem:
         self._check(lib().ba_get_info(self.h, ctypes.byref(i)))
         return _struct_dict(i)
 
+    def autotune(self):
+        r = TuneReport()
+        self._check(lib().ba_autotune(self.h, ctypes.byref(r)))
+        return _struct_dict(r)
+
     def set_profiling(self, enable=True):
         self._check(lib().ba_set_profiling(self.h, 1 if enable else 0))
 
@@ -349,3 +390,74 @@ class Problem:
         dl = np.zeros(3 * self.n_pt, np.float32)
         self._check(lib().ba_debug_export_step(self.h, _ptr(dp, _f), _ptr(dl, _f)))
         return dp.reshape(-1, 9), dl.reshape(-1, 3)
+
+
+class Batch:
+    """Independent problems solved together (ba_batch_create).  `problems`
+    is a sequence of (cams, pts, obs_cam, obs_pt, obs_xy) tuples or objects
+    with those attributes, indices local to each problem."""
+
+    def __init__(self, problems, options=None, stream=None, **kw):
+        L = lib()
+        self._keep = []
+        descs = (ProblemDesc * len(problems))()
+        self.sizes = []
+        for i, pr in enumerate(problems):
+            if not isinstance(pr, tuple):
+                pr = (pr.cams, pr.pts, pr.obs_cam, pr.obs_pt, pr.obs_xy)
+            c = np.ascontiguousarray(pr[0], np.float64)
+            x = np.ascontiguousarray(pr[1], np.float64)
+            oc = np.ascontiguousarray(pr[2], np.int32)
+            op = np.ascontiguousarray(pr[3], np.int32)
+            xy = np.ascontiguousarray(pr[4], np.float64)
+            self._keep += [c, x, oc, op, xy]
+            descs[i] = ProblemDesc(_ptr(c, _d), c.shape[0], _ptr(x, _d), x.shape[0], _ptr(oc, _i32),
+                                   _ptr(op, _i32), _ptr(xy, _d), oc.shape[0])
+            self.sizes.append((c.shape[0], x.shape[0], oc.shape[0]))
+        opt = options if options is not None else default_options(**kw)
+        h = _P()
+        rc = L.ba_batch_create(descs, len(problems), ctypes.byref(opt), _P(stream) if stream else None,
+                               ctypes.byref(h))
+        self._keep = []
+        if rc != BA_OK:
+            raise BAError(rc, L.ba_batch_last_error(None).decode())
+        self.h = h
+        self.options = opt
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ba_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != BA_OK:
+            raise BAError(rc, lib().ba_batch_last_error(self.h).decode())
+
+    def solve(self):
+        n = len(self.sizes)
+        reps = (BatchReport * n)()
+        summ = BatchSummary()
+        self._check(lib().ba_batch_solve(self.h, reps, ctypes.byref(summ)))
+        return [_struct_dict(r) for r in reps], _struct_dict(summ)
+
+    def restart(self):
+        self._check(lib().ba_batch_restart(self.h))
+
+    def get_params(self, i):
+        nc, npt, _ = self.sizes[i]
+        c = np.zeros((nc, 9))
+        p = np.zeros((npt, 3))
+        self._check(lib().ba_batch_get_params(self.h, int(i), _ptr(c, _d), _ptr(p, _d)))
+        return c, p

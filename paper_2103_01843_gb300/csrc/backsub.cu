@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(32 * BS_WARPS)
 k_backsub(int n_pt, const int32_t* __restrict__ pt_off, const int32_t* __restrict__ obs_cam_s,
           const float2* __restrict__ obs_xy_s, const float* __restrict__ tpool,
           const float* __restrict__ cams, const float* __restrict__ pts, const float* __restrict__ dp,
-          float* __restrict__ dl, double* __restrict__ partials) {
+          float* __restrict__ dl, double* __restrict__ partials, double* __restrict__ lm_model) {
     __shared__ double wsum[BS_WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int j = blockIdx.x * BS_WARPS + w;
@@ -72,6 +72,7 @@ k_backsub(int n_pt, const int32_t* __restrict__ pt_off, const int32_t* __restric
             }
         }
         msum = warp_sum_d(msum);
+        if (lm_model && lane == 0) lm_model[j] = msum;
     }
     if (lane == 0) wsum[w] = msum;
     __syncthreads();
@@ -134,7 +135,7 @@ void launch_backsub(Problem& p) {
     count_launches(p, 2);
     const int nb = ceil_div(p.n_pt, BS_WARPS);
     k_backsub<<<nb, 32 * BS_WARPS, 0, p.stream>>>(p.n_pt, p.pt_off, p.obs_cam_s, p.obs_xy_s, p.tpool, p.cams,
-                                                  p.pts, p.x, p.dl, p.partials);
+                                                  p.pts, p.x, p.dl, p.partials, p.batch.lm_model);
     k_sum_partials<<<1, 1024, 0, p.stream>>>(p.partials, nb, p.dsum + 1);
     BA_LAUNCH_CHECK();
 }

@@ -4,6 +4,7 @@
 // reads back a few scalars per LM iteration (the PCG scalars, the FP64 model
 // cost and the FP64 candidate cost); everything else stays on the device.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -21,6 +22,12 @@ using namespace sqrtba;
 
 struct ba_problem {
     Problem p;
+};
+
+struct ba_batch {
+    Problem p;
+    float* init_cams = nullptr;  // initial state (device), for ba_batch_restart
+    float* init_pts = nullptr;
 };
 
 namespace {
@@ -117,6 +124,10 @@ void destroy_graph(Problem& p) {
 
 void free_all(Problem& p) {
     destroy_graph(p);
+    for (cudaEvent_t e : p.batch.iter_events) cudaEventDestroy(e);
+    p.batch.iter_events.clear();
+    if (p.batch.n_active_host) cudaFreeHost(p.batch.n_active_host);
+    p.batch.n_active_host = nullptr;
     for (cudaEvent_t e : p.prof.events) cudaEventDestroy(e);
     for (cudaEvent_t e : p.mv_events) cudaEventDestroy(e);
     p.prof.events.clear();
@@ -185,8 +196,75 @@ void capture_pcg_graph(Problem& p) {
     p.pcg_graph_iters = PCG_CHUNK;
 }
 
+// --- matvec autotuner ----------------------------------------------------------
+struct EventSet {
+    std::vector<cudaEvent_t> ev;
+    explicit EventSet(int n) : ev(n, nullptr) {
+        for (auto& e : ev) BA_CUDA_TRY(cudaEventCreate(&e));
+    }
+    ~EventSet() {
+        for (auto e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+};
+
+// median of five timed matvec launches with the plan (ksmall, bytes)
+double time_matvec_plan(Problem& p, int ksmall, int bytes, EventSet& es) {
+    p.mv_ksmall = ksmall;
+    p.mv_small_bytes = bytes;
+    plan_matvec(p);
+    count_launches(p, 6);
+    launch_matvec_raw(p, p.p, p.q, nullptr);
+    for (int i = 0; i < 5; ++i) {
+        BA_CUDA_TRY(cudaEventRecord(es.ev[2 * i], p.stream));
+        launch_matvec_raw(p, p.p, p.q, nullptr);
+        BA_CUDA_TRY(cudaEventRecord(es.ev[2 * i + 1], p.stream));
+    }
+    BA_CUDA_TRY(cudaStreamSynchronize(p.stream));
+    std::vector<float> t(5);
+    for (int i = 0; i < 5; ++i) BA_CUDA_TRY(cudaEventElapsedTime(&t[i], es.ev[2 * i], es.ev[2 * i + 1]));
+    std::sort(t.begin(), t.end());
+    return t[2];
+}
+
+void run_autotune(Problem& p, ba_tune_report* rep) {
+    require(p.damped, BA_ERR_STATE, "ba_autotune: blocks are not marginalised (call ba_marginalize_qr)");
+    const auto t0 = std::chrono::steady_clock::now();
+    EventSet es(10);
+    BA_CUDA_TRY(cudaMemsetAsync(p.p, 0, sizeof(float) * 9 * p.n_cam, p.stream));
+    const int ks_opts[3] = {8, 13, 21};
+    const int by_opts[3] = {8192, 16384, 32768};
+    const double def = time_matvec_plan(p, 13, 32768, es);
+    double best = def;
+    int best_ks = 13, best_by = 32768;
+    for (int ks : ks_opts)
+        for (int by : by_opts) {
+            if (ks == 13 && by == 32768) continue;
+            const double t = time_matvec_plan(p, std::min(ks, matvec_ksmall_limit()), by, es);
+            if (t < best) {
+                best = t;
+                best_ks = ks;
+                best_by = by;
+            }
+        }
+    p.mv_ksmall = best_ks;
+    p.mv_small_bytes = best_by;
+    plan_matvec(p);
+    destroy_graph(p);  // the captured launches hold the old plan
+    p.tuned = true;
+    const double wall = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (rep) {
+        rep->ksmall = best_ks;
+        rep->small_bytes = best_by;
+        rep->matvec_ms = best;
+        rep->default_ms = def;
+        rep->tune_ms = wall;
+    }
+}
+
 void do_pcg(Problem& p, ba_pcg_report* rep) {
     require(p.damped, BA_ERR_STATE, "ba_pcg_solve: blocks are not marginalised (call ba_marginalize_qr)");
+    if (p.opt.autotune && !p.tuned) run_autotune(p, nullptr);
     PhaseTimer t(p, PROF_PRECOND);
     launch_precond_rhs(p);
     launch_pcg_init(p);
@@ -304,6 +382,272 @@ void do_lm_step(Problem& p, ba_lm_report* rep) {
     if (rep) *rep = r;
 }
 
+// Allocates and fills a problem from host FP64 arrays: validation, grouping
+// by landmark, storage and matvec plan, block pools.
+void create_problem(Problem& p, const double* cams, int32_t n_cam, const double* pts, int32_t n_pt,
+                    const int32_t* obs_cam, const int32_t* obs_pt, const double* obs_xy, int64_t n_obs,
+                    const ba_options* opt, void* cuda_stream) {
+    require(cams && pts && obs_cam && obs_pt && obs_xy, BA_ERR_INVALID_ARG, "null input pointer");
+    require(n_cam >= 1 && n_pt >= 1 && n_obs >= 2, BA_ERR_INVALID_ARG, "empty problem");
+    require(n_obs < ((int64_t)1 << 31) - 1, BA_ERR_INVALID_ARG, "too many observations (limit 2^31 - 2)");
+    ba_default_options(&p.opt);
+    if (opt) p.opt = *opt;
+    require(p.opt.lambda0 > 0 && p.opt.max_lm_iters >= 1 && p.opt.max_cg_iters >= 1 && p.opt.cg_eta > 0,
+            BA_ERR_INVALID_ARG, "invalid options");
+    p.n_cam = n_cam;
+    p.n_pt = n_pt;
+    p.n_obs = n_obs;
+    p.lambda = p.opt.lambda0;
+    p.nu = 2.0;
+    if (cuda_stream) {
+        p.stream = (cudaStream_t)cuda_stream;
+    } else {
+        BA_CUDA_TRY(cudaStreamCreateWithFlags(&p.stream, cudaStreamNonBlocking));
+        p.own_stream = true;
+    }
+    int dev = 0;
+    BA_CUDA_TRY(cudaGetDevice(&dev));
+    BA_CUDA_TRY(cudaDeviceGetAttribute(&p.sm_count, cudaDevAttrMultiProcessorCount, dev));
+    p.mv_grid = p.sm_count * matvec_ctas_per_sm();
+    p.red_grid = p.sm_count * 4;
+
+    p.cams = dalloc<float>(p, 9 * (int64_t)n_cam);
+    p.cand_cams = dalloc<float>(p, 9 * (int64_t)n_cam);
+    p.pts = dalloc<float>(p, 3 * (int64_t)n_pt);
+    p.cand_pts = dalloc<float>(p, 3 * (int64_t)n_pt);
+    p.obs_cam_s = dalloc<int32_t>(p, n_obs);
+    p.obs_pt_s = dalloc<int32_t>(p, n_obs);
+    p.perm = dalloc<int32_t>(p, n_obs);
+    p.obs_xy_s = dalloc<float2>(p, n_obs);
+    p.pt_off = dalloc<int32_t>(p, n_pt + 1);
+    p.cam_off = dalloc<int32_t>(p, n_cam + 1);
+    p.cam_list = dalloc<int32_t>(p, n_obs);
+    p.a_off = dalloc<int64_t>(p, n_pt + 1);
+    p.lm_by_k = dalloc<int32_t>(p, n_pt);
+    p.mv_cam = dalloc<int32_t>(p, n_obs + 8);
+    p.c_off = dalloc<int32_t>(p, n_pt + 1);
+    p.cam_list_st = dalloc<int32_t>(p, n_obs);
+    p.err = dalloc<uint32_t>(p, 4);
+    p.dsum = dalloc<double>(p, 4);
+    p.pcg = dalloc<PcgScalars>(p, 1);
+    BA_CUDA_TRY(cudaMallocHost(&p.pcg_host, sizeof(PcgScalars)));
+    BA_CUDA_TRY(cudaMallocHost(&p.dsum_host, 4 * sizeof(double)));
+    std::memset(p.pcg_host, 0, sizeof(PcgScalars));
+
+    // stage the FP64 inputs on the device for validation and grouping
+    double *d_cams = nullptr, *d_pts = nullptr, *d_xy = nullptr;
+    int32_t *d_oc = nullptr, *d_op = nullptr;
+    BA_CUDA_TRY(cudaMallocAsync(&d_cams, sizeof(double) * 9 * n_cam, p.stream));
+    BA_CUDA_TRY(cudaMallocAsync(&d_pts, sizeof(double) * 3 * n_pt, p.stream));
+    BA_CUDA_TRY(cudaMallocAsync(&d_xy, sizeof(double) * 2 * n_obs, p.stream));
+    BA_CUDA_TRY(cudaMallocAsync(&d_oc, sizeof(int32_t) * n_obs, p.stream));
+    BA_CUDA_TRY(cudaMallocAsync(&d_op, sizeof(int32_t) * n_obs, p.stream));
+    struct StageGuard {
+        Problem& p;
+        void* b[5];
+        ~StageGuard() {
+            for (void* x : b)
+                if (x) cudaFreeAsync(x, p.stream);
+        }
+    } sg{p, {d_cams, d_pts, d_xy, d_oc, d_op}};
+    h2d(p, d_cams, cams, 9 * (int64_t)n_cam);
+    h2d(p, d_pts, pts, 3 * (int64_t)n_pt);
+    h2d(p, d_xy, obs_xy, 2 * n_obs);
+    h2d(p, d_oc, obs_cam, n_obs);
+    h2d(p, d_op, obs_pt, n_obs);
+    build_index(p, d_oc, d_op, d_xy, d_cams, d_pts);
+    require(p.k_max <= linearize_k_limit(), BA_ERR_INVALID_ARG,
+            "a landmark has more observations than the supported maximum (900)");
+    plan_matvec(p);
+
+    p.apool = dalloc<float>(p, p.a_floats);
+    p.t_floats = 3 * (9 * n_obs + 4 * (int64_t)n_pt);
+    p.tpool = dalloc<float>(p, p.t_floats);
+    p.cpool = dalloc<float>(p, 2 * n_obs + 8);
+    p.rot = dalloc<float>(p, 12 * (int64_t)n_pt);
+    p.dp2 = dalloc<float>(p, 9 * (int64_t)n_cam);
+    p.dl2 = dalloc<float>(p, 3 * (int64_t)n_pt);
+    const int64_t nv = 9 * (int64_t)n_cam;
+    p.g = dalloc<float>(p, nv);
+    p.x = dalloc<float>(p, nv);
+    p.r = dalloc<float>(p, nv);
+    p.z = dalloc<float>(p, nv);
+    p.p = dalloc<float>(p, nv);
+    p.q = dalloc<float>(p, nv);
+    p.minv = dalloc<float>(p, 81 * (int64_t)n_cam);
+    p.mdiag = dalloc<float>(p, 81 * (int64_t)n_cam);
+    p.prec = dalloc<float>(p, 56 * n_obs);
+    p.dl = dalloc<float>(p, 3 * (int64_t)n_pt);
+    p.partials = dalloc<double>(p, std::max<int64_t>((n_pt + 3) / 4 + 1, p.red_grid + 1));
+    BA_CUDA_TRY(cudaMemsetAsync(p.x, 0, sizeof(float) * nv, p.stream));
+    BA_CUDA_TRY(cudaMemsetAsync(p.dl, 0, sizeof(float) * 3 * n_pt, p.stream));
+    configure_linearize(p);
+    configure_matvec(p);
+    sync(p);
+}
+
+// --- batches of independent problems -----------------------------------------------
+thread_local std::string g_batch_create_error;
+
+void create_batch(ba_batch* bh, const ba_problem_desc* descs, int32_t n, const ba_options* opt, void* stream) {
+    require(descs != nullptr && n >= 1, BA_ERR_INVALID_ARG, "no problems");
+    int64_t tc = 0, tp = 0, to = 0;
+    for (int32_t b = 0; b < n; ++b) {
+        const ba_problem_desc& d = descs[b];
+        require(d.cams && d.pts && d.obs_cam && d.obs_pt && d.obs_xy, BA_ERR_INVALID_ARG, "null input pointer");
+        require(d.n_cam >= 1 && d.n_pt >= 1 && d.n_obs >= 2, BA_ERR_INVALID_ARG, "empty problem in the batch");
+        for (int64_t o = 0; o < d.n_obs; ++o) {
+            require(d.obs_cam[o] >= 0 && d.obs_cam[o] < d.n_cam, BA_ERR_INVALID_ARG,
+                    "camera index out of its problem's range");
+            require(d.obs_pt[o] >= 0 && d.obs_pt[o] < d.n_pt, BA_ERR_INVALID_ARG,
+                    "landmark index out of its problem's range");
+        }
+        tc += d.n_cam;
+        tp += d.n_pt;
+        to += d.n_obs;
+    }
+    require(tc < ((int64_t)1 << 31) && tp < ((int64_t)1 << 31), BA_ERR_INVALID_ARG, "batch too large");
+    std::vector<double> cams(9 * tc), pts(3 * tp), xy(2 * to);
+    std::vector<int32_t> oc(to), op(to), cam_prob(tc), lm_prob(tp);
+    BatchState& B = bh->p.batch;
+    B.h_cam_off.assign(n + 1, 0);
+    B.h_lm_off.assign(n + 1, 0);
+    B.h_obs_off.assign(n + 1, 0);
+    for (int32_t b = 0; b < n; ++b) {
+        const ba_problem_desc& d = descs[b];
+        const int32_t c0 = B.h_cam_off[b], l0 = B.h_lm_off[b];
+        const int64_t o0 = B.h_obs_off[b];
+        std::memcpy(&cams[9 * (int64_t)c0], d.cams, sizeof(double) * 9 * d.n_cam);
+        std::memcpy(&pts[3 * (int64_t)l0], d.pts, sizeof(double) * 3 * d.n_pt);
+        std::memcpy(&xy[2 * o0], d.obs_xy, sizeof(double) * 2 * d.n_obs);
+        for (int64_t o = 0; o < d.n_obs; ++o) {
+            oc[o0 + o] = c0 + d.obs_cam[o];
+            op[o0 + o] = l0 + d.obs_pt[o];
+        }
+        for (int32_t i = 0; i < d.n_cam; ++i) cam_prob[c0 + i] = b;
+        for (int32_t i = 0; i < d.n_pt; ++i) lm_prob[l0 + i] = b;
+        B.h_cam_off[b + 1] = c0 + d.n_cam;
+        B.h_lm_off[b + 1] = l0 + d.n_pt;
+        B.h_obs_off[b + 1] = o0 + d.n_obs;
+    }
+    Problem& p = bh->p;
+    create_problem(p, cams.data(), (int32_t)tc, pts.data(), (int32_t)tp, oc.data(), op.data(), xy.data(), to, opt,
+                   stream);
+    // sorted observations are grouped by landmark and every problem's
+    // landmarks are contiguous, so problem b owns sorted positions
+    // h_obs_off[b] .. h_obs_off[b + 1] - 1
+    B.n_prob = n;
+    B.cam_prob = dalloc<int32_t>(p, tc);
+    B.lm_prob = dalloc<int32_t>(p, tp);
+    B.prob_cam_off = dalloc<int32_t>(p, n + 1);
+    B.prob_lm_off = dalloc<int32_t>(p, n + 1);
+    B.prob_obs_off = dalloc<int64_t>(p, n + 1);
+    B.lam = dalloc<float>(p, n);
+    B.pcg = dalloc<PcgScalars>(p, n);
+    B.n_done = dalloc<int32_t>(p, 1);
+    B.lm = dalloc<BatchLm>(p, n);
+    B.lm_model = dalloc<double>(p, tp);
+    B.cost_a = dalloc<double>(p, n);
+    B.cost_b = dalloc<double>(p, n);
+    B.n_active = dalloc<int32_t>(p, 1);
+    BA_CUDA_TRY(cudaMallocHost(&B.n_active_host, sizeof(int32_t)));
+    h2d(p, B.cam_prob, cam_prob.data(), tc);
+    h2d(p, B.lm_prob, lm_prob.data(), tp);
+    h2d(p, B.prob_cam_off, B.h_cam_off.data(), n + 1);
+    h2d(p, B.prob_lm_off, B.h_lm_off.data(), n + 1);
+    h2d(p, B.prob_obs_off, B.h_obs_off.data(), n + 1);
+    bh->init_cams = dalloc<float>(p, 9 * tc);
+    bh->init_pts = dalloc<float>(p, 3 * tp);
+    BA_CUDA_TRY(cudaMemcpyAsync(bh->init_cams, p.cams, sizeof(float) * 9 * tc, cudaMemcpyDeviceToDevice, p.stream));
+    BA_CUDA_TRY(cudaMemcpyAsync(bh->init_pts, p.pts, sizeof(float) * 3 * tp, cudaMemcpyDeviceToDevice, p.stream));
+    sync(p);
+}
+
+void do_batch_solve(Problem& p, ba_batch_report* reps, ba_batch_summary* sum) {
+    BatchState& B = p.batch;
+    const int max_it = p.opt.max_lm_iters;
+    while ((int)B.iter_events.size() < max_it + 1) {
+        cudaEvent_t e;
+        BA_CUDA_TRY(cudaEventCreate(&e));
+        B.iter_events.push_back(e);
+    }
+    const int64_t launches0 = p.launches;
+    double tune_ms = 0.0;
+    BA_CUDA_TRY(cudaEventRecord(B.iter_events[0], p.stream));
+    int n_it = 0;
+    for (int it = 0; it < max_it; ++it) {
+        // K1 for every problem (a problem whose last step was rejected
+        // recomputes the blocks of its unchanged state)
+        PhaseTimer tl(p, PROF_LINEARIZE);
+        launch_camera_diag(p);
+        launch_linearize(p);
+        tl.end();
+        if (it == 0) {
+            launch_batch_cost(p, false, B.cost_a);
+            launch_batch_start(p);
+        }
+        p.linearized = true;
+        PhaseTimer td(p, PROF_DAMP);
+        launch_damp(p, false, 1.f);  // per-problem damping from B.lam
+        td.end();
+        p.damped = true;
+        if (p.opt.autotune && !p.tuned) {
+            ba_tune_report tr{};
+            run_autotune(p, &tr);
+            tune_ms = tr.tune_ms;
+        }
+        do_pcg(p, nullptr);
+        PhaseTimer tb(p, PROF_BACKSUB);
+        launch_backsub(p);
+        launch_batch_model(p);
+        tb.end();
+        PhaseTimer tc(p, PROF_COST);
+        launch_candidate(p);
+        launch_batch_cost(p, true, B.cost_a);
+        tc.end();
+        launch_batch_decide(p, it);
+        launch_batch_commit(p);
+        BA_CUDA_TRY(cudaEventRecord(B.iter_events[it + 1], p.stream));
+        d2h(p, B.n_active_host, B.n_active, 1);
+        sync(p);
+        n_it = it + 1;
+        if (*B.n_active_host == 0) break;
+    }
+    p.linearized = p.damped = p.solved = p.backsubbed = false;
+    std::vector<BatchLm> lm(B.n_prob);
+    d2h(p, lm.data(), B.lm, B.n_prob);
+    sync(p);
+    std::vector<double> t_end(n_it + 1, 0.0);
+    for (int i = 1; i <= n_it; ++i) {
+        float ms = 0.f;
+        BA_CUDA_TRY(cudaEventElapsedTime(&ms, B.iter_events[0], B.iter_events[i]));
+        t_end[i] = ms;
+    }
+    if (reps) {
+        for (int b = 0; b < B.n_prob; ++b) {
+            ba_batch_report& r = reps[b];
+            r.iterations = lm[b].iter;
+            r.accepted = lm[b].accepted;
+            r.cg_iters = lm[b].cg_total;
+            r.stop = lm[b].stop;
+            r.initial_cost = lm[b].cost0;
+            r.final_cost = lm[b].cost;
+            r.lambda = lm[b].lambda;
+            const int f = lm[b].finish >= 0 ? lm[b].finish + 1 : n_it;
+            r.solve_ms = t_end[std::min(f, n_it)];
+        }
+    }
+    if (sum) {
+        sum->n_problems = B.n_prob;
+        sum->lm_iterations = n_it;
+        sum->tuned_ksmall = p.mv_ksmall;
+        sum->tuned_small_bytes = p.mv_small_bytes;
+        sum->total_ms = t_end[n_it];
+        sum->tune_ms = tune_ms;
+        sum->kernel_launches = p.launches - launches0;
+    }
+}
+
 }  // namespace
 
 namespace sqrtba {
@@ -332,105 +676,8 @@ ba_status ba_create(const double* cams, int32_t n_cam, const double* pts, int32_
     try {
         require(out != nullptr, BA_ERR_INVALID_ARG, "out is NULL");
         *out = nullptr;
-        require(cams && pts && obs_cam && obs_pt && obs_xy, BA_ERR_INVALID_ARG, "null input pointer");
-        require(n_cam >= 1 && n_pt >= 1 && n_obs >= 2, BA_ERR_INVALID_ARG, "empty problem");
-        require(n_obs < ((int64_t)1 << 31) - 1, BA_ERR_INVALID_ARG, "too many observations (limit 2^31 - 2)");
         h = new ba_problem();
-        Problem& p = h->p;
-        ba_default_options(&p.opt);
-        if (opt) p.opt = *opt;
-        require(p.opt.lambda0 > 0 && p.opt.max_lm_iters >= 1 && p.opt.max_cg_iters >= 1 && p.opt.cg_eta > 0,
-                BA_ERR_INVALID_ARG, "invalid options");
-        p.n_cam = n_cam;
-        p.n_pt = n_pt;
-        p.n_obs = n_obs;
-        p.lambda = p.opt.lambda0;
-        p.nu = 2.0;
-        if (cuda_stream) {
-            p.stream = (cudaStream_t)cuda_stream;
-        } else {
-            BA_CUDA_TRY(cudaStreamCreateWithFlags(&p.stream, cudaStreamNonBlocking));
-            p.own_stream = true;
-        }
-        int dev = 0;
-        BA_CUDA_TRY(cudaGetDevice(&dev));
-        BA_CUDA_TRY(cudaDeviceGetAttribute(&p.sm_count, cudaDevAttrMultiProcessorCount, dev));
-        p.mv_grid = p.sm_count * matvec_ctas_per_sm();
-        p.red_grid = p.sm_count * 4;
-
-        p.cams = dalloc<float>(p, 9 * (int64_t)n_cam);
-        p.cand_cams = dalloc<float>(p, 9 * (int64_t)n_cam);
-        p.pts = dalloc<float>(p, 3 * (int64_t)n_pt);
-        p.cand_pts = dalloc<float>(p, 3 * (int64_t)n_pt);
-        p.obs_cam_s = dalloc<int32_t>(p, n_obs);
-        p.obs_pt_s = dalloc<int32_t>(p, n_obs);
-        p.perm = dalloc<int32_t>(p, n_obs);
-        p.obs_xy_s = dalloc<float2>(p, n_obs);
-        p.pt_off = dalloc<int32_t>(p, n_pt + 1);
-        p.cam_off = dalloc<int32_t>(p, n_cam + 1);
-        p.cam_list = dalloc<int32_t>(p, n_obs);
-        p.a_off = dalloc<int64_t>(p, n_pt + 1);
-        p.lm_by_k = dalloc<int32_t>(p, n_pt);
-        p.mv_cam = dalloc<int32_t>(p, n_obs + 8);
-        p.c_off = dalloc<int32_t>(p, n_pt + 1);
-        p.cam_list_st = dalloc<int32_t>(p, n_obs);
-        p.err = dalloc<uint32_t>(p, 4);
-        p.dsum = dalloc<double>(p, 4);
-        p.pcg = dalloc<PcgScalars>(p, 1);
-        BA_CUDA_TRY(cudaMallocHost(&p.pcg_host, sizeof(PcgScalars)));
-        BA_CUDA_TRY(cudaMallocHost(&p.dsum_host, 4 * sizeof(double)));
-        std::memset(p.pcg_host, 0, sizeof(PcgScalars));
-
-        // stage the FP64 inputs on the device for validation and grouping
-        double *d_cams = nullptr, *d_pts = nullptr, *d_xy = nullptr;
-        int32_t *d_oc = nullptr, *d_op = nullptr;
-        BA_CUDA_TRY(cudaMallocAsync(&d_cams, sizeof(double) * 9 * n_cam, p.stream));
-        BA_CUDA_TRY(cudaMallocAsync(&d_pts, sizeof(double) * 3 * n_pt, p.stream));
-        BA_CUDA_TRY(cudaMallocAsync(&d_xy, sizeof(double) * 2 * n_obs, p.stream));
-        BA_CUDA_TRY(cudaMallocAsync(&d_oc, sizeof(int32_t) * n_obs, p.stream));
-        BA_CUDA_TRY(cudaMallocAsync(&d_op, sizeof(int32_t) * n_obs, p.stream));
-        struct StageGuard {
-            Problem& p;
-            void* b[5];
-            ~StageGuard() {
-                for (void* x : b)
-                    if (x) cudaFreeAsync(x, p.stream);
-            }
-        } sg{p, {d_cams, d_pts, d_xy, d_oc, d_op}};
-        h2d(p, d_cams, cams, 9 * (int64_t)n_cam);
-        h2d(p, d_pts, pts, 3 * (int64_t)n_pt);
-        h2d(p, d_xy, obs_xy, 2 * n_obs);
-        h2d(p, d_oc, obs_cam, n_obs);
-        h2d(p, d_op, obs_pt, n_obs);
-        build_index(p, d_oc, d_op, d_xy, d_cams, d_pts);
-        require(p.k_max <= linearize_k_limit(), BA_ERR_INVALID_ARG,
-                "a landmark has more observations than the supported maximum (900)");
-        plan_matvec(p);
-
-        p.apool = dalloc<float>(p, p.a_floats);
-        p.t_floats = 3 * (9 * n_obs + 4 * (int64_t)n_pt);
-        p.tpool = dalloc<float>(p, p.t_floats);
-        p.cpool = dalloc<float>(p, 2 * n_obs + 8);
-        p.rot = dalloc<float>(p, 12 * (int64_t)n_pt);
-        p.dp2 = dalloc<float>(p, 9 * (int64_t)n_cam);
-        p.dl2 = dalloc<float>(p, 3 * (int64_t)n_pt);
-        const int64_t nv = 9 * (int64_t)n_cam;
-        p.g = dalloc<float>(p, nv);
-        p.x = dalloc<float>(p, nv);
-        p.r = dalloc<float>(p, nv);
-        p.z = dalloc<float>(p, nv);
-        p.p = dalloc<float>(p, nv);
-        p.q = dalloc<float>(p, nv);
-        p.minv = dalloc<float>(p, 81 * (int64_t)n_cam);
-        p.mdiag = dalloc<float>(p, 81 * (int64_t)n_cam);
-        p.prec = dalloc<float>(p, 56 * n_obs);
-        p.dl = dalloc<float>(p, 3 * (int64_t)n_pt);
-        p.partials = dalloc<double>(p, std::max<int64_t>((n_pt + 3) / 4 + 1, p.red_grid + 1));
-        BA_CUDA_TRY(cudaMemsetAsync(p.x, 0, sizeof(float) * nv, p.stream));
-        BA_CUDA_TRY(cudaMemsetAsync(p.dl, 0, sizeof(float) * 3 * n_pt, p.stream));
-        configure_linearize(p);
-        configure_matvec(p);
-        sync(p);
+        create_problem(h->p, cams, n_cam, pts, n_pt, obs_cam, obs_pt, obs_xy, n_obs, opt, cuda_stream);
         *out = h;
         return BA_OK;
     } catch (const Error& e) {
@@ -760,6 +1007,112 @@ ba_status ba_debug_export_step(ba_problem* h, float* dp, float* dl) {
     sync(p);
     return BA_OK;
     API_CATCH(h)
+}
+
+ba_status ba_autotune(ba_problem* h, ba_tune_report* rep) {
+    if (!h) return BA_ERR_INVALID_ARG;
+    API_TRY
+    run_autotune(h->p, rep);
+    return BA_OK;
+    API_CATCH(h)
+}
+
+// --- batches -----------------------------------------------------------------------
+#define BATCH_TRY try {
+#define BATCH_CATCH(b)                                \
+    }                                                 \
+    catch (const Error& e) {                          \
+        (b)->p.last_error = e.msg;                    \
+        return e.code;                                \
+    }                                                 \
+    catch (const std::bad_alloc&) {                   \
+        (b)->p.last_error = "host allocation failed"; \
+        return BA_ERR_OOM;                            \
+    }                                                 \
+    catch (...) {                                     \
+        (b)->p.last_error = "unexpected exception";   \
+        return BA_ERR_CUDA;                           \
+    }
+
+ba_status ba_batch_create(const ba_problem_desc* descs, int32_t n, const ba_options* opt, void* cuda_stream,
+                          ba_batch** out) {
+    ba_batch* b = nullptr;
+    g_batch_create_error.clear();
+    try {
+        require(out != nullptr, BA_ERR_INVALID_ARG, "out is NULL");
+        *out = nullptr;
+        b = new ba_batch();
+        create_batch(b, descs, n, opt, cuda_stream);
+        *out = b;
+        return BA_OK;
+    } catch (const Error& e) {
+        g_batch_create_error = e.msg;
+        if (b) {
+            free_all(b->p);
+            delete b;
+        }
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        g_batch_create_error = "host allocation failed";
+        if (b) {
+            free_all(b->p);
+            delete b;
+        }
+        return BA_ERR_OOM;
+    }
+}
+
+ba_status ba_batch_destroy(ba_batch* b) {
+    if (!b) return BA_OK;
+    if (b->p.stream) cudaStreamSynchronize(b->p.stream);
+    free_all(b->p);
+    delete b;
+    return BA_OK;
+}
+
+ba_status ba_batch_solve(ba_batch* b, ba_batch_report* reports, ba_batch_summary* summary) {
+    if (!b) return BA_ERR_INVALID_ARG;
+    BATCH_TRY
+    do_batch_solve(b->p, reports, summary);
+    return BA_OK;
+    BATCH_CATCH(b)
+}
+
+ba_status ba_batch_restart(ba_batch* b) {
+    if (!b) return BA_ERR_INVALID_ARG;
+    BATCH_TRY
+    Problem& p = b->p;
+    BA_CUDA_TRY(cudaMemcpyAsync(p.cams, b->init_cams, sizeof(float) * 9 * p.n_cam, cudaMemcpyDeviceToDevice,
+                                p.stream));
+    BA_CUDA_TRY(cudaMemcpyAsync(p.pts, b->init_pts, sizeof(float) * 3 * p.n_pt, cudaMemcpyDeviceToDevice,
+                                p.stream));
+    p.linearized = p.damped = p.solved = p.backsubbed = false;
+    return BA_OK;
+    BATCH_CATCH(b)
+}
+
+ba_status ba_batch_get_params(ba_batch* b, int32_t i, double* cams, double* pts) {
+    if (!b) return BA_ERR_INVALID_ARG;
+    BATCH_TRY
+    Problem& p = b->p;
+    const BatchState& B = p.batch;
+    require(i >= 0 && i < B.n_prob, BA_ERR_INVALID_ARG, "problem index out of range");
+    const int32_t c0 = B.h_cam_off[i], nc = B.h_cam_off[i + 1] - c0;
+    const int32_t l0 = B.h_lm_off[i], nl = B.h_lm_off[i + 1] - l0;
+    std::vector<float> c(9 * (size_t)nc), x(3 * (size_t)nl);
+    if (cams) d2h(p, c.data(), p.cams + 9 * (int64_t)c0, (int64_t)c.size());
+    if (pts) d2h(p, x.data(), p.pts + 3 * (int64_t)l0, (int64_t)x.size());
+    sync(p);
+    if (cams)
+        for (size_t k = 0; k < c.size(); ++k) cams[k] = c[k];
+    if (pts)
+        for (size_t k = 0; k < x.size(); ++k) pts[k] = x[k];
+    return BA_OK;
+    BATCH_CATCH(b)
+}
+
+const char* ba_batch_last_error(const ba_batch* b) {
+    return b ? b->p.last_error.c_str() : g_batch_create_error.c_str();
 }
 
 }  // extern "C"

@@ -12,6 +12,8 @@
 // (Fig. 3c), which restores the undamped block up to rounding, then applies
 // the new damping.
 //
+// In a batch of problems each landmark takes the damping of its problem.
+//
 // Layout of the work: a CTA takes DB landmarks.  Phase 1, one landmark per
 // thread: undo/redo on the 3x3 landmark part and the new rotations.  Phase 2:
 // the CTA's (landmark, column) pairs, flattened through a prefix sum over the
@@ -34,7 +36,7 @@ __global__ void __launch_bounds__(DB)
 k_damp(int n_pt, const int32_t* __restrict__ pt_off, const int64_t* __restrict__ a_off,
        const int32_t* __restrict__ c_off, float* __restrict__ tpool, float* __restrict__ apool,
        float* __restrict__ cpool, const float* __restrict__ dl2, float* __restrict__ rot, float sqrt_lambda,
-       int undo) {
+       const float* __restrict__ lam_prob, const int32_t* __restrict__ lm_prob, int undo) {
     __shared__ float s_rot[DB][24];  // old (12) and new (12) rotations
     __shared__ int s_off[DB + 1];    // prefix of the column counts 9k + 1
     __shared__ int s_k[DB];
@@ -81,7 +83,8 @@ k_damp(int n_pt, const int32_t* __restrict__ pt_off, const int64_t* __restrict__
                 rs[m + 1] = 0.f;
             }
         }
-        for (int d = 0; d < 3; ++d) D[d][d] = sqrt_lambda * sqrtf(dl2[3 * j + d]);
+        const float sl = lam_prob ? sqrtf(lam_prob[lm_prob[j]]) : sqrt_lambda;
+        for (int d = 0; d < 3; ++d) D[d][d] = sl * sqrtf(dl2[3 * j + d]);
         for (int m = 0; m < 6; ++m) {
             int c, d;
             rot_pair(m, c, d);
@@ -174,7 +177,8 @@ k_damp(int n_pt, const int32_t* __restrict__ pt_off, const int64_t* __restrict__
 void launch_damp(Problem& p, bool undo_old, float lambda) {
     count_launches(p, 1);
     k_damp<<<ceil_div(p.n_pt, DB), DB, 0, p.stream>>>(p.n_pt, p.pt_off, p.a_off, p.c_off, p.tpool, p.apool, p.cpool,
-                                                      p.dl2, p.rot, sqrtf(lambda), undo_old ? 1 : 0);
+                                                      p.dl2, p.rot, sqrtf(lambda), p.batch.lam, p.batch.lm_prob,
+                                                      undo_old ? 1 : 0);
     BA_LAUNCH_CHECK();
 }
 

@@ -35,7 +35,7 @@ constexpr int MV_STAGE_C = 1024;    // bytes of camera indices per stage
 // CTA's 16 warps spread four to a sub-partition: 128 registers per thread.
 constexpr int MV_CONSUMERS = 15;    // consumer warps per CTA
 constexpr int MV_THREADS = 32 * (MV_CONSUMERS + 1);
-constexpr int MV_KSMALL = 13;       // whole blocks, specialised per k (>= 2 per tile)
+constexpr int MV_KSMALL_MAX = 21;   // whole blocks, specialised per k (up to the planner's mv_ksmall)
 constexpr int MV_KBIG = 222;        // row ranges, multiples of 4 rows (36k * 4 <= 32 KB)
 constexpr int MV_UMAX = 45;         // rows of one big tile (multiple of MV_CONSUMERS)
 constexpr uint64_t MV_WAIT_NS = 2000000000ull;
@@ -566,8 +566,10 @@ void plan_matvec(Problem& p) {
     // atomically: the observations of the landmarks with k above the
     // smallest split k, which come first in storage order, are zeroed before
     // each preconditioner pass (the records of unsplit blocks are stored)
+    const int ksmall = std::min(p.mv_ksmall, MV_KSMALL_MAX);
+    const int small_bytes = std::min(p.mv_small_bytes, MV_STAGE_A);
     p.n_obs_direct_big = 0;
-    for (int b = 0; b <= kmax && kmax - b > MV_KSMALL; ++b)
+    for (int b = 0; b <= kmax && kmax - b > ksmall; ++b)
         if (big_tile_rows(kmax - b) < 2 * (kmax - b)) p.n_obs_direct_big = p.run_co[b + 1];
     for (int b = 0; b <= kmax; ++b) {
         const int k = kmax - b;
@@ -579,8 +581,8 @@ void plan_matvec(Problem& p) {
             for (int bb = 0; bb < b; ++bb) q += p.k_run_count[bb];
             return q;
         }();
-        if (k <= MV_KSMALL) {
-            const int64_t per = std::max<int64_t>(1, MV_STAGE_A / (4 * bf));
+        if (k <= ksmall) {
+            const int64_t per = std::max<int64_t>(1, small_bytes / (4 * bf));
             for (int64_t l = 0; l < cnt; l += per) {
                 MvTile t{};
                 const int64_t n = std::min(per, cnt - l);
@@ -637,8 +639,12 @@ void plan_matvec(Problem& p) {
     begin[grid] = (int32_t)perm.size();
     tiles.swap(perm);
     p.n_mv_tiles = (int)tiles.size();
-    p.mv_tiles = dalloc<MvTile>(p, std::max<int64_t>(1, (int64_t)tiles.size()));
-    p.mv_tile_begin = dalloc<int32_t>(p, grid + 1);
+    if (!p.mv_tiles || p.mv_tile_cap < p.n_mv_tiles) {
+        // re-planning (autotuner) reuses the allocation when it is large enough
+        p.mv_tile_cap = std::max(1, p.n_mv_tiles);
+        p.mv_tiles = dalloc<MvTile>(p, p.mv_tile_cap);
+    }
+    if (!p.mv_tile_begin) p.mv_tile_begin = dalloc<int32_t>(p, grid + 1);
     if (!tiles.empty())
         BA_CUDA_TRY(cudaMemcpyAsync(p.mv_tiles, tiles.data(), sizeof(MvTile) * tiles.size(), cudaMemcpyHostToDevice,
                                     p.stream));
@@ -648,6 +654,8 @@ void plan_matvec(Problem& p) {
 }
 
 int matvec_ctas_per_sm() { return 1; }
+int matvec_ksmall_limit() { return MV_KSMALL_MAX; }
+int matvec_stage_bytes() { return MV_STAGE_A; }
 
 void configure_matvec(Problem& p) {
     const int sm = (int)smem_bytes(p);

@@ -95,7 +95,8 @@ __device__ void finish_block_warp(int cam, const float* tot, const float* __rest
 // flight per warp; the camera's records are summed in a fixed order
 __global__ void __launch_bounds__(32 * PC_WARPS)
 k_precond_reduce(int n_cam, const int32_t* __restrict__ cam_off, const int32_t* __restrict__ cam_list_st,
-                 const float* __restrict__ rec, const float* __restrict__ dp2, const float lam,
+                 const float* __restrict__ rec, const float* __restrict__ dp2, float lam,
+                 const float* __restrict__ lam_prob, const int32_t* __restrict__ cam_prob,
                  float* __restrict__ mdiag, float* __restrict__ minv, float* __restrict__ g, uint32_t* err) {
     constexpr int U = 4;
     __shared__ float4 part[2 * PC_WARPS][14];
@@ -152,18 +153,24 @@ k_precond_reduce(int n_cam, const int32_t* __restrict__ cam_off, const int32_t* 
         tot[4 * threadIdx.x + 3] = s4.w;
     }
     __syncthreads();
+    if (lam_prob) lam = lam_prob[cam_prob[cam]];
     if (w == 0) finish_block_warp(cam, tot, dp2, lam, mdiag, minv, g, err, sM, sL, lane);
 }
 
 // ---------------------------------------------------------------------------
-// K5: the CG recursion, one CTA (the vectors hold 9 n_cam floats)
+// K5: the CG recursion.  One CTA works on the camera range [c0, c1) of one
+// problem (9 floats per camera): a single problem uses one CTA of 1024
+// threads; a batch of independent problems one CTA of 256 threads per
+// problem, with the problem's own scalars and damping.
 // ---------------------------------------------------------------------------
 constexpr int PCG_T = 1024;
+constexpr int BPCG_T = 256;
 
-__device__ __forceinline__ void precond_apply(int n_cam, const float* __restrict__ minv,
-                                              const float* __restrict__ r, float* __restrict__ z,
-                                              float& rz) {
-    for (int i = threadIdx.x; i < 9 * n_cam; i += PCG_T) {
+template <int T>
+__device__ __forceinline__ float precond_apply(int c0, int c1, const float* __restrict__ minv,
+                                               const float* __restrict__ r, float* __restrict__ z) {
+    float rz = 0.f;
+    for (int i = 9 * c0 + threadIdx.x; i < 9 * c1; i += T) {
         const int cam = i / 9, row = i - 9 * cam;
         const float* Mi = minv + 81 * (int64_t)cam + 9 * row;
         const float* rc = r + 9 * cam;
@@ -173,28 +180,30 @@ __device__ __forceinline__ void precond_apply(int n_cam, const float* __restrict
         z[i] = s;
         rz += r[i] * s;
     }
+    return rz;
 }
 
-__global__ void __launch_bounds__(PCG_T)
-k_pcg_init(int n_cam, const float* __restrict__ g, const float* __restrict__ minv, float* x, float* r,
-           float* z, float* p, float* q, PcgScalars* S, float lambda, float eta, int max_it) {
-    __shared__ float red[32];
-    const int n = 9 * n_cam;
+// x = 0, r = g, z = M^-1 r, p = z; returns true if there is nothing to solve
+// (zero right-hand side, or skip)
+template <int T>
+__device__ bool pcg_init_range(int c0, int c1, const float* __restrict__ g, const float* __restrict__ minv,
+                               float* x, float* r, float* z, float* p, float* q, PcgScalars* S, float lambda,
+                               float eta, int max_it, bool skip, float* red) {
     float gg = 0.f;
-    for (int i = threadIdx.x; i < n; i += PCG_T) {
-        const float gi = g[i];
+    for (int i = 9 * c0 + threadIdx.x; i < 9 * c1; i += T) {
+        const float gi = skip ? 0.f : g[i];
         x[i] = 0.f;
         r[i] = gi;
         q[i] = 0.f;
         gg += gi * gi;
     }
     __syncthreads();
-    float rz = 0.f;
-    precond_apply(n_cam, minv, r, z, rz);
+    float rz = precond_apply<T>(c0, c1, minv, r, z);
     gg = block_sum(gg, red);
     rz = block_sum(rz, red);
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += PCG_T) p[i] = z[i];
+    for (int i = 9 * c0 + threadIdx.x; i < 9 * c1; i += T) p[i] = z[i];
+    const bool done = !(gg > 0.f && rz > 0.f);
     if (threadIdx.x == 0) {
         S->rho = rz;
         S->q_prev = 0.f;
@@ -204,22 +213,22 @@ k_pcg_init(int n_cam, const float* __restrict__ g, const float* __restrict__ min
         S->eta = eta;
         S->it = 0;
         S->max_it = max_it;
-        S->done = (gg > 0.f && rz > 0.f) ? 0 : 1;
-        S->stop = (gg > 0.f && rz > 0.f) ? -1 : 4;
+        S->done = done ? 1 : 0;
+        S->stop = done ? 4 : -1;
     }
+    return done;
 }
 
-__global__ void __launch_bounds__(PCG_T)
-k_pcg_update(int n_cam, const float* __restrict__ g, const float* __restrict__ dp2,
-             const float* __restrict__ minv, float* x, float* r, float* z, float* p, float* q,
-             PcgScalars* S) {
-    __shared__ float red[32];
-    if (S->done) return;
-    const int n = 9 * n_cam;
+// one CG iteration after q = A^T A p (the matvec); adds the pose damping
+// lambda D_p^2 p to q.  Returns true if a stop rule fired in this call.
+template <int T>
+__device__ bool pcg_update_range(int c0, int c1, const float* __restrict__ g, const float* __restrict__ dp2,
+                                 const float* __restrict__ minv, float* x, float* r, float* z, float* p, float* q,
+                                 PcgScalars* S, float* red) {
     const float lam = S->lambda;
     const float rho = S->rho;
     float pq = 0.f;
-    for (int i = threadIdx.x; i < n; i += PCG_T) {
+    for (int i = 9 * c0 + threadIdx.x; i < 9 * c1; i += T) {
         const float qi = q[i] + lam * dp2[i] * p[i];
         q[i] = qi;
         pq += p[i] * qi;
@@ -230,11 +239,11 @@ k_pcg_update(int n_cam, const float* __restrict__ g, const float* __restrict__ d
             S->done = 1;
             S->stop = 3;
         }
-        return;
+        return true;
     }
     const float alpha = rho / pq;
     float rr = 0.f, xgr = 0.f;
-    for (int i = threadIdx.x; i < n; i += PCG_T) {
+    for (int i = 9 * c0 + threadIdx.x; i < 9 * c1; i += T) {
         const float xi = x[i] + alpha * p[i];
         const float ri = r[i] - alpha * q[i];
         x[i] = xi;
@@ -261,17 +270,65 @@ k_pcg_update(int n_cam, const float* __restrict__ g, const float* __restrict__ d
             S->stop = stop;
         }
     }
-    if (stop >= 0) return;
-    float rz = 0.f;
-    precond_apply(n_cam, minv, r, z, rz);
+    if (stop >= 0) return true;
+    float rz = precond_apply<T>(c0, c1, minv, r, z);
     rz = block_sum(rz, red);
     const float beta = rz / rho;
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += PCG_T) {
+    for (int i = 9 * c0 + threadIdx.x; i < 9 * c1; i += T) {
         p[i] = z[i] + beta * p[i];
         q[i] = 0.f;
     }
     if (threadIdx.x == 0) S->rho = rz;
+    return false;
+}
+
+__global__ void __launch_bounds__(PCG_T)
+k_pcg_init(int n_cam, const float* __restrict__ g, const float* __restrict__ minv, float* x, float* r,
+           float* z, float* p, float* q, PcgScalars* S, float lambda, float eta, int max_it) {
+    __shared__ float red[32];
+    pcg_init_range<PCG_T>(0, n_cam, g, minv, x, r, z, p, q, S, lambda, eta, max_it, false, red);
+}
+
+__global__ void __launch_bounds__(PCG_T)
+k_pcg_update(int n_cam, const float* __restrict__ g, const float* __restrict__ dp2,
+             const float* __restrict__ minv, float* x, float* r, float* z, float* p, float* q,
+             PcgScalars* S) {
+    __shared__ float red[32];
+    if (S->done) return;
+    pcg_update_range<PCG_T>(0, n_cam, g, dp2, minv, x, r, z, p, q, S, red);
+}
+
+// batch: a problem that finishes bumps the counter; the last one marks the
+// batch-wide scalars done (read by the matvec to skip the remaining launches
+// of a graph chunk)
+__device__ __forceinline__ void batch_problem_done(int n_prob, int32_t* n_done, PcgScalars* S_all, int it) {
+    atomicMax(&S_all->it, it);
+    if (atomicAdd(n_done, 1) == n_prob - 1) S_all->done = 1;
+}
+
+__global__ void __launch_bounds__(BPCG_T)
+k_bpcg_init(int n_prob, const int32_t* __restrict__ prob_cam_off, const BatchLm* __restrict__ lm,
+            const float* __restrict__ lam, const float* __restrict__ g, const float* __restrict__ minv, float* x,
+            float* r, float* z, float* p, float* q, PcgScalars* Sb, PcgScalars* S_all, int32_t* n_done, float eta,
+            int max_it) {
+    __shared__ float red[32];
+    const int b = blockIdx.x;
+    const bool done = pcg_init_range<BPCG_T>(prob_cam_off[b], prob_cam_off[b + 1], g, minv, x, r, z, p, q, Sb + b,
+                                             lam[b], eta, max_it, !lm[b].active, red);
+    if (done && threadIdx.x == 0) batch_problem_done(n_prob, n_done, S_all, 0);
+}
+
+__global__ void __launch_bounds__(BPCG_T)
+k_bpcg_update(int n_prob, const int32_t* __restrict__ prob_cam_off, const float* __restrict__ g,
+              const float* __restrict__ dp2, const float* __restrict__ minv, float* x, float* r, float* z, float* p,
+              float* q, PcgScalars* Sb, PcgScalars* S_all, int32_t* n_done) {
+    __shared__ float red[32];
+    const int b = blockIdx.x;
+    PcgScalars* S = Sb + b;
+    if (S->done) return;
+    const bool fin = pcg_update_range<BPCG_T>(prob_cam_off[b], prob_cam_off[b + 1], g, dp2, minv, x, r, z, p, q, S, red);
+    if (fin && threadIdx.x == 0) batch_problem_done(n_prob, n_done, S_all, S->it);
 }
 
 }  // namespace
@@ -280,11 +337,23 @@ void launch_precond_rhs(Problem& p) {
     launch_precond_records(p);
     count_launches(p, 2 + (p.n_obs_direct_big > 0 ? 1 : 0));
     k_precond_reduce<<<p.n_cam, 32 * PC_WARPS, 0, p.stream>>>(p.n_cam, p.cam_off, p.cam_list_st, p.prec, p.dp2,
-                                                             (float)p.lambda_damped, p.mdiag, p.minv, p.g, p.err);
+                                                             (float)p.lambda_damped, p.batch.lam, p.batch.cam_prob,
+                                                             p.mdiag, p.minv, p.g, p.err);
     BA_LAUNCH_CHECK();
 }
 
 void launch_pcg_init(Problem& p) {
+    if (p.batch.n_prob > 0) {
+        BatchState& B = p.batch;
+        count_launches(p, 1);
+        BA_CUDA_TRY(cudaMemsetAsync(p.pcg, 0, sizeof(PcgScalars), p.stream));
+        BA_CUDA_TRY(cudaMemsetAsync(B.n_done, 0, sizeof(int32_t), p.stream));
+        k_bpcg_init<<<B.n_prob, BPCG_T, 0, p.stream>>>(B.n_prob, B.prob_cam_off, B.lm, B.lam, p.g, p.minv, p.x, p.r,
+                                                      p.z, p.p, p.q, B.pcg, p.pcg, B.n_done, (float)p.opt.cg_eta,
+                                                      p.opt.max_cg_iters);
+        BA_LAUNCH_CHECK();
+        return;
+    }
     count_launches(p, 1);
     k_pcg_init<<<1, PCG_T, 0, p.stream>>>(p.n_cam, p.g, p.minv, p.x, p.r, p.z, p.p, p.q, p.pcg,
                                           (float)p.lambda_damped, (float)p.opt.cg_eta, p.opt.max_cg_iters);
@@ -301,7 +370,13 @@ void launch_pcg_iteration(Problem& p, cudaEvent_t mv_begin, cudaEvent_t mv_end) 
     record(mv_begin);
     launch_matvec_raw(p, p.p, p.q, p.pcg);
     record(mv_end);
-    k_pcg_update<<<1, PCG_T, 0, p.stream>>>(p.n_cam, p.g, p.dp2, p.minv, p.x, p.r, p.z, p.p, p.q, p.pcg);
+    if (p.batch.n_prob > 0) {
+        BatchState& B = p.batch;
+        k_bpcg_update<<<B.n_prob, BPCG_T, 0, p.stream>>>(B.n_prob, B.prob_cam_off, p.g, p.dp2, p.minv, p.x, p.r, p.z,
+                                                        p.p, p.q, B.pcg, p.pcg, B.n_done);
+    } else {
+        k_pcg_update<<<1, PCG_T, 0, p.stream>>>(p.n_cam, p.g, p.dp2, p.minv, p.x, p.r, p.z, p.p, p.q, p.pcg);
+    }
     BA_LAUNCH_CHECK();
 }
 

@@ -44,6 +44,44 @@ struct PcgScalars {
     int32_t stop;     // reason (ba_pcg_report.stop_reason)
 };
 
+// Levenberg-Marquardt state of one problem of a batch (device resident;
+// the accept / reject decision runs on the device, Sec. 6.1 rules).
+struct BatchLm {
+    double lambda, nu;
+    double cost;        // E at the current state
+    double cost0;       // E at the initial state
+    double new_cost;    // E at the last candidate
+    double model_cost;  // L of the last step
+    int32_t iter;       // linear solves done
+    int32_t accepted;   // accepted steps
+    int32_t cg_total;   // PCG iterations over all LM iterations
+    int32_t stop;       // 0 running, 1 function tolerance, 2 iteration limit, 3 lambda limit
+    int32_t active;     // 1 while the problem iterates
+    int32_t finish;     // batch LM iteration after which the problem stopped (-1: running)
+    int32_t last_acc;   // the last candidate was accepted
+    int32_t pad;
+};
+
+// Index spaces of a batch of independent problems concatenated into one
+// problem (cameras, landmarks and observations of problem b are contiguous).
+struct BatchState {
+    int32_t n_prob = 0;                  // 0: a single problem
+    int32_t *cam_prob = nullptr, *lm_prob = nullptr;  // owning problem of each camera / landmark
+    int32_t *prob_cam_off = nullptr, *prob_lm_off = nullptr;  // [n_prob + 1]
+    int64_t* prob_obs_off = nullptr;     // [n_prob + 1], sorted observation ranges
+    float* lam = nullptr;                // [n_prob] damping of the current blocks
+    PcgScalars* pcg = nullptr;           // [n_prob] per-problem CG scalars
+    int32_t* n_done = nullptr;           // problems whose CG has stopped
+    BatchLm* lm = nullptr;               // [n_prob]
+    double* lm_model = nullptr;          // [n_pt] per-landmark model cost terms
+    double *cost_a = nullptr, *cost_b = nullptr;  // [n_prob] segmented sums
+    int32_t* n_active = nullptr;         // problems still iterating
+    int32_t* n_active_host = nullptr;    // pinned mirror
+    std::vector<int32_t> h_cam_off, h_lm_off;
+    std::vector<int64_t> h_obs_off;
+    std::vector<cudaEvent_t> iter_events;  // one per batch LM iteration (+ start)
+};
+
 // Optional timing of the phases of the hot path with CUDA events.
 enum ProfSlot { PROF_LINEARIZE = 0, PROF_DAMP, PROF_PRECOND, PROF_MATVEC, PROF_PCG_UPDATE,
                 PROF_BACKSUB, PROF_COST, PROF_NSLOT };
@@ -91,7 +129,14 @@ struct Problem {
     void* mv_tiles = nullptr;        // MvTile[n_mv_tiles]
     int32_t* mv_tile_begin = nullptr;  // first tile of each CTA (grid + 1)
     int n_mv_tiles = 0;
+    int mv_tile_cap = 0;             // tiles the allocation holds
     int mv_grid = 0;
+    // planner parameters (set by the autotuner): blocks with k <= mv_ksmall
+    // are grouped into tiles of up to mv_small_bytes; larger ones are cut
+    // into row tiles
+    int mv_ksmall = 13;
+    int mv_small_bytes = 32768;
+    bool tuned = false;              // the autotuner has chosen the plan
     // blocks
     float *apool = nullptr, *tpool = nullptr, *cpool = nullptr, *rot = nullptr;
     float *dp2 = nullptr, *dl2 = nullptr;
@@ -115,6 +160,9 @@ struct Problem {
     int pcg_graph_iters = 0;
     bool capturing = false;
     std::vector<cudaEvent_t> mv_events;  // 2 per captured PCG iteration (profiling)
+
+    // batch of independent problems (n_prob = 0 for a single problem)
+    BatchState batch;
 
     // counters
     Profiler prof;
@@ -158,11 +206,20 @@ void launch_precond_records(Problem& p);
 int matvec_ctas_per_sm();
 // K6: back substitution + model cost (backsub.cu)
 void launch_backsub(Problem& p);
+// batch: segmented FP64 sums, LM decision and commit (batch.cu)
+void launch_batch_cost(Problem& p, bool candidate, double* out);
+void launch_batch_model(Problem& p);
+void launch_batch_start(Problem& p);
+void launch_batch_decide(Problem& p, int iteration);
+void launch_batch_commit(Problem& p);
 // one-time kernel attributes (dynamic shared memory limits)
 void configure_linearize(Problem& p);
 void configure_matvec(Problem& p);
 // matvec tile plan (host planning + upload), after build_index
 void plan_matvec(Problem& p);
+// planner limits: largest mv_ksmall, largest mv_small_bytes
+int matvec_ksmall_limit();
+int matvec_stage_bytes();
 
 // kernel launch counter (not counted while a graph is being captured)
 inline void count_launches(Problem& p, int n) {
