@@ -337,6 +337,12 @@ SQRTBA_API ba_status ba_batch_restart(ba_batch* b);
 /* Copies problem i's current state to host FP64 arrays (either may be NULL). */
 SQRTBA_API ba_status ba_batch_get_params(ba_batch* b, int32_t i, double* cams, double* pts);
 
+/* Profiling, counters and sizes of the whole batch (as ba_set_profiling,
+ * ba_get_profile and ba_get_info; sizes are totals over the problems). */
+SQRTBA_API ba_status ba_batch_set_profiling(ba_batch* b, int32_t enable);
+SQRTBA_API ba_status ba_batch_get_profile(ba_batch* b, ba_profile* out);
+SQRTBA_API ba_status ba_batch_get_info(ba_batch* b, ba_info* info);
+
 /* Like ba_last_error for a batch (b = NULL: the last ba_batch_create failure). */
 SQRTBA_API const char* ba_batch_last_error(const ba_batch* b);
 

@@ -144,6 +144,9 @@ _SIGS = {
     "ba_batch_solve": [_P, ctypes.POINTER(BatchReport), ctypes.POINTER(BatchSummary)],
     "ba_batch_restart": [_P],
     "ba_batch_get_params": [_P, ctypes.c_int32, _d, _d],
+    "ba_batch_set_profiling": [_P, ctypes.c_int32],
+    "ba_batch_get_profile": [_P, ctypes.POINTER(Profile)],
+    "ba_batch_get_info": [_P, ctypes.POINTER(Info)],
     "ba_debug_export_order": [_P, _i32, _i64, _i64, _i32],
     "ba_debug_export_landmark": [_P, ctypes.c_int32, ctypes.c_int32, _f, _f, _f, _f, _i32],
     "ba_debug_export_damping": [_P, _f, _f],
@@ -454,6 +457,21 @@ class Batch:
 
     def restart(self):
         self._check(lib().ba_batch_restart(self.h))
+
+    def set_profiling(self, enable=True):
+        self._check(lib().ba_batch_set_profiling(self.h, 1 if enable else 0))
+
+    def profile(self):
+        pr = Profile()
+        self._check(lib().ba_batch_get_profile(self.h, ctypes.byref(pr)))
+        out = {name: dict(ms=pr.ms[i], count=pr.count[i]) for i, name in enumerate(PROFILE_SLOTS)}
+        out.update(kernel_launches=pr.kernel_launches, h2d_bytes=pr.h2d_bytes, d2h_bytes=pr.d2h_bytes)
+        return out
+
+    def info(self):
+        i = Info()
+        self._check(lib().ba_batch_get_info(self.h, ctypes.byref(i)))
+        return _struct_dict(i)
 
     def get_params(self, i):
         nc, npt, _ = self.sizes[i]

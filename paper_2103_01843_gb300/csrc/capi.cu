@@ -486,6 +486,37 @@ void create_problem(Problem& p, const double* cams, int32_t n_cam, const double*
     sync(p);
 }
 
+void set_profiling_impl(Problem& p, int32_t enable) {
+    sync(p);
+    p.prof.on = false;
+    p.prof.pending.clear();
+    p.prof.next = 0;
+    for (int i = 0; i < PROF_NSLOT; ++i) {
+        p.prof.ms[i] = 0.0;
+        p.prof.count[i] = 0;
+    }
+    p.launches = 0;
+    p.h2d_bytes = p.d2h_bytes = 0;
+    if (enable && p.mv_events.empty()) {
+        p.mv_events.resize(2 * PCG_CHUNK);
+        for (auto& e : p.mv_events) BA_CUDA_TRY(cudaEventCreate(&e));
+    }
+    destroy_graph(p);  // recaptured on the next solve, with event nodes only when profiling
+    p.prof.on = enable != 0;
+}
+
+void get_profile_impl(Problem& p, ba_profile* out) {
+    sync(p);
+    std::memset(out, 0, sizeof(*out));
+    for (int i = 0; i < PROF_NSLOT; ++i) {
+        out->ms[i] = p.prof.ms[i];
+        out->count[i] = p.prof.count[i];
+    }
+    out->kernel_launches = p.launches;
+    out->h2d_bytes = p.h2d_bytes;
+    out->d2h_bytes = p.d2h_bytes;
+}
+
 // --- batches of independent problems -----------------------------------------------
 thread_local std::string g_batch_create_error;
 
@@ -848,23 +879,7 @@ ba_status ba_get_info(ba_problem* h, ba_info* info) {
 ba_status ba_set_profiling(ba_problem* h, int32_t enable) {
     if (!h) return BA_ERR_INVALID_ARG;
     API_TRY
-    Problem& p = h->p;
-    sync(p);
-    p.prof.on = false;
-    p.prof.pending.clear();
-    p.prof.next = 0;
-    for (int i = 0; i < PROF_NSLOT; ++i) {
-        p.prof.ms[i] = 0.0;
-        p.prof.count[i] = 0;
-    }
-    p.launches = 0;
-    p.h2d_bytes = p.d2h_bytes = 0;
-    if (enable && p.mv_events.empty()) {
-        p.mv_events.resize(2 * PCG_CHUNK);
-        for (auto& e : p.mv_events) BA_CUDA_TRY(cudaEventCreate(&e));
-    }
-    destroy_graph(p);  // recaptured on the next solve, with event nodes only when profiling
-    p.prof.on = enable != 0;
+    set_profiling_impl(h->p, enable);
     return BA_OK;
     API_CATCH(h)
 }
@@ -872,16 +887,7 @@ ba_status ba_set_profiling(ba_problem* h, int32_t enable) {
 ba_status ba_get_profile(ba_problem* h, ba_profile* out) {
     if (!h || !out) return BA_ERR_INVALID_ARG;
     API_TRY
-    Problem& p = h->p;
-    sync(p);
-    std::memset(out, 0, sizeof(*out));
-    for (int i = 0; i < PROF_NSLOT; ++i) {
-        out->ms[i] = p.prof.ms[i];
-        out->count[i] = p.prof.count[i];
-    }
-    out->kernel_launches = p.launches;
-    out->h2d_bytes = p.h2d_bytes;
-    out->d2h_bytes = p.d2h_bytes;
+    get_profile_impl(h->p, out);
     return BA_OK;
     API_CATCH(h)
 }
@@ -1109,6 +1115,35 @@ ba_status ba_batch_get_params(ba_batch* b, int32_t i, double* cams, double* pts)
         for (size_t k = 0; k < x.size(); ++k) pts[k] = x[k];
     return BA_OK;
     BATCH_CATCH(b)
+}
+
+ba_status ba_batch_set_profiling(ba_batch* b, int32_t enable) {
+    if (!b) return BA_ERR_INVALID_ARG;
+    BATCH_TRY
+    set_profiling_impl(b->p, enable);
+    return BA_OK;
+    BATCH_CATCH(b)
+}
+
+ba_status ba_batch_get_profile(ba_batch* b, ba_profile* out) {
+    if (!b || !out) return BA_ERR_INVALID_ARG;
+    BATCH_TRY
+    get_profile_impl(b->p, out);
+    return BA_OK;
+    BATCH_CATCH(b)
+}
+
+ba_status ba_batch_get_info(ba_batch* b, ba_info* info) {
+    if (!b || !info) return BA_ERR_INVALID_ARG;
+    std::memset(info, 0, sizeof(*info));
+    info->n_cam = b->p.n_cam;
+    info->n_pt = b->p.n_pt;
+    info->n_obs = b->p.n_obs;
+    info->a_pool_floats = b->p.a_floats;
+    info->sum_k2 = b->p.sum_k2;
+    info->k_max = b->p.k_max;
+    info->device_bytes = b->p.device_bytes;
+    return BA_OK;
 }
 
 const char* ba_batch_last_error(const ba_batch* b) {
