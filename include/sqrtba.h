@@ -72,7 +72,9 @@ typedef struct {
     int32_t use_graph;    /* 1 (default): PCG iterations replayed from a CUDA graph */
     int32_t autotune;     /* 1: the first PCG solve first runs the matvec autotuner
                              (ba_autotune); default 0 */
-    int32_t reserved[6];  /* zero */
+    int32_t use_learned;  /* 1: PCG with the learned warm start and corrected block
+                             preconditioner of the model attached by ba_set_learned */
+    int32_t reserved[5];  /* zero */
 } ba_options;
 
 /* Fills *opt with the defaults above. */
@@ -83,6 +85,8 @@ typedef struct {
     int32_t stop_reason;  /* 0 forcing test, 1 residual, 2 iteration limit, 3 breakdown, 4 zero rhs */
     double residual_norm; /* ||g - H~ x|| by the CG recursion */
     double rhs_norm;      /* ||g|| */
+    int32_t learned;      /* 1 if the learned warm start / preconditioner was used */
+    int32_t warm_start;   /* 1 if the learned warm start was kept (see ba_set_learned) */
 } ba_pcg_report;
 
 typedef struct {
@@ -345,6 +349,68 @@ SQRTBA_API ba_status ba_batch_get_info(ba_batch* b, ba_info* info);
 
 /* Like ba_last_error for a batch (b = NULL: the last ba_batch_create failure). */
 SQRTBA_API const char* ba_batch_last_error(const ba_batch* b);
+
+/* ---------------------------------------------------------------------- */
+/* Learned warm start and block-preconditioner correction.                 */
+/* ---------------------------------------------------------------------- */
+
+/* The paper has no learned part; this is an extension of its block-Jacobi
+ * PCG (Sec. 5.4).  Per camera i, with M_i the damped 9x9 diagonal block of
+ * the reduced camera system (the block-Jacobi block), M_i = L_i L_i^T, and
+ * g_i the camera's right-hand side, a small MLP (19 -> 256 -> 256 -> 256 ->
+ * 54, GELU, BF16 weights and activations on the tensor cores, FP32
+ * accumulation) maps the features
+ *   [log diag(M_i) (9), (L_i^-1 g_i) / |L_i^-1 g_i| (9), log(observations of i)]
+ * to o_i (9) and the lower triangle of E_i (45, row by row), giving
+ *   a warm start            x0_i = (M_i^-1 g_i) * (1 + tanh(o_i))  (elementwise)
+ *   a corrected block       B_i = L_i^-T (I + E_i)(I + E_i)^T L_i^-1,
+ *                           diag(I + E_i) = 1 + 0.9 tanh(e_ii) > 0.1 (SPD).
+ * With use_learned the PCG starts from x0 (kept only if the quadratic model
+ * Q(x0) = -1/2 x0^T (g + r0) is negative, i.e. better than the zero start,
+ * judged on the true residual r0 = g - H~ x0) and applies B_i instead of
+ * M_i^-1.  If that CG breaks down or ends with a residual no smaller than
+ * |g|, the plain block-Jacobi CG from zero is run instead (counted by
+ * ba_learned_fallbacks).
+ *
+ * Parameters: BA_MLP_PARAMS floats, FP32, in this order: W0 (256 x 19,
+ * row-major, out x in), b0 (256), W1 (256 x 256), b1, W2 (256 x 256), b2,
+ * W3 (54 x 256), b3 (54). */
+#define BA_MLP_PARAMS 150582
+typedef struct ba_mlp ba_mlp; /* opaque */
+
+/* Creates a model from host FP32 parameters (copied).  Errors:
+ * BA_ERR_INVALID_ARG for a null pointer or a non-finite value. */
+SQRTBA_API ba_status ba_mlp_create(const float* params, void* cuda_stream, ba_mlp** out);
+SQRTBA_API ba_status ba_mlp_destroy(ba_mlp* m);
+/* Copies the FP32 master parameters to host memory. */
+SQRTBA_API ba_status ba_mlp_get_params(ba_mlp* m, float* params);
+/* Forward pass: d_feats (device, n x 19 FP32, row-major) -> d_out (device,
+ * n x 54 FP32).  Synchronises the model's stream. */
+SQRTBA_API ba_status ba_mlp_forward(ba_mlp* m, const float* d_feats, int32_t n, float* d_out);
+/* Training samples from solver data (device pointers): d_M (n x 81, the
+ * damped blocks M_i), d_g (n x 9), d_xstar (n x 9, the camera blocks of a
+ * tight solve; may be NULL), d_count (n, observations per camera) ->
+ * d_feats (n x 19) and d_aux (n x 72: L_i lower triangle row by row, w_i =
+ * L_i^-1 g_i, s_i = M_i^-1 g_i, z*_i = L_i^T x*_i).  A block that is not
+ * positive definite gives zero features and head inputs (zero loss). */
+SQRTBA_API ba_status ba_mlp_prepare(ba_mlp* m, const float* d_M, const float* d_g, const float* d_xstar,
+                                    const int32_t* d_count, int32_t n, float* d_feats, float* d_aux);
+/* Mean training loss over n samples,
+ *   ( |L^T x0 - z*|^2 + |F F^T w - z*|^2 ) / |z*|^2,  F = I + E,
+ * i.e. |x0 - x*|_M^2 + |B g - x*|_M^2 normalised per camera, and (grads,
+ * host, BA_MLP_PARAMS floats, may be NULL) its gradient. */
+SQRTBA_API ba_status ba_mlp_loss_grad(ba_mlp* m, const float* d_feats, const float* d_aux, int32_t n,
+                                      double* loss, float* grads);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the loss of n samples;
+ * *loss (may be NULL) gets the loss before the step. */
+SQRTBA_API ba_status ba_mlp_train_step(ba_mlp* m, const float* d_feats, const float* d_aux, int32_t n,
+                                       float lr, double* loss);
+SQRTBA_API const char* ba_mlp_last_error(const ba_mlp* m);
+/* Attaches a model to a problem (NULL detaches); the model must outlive its
+ * use and is run on the problem's stream. */
+SQRTBA_API ba_status ba_set_learned(ba_problem* h, ba_mlp* model);
+/* Number of learned solves that were replaced by the plain CG. */
+SQRTBA_API ba_status ba_learned_fallbacks(ba_problem* h, int64_t* count);
 
 /* ---------------------------------------------------------------------- */
 /* Inspection exports for tests (copy device state to host buffers).       */

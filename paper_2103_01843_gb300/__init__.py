@@ -39,12 +39,14 @@ class Options(ctypes.Structure):
     _fields_ = [("lambda0", ctypes.c_double), ("max_lm_iters", ctypes.c_int32),
                 ("func_tol", ctypes.c_double), ("max_cg_iters", ctypes.c_int32),
                 ("cg_eta", ctypes.c_double), ("use_graph", ctypes.c_int32),
-                ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("autotune", ctypes.c_int32), ("use_learned", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class PcgReport(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("stop_reason", ctypes.c_int32),
-                ("residual_norm", ctypes.c_double), ("rhs_norm", ctypes.c_double)]
+                ("residual_norm", ctypes.c_double), ("rhs_norm", ctypes.c_double),
+                ("learned", ctypes.c_int32), ("warm_start", ctypes.c_int32)]
 
 
 class LmReport(ctypes.Structure):
@@ -147,6 +149,15 @@ _SIGS = {
     "ba_batch_set_profiling": [_P, ctypes.c_int32],
     "ba_batch_get_profile": [_P, ctypes.POINTER(Profile)],
     "ba_batch_get_info": [_P, ctypes.POINTER(Info)],
+    "ba_mlp_create": [_f, _P, ctypes.POINTER(_P)],
+    "ba_mlp_destroy": [_P],
+    "ba_mlp_get_params": [_P, _f],
+    "ba_mlp_forward": [_P, _P, ctypes.c_int32, _P],
+    "ba_mlp_prepare": [_P, _P, _P, _P, _P, ctypes.c_int32, _P, _P],
+    "ba_mlp_loss_grad": [_P, _P, _P, ctypes.c_int32, _d, _f],
+    "ba_mlp_train_step": [_P, _P, _P, ctypes.c_int32, ctypes.c_float, _d],
+    "ba_set_learned": [_P, _P],
+    "ba_learned_fallbacks": [_P, _i64],
     "ba_debug_export_order": [_P, _i32, _i64, _i64, _i32],
     "ba_debug_export_landmark": [_P, ctypes.c_int32, ctypes.c_int32, _f, _f, _f, _f, _i32],
     "ba_debug_export_damping": [_P, _f, _f],
@@ -176,13 +187,16 @@ def lib():
             L.ba_last_error.restype = ctypes.c_char_p
             L.ba_batch_last_error.argtypes = [_P]
             L.ba_batch_last_error.restype = ctypes.c_char_p
+            L.ba_mlp_last_error.argtypes = [_P]
+            L.ba_mlp_last_error.restype = ctypes.c_char_p
             _lib = L
     return _lib
 
 
 def exported_symbols():
     """Names the binding expects the library to export."""
-    return sorted(list(_SIGS) + ["ba_default_options", "ba_last_error", "ba_batch_last_error"])
+    return sorted(list(_SIGS) + ["ba_default_options", "ba_last_error", "ba_batch_last_error",
+                                 "ba_mlp_last_error"])
 
 
 def default_options(**kw):
@@ -329,6 +343,16 @@ class Problem:
         r = TuneReport()
         self._check(lib().ba_autotune(self.h, ctypes.byref(r)))
         return _struct_dict(r)
+
+    def set_learned(self, model):
+        """Attach a Mlp (None detaches); the model must outlive its use."""
+        self._model = model
+        self._check(lib().ba_set_learned(self.h, model.h if model is not None else None))
+
+    def learned_fallbacks(self):
+        c = ctypes.c_int64()
+        self._check(lib().ba_learned_fallbacks(self.h, ctypes.byref(c)))
+        return c.value
 
     def set_profiling(self, enable=True):
         self._check(lib().ba_set_profiling(self.h, 1 if enable else 0))
@@ -479,3 +503,85 @@ class Batch:
         p = np.zeros((npt, 3))
         self._check(lib().ba_batch_get_params(self.h, int(i), _ptr(c, _d), _ptr(p, _d)))
         return c, p
+
+
+MLP_PARAMS = 150582
+MLP_IN, MLP_OUT, MLP_AUX = 19, 54, 72
+
+
+class Mlp:
+    """The learned warm start / preconditioner model (ba_mlp_*).  Device
+    arguments are CUDA tensors (float32 / int32, contiguous) or raw device
+    addresses; parameters are host float32 arrays of MLP_PARAMS values."""
+
+    def __init__(self, params, stream=None):
+        L = lib()
+        prm = np.ascontiguousarray(params, np.float32).ravel()
+        assert prm.size == MLP_PARAMS
+        h = _P()
+        rc = L.ba_mlp_create(_ptr(prm, _f), _P(stream) if stream else None, ctypes.byref(h))
+        if rc != BA_OK:
+            raise BAError(rc, L.ba_mlp_last_error(None).decode())
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ba_mlp_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != BA_OK:
+            raise BAError(rc, lib().ba_mlp_last_error(self.h).decode())
+
+    def params(self):
+        out = np.zeros(MLP_PARAMS, np.float32)
+        self._check(lib().ba_mlp_get_params(self.h, _ptr(out, _f)))
+        return out
+
+    def forward(self, feats, out):
+        self._check(lib().ba_mlp_forward(self.h, _devptr(feats), int(feats.shape[0]), _devptr(out)))
+
+    def prepare(self, M, g, xstar, count, feats, aux):
+        self._check(lib().ba_mlp_prepare(self.h, _devptr(M), _devptr(g), _devptr(xstar) if xstar is not None else None,
+                                         _devptr(count), int(count.shape[0]), _devptr(feats), _devptr(aux)))
+
+    def loss_grad(self, feats, aux, with_grads=True):
+        loss = ctypes.c_double()
+        grads = np.zeros(MLP_PARAMS, np.float32) if with_grads else None
+        self._check(lib().ba_mlp_loss_grad(self.h, _devptr(feats), _devptr(aux), int(feats.shape[0]),
+                                           ctypes.byref(loss), _ptr(grads, _f) if with_grads else None))
+        return loss.value, grads
+
+    def train_step(self, feats, aux, lr):
+        loss = ctypes.c_double()
+        self._check(lib().ba_mlp_train_step(self.h, _devptr(feats), _devptr(aux), int(feats.shape[0]),
+                                            float(lr), ctypes.byref(loss)))
+        return loss.value
+
+
+def mlp_params_flat(params):
+    """Flatten [(W, b), ...] (the oracle's layout) into the C-ABI order."""
+    return np.concatenate([np.concatenate([W.ravel(), b.ravel()]) for W, b in params]).astype(np.float32)
+
+
+def mlp_params_unflat(flat, sizes=(19, 256, 256, 256, 54)):
+    out, o = [], 0
+    for i, n in zip(sizes[:-1], sizes[1:]):
+        W = np.asarray(flat[o:o + n * i], np.float64).reshape(n, i)
+        o += n * i
+        b = np.asarray(flat[o:o + n], np.float64)
+        o += n
+        out.append((W, b))
+    return out

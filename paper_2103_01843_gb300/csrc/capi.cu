@@ -12,6 +12,7 @@
 #include <utility>
 #include <vector>
 
+#include "learned.cuh"
 #include "problem.cuh"
 
 namespace sqrtba {
@@ -22,6 +23,10 @@ using namespace sqrtba;
 
 struct ba_problem {
     Problem p;
+};
+
+struct ba_mlp {
+    Mlp m;
 };
 
 struct ba_batch {
@@ -262,14 +267,38 @@ void run_autotune(Problem& p, ba_tune_report* rep) {
     }
 }
 
+// K8 before the CG: features of every camera, the MLP, the warm start x0
+// (into x) and the corrected blocks B_i; q = (A^T A) x0 for the residual.
+void start_learned(Problem& p) {
+    if (!p.minv_l) {
+        p.lfeat = dalloc<float>(p, (int64_t)ML_IN * p.n_cam);
+        p.laux = dalloc<float>(p, (int64_t)ML_AUX * p.n_cam);
+        p.minv_l = dalloc<float>(p, 81LL * p.n_cam);
+    }
+    learned_apply(p, *p.mlp);
+    BA_CUDA_TRY(cudaMemsetAsync(p.q, 0, sizeof(float) * 9 * p.n_cam, p.stream));
+    count_launches(p, 1);
+    launch_matvec_raw(p, p.x, p.q, nullptr);
+    launch_pcg_init_warm(p);
+}
+
 void do_pcg(Problem& p, ba_pcg_report* rep) {
     require(p.damped, BA_ERR_STATE, "ba_pcg_solve: blocks are not marginalised (call ba_marginalize_qr)");
+    const bool learned = p.opt.use_learned != 0;
+    require(!learned || p.mlp, BA_ERR_STATE, "use_learned is set but no model is attached (ba_set_learned)");
+    require(!learned || p.batch.n_prob == 0, BA_ERR_INVALID_ARG, "the learned mode solves single problems");
     if (p.opt.autotune && !p.tuned) run_autotune(p, nullptr);
     PhaseTimer t(p, PROF_PRECOND);
     launch_precond_rhs(p);
-    launch_pcg_init(p);
+    p.learned_active = learned;
+    if (learned) start_learned(p);
+    else launch_pcg_init(p);
     t.end();
-    if (p.opt.use_graph && !p.pcg_graph) capture_pcg_graph(p);
+    if (p.pcg_graph && p.graph_learned != p.learned_active) destroy_graph(p);
+    if (p.opt.use_graph && !p.pcg_graph) {
+        capture_pcg_graph(p);
+        p.graph_learned = p.learned_active;
+    }
     int launched = 0, it_before = 0;
     for (;;) {
         if (p.opt.use_graph) {
@@ -291,7 +320,25 @@ void do_pcg(Problem& p, ba_pcg_report* rep) {
             }
         }
         it_before = p.pcg_host->it;
-        if (p.pcg_host->done || launched >= p.opt.max_cg_iters + PCG_CHUNK) break;
+        if (p.pcg_host->done || launched >= p.opt.max_cg_iters + PCG_CHUNK) {
+            // the true residual judges the learned solve: on a breakdown, or
+            // no reduction of the residual, plain block-Jacobi CG from zero
+            // is run instead
+            if (p.learned_active && (p.pcg_host->stop == 3 || !(p.pcg_host->rnorm < p.pcg_host->gnorm))) {
+                p.learned_active = false;
+                p.learned_fallbacks += 1;
+                destroy_graph(p);
+                launch_pcg_init(p);
+                if (p.opt.use_graph) {
+                    capture_pcg_graph(p);
+                    p.graph_learned = false;
+                }
+                launched = 0;
+                it_before = 0;
+                continue;
+            }
+            break;
+        }
     }
     p.solved = true;
     p.backsubbed = false;
@@ -300,6 +347,8 @@ void do_pcg(Problem& p, ba_pcg_report* rep) {
         rep->stop_reason = p.pcg_host->stop;
         rep->residual_norm = p.pcg_host->rnorm;
         rep->rhs_norm = p.pcg_host->gnorm;
+        rep->learned = p.learned_active ? 1 : 0;
+        rep->warm_start = p.learned_active ? p.pcg_host->warm : 0;
     }
 }
 
@@ -519,6 +568,7 @@ void get_profile_impl(Problem& p, ba_profile* out) {
 
 // --- batches of independent problems -----------------------------------------------
 thread_local std::string g_batch_create_error;
+thread_local std::string g_mlp_create_error;
 
 void create_batch(ba_batch* bh, const ba_problem_desc* descs, int32_t n, const ba_options* opt, void* stream) {
     require(descs != nullptr && n >= 1, BA_ERR_INVALID_ARG, "no problems");
@@ -1148,6 +1198,124 @@ ba_status ba_batch_get_info(ba_batch* b, ba_info* info) {
 
 const char* ba_batch_last_error(const ba_batch* b) {
     return b ? b->p.last_error.c_str() : g_batch_create_error.c_str();
+}
+
+// --- learned warm start / preconditioner correction -----------------------------
+#define MLP_TRY try {
+#define MLP_CATCH(h)                                  \
+    }                                                 \
+    catch (const Error& e) {                          \
+        (h)->m.last_error = e.msg;                    \
+        return e.code;                                \
+    }                                                 \
+    catch (const std::bad_alloc&) {                   \
+        (h)->m.last_error = "host allocation failed"; \
+        return BA_ERR_OOM;                            \
+    }
+
+ba_status ba_mlp_create(const float* params, void* cuda_stream, ba_mlp** out) {
+    ba_mlp* h = nullptr;
+    g_mlp_create_error.clear();
+    try {
+        require(out != nullptr && params != nullptr, BA_ERR_INVALID_ARG, "null pointer");
+        *out = nullptr;
+        for (int64_t i = 0; i < ML_P; ++i) require(std::isfinite(params[i]), BA_ERR_INVALID_ARG, "non-finite parameter");
+        h = new ba_mlp();
+        mlp_init(h->m, params, (cudaStream_t)cuda_stream);
+        *out = h;
+        return BA_OK;
+    } catch (const Error& e) {
+        g_mlp_create_error = e.msg;
+        if (h) {
+            mlp_free(h->m);
+            delete h;
+        }
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        g_mlp_create_error = "host allocation failed";
+        if (h) {
+            mlp_free(h->m);
+            delete h;
+        }
+        return BA_ERR_OOM;
+    }
+}
+
+ba_status ba_mlp_destroy(ba_mlp* h) {
+    if (!h) return BA_OK;
+    mlp_free(h->m);
+    delete h;
+    return BA_OK;
+}
+
+ba_status ba_mlp_get_params(ba_mlp* h, float* params) {
+    if (!h || !params) return BA_ERR_INVALID_ARG;
+    MLP_TRY
+    BA_CUDA_TRY(cudaMemcpyAsync(params, h->m.master, sizeof(float) * ML_P, cudaMemcpyDeviceToHost, h->m.stream));
+    BA_CUDA_TRY(cudaStreamSynchronize(h->m.stream));
+    return BA_OK;
+    MLP_CATCH(h)
+}
+
+ba_status ba_mlp_forward(ba_mlp* h, const float* d_feats, int32_t n, float* d_out) {
+    if (!h || !d_feats || !d_out || n < 1) return BA_ERR_INVALID_ARG;
+    MLP_TRY
+    mlp_forward(h->m, d_feats, n, d_out);
+    BA_CUDA_TRY(cudaStreamSynchronize(h->m.stream));
+    return BA_OK;
+    MLP_CATCH(h)
+}
+
+ba_status ba_mlp_prepare(ba_mlp* h, const float* d_M, const float* d_g, const float* d_xstar, const int32_t* d_count,
+                         int32_t n, float* d_feats, float* d_aux) {
+    if (!h || !d_M || !d_g || !d_count || !d_feats || !d_aux || n < 1) return BA_ERR_INVALID_ARG;
+    MLP_TRY
+    mlp_prepare(h->m.stream, d_M, d_g, d_xstar, d_count, n, d_feats, d_aux);
+    BA_CUDA_TRY(cudaStreamSynchronize(h->m.stream));
+    return BA_OK;
+    MLP_CATCH(h)
+}
+
+ba_status ba_mlp_loss_grad(ba_mlp* h, const float* d_feats, const float* d_aux, int32_t n, double* loss,
+                           float* grads) {
+    if (!h || !d_feats || !d_aux || n < 1) return BA_ERR_INVALID_ARG;
+    MLP_TRY
+    const double l = mlp_loss_grad(h->m, d_feats, d_aux, n);
+    if (loss) *loss = l;
+    if (grads) {
+        BA_CUDA_TRY(cudaMemcpyAsync(grads, h->m.grad, sizeof(float) * ML_P, cudaMemcpyDeviceToHost, h->m.stream));
+        BA_CUDA_TRY(cudaStreamSynchronize(h->m.stream));
+    }
+    return BA_OK;
+    MLP_CATCH(h)
+}
+
+ba_status ba_mlp_train_step(ba_mlp* h, const float* d_feats, const float* d_aux, int32_t n, float lr,
+                            double* loss) {
+    if (!h || !d_feats || !d_aux || n < 1 || !(lr > 0.f)) return BA_ERR_INVALID_ARG;
+    MLP_TRY
+    const double l = mlp_loss_grad(h->m, d_feats, d_aux, n);
+    mlp_adam(h->m, lr, 0.9f, 0.999f, 1e-8f);
+    if (loss) *loss = l;
+    return BA_OK;
+    MLP_CATCH(h)
+}
+
+const char* ba_mlp_last_error(const ba_mlp* h) { return h ? h->m.last_error.c_str() : g_mlp_create_error.c_str(); }
+
+ba_status ba_set_learned(ba_problem* h, ba_mlp* model) {
+    if (!h) return BA_ERR_INVALID_ARG;
+    API_TRY
+    sync(h->p);
+    h->p.mlp = model ? &model->m : nullptr;
+    return BA_OK;
+    API_CATCH(h)
+}
+
+ba_status ba_learned_fallbacks(ba_problem* h, int64_t* count) {
+    if (!h || !count) return BA_ERR_INVALID_ARG;
+    *count = h->p.learned_fallbacks;
+    return BA_OK;
 }
 
 }  // extern "C"

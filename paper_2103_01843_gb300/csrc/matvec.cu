@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "problem.cuh"
+#include "ptx.cuh"
 
 namespace sqrtba {
 
@@ -38,7 +39,6 @@ constexpr int MV_THREADS = 32 * (MV_CONSUMERS + 1);
 constexpr int MV_KSMALL_MAX = 21;   // whole blocks, specialised per k (up to the planner's mv_ksmall)
 constexpr int MV_KBIG = 222;        // row ranges, multiples of 4 rows (36k * 4 <= 32 KB)
 constexpr int MV_UMAX = 45;         // rows of one big tile (multiple of MV_CONSUMERS)
-constexpr uint64_t MV_WAIT_NS = 2000000000ull;
 
 constexpr int MV_STAGE_R = 2048;    // bytes of c_j values per stage (preconditioner mode)
 // Shared-memory layout for NS stages; ACC_OFF starts the per-CTA
@@ -90,60 +90,6 @@ struct MvArgs {
     const float* cpool;  // preconditioner mode: c_j in storage order
     float* rec;          // preconditioner mode: REC floats per observation (storage order)
 };
-
-// --- PTX wrappers ---------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-// Bounded wait for the phase of `parity`; false after MV_WAIT_NS or when another
-// warp has aborted (honour_abort).
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint32_t* err,
-                          bool honour_abort = true) {
-    if (mbar_try(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    for (;;) {
-        if (mbar_try(bar, parity)) return true;
-        if (honour_abort && *abort_flag) return false;
-        if (global_ns() - t0 > MV_WAIT_NS) {
-            *abort_flag = 1;
-            atomicOr(err, ERRBIT_TIMEOUT);
-            return false;
-        }
-    }
-}
 
 // --- consumers ---------------------------------------------------------------------
 template <int K>

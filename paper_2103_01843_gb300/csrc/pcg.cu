@@ -215,6 +215,7 @@ __device__ bool pcg_init_range(int c0, int c1, const float* __restrict__ g, cons
         S->max_it = max_it;
         S->done = done ? 1 : 0;
         S->stop = done ? 4 : -1;
+        S->warm = 0;
     }
     return done;
 }
@@ -283,6 +284,68 @@ __device__ bool pcg_update_range(int c0, int c1, const float* __restrict__ g, co
     return false;
 }
 
+// Warm start (learned): x = x0 is given and q = (A^T A) x0 from the matvec;
+// r = g - q - lambda D_p^2 x0 and Q(x0) = -1/2 x0^T (g + r).  The true
+// residual judges the warm start: unless Q(x0) < 0 (a decrease of the
+// quadratic model from the zero start) it is dropped and CG starts from 0.
+template <int T>
+__device__ bool pcg_init_warm_range(int c0, int c1, const float* __restrict__ g, const float* __restrict__ dp2,
+                                    const float* __restrict__ minv, float* x, float* r, float* z, float* p,
+                                    float* q, PcgScalars* S, float lambda, float eta, int max_it, float* red) {
+    float gg = 0.f, xgr = 0.f;
+    for (int i = 9 * c0 + threadIdx.x; i < 9 * c1; i += T) {
+        const float gi = g[i], xi = x[i];
+        const float ri = gi - q[i] - lambda * dp2[i] * xi;
+        r[i] = ri;
+        gg += gi * gi;
+        xgr += xi * (gi + ri);
+    }
+    gg = block_sum(gg, red);
+    xgr = block_sum(xgr, red);
+    const float q0 = -0.5f * xgr;
+    const bool keep = q0 < 0.f;
+    __syncthreads();
+    for (int i = 9 * c0 + threadIdx.x; i < 9 * c1; i += T) {
+        if (!keep) {
+            x[i] = 0.f;
+            r[i] = g[i];
+        }
+        q[i] = 0.f;
+    }
+    __syncthreads();
+    float rz = precond_apply<T>(c0, c1, minv, r, z);
+    float rr = 0.f;
+    for (int i = 9 * c0 + threadIdx.x; i < 9 * c1; i += T) rr += r[i] * r[i];
+    rz = block_sum(rz, red);
+    rr = block_sum(rr, red);
+    __syncthreads();
+    for (int i = 9 * c0 + threadIdx.x; i < 9 * c1; i += T) p[i] = z[i];
+    const float rn = sqrtf(rr), gn = sqrtf(gg);
+    const bool done = !(gg > 0.f && rz > 0.f) || rn <= 1e-10f * gn;
+    if (threadIdx.x == 0) {
+        S->rho = rz;
+        S->q_prev = keep ? q0 : 0.f;
+        S->gnorm = gn;
+        S->rnorm = rn;
+        S->lambda = lambda;
+        S->eta = eta;
+        S->it = 0;
+        S->max_it = max_it;
+        S->done = done ? 1 : 0;
+        S->stop = done ? (gg > 0.f ? 1 : 4) : -1;
+        S->warm = keep ? 1 : 0;
+    }
+    return done;
+}
+
+__global__ void __launch_bounds__(PCG_T)
+k_pcg_init_warm(int n_cam, const float* __restrict__ g, const float* __restrict__ dp2,
+                const float* __restrict__ minv, float* x, float* r, float* z, float* p, float* q, PcgScalars* S,
+                float lambda, float eta, int max_it) {
+    __shared__ float red[32];
+    pcg_init_warm_range<PCG_T>(0, n_cam, g, dp2, minv, x, r, z, p, q, S, lambda, eta, max_it, red);
+}
+
 __global__ void __launch_bounds__(PCG_T)
 k_pcg_init(int n_cam, const float* __restrict__ g, const float* __restrict__ minv, float* x, float* r,
            float* z, float* p, float* q, PcgScalars* S, float lambda, float eta, int max_it) {
@@ -342,6 +405,10 @@ void launch_precond_rhs(Problem& p) {
     BA_LAUNCH_CHECK();
 }
 
+// the block inverses the CG applies: plain block Jacobi, or the learned
+// correction B_i when the learned mode is active for this solve
+const float* active_minv(const Problem& p) { return p.learned_active ? p.minv_l : p.minv; }
+
 void launch_pcg_init(Problem& p) {
     if (p.batch.n_prob > 0) {
         BatchState& B = p.batch;
@@ -355,8 +422,15 @@ void launch_pcg_init(Problem& p) {
         return;
     }
     count_launches(p, 1);
-    k_pcg_init<<<1, PCG_T, 0, p.stream>>>(p.n_cam, p.g, p.minv, p.x, p.r, p.z, p.p, p.q, p.pcg,
+    k_pcg_init<<<1, PCG_T, 0, p.stream>>>(p.n_cam, p.g, active_minv(p), p.x, p.r, p.z, p.p, p.q, p.pcg,
                                           (float)p.lambda_damped, (float)p.opt.cg_eta, p.opt.max_cg_iters);
+    BA_LAUNCH_CHECK();
+}
+
+void launch_pcg_init_warm(Problem& p) {
+    count_launches(p, 1);
+    k_pcg_init_warm<<<1, PCG_T, 0, p.stream>>>(p.n_cam, p.g, p.dp2, active_minv(p), p.x, p.r, p.z, p.p, p.q, p.pcg,
+                                               (float)p.lambda_damped, (float)p.opt.cg_eta, p.opt.max_cg_iters);
     BA_LAUNCH_CHECK();
 }
 
@@ -375,7 +449,8 @@ void launch_pcg_iteration(Problem& p, cudaEvent_t mv_begin, cudaEvent_t mv_end) 
         k_bpcg_update<<<B.n_prob, BPCG_T, 0, p.stream>>>(B.n_prob, B.prob_cam_off, p.g, p.dp2, p.minv, p.x, p.r, p.z,
                                                         p.p, p.q, B.pcg, p.pcg, B.n_done);
     } else {
-        k_pcg_update<<<1, PCG_T, 0, p.stream>>>(p.n_cam, p.g, p.dp2, p.minv, p.x, p.r, p.z, p.p, p.q, p.pcg);
+        k_pcg_update<<<1, PCG_T, 0, p.stream>>>(p.n_cam, p.g, p.dp2, active_minv(p), p.x, p.r, p.z, p.p, p.q,
+                                                p.pcg);
     }
     BA_LAUNCH_CHECK();
 }

@@ -42,6 +42,8 @@ struct PcgScalars {
     int32_t max_it;
     int32_t done;     // 1 once a stop rule fired
     int32_t stop;     // reason (ba_pcg_report.stop_reason)
+    int32_t warm;     // 1 if the learned warm start was kept
+    int32_t pad;
 };
 
 // Levenberg-Marquardt state of one problem of a batch (device resident;
@@ -164,6 +166,15 @@ struct Problem {
     // batch of independent problems (n_prob = 0 for a single problem)
     BatchState batch;
 
+    // learned warm start and preconditioner correction (K8)
+    struct Mlp* mlp = nullptr;       // attached model (not owned)
+    float* lfeat = nullptr;          // [n_cam][19] features
+    float* laux = nullptr;           // [n_cam][72] head inputs
+    float* minv_l = nullptr;         // [n_cam][81] corrected block inverses B_i
+    bool learned_active = false;     // the CG of this solve uses minv_l
+    bool graph_learned = false;      // the captured graph was built with minv_l
+    int64_t learned_fallbacks = 0;   // learned solves replaced by the plain CG
+
     // counters
     Profiler prof;
     int64_t launches = 0;      // kernels launched by the library
@@ -199,6 +210,8 @@ void launch_damp(Problem& p, bool undo_old, float lambda);
 // K3, K5: preconditioner and PCG (pcg.cu); K4: matvec (matvec.cu)
 void launch_precond_rhs(Problem& p);
 void launch_pcg_init(Problem& p);
+void launch_pcg_init_warm(Problem& p);
+const float* active_minv(const Problem& p);
 void launch_pcg_iteration(Problem& p, cudaEvent_t mv_begin = nullptr, cudaEvent_t mv_end = nullptr);
 void launch_matvec(Problem& p, const float* v, float* y, bool add_damping);
 void launch_matvec_raw(Problem& p, const float* v, float* y, const PcgScalars* S);

@@ -312,7 +312,7 @@ def _finish(rng, name, seed, R, t, f, k1, k2, X, obs_cam, obs_pt,
                  name=name, seed=seed)
 
 
-CONFIGS = ("tiny", "medium", "large", "small", "batched_member")
+CONFIGS = ("tiny", "medium", "large", "small", "batched_member", "walk")
 
 
 def make_scene(name="tiny", seed=0, noise_px=1.0, perturb=True, **kw):
@@ -331,6 +331,10 @@ def make_scene(name="tiny", seed=0, noise_px=1.0, perturb=True, **kw):
              (defaults 32 cams, 2000 points, p = 0.3, cap 32).
     batched_member : member `seed` of the 256-problem batch: cams U[8, 64],
              points U[200, 5000], k = 2 + Geom0(0.3) capped at n_cam.
+    walk   : medium-shaped (the medium generator and k distribution) with
+             n_cam / n_pt given by keywords (defaults 100 cams, 20000
+             points); the training and evaluation scenes of the learned
+             warm start.
     """
     rng = np.random.default_rng(seed)
     if name == "tiny":
@@ -346,6 +350,8 @@ def make_scene(name="tiny", seed=0, noise_px=1.0, perturb=True, **kw):
         gt = _gt_ring(rng, n_cam, n_pt, 10.0, 2.5,
                       _geom0(kw.get("p", 0.3), kw.get("cap", 32)),
                       height_sigma=0.5)
+    elif name == "walk":
+        gt = _gt_walk(rng, kw.get("n_cam", 100), kw.get("n_pt", 20_000), _geom0(0.2, 64))
     elif name == "batched_member":
         n_cam = int(rng.integers(8, 65))
         n_pt = int(rng.integers(200, 5001))
