@@ -368,9 +368,9 @@ SQRTBA_API const char* ba_batch_last_error(const ba_batch* b);
  * With use_learned the PCG starts from x0 (kept only if the quadratic model
  * Q(x0) = -1/2 x0^T (g + r0) is negative, i.e. better than the zero start,
  * judged on the true residual r0 = g - H~ x0) and applies B_i instead of
- * M_i^-1.  If that CG breaks down or ends with a residual no smaller than
- * |g|, the plain block-Jacobi CG from zero is run instead (counted by
- * ba_learned_fallbacks).
+ * M_i^-1.  If that CG breaks down or ends without a decrease of the
+ * quadratic model below Q(0) = 0, the plain block-Jacobi CG from zero is run
+ * instead (counted by ba_learned_fallbacks).
  *
  * Parameters: BA_MLP_PARAMS floats, FP32, in this order: W0 (256 x 19,
  * row-major, out x in), b0 (256), W1 (256 x 256), b1, W2 (256 x 256), b2,

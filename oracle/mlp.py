@@ -15,7 +15,7 @@ of the right-hand side g_i to
 
 Features (19 per camera): log of the 9 diagonal entries of M_i, the
 direction of the whitened right-hand side w_i = L_i^-1 g_i (w_i / |w_i|),
-and log of the camera's observation count.
+and log of the camera's observation count (at least 1).
 
 Training loss per camera, with x*_i the camera block of a tight solve of the
 reduced system and z*_i = L_i^T x*_i:
@@ -74,7 +74,8 @@ def features(M, g, count):
     s = np.linalg.solve(M, g[..., None])[..., 0]
     nw = np.linalg.norm(w, axis=1, keepdims=True)
     wd = np.where(nw > 0, w / np.where(nw > 0, nw, 1.0), 0.0)
-    f = np.concatenate([np.log(np.einsum("nii->ni", M)), wd, np.log(np.asarray(count, np.float64))[:, None]], axis=1)
+    cnt = np.maximum(np.asarray(count, np.float64), 1.0)  # a camera without observations counts as one
+    f = np.concatenate([np.log(np.einsum("nii->ni", M)), wd, np.log(cnt)[:, None]], axis=1)
     return f, L, w, s
 
 

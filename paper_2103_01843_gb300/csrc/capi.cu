@@ -321,10 +321,11 @@ void do_pcg(Problem& p, ba_pcg_report* rep) {
         }
         it_before = p.pcg_host->it;
         if (p.pcg_host->done || launched >= p.opt.max_cg_iters + PCG_CHUNK) {
-            // the true residual judges the learned solve: on a breakdown, or
-            // no reduction of the residual, plain block-Jacobi CG from zero
-            // is run instead
-            if (p.learned_active && (p.pcg_host->stop == 3 || !(p.pcg_host->rnorm < p.pcg_host->gnorm))) {
+            // the learned solve is judged by the quadratic model of its
+            // iterate, Q(x) = -1/2 x^T (g + r) with r the recursion's
+            // residual: on a breakdown, or no decrease below Q(0) = 0, the
+            // plain block-Jacobi CG from zero is run instead
+            if (p.learned_active && (p.pcg_host->stop == 3 || !(p.pcg_host->q_prev < 0.f))) {
                 p.learned_active = false;
                 p.learned_fallbacks += 1;
                 destroy_graph(p);

@@ -305,7 +305,7 @@ __device__ void prepare_one(const float* M, const float* g, const float* xs, int
         f[i] = logf(M[i * 9 + i]);
         f[9 + i] = nw > 0.f ? w[i] / nw : 0.f;
     }
-    f[18] = logf((float)count);
+    f[18] = logf((float)max(count, 1));
     int t = 0;
     for (int i = 0; i < 9; ++i)
         for (int j = 0; j <= i; ++j) aux[t++] = L[i * 9 + j];
@@ -538,7 +538,7 @@ __global__ void k_camera_prepare(int n_cam, const float* __restrict__ mdiag, con
                                  float* __restrict__ aux) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_cam) return;
-    prepare_one(mdiag + 81LL * i, g + 9LL * i, nullptr, max(1, cam_off[i + 1] - cam_off[i]),
+    prepare_one(mdiag + 81LL * i, g + 9LL * i, nullptr, cam_off[i + 1] - cam_off[i],
                 feats + (int64_t)ML_IN * i, aux + (int64_t)ML_AUX * i);
 }
 

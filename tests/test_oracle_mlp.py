@@ -39,6 +39,8 @@ def test_head_closed_forms():
     np.testing.assert_allclose(f[:, :9], np.log(np.einsum("nii->ni", M)))
     np.testing.assert_allclose(np.linalg.norm(f[:, 9:18], axis=1), 1.0)
     np.testing.assert_allclose(f[:, 18], np.log(np.arange(1, 6)))
+    f0, _, _, _ = mlp.features(M[:1], g[:1], [0])
+    assert f0[0, 18] == 0.0  # a camera without observations counts as one
     np.testing.assert_allclose(np.einsum("nij,nj->ni", L, w), g, rtol=1e-10)
 
 
