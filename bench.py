@@ -15,6 +15,7 @@ FP64 oracle (explicit Schur complement) on the host cores instead.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
     python bench.py --config batched   # 256 independent problems: problems/s, p50/p99
+    python bench.py --config learned --steps 3   # learned vs plain PCG (trains first)
 """
 from __future__ import annotations
 
@@ -48,6 +49,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--learned-train", type=int, default=32)
+    ap.add_argument("--learned-eval", type=int, default=8)
+    ap.add_argument("--learned-steps", type=int, default=3000)
     ap.add_argument("--mode", default="solve", choices=["solve", "matvec"],
                     help="matvec: only repeat the PCG matvec on a linearised, damped problem "
                          "(a short run for kernel profiling; prints no bench line)")
@@ -534,6 +538,55 @@ def run_reference_batched(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# learned warm start + preconditioner: PCG iterations and time, learned vs plain
+# ---------------------------------------------------------------------------
+LEARNED_METRIC = "PCG iters learned vs plain"
+
+
+def run_learned(args):
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2103_01843_gb300 as sq
+    from paper_2103_01843_gb300 import learned
+    from paper_2103_01843_gb300.synth import make_scene
+    sq.lib()
+    n_train, n_eval = args.learned_train, args.learned_eval
+    t0 = time.perf_counter()
+    samples = [learned.solver_samples(make_scene("walk", s)) for s in range(1000, 1000 + n_train)]
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    model, losses = learned.train(samples, steps=args.learned_steps, lr=1e-3, seed=0)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    res = [learned.compare(make_scene("walk", s), model, repeats=max(1, args.steps))
+           for s in range(100000, 100000 + n_eval)]
+    def agg(name, key):
+        return float(np.mean([r[name][key] for r in res]))
+    pcg_p = agg("plain", "pcg_iters") / max(agg("plain", "lm_iters"), 1e-9)
+    pcg_l = agg("learned", "pcg_iters") / max(agg("learned", "lm_iters"), 1e-9)
+    rel_cost = max(abs(r["learned"]["final_cost"] - r["plain"]["final_cost"]) / r["plain"]["final_cost"] for r in res)
+    line = {
+        "metric": LEARNED_METRIC, "value": pcg_l / pcg_p, "unit": "ratio (PCG iterations per LM iteration)",
+        "n_gpus": 1, "steps": args.steps, "warmup": 0, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 MLP / f32 solver", "data": "synthetic",
+        "config": {"workload": f"learned: trained on {n_train} medium-shaped walk scenes (100 cams, 20000 "
+                               f"landmarks, seeds 1000..), evaluated on {n_eval} held-out seeds (100000..)",
+                   "train_samples": int(sum(x["g"].shape[0] for x in samples)), "train_steps": args.learned_steps,
+                   "data_gen_s": t_data, "train_s": t_train,
+                   "loss_first": losses[0], "loss_last50": float(np.mean(losses[-50:]))},
+        "pcg_iters_per_lm_iter": {"plain": pcg_p, "learned": pcg_l},
+        "time_to_tol_s": {"plain": agg("plain", "seconds"), "learned": agg("learned", "seconds")},
+        "lm_iters_to_tol": {"plain": agg("plain", "lm_iters"), "learned": agg("learned", "lm_iters")},
+        "final_cost_max_rel_diff": rel_cost,
+        "fallbacks": int(sum(r["learned"]["fallbacks"] for r in res)),
+    }
+    print(json.dumps(line), flush=True)
+    model.close()
+    return 0
+
+
 def run_matvec_only(args):
     """Linearise and damp once, then `steps` PCG matvecs (kernel profiling)."""
     import numpy as np
@@ -555,6 +608,12 @@ def main():
     args = parse()
     if args.mode == "matvec":
         return run_matvec_only(args)
+    if args.config == "learned":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the learned mode has no oracle-side solver to time "
+                              "(the oracle pins its MLP numerics only)"}), flush=True)
+            return 0
+        return run_learned(args)
     if args.config == "batched":
         return run_reference_batched(args) if args.impl == "reference" else run_batched(args)
     if args.impl == "reference":
