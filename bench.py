@@ -52,9 +52,10 @@ def parse():
     ap.add_argument("--learned-train", type=int, default=32)
     ap.add_argument("--learned-eval", type=int, default=8)
     ap.add_argument("--learned-steps", type=int, default=3000)
-    ap.add_argument("--mode", default="solve", choices=["solve", "matvec"],
-                    help="matvec: only repeat the PCG matvec on a linearised, damped problem "
-                         "(a short run for kernel profiling; prints no bench line)")
+    ap.add_argument("--mode", default="solve", choices=["solve", "matvec", "kernels", "mlp"],
+                    help="kernel-profiling runs that print no bench line: matvec repeats the PCG "
+                         "matvec on a linearised, damped problem; kernels runs every kernel of one "
+                         "LM iteration; mlp runs the learned model's forward on 4096 rows")
     return ap.parse_args()
 
 
@@ -587,6 +588,44 @@ def run_learned(args):
     return 0
 
 
+def run_kernels_only(args):
+    """Every kernel of one LM iteration, `warmup + steps` times (kernel
+    profiling): linearise + QR, damping, preconditioner + PCG, back
+    substitution, candidate cost."""
+    import torch
+    import paper_2103_01843_gb300 as sq
+    from paper_2103_01843_gb300.synth import make_scene
+    torch.cuda.set_device(0)
+    scene = make_scene(args.config, args.seed)
+    with sq.Problem.from_scene(scene, stream=torch.cuda.current_stream().cuda_stream) as p:
+        for _ in range(args.warmup + args.steps):
+            p.linearize()
+            p.marginalize_qr(1e-4)
+            p.pcg_solve()
+            p.backsubstitute()
+            p.eval_cost(candidate=True)
+    return 0
+
+
+def run_mlp_only(args):
+    """The learned model's tensor-core forward on 4096 rows (kernel profiling)."""
+    import numpy as np
+    import torch
+    import paper_2103_01843_gb300 as sq
+    from paper_2103_01843_gb300 import learned
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(0)
+    prm = learned.init_params(0)
+    prm[-13878:] = rng.standard_normal(13878).astype(np.float32) * 0.05  # non-zero output layer
+    n = 4096
+    feats = torch.as_tensor(rng.standard_normal((n, 19)).astype(np.float32), device="cuda")
+    out = torch.zeros((n, 54), dtype=torch.float32, device="cuda")
+    with sq.Mlp(prm) as m:
+        for _ in range(args.warmup + args.steps):
+            m.forward(feats, out)
+    return 0
+
+
 def run_matvec_only(args):
     """Linearise and damp once, then `steps` PCG matvecs (kernel profiling)."""
     import numpy as np
@@ -608,6 +647,10 @@ def main():
     args = parse()
     if args.mode == "matvec":
         return run_matvec_only(args)
+    if args.mode == "kernels":
+        return run_kernels_only(args)
+    if args.mode == "mlp":
+        return run_mlp_only(args)
     if args.config == "learned":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the learned mode has no oracle-side solver to time "
