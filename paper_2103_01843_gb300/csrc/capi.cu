@@ -148,17 +148,22 @@ void free_all(Problem& p) {
 }
 
 // --- the steps of the hot path ------------------------------------------------
-void do_linearize(Problem& p) {
+// K1 (+ D_p^2).  The energy at the linearisation point is evaluated unless
+// the host already knows it (the accepted candidate's cost).
+void do_linearize(Problem& p, bool need_cost = true) {
     PhaseTimer t(p, PROF_LINEARIZE);
     launch_camera_diag(p);
     launch_linearize(p);
     t.end();
-    PhaseTimer tc(p, PROF_COST);
-    launch_cost(p, false);
-    tc.end();
-    d2h(p, p.dsum_host, p.dsum, 1);
-    sync(p);
-    p.cost = p.dsum_host[0];
+    if (need_cost || !p.cost_valid) {
+        PhaseTimer tc(p, PROF_COST);
+        launch_cost(p, false);
+        tc.end();
+        d2h(p, p.dsum_host, p.dsum, 1);
+        sync(p);
+        p.cost = p.dsum_host[0];
+        p.cost_valid = true;
+    }
     p.linearized = true;
     p.damped = false;
     p.solved = false;
@@ -199,6 +204,47 @@ void capture_pcg_graph(Problem& p) {
     cudaGraphDestroy(graph);
     BA_CUDA_TRY(e);
     p.pcg_graph_iters = PCG_CHUNK;
+}
+
+// The whole CG as one graph launch: a conditional WHILE node whose body is
+// one iteration (matvec + update); the update kernel clears the condition
+// when a stop rule fires (the iteration limit bounds the loop).  Event
+// record nodes are not allowed in conditional bodies, so profiling runs use
+// the chunked graph above.
+void capture_pcg_while_graph(Problem& p) {
+    cudaGraph_t graph = nullptr;
+    BA_CUDA_TRY(cudaGraphCreate(&graph, 0));
+    try {
+        cudaGraphConditionalHandle cond;
+        BA_CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams prm = {};
+        prm.type = cudaGraphNodeTypeConditional;
+        prm.conditional.handle = cond;
+        prm.conditional.type = cudaGraphCondTypeWhile;
+        prm.conditional.size = 1;
+        cudaGraphNode_t node;
+        BA_CUDA_TRY(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &prm));
+        cudaGraph_t body = prm.conditional.phGraph_out[0];
+        BA_CUDA_TRY(cudaStreamBeginCaptureToGraph(p.stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        p.capturing = true;
+        try {
+            launch_pcg_iteration(p, nullptr, nullptr, true, cond);
+        } catch (...) {
+            p.capturing = false;
+            cudaGraph_t g2 = nullptr;
+            cudaStreamEndCapture(p.stream, &g2);
+            throw;
+        }
+        p.capturing = false;
+        cudaGraph_t g2 = nullptr;
+        BA_CUDA_TRY(cudaStreamEndCapture(p.stream, &g2));
+        BA_CUDA_TRY(cudaGraphInstantiate(&p.pcg_graph, graph, 0));
+    } catch (...) {
+        cudaGraphDestroy(graph);
+        throw;
+    }
+    cudaGraphDestroy(graph);
+    p.pcg_graph_iters = 0;  // the graph runs the CG to its end
 }
 
 // --- matvec autotuner ----------------------------------------------------------
@@ -282,7 +328,8 @@ void start_learned(Problem& p) {
     launch_pcg_init_warm(p);
 }
 
-void do_pcg(Problem& p, ba_pcg_report* rep) {
+// K3 and the CG start (plain, or K8 with the learned warm start)
+void pcg_start(Problem& p) {
     require(p.damped, BA_ERR_STATE, "ba_pcg_solve: blocks are not marginalised (call ba_marginalize_qr)");
     const bool learned = p.opt.use_learned != 0;
     require(!learned || p.mlp, BA_ERR_STATE, "use_learned is set but no model is attached (ba_set_learned)");
@@ -294,10 +341,29 @@ void do_pcg(Problem& p, ba_pcg_report* rep) {
     if (learned) start_learned(p);
     else launch_pcg_init(p);
     t.end();
-    if (p.pcg_graph && p.graph_learned != p.learned_active) destroy_graph(p);
+}
+
+// Runs the CG iterations.  The WHILE graph needs no host round trip: the
+// scalars are copied back behind it and read at the next synchronisation
+// (wait = true synchronises here).  The chunked forms (profiling, or no
+// graphs) poll the done flag after every chunk of PCG_CHUNK iterations.
+void pcg_iterate(Problem& p, bool wait) {
+    const bool while_graph = p.opt.use_graph && !p.prof.on;
+    const int kind = !p.opt.use_graph ? 0 : (while_graph ? 2 : 1);
+    if (p.pcg_graph && (p.graph_learned != p.learned_active || p.graph_kind != kind)) destroy_graph(p);
     if (p.opt.use_graph && !p.pcg_graph) {
-        capture_pcg_graph(p);
+        if (while_graph) capture_pcg_while_graph(p);
+        else capture_pcg_graph(p);
         p.graph_learned = p.learned_active;
+        p.graph_kind = kind;
+    }
+    if (while_graph) {
+        BA_CUDA_TRY(cudaGraphLaunch(p.pcg_graph, p.stream));
+        count_launches(p, 2);  // per iteration; the rest is added when the count is known
+        p.pending_iteration_launches = true;
+        d2h(p, p.pcg_host, p.pcg, 1);
+        if (wait) sync(p);
+        return;
     }
     int launched = 0, it_before = 0;
     for (;;) {
@@ -320,37 +386,49 @@ void do_pcg(Problem& p, ba_pcg_report* rep) {
             }
         }
         it_before = p.pcg_host->it;
-        if (p.pcg_host->done || launched >= p.opt.max_cg_iters + PCG_CHUNK) {
-            // the learned solve is judged by the quadratic model of its
-            // iterate, Q(x) = -1/2 x^T (g + r) with r the recursion's
-            // residual: on a breakdown, or no decrease below Q(0) = 0, the
-            // plain block-Jacobi CG from zero is run instead
-            if (p.learned_active && (p.pcg_host->stop == 3 || !(p.pcg_host->q_prev < 0.f))) {
-                p.learned_active = false;
-                p.learned_fallbacks += 1;
-                destroy_graph(p);
-                launch_pcg_init(p);
-                if (p.opt.use_graph) {
-                    capture_pcg_graph(p);
-                    p.graph_learned = false;
-                }
-                launched = 0;
-                it_before = 0;
-                continue;
-            }
-            break;
-        }
+        if (p.pcg_host->done || launched >= p.opt.max_cg_iters + PCG_CHUNK) break;
     }
+}
+
+// After the CG's scalars are on the host: the learned solve is judged by the
+// quadratic model of its iterate, Q(x) = -1/2 x^T (g + r) with r the
+// recursion's residual; on a breakdown, or no decrease below Q(0) = 0, the
+// plain block-Jacobi CG from zero is run instead.  Returns true if it re-ran.
+bool pcg_judge(Problem& p) {
+    if (p.pending_iteration_launches) {
+        // the loop body ran max(it, 1) times (a batch: once more, to end the loop)
+        count_launches(p, 2 * std::max(0, p.pcg_host->it - 1) + (p.batch.n_prob > 0 ? 2 : 0));
+        p.pending_iteration_launches = false;
+    }
+    if (!(p.learned_active && (p.pcg_host->stop == 3 || !(p.pcg_host->q_prev < 0.f)))) return false;
+    p.learned_active = false;
+    p.learned_fallbacks += 1;
+    launch_pcg_init(p);
+    pcg_iterate(p, true);
+    if (p.pending_iteration_launches) {
+        count_launches(p, 2 * std::max(0, p.pcg_host->it - 1));
+        p.pending_iteration_launches = false;
+    }
+    return true;
+}
+
+void fill_pcg_report(const Problem& p, ba_pcg_report* rep) {
+    if (!rep) return;
+    rep->iterations = p.pcg_host->it;
+    rep->stop_reason = p.pcg_host->stop;
+    rep->residual_norm = p.pcg_host->rnorm;
+    rep->rhs_norm = p.pcg_host->gnorm;
+    rep->learned = p.learned_active ? 1 : 0;
+    rep->warm_start = p.learned_active ? p.pcg_host->warm : 0;
+}
+
+void do_pcg(Problem& p, ba_pcg_report* rep) {
+    pcg_start(p);
+    pcg_iterate(p, true);
+    pcg_judge(p);
     p.solved = true;
     p.backsubbed = false;
-    if (rep) {
-        rep->iterations = p.pcg_host->it;
-        rep->stop_reason = p.pcg_host->stop;
-        rep->residual_norm = p.pcg_host->rnorm;
-        rep->rhs_norm = p.pcg_host->gnorm;
-        rep->learned = p.learned_active ? 1 : 0;
-        rep->warm_start = p.learned_active ? p.pcg_host->warm : 0;
-    }
+    fill_pcg_report(p, rep);
 }
 
 double do_backsub(Problem& p) {
@@ -382,16 +460,36 @@ void do_lm_step(Problem& p, ba_lm_report* rep) {
     ba_lm_report r{};
     r.iteration = p.iteration;
     if (!p.linearized) {
-        do_linearize(p);
+        do_linearize(p, false);
         r.relinearized = 1;
     }
     const double E = p.cost;
     const double lam = p.lambda;
     do_marginalize(p, lam);
+    // K3-K7 enqueued back to back; one synchronisation for the scalars
+    // (the learned mode synchronises once more to judge its CG)
+    pcg_start(p);
+    const bool learned = p.learned_active;
+    pcg_iterate(p, learned);
+    if (learned) pcg_judge(p);
+    p.solved = true;
+    {
+        PhaseTimer tb(p, PROF_BACKSUB);
+        launch_backsub(p);
+        tb.end();
+        PhaseTimer tc(p, PROF_COST);
+        launch_candidate(p);
+        launch_cost(p, true);
+        tc.end();
+    }
+    d2h(p, p.dsum_host, p.dsum, 2);
+    sync(p);
+    if (!learned) pcg_judge(p);
     ba_pcg_report pr{};
-    do_pcg(p, &pr);
-    const double L = do_backsub(p);
-    const double En = do_eval_cost(p, true);
+    fill_pcg_report(p, &pr);
+    p.backsubbed = true;
+    const double L = p.dsum_host[1];
+    const double En = p.dsum_host[0];
     // a step is accepted only if the model predicts a decrease (E - L > 0);
     // near convergence both differences sink below the FP32 evaluation noise
     // and their ratio alone would accept noise
@@ -409,6 +507,7 @@ void do_lm_step(Problem& p, ba_lm_report* rep) {
         std::swap(p.cams, p.cand_cams);
         std::swap(p.pts, p.cand_pts);
         p.cost = En;
+        p.cost_valid = true;
         p.linearized = false;
         p.damped = false;
         p.solved = false;
@@ -884,6 +983,7 @@ ba_status ba_set_params(ba_problem* h, const double* cams, const double* pts) {
     h2d(p, p.pts, x.data(), (int64_t)x.size());
     sync(p);
     p.linearized = p.damped = p.solved = p.backsubbed = false;
+    p.cost_valid = false;
     p.lambda = p.opt.lambda0;
     p.nu = 2.0;
     p.iteration = 0;

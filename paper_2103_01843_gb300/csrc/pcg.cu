@@ -353,22 +353,30 @@ k_pcg_init(int n_cam, const float* __restrict__ g, const float* __restrict__ min
     pcg_init_range<PCG_T>(0, n_cam, g, minv, x, r, z, p, q, S, lambda, eta, max_it, false, red);
 }
 
+// `cond`: when the iterations run inside a conditional WHILE node of a CUDA
+// graph (cond_on != 0), the kernel ends the loop by setting the node's
+// condition to 0 once the CG has stopped; the only writer is thread 0.
 __global__ void __launch_bounds__(PCG_T)
 k_pcg_update(int n_cam, const float* __restrict__ g, const float* __restrict__ dp2,
              const float* __restrict__ minv, float* x, float* r, float* z, float* p, float* q,
-             PcgScalars* S) {
+             PcgScalars* S, cudaGraphConditionalHandle cond, int cond_on) {
     __shared__ float red[32];
-    if (S->done) return;
-    pcg_update_range<PCG_T>(0, n_cam, g, dp2, minv, x, r, z, p, q, S, red);
+    if (S->done) {
+        if (cond_on && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
+        return;
+    }
+    const bool fin = pcg_update_range<PCG_T>(0, n_cam, g, dp2, minv, x, r, z, p, q, S, red);
+    if (fin && cond_on && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
 }
 
 // batch: a problem that finishes bumps the counter; the last one marks the
-// batch-wide scalars done (read by the matvec to skip the remaining launches
-// of a graph chunk)
+// batch-wide scalars done (read by the matvec to skip the remaining work)
 __device__ __forceinline__ void batch_problem_done(int n_prob, int32_t* n_done, PcgScalars* S_all, int it) {
     atomicMax(&S_all->it, it);
     if (atomicAdd(n_done, 1) == n_prob - 1) S_all->done = 1;
 }
+
+__global__ void k_set_max_it(PcgScalars* S, int max_it) { S->max_it = max_it; }
 
 __global__ void __launch_bounds__(BPCG_T)
 k_bpcg_init(int n_prob, const int32_t* __restrict__ prob_cam_off, const BatchLm* __restrict__ lm,
@@ -382,12 +390,24 @@ k_bpcg_init(int n_prob, const int32_t* __restrict__ prob_cam_off, const BatchLm*
     if (done && threadIdx.x == 0) batch_problem_done(n_prob, n_done, S_all, 0);
 }
 
+// In a WHILE node the loop is ended by CTA 0 alone, at the start of the
+// iteration after the batch-wide done flag was set (one writer, no race), or
+// once the iterations exceed max_it + 2 (a guard: every problem stops at
+// max_it by itself).
 __global__ void __launch_bounds__(BPCG_T)
 k_bpcg_update(int n_prob, const int32_t* __restrict__ prob_cam_off, const float* __restrict__ g,
               const float* __restrict__ dp2, const float* __restrict__ minv, float* x, float* r, float* z, float* p,
-              float* q, PcgScalars* Sb, PcgScalars* S_all, int32_t* n_done) {
+              float* q, PcgScalars* Sb, PcgScalars* S_all, int32_t* n_done, cudaGraphConditionalHandle cond,
+              int cond_on) {
     __shared__ float red[32];
     const int b = blockIdx.x;
+    if (cond_on && b == 0 && threadIdx.x == 0) {
+        const int loops = ++S_all->pad;
+        if (S_all->done || loops > S_all->max_it + 2) {
+            S_all->done = 1;
+            cudaGraphSetConditional(cond, 0);
+        }
+    }
     PcgScalars* S = Sb + b;
     if (S->done) return;
     const bool fin = pcg_update_range<BPCG_T>(prob_cam_off[b], prob_cam_off[b + 1], g, dp2, minv, x, r, z, p, q, S, red);
@@ -415,6 +435,7 @@ void launch_pcg_init(Problem& p) {
         count_launches(p, 1);
         BA_CUDA_TRY(cudaMemsetAsync(p.pcg, 0, sizeof(PcgScalars), p.stream));
         BA_CUDA_TRY(cudaMemsetAsync(B.n_done, 0, sizeof(int32_t), p.stream));
+        k_set_max_it<<<1, 1, 0, p.stream>>>(p.pcg, p.opt.max_cg_iters);
         k_bpcg_init<<<B.n_prob, BPCG_T, 0, p.stream>>>(B.n_prob, B.prob_cam_off, B.lm, B.lam, p.g, p.minv, p.x, p.r,
                                                       p.z, p.p, p.q, B.pcg, p.pcg, B.n_done, (float)p.opt.cg_eta,
                                                       p.opt.max_cg_iters);
@@ -434,7 +455,8 @@ void launch_pcg_init_warm(Problem& p) {
     BA_LAUNCH_CHECK();
 }
 
-void launch_pcg_iteration(Problem& p, cudaEvent_t mv_begin, cudaEvent_t mv_end) {
+void launch_pcg_iteration(Problem& p, cudaEvent_t mv_begin, cudaEvent_t mv_end, bool in_while,
+                          cudaGraphConditionalHandle cond) {
     count_launches(p, 2);
     auto record = [&](cudaEvent_t ev) {
         if (!ev) return;
@@ -447,10 +469,10 @@ void launch_pcg_iteration(Problem& p, cudaEvent_t mv_begin, cudaEvent_t mv_end) 
     if (p.batch.n_prob > 0) {
         BatchState& B = p.batch;
         k_bpcg_update<<<B.n_prob, BPCG_T, 0, p.stream>>>(B.n_prob, B.prob_cam_off, p.g, p.dp2, p.minv, p.x, p.r, p.z,
-                                                        p.p, p.q, B.pcg, p.pcg, B.n_done);
+                                                        p.p, p.q, B.pcg, p.pcg, B.n_done, cond, in_while ? 1 : 0);
     } else {
         k_pcg_update<<<1, PCG_T, 0, p.stream>>>(p.n_cam, p.g, p.dp2, active_minv(p), p.x, p.r, p.z, p.p, p.q,
-                                                p.pcg);
+                                                p.pcg, cond, in_while ? 1 : 0);
     }
     BA_LAUNCH_CHECK();
 }

@@ -43,7 +43,7 @@ struct PcgScalars {
     int32_t done;     // 1 once a stop rule fired
     int32_t stop;     // reason (ba_pcg_report.stop_reason)
     int32_t warm;     // 1 if the learned warm start was kept
-    int32_t pad;
+    int32_t pad;      // batch-wide scalars: iterations of the graph loop
 };
 
 // Levenberg-Marquardt state of one problem of a batch (device resident;
@@ -160,6 +160,8 @@ struct Problem {
     // CUDA graph of a chunk of PCG iterations
     cudaGraphExec_t pcg_graph = nullptr;
     int pcg_graph_iters = 0;
+    int graph_kind = 0;              // 1 chunk of PCG_CHUNK iterations, 2 conditional WHILE loop
+    bool pending_iteration_launches = false;  // WHILE launch: kernel count known after the sync
     bool capturing = false;
     std::vector<cudaEvent_t> mv_events;  // 2 per captured PCG iteration (profiling)
 
@@ -186,7 +188,8 @@ struct Problem {
     double lambda = 1e-4, nu = 2.0;
     int32_t iteration = 0;
     bool stopped = false;
-    double cost = 0.0;               // E at the current state (valid when linearized)
+    double cost = 0.0;               // E at the current state
+    bool cost_valid = false;         // cost holds E of the current state
     int64_t device_bytes = 0;
     std::vector<void*> allocations;
     std::string last_error;
@@ -212,7 +215,10 @@ void launch_precond_rhs(Problem& p);
 void launch_pcg_init(Problem& p);
 void launch_pcg_init_warm(Problem& p);
 const float* active_minv(const Problem& p);
-void launch_pcg_iteration(Problem& p, cudaEvent_t mv_begin = nullptr, cudaEvent_t mv_end = nullptr);
+// in_while: the launch is captured into the body of a conditional WHILE
+// graph node whose condition `cond` the update kernel clears when the CG stops
+void launch_pcg_iteration(Problem& p, cudaEvent_t mv_begin = nullptr, cudaEvent_t mv_end = nullptr,
+                          bool in_while = false, cudaGraphConditionalHandle cond = 0);
 void launch_matvec(Problem& p, const float* v, float* y, bool add_damping);
 void launch_matvec_raw(Problem& p, const float* v, float* y, const PcgScalars* S);
 void launch_precond_records(Problem& p);
