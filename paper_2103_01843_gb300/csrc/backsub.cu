@@ -1,8 +1,9 @@
 // K6: landmark back substitution (Eq. backsub_nm, damped form of Sec. 5.3):
 //     dx_l = -R1^-1 (Q1^T r + Q1^T J_p dx_p)
-// from the three top rows of each landmark block, followed by the
-// Gauss-Newton model cost L(dx) = ||r + J_p dx_p + J_l dx_l||^2 (undamped)
-// evaluated per observation from the camera model and summed in FP64.
+// from the three top rows of each landmark block (one warp per landmark),
+// followed by the Gauss-Newton model cost L(dx) = ||r + J_p dx_p + J_l dx_l||^2
+// (undamped) evaluated per observation (one thread each) from the camera
+// model and summed in FP64.
 //
 // K7 (same file): candidate state x (+) dx (rotation Exp(dw) R, everything
 // else additive) and the energy E = sum ||r||^2 (Eq. ba_energy) with FP32
@@ -17,31 +18,30 @@ namespace sqrtba {
 
 namespace {
 
-constexpr int BS_WARPS = 4;
+constexpr int BS_WARPS = 8;
 
+// dl_j for one landmark per warp: lanes over the 9k pose columns of the
+// three top rows (coalesced), then the 3x3 triangular solve
 __global__ void __launch_bounds__(32 * BS_WARPS)
-k_backsub(int n_pt, const int32_t* __restrict__ pt_off, const int32_t* __restrict__ obs_cam_s,
-          const float2* __restrict__ obs_xy_s, const float* __restrict__ tpool,
-          const float* __restrict__ cams, const float* __restrict__ pts, const float* __restrict__ dp,
-          float* __restrict__ dl, double* __restrict__ partials, double* __restrict__ lm_model) {
-    __shared__ double wsum[BS_WARPS];
+k_backsub_dl(int n_pt, const int32_t* __restrict__ pt_off, const int32_t* __restrict__ obs_cam_s,
+             const float* __restrict__ tpool, const float* __restrict__ dp, float* __restrict__ dl) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int j = blockIdx.x * BS_WARPS + w;
-    double msum = 0.0;
-    if (j < n_pt) {
-        const int s0 = pt_off[j], k = pt_off[j + 1] - s0, ncol = 9 * k;
-        const float* top = tpool + top_offset(s0, j);
-        float t0 = 0.f, t1 = 0.f, t2 = 0.f;
-        for (int col = lane; col < ncol; col += 32) {
-            const int s = col / 9;
-            const float d = dp[9 * obs_cam_s[s0 + s] + (col - 9 * s)];
-            t0 += top[col] * d;
-            t1 += top[(ncol + 4) + col] * d;
-            t2 += top[2 * (ncol + 4) + col] * d;
-        }
-        t0 = warp_sum(t0);
-        t1 = warp_sum(t1);
-        t2 = warp_sum(t2);
+    if (j >= n_pt) return;
+    const int s0 = pt_off[j], k = pt_off[j + 1] - s0, ncol = 9 * k;
+    const float* top = tpool + top_offset(s0, j);
+    float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+    for (int col = lane; col < ncol; col += 32) {
+        const int s = col / 9;
+        const float d = __ldg(dp + 9 * obs_cam_s[s0 + s] + (col - 9 * s));
+        t0 += top[col] * d;
+        t1 += top[(ncol + 4) + col] * d;
+        t2 += top[2 * (ncol + 4) + col] * d;
+    }
+    t0 = warp_sum(t0);
+    t1 = warp_sum(t1);
+    t2 = warp_sum(t2);
+    if (lane == 0) {
         const float* R0 = top + ncol;
         const float* R1 = top + (ncol + 4) + ncol;
         const float* R2 = top + 2 * (ncol + 4) + ncol;
@@ -51,35 +51,78 @@ k_backsub(int n_pt, const int32_t* __restrict__ pt_off, const int32_t* __restric
         const float l2 = -t2 / R2[2];
         const float l1 = (-t1 - R1[2] * l2) / R1[1];
         const float l0 = (-t0 - R0[1] * l1 - R0[2] * l2) / R0[0];
-        if (lane == 0) {
-            dl[3 * j] = l0;
-            dl[3 * j + 1] = l1;
-            dl[3 * j + 2] = l2;
-        }
-        const float X0 = pts[3 * j], X1 = pts[3 * j + 1], X2 = pts[3 * j + 2];
-        for (int s = lane; s < k; s += 32) {
-            const int cam = obs_cam_s[s0 + s];
-            const float2 z = obs_xy_s[s0 + s];
-            float r[2], Jp[18], Jl[6];
-            project_jacobians(cams + 9 * cam, X0, X1, X2, z.x, z.y, r, Jp, Jl);
-            const float* d = dp + 9 * cam;
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                float e = r[i] + Jl[3 * i] * l0 + Jl[3 * i + 1] * l1 + Jl[3 * i + 2] * l2;
-#pragma unroll
-                for (int c = 0; c < 9; ++c) e += Jp[9 * i + c] * d[c];
-                msum += (double)e * (double)e;
-            }
-        }
-        msum = warp_sum_d(msum);
-        if (lm_model && lane == 0) lm_model[j] = msum;
+        dl[3 * j] = l0;
+        dl[3 * j + 1] = l1;
+        dl[3 * j + 2] = l2;
     }
-    if (lane == 0) wsum[w] = msum;
-    __syncthreads();
+}
+
+// One observation: the Gauss-Newton model term ||r + J_p dp + J_l dl||^2 at
+// the current state and, optionally, the energy term ||r||^2 at the candidate.
+__device__ __forceinline__ void model_cost_obs(int64_t s, const float* __restrict__ cams, const float* __restrict__ pts,
+                                               const int32_t* __restrict__ obs_cam_s,
+                                               const int32_t* __restrict__ obs_pt_s,
+                                               const float2* __restrict__ obs_xy_s, const float* __restrict__ dp,
+                                               const float* __restrict__ dl, const float* __restrict__ cand_cams,
+                                               const float* __restrict__ cand_pts, double& m, double& c) {
+    const int j = obs_pt_s[s], cam = obs_cam_s[s];
+    const float2 z = obs_xy_s[s];
+    float r[2], Jp[18], Jl[6];
+    project_jacobians(cams + 9 * cam, pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], z.x, z.y, r, Jp, Jl);
+    const float* d = dp + 9 * cam;
+    const float l0 = dl[3 * j], l1 = dl[3 * j + 1], l2 = dl[3 * j + 2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        float e = r[i] + Jl[3 * i] * l0 + Jl[3 * i + 1] * l1 + Jl[3 * i + 2] * l2;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) e += Jp[9 * i + q] * d[q];
+        m += (double)e * (double)e;
+    }
+    if (cand_cams) {
+        float r0, r1;
+        project_residual(cand_cams + 9 * cam, cand_pts[3 * j], cand_pts[3 * j + 1], cand_pts[3 * j + 2], z.x, z.y, r0,
+                         r1);
+        c += (double)r0 * (double)r0 + (double)r1 * (double)r1;
+    }
+}
+
+// K6 model cost (and with the candidate state, K7's energy) per observation,
+// FP64 partial sums per CTA
+__global__ void __launch_bounds__(256)
+k_model_cost(int64_t n_obs, const float* __restrict__ cams, const float* __restrict__ pts,
+             const int32_t* __restrict__ obs_cam_s, const int32_t* __restrict__ obs_pt_s,
+             const float2* __restrict__ obs_xy_s, const float* __restrict__ dp, const float* __restrict__ dl,
+             const float* __restrict__ cand_cams, const float* __restrict__ cand_pts, double* __restrict__ part_m,
+             double* __restrict__ part_c) {
+    __shared__ double red[32];
+    double m = 0.0, c = 0.0;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_obs; s += (int64_t)gridDim.x * blockDim.x)
+        model_cost_obs(s, cams, pts, obs_cam_s, obs_pt_s, obs_xy_s, dp, dl, cand_cams, cand_pts, m, c);
+    m = block_sum_d(m, red);
+    if (cand_cams) c = block_sum_d(c, red);
     if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int m = 0; m < BS_WARPS; ++m) s += wsum[m];
-        partials[blockIdx.x] = s;
+        part_m[blockIdx.x] = m;
+        if (cand_cams) part_c[blockIdx.x] = c;
+    }
+}
+
+// batch: the same per problem (one CTA per problem, its observation range)
+__global__ void __launch_bounds__(256)
+k_model_cost_seg(const int64_t* __restrict__ prob_obs_off, const float* __restrict__ cams,
+                 const float* __restrict__ pts, const int32_t* __restrict__ obs_cam_s,
+                 const int32_t* __restrict__ obs_pt_s, const float2* __restrict__ obs_xy_s,
+                 const float* __restrict__ dp, const float* __restrict__ dl, const float* __restrict__ cand_cams,
+                 const float* __restrict__ cand_pts, double* __restrict__ model, double* __restrict__ cost) {
+    __shared__ double red[32];
+    const int b = blockIdx.x;
+    double m = 0.0, c = 0.0;
+    for (int64_t s = prob_obs_off[b] + threadIdx.x; s < prob_obs_off[b + 1]; s += blockDim.x)
+        model_cost_obs(s, cams, pts, obs_cam_s, obs_pt_s, obs_xy_s, dp, dl, cand_cams, cand_pts, m, c);
+    m = block_sum_d(m, red);
+    c = block_sum_d(c, red);
+    if (threadIdx.x == 0) {
+        model[b] = m;
+        cost[b] = c;
     }
 }
 
@@ -110,6 +153,22 @@ k_sum_partials(const double* __restrict__ partials, int n, double* out) {
     if (threadIdx.x == 0) *out = acc;
 }
 
+__global__ void __launch_bounds__(1024)
+k_sum_partials2(const double* __restrict__ a, const double* __restrict__ b, int n, double* out_a, double* out_b) {
+    __shared__ double red[32];
+    double sa = 0.0, sb = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        sa += a[i];
+        sb += b[i];
+    }
+    sa = block_sum_d(sa, red);
+    sb = block_sum_d(sb, red);
+    if (threadIdx.x == 0) {
+        *out_a = sa;
+        *out_b = sb;
+    }
+}
+
 __global__ void k_candidate(int n_cam, const float* __restrict__ cams, const float* __restrict__ dp,
                             float* __restrict__ cand_cams, int n_pt, const float* __restrict__ pts,
                             const float* __restrict__ dl, float* __restrict__ cand_pts) {
@@ -131,12 +190,37 @@ __global__ void k_candidate(int n_cam, const float* __restrict__ cams, const flo
 
 }  // namespace
 
+// K6: dl per landmark, then the model cost L(dx) per observation (FP64)
 void launch_backsub(Problem& p) {
-    count_launches(p, 2);
-    const int nb = ceil_div(p.n_pt, BS_WARPS);
-    k_backsub<<<nb, 32 * BS_WARPS, 0, p.stream>>>(p.n_pt, p.pt_off, p.obs_cam_s, p.obs_xy_s, p.tpool, p.cams,
-                                                  p.pts, p.x, p.dl, p.partials, p.batch.lm_model);
-    k_sum_partials<<<1, 1024, 0, p.stream>>>(p.partials, nb, p.dsum + 1);
+    count_launches(p, 3);
+    k_backsub_dl<<<ceil_div(p.n_pt, BS_WARPS), 32 * BS_WARPS, 0, p.stream>>>(p.n_pt, p.pt_off, p.obs_cam_s, p.tpool,
+                                                                             p.x, p.dl);
+    k_model_cost<<<p.red_grid, 256, 0, p.stream>>>(p.n_obs, p.cams, p.pts, p.obs_cam_s, p.obs_pt_s, p.obs_xy_s, p.x,
+                                                   p.dl, nullptr, nullptr, p.partials, nullptr);
+    k_sum_partials<<<1, 1024, 0, p.stream>>>(p.partials, p.red_grid, p.dsum + 1);
+    BA_LAUNCH_CHECK();
+}
+
+// K6 + K7 of one LM iteration fused: dl, the candidate state, then one pass
+// over the observations for the model cost (dsum[1]) and the candidate's
+// energy (dsum[0]); a batch gets both per problem (cost_a, cost_b)
+void launch_backsub_candidate_cost(Problem& p) {
+    count_launches(p, p.batch.n_prob > 0 ? 2 : 3);
+    k_backsub_dl<<<ceil_div(p.n_pt, BS_WARPS), 32 * BS_WARPS, 0, p.stream>>>(p.n_pt, p.pt_off, p.obs_cam_s, p.tpool,
+                                                                             p.x, p.dl);
+    launch_candidate(p);
+    if (p.batch.n_prob > 0) {
+        BatchState& B = p.batch;
+        k_model_cost_seg<<<B.n_prob, 256, 0, p.stream>>>(B.prob_obs_off, p.cams, p.pts, p.obs_cam_s, p.obs_pt_s,
+                                                         p.obs_xy_s, p.x, p.dl, p.cand_cams, p.cand_pts, B.cost_b,
+                                                         B.cost_a);
+    } else {
+        k_model_cost<<<p.red_grid, 256, 0, p.stream>>>(p.n_obs, p.cams, p.pts, p.obs_cam_s, p.obs_pt_s, p.obs_xy_s,
+                                                       p.x, p.dl, p.cand_cams, p.cand_pts, p.partials,
+                                                       p.partials + p.red_grid);
+        k_sum_partials2<<<1, 1024, 0, p.stream>>>(p.partials, p.partials + p.red_grid, p.red_grid, p.dsum + 1,
+                                                  p.dsum + 0);
+    }
     BA_LAUNCH_CHECK();
 }
 

@@ -40,17 +40,6 @@ k_cost_seg(const int64_t* __restrict__ prob_obs_off, const float* __restrict__ c
     if (threadIdx.x == 0) out[b] = acc;
 }
 
-// out_b = sum of v over the landmarks of problem b (FP64)
-__global__ void __launch_bounds__(SEG_T)
-k_seg_sum(const int32_t* __restrict__ off, const double* __restrict__ v, double* __restrict__ out) {
-    __shared__ double red[32];
-    const int b = blockIdx.x;
-    double acc = 0.0;
-    for (int i = off[b] + threadIdx.x; i < off[b + 1]; i += SEG_T) acc += v[i];
-    acc = block_sum_d(acc, red);
-    if (threadIdx.x == 0) out[b] = acc;
-}
-
 __global__ void k_batch_start(int n_prob, BatchLm* __restrict__ lm, const double* __restrict__ cost,
                               float* __restrict__ lam, double lambda0) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -139,13 +128,6 @@ void launch_batch_cost(Problem& p, bool candidate, double* out) {
     k_cost_seg<<<B.n_prob, SEG_T, 0, p.stream>>>(B.prob_obs_off, candidate ? p.cand_cams : p.cams,
                                                  candidate ? p.cand_pts : p.pts, p.obs_cam_s, p.obs_pt_s,
                                                  p.obs_xy_s, out);
-    BA_LAUNCH_CHECK();
-}
-
-void launch_batch_model(Problem& p) {
-    BatchState& B = p.batch;
-    count_launches(p, 1);
-    k_seg_sum<<<B.n_prob, SEG_T, 0, p.stream>>>(B.prob_lm_off, B.lm_model, B.cost_b);
     BA_LAUNCH_CHECK();
 }
 

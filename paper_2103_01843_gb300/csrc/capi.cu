@@ -475,12 +475,8 @@ void do_lm_step(Problem& p, ba_lm_report* rep) {
     p.solved = true;
     {
         PhaseTimer tb(p, PROF_BACKSUB);
-        launch_backsub(p);
+        launch_backsub_candidate_cost(p);
         tb.end();
-        PhaseTimer tc(p, PROF_COST);
-        launch_candidate(p);
-        launch_cost(p, true);
-        tc.end();
     }
     d2h(p, p.dsum_host, p.dsum, 2);
     sync(p);
@@ -627,7 +623,7 @@ void create_problem(Problem& p, const double* cams, int32_t n_cam, const double*
     p.mdiag = dalloc<float>(p, 81 * (int64_t)n_cam);
     p.prec = dalloc<float>(p, 56 * n_obs);
     p.dl = dalloc<float>(p, 3 * (int64_t)n_pt);
-    p.partials = dalloc<double>(p, std::max<int64_t>((n_pt + 3) / 4 + 1, p.red_grid + 1));
+    p.partials = dalloc<double>(p, 2LL * p.red_grid + 2);
     BA_CUDA_TRY(cudaMemsetAsync(p.x, 0, sizeof(float) * nv, p.stream));
     BA_CUDA_TRY(cudaMemsetAsync(p.dl, 0, sizeof(float) * 3 * n_pt, p.stream));
     configure_linearize(p);
@@ -727,7 +723,6 @@ void create_batch(ba_batch* bh, const ba_problem_desc* descs, int32_t n, const b
     B.pcg = dalloc<PcgScalars>(p, n);
     B.n_done = dalloc<int32_t>(p, 1);
     B.lm = dalloc<BatchLm>(p, n);
-    B.lm_model = dalloc<double>(p, tp);
     B.cost_a = dalloc<double>(p, n);
     B.cost_b = dalloc<double>(p, n);
     B.n_active = dalloc<int32_t>(p, 1);
@@ -779,13 +774,8 @@ void do_batch_solve(Problem& p, ba_batch_report* reps, ba_batch_summary* sum) {
         }
         do_pcg(p, nullptr);
         PhaseTimer tb(p, PROF_BACKSUB);
-        launch_backsub(p);
-        launch_batch_model(p);
+        launch_backsub_candidate_cost(p);
         tb.end();
-        PhaseTimer tc(p, PROF_COST);
-        launch_candidate(p);
-        launch_batch_cost(p, true, B.cost_a);
-        tc.end();
         launch_batch_decide(p, it);
         launch_batch_commit(p);
         BA_CUDA_TRY(cudaEventRecord(B.iter_events[it + 1], p.stream));

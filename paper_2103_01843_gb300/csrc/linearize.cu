@@ -105,7 +105,11 @@ struct LinArgs {
 
 // Linearise and marginalise landmark j; sm holds lin_smem_floats(k) floats.
 // write = false runs the same steps without storing (an idle team of a warp).
-template <int TEAM>
+// MC: columns per lane for TEAM <= 32 (ceil(9 k_max / TEAM)); the team's
+// lanes own the pose columns col = rank + TEAM m, keep their W = Tm^T V^T J_p
+// entries in registers and write Q^T J_p row by row (coalesced), three FMAs
+// per element.  The CTA-wide team (k > 32) goes through shared memory.
+template <int TEAM, int MC = 1>
 __device__ void marginalize_landmark(const LinArgs& A, int j, float* sm, float* red, bool write = true) {
     using T = Team<TEAM>;
     const int rank = T::rank();
@@ -228,52 +232,86 @@ __device__ void marginalize_landmark(const LinArgs& A, int j, float* sm, float* 
         T::sync();
     }
 
-    // 4. W = Tm^T (V^T J_p) for the pose columns (two non-zero rows each)
-    {
-        const float* Tm = misc + 5;
-        const float T00 = Tm[0], T01 = Tm[1], T02 = Tm[2], T11 = Tm[4], T12 = Tm[5], T22 = Tm[8];
-        for (int col = rank; col < ncol; col += TEAM) {
-            const int s = col / 9, c = col - 9 * s;
-            const float ja = JP[(2 * s) * 9 + c], jb = JP[(2 * s + 1) * 9 + c];
-            const float m0 = V[3 * (2 * s)] * ja + V[3 * (2 * s + 1)] * jb;
-            const float m1 = V[3 * (2 * s) + 1] * ja + V[3 * (2 * s + 1) + 1] * jb;
-            const float m2 = V[3 * (2 * s) + 2] * ja + V[3 * (2 * s + 1) + 2] * jb;
-            W[col] = T00 * m0;
-            W[(ncol + 1) + col] = T01 * m0 + T11 * m1;
-            W[2 * (ncol + 1) + col] = T02 * m0 + T12 * m1 + T22 * m2;
-        }
-        if (rank == 0) {
-            W[ncol] = misc[14];
-            W[(ncol + 1) + ncol] = misc[15];
-            W[2 * (ncol + 1) + ncol] = misc[16];
-        }
-        T::sync();
-    }
-
-    // 5. write Q^T [J_p | r]: rows 0..2 to the top block, rows 3.. to A_j / c_j
     const int64_t toff = top_offset(s0, j);
     float* __restrict__ top = A.tpool + toff;
     float* __restrict__ Aj = A.apool + A.a_off[j];
-    const int64_t total = (int64_t)nr * ncol;
-    int e = rank;
-    int i = e / ncol, col = e - i * ncol;
-    for (; write && e < total; e += TEAM) {
-        const int s = col / 9;
-        const float mval = (s == (i >> 1)) ? JP[i * 9 + (col - 9 * s)] : 0.f;
-        const float out = mval - (V[3 * i] * W[col] + V[3 * i + 1] * W[(ncol + 1) + col] +
-                                  V[3 * i + 2] * W[2 * (ncol + 1) + col]);
-        if (i < 3) top[i * (ncol + 4) + col] = out;
-        else if (i < nr) Aj[e - 3 * ncol] = out;
-        col += TEAM;
-        while (col >= ncol) {
-            col -= ncol;
-            ++i;
+    if constexpr (TEAM <= 32) {
+        // 4+5. W for this lane's columns (registers), then Q^T J_p row by row:
+        // out[i][col] = J_p[i][col] - (V[i][0] W0 + V[i][1] W1 + V[i][2] W2);
+        // J_p[i][col] is non-zero only in the 9 columns of row i's observation
+        const float* Tm = misc + 5;
+        const float T00 = Tm[0], T01 = Tm[1], T02 = Tm[2], T11 = Tm[4], T12 = Tm[5], T22 = Tm[8];
+        float w0[MC], w1[MC], w2[MC];
+        int cs[MC];
+#pragma unroll
+        for (int m = 0; m < MC; ++m) {
+            const int col = rank + TEAM * m;
+            const bool ok = col < ncol;
+            const int sb = ok ? col / 9 : 0, c = ok ? col - 9 * sb : 0;
+            const float ja = ok ? JP[(2 * sb) * 9 + c] : 0.f, jb = ok ? JP[(2 * sb + 1) * 9 + c] : 0.f;
+            const float m0 = V[3 * (2 * sb)] * ja + V[3 * (2 * sb + 1)] * jb;
+            const float m1 = V[3 * (2 * sb) + 1] * ja + V[3 * (2 * sb + 1) + 1] * jb;
+            const float m2 = V[3 * (2 * sb) + 2] * ja + V[3 * (2 * sb + 1) + 2] * jb;
+            w0[m] = T00 * m0;
+            w1[m] = T01 * m0 + T11 * m1;
+            w2[m] = T02 * m0 + T12 * m1 + T22 * m2;
+            cs[m] = ok ? sb : -1;
+        }
+        for (int i = 0; write && i < nr; ++i) {
+            const float v0 = V[3 * i], v1 = V[3 * i + 1], v2 = V[3 * i + 2];
+            const int si = i >> 1;
+            float* __restrict__ dst = i < 3 ? top + i * (ncol + 4) : Aj + (int64_t)(i - 3) * ncol;
+            const float* jrow = JP + i * 9 - 9 * si;
+#pragma unroll
+            for (int m = 0; m < MC; ++m) {
+                const int col = rank + TEAM * m;
+                if (cs[m] >= 0) {
+                    float out = -(v0 * w0[m] + v1 * w1[m] + v2 * w2[m]);
+                    if (cs[m] == si) out += jrow[col];
+                    dst[col] = out;
+                }
+            }
+        }
+    } else {
+        // 4. W = Tm^T (V^T J_p) for the pose columns (two non-zero rows each)
+        {
+            const float* Tm = misc + 5;
+            const float T00 = Tm[0], T01 = Tm[1], T02 = Tm[2], T11 = Tm[4], T12 = Tm[5], T22 = Tm[8];
+            for (int col = rank; col < ncol; col += TEAM) {
+                const int s = col / 9, c = col - 9 * s;
+                const float ja = JP[(2 * s) * 9 + c], jb = JP[(2 * s + 1) * 9 + c];
+                const float m0 = V[3 * (2 * s)] * ja + V[3 * (2 * s + 1)] * jb;
+                const float m1 = V[3 * (2 * s) + 1] * ja + V[3 * (2 * s + 1) + 1] * jb;
+                const float m2 = V[3 * (2 * s) + 2] * ja + V[3 * (2 * s + 1) + 2] * jb;
+                W[col] = T00 * m0;
+                W[(ncol + 1) + col] = T01 * m0 + T11 * m1;
+                W[2 * (ncol + 1) + col] = T02 * m0 + T12 * m1 + T22 * m2;
+            }
+            T::sync();
+        }
+        // 5. write Q^T J_p: rows 0..2 to the top block, rows 3.. to A_j
+        const int64_t total = (int64_t)nr * ncol;
+        int e = rank;
+        int i = e / ncol, col = e - i * ncol;
+        for (; write && e < total; e += TEAM) {
+            const int s = col / 9;
+            const float mval = (s == (i >> 1)) ? JP[i * 9 + (col - 9 * s)] : 0.f;
+            const float out = mval - (V[3 * i] * W[col] + V[3 * i + 1] * W[(ncol + 1) + col] +
+                                      V[3 * i + 2] * W[2 * (ncol + 1) + col]);
+            if (i < 3) top[i * (ncol + 4) + col] = out;
+            else if (i < nr) Aj[e - 3 * ncol] = out;
+            col += TEAM;
+            while (col >= ncol) {
+                col -= ncol;
+                ++i;
+            }
         }
     }
+    // the residual column's W (misc[14..16], computed above)
+    const float wr0 = misc[14], wr1 = misc[15], wr2 = misc[16];
     // residual column and R1
     for (int ii = rank; write && ii < nr; ii += TEAM) {
-        const float out = RV[ii] - (V[3 * ii] * W[ncol] + V[3 * ii + 1] * W[(ncol + 1) + ncol] +
-                                    V[3 * ii + 2] * W[2 * (ncol + 1) + ncol]);
+        const float out = RV[ii] - (V[3 * ii] * wr0 + V[3 * ii + 1] * wr1 + V[3 * ii + 2] * wr2);
         if (ii < 3) {
             float* row = top + ii * (ncol + 4) + ncol;
             row[0] = ii <= 0 ? L[3 * ii] : 0.f;
@@ -298,7 +336,7 @@ k_linearize_team(LinArgs A, const int32_t* __restrict__ order, int first, int co
     const int idx = idx0 + tm;
     const bool active = idx < count;
     float* sm = smem + (w * TPW + tm) * lin_smem_floats(KMAX);
-    marginalize_landmark<W>(A, order[first + (active ? idx : idx0)], sm, nullptr, active);
+    marginalize_landmark<W, (9 * KMAX + W - 1) / W>(A, order[first + (active ? idx : idx0)], sm, nullptr, active);
 }
 
 __global__ void __launch_bounds__(BIG_TEAM)

@@ -75,7 +75,6 @@ struct BatchState {
     PcgScalars* pcg = nullptr;           // [n_prob] per-problem CG scalars
     int32_t* n_done = nullptr;           // problems whose CG has stopped
     BatchLm* lm = nullptr;               // [n_prob]
-    double* lm_model = nullptr;          // [n_pt] per-landmark model cost terms
     double *cost_a = nullptr, *cost_b = nullptr;  // [n_prob] segmented sums
     int32_t* n_active = nullptr;         // problems still iterating
     int32_t* n_active_host = nullptr;    // pinned mirror
@@ -225,9 +224,9 @@ void launch_precond_records(Problem& p);
 int matvec_ctas_per_sm();
 // K6: back substitution + model cost (backsub.cu)
 void launch_backsub(Problem& p);
+void launch_backsub_candidate_cost(Problem& p);
 // batch: segmented FP64 sums, LM decision and commit (batch.cu)
 void launch_batch_cost(Problem& p, bool candidate, double* out);
-void launch_batch_model(Problem& p);
 void launch_batch_start(Problem& p);
 void launch_batch_decide(Problem& p, int iteration);
 void launch_batch_commit(Problem& p);
