@@ -59,16 +59,16 @@ k_backsub_dl(int n_pt, const int32_t* __restrict__ pt_off, const int32_t* __rest
 
 // One observation: the Gauss-Newton model term ||r + J_p dp + J_l dl||^2 at
 // the current state and, optionally, the energy term ||r||^2 at the candidate.
-__device__ __forceinline__ void model_cost_obs(int64_t s, const float* __restrict__ cams, const float* __restrict__ pts,
+__device__ __forceinline__ void model_cost_obs(int64_t s, const float* __restrict__ frames, const float* __restrict__ pts,
                                                const int32_t* __restrict__ obs_cam_s,
                                                const int32_t* __restrict__ obs_pt_s,
                                                const float2* __restrict__ obs_xy_s, const float* __restrict__ dp,
-                                               const float* __restrict__ dl, const float* __restrict__ cand_cams,
+                                               const float* __restrict__ dl, const float* __restrict__ cand_frames,
                                                const float* __restrict__ cand_pts, double& m, double& c) {
     const int j = obs_pt_s[s], cam = obs_cam_s[s];
     const float2 z = obs_xy_s[s];
     float r[2], Jp[18], Jl[6];
-    project_jacobians(cams + 9 * cam, pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], z.x, z.y, r, Jp, Jl);
+    frame_jacobians(frames + FRAME * cam, pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], z.x, z.y, r, Jp, Jl);
     const float* d = dp + 9 * cam;
     const float l0 = dl[3 * j], l1 = dl[3 * j + 1], l2 = dl[3 * j + 2];
 #pragma unroll
@@ -78,10 +78,10 @@ __device__ __forceinline__ void model_cost_obs(int64_t s, const float* __restric
         for (int q = 0; q < 9; ++q) e += Jp[9 * i + q] * d[q];
         m += (double)e * (double)e;
     }
-    if (cand_cams) {
+    if (cand_frames) {
         float r0, r1;
-        project_residual(cand_cams + 9 * cam, cand_pts[3 * j], cand_pts[3 * j + 1], cand_pts[3 * j + 2], z.x, z.y, r0,
-                         r1);
+        frame_residual(cand_frames + FRAME * cam, cand_pts[3 * j], cand_pts[3 * j + 1], cand_pts[3 * j + 2], z.x, z.y,
+                       r0, r1);
         c += (double)r0 * (double)r0 + (double)r1 * (double)r1;
     }
 }
@@ -89,35 +89,35 @@ __device__ __forceinline__ void model_cost_obs(int64_t s, const float* __restric
 // K6 model cost (and with the candidate state, K7's energy) per observation,
 // FP64 partial sums per CTA
 __global__ void __launch_bounds__(256)
-k_model_cost(int64_t n_obs, const float* __restrict__ cams, const float* __restrict__ pts,
+k_model_cost(int64_t n_obs, const float* __restrict__ frames, const float* __restrict__ pts,
              const int32_t* __restrict__ obs_cam_s, const int32_t* __restrict__ obs_pt_s,
              const float2* __restrict__ obs_xy_s, const float* __restrict__ dp, const float* __restrict__ dl,
-             const float* __restrict__ cand_cams, const float* __restrict__ cand_pts, double* __restrict__ part_m,
+             const float* __restrict__ cand_frames, const float* __restrict__ cand_pts, double* __restrict__ part_m,
              double* __restrict__ part_c) {
     __shared__ double red[32];
     double m = 0.0, c = 0.0;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_obs; s += (int64_t)gridDim.x * blockDim.x)
-        model_cost_obs(s, cams, pts, obs_cam_s, obs_pt_s, obs_xy_s, dp, dl, cand_cams, cand_pts, m, c);
+        model_cost_obs(s, frames, pts, obs_cam_s, obs_pt_s, obs_xy_s, dp, dl, cand_frames, cand_pts, m, c);
     m = block_sum_d(m, red);
-    if (cand_cams) c = block_sum_d(c, red);
+    if (cand_frames) c = block_sum_d(c, red);
     if (threadIdx.x == 0) {
         part_m[blockIdx.x] = m;
-        if (cand_cams) part_c[blockIdx.x] = c;
+        if (cand_frames) part_c[blockIdx.x] = c;
     }
 }
 
 // batch: the same per problem (one CTA per problem, its observation range)
 __global__ void __launch_bounds__(256)
-k_model_cost_seg(const int64_t* __restrict__ prob_obs_off, const float* __restrict__ cams,
+k_model_cost_seg(const int64_t* __restrict__ prob_obs_off, const float* __restrict__ frames,
                  const float* __restrict__ pts, const int32_t* __restrict__ obs_cam_s,
                  const int32_t* __restrict__ obs_pt_s, const float2* __restrict__ obs_xy_s,
-                 const float* __restrict__ dp, const float* __restrict__ dl, const float* __restrict__ cand_cams,
+                 const float* __restrict__ dp, const float* __restrict__ dl, const float* __restrict__ cand_frames,
                  const float* __restrict__ cand_pts, double* __restrict__ model, double* __restrict__ cost) {
     __shared__ double red[32];
     const int b = blockIdx.x;
     double m = 0.0, c = 0.0;
     for (int64_t s = prob_obs_off[b] + threadIdx.x; s < prob_obs_off[b + 1]; s += blockDim.x)
-        model_cost_obs(s, cams, pts, obs_cam_s, obs_pt_s, obs_xy_s, dp, dl, cand_cams, cand_pts, m, c);
+        model_cost_obs(s, frames, pts, obs_cam_s, obs_pt_s, obs_xy_s, dp, dl, cand_frames, cand_pts, m, c);
     m = block_sum_d(m, red);
     c = block_sum_d(c, red);
     if (threadIdx.x == 0) {
@@ -127,7 +127,7 @@ k_model_cost_seg(const int64_t* __restrict__ prob_obs_off, const float* __restri
 }
 
 __global__ void __launch_bounds__(256)
-k_cost(int64_t n_obs, const float* __restrict__ cams, const float* __restrict__ pts,
+k_cost(int64_t n_obs, const float* __restrict__ frames, const float* __restrict__ pts,
        const int32_t* __restrict__ obs_cam_s, const int32_t* __restrict__ obs_pt_s,
        const float2* __restrict__ obs_xy_s, double* __restrict__ partials) {
     __shared__ double red[32];
@@ -137,7 +137,7 @@ k_cost(int64_t n_obs, const float* __restrict__ cams, const float* __restrict__ 
         const int j = obs_pt_s[s];
         const float2 z = obs_xy_s[s];
         float r0, r1;
-        project_residual(cams + 9 * obs_cam_s[s], pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], z.x, z.y, r0, r1);
+        frame_residual(frames + FRAME * obs_cam_s[s], pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], z.x, z.y, r0, r1);
         acc += (double)r0 * (double)r0 + (double)r1 * (double)r1;
     }
     acc = block_sum_d(acc, red);
@@ -170,8 +170,8 @@ k_sum_partials2(const double* __restrict__ a, const double* __restrict__ b, int 
 }
 
 __global__ void k_candidate(int n_cam, const float* __restrict__ cams, const float* __restrict__ dp,
-                            float* __restrict__ cand_cams, int n_pt, const float* __restrict__ pts,
-                            const float* __restrict__ dl, float* __restrict__ cand_pts) {
+                            float* __restrict__ cand_cams, float* __restrict__ cand_frames, int n_pt,
+                            const float* __restrict__ pts, const float* __restrict__ dl, float* __restrict__ cand_pts) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n_cam) {
         const float* c = cams + 9 * i;
@@ -184,6 +184,7 @@ __global__ void k_candidate(int n_cam, const float* __restrict__ cams, const flo
         o[2] = w[2];
 #pragma unroll
         for (int m = 3; m < 9; ++m) o[m] = c[m] + d[m];
+        make_frame(o, cand_frames + FRAME * i);
     }
     if (i < 3 * n_pt) cand_pts[i] = pts[i] + dl[i];
 }
@@ -195,7 +196,7 @@ void launch_backsub(Problem& p) {
     count_launches(p, 3);
     k_backsub_dl<<<ceil_div(p.n_pt, BS_WARPS), 32 * BS_WARPS, 0, p.stream>>>(p.n_pt, p.pt_off, p.obs_cam_s, p.tpool,
                                                                              p.x, p.dl);
-    k_model_cost<<<p.red_grid, 256, 0, p.stream>>>(p.n_obs, p.cams, p.pts, p.obs_cam_s, p.obs_pt_s, p.obs_xy_s, p.x,
+    k_model_cost<<<p.red_grid, 256, 0, p.stream>>>(p.n_obs, p.frames, p.pts, p.obs_cam_s, p.obs_pt_s, p.obs_xy_s, p.x,
                                                    p.dl, nullptr, nullptr, p.partials, nullptr);
     k_sum_partials<<<1, 1024, 0, p.stream>>>(p.partials, p.red_grid, p.dsum + 1);
     BA_LAUNCH_CHECK();
@@ -211,12 +212,12 @@ void launch_backsub_candidate_cost(Problem& p) {
     launch_candidate(p);
     if (p.batch.n_prob > 0) {
         BatchState& B = p.batch;
-        k_model_cost_seg<<<B.n_prob, 256, 0, p.stream>>>(B.prob_obs_off, p.cams, p.pts, p.obs_cam_s, p.obs_pt_s,
-                                                         p.obs_xy_s, p.x, p.dl, p.cand_cams, p.cand_pts, B.cost_b,
+        k_model_cost_seg<<<B.n_prob, 256, 0, p.stream>>>(B.prob_obs_off, p.frames, p.pts, p.obs_cam_s, p.obs_pt_s,
+                                                         p.obs_xy_s, p.x, p.dl, p.cand_frames, p.cand_pts, B.cost_b,
                                                          B.cost_a);
     } else {
-        k_model_cost<<<p.red_grid, 256, 0, p.stream>>>(p.n_obs, p.cams, p.pts, p.obs_cam_s, p.obs_pt_s, p.obs_xy_s,
-                                                       p.x, p.dl, p.cand_cams, p.cand_pts, p.partials,
+        k_model_cost<<<p.red_grid, 256, 0, p.stream>>>(p.n_obs, p.frames, p.pts, p.obs_cam_s, p.obs_pt_s, p.obs_xy_s,
+                                                       p.x, p.dl, p.cand_frames, p.cand_pts, p.partials,
                                                        p.partials + p.red_grid);
         k_sum_partials2<<<1, 1024, 0, p.stream>>>(p.partials, p.partials + p.red_grid, p.red_grid, p.dsum + 1,
                                                   p.dsum + 0);
@@ -227,14 +228,17 @@ void launch_backsub_candidate_cost(Problem& p) {
 void launch_candidate(Problem& p) {
     count_launches(p, 1);
     const int n = std::max(p.n_cam, 3 * p.n_pt);
-    k_candidate<<<ceil_div(n, 256), 256, 0, p.stream>>>(p.n_cam, p.cams, p.x, p.cand_cams, p.n_pt, p.pts, p.dl,
-                                                       p.cand_pts);
+    k_candidate<<<ceil_div(n, 256), 256, 0, p.stream>>>(p.n_cam, p.cams, p.x, p.cand_cams, p.cand_frames, p.n_pt,
+                                                       p.pts, p.dl, p.cand_pts);
     BA_LAUNCH_CHECK();
 }
 
+// E at the current state (its frames are recomputed first) or at the
+// candidate (frames written by k_candidate)
 void launch_cost(Problem& p, bool candidate) {
+    if (!candidate) launch_frames(p);
     count_launches(p, 2);
-    k_cost<<<p.red_grid, 256, 0, p.stream>>>(p.n_obs, candidate ? p.cand_cams : p.cams,
+    k_cost<<<p.red_grid, 256, 0, p.stream>>>(p.n_obs, candidate ? p.cand_frames : p.frames,
                                              candidate ? p.cand_pts : p.pts, p.obs_cam_s, p.obs_pt_s,
                                              p.obs_xy_s, p.partials);
     k_sum_partials<<<1, 1024, 0, p.stream>>>(p.partials, p.red_grid, p.dsum + 0);

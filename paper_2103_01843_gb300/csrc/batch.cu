@@ -23,7 +23,7 @@ constexpr int SEG_T = 256;
 
 // E_b = sum ||r||^2 over the sorted observations of problem b (FP64)
 __global__ void __launch_bounds__(SEG_T)
-k_cost_seg(const int64_t* __restrict__ prob_obs_off, const float* __restrict__ cams, const float* __restrict__ pts,
+k_cost_seg(const int64_t* __restrict__ prob_obs_off, const float* __restrict__ frames, const float* __restrict__ pts,
            const int32_t* __restrict__ obs_cam_s, const int32_t* __restrict__ obs_pt_s,
            const float2* __restrict__ obs_xy_s, double* __restrict__ out) {
     __shared__ double red[32];
@@ -33,7 +33,7 @@ k_cost_seg(const int64_t* __restrict__ prob_obs_off, const float* __restrict__ c
         const int j = obs_pt_s[s];
         const float2 z = obs_xy_s[s];
         float r0, r1;
-        project_residual(cams + 9 * obs_cam_s[s], pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], z.x, z.y, r0, r1);
+        frame_residual(frames + FRAME * obs_cam_s[s], pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], z.x, z.y, r0, r1);
         acc += (double)r0 * (double)r0 + (double)r1 * (double)r1;
     }
     acc = block_sum_d(acc, red);
@@ -125,7 +125,8 @@ __global__ void k_batch_commit(int n_cam, int n_pt, const int32_t* __restrict__ 
 void launch_batch_cost(Problem& p, bool candidate, double* out) {
     BatchState& B = p.batch;
     count_launches(p, 1);
-    k_cost_seg<<<B.n_prob, SEG_T, 0, p.stream>>>(B.prob_obs_off, candidate ? p.cand_cams : p.cams,
+    if (!candidate) launch_frames(p);
+    k_cost_seg<<<B.n_prob, SEG_T, 0, p.stream>>>(B.prob_obs_off, candidate ? p.cand_frames : p.frames,
                                                  candidate ? p.cand_pts : p.pts, p.obs_cam_s, p.obs_pt_s,
                                                  p.obs_xy_s, out);
     BA_LAUNCH_CHECK();

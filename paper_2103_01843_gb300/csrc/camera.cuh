@@ -110,6 +110,92 @@ __device__ __forceinline__ void project_jacobians(const float* __restrict__ cam,
     }
 }
 
+// Camera frames: the rotation matrix evaluated once per camera and state,
+// 16 floats per camera (R row-major, t, f, k1, k2, 0), 16-byte aligned, so
+// that the per-observation kernels skip the trigonometry of R(w).
+constexpr int FRAME = 16;
+
+__device__ __forceinline__ void make_frame(const float* __restrict__ cam, float* __restrict__ fr) {
+    float R[9];
+    rotation_matrix(cam[0], cam[1], cam[2], R);
+    float4* o = reinterpret_cast<float4*>(fr);
+    o[0] = make_float4(R[0], R[1], R[2], R[3]);
+    o[1] = make_float4(R[4], R[5], R[6], R[7]);
+    o[2] = make_float4(R[8], cam[3], cam[4], cam[5]);
+    o[3] = make_float4(cam[6], cam[7], cam[8], 0.f);
+}
+
+struct Frame {
+    float R[9], t[3], f, k1, k2;
+};
+
+__device__ __forceinline__ Frame load_frame(const float* __restrict__ fr) {
+    const float4* q = reinterpret_cast<const float4*>(fr);
+    const float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3);
+    return Frame{{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x}, {c.y, c.z, c.w}, d.x, d.y, d.z};
+}
+
+// Residual from a camera frame (same arithmetic as project_residual).
+__device__ __forceinline__ void frame_residual(const float* __restrict__ fr, float X0, float X1, float X2, float z0,
+                                               float z1, float& r0, float& r1) {
+    const Frame F = load_frame(fr);
+    const float P0 = F.R[0] * X0 + F.R[1] * X1 + F.R[2] * X2 + F.t[0];
+    const float P1 = F.R[3] * X0 + F.R[4] * X1 + F.R[5] * X2 + F.t[1];
+    const float P2 = F.R[6] * X0 + F.R[7] * X1 + F.R[8] * X2 + F.t[2];
+    const float iz = 1.0f / P2;
+    const float p0 = -P0 * iz, p1 = -P1 * iz;
+    const float r2 = p0 * p0 + p1 * p1;
+    const float fd = F.f * (1.0f + F.k1 * r2 + F.k2 * r2 * r2);
+    r0 = fd * p0 - z0;
+    r1 = fd * p1 - z1;
+}
+
+// Residual and Jacobians from a camera frame (same arithmetic as
+// project_jacobians).
+__device__ __forceinline__ void frame_jacobians(const float* __restrict__ fr, float X0, float X1, float X2, float z0,
+                                                float z1, float r[2], float Jp[18], float Jl[6]) {
+    const Frame F = load_frame(fr);
+    const float* R = F.R;
+    const float Y0 = R[0] * X0 + R[1] * X1 + R[2] * X2;
+    const float Y1 = R[3] * X0 + R[4] * X1 + R[5] * X2;
+    const float Y2 = R[6] * X0 + R[7] * X1 + R[8] * X2;
+    const float P0 = Y0 + F.t[0], P1 = Y1 + F.t[1], P2 = Y2 + F.t[2];
+    const float f = F.f, k1 = F.k1, k2 = F.k2;
+    const float iz = 1.0f / P2;
+    const float p0 = -P0 * iz, p1 = -P1 * iz;
+    const float r2 = p0 * p0 + p1 * p1;
+    const float d = 1.0f + k1 * r2 + k2 * r2 * r2;
+    r[0] = f * d * p0 - z0;
+    r[1] = f * d * p1 - z1;
+    const float g = 2.0f * (k1 + 2.0f * k2 * r2);
+    const float D00 = f * (d + g * p0 * p0), D01 = f * g * p0 * p1, D11 = f * (d + g * p1 * p1);
+    const float iz2 = iz * iz;
+    float A[6];
+    A[0] = -D00 * iz;
+    A[1] = -D01 * iz;
+    A[2] = (D00 * P0 + D01 * P1) * iz2;
+    A[3] = -D01 * iz;
+    A[4] = -D11 * iz;
+    A[5] = (D01 * P0 + D11 * P1) * iz2;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float a0 = A[3 * i], a1 = A[3 * i + 1], a2 = A[3 * i + 2];
+        Jp[9 * i + 0] = -a1 * Y2 + a2 * Y1;
+        Jp[9 * i + 1] = a0 * Y2 - a2 * Y0;
+        Jp[9 * i + 2] = -a0 * Y1 + a1 * Y0;
+        Jp[9 * i + 3] = a0;
+        Jp[9 * i + 4] = a1;
+        Jp[9 * i + 5] = a2;
+        const float pi = i == 0 ? p0 : p1;
+        Jp[9 * i + 6] = d * pi;
+        Jp[9 * i + 7] = f * r2 * pi;
+        Jp[9 * i + 8] = f * r2 * r2 * pi;
+        Jl[3 * i + 0] = a0 * R[0] + a1 * R[3] + a2 * R[6];
+        Jl[3 * i + 1] = a0 * R[1] + a1 * R[4] + a2 * R[7];
+        Jl[3 * i + 2] = a0 * R[2] + a1 * R[5] + a2 * R[8];
+    }
+}
+
 // w_out = Log(Exp(dw) Exp(w)) through unit quaternions (angle kept in [0, pi]).
 __device__ __forceinline__ void compose_rotation(const float dw[3], const float w[3], float out[3]) {
     float qa[4], qb[4];

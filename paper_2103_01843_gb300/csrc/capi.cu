@@ -12,6 +12,7 @@
 #include <utility>
 #include <vector>
 
+#include "camera.cuh"
 #include "learned.cuh"
 #include "problem.cuh"
 
@@ -143,6 +144,11 @@ void free_all(Problem& p) {
     if (p.dsum_host) cudaFreeHost(p.dsum_host);
     p.pcg_host = nullptr;
     p.dsum_host = nullptr;
+    if (p.side) cudaStreamDestroy(p.side);
+    if (p.ev_fork) cudaEventDestroy(p.ev_fork);
+    if (p.ev_join) cudaEventDestroy(p.ev_join);
+    p.side = nullptr;
+    p.ev_fork = p.ev_join = nullptr;
     if (p.own_stream && p.stream) cudaStreamDestroy(p.stream);
     p.stream = nullptr;
 }
@@ -152,6 +158,7 @@ void free_all(Problem& p) {
 // the host already knows it (the accepted candidate's cost).
 void do_linearize(Problem& p, bool need_cost = true) {
     PhaseTimer t(p, PROF_LINEARIZE);
+    launch_frames(p);
     launch_camera_diag(p);
     launch_linearize(p);
     t.end();
@@ -502,6 +509,7 @@ void do_lm_step(Problem& p, ba_lm_report* rep) {
     if (acc) {
         std::swap(p.cams, p.cand_cams);
         std::swap(p.pts, p.cand_pts);
+        std::swap(p.frames, p.cand_frames);
         p.cost = En;
         p.cost_valid = true;
         p.linearized = false;
@@ -550,6 +558,9 @@ void create_problem(Problem& p, const double* cams, int32_t n_cam, const double*
         BA_CUDA_TRY(cudaStreamCreateWithFlags(&p.stream, cudaStreamNonBlocking));
         p.own_stream = true;
     }
+    BA_CUDA_TRY(cudaStreamCreateWithFlags(&p.side, cudaStreamNonBlocking));
+    BA_CUDA_TRY(cudaEventCreateWithFlags(&p.ev_fork, cudaEventDisableTiming));
+    BA_CUDA_TRY(cudaEventCreateWithFlags(&p.ev_join, cudaEventDisableTiming));
     int dev = 0;
     BA_CUDA_TRY(cudaGetDevice(&dev));
     BA_CUDA_TRY(cudaDeviceGetAttribute(&p.sm_count, cudaDevAttrMultiProcessorCount, dev));
@@ -560,6 +571,8 @@ void create_problem(Problem& p, const double* cams, int32_t n_cam, const double*
     p.cand_cams = dalloc<float>(p, 9 * (int64_t)n_cam);
     p.pts = dalloc<float>(p, 3 * (int64_t)n_pt);
     p.cand_pts = dalloc<float>(p, 3 * (int64_t)n_pt);
+    p.frames = dalloc<float>(p, FRAME * (int64_t)n_cam);
+    p.cand_frames = dalloc<float>(p, FRAME * (int64_t)n_cam);
     p.obs_cam_s = dalloc<int32_t>(p, n_obs);
     p.obs_pt_s = dalloc<int32_t>(p, n_obs);
     p.perm = dalloc<int32_t>(p, n_obs);
@@ -755,6 +768,7 @@ void do_batch_solve(Problem& p, ba_batch_report* reps, ba_batch_summary* sum) {
         // K1 for every problem (a problem whose last step was rejected
         // recomputes the blocks of its unchanged state)
         PhaseTimer tl(p, PROF_LINEARIZE);
+        launch_frames(p);
         launch_camera_diag(p);
         launch_linearize(p);
         tl.end();

@@ -16,37 +16,35 @@
 //
 // Layout of the work: a CTA takes DB landmarks.  Phase 1, one landmark per
 // thread: undo/redo on the 3x3 landmark part and the new rotations.  Phase 2:
-// the CTA's (landmark, column) pairs, flattened through a prefix sum over the
-// landmarks' 9k + 1 columns, one pair per thread at a time, so that
-// consecutive threads touch consecutive columns of the six rows.
+// one warp per landmark, lanes over its 9k + 1 columns, so that consecutive
+// lanes touch consecutive columns of the six rows; 8 warps per CTA keep many
+// landmarks' loads in flight per SM (the kernel is latency-bound otherwise).
 #include "problem.cuh"
 
 namespace sqrtba {
 
 namespace {
 
-constexpr int DB = 128;  // landmarks (and threads) per CTA
+constexpr int DB = 64;   // landmarks per CTA (phase 1: one thread each)
+constexpr int DT = 256;  // threads per CTA (phase 2: 8 warps, DB / 8 landmarks each)
 
 __device__ __forceinline__ void rot_pair(int m, int& c, int& d) {
     c = m < 3 ? m : (m < 5 ? m - 2 : 2);
     d = m < 3 ? 0 : (m < 5 ? 1 : 2);
 }
 
-__global__ void __launch_bounds__(DB)
+__global__ void __launch_bounds__(DT)
 k_damp(int n_pt, const int32_t* __restrict__ pt_off, const int64_t* __restrict__ a_off,
        const int32_t* __restrict__ c_off, float* __restrict__ tpool, float* __restrict__ apool,
        float* __restrict__ cpool, const float* __restrict__ dl2, float* __restrict__ rot, float sqrt_lambda,
        const float* __restrict__ lam_prob, const int32_t* __restrict__ lm_prob, int undo) {
     __shared__ float s_rot[DB][24];  // old (12) and new (12) rotations
-    __shared__ int s_off[DB + 1];    // prefix of the column counts 9k + 1
     __shared__ int s_k[DB];
     __shared__ int64_t s_top[DB], s_damp[DB];
     __shared__ int s_cd[DB];
-    __shared__ int s_w[DB / 32];
     const int tid = threadIdx.x;
     const int j = blockIdx.x * DB + tid;
-    int ncols = 0;
-    if (j < n_pt) {
+    if (tid < DB && j < n_pt) {
         const int s0 = pt_off[j], k = pt_off[j + 1] - s0;
         const int ncol = 9 * k, nr = 2 * k;
         const int64_t toff = top_offset(s0, j);
@@ -55,7 +53,6 @@ k_damp(int n_pt, const int32_t* __restrict__ pt_off, const int64_t* __restrict__
         s_top[tid] = toff;
         s_damp[tid] = a_off[j] + (int64_t)(nr - 3) * ncol;
         s_cd[tid] = c_off[j] + (nr - 3);
-        ncols = ncol + 1;
         float R[3][3], D[3][3];
         for (int i = 0; i < 3; ++i)
             for (int c = 0; c < 3; ++c) {
@@ -108,66 +105,55 @@ k_damp(int n_pt, const int32_t* __restrict__ pt_off, const int64_t* __restrict__
             for (int c = 0; c < 3; ++c) top[i * (ncol + 4) + ncol + c] = c >= i ? R[i][c] : 0.f;
         for (int m = 0; m < 12; ++m) rot[12 * (int64_t)j + m] = rs[12 + m];
     }
-    // exclusive prefix of the column counts (block scan)
-    {
-        const int lane = tid & 31, w = tid >> 5;
-        int inc = ncols;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += t;
-        }
-        if (lane == 31) s_w[w] = inc;
-        __syncthreads();
-        int base = 0;
-        for (int q = 0; q < w; ++q) base += s_w[q];
-        s_off[tid] = base + inc - ncols;
-        if (tid == DB - 1) s_off[DB] = base + inc;
-        __syncthreads();
-    }
-    const int total = s_off[DB];
-    int l = 0;
-    for (int item = tid; item < total; item += DB) {
-        while (s_off[l + 1] <= item) ++l;  // items are visited in increasing order
-        const int col = item - s_off[l];
+    __syncthreads();
+    // Phase 2, one warp per landmark: lanes over the 9k + 1 columns of the
+    // six rows (three top rows, three damping rows; coalesced row segments)
+    const int lane = tid & 31, w = tid >> 5;
+    for (int l = w; l < DB; l += DT / 32) {
+        if (blockIdx.x * DB + l >= n_pt) break;
         const int ncol = 9 * s_k[l];
-        float* top = tpool + s_top[l];
-        const int tc = col < ncol ? col : ncol + 3;
-        const float* rs = s_rot[l];
-        float u[3], v[3];
+        float* __restrict__ top = tpool + s_top[l];
+        float* __restrict__ dmp = apool + s_damp[l];
+        float* __restrict__ cdm = cpool + s_cd[l];
+        float ro[12], rn[12];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            u[i] = top[i * (ncol + 4) + tc];
-            v[i] = 0.f;
+        for (int m = 0; m < 12; ++m) {
+            ro[m] = s_rot[l][m];
+            rn[m] = s_rot[l][12 + m];
         }
-        if (undo) {
+        for (int col = lane; col <= ncol; col += 32) {
+            const int tc = col < ncol ? col : ncol + 3;
+            float u[3], v[3];
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
-                v[i] = col < ncol ? apool[s_damp[l] + (int64_t)i * ncol + col] : cpool[s_cd[l] + i];
+            for (int i = 0; i < 3; ++i) u[i] = top[i * (ncol + 4) + tc];
+            if (undo) {
 #pragma unroll
-            for (int m = 5; m >= 0; --m) {
-                int c, d;
-                rot_pair(m, c, d);
-                const float a = u[c], b = v[d];
-                u[c] = rs[2 * m] * a - rs[2 * m + 1] * b;
-                v[d] = rs[2 * m + 1] * a + rs[2 * m] * b;
+                for (int i = 0; i < 3; ++i) v[i] = col < ncol ? dmp[(int64_t)i * ncol + col] : cdm[i];
+#pragma unroll
+                for (int m = 5; m >= 0; --m) {
+                    int c, d;
+                    rot_pair(m, c, d);
+                    const float a = u[c], b = v[d];
+                    u[c] = ro[2 * m] * a - ro[2 * m + 1] * b;
+                    v[d] = ro[2 * m + 1] * a + ro[2 * m] * b;
+                }
             }
 #pragma unroll
             for (int i = 0; i < 3; ++i) v[i] = 0.f;
-        }
 #pragma unroll
-        for (int m = 0; m < 6; ++m) {
-            int c, d;
-            rot_pair(m, c, d);
-            const float a = u[c], b = v[d];
-            u[c] = rs[12 + 2 * m] * a + rs[13 + 2 * m] * b;
-            v[d] = -rs[13 + 2 * m] * a + rs[12 + 2 * m] * b;
-        }
+            for (int m = 0; m < 6; ++m) {
+                int c, d;
+                rot_pair(m, c, d);
+                const float a = u[c], b = v[d];
+                u[c] = rn[2 * m] * a + rn[2 * m + 1] * b;
+                v[d] = -rn[2 * m + 1] * a + rn[2 * m] * b;
+            }
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            top[i * (ncol + 4) + tc] = u[i];
-            if (col < ncol) apool[s_damp[l] + (int64_t)i * ncol + col] = v[i];
-            else cpool[s_cd[l] + i] = v[i];
+            for (int i = 0; i < 3; ++i) {
+                top[i * (ncol + 4) + tc] = u[i];
+                if (col < ncol) dmp[(int64_t)i * ncol + col] = v[i];
+                else cdm[i] = v[i];
+            }
         }
     }
 }
@@ -176,7 +162,7 @@ k_damp(int n_pt, const int32_t* __restrict__ pt_off, const int64_t* __restrict__
 
 void launch_damp(Problem& p, bool undo_old, float lambda) {
     count_launches(p, 1);
-    k_damp<<<ceil_div(p.n_pt, DB), DB, 0, p.stream>>>(p.n_pt, p.pt_off, p.a_off, p.c_off, p.tpool, p.apool, p.cpool,
+    k_damp<<<ceil_div(p.n_pt, DB), DT, 0, p.stream>>>(p.n_pt, p.pt_off, p.a_off, p.c_off, p.tpool, p.apool, p.cpool,
                                                       p.dl2, p.rot, sqrtf(lambda), p.batch.lam, p.batch.lm_prob,
                                                       undo_old ? 1 : 0);
     BA_LAUNCH_CHECK();

@@ -31,7 +31,8 @@ __host__ __device__ constexpr int lin_smem_floats(int k) { return 59 * k + 24; }
 
 // A team of TEAM threads factors one landmark block.  TEAM = 8 or 16: a
 // sub-warp team (segmented shuffles), several landmarks per warp; 32: a warp;
-// BIG_TEAM: a CTA.  Every team of a warp runs the same sequence of shuffles
+// BIG_TEAM: a CTA.  Teams: 8 lanes for k <= 4, 16 for k <= 8, a warp for
+// k <= 32, a CTA above.  Every team of a warp runs the same sequence of shuffles
 // and syncs whatever its k, so teams of one warp may hold different k.
 template <int TEAM>
 struct Team {
@@ -90,7 +91,7 @@ struct Team<BIG_TEAM> {
 };
 
 struct LinArgs {
-    const float* cams;
+    const float* frames;   // camera frames (FRAME floats per camera)
     const float* pts;
     const int32_t* obs_cam_s;
     const float2* obs_xy_s;
@@ -129,7 +130,7 @@ __device__ void marginalize_landmark(const LinArgs& A, int j, float* sm, float* 
     for (int s = rank; s < k; s += TEAM) {
         const float2 z = A.obs_xy_s[s0 + s];
         float r[2], Jp[18], Jl[6];
-        project_jacobians(A.cams + 9 * A.obs_cam_s[s0 + s], X0, X1, X2, z.x, z.y, r, Jp, Jl);
+        frame_jacobians(A.frames + FRAME * A.obs_cam_s[s0 + s], X0, X1, X2, z.x, z.y, r, Jp, Jl);
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             RV[2 * s + i] = r[i];
@@ -352,7 +353,7 @@ k_linearize_block(LinArgs A, const int32_t* __restrict__ order, int count) {
 // (deterministic).
 constexpr int CD_THREADS = 256;
 __global__ void __launch_bounds__(CD_THREADS)
-k_camera_diag(int n_cam, const float* __restrict__ cams, const float* __restrict__ pts,
+k_camera_diag(int n_cam, const float* __restrict__ frames, const float* __restrict__ pts,
               const int32_t* __restrict__ obs_pt_s, const float2* __restrict__ obs_xy_s,
               const int32_t* __restrict__ cam_off, const int32_t* __restrict__ cam_list,
               float* __restrict__ dp2) {
@@ -367,7 +368,7 @@ k_camera_diag(int n_cam, const float* __restrict__ cams, const float* __restrict
         const int j = obs_pt_s[s];
         const float2 z = obs_xy_s[s];
         float r[2], Jp[18], Jl[6];
-        project_jacobians(cams + 9 * cam, pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], z.x, z.y, r, Jp, Jl);
+        frame_jacobians(frames + FRAME * cam, pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], z.x, z.y, r, Jp, Jl);
 #pragma unroll
         for (int c = 0; c < 9; ++c) acc[c] += Jp[c] * Jp[c] + Jp[9 + c] * Jp[9 + c];
     }
@@ -384,7 +385,7 @@ k_camera_diag(int n_cam, const float* __restrict__ cams, const float* __restrict
     }
 }
 
-__global__ void k_export_jacobians(int64_t n_obs, const float* __restrict__ cams, const float* __restrict__ pts,
+__global__ void k_export_jacobians(int64_t n_obs, const float* __restrict__ frames, const float* __restrict__ pts,
                                    const int32_t* __restrict__ obs_cam_s, const int32_t* __restrict__ obs_pt_s,
                                    const float2* __restrict__ obs_xy_s, float* r_out, float* jp_out,
                                    float* jl_out) {
@@ -393,15 +394,26 @@ __global__ void k_export_jacobians(int64_t n_obs, const float* __restrict__ cams
         const int j = obs_pt_s[s];
         const float2 z = obs_xy_s[s];
         float r[2], Jp[18], Jl[6];
-        project_jacobians(cams + 9 * obs_cam_s[s], pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], z.x, z.y, r,
-                          Jp, Jl);
+        frame_jacobians(frames + FRAME * obs_cam_s[s], pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], z.x, z.y, r,
+                        Jp, Jl);
         for (int i = 0; i < 2; ++i) r_out[2 * s + i] = r[i];
         for (int i = 0; i < 18; ++i) jp_out[18 * s + i] = Jp[i];
         for (int i = 0; i < 6; ++i) jl_out[6 * s + i] = Jl[i];
     }
 }
 
+__global__ void k_frames(int n_cam, const float* __restrict__ cams, float* __restrict__ frames) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_cam) make_frame(cams + 9 * i, frames + FRAME * i);
+}
+
 }  // namespace
+
+void launch_frames(Problem& p) {
+    count_launches(p, 1);
+    k_frames<<<ceil_div(p.n_cam, 128), 128, 0, p.stream>>>(p.n_cam, p.cams, p.frames);
+    BA_LAUNCH_CHECK();
+}
 
 int linearize_k_limit() { return 900; }
 
@@ -431,21 +443,28 @@ void configure_linearize(Problem& p) {
 
 void launch_camera_diag(Problem& p) {
     count_launches(p, 1);
-    k_camera_diag<<<p.n_cam, CD_THREADS, 0, p.stream>>>(p.n_cam, p.cams, p.pts, p.obs_pt_s, p.obs_xy_s, p.cam_off,
+    k_camera_diag<<<p.n_cam, CD_THREADS, 0, p.stream>>>(p.n_cam, p.frames, p.pts, p.obs_pt_s, p.obs_xy_s, p.cam_off,
                                                        p.cam_list, p.dp2);
     BA_LAUNCH_CHECK();
 }
 
 void launch_linearize(Problem& p) {
-    LinArgs A{p.cams, p.pts, p.obs_cam_s, p.obs_xy_s, p.pt_off, p.a_off,
+    LinArgs A{p.frames, p.pts, p.obs_cam_s, p.obs_xy_s, p.pt_off, p.a_off,
               p.apool, p.tpool, p.cpool, p.c_off, p.dl2};
     // segments of lm_by_k: k > 32 | 9..32 | 5..8 | 2..4
     const int n_big = p.n_big, n32 = count_k(p, 8, 32), n16 = count_k(p, 4, 8), n8 = count_k(p, 1, 4);
     int first = 0;
     if (n_big > 0) {
+        // the few landmarks with k > 32 take one CTA each and run for the
+        // latency of a long sequential factorisation: on a side stream, in
+        // parallel with the team kernels (disjoint landmarks)
+        BA_CUDA_TRY(cudaEventRecord(p.ev_fork, p.stream));
+        BA_CUDA_TRY(cudaStreamWaitEvent(p.side, p.ev_fork, 0));
         const size_t sm = sizeof(float) * lin_smem_floats(p.k_max);
-        k_linearize_block<<<n_big, BIG_TEAM, sm, p.stream>>>(A, p.lm_by_k, n_big);
+        k_linearize_block<<<n_big, BIG_TEAM, sm, p.side>>>(A, p.lm_by_k, n_big);
         count_launches(p, 1);
+        BA_LAUNCH_CHECK();
+        BA_CUDA_TRY(cudaEventRecord(p.ev_join, p.side));
     }
     first += n_big;
     if (n32 > 0) {
@@ -466,10 +485,12 @@ void launch_linearize(Problem& p) {
         count_launches(p, 1);
     }
     BA_LAUNCH_CHECK();
+    if (n_big > 0) BA_CUDA_TRY(cudaStreamWaitEvent(p.stream, p.ev_join, 0));
 }
 
 void launch_export_jacobians(Problem& p, float* r, float* jp, float* jl) {
-    k_export_jacobians<<<p.sm_count * 4, 256, 0, p.stream>>>(p.n_obs, p.cams, p.pts, p.obs_cam_s, p.obs_pt_s,
+    launch_frames(p);
+    k_export_jacobians<<<p.sm_count * 4, 256, 0, p.stream>>>(p.n_obs, p.frames, p.pts, p.obs_cam_s, p.obs_pt_s,
                                                              p.obs_xy_s, r, jp, jl);
     BA_LAUNCH_CHECK();
 }

@@ -110,10 +110,13 @@ struct Problem {
     ba_options opt{};
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t side = nullptr;     // second stream for work that overlaps (joined by events)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int sm_count = 0;
 
     // parameters
     float *cams = nullptr, *pts = nullptr, *cand_cams = nullptr, *cand_pts = nullptr;
+    float *frames = nullptr, *cand_frames = nullptr;  // camera frames (R, t, f, k1, k2) of cams / cand_cams
     // sorted observations and index
     int32_t *obs_cam_s = nullptr, *obs_pt_s = nullptr, *perm = nullptr;
     float2* obs_xy_s = nullptr;
@@ -201,6 +204,7 @@ struct Problem {
 void build_index(Problem& p, const int32_t* d_obs_cam, const int32_t* d_obs_pt,
                  const double* d_obs_xy, const double* d_cams, const double* d_pts);
 // K1: damping diagonals, linearisation + Householder QR (linearize.cu)
+void launch_frames(Problem& p);   // frames of the current cams
 void launch_camera_diag(Problem& p);
 void launch_linearize(Problem& p);
 void launch_export_jacobians(Problem& p, float* r, float* jp, float* jl);
