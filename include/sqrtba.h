@@ -125,6 +125,11 @@ SQRTBA_API ba_status ba_destroy(ba_problem* h);
  * undamped.  Also evaluates the cost at the current state. */
 SQRTBA_API ba_status ba_linearize(ba_problem* h);
 
+/* ba_linearize followed by ba_marginalize_qr(lambda) in one call (the
+ * damping kernel runs straight after the factorisation, no undo needed).
+ * Errors: BA_ERR_INVALID_ARG if lambda <= 0 or not finite. */
+SQRTBA_API ba_status ba_linearize_damped(ba_problem* h, double lambda);
+
 /* Applies landmark damping sqrt(lambda) D_l with six Givens rotations per
  * landmark block (Sec. 5.3, Fig. 3 a-b), first undoing the previous damping
  * with the stored rotations if the blocks are damped (Fig. 3 c).

@@ -126,6 +126,7 @@ _SIGS = {
     "ba_destroy": [_P],
     "ba_linearize": [_P],
     "ba_marginalize_qr": [_P, ctypes.c_double],
+    "ba_linearize_damped": [_P, ctypes.c_double],
     "ba_pcg_solve": [_P, ctypes.POINTER(PcgReport)],
     "ba_backsubstitute": [_P, _d],
     "ba_eval_cost": [_P, ctypes.c_int32, _d],
@@ -282,6 +283,9 @@ class Problem:
     # --- the hot path -----------------------------------------------------------
     def linearize(self):
         self._check(lib().ba_linearize(self.h))
+
+    def linearize_damped(self, lam):
+        self._check(lib().ba_linearize_damped(self.h, float(lam)))
 
     def marginalize_qr(self, lam):
         self._check(lib().ba_marginalize_qr(self.h, float(lam)))

@@ -156,12 +156,17 @@ void free_all(Problem& p) {
 // --- the steps of the hot path ------------------------------------------------
 // K1 (+ D_p^2).  The energy at the linearisation point is evaluated unless
 // the host already knows it (the accepted candidate's cost).
-void do_linearize(Problem& p, bool need_cost = true) {
+void do_linearize(Problem& p, bool need_cost = true, double damp_lambda = 0.0) {
     PhaseTimer t(p, PROF_LINEARIZE);
     launch_frames(p);
     launch_camera_diag(p);
     launch_linearize(p);
     t.end();
+    if (damp_lambda > 0.0) {
+        PhaseTimer td(p, PROF_DAMP);
+        launch_damp(p, false, (float)damp_lambda);
+        td.end();
+    }
     if (need_cost || !p.cost_valid) {
         PhaseTimer tc(p, PROF_COST);
         launch_cost(p, false);
@@ -172,7 +177,8 @@ void do_linearize(Problem& p, bool need_cost = true) {
         p.cost_valid = true;
     }
     p.linearized = true;
-    p.damped = false;
+    p.damped = damp_lambda > 0.0;
+    p.lambda_damped = damp_lambda;
     p.solved = false;
     p.backsubbed = false;
 }
@@ -466,13 +472,13 @@ void do_lm_step(Problem& p, ba_lm_report* rep) {
     require(!p.stopped, BA_ERR_STATE, "ba_lm_step: the LM loop has stopped");
     ba_lm_report r{};
     r.iteration = p.iteration;
+    const double lam = p.lambda;
     if (!p.linearized) {
-        do_linearize(p, false);
+        do_linearize(p, false, lam);
         r.relinearized = 1;
     }
     const double E = p.cost;
-    const double lam = p.lambda;
-    do_marginalize(p, lam);
+    if (!p.damped || p.lambda_damped != lam) do_marginalize(p, lam);
     // K3-K7 enqueued back to back; one synchronisation for the scalars
     // (the learned mode synchronises once more to judge its CG)
     pcg_start(p);
@@ -764,18 +770,17 @@ void do_batch_solve(Problem& p, ba_batch_report* reps, ba_batch_summary* sum) {
     double tune_ms = 0.0;
     BA_CUDA_TRY(cudaEventRecord(B.iter_events[0], p.stream));
     int n_it = 0;
+    launch_batch_cost(p, false, B.cost_a);
+    launch_batch_start(p);  // lambda0 for every problem
     for (int it = 0; it < max_it; ++it) {
         // K1 for every problem (a problem whose last step was rejected
-        // recomputes the blocks of its unchanged state)
+        // recomputes the blocks of its unchanged state), then K2 with each
+        // problem's damping
         PhaseTimer tl(p, PROF_LINEARIZE);
         launch_frames(p);
         launch_camera_diag(p);
         launch_linearize(p);
         tl.end();
-        if (it == 0) {
-            launch_batch_cost(p, false, B.cost_a);
-            launch_batch_start(p);
-        }
         p.linearized = true;
         PhaseTimer td(p, PROF_DAMP);
         launch_damp(p, false, 1.f);  // per-problem damping from B.lam
@@ -894,6 +899,15 @@ ba_status ba_linearize(ba_problem* h) {
     if (!h) return BA_ERR_INVALID_ARG;
     API_TRY
     do_linearize(h->p);
+    return BA_OK;
+    API_CATCH(h)
+}
+
+ba_status ba_linearize_damped(ba_problem* h, double lambda) {
+    if (!h) return BA_ERR_INVALID_ARG;
+    API_TRY
+    require(std::isfinite(lambda) && lambda > 0.0, BA_ERR_INVALID_ARG, "lambda must be positive and finite");
+    do_linearize(h->p, true, lambda);
     return BA_OK;
     API_CATCH(h)
 }

@@ -89,6 +89,13 @@ __device__ __forceinline__ double block_sum_d(double v, double* scratch) {
 
 __host__ __device__ __forceinline__ int64_t pad4(int64_t n) { return (n + 3) & ~int64_t(3); }
 
+// Givens rotation m (0..5) of the landmark damping (Sec. 5.3) acts on R1 row c
+// and damping row d: (d, c) = (0,0) (0,1) (0,2) (1,1) (1,2) (2,2)
+__host__ __device__ __forceinline__ void givens_pair(int m, int& c, int& d) {
+    c = m < 3 ? m : (m < 5 ? m - 2 : 2);
+    d = m < 3 ? 0 : (m < 5 ? 1 : 2);
+}
+
 // Float offset of landmark j's top block (3 rows x (9k + 4)).
 __host__ __device__ __forceinline__ int64_t top_offset(int64_t obs_off_j, int64_t j) {
     return 3 * (9 * obs_off_j + 4 * j);

@@ -5,7 +5,7 @@
 // block (they are the last three rows of A_j); rotation m acts on the pair
 // (R1 row c, damping row d) for (d, c) = (0,0) (0,1) (0,2) (1,1) (1,2) (2,2)
 // and zeroes the damping row's entry in landmark column c:
-//     rho = hypot(a, b), cos = a / rho, sin = b / rho  (a = pivot, b = damping entry)
+//     rho = sqrt(a^2 + b^2), cos = a / rho, sin = b / rho  (a = pivot, b = damping entry)
 //     pivot_row' = cos pivot_row + sin damp_row,  damp_row' = -sin pivot_row + cos damp_row.
 // The rotations are stored individually; re-damping first applies the
 // transposed rotations in reverse order and zeroes the damping rows
@@ -28,10 +28,6 @@ namespace {
 constexpr int DB = 64;   // landmarks per CTA (phase 1: one thread each)
 constexpr int DT = 256;  // threads per CTA (phase 2: 8 warps, DB / 8 landmarks each)
 
-__device__ __forceinline__ void rot_pair(int m, int& c, int& d) {
-    c = m < 3 ? m : (m < 5 ? m - 2 : 2);
-    d = m < 3 ? 0 : (m < 5 ? 1 : 2);
-}
 
 __global__ void __launch_bounds__(DT)
 k_damp(int n_pt, const int32_t* __restrict__ pt_off, const int64_t* __restrict__ a_off,
@@ -64,7 +60,7 @@ k_damp(int n_pt, const int32_t* __restrict__ pt_off, const int64_t* __restrict__
             for (int m = 0; m < 12; ++m) rs[m] = rot[12 * (int64_t)j + m];
             for (int m = 5; m >= 0; --m) {
                 int c, d;
-                rot_pair(m, c, d);
+                givens_pair(m, c, d);
                 const float cs = rs[2 * m], sn = rs[2 * m + 1];
                 for (int col = 0; col < 3; ++col) {
                     const float u = R[c][col], v = D[d][col];
@@ -84,13 +80,14 @@ k_damp(int n_pt, const int32_t* __restrict__ pt_off, const int64_t* __restrict__
         for (int d = 0; d < 3; ++d) D[d][d] = sl * sqrtf(dl2[3 * j + d]);
         for (int m = 0; m < 6; ++m) {
             int c, d;
-            rot_pair(m, c, d);
+            givens_pair(m, c, d);
             const float a = R[c][c], b = D[d][c];
-            const float rho = hypotf(a, b);
+            const float r2 = a * a + b * b;
             float cs = 1.f, sn = 0.f;
-            if (rho > 0.f) {
-                cs = a / rho;
-                sn = b / rho;
+            if (r2 > 0.f) {
+                const float inv = rsqrtf(r2);
+                cs = a * inv;
+                sn = b * inv;
             }
             for (int col = c; col < 3; ++col) {
                 const float u = R[c][col], v = D[d][col];
@@ -132,7 +129,7 @@ k_damp(int n_pt, const int32_t* __restrict__ pt_off, const int64_t* __restrict__
 #pragma unroll
                 for (int m = 5; m >= 0; --m) {
                     int c, d;
-                    rot_pair(m, c, d);
+                    givens_pair(m, c, d);
                     const float a = u[c], b = v[d];
                     u[c] = ro[2 * m] * a - ro[2 * m + 1] * b;
                     v[d] = ro[2 * m + 1] * a + ro[2 * m] * b;
@@ -143,7 +140,7 @@ k_damp(int n_pt, const int32_t* __restrict__ pt_off, const int64_t* __restrict__
 #pragma unroll
             for (int m = 0; m < 6; ++m) {
                 int c, d;
-                rot_pair(m, c, d);
+                givens_pair(m, c, d);
                 const float a = u[c], b = v[d];
                 u[c] = rn[2 * m] * a + rn[2 * m + 1] * b;
                 v[d] = -rn[2 * m + 1] * a + rn[2 * m] * b;

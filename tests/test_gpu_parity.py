@@ -431,3 +431,43 @@ def test_lm_heavy_matches_oracle(pkg, heavy):
     with pkg.Problem.from_scene(heavy, max_lm_iters=15) as p:
         reps = p.solve()
     assert abs(_final(reps) - _final(ref)) <= 1e-3 * _final(ref)
+
+
+@pytest.mark.parametrize("scene", ["tiny", "heavy"])
+def test_linearize_damped_equals_separate_calls(pkg, tiny, heavy, scene):
+    """ba_linearize_damped (a fresh linearisation damped in the same call, as
+    ba_lm_step does) must equal the separate calls: blocks, stored rotations
+    and a later re-damping (undo with those rotations), and the first LM step
+    must equal linearise -> marginalise -> PCG -> back substitution ->
+    candidate cost.  Same implementation on both sides, so blocks are
+    compared element by element."""
+    s = tiny if scene == "tiny" else heavy
+    ks = np.bincount(s.obs_pt, minlength=s.n_pt)
+    lms = [int(np.argmax(ks)), int(np.argmin(ks)), 7]
+    with pkg.Problem.from_scene(s) as p, pkg.Problem.from_scene(s) as q:
+        p.linearize()
+        p.marginalize_qr(2e-3)
+        q.linearize_damped(2e-3)
+        for j in lms:
+            a, b = p.export_landmark(j, k_cap=128), q.export_landmark(j, k_cap=128)
+            for key in ("top", "a", "c", "rot"):
+                np.testing.assert_allclose(b[key], a[key], rtol=1e-5, atol=1e-6 * np.abs(a[key]).max())
+        p.marginalize_qr(5e-1)
+        q.marginalize_qr(5e-1)
+        for j in lms:
+            a, b = p.export_landmark(j, k_cap=128), q.export_landmark(j, k_cap=128)
+            for key in ("top", "a", "c", "rot"):
+                np.testing.assert_allclose(b[key], a[key], rtol=1e-5, atol=1e-6 * np.abs(a[key]).max())
+        p.pcg_solve()
+        q.pcg_solve()
+        assert abs(q.backsubstitute() - p.backsubstitute()) <= 1e-5 * p.backsubstitute()
+    with pkg.Problem.from_scene(s) as p:
+        p.linearize()
+        p.marginalize_qr(1e-4)
+        p.pcg_solve()
+        L = p.backsubstitute()
+        En = p.eval_cost(candidate=True)
+    with pkg.Problem.from_scene(s) as q:
+        r = q.lm_step()
+    assert abs(r["model_cost"] - L) <= 1e-4 * L
+    assert abs(r["new_cost"] - En) <= 1e-4 * En
