@@ -124,20 +124,67 @@ __device__ __forceinline__ void small_tile(const float* __restrict__ sa, const i
             vr[m] = ok ? __ldg(v + yi[m]) : 0.f;
             yr[m] = 0.f;
         }
-#pragma unroll 4
-        for (int r = 0; r < S::NR; ++r) {
-            float a[S::NM];
-            float part = 0.f;
+        if constexpr (S::W >= 16) {
+            // teams of 16 or 32 lanes: rows in groups of 8; the 8 row sums
+            // u_r are reduce-scattered (three halving steps over the team's
+            // top lane bits leave each lane one row, summed over 8 lanes; the
+            // remaining steps complete it) and broadcast back: 16-17
+            // shuffles per 8 rows instead of 32-40
+            constexpr int O1 = S::W / 2, O2 = S::W / 4, O3 = S::W / 8;
+            const bool bA = lane & O1, bB = lane & O2, bC = lane & O3;
+            const int tbase = lane & ~(S::W - 1);
+#pragma unroll 1
+            for (int r0 = 0; r0 < S::NR; r0 += 8) {
+                float a[8][S::NM];
+                float pr[8];
 #pragma unroll
-            for (int m = 0; m < S::NM; ++m) {
-                const int col = t + S::W * m;
-                a[m] = (active && col < S::NC) ? blk[r * S::NC + col] : 0.f;
-                part += a[m] * vr[m];
+                for (int q = 0; q < 8; ++q) {
+                    pr[q] = 0.f;
+#pragma unroll
+                    for (int m = 0; m < S::NM; ++m) {
+                        const int col = t + S::W * m;
+                        a[q][m] = (active && r0 + q < S::NR && col < S::NC) ? blk[(r0 + q) * S::NC + col] : 0.f;
+                        pr[q] += a[q][m] * vr[m];
+                    }
+                }
+                float h4[4], h2[2];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float send = bA ? pr[i] : pr[i + 4], keep = bA ? pr[i + 4] : pr[i];
+                    h4[i] = keep + __shfl_xor_sync(0xffffffffu, send, O1);
+                }
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const float send = bB ? h4[i] : h4[i + 2], keep = bB ? h4[i + 2] : h4[i];
+                    h2[i] = keep + __shfl_xor_sync(0xffffffffu, send, O2);
+                }
+                float u = (bC ? h2[1] : h2[0]) + __shfl_xor_sync(0xffffffffu, bC ? h2[0] : h2[1], O3);
+#pragma unroll
+                for (int o = O3 / 2; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int src = tbase + ((q >> 2) & 1) * O1 + ((q >> 1) & 1) * O2 + (q & 1) * O3;
+                    const float uq = __shfl_sync(0xffffffffu, u, src);
+#pragma unroll
+                    for (int m = 0; m < S::NM; ++m) yr[m] += uq * a[q][m];
+                }
             }
+        } else {
+#pragma unroll 4
+            for (int r = 0; r < S::NR; ++r) {
+                float a[S::NM];
+                float part = 0.f;
 #pragma unroll
-            for (int o = S::W / 2; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                for (int m = 0; m < S::NM; ++m) {
+                    const int col = t + S::W * m;
+                    a[m] = (active && col < S::NC) ? blk[r * S::NC + col] : 0.f;
+                    part += a[m] * vr[m];
+                }
 #pragma unroll
-            for (int m = 0; m < S::NM; ++m) yr[m] += part * a[m];
+                for (int o = S::W / 2; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+#pragma unroll
+                for (int m = 0; m < S::NM; ++m) yr[m] += part * a[m];
+            }
         }
 #pragma unroll
         for (int m = 0; m < S::NM; ++m) {
