@@ -260,15 +260,21 @@ __device__ void marginalize_landmark(const LinArgs& A, int j, float* sm, float* 
         }
         for (int i = 0; write && i < nr; ++i) {
             const float v0 = V[3 * i], v1 = V[3 * i + 1], v2 = V[3 * i + 2];
-            const int si = i >> 1;
             float* __restrict__ dst = i < 3 ? top + i * (ncol + 4) : Aj + (int64_t)(i - 3) * ncol;
-            const float* jrow = JP + i * 9 - 9 * si;
+            // row i's J_p entries sit in columns 9 (i / 2) .. + 8: this lane's
+            // first such column is m0 (and, for teams narrower than 9, m0 + 1)
+            const int base = 9 * (i >> 1);
+            const int m0 = base > rank ? (base - rank + TEAM - 1) / TEAM : 0;
+            const int c0 = rank + TEAM * m0 - base, c1 = c0 + TEAM;
+            const float j0 = c0 < 9 ? JP[i * 9 + c0] : 0.f;
+            const float j1 = (TEAM < 9 && c1 < 9) ? JP[i * 9 + c1] : 0.f;
 #pragma unroll
             for (int m = 0; m < MC; ++m) {
                 const int col = rank + TEAM * m;
                 if (cs[m] >= 0) {
                     float out = -(v0 * w0[m] + v1 * w1[m] + v2 * w2[m]);
-                    if (cs[m] == si) out += jrow[col];
+                    if (m == m0) out += j0;
+                    if (TEAM < 9 && m == m0 + 1) out += j1;
                     dst[col] = out;
                 }
             }
