@@ -615,7 +615,7 @@ def run_kernels_only(args):
     from paper_2103_01843_gb300.synth import make_scene
     torch.cuda.set_device(0)
     scene = make_scene(args.config, args.seed)
-    with sq.Problem.from_scene(scene, stream=torch.cuda.current_stream().cuda_stream) as p:
+    with sq.Problem.from_scene(scene, stream=torch.cuda.current_stream().cuda_stream, autotune=1) as p:
         for _ in range(args.warmup + args.steps):
             p.linearize()
             p.marginalize_qr(1e-4)
@@ -655,6 +655,7 @@ def run_matvec_only(args):
     with sq.Problem.from_scene(scene, stream=torch.cuda.current_stream().cuda_stream) as p:
         p.linearize()
         p.marginalize_qr(1e-4)
+        p.autotune()
         v = np.random.default_rng(0).normal(size=9 * scene.n_cam).astype(np.float32)
         for _ in range(args.warmup + args.steps):
             p.matvec(v)
