@@ -258,21 +258,24 @@ SQRTBA_API ba_status ba_eval_cost_noalloc(const float* d_cams, int32_t n_cam, co
 /* Autotuner of the K4 matvec work plan.                                   */
 /* ---------------------------------------------------------------------- */
 
-/* The matvec streams the landmark blocks, stored by decreasing k, as tiles:
- * blocks with k <= ksmall are grouped into tiles of up to small_bytes
- * (specialised code per k), larger blocks are cut into row tiles.  The
- * tuner times the matvec on the current damped blocks for ksmall in
- * {8, 13, 21} and small_bytes in {8192, 16384, 32768} (median of five
- * launches each, CUDA events on the problem's stream), keeps the fastest
- * plan and reports it.  The paper parallelises over landmarks with a
- * parallel-for (Sec. 6.1) and has no tuner.
+/* The matvec (K4) and the preconditioner's record pass (K3) stream the
+ * landmark blocks, stored by decreasing k, as tiles: blocks with k <= ksmall
+ * are grouped into tiles of up to small_bytes (specialised code per k),
+ * larger blocks are cut into row tiles.  The tuner times each of the two
+ * kernels on the current damped blocks for ksmall in {8, 13, 21} and
+ * small_bytes in {8192, 16384, 32768} (median of five launches each, CUDA
+ * events on the problem's stream), keeps the fastest plan of each and
+ * reports them.  The paper parallelises over landmarks with a parallel-for
+ * (Sec. 6.1) and has no tuner.
  * Errors: BA_ERR_STATE if the blocks are not marginalised. */
 typedef struct {
-    int32_t ksmall;       /* chosen bucket limit */
-    int32_t small_bytes;  /* chosen tile size of the small-block buckets */
+    int32_t ksmall;       /* chosen bucket limit of the matvec */
+    int32_t small_bytes;  /* chosen tile size of the matvec's small-block buckets */
     double matvec_ms;     /* its matvec time */
     double default_ms;    /* matvec time of the default plan (13, 32768) */
-    double tune_ms;       /* wall time of the tuning */
+    double tune_ms;       /* wall time of the tuning (both kernels) */
+    int32_t pc_ksmall;    /* chosen plan of the preconditioner record pass */
+    int32_t pc_small_bytes;
 } ba_tune_report;
 SQRTBA_API ba_status ba_autotune(ba_problem* h, ba_tune_report* report);
 

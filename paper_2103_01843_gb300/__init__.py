@@ -79,7 +79,8 @@ class Profile(ctypes.Structure):
 class TuneReport(ctypes.Structure):
     _fields_ = [("ksmall", ctypes.c_int32), ("small_bytes", ctypes.c_int32),
                 ("matvec_ms", ctypes.c_double), ("default_ms", ctypes.c_double),
-                ("tune_ms", ctypes.c_double)]
+                ("tune_ms", ctypes.c_double), ("pc_ksmall", ctypes.c_int32),
+                ("pc_small_bytes", ctypes.c_int32)]
 
 
 class ProblemDesc(ctypes.Structure):

@@ -272,16 +272,22 @@ struct EventSet {
     }
 };
 
-// median of five timed matvec launches with the plan (ksmall, bytes)
-double time_matvec_plan(Problem& p, int ksmall, int bytes, EventSet& es) {
-    p.mv_ksmall = ksmall;
-    p.mv_small_bytes = bytes;
-    plan_matvec(p);
+// median of five timed launches of the matvec (pc = false) or of the
+// preconditioner record pass (pc = true) with the plan (ksmall, bytes)
+double time_plan(Problem& p, bool pc, int ksmall, int bytes, EventSet& es) {
+    Problem::TilePlan& plan = pc ? p.pc_plan : p.mv_plan;
+    plan.ksmall = ksmall;
+    plan.small_bytes = bytes;
+    plan_tiles(p, pc);
     count_launches(p, 6);
-    launch_matvec_raw(p, p.p, p.q, nullptr);
+    auto run = [&] {
+        if (pc) launch_precond_records(p);
+        else launch_matvec_raw(p, p.p, p.q, nullptr);
+    };
+    run();
     for (int i = 0; i < 5; ++i) {
         BA_CUDA_TRY(cudaEventRecord(es.ev[2 * i], p.stream));
-        launch_matvec_raw(p, p.p, p.q, nullptr);
+        run();
         BA_CUDA_TRY(cudaEventRecord(es.ev[2 * i + 1], p.stream));
     }
     BA_CUDA_TRY(cudaStreamSynchronize(p.stream));
@@ -291,6 +297,8 @@ double time_matvec_plan(Problem& p, int ksmall, int bytes, EventSet& es) {
     return t[2];
 }
 
+// Times every plan (ksmall in {8, 13, 21} x small_bytes in {8, 16, 32} KB)
+// for the matvec and for the record pass and keeps the fastest of each.
 void run_autotune(Problem& p, ba_tune_report* rep) {
     require(p.damped, BA_ERR_STATE, "ba_autotune: blocks are not marginalised (call ba_marginalize_qr)");
     const auto t0 = std::chrono::steady_clock::now();
@@ -298,32 +306,40 @@ void run_autotune(Problem& p, ba_tune_report* rep) {
     BA_CUDA_TRY(cudaMemsetAsync(p.p, 0, sizeof(float) * 9 * p.n_cam, p.stream));
     const int ks_opts[3] = {8, 13, 21};
     const int by_opts[3] = {8192, 16384, 32768};
-    const double def = time_matvec_plan(p, 13, 32768, es);
-    double best = def;
-    int best_ks = 13, best_by = 32768;
-    for (int ks : ks_opts)
-        for (int by : by_opts) {
-            if (ks == 13 && by == 32768) continue;
-            const double t = time_matvec_plan(p, std::min(ks, matvec_ksmall_limit()), by, es);
-            if (t < best) {
-                best = t;
-                best_ks = ks;
-                best_by = by;
+    double def = 0.0;
+    for (int pc = 0; pc < 2; ++pc) {
+        double best = time_plan(p, pc, 13, 32768, es);
+        if (!pc) def = best;
+        int best_ks = 13, best_by = 32768;
+        for (int ks : ks_opts)
+            for (int by : by_opts) {
+                if (ks == 13 && by == 32768) continue;
+                const double t = time_plan(p, pc, std::min(ks, matvec_ksmall_limit()), by, es);
+                if (t < best) {
+                    best = t;
+                    best_ks = ks;
+                    best_by = by;
+                }
             }
+        Problem::TilePlan& plan = pc ? p.pc_plan : p.mv_plan;
+        plan.ksmall = best_ks;
+        plan.small_bytes = best_by;
+        plan_tiles(p, pc);
+        if (rep && !pc) {
+            rep->ksmall = best_ks;
+            rep->small_bytes = best_by;
+            rep->matvec_ms = best;
+            rep->default_ms = def;
         }
-    p.mv_ksmall = best_ks;
-    p.mv_small_bytes = best_by;
-    plan_matvec(p);
+        if (rep && pc) {
+            rep->pc_ksmall = best_ks;
+            rep->pc_small_bytes = best_by;
+        }
+    }
     destroy_graph(p);  // the captured launches hold the old plan
     p.tuned = true;
     const double wall = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    if (rep) {
-        rep->ksmall = best_ks;
-        rep->small_bytes = best_by;
-        rep->matvec_ms = best;
-        rep->default_ms = def;
-        rep->tune_ms = wall;
-    }
+    if (rep) rep->tune_ms = wall;
 }
 
 // K8 before the CG: features of every camera, the MLP, the warm start x0
@@ -830,8 +846,8 @@ void do_batch_solve(Problem& p, ba_batch_report* reps, ba_batch_summary* sum) {
     if (sum) {
         sum->n_problems = B.n_prob;
         sum->lm_iterations = n_it;
-        sum->tuned_ksmall = p.mv_ksmall;
-        sum->tuned_small_bytes = p.mv_small_bytes;
+        sum->tuned_ksmall = p.mv_plan.ksmall;
+        sum->tuned_small_bytes = p.mv_plan.small_bytes;
         sum->total_ms = t_end[n_it];
         sum->tune_ms = tune_ms;
         sum->kernel_launches = p.launches - launches0;

@@ -539,8 +539,8 @@ __global__ void k_add_damping(int n, const float* __restrict__ dp2, float lam, c
 bool smem_y(const Problem& p) { return Layout<MV_STAGES>::ACC_OFF + 36 * (int64_t)p.n_cam <= SMEM_LIMIT; }
 size_t smem_bytes(const Problem& p) { return Layout<MV_STAGES>::ACC_OFF + (smem_y(p) ? 36 * (size_t)p.n_cam : 0); }
 
-MvArgs make_args(Problem& p, const float* v, float* y, const PcgScalars* S) {
-    return MvArgs{static_cast<const MvTile*>(p.mv_tiles), p.mv_tile_begin, p.apool, p.mv_cam, p.lm_by_k, p.pt_off,
+MvArgs make_args(Problem& p, const Problem::TilePlan& plan, const float* v, float* y, const PcgScalars* S) {
+    return MvArgs{static_cast<const MvTile*>(plan.tiles), plan.begin, p.apool, p.mv_cam, p.lm_by_k, p.pt_off,
                   p.obs_cam_s, p.a_off, v, y, p.n_cam, S, p.err, p.cpool, p.prec};
 }
 
@@ -552,18 +552,19 @@ int big_tile_rows(int k) { return std::min(MV_UMAX & ~3, (MV_STAGE_A / (36 * k))
 // Host planning of the tiles: runs of equal-k blocks in storage order
 // (decreasing k), cut into stage-sized tiles, then contiguous tile ranges per
 // CTA balanced by bytes.
-void plan_matvec(Problem& p) {
+void plan_tiles(Problem& p, bool pc) {
+    Problem::TilePlan& plan = pc ? p.pc_plan : p.mv_plan;
     std::vector<MvTile> tiles;
     const int kmax = p.k_max;
     // records of blocks that are split into row tiles are accumulated
     // atomically: the observations of the landmarks with k above the
     // smallest split k, which come first in storage order, are zeroed before
     // each preconditioner pass (the records of unsplit blocks are stored)
-    const int ksmall = std::min(p.mv_ksmall, MV_KSMALL_MAX);
-    const int small_bytes = std::min(p.mv_small_bytes, MV_STAGE_A);
-    p.n_obs_direct_big = 0;
+    const int ksmall = std::min(plan.ksmall, MV_KSMALL_MAX);
+    const int small_bytes = std::min(plan.small_bytes, MV_STAGE_A);
+    plan.n_obs_split = 0;
     for (int b = 0; b <= kmax && kmax - b > ksmall; ++b)
-        if (big_tile_rows(kmax - b) < 2 * (kmax - b)) p.n_obs_direct_big = p.run_co[b + 1];
+        if (big_tile_rows(kmax - b) < 2 * (kmax - b)) plan.n_obs_split = p.run_co[b + 1];
     for (int b = 0; b <= kmax; ++b) {
         const int k = kmax - b;
         const int64_t cnt = p.k_run_count[b];
@@ -631,19 +632,24 @@ void plan_matvec(Problem& p) {
     }
     begin[grid] = (int32_t)perm.size();
     tiles.swap(perm);
-    p.n_mv_tiles = (int)tiles.size();
-    if (!p.mv_tiles || p.mv_tile_cap < p.n_mv_tiles) {
+    plan.n = (int)tiles.size();
+    if (!plan.tiles || plan.cap < plan.n) {
         // re-planning (autotuner) reuses the allocation when it is large enough
-        p.mv_tile_cap = std::max(1, p.n_mv_tiles);
-        p.mv_tiles = dalloc<MvTile>(p, p.mv_tile_cap);
+        plan.cap = std::max(1, plan.n);
+        plan.tiles = dalloc<MvTile>(p, plan.cap);
     }
-    if (!p.mv_tile_begin) p.mv_tile_begin = dalloc<int32_t>(p, grid + 1);
+    if (!plan.begin) plan.begin = dalloc<int32_t>(p, grid + 1);
     if (!tiles.empty())
-        BA_CUDA_TRY(cudaMemcpyAsync(p.mv_tiles, tiles.data(), sizeof(MvTile) * tiles.size(), cudaMemcpyHostToDevice,
+        BA_CUDA_TRY(cudaMemcpyAsync(plan.tiles, tiles.data(), sizeof(MvTile) * tiles.size(), cudaMemcpyHostToDevice,
                                     p.stream));
-    BA_CUDA_TRY(cudaMemcpyAsync(p.mv_tile_begin, begin.data(), sizeof(int32_t) * (grid + 1), cudaMemcpyHostToDevice,
+    BA_CUDA_TRY(cudaMemcpyAsync(plan.begin, begin.data(), sizeof(int32_t) * (grid + 1), cudaMemcpyHostToDevice,
                                 p.stream));
     BA_CUDA_TRY(cudaStreamSynchronize(p.stream));
+}
+
+void plan_matvec(Problem& p) {
+    plan_tiles(p, false);
+    plan_tiles(p, true);
 }
 
 int matvec_ctas_per_sm() { return 1; }
@@ -661,7 +667,7 @@ void configure_matvec(Problem& p) {
 }
 
 void launch_matvec_raw(Problem& p, const float* v, float* y, const PcgScalars* S) {
-    const MvArgs a = make_args(p, v, y, S);
+    const MvArgs a = make_args(p, p.mv_plan, v, y, S);
     if (smem_y(p)) k_matvec_tiles<MODE_MATVEC, true, MV_STAGES><<<p.mv_grid, MV_THREADS, smem_bytes(p), p.stream>>>(a);
     else k_matvec_tiles<MODE_MATVEC, false, MV_STAGES><<<p.mv_grid, MV_THREADS, smem_bytes(p), p.stream>>>(a);
     BA_LAUNCH_CHECK();
@@ -672,9 +678,9 @@ void launch_matvec_raw(Problem& p, const float* v, float* y, const PcgScalars* S
 // storage order.  Records of blocks split over row tiles are accumulated, so
 // their prefix is zeroed first.
 void launch_precond_records(Problem& p) {
-    const MvArgs a = make_args(p, nullptr, nullptr, nullptr);
-    if (p.n_obs_direct_big > 0)
-        BA_CUDA_TRY(cudaMemsetAsync(p.prec, 0, sizeof(float) * REC_STRIDE * p.n_obs_direct_big, p.stream));
+    const MvArgs a = make_args(p, p.pc_plan, nullptr, nullptr, nullptr);
+    if (p.pc_plan.n_obs_split > 0)
+        BA_CUDA_TRY(cudaMemsetAsync(p.prec, 0, sizeof(float) * REC_STRIDE * p.pc_plan.n_obs_split, p.stream));
     k_matvec_tiles<MODE_PRECOND, false, MV_STAGES><<<p.mv_grid, MV_THREADS, Layout<MV_STAGES>::ACC_OFF, p.stream>>>(a);
     BA_LAUNCH_CHECK();
 }

@@ -418,7 +418,7 @@ k_bpcg_update(int n_prob, const int32_t* __restrict__ prob_cam_off, const float*
 
 void launch_precond_rhs(Problem& p) {
     launch_precond_records(p);
-    count_launches(p, 2 + (p.n_obs_direct_big > 0 ? 1 : 0));
+    count_launches(p, 2 + (p.pc_plan.n_obs_split > 0 ? 1 : 0));
     k_precond_reduce<<<p.n_cam, 32 * PC_WARPS, 0, p.stream>>>(p.n_cam, p.cam_off, p.cam_list_st, p.prec, p.dp2,
                                                              (float)p.lambda_damped, p.batch.lam, p.batch.cam_prob,
                                                              p.mdiag, p.minv, p.g, p.err);

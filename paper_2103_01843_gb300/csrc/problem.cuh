@@ -126,20 +126,23 @@ struct Problem {
     int32_t* mv_cam = nullptr;       // camera of every observation in storage order
     int32_t* c_off = nullptr;        // float offset of c_j = Q2^T r (storage order, 2k per landmark)
     int32_t* cam_list_st = nullptr;  // camera lists as storage-order observation indices
-    int64_t n_obs_direct_big = 0;    // observations of blocks split into row tiles (first in storage order)
     std::vector<int32_t> k_run_count;  // host: landmarks with k = k_max - b
     std::vector<int64_t> run_off, run_co;  // host: float / observation offset of run b
-    // matvec work plan: tiles of the block pool streamed through shared memory
-    void* mv_tiles = nullptr;        // MvTile[n_mv_tiles]
-    int32_t* mv_tile_begin = nullptr;  // first tile of each CTA (grid + 1)
-    int n_mv_tiles = 0;
-    int mv_tile_cap = 0;             // tiles the allocation holds
+    // work plans of the tile pipeline: tiles of the block pool streamed
+    // through shared memory.  Blocks with k <= ksmall are grouped into tiles
+    // of up to small_bytes; larger ones are cut into row tiles.  The matvec
+    // (K4) and the preconditioner record pass (K3) have a plan each (the
+    // autotuner chooses both).
+    struct TilePlan {
+        void* tiles = nullptr;           // MvTile[n]
+        int32_t* begin = nullptr;        // first tile of each CTA (grid + 1)
+        int n = 0, cap = 0;
+        int ksmall = 13;
+        int small_bytes = 32768;
+        int64_t n_obs_split = 0;         // observations of blocks split into row tiles (first in storage order)
+    };
+    TilePlan mv_plan, pc_plan;
     int mv_grid = 0;
-    // planner parameters (set by the autotuner): blocks with k <= mv_ksmall
-    // are grouped into tiles of up to mv_small_bytes; larger ones are cut
-    // into row tiles
-    int mv_ksmall = 13;
-    int mv_small_bytes = 32768;
     bool tuned = false;              // the autotuner has chosen the plan
     // blocks
     float *apool = nullptr, *tpool = nullptr, *cpool = nullptr, *rot = nullptr;
@@ -237,8 +240,10 @@ void launch_batch_commit(Problem& p);
 // one-time kernel attributes (dynamic shared memory limits)
 void configure_linearize(Problem& p);
 void configure_matvec(Problem& p);
-// matvec tile plan (host planning + upload), after build_index
+// tile plans (host planning + upload), after build_index: both plans, or
+// one of them (pc = true: the preconditioner record pass's)
 void plan_matvec(Problem& p);
+void plan_tiles(Problem& p, bool pc);
 // planner limits: largest mv_ksmall, largest mv_small_bytes
 int matvec_ksmall_limit();
 int matvec_stage_bytes();
