@@ -149,16 +149,12 @@ class ClockSampler:
 
 
 def solve_to_tol(p, f_tau):
-    """LM iterations until an accepted cost <= f_tau; returns (iters, cg, reached)."""
-    iters, cg = 0, 0
-    while True:
-        r = p.lm_step()
-        iters += 1
-        cg += r["cg_iters"]
-        if r["accepted"] and r["new_cost"] <= f_tau:
-            return iters, cg, True
-        if r["stop"]:
-            return iters, cg, False
+    """LM iterations until an accepted cost <= f_tau (one ba_solve call with
+    target_cost = f_tau); returns (iters, cg, reached)."""
+    reps = p.solve(max_reports=64)
+    cg = sum(r["cg_iters"] for r in reps)
+    reached = any(r["accepted"] and r["new_cost"] <= f_tau for r in reps)
+    return len(reps), cg, reached
 
 
 # ---------------------------------------------------------------------------
@@ -244,6 +240,7 @@ def run_ours(args):
     f_star = min([r["new_cost"] for r in reps if r["accepted"]] + [f0])
     f_tau = f_star + TAU * (f0 - f_star)
     cams0, pts0 = scene.cams, scene.pts
+    p.set_target_cost(f_tau)
 
     clocks = ClockSampler(dev)
     clocks.start()
@@ -330,7 +327,7 @@ def run_ours(args):
     for _ in range(args.e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        q = sq.Problem.from_scene(scene, stream=stream.cuda_stream)
+        q = sq.Problem.from_scene(scene, stream=stream.cuda_stream, target_cost=f_tau)
         solve_to_tol(q, f_tau)
         q.get_params()
         pr = q.profile()

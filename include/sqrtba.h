@@ -74,7 +74,10 @@ typedef struct {
                              (ba_autotune); default 0 */
     int32_t use_learned;  /* 1: PCG with the learned warm start and corrected block
                              preconditioner of the model attached by ba_set_learned */
-    int32_t reserved[5];  /* zero */
+    int32_t reserved0;    /* zero */
+    double target_cost;   /* > 0: the LM also stops after an accepted step whose cost is
+                             <= target_cost (e.g. the f_tau of a tolerance test); default 0 */
+    int32_t reserved[2];  /* zero */
 } ba_options;
 
 /* Fills *opt with the defaults above. */
@@ -175,6 +178,10 @@ SQRTBA_API ba_status ba_get_params(ba_problem* h, double* cams, double* pts);
 /* Replaces the state (host FP64 arrays, same layout), resets lambda to
  * lambda0 and the LM iteration counter, and marks the linearisation stale. */
 SQRTBA_API ba_status ba_set_params(ba_problem* h, const double* cams, const double* pts);
+
+/* Replaces the solver settings of a problem (validated as by ba_create);
+ * the next LM step and solve use them. */
+SQRTBA_API ba_status ba_set_options(ba_problem* h, const ba_options* opt);
 
 /* Checkpoint of the LM state besides the parameters. */
 typedef struct {

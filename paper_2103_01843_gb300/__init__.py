@@ -40,7 +40,8 @@ class Options(ctypes.Structure):
                 ("func_tol", ctypes.c_double), ("max_cg_iters", ctypes.c_int32),
                 ("cg_eta", ctypes.c_double), ("use_graph", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("use_learned", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("reserved0", ctypes.c_int32), ("target_cost", ctypes.c_double),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class PcgReport(ctypes.Structure):
@@ -108,7 +109,7 @@ PROFILE_SLOTS = ("linearize", "damp", "precond", "matvec", "unused", "backsub", 
 
 
 def _struct_dict(s):
-    return {name.rstrip("_"): getattr(s, name) for name, _ in s._fields_ if name != "reserved"}
+    return {name.rstrip("_"): getattr(s, name) for name, _ in s._fields_ if not name.startswith("reserved")}
 
 
 _lib = None
@@ -136,6 +137,7 @@ _SIGS = {
     "ba_get_params": [_P, _d, _d],
     "ba_set_params": [_P, _d, _d],
     "ba_get_state": [_P, ctypes.POINTER(LmState)],
+    "ba_set_options": [_P, ctypes.POINTER(Options)],
     "ba_set_state": [_P, ctypes.POINTER(LmState)],
     "ba_get_info": [_P, ctypes.POINTER(Info)],
     "ba_set_profiling": [_P, ctypes.c_int32],
@@ -310,6 +312,11 @@ class Problem:
         r = LmReport()
         self._check(lib().ba_lm_step(self.h, ctypes.byref(r)))
         return _struct_dict(r)
+
+    def set_target_cost(self, target):
+        """Stop the LM after an accepted step with cost <= target (0: off)."""
+        self.options.target_cost = float(target)
+        self._check(lib().ba_set_options(self.h, ctypes.byref(self.options)))
 
     def solve(self, max_reports=1000):
         reps = (LmReport * max_reports)()

@@ -543,6 +543,7 @@ void do_lm_step(Problem& p, ba_lm_report* rep) {
         p.lambda = std::max(p.lambda, 1e-16);
         p.nu = 2.0;
         if (std::fabs(E - En) / E < p.opt.func_tol) p.stopped = true;
+        if (p.opt.target_cost > 0.0 && En <= p.opt.target_cost) p.stopped = true;
     } else {
         p.lambda *= p.nu;
         p.nu *= 2.0;
@@ -1022,6 +1023,20 @@ ba_status ba_set_params(ba_problem* h, const double* cams, const double* pts) {
     p.nu = 2.0;
     p.iteration = 0;
     p.stopped = false;
+    return BA_OK;
+    API_CATCH(h)
+}
+
+ba_status ba_set_options(ba_problem* h, const ba_options* opt) {
+    if (!h || !opt) return BA_ERR_INVALID_ARG;
+    API_TRY
+    require(opt->lambda0 > 0 && opt->max_lm_iters >= 1 && opt->max_cg_iters >= 1 && opt->cg_eta > 0,
+            BA_ERR_INVALID_ARG, "invalid options");
+    Problem& p = h->p;
+    sync(p);
+    const bool graph_change = opt->use_graph != p.opt.use_graph;
+    p.opt = *opt;
+    if (graph_change) destroy_graph(p);
     return BA_OK;
     API_CATCH(h)
 }

@@ -118,38 +118,54 @@ k_damp(int n_pt, const int32_t* __restrict__ pt_off, const int64_t* __restrict__
             ro[m] = s_rot[l][m];
             rn[m] = s_rot[l][12 + m];
         }
-        for (int col = lane; col <= ncol; col += 32) {
-            const int tc = col < ncol ? col : ncol + 3;
-            float u[3], v[3];
+        // two columns per lane and step, loads of both issued first (the
+        // kernel is bound by the latency of these loads)
+        for (int col0 = lane; col0 <= ncol; col0 += 64) {
+            float u[2][3], v[2][3];
 #pragma unroll
-            for (int i = 0; i < 3; ++i) u[i] = top[i * (ncol + 4) + tc];
-            if (undo) {
+            for (int h = 0; h < 2; ++h) {
+                const int col = col0 + 32 * h;
+                const int tc = col < ncol ? col : ncol + 3;
 #pragma unroll
-                for (int i = 0; i < 3; ++i) v[i] = col < ncol ? dmp[(int64_t)i * ncol + col] : cdm[i];
-#pragma unroll
-                for (int m = 5; m >= 0; --m) {
-                    int c, d;
-                    givens_pair(m, c, d);
-                    const float a = u[c], b = v[d];
-                    u[c] = ro[2 * m] * a - ro[2 * m + 1] * b;
-                    v[d] = ro[2 * m + 1] * a + ro[2 * m] * b;
+                for (int i = 0; i < 3; ++i) {
+                    u[h][i] = col <= ncol ? top[i * (ncol + 4) + tc] : 0.f;
+                    v[h][i] = (undo && col <= ncol) ? (col < ncol ? dmp[(int64_t)i * ncol + col] : cdm[i]) : 0.f;
                 }
             }
 #pragma unroll
-            for (int i = 0; i < 3; ++i) v[i] = 0.f;
+            for (int h = 0; h < 2; ++h) {
+                if (undo) {
 #pragma unroll
-            for (int m = 0; m < 6; ++m) {
-                int c, d;
-                givens_pair(m, c, d);
-                const float a = u[c], b = v[d];
-                u[c] = rn[2 * m] * a + rn[2 * m + 1] * b;
-                v[d] = -rn[2 * m + 1] * a + rn[2 * m] * b;
+                    for (int m = 5; m >= 0; --m) {
+                        int c, d;
+                        givens_pair(m, c, d);
+                        const float a = u[h][c], b = v[h][d];
+                        u[h][c] = ro[2 * m] * a - ro[2 * m + 1] * b;
+                        v[h][d] = ro[2 * m + 1] * a + ro[2 * m] * b;
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 3; ++i) v[h][i] = 0.f;
+#pragma unroll
+                for (int m = 0; m < 6; ++m) {
+                    int c, d;
+                    givens_pair(m, c, d);
+                    const float a = u[h][c], b = v[h][d];
+                    u[h][c] = rn[2 * m] * a + rn[2 * m + 1] * b;
+                    v[h][d] = -rn[2 * m + 1] * a + rn[2 * m] * b;
+                }
             }
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                top[i * (ncol + 4) + tc] = u[i];
-                if (col < ncol) dmp[(int64_t)i * ncol + col] = v[i];
-                else cdm[i] = v[i];
+            for (int h = 0; h < 2; ++h) {
+                const int col = col0 + 32 * h;
+                if (col > ncol) continue;
+                const int tc = col < ncol ? col : ncol + 3;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    top[i * (ncol + 4) + tc] = u[h][i];
+                    if (col < ncol) dmp[(int64_t)i * ncol + col] = v[h][i];
+                    else cdm[i] = v[h][i];
+                }
             }
         }
     }
