@@ -63,6 +63,18 @@ def rank_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(value, device="cuda"):
+    """The largest value over the ranks of the process group (the job's
+    time is the slowest rank's); the value itself without a group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -282,11 +294,7 @@ def run_ours(args):
     prof = p.profile()
     prof_steps = min(args.steps, 20)
 
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms))
     ms_per_step = total_ms / args.steps
 
     # roofline of the kernels (algorithmic bytes / event-timed launch durations)
@@ -446,11 +454,7 @@ def run_batched(args):
         b.restart()
         b.solve()
     prof = b.profile()
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms))
     ms_per_step = total_ms / args.steps
     peak, peak_kind = measured_peaks()
     e = prof["matvec"]
