@@ -104,6 +104,67 @@ struct LinArgs {
     float* dl2;
 };
 
+// Q^T J_p rows of a landmark with K observations, lanes over the columns
+// col = rank + TEAM m (W of those columns in registers):
+//   out[i][col] = J_p[i][col] - (V[i][0] W0 + V[i][1] W1 + V[i][2] W2),
+// rows 0..2 to the top block, rows 3.. to A_j.  Specialised per K so that the
+// column count, the row strides and the valid columns are compile-time; row
+// i's J_p entries sit in columns 9 (i / 2) .. + 8, this lane's first such
+// column is m0 (and, for teams narrower than 9, m0 + 1).
+template <int TEAM, int K, int MC>
+__device__ __forceinline__ void write_rows(const float* __restrict__ V, const float* __restrict__ JP,
+                                           const float (&w0)[MC], const float (&w1)[MC], const float (&w2)[MC],
+                                           float* __restrict__ top, float* __restrict__ Aj, int rank) {
+    constexpr int NC = 9 * K, NR = 2 * K;
+    constexpr int MK = (NC + TEAM - 1) / TEAM;
+    static_assert(MK <= MC, "columns per lane");
+    const int mfull = (NC - rank + TEAM - 1) / TEAM;  // this lane's valid columns
+#pragma unroll 2
+    for (int i = 0; i < NR; ++i) {
+        const float v0 = V[3 * i], v1 = V[3 * i + 1], v2 = V[3 * i + 2];
+        float* __restrict__ dst = i < 3 ? top + i * (NC + 4) : Aj + (i - 3) * NC;
+        const int base = 9 * (i >> 1);
+        const int m0 = base > rank ? (base - rank + TEAM - 1) / TEAM : 0;
+        const int c0 = rank + TEAM * m0 - base, c1 = c0 + TEAM;
+        const float j0 = c0 < 9 ? JP[i * 9 + c0] : 0.f;
+        const float j1 = (TEAM < 9 && c1 < 9) ? JP[i * 9 + c1] : 0.f;
+#pragma unroll
+        for (int m = 0; m < MK; ++m) {
+            float out = -(v0 * w0[m] + v1 * w1[m] + v2 * w2[m]);
+            if (m == m0) out += j0;
+            if (TEAM < 9 && m == m0 + 1) out += j1;
+            if (m < MK - 1 || m < mfull) dst[rank + TEAM * m] = out;
+        }
+    }
+}
+
+template <int TEAM, int MC>
+__device__ __forceinline__ void write_rows_dispatch(int k, const float* V, const float* JP, const float (&w0)[MC],
+                                                    const float (&w1)[MC], const float (&w2)[MC], float* top,
+                                                    float* Aj, int rank) {
+    if constexpr (TEAM == 32) {
+        switch (k) {
+#define WR_CASE(KK) \
+    case KK: write_rows<TEAM, KK, MC>(V, JP, w0, w1, w2, top, Aj, rank); break;
+            WR_CASE(9) WR_CASE(10) WR_CASE(11) WR_CASE(12) WR_CASE(13) WR_CASE(14) WR_CASE(15) WR_CASE(16)
+            WR_CASE(17) WR_CASE(18) WR_CASE(19) WR_CASE(20) WR_CASE(21) WR_CASE(22) WR_CASE(23) WR_CASE(24)
+            WR_CASE(25) WR_CASE(26) WR_CASE(27) WR_CASE(28) WR_CASE(29) WR_CASE(30) WR_CASE(31) WR_CASE(32)
+            default: break;
+        }
+    } else if constexpr (TEAM == 16) {
+        switch (k) {
+            WR_CASE(5) WR_CASE(6) WR_CASE(7) WR_CASE(8)
+            default: break;
+        }
+    } else {
+        switch (k) {
+            WR_CASE(2) WR_CASE(3) WR_CASE(4)
+            default: break;
+        }
+#undef WR_CASE
+    }
+}
+
 // Linearise and marginalise landmark j; sm holds lin_smem_floats(k) floats.
 // write = false runs the same steps without storing (an idle team of a warp).
 // MC: columns per lane for TEAM <= 32 (ceil(9 k_max / TEAM)); the team's
@@ -237,13 +298,10 @@ __device__ void marginalize_landmark(const LinArgs& A, int j, float* sm, float* 
     float* __restrict__ top = A.tpool + toff;
     float* __restrict__ Aj = A.apool + A.a_off[j];
     if constexpr (TEAM <= 32) {
-        // 4+5. W for this lane's columns (registers), then Q^T J_p row by row:
-        // out[i][col] = J_p[i][col] - (V[i][0] W0 + V[i][1] W1 + V[i][2] W2);
-        // J_p[i][col] is non-zero only in the 9 columns of row i's observation
+        // 4+5. W for this lane's columns (registers), then Q^T J_p row by row
         const float* Tm = misc + 5;
         const float T00 = Tm[0], T01 = Tm[1], T02 = Tm[2], T11 = Tm[4], T12 = Tm[5], T22 = Tm[8];
         float w0[MC], w1[MC], w2[MC];
-        int cs[MC];
 #pragma unroll
         for (int m = 0; m < MC; ++m) {
             const int col = rank + TEAM * m;
@@ -256,29 +314,8 @@ __device__ void marginalize_landmark(const LinArgs& A, int j, float* sm, float* 
             w0[m] = T00 * m0;
             w1[m] = T01 * m0 + T11 * m1;
             w2[m] = T02 * m0 + T12 * m1 + T22 * m2;
-            cs[m] = ok ? sb : -1;
         }
-        for (int i = 0; write && i < nr; ++i) {
-            const float v0 = V[3 * i], v1 = V[3 * i + 1], v2 = V[3 * i + 2];
-            float* __restrict__ dst = i < 3 ? top + i * (ncol + 4) : Aj + (int64_t)(i - 3) * ncol;
-            // row i's J_p entries sit in columns 9 (i / 2) .. + 8: this lane's
-            // first such column is m0 (and, for teams narrower than 9, m0 + 1)
-            const int base = 9 * (i >> 1);
-            const int m0 = base > rank ? (base - rank + TEAM - 1) / TEAM : 0;
-            const int c0 = rank + TEAM * m0 - base, c1 = c0 + TEAM;
-            const float j0 = c0 < 9 ? JP[i * 9 + c0] : 0.f;
-            const float j1 = (TEAM < 9 && c1 < 9) ? JP[i * 9 + c1] : 0.f;
-#pragma unroll
-            for (int m = 0; m < MC; ++m) {
-                const int col = rank + TEAM * m;
-                if (cs[m] >= 0) {
-                    float out = -(v0 * w0[m] + v1 * w1[m] + v2 * w2[m]);
-                    if (m == m0) out += j0;
-                    if (TEAM < 9 && m == m0 + 1) out += j1;
-                    dst[col] = out;
-                }
-            }
-        }
+        if (write) write_rows_dispatch<TEAM, MC>(k, V, JP, w0, w1, w2, top, Aj, rank);
     } else {
         // 4. W = Tm^T (V^T J_p) for the pose columns (two non-zero rows each)
         {
