@@ -74,7 +74,8 @@ typedef struct {
                              (ba_autotune); default 0 */
     int32_t use_learned;  /* 1: PCG with the learned warm start and corrected block
                              preconditioner of the model attached by ba_set_learned */
-    int32_t reserved0;    /* zero */
+    int32_t pipeline_stages; /* 0 (default): the K3 / K4 tile pipeline runs 6 stages, or the
+                             depths the autotuner chose; 4, 5 or 6 forces that depth */
     double target_cost;   /* > 0: the LM also stops after an accepted step whose cost is
                              <= target_cost (e.g. the f_tau of a tolerance test); default 0 */
     int32_t reserved[2];  /* zero */
@@ -271,18 +272,25 @@ SQRTBA_API ba_status ba_eval_cost_noalloc(const float* d_cams, int32_t n_cam, co
  * larger blocks are cut into row tiles.  The tuner times each of the two
  * kernels on the current damped blocks for ksmall in {8, 13, 21} and
  * small_bytes in {8192, 16384, 32768} (median of five launches each, CUDA
- * events on the problem's stream), keeps the fastest plan of each and
- * reports them.  The paper parallelises over landmarks with a parallel-for
+ * events on the problem's stream), keeps the fastest plan of each, then
+ * times that plan with 4, 5 and 6 pipeline stages (the matvec also with y
+ * accumulated in global instead of shared memory) and keeps the fastest
+ * depth.  It reports the choices.  The paper parallelises over landmarks with a parallel-for
  * (Sec. 6.1) and has no tuner.
  * Errors: BA_ERR_STATE if the blocks are not marginalised. */
 typedef struct {
     int32_t ksmall;       /* chosen bucket limit of the matvec */
     int32_t small_bytes;  /* chosen tile size of the matvec's small-block buckets */
     double matvec_ms;     /* its matvec time */
-    double default_ms;    /* matvec time of the default plan (13, 32768) */
+    double default_ms;    /* matvec time of the default plan (21, 32768, 6 stages) */
     double tune_ms;       /* wall time of the tuning (both kernels) */
     int32_t pc_ksmall;    /* chosen plan of the preconditioner record pass */
     int32_t pc_small_bytes;
+    int32_t ns;           /* chosen pipeline depth of the matvec (4, 5 or 6 stages of 32 KB) */
+    int32_t y_smem;       /* 1: the matvec accumulates y in shared memory (0: in global memory,
+                             chosen, or y does not fit beside the stages) */
+    int32_t pc_ns;        /* chosen pipeline depth of the record pass */
+    int32_t reserved;
 } ba_tune_report;
 SQRTBA_API ba_status ba_autotune(ba_problem* h, ba_tune_report* report);
 

@@ -40,7 +40,7 @@ class Options(ctypes.Structure):
                 ("func_tol", ctypes.c_double), ("max_cg_iters", ctypes.c_int32),
                 ("cg_eta", ctypes.c_double), ("use_graph", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("use_learned", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("target_cost", ctypes.c_double),
+                ("pipeline_stages", ctypes.c_int32), ("target_cost", ctypes.c_double),
                 ("reserved", ctypes.c_int32 * 2)]
 
 
@@ -81,7 +81,8 @@ class TuneReport(ctypes.Structure):
     _fields_ = [("ksmall", ctypes.c_int32), ("small_bytes", ctypes.c_int32),
                 ("matvec_ms", ctypes.c_double), ("default_ms", ctypes.c_double),
                 ("tune_ms", ctypes.c_double), ("pc_ksmall", ctypes.c_int32),
-                ("pc_small_bytes", ctypes.c_int32)]
+                ("pc_small_bytes", ctypes.c_int32), ("ns", ctypes.c_int32), ("y_smem", ctypes.c_int32),
+                ("pc_ns", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class ProblemDesc(ctypes.Structure):

@@ -273,12 +273,17 @@ struct EventSet {
 };
 
 // median of five timed launches of the matvec (pc = false) or of the
-// preconditioner record pass (pc = true) with the plan (ksmall, bytes)
-double time_plan(Problem& p, bool pc, int ksmall, int bytes, EventSet& es) {
+// preconditioner record pass (pc = true) with the plan (ksmall, bytes) at
+// pipeline depth ns (y in shared memory where y_smem and it fits)
+double time_plan(Problem& p, bool pc, int ksmall, int bytes, int ns, int y_smem, EventSet& es) {
     Problem::TilePlan& plan = pc ? p.pc_plan : p.mv_plan;
-    plan.ksmall = ksmall;
-    plan.small_bytes = bytes;
-    plan_tiles(p, pc);
+    if (plan.ksmall != ksmall || plan.small_bytes != bytes || plan.n == 0) {
+        plan.ksmall = ksmall;
+        plan.small_bytes = bytes;
+        plan_tiles(p, pc);
+    }
+    plan.ns = ns;
+    plan.y_smem = y_smem;
     count_launches(p, 6);
     auto run = [&] {
         if (pc) launch_precond_records(p);
@@ -298,7 +303,10 @@ double time_plan(Problem& p, bool pc, int ksmall, int bytes, EventSet& es) {
 }
 
 // Times every plan (ksmall in {8, 13, 21} x small_bytes in {8, 16, 32} KB)
-// for the matvec and for the record pass and keeps the fastest of each.
+// for the matvec and for the record pass at the default depth (6 stages, y
+// in shared memory where it fits), keeps the fastest of each, then times that
+// plan at depths 4, 5 and 6 (the matvec also with y in global memory) and
+// keeps the fastest depth.
 void run_autotune(Problem& p, ba_tune_report* rep) {
     require(p.damped, BA_ERR_STATE, "ba_autotune: blocks are not marginalised (call ba_marginalize_qr)");
     const auto t0 = std::chrono::steady_clock::now();
@@ -306,34 +314,53 @@ void run_autotune(Problem& p, ba_tune_report* rep) {
     BA_CUDA_TRY(cudaMemsetAsync(p.p, 0, sizeof(float) * 9 * p.n_cam, p.stream));
     const int ks_opts[3] = {8, 13, 21};
     const int by_opts[3] = {8192, 16384, 32768};
+    const Problem::TilePlan dflt{};
     double def = 0.0;
     for (int pc = 0; pc < 2; ++pc) {
-        double best = time_plan(p, pc, 13, 32768, es);
+        double best = time_plan(p, pc, dflt.ksmall, dflt.small_bytes, dflt.ns, 1, es);
         if (!pc) def = best;
-        int best_ks = 13, best_by = 32768;
+        int best_ks = dflt.ksmall, best_by = dflt.small_bytes;
         for (int ks : ks_opts)
             for (int by : by_opts) {
-                if (ks == 13 && by == 32768) continue;
-                const double t = time_plan(p, pc, std::min(ks, matvec_ksmall_limit()), by, es);
+                if (ks == dflt.ksmall && by == dflt.small_bytes) continue;
+                const double t = time_plan(p, pc, std::min(ks, matvec_ksmall_limit()), by, dflt.ns, 1, es);
                 if (t < best) {
                     best = t;
                     best_ks = ks;
                     best_by = by;
                 }
             }
+        int best_ns = dflt.ns, best_y = 1;
+        for (int ns = 4; ns <= 6 && p.opt.pipeline_stages == 0; ++ns)
+            for (int y = pc ? 0 : 1; y >= 0; --y) {
+                if (ns == dflt.ns && (y == 1 || pc)) continue;  // timed above
+                const double t = time_plan(p, pc, best_ks, best_by, ns, y, es);
+                if (t < best) {
+                    best = t;
+                    best_ns = ns;
+                    best_y = y;
+                }
+            }
         Problem::TilePlan& plan = pc ? p.pc_plan : p.mv_plan;
-        plan.ksmall = best_ks;
-        plan.small_bytes = best_by;
-        plan_tiles(p, pc);
+        if (plan.ksmall != best_ks || plan.small_bytes != best_by) {
+            plan.ksmall = best_ks;
+            plan.small_bytes = best_by;
+            plan_tiles(p, pc);
+        }
+        plan.ns = best_ns;
+        plan.y_smem = best_y;
         if (rep && !pc) {
             rep->ksmall = best_ks;
             rep->small_bytes = best_by;
             rep->matvec_ms = best;
             rep->default_ms = def;
+            rep->ns = p.opt.pipeline_stages ? p.opt.pipeline_stages : best_ns;
+            rep->y_smem = matvec_y_in_smem(p) ? 1 : 0;
         }
         if (rep && pc) {
             rep->pc_ksmall = best_ks;
             rep->pc_small_bytes = best_by;
+            rep->pc_ns = p.opt.pipeline_stages ? p.opt.pipeline_stages : best_ns;
         }
     }
     destroy_graph(p);  // the captured launches hold the old plan
@@ -568,7 +595,8 @@ void create_problem(Problem& p, const double* cams, int32_t n_cam, const double*
     require(n_obs < ((int64_t)1 << 31) - 1, BA_ERR_INVALID_ARG, "too many observations (limit 2^31 - 2)");
     ba_default_options(&p.opt);
     if (opt) p.opt = *opt;
-    require(p.opt.lambda0 > 0 && p.opt.max_lm_iters >= 1 && p.opt.max_cg_iters >= 1 && p.opt.cg_eta > 0,
+    require(p.opt.lambda0 > 0 && p.opt.max_lm_iters >= 1 && p.opt.max_cg_iters >= 1 && p.opt.cg_eta > 0 &&
+            (p.opt.pipeline_stages == 0 || (p.opt.pipeline_stages >= 4 && p.opt.pipeline_stages <= 6)),
             BA_ERR_INVALID_ARG, "invalid options");
     p.n_cam = n_cam;
     p.n_pt = n_pt;
@@ -1030,11 +1058,12 @@ ba_status ba_set_params(ba_problem* h, const double* cams, const double* pts) {
 ba_status ba_set_options(ba_problem* h, const ba_options* opt) {
     if (!h || !opt) return BA_ERR_INVALID_ARG;
     API_TRY
-    require(opt->lambda0 > 0 && opt->max_lm_iters >= 1 && opt->max_cg_iters >= 1 && opt->cg_eta > 0,
+    require(opt->lambda0 > 0 && opt->max_lm_iters >= 1 && opt->max_cg_iters >= 1 && opt->cg_eta > 0 &&
+            (opt->pipeline_stages == 0 || (opt->pipeline_stages >= 4 && opt->pipeline_stages <= 6)),
             BA_ERR_INVALID_ARG, "invalid options");
     Problem& p = h->p;
     sync(p);
-    const bool graph_change = opt->use_graph != p.opt.use_graph;
+    const bool graph_change = opt->use_graph != p.opt.use_graph || opt->pipeline_stages != p.opt.pipeline_stages;
     p.opt = *opt;
     if (graph_change) destroy_graph(p);
     return BA_OK;

@@ -29,7 +29,6 @@ namespace sqrtba {
 
 namespace {
 
-constexpr int MV_STAGES = 4;
 constexpr int MV_STAGE_A = 32768;   // bytes of blocks per stage
 constexpr int MV_STAGE_C = 1024;    // bytes of camera indices per stage
 // Registers are split over the SM's four sub-partitions (16K each) and the
@@ -54,6 +53,7 @@ struct Layout {
     static constexpr int ACC_OFF = FLAG_OFF + 16;
 };
 constexpr int SMEM_LIMIT = 227 * 1024;
+static_assert(Layout<6>::ACC_OFF <= SMEM_LIMIT, "six stages fit the opt-in shared memory");
 
 enum : int16_t { TILE_SMALL = 0, TILE_BIG = 1, TILE_GLOBAL = 2 };
 
@@ -101,6 +101,8 @@ struct SmallShape {
 };
 
 // One tile of `count` blocks with k = K; consumer warp cw of MV_CONSUMERS.
+// Teams past the tile's last block read its first block (finite data) with
+// v = 0, so they add nothing; their y is not written.
 template <int K>
 __device__ __forceinline__ void small_tile(const float* __restrict__ sa, const int32_t* __restrict__ sc, int count,
                                            const float* __restrict__ v, float* __restrict__ yt, int cw, int lane) {
@@ -143,7 +145,7 @@ __device__ __forceinline__ void small_tile(const float* __restrict__ sa, const i
 #pragma unroll
                     for (int m = 0; m < S::NM; ++m) {
                         const int col = t + S::W * m;
-                        a[q][m] = (active && r0 + q < S::NR && col < S::NC) ? blk[(r0 + q) * S::NC + col] : 0.f;
+                        a[q][m] = (r0 + q < S::NR && col < S::NC) ? blk[(r0 + q) * S::NC + col] : 0.f;
                         pr[q] += a[q][m] * vr[m];
                     }
                 }
@@ -177,7 +179,7 @@ __device__ __forceinline__ void small_tile(const float* __restrict__ sa, const i
 #pragma unroll
                 for (int m = 0; m < S::NM; ++m) {
                     const int col = t + S::W * m;
-                    a[m] = (active && col < S::NC) ? blk[r * S::NC + col] : 0.f;
+                    a[m] = col < S::NC ? blk[r * S::NC + col] : 0.f;
                     part += a[m] * vr[m];
                 }
 #pragma unroll
@@ -536,8 +538,31 @@ __global__ void k_add_damping(int n, const float* __restrict__ dp2, float lam, c
     if (i < n) y[i] += lam * dp2[i] * v[i];
 }
 
-bool smem_y(const Problem& p) { return Layout<MV_STAGES>::ACC_OFF + 36 * (int64_t)p.n_cam <= SMEM_LIMIT; }
-size_t smem_bytes(const Problem& p) { return Layout<MV_STAGES>::ACC_OFF + (smem_y(p) ? 36 * (size_t)p.n_cam : 0); }
+// Pipeline depths built: 4, 5 and 6 stages of 32 KB (the planner's tiles do
+// not depend on the depth; the autotuner picks it per plan).
+int acc_off(int ns) { return ns == 6 ? Layout<6>::ACC_OFF : ns == 5 ? Layout<5>::ACC_OFF : Layout<4>::ACC_OFF; }
+bool y_fits(const Problem& p, int ns) { return acc_off(ns) + 36 * (int64_t)p.n_cam <= SMEM_LIMIT; }
+// the depth in use: the plan's, unless the options force one
+int depth(const Problem& p, const Problem::TilePlan& plan) {
+    return p.opt.pipeline_stages ? p.opt.pipeline_stages : plan.ns;
+}
+// y is accumulated in shared memory when the plan asks for it and it fits
+bool smem_y(const Problem& p, const Problem::TilePlan& plan) { return plan.y_smem && y_fits(p, depth(p, plan)); }
+size_t smem_bytes(const Problem& p, const Problem::TilePlan& plan, bool pc) {
+    return acc_off(depth(p, plan)) + (!pc && smem_y(p, plan) ? 36 * (size_t)p.n_cam : 0);
+}
+
+using MvKernel = void (*)(MvArgs);
+template <int NS>
+MvKernel kernel_ns(bool pc, bool y) {
+    if (pc) return k_matvec_tiles<MODE_PRECOND, false, NS>;
+    return y ? k_matvec_tiles<MODE_MATVEC, true, NS> : k_matvec_tiles<MODE_MATVEC, false, NS>;
+}
+MvKernel pick_kernel(const Problem& p, const Problem::TilePlan& plan, bool pc) {
+    const bool y = !pc && smem_y(p, plan);
+    const int ns = depth(p, plan);
+    return ns == 6 ? kernel_ns<6>(pc, y) : ns == 5 ? kernel_ns<5>(pc, y) : kernel_ns<4>(pc, y);
+}
 
 MvArgs make_args(Problem& p, const Problem::TilePlan& plan, const float* v, float* y, const PcgScalars* S) {
     return MvArgs{static_cast<const MvTile*>(plan.tiles), plan.begin, p.apool, p.mv_cam, p.lm_by_k, p.pt_off,
@@ -563,7 +588,8 @@ void plan_tiles(Problem& p, bool pc) {
     const int ksmall = std::min(plan.ksmall, MV_KSMALL_MAX);
     const int small_bytes = std::min(plan.small_bytes, MV_STAGE_A);
     plan.n_obs_split = 0;
-    for (int b = 0; b <= kmax && kmax - b > ksmall; ++b)
+    auto whole = [&](int k) { return k <= ksmall && 4 * pad4(18LL * k * k) <= MV_STAGE_A; };
+    for (int b = 0; b <= kmax && !whole(kmax - b); ++b)
         if (big_tile_rows(kmax - b) < 2 * (kmax - b)) plan.n_obs_split = p.run_co[b + 1];
     for (int b = 0; b <= kmax; ++b) {
         const int k = kmax - b;
@@ -575,7 +601,7 @@ void plan_tiles(Problem& p, bool pc) {
             for (int bb = 0; bb < b; ++bb) q += p.k_run_count[bb];
             return q;
         }();
-        if (k <= ksmall) {
+        if (whole(k)) {  // a whole block must fit one stage
             const int64_t per = std::max<int64_t>(1, small_bytes / (4 * bf));
             for (int64_t l = 0; l < cnt; l += per) {
                 MvTile t{};
@@ -654,22 +680,23 @@ void plan_matvec(Problem& p) {
 
 int matvec_ctas_per_sm() { return 1; }
 int matvec_ksmall_limit() { return MV_KSMALL_MAX; }
+bool matvec_y_in_smem(const Problem& p) { return smem_y(p, p.mv_plan); }
 int matvec_stage_bytes() { return MV_STAGE_A; }
 
-void configure_matvec(Problem& p) {
-    const int sm = (int)smem_bytes(p);
-    BA_CUDA_TRY(cudaFuncSetAttribute(k_matvec_tiles<MODE_MATVEC, true, MV_STAGES>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    BA_CUDA_TRY(cudaFuncSetAttribute(k_matvec_tiles<MODE_MATVEC, false, MV_STAGES>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    BA_CUDA_TRY(cudaFuncSetAttribute(k_matvec_tiles<MODE_PRECOND, false, MV_STAGES>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Layout<MV_STAGES>::ACC_OFF));
+void configure_matvec(Problem&) {
+    // every variant may take the whole opt-in shared memory: the attribute is
+    // per kernel, not per problem, so it must hold for any problem's plan
+    for (int ns = 4; ns <= 6; ++ns)
+        for (int v = 0; v < 3; ++v) {
+            const MvKernel k = ns == 6 ? kernel_ns<6>(v == 2, v == 1) : ns == 5 ? kernel_ns<5>(v == 2, v == 1)
+                                                                          : kernel_ns<4>(v == 2, v == 1);
+            BA_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT));
+        }
 }
 
 void launch_matvec_raw(Problem& p, const float* v, float* y, const PcgScalars* S) {
     const MvArgs a = make_args(p, p.mv_plan, v, y, S);
-    if (smem_y(p)) k_matvec_tiles<MODE_MATVEC, true, MV_STAGES><<<p.mv_grid, MV_THREADS, smem_bytes(p), p.stream>>>(a);
-    else k_matvec_tiles<MODE_MATVEC, false, MV_STAGES><<<p.mv_grid, MV_THREADS, smem_bytes(p), p.stream>>>(a);
+    pick_kernel(p, p.mv_plan, false)<<<p.mv_grid, MV_THREADS, smem_bytes(p, p.mv_plan, false), p.stream>>>(a);
     BA_LAUNCH_CHECK();
 }
 
@@ -681,7 +708,7 @@ void launch_precond_records(Problem& p) {
     const MvArgs a = make_args(p, p.pc_plan, nullptr, nullptr, nullptr);
     if (p.pc_plan.n_obs_split > 0)
         BA_CUDA_TRY(cudaMemsetAsync(p.prec, 0, sizeof(float) * REC_STRIDE * p.pc_plan.n_obs_split, p.stream));
-    k_matvec_tiles<MODE_PRECOND, false, MV_STAGES><<<p.mv_grid, MV_THREADS, Layout<MV_STAGES>::ACC_OFF, p.stream>>>(a);
+    pick_kernel(p, p.pc_plan, true)<<<p.mv_grid, MV_THREADS, smem_bytes(p, p.pc_plan, true), p.stream>>>(a);
     BA_LAUNCH_CHECK();
 }
 

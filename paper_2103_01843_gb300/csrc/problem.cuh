@@ -137,9 +137,11 @@ struct Problem {
         void* tiles = nullptr;           // MvTile[n]
         int32_t* begin = nullptr;        // first tile of each CTA (grid + 1)
         int n = 0, cap = 0;
-        int ksmall = 13;
+        int ksmall = 21;
         int small_bytes = 32768;
         int64_t n_obs_split = 0;         // observations of blocks split into row tiles (first in storage order)
+        int ns = 6;                      // pipeline depth (4, 5 or 6 stages)
+        int y_smem = 1;                  // matvec: accumulate y in shared memory where it fits
     };
     TilePlan mv_plan, pc_plan;
     int mv_grid = 0;
@@ -246,6 +248,7 @@ void plan_matvec(Problem& p);
 void plan_tiles(Problem& p, bool pc);
 // planner limits: largest mv_ksmall, largest mv_small_bytes
 int matvec_ksmall_limit();
+bool matvec_y_in_smem(const Problem& p);  // the matvec plan in use accumulates y in shared memory
 int matvec_stage_bytes();
 
 // kernel launch counter (not counted while a graph is being captured)

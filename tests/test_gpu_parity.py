@@ -318,6 +318,32 @@ def test_many_cameras_records_path(pkg):
     assert rel_fro(Y, oracle.rcs_matvec(s, lam, V)) < 1e-4
 
 
+@pytest.mark.parametrize("stages", [4, 5, 6])
+def test_pipeline_depths(pkg, heavy, stages):
+    """Every depth of the K3 / K4 tile pipeline gives the same reduced system:
+    with 700 cameras y is accumulated in shared memory at 4 and 5 stages and
+    in global memory at 6 (it no longer fits beside six stages)."""
+    many = make_scene("small", 9, n_cam=700, n_pt=2500, p=0.25, cap=40)
+    for sc, lam in ((heavy, 1e-3), (many, 1e-2)):
+        s = Rounded(sc)
+        with pkg.Problem.from_scene(sc, pipeline_stages=stages) as p:
+            p.linearize()
+            p.marginalize_qr(lam)
+            p.pcg_solve()
+            M, g = p.export_rcs_diag()
+            V = np.random.default_rng(stages).normal(size=(2, 9 * s.n_cam)).astype(np.float32)
+            Y = np.stack([p.matvec(v) for v in V])
+        Mref, bt = oracle.rcs_diag(s, lam)
+        assert rel_fro(M, Mref) < 1e-4, (stages, rel_fro(M, Mref))
+        assert rel_fro(g, -bt) < 1e-4
+        assert rel_fro(Y, oracle.rcs_matvec(s, lam, V)) < 1e-4, (stages, rel_fro(Y, oracle.rcs_matvec(s, lam, V)))
+
+
+def test_invalid_pipeline_depth_is_rejected(pkg, tiny):
+    with pytest.raises(Exception):
+        pkg.Problem.from_scene(tiny, pipeline_stages=3)
+
+
 def test_pcg_solution_and_back_substitution(pkg, tiny):
     s = Rounded(tiny)
     lam = 1e-3
