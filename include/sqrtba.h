@@ -275,7 +275,8 @@ SQRTBA_API ba_status ba_eval_cost_noalloc(const float* d_cams, int32_t n_cam, co
  * events on the problem's stream), keeps the fastest plan of each, then
  * times that plan with 4, 5 and 6 pipeline stages (the matvec also with y
  * accumulated in global instead of shared memory) and keeps the fastest
- * depth.  It reports the choices.  The paper parallelises over landmarks with a parallel-for
+ * depth, then (when some blocks are cut into row tiles) the largest k whose
+ * row tiles take eight rows a warp.  It reports the choices.  The paper parallelises over landmarks with a parallel-for
  * (Sec. 6.1) and has no tuner.
  * Errors: BA_ERR_STATE if the blocks are not marginalised. */
 typedef struct {
@@ -290,7 +291,8 @@ typedef struct {
     int32_t y_smem;       /* 1: the matvec accumulates y in shared memory (0: in global memory,
                              chosen, or y does not fit beside the stages) */
     int32_t pc_ns;        /* chosen pipeline depth of the record pass */
-    int32_t reserved;
+    int32_t big8_kmax;    /* matvec row tiles (blocks too large for one stage) with k up to
+                             this take eight rows a warp, larger ones four */
 } ba_tune_report;
 SQRTBA_API ba_status ba_autotune(ba_problem* h, ba_tune_report* report);
 

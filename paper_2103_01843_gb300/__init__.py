@@ -82,7 +82,7 @@ class TuneReport(ctypes.Structure):
                 ("matvec_ms", ctypes.c_double), ("default_ms", ctypes.c_double),
                 ("tune_ms", ctypes.c_double), ("pc_ksmall", ctypes.c_int32),
                 ("pc_small_bytes", ctypes.c_int32), ("ns", ctypes.c_int32), ("y_smem", ctypes.c_int32),
-                ("pc_ns", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("pc_ns", ctypes.c_int32), ("big8_kmax", ctypes.c_int32)]
 
 
 class ProblemDesc(ctypes.Structure):

@@ -275,8 +275,9 @@ struct EventSet {
 // median of five timed launches of the matvec (pc = false) or of the
 // preconditioner record pass (pc = true) with the plan (ksmall, bytes) at
 // pipeline depth ns (y in shared memory where y_smem and it fits)
-double time_plan(Problem& p, bool pc, int ksmall, int bytes, int ns, int y_smem, EventSet& es) {
+double time_plan(Problem& p, bool pc, int ksmall, int bytes, int ns, int y_smem, EventSet& es, int big8 = -1) {
     Problem::TilePlan& plan = pc ? p.pc_plan : p.mv_plan;
+    if (big8 >= 0) plan.big8_kmax = big8;
     if (plan.ksmall != ksmall || plan.small_bytes != bytes || plan.n == 0) {
         plan.ksmall = ksmall;
         plan.small_bytes = bytes;
@@ -306,7 +307,8 @@ double time_plan(Problem& p, bool pc, int ksmall, int bytes, int ns, int y_smem,
 // for the matvec and for the record pass at the default depth (6 stages, y
 // in shared memory where it fits), keeps the fastest of each, then times that
 // plan at depths 4, 5 and 6 (the matvec also with y in global memory) and
-// keeps the fastest depth.
+// keeps the fastest depth; last, for a matvec plan with row tiles, the
+// largest k whose row tiles take eight rows a warp (0, 32, 40, 64, all).
 void run_autotune(Problem& p, ba_tune_report* rep) {
     require(p.damped, BA_ERR_STATE, "ba_autotune: blocks are not marginalised (call ba_marginalize_qr)");
     const auto t0 = std::chrono::steady_clock::now();
@@ -315,6 +317,7 @@ void run_autotune(Problem& p, ba_tune_report* rep) {
     const int ks_opts[3] = {8, 13, 21};
     const int by_opts[3] = {8192, 16384, 32768};
     const Problem::TilePlan dflt{};
+    p.mv_plan.big8_kmax = dflt.big8_kmax;
     double def = 0.0;
     for (int pc = 0; pc < 2; ++pc) {
         double best = time_plan(p, pc, dflt.ksmall, dflt.small_bytes, dflt.ns, 1, es);
@@ -341,7 +344,18 @@ void run_autotune(Problem& p, ba_tune_report* rep) {
                     best_y = y;
                 }
             }
+        // matvec row tiles: the largest k that takes eight rows a warp
+        int best_b8 = dflt.big8_kmax;
+        if (!pc && p.k_max > std::min(best_ks, matvec_ksmall_limit()))
+            for (int b8 : {0, 32, 64, 1 << 20}) {
+                const double t = time_plan(p, pc, best_ks, best_by, best_ns, best_y, es, b8);
+                if (t < best) {
+                    best = t;
+                    best_b8 = b8;
+                }
+            }
         Problem::TilePlan& plan = pc ? p.pc_plan : p.mv_plan;
+        plan.big8_kmax = best_b8;
         if (plan.ksmall != best_ks || plan.small_bytes != best_by) {
             plan.ksmall = best_ks;
             plan.small_bytes = best_by;
@@ -356,6 +370,7 @@ void run_autotune(Problem& p, ba_tune_report* rep) {
             rep->default_ms = def;
             rep->ns = p.opt.pipeline_stages ? p.opt.pipeline_stages : best_ns;
             rep->y_smem = matvec_y_in_smem(p) ? 1 : 0;
+            rep->big8_kmax = best_b8;
         }
         if (rep && pc) {
             rep->pc_ksmall = best_ks;

@@ -89,6 +89,7 @@ struct MvArgs {
     uint32_t* err;
     const float* cpool;  // preconditioner mode: c_j in storage order
     float* rec;          // preconditioner mode: REC floats per observation (storage order)
+    int big8_kmax;       // big tiles with k up to this take eight rows a warp (else four)
 };
 
 // --- consumers ---------------------------------------------------------------------
@@ -297,12 +298,15 @@ __device__ __forceinline__ void small_dispatch(int k, const float* sa, const int
 }
 
 // Rows [r0, r0 + nrows) of one block with k > MV_KSMALL, staged in sa.  Each
-// warp owns BIG_RPW consecutive rows (no cross-warp dependency): u_r for its
-// rows over all columns, with v gathered once per column chunk for all of
-// its rows, then its rows' contribution A[r, col] u_r to every column.  A
-// tile keeps ceil(nrows / BIG_RPW) warps busy; tiles rotate over the warps.
-constexpr int BIG_RPW = 4;   // rows per warp
+// warp owns RPW (4 or 8) consecutive rows (no cross-warp dependency): u_r
+// for its rows over all columns, with v gathered once per column chunk for
+// all of its rows, then its rows' contribution A[r, col] u_r to every column.
+// A tile keeps ceil(nrows / RPW) warps busy; tiles rotate over the warps.
+// Eight rows a warp halve the y updates and v gathers per row; four spread a
+// short tile (large k) over more warps.  The plan sets the largest k that
+// takes eight (big8_kmax).
 constexpr int BIG_CH = 4;    // columns per lane per chunk
+template <int BIG_RPW>
 __device__ __forceinline__ void big_tile(const float* __restrict__ sa, const int32_t* __restrict__ sc, int k,
                                          int nrows, const float* __restrict__ v, float* __restrict__ yt, int vcw,
                                          int lane) {
@@ -379,7 +383,7 @@ __device__ void global_block(const MvArgs& a, int pos, float* __restrict__ ub, f
 }
 
 // consumer warps a tile keeps busy (at most MV_CONSUMERS)
-__device__ __forceinline__ int tile_warps(const MvTile& t, int mode) {
+__device__ __forceinline__ int tile_warps(const MvTile& t, int mode, int big8_kmax) {
     int w;
     if (mode == MODE_MATVEC) {
         if (t.kind == TILE_SMALL) {
@@ -387,7 +391,8 @@ __device__ __forceinline__ int tile_warps(const MvTile& t, int mode) {
             const int tpw = nc <= 32 ? 4 : (nc <= 64 ? 2 : 1);
             w = (t.count + tpw - 1) / tpw;
         } else if (t.kind == TILE_BIG) {
-            w = (t.count + BIG_RPW - 1) / BIG_RPW;
+            const int rpw = t.k <= big8_kmax ? 8 : 4;
+            w = (t.count + rpw - 1) / rpw;
         } else {
             w = 1;
         }
@@ -505,11 +510,13 @@ __global__ void __launch_bounds__(MV_THREADS, 1) k_matvec_tiles(MvArgs a) {
             // A tile rarely needs all consumer warps; successive tiles start at
             // successive groups of warps (rotation by the warps the tile needs),
             // so that the tiles in flight are worked on by disjoint warps.
-            const int need = tile_warps(tile, MODE);
+            const int need = tile_warps(tile, MODE, a.big8_kmax);
             const int vcw = (cw + MV_CONSUMERS - (i * need) % MV_CONSUMERS) % MV_CONSUMERS;
             if (MODE == MODE_MATVEC) {
                 if (tile.kind == TILE_SMALL) small_dispatch(tile.k, sa, sc, tile.count, a.v, yt, vcw, lane);
-                else if (tile.kind == TILE_BIG) big_tile(sa, sc, tile.k, tile.count, a.v, yt, vcw, lane);
+                else if (tile.kind == TILE_BIG && tile.k <= a.big8_kmax)
+                    big_tile<8>(sa, sc, tile.k, tile.count, a.v, yt, vcw, lane);
+                else if (tile.kind == TILE_BIG) big_tile<4>(sa, sc, tile.k, tile.count, a.v, yt, vcw, lane);
                 else if (vcw == 0) global_block(a, tile.first, ub, yt, lane);
             } else {
                 const int tid = vcw * 32 + lane;
@@ -566,7 +573,7 @@ MvKernel pick_kernel(const Problem& p, const Problem::TilePlan& plan, bool pc) {
 
 MvArgs make_args(Problem& p, const Problem::TilePlan& plan, const float* v, float* y, const PcgScalars* S) {
     return MvArgs{static_cast<const MvTile*>(plan.tiles), plan.begin, p.apool, p.mv_cam, p.lm_by_k, p.pt_off,
-                  p.obs_cam_s, p.a_off, v, y, p.n_cam, S, p.err, p.cpool, p.prec};
+                  p.obs_cam_s, p.a_off, v, y, p.n_cam, S, p.err, p.cpool, p.prec, plan.big8_kmax};
 }
 
 }  // namespace
@@ -617,7 +624,10 @@ void plan_tiles(Problem& p, bool pc) {
             }
         } else if (k <= MV_KBIG) {
             const int nc = 9 * k, nr = 2 * k;
-            const int rows = big_tile_rows(k);
+            // the fewest row tiles that fit a stage, of near-equal size
+            // (multiples of 4 rows keep every tile 16-byte aligned)
+            const int maxr = big_tile_rows(k), nt = (nr + maxr - 1) / maxr;
+            const int rows = std::min(maxr, ((nr + nt - 1) / nt + 3) & ~3);
             for (int64_t l = 0; l < cnt; ++l) {
                 for (int r0 = 0; r0 < nr; r0 += rows) {
                     MvTile t{};

@@ -142,6 +142,7 @@ struct Problem {
         int64_t n_obs_split = 0;         // observations of blocks split into row tiles (first in storage order)
         int ns = 6;                      // pipeline depth (4, 5 or 6 stages)
         int y_smem = 1;                  // matvec: accumulate y in shared memory where it fits
+        int big8_kmax = 40;              // matvec: row tiles with k up to this take 8 rows a warp (else 4)
     };
     TilePlan mv_plan, pc_plan;
     int mv_grid = 0;

@@ -119,6 +119,7 @@ def test_autotune_single_problem(pkg, members):
         t = p.autotune()
         assert t["ksmall"] in (8, 13, 21) and t["small_bytes"] in (8192, 16384, 32768)
         assert t["ns"] in (4, 5, 6) and t["pc_ns"] in (4, 5, 6) and t["y_smem"] in (0, 1)
+        assert t["big8_kmax"] in (0, 32, 40, 64, 1 << 20)
         assert 0 < t["matvec_ms"] <= t["default_ms"]
         # the re-planned matvec is the same operator
         v = np.random.default_rng(0).standard_normal(9 * s.cams.shape[0]).astype(np.float32)
