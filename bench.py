@@ -308,8 +308,11 @@ def run_ours(args):
         # read the observations (12 B each), points and cameras
         "linearize": 4.0 * (18.0 * sum_k2 + 35.0 * n_obs + 12.0 * n_pt) + 12.0 * n_obs + 12.0 * n_pt
         + 36.0 * n_cam,
-        # K3: read A_j and c_j once, write 90 floats per camera
-        "precond": 4.0 * (18.0 * sum_k2 + 2.0 * n_obs) + 4.0 * 90 * n_cam,
+        # K3 (Gram form): per observation its camera-list entry, landmark index,
+        # measurement, landmark offsets and point (36 B) and its 3 x 9 slice and
+        # residual column of the top rows (120 B); per camera its frame and
+        # D_p^2 read, the block, its inverse and g written (4 (16 + 9 + 171) B)
+        "precond": 156.0 * n_obs + 4.0 * 196 * n_cam,
     }
     kernels = {}
     for name in ("linearize", "damp", "precond", "matvec", "backsub", "cost"):

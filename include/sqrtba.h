@@ -78,7 +78,11 @@ typedef struct {
                              depths the autotuner chose; 4, 5 or 6 forces that depth */
     double target_cost;   /* > 0: the LM also stops after an accepted step whose cost is
                              <= target_cost (e.g. the f_tau of a tolerance test); default 0 */
-    int32_t reserved[2];  /* zero */
+    int32_t precond_from_blocks; /* 0 (default): the block-Jacobi blocks and g come from the
+                             Gram identity (J_s^T J_s - T_s^T T_s per observation, see
+                             ba_pcg_solve); 1: summed from the stored blocks A_j, as the
+                             matvec reads them */
+    int32_t reserved;     /* zero */
 } ba_options;
 
 /* Fills *opt with the defaults above. */
@@ -143,9 +147,17 @@ SQRTBA_API ba_status ba_marginalize_qr(ba_problem* h, double lambda);
 
 /* Solves the damped reduced camera system H~ dx_p = -b~ with block-Jacobi
  * PCG (Sec. 5.4, Eq. cg_mult; Sec. 6.1): builds the per-camera 9x9 blocks of
- * H~ from the landmark blocks, then iterates the matvec
+ * H~ and g = -b~, then iterates the matvec
  * (Q2^T J_p)^T (Q2^T J_p v) + lambda D_p^2 v.  Stops by the Nash-Sofer test
  * with cg_eta, ||r|| <= 1e-10 ||g||, or max_cg_iters.  report may be NULL.
+ * The blocks are sum_j A_ji^T A_ji over the landmarks camera i observes, and
+ * b~_i = sum_j A_ji^T c_j (Eq. red_H, red_b).  The QR and Givens transforms
+ * keep the Gram matrix of a block's pose and residual columns, so each term
+ * equals J_s^T J_s - T_s^T T_s (and J_s^T r_s - T_s^T t) with J_s, r_s the
+ * observation's Jacobian rows and residuals and T_s, t its columns of the
+ * damped top rows [Q1^T J_p | R1 | Q1^T r]; by default the blocks are formed
+ * that way (30 floats read per observation), with precond_from_blocks = 1
+ * from the stored A_j and c_j (18 k floats per observation).
  * Errors: BA_ERR_STATE if not marginalised. */
 SQRTBA_API ba_status ba_pcg_solve(ba_problem* h, ba_pcg_report* report);
 

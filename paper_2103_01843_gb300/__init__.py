@@ -41,7 +41,7 @@ class Options(ctypes.Structure):
                 ("cg_eta", ctypes.c_double), ("use_graph", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("use_learned", ctypes.c_int32),
                 ("pipeline_stages", ctypes.c_int32), ("target_cost", ctypes.c_double),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("precond_from_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class PcgReport(ctypes.Structure):

@@ -319,7 +319,13 @@ void run_autotune(Problem& p, ba_tune_report* rep) {
     const Problem::TilePlan dflt{};
     p.mv_plan.big8_kmax = dflt.big8_kmax;
     double def = 0.0;
-    for (int pc = 0; pc < 2; ++pc) {
+    if (rep) {  // the record pass's plan as it stands (replaced below when it is tuned)
+        rep->pc_ksmall = p.pc_plan.ksmall;
+        rep->pc_small_bytes = p.pc_plan.small_bytes;
+        rep->pc_ns = p.opt.pipeline_stages ? p.opt.pipeline_stages : p.pc_plan.ns;
+    }
+    // the record pass runs only when the blocks are summed from A_j
+    for (int pc = 0; pc < (p.opt.precond_from_blocks ? 2 : 1); ++pc) {
         double best = time_plan(p, pc, dflt.ksmall, dflt.small_bytes, dflt.ns, 1, es);
         if (!pc) def = best;
         int best_ks = dflt.ksmall, best_by = dflt.small_bytes;
@@ -700,7 +706,6 @@ void create_problem(Problem& p, const double* cams, int32_t n_cam, const double*
     p.q = dalloc<float>(p, nv);
     p.minv = dalloc<float>(p, 81 * (int64_t)n_cam);
     p.mdiag = dalloc<float>(p, 81 * (int64_t)n_cam);
-    p.prec = dalloc<float>(p, 56 * n_obs);
     p.dl = dalloc<float>(p, 3 * (int64_t)n_pt);
     p.partials = dalloc<double>(p, 2LL * p.red_grid + 2);
     BA_CUDA_TRY(cudaMemsetAsync(p.x, 0, sizeof(float) * nv, p.stream));

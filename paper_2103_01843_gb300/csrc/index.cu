@@ -281,6 +281,17 @@ __global__ void k_map_list(int64_t n, const int32_t* __restrict__ list, const in
         out[e] = map[list[e]];
 }
 
+__global__ void k_chunk_count(int n_cam, const int32_t* __restrict__ cam_off, int32_t* __restrict__ cnt) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n_cam) cnt[c] = (cam_off[c + 1] - cam_off[c] + PG_CHUNK - 1) / PG_CHUNK;
+}
+
+__global__ void k_chunk_fill(int n_cam, const int32_t* __restrict__ chunk_off, int32_t* __restrict__ chunk_cam) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_cam) return;
+    for (int q = chunk_off[c]; q < chunk_off[c + 1]; ++q) chunk_cam[q] = c;
+}
+
 }  // namespace
 
 void build_index(Problem& p, const int32_t* d_oc, const int32_t* d_op, const double* d_xy,
@@ -402,6 +413,18 @@ void build_index(Problem& p, const int32_t* d_oc, const int32_t* d_op, const dou
     k_storage<<<ceil_div(p.n_pt, 256), 256, 0, st>>>(p.n_pt, p.lm_by_k, kcount, kmax, ko, d_run, d_run + kmax + 2,
                                                      p.pt_off, p.obs_cam_s, p.a_off, p.mv_cam, p.c_off, obs_store);
     k_map_list<<<gsz, TPB, 0, st>>>(n, p.cam_list, obs_store, p.cam_list_st);
+    BA_LAUNCH_CHECK();
+
+    // chunks of the camera lists for the Gram-form preconditioner
+    int32_t* nch = (int32_t*)tmp_alloc(sizeof(int32_t) * (p.n_cam + 1));
+    k_chunk_count<<<ceil_div(p.n_cam, 256), 256, 0, st>>>(p.n_cam, p.cam_off, nch);
+    p.pg_chunk_off = dalloc<int32_t>(p, p.n_cam + 1);
+    exclusive_scan(nch, p.n_cam, p.pg_chunk_off, scan_tmp, st);
+    BA_CUDA_TRY(cudaMemcpyAsync(&p.pg_chunks, p.pg_chunk_off + p.n_cam, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    BA_CUDA_TRY(cudaStreamSynchronize(st));
+    p.pg_chunk_cam = dalloc<int32_t>(p, p.pg_chunks);
+    p.pg_part = dalloc<float>(p, 56LL * p.pg_chunks);
+    k_chunk_fill<<<ceil_div(p.n_cam, 256), 256, 0, st>>>(p.n_cam, p.pg_chunk_off, p.pg_chunk_cam);
     BA_LAUNCH_CHECK();
 
     BA_CUDA_TRY(cudaStreamSynchronize(st));

@@ -715,6 +715,7 @@ void launch_matvec_raw(Problem& p, const float* v, float* y, const PcgScalars* S
 // storage order.  Records of blocks split over row tiles are accumulated, so
 // their prefix is zeroed first.
 void launch_precond_records(Problem& p) {
+    if (!p.prec) p.prec = dalloc<float>(p, REC_STRIDE * p.n_obs);  // on first use
     const MvArgs a = make_args(p, p.pc_plan, nullptr, nullptr, nullptr);
     if (p.pc_plan.n_obs_split > 0)
         BA_CUDA_TRY(cudaMemsetAsync(p.prec, 0, sizeof(float) * REC_STRIDE * p.pc_plan.n_obs_split, p.stream));

@@ -126,6 +126,11 @@ struct Problem {
     int32_t* mv_cam = nullptr;       // camera of every observation in storage order
     int32_t* c_off = nullptr;        // float offset of c_j = Q2^T r (storage order, 2k per landmark)
     int32_t* cam_list_st = nullptr;  // camera lists as storage-order observation indices
+    // chunks of at most PG_CHUNK observations of one camera (K3 in Gram form):
+    // camera c owns chunks pg_chunk_off[c] .. pg_chunk_off[c + 1]
+    int32_t *pg_chunk_off = nullptr, *pg_chunk_cam = nullptr;
+    float* pg_part = nullptr;        // REC-sized partial sums per chunk
+    int32_t pg_chunks = 0;
     std::vector<int32_t> k_run_count;  // host: landmarks with k = k_max - b
     std::vector<int64_t> run_off, run_co;  // host: float / observation offset of run b
     // work plans of the tile pipeline: tiles of the block pool streamed
@@ -251,6 +256,8 @@ void plan_tiles(Problem& p, bool pc);
 int matvec_ksmall_limit();
 bool matvec_y_in_smem(const Problem& p);  // the matvec plan in use accumulates y in shared memory
 int matvec_stage_bytes();
+
+constexpr int PG_CHUNK = 256;  // observations per chunk of the Gram-form K3
 
 // kernel launch counter (not counted while a graph is being captured)
 inline void count_launches(Problem& p, int n) {

@@ -283,11 +283,12 @@ def test_heavy_reduced_system_and_matvec(pkg, heavy):
     assert rel_fro(M, Mref) < 1e-4
 
 
-def test_repeated_solves_keep_preconditioner_exact(pkg, heavy):
+@pytest.mark.parametrize("from_blocks", [0, 1])
+def test_repeated_solves_keep_preconditioner_exact(pkg, heavy, from_blocks):
     """Re-damping and re-solving with a new lambda rebuilds the block-Jacobi
     blocks from scratch: no state of an earlier pass may leak into them."""
     s = Rounded(heavy)
-    with pkg.Problem.from_scene(heavy) as p:
+    with pkg.Problem.from_scene(heavy, precond_from_blocks=from_blocks) as p:
         p.linearize()
         for lam in (1e-3, 1e-1, 1e-2, 1e-1):
             p.marginalize_qr(lam)
@@ -298,13 +299,15 @@ def test_repeated_solves_keep_preconditioner_exact(pkg, heavy):
             assert rel_fro(g, -bt) < 1e-4
 
 
-def test_many_cameras_records_path(pkg):
-    """With many cameras the per-camera blocks do not fit the matvec CTA's
-    shared memory: the preconditioner goes through per-observation records."""
+@pytest.mark.parametrize("from_blocks", [0, 1])
+def test_many_cameras_records_path(pkg, from_blocks):
+    """700 cameras: the preconditioner blocks from the Gram identity
+    (J_s^T J_s - T_s^T T_s per observation) and from the stored blocks
+    (per-observation records of the tile pipeline, summed per camera)."""
     sc = make_scene("small", 9, n_cam=700, n_pt=2500, p=0.25, cap=40)
     s = Rounded(sc)
     lam = 1e-3
-    with pkg.Problem.from_scene(sc) as p:
+    with pkg.Problem.from_scene(sc, precond_from_blocks=from_blocks) as p:
         p.linearize()
         for lam in (1e-3, 1e-1):
             p.marginalize_qr(lam)
@@ -342,6 +345,26 @@ def test_pipeline_depths(pkg, heavy, stages):
 def test_invalid_pipeline_depth_is_rejected(pkg, tiny):
     with pytest.raises(Exception):
         pkg.Problem.from_scene(tiny, pipeline_stages=3)
+
+
+@pytest.mark.parametrize("lam", [1e-6, 1e-2, 1e2])
+def test_gram_and_block_preconditioners_agree(pkg, heavy, lam):
+    """Both forms of the block-Jacobi blocks and g (the Gram identity and the
+    sum over the stored blocks) against each other and the oracle, from weak
+    to strong damping."""
+    s = Rounded(heavy)
+    out = []
+    for fb in (0, 1):
+        with pkg.Problem.from_scene(heavy, precond_from_blocks=fb) as p:
+            p.linearize()
+            p.marginalize_qr(lam)
+            p.pcg_solve()
+            out.append(p.export_rcs_diag())
+    Mref, bt = oracle.rcs_diag(s, lam)
+    for M, g in out:
+        assert rel_fro(M, Mref) < 1e-4, (lam, rel_fro(M, Mref))
+        assert rel_fro(g, -bt) < 1e-4, (lam, rel_fro(g, -bt))
+    assert rel_fro(out[0][0], out[1][0]) < 1e-4
 
 
 def test_pcg_solution_and_back_substitution(pkg, tiny):
