@@ -145,8 +145,8 @@ void free_all(Problem& p) {
     p.pcg_host = nullptr;
     p.dsum_host = nullptr;
     if (p.side) cudaStreamDestroy(p.side);
-    if (p.ev_fork) cudaEventDestroy(p.ev_fork);
-    if (p.ev_join) cudaEventDestroy(p.ev_join);
+    for (cudaEvent_t e : {p.ev_fork, p.ev_join})
+        if (e) cudaEventDestroy(e);
     p.side = nullptr;
     p.ev_fork = p.ev_join = nullptr;
     if (p.own_stream && p.stream) cudaStreamDestroy(p.stream);
@@ -159,7 +159,6 @@ void free_all(Problem& p) {
 void do_linearize(Problem& p, bool need_cost = true, double damp_lambda = 0.0) {
     PhaseTimer t(p, PROF_LINEARIZE);
     launch_frames(p);
-    launch_camera_diag(p);
     launch_linearize(p);
     t.end();
     if (damp_lambda > 0.0) {
@@ -631,8 +630,8 @@ void create_problem(Problem& p, const double* cams, int32_t n_cam, const double*
         p.own_stream = true;
     }
     BA_CUDA_TRY(cudaStreamCreateWithFlags(&p.side, cudaStreamNonBlocking));
-    BA_CUDA_TRY(cudaEventCreateWithFlags(&p.ev_fork, cudaEventDisableTiming));
-    BA_CUDA_TRY(cudaEventCreateWithFlags(&p.ev_join, cudaEventDisableTiming));
+    for (cudaEvent_t* e : {&p.ev_fork, &p.ev_join})
+        BA_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     int dev = 0;
     BA_CUDA_TRY(cudaGetDevice(&dev));
     BA_CUDA_TRY(cudaDeviceGetAttribute(&p.sm_count, cudaDevAttrMultiProcessorCount, dev));
@@ -843,7 +842,6 @@ void do_batch_solve(Problem& p, ba_batch_report* reps, ba_batch_summary* sum) {
         // problem's damping
         PhaseTimer tl(p, PROF_LINEARIZE);
         launch_frames(p);
-        launch_camera_diag(p);
         launch_linearize(p);
         tl.end();
         p.linearized = true;

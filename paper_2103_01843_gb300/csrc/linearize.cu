@@ -484,32 +484,27 @@ void configure_linearize(Problem& p) {
                                      team_smem_bytes<8, 4>()));
 }
 
-void launch_camera_diag(Problem& p) {
-    count_launches(p, 1);
-    k_camera_diag<<<p.n_cam, CD_THREADS, 0, p.stream>>>(p.n_cam, p.frames, p.pts, p.obs_pt_s, p.obs_xy_s, p.cam_off,
-                                                       p.cam_list, p.dp2);
-    BA_LAUNCH_CHECK();
-}
-
+// The K1 kernels work on disjoint landmarks and D_p^2 only reads: D_p^2 and
+// the few long k > 32 factorisations run on a side stream (forked from and
+// joined back into the problem's stream) beside the team kernels, which run
+// one after the other (run side by side they only contend).
 void launch_linearize(Problem& p) {
     LinArgs A{p.frames, p.pts, p.obs_cam_s, p.obs_xy_s, p.pt_off, p.a_off,
               p.apool, p.tpool, p.cpool, p.c_off, p.dl2};
     // segments of lm_by_k: k > 32 | 9..32 | 5..8 | 2..4
     const int n_big = p.n_big, n32 = count_k(p, 8, 32), n16 = count_k(p, 4, 8), n8 = count_k(p, 1, 4);
-    int first = 0;
+    BA_CUDA_TRY(cudaEventRecord(p.ev_fork, p.stream));
+    BA_CUDA_TRY(cudaStreamWaitEvent(p.side, p.ev_fork, 0));
+    // side: D_p^2, then the landmarks with k > 32 (one CTA each)
+    k_camera_diag<<<p.n_cam, CD_THREADS, 0, p.side>>>(p.n_cam, p.frames, p.pts, p.obs_pt_s, p.obs_xy_s, p.cam_off,
+                                                      p.cam_list, p.dp2);
+    count_launches(p, 1);
     if (n_big > 0) {
-        // the few landmarks with k > 32 take one CTA each and run for the
-        // latency of a long sequential factorisation: on a side stream, in
-        // parallel with the team kernels (disjoint landmarks)
-        BA_CUDA_TRY(cudaEventRecord(p.ev_fork, p.stream));
-        BA_CUDA_TRY(cudaStreamWaitEvent(p.side, p.ev_fork, 0));
         const size_t sm = sizeof(float) * lin_smem_floats(p.k_max);
         k_linearize_block<<<n_big, BIG_TEAM, sm, p.side>>>(A, p.lm_by_k, n_big);
         count_launches(p, 1);
-        BA_LAUNCH_CHECK();
-        BA_CUDA_TRY(cudaEventRecord(p.ev_join, p.side));
     }
-    first += n_big;
+    int first = n_big;
     if (n32 > 0) {
         k_linearize_team<32, 32><<<ceil_div(n32, LIN_WARPS), 32 * LIN_WARPS, team_smem_bytes<32, 32>(), p.stream>>>(
             A, p.lm_by_k, first, n32);
@@ -528,7 +523,8 @@ void launch_linearize(Problem& p) {
         count_launches(p, 1);
     }
     BA_LAUNCH_CHECK();
-    if (n_big > 0) BA_CUDA_TRY(cudaStreamWaitEvent(p.stream, p.ev_join, 0));
+    BA_CUDA_TRY(cudaEventRecord(p.ev_join, p.side));
+    BA_CUDA_TRY(cudaStreamWaitEvent(p.stream, p.ev_join, 0));
 }
 
 void launch_export_jacobians(Problem& p, float* r, float* jp, float* jl) {

@@ -7,17 +7,18 @@
 // Blocks are stored by decreasing k, so equal-k blocks are adjacent.  The
 // host plans tiles of the block pool (runs of equal-k blocks up to 32 KB, or
 // 4-row-aligned row ranges of one block when a block is larger); each CTA
-// (one per SM) streams its contiguous range of tiles through a 4-stage ring
-// in shared memory with bulk asynchronous copies (cp.async.bulk + mbarrier),
+// (one per SM) streams its range of tiles through a ring of 4 to 6 stages in
+// shared memory with bulk asynchronous copies (cp.async.bulk + mbarrier),
 // one producer thread and 15 consumer warps.  A tile rarely needs every
-// consumer warp, so successive tiles are handed to successive groups of warps.
+// consumer warp, so successive tiles are handed to successive groups of
+// warps, and a stage is released once the warps of its tile are done.
 //   small tiles (k <= 21): teams of 8/16/32 lanes, one block per team, code
 //     specialised per k; per row u_r = A_j[r,:] v_j (team shuffle reduction)
 //     and y_j += u_r A_j[r,:] (single pass over the block);
 //   big tiles (21 < k <= 222): u for the tile's rows, then column sums;
 //   k > 222: read directly from global memory (two passes).
 // y accumulates in a per-CTA shared copy flushed once per CTA (one atomic per
-// touched entry).  Every wait is bounded (2 s by %globaltimer); on a timeout
+// touched entry) when it fits beside the stages, else in global memory.  Every wait is bounded (2 s by %globaltimer); on a timeout
 // the kernel raises ERRBIT_TIMEOUT, waits for its own copies and returns.
 #include <algorithm>
 #include <vector>
@@ -48,9 +49,9 @@ struct Layout {
     static constexpr int STAGE_R_OFF = STAGE_C_OFF + NS * MV_STAGE_C;
     static constexpr int U_OFF = STAGE_R_OFF + NS * MV_STAGE_R;
     static constexpr int BAR_OFF = (U_OFF + NS * MV_UMAX * 4 + 7) & ~7;
-    static constexpr int DESC_OFF = BAR_OFF + 2 * NS * 8;  // tile record of each stage
-    static constexpr int FLAG_OFF = DESC_OFF + NS * 32;
-    static constexpr int ACC_OFF = FLAG_OFF + 16;
+    static constexpr int FLAG_OFF = BAR_OFF + 2 * NS * 8;
+    static constexpr int SEQ_OFF = FLAG_OFF + 16;          // tile index each stage holds
+    static constexpr int ACC_OFF = SEQ_OFF + 32;
 };
 constexpr int SMEM_LIMIT = 227 * 1024;
 static_assert(Layout<6>::ACC_OFF <= SMEM_LIMIT, "six stages fit the opt-in shared memory");
@@ -416,6 +417,7 @@ __global__ void __launch_bounds__(MV_THREADS, 1) k_matvec_tiles(MvArgs a) {
     static_assert(MODE == MODE_MATVEC || !SMEM_ACC, "records are written to global memory");
     const int acc_n = 9 * a.n_cam;
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L::FLAG_OFF);
+    volatile int* seq = reinterpret_cast<volatile int*>(smem + L::SEQ_OFF);
     const uint32_t bar0 = smem_u32(smem + L::BAR_OFF);
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
     auto empty_bar = [&](int s) { return bar0 + 8u * (MV_STAGES + s); };
@@ -426,6 +428,7 @@ __global__ void __launch_bounds__(MV_THREADS, 1) k_matvec_tiles(MvArgs a) {
             mbar_init(empty_bar(s), MV_CONSUMERS);
         }
         *abort_flag = 0;
+        for (int q = 0; q < MV_STAGES; ++q) seq[q] = -1;
         mbar_fence_init();
     }
     if (SMEM_ACC)
@@ -436,9 +439,7 @@ __global__ void __launch_bounds__(MV_THREADS, 1) k_matvec_tiles(MvArgs a) {
     const int tb = a.tile_begin[blockIdx.x], te = a.tile_begin[blockIdx.x + 1];
     if (warp == 0) {
         // producer warp: tile records are fetched 32 at a time (one coalesced
-        // load, lane l holds record base + l), lane 0 publishes each record in
-        // the stage's descriptor slot and issues the bulk copies
-        MvTile* desc = reinterpret_cast<MvTile*>(smem + L::DESC_OFF);
+        // load, lane l holds record base + l), lane 0 issues the bulk copies
         int issued = 0;
         bool stop = false;
         for (int base = tb; base < te && !stop; base += 32) {
@@ -461,7 +462,10 @@ __global__ void __launch_bounds__(MV_THREADS, 1) k_matvec_tiles(MvArgs a) {
                     if (i >= MV_STAGES && !mbar_wait(empty_bar(s), ((i / MV_STAGES) - 1) & 1, abort_flag, a.err)) {
                         ok = 0;
                     } else {
-                        desc[s] = tile;
+                        // the consumer warps the tile does not need arrive on
+                        // its empty barrier here, before its data can land
+                        const int need = tile_warps(tile, MODE, a.big8_kmax);
+                        if (need < MV_CONSUMERS) mbar_arrive_cnt(empty_bar(s), (uint32_t)(MV_CONSUMERS - need));
                         if (tile.kind == TILE_GLOBAL) {
                             mbar_arrive(full_bar(s));
                         } else {
@@ -483,6 +487,7 @@ __global__ void __launch_bounds__(MV_THREADS, 1) k_matvec_tiles(MvArgs a) {
                                 bulk_g2s(smem_u32(smem + L::STAGE_R_OFF + s * MV_STAGE_R), a.cpool + r4, rbytes,
                                          full_bar(s));
                         }
+                        seq[s] = i;  // stage s is armed with tile i
                         ++issued;
                     }
                 }
@@ -499,35 +504,61 @@ __global__ void __launch_bounds__(MV_THREADS, 1) k_matvec_tiles(MvArgs a) {
         }
     } else {
         const int cw = warp - 1;
-        for (int t = tb; t < te; ++t) {
-            const int i = t - tb, s = i % MV_STAGES;
-            if (!mbar_wait(full_bar(s), (i / MV_STAGES) & 1, abort_flag, a.err)) break;
-            const MvTile tile = reinterpret_cast<const MvTile*>(smem + L::DESC_OFF)[s];
-            const float* sa = reinterpret_cast<const float*>(smem + s * MV_STAGE_A);
-            const int32_t* sc = reinterpret_cast<const int32_t*>(smem + L::STAGE_C_OFF + s * MV_STAGE_C) +
-                                (tile.cam_off & 3);
-            float* ub = reinterpret_cast<float*>(smem + L::U_OFF) + s * MV_UMAX;
-            // A tile rarely needs all consumer warps; successive tiles start at
-            // successive groups of warps (rotation by the warps the tile needs),
-            // so that the tiles in flight are worked on by disjoint warps.
-            const int need = tile_warps(tile, MODE, a.big8_kmax);
-            const int vcw = (cw + MV_CONSUMERS - (i * need) % MV_CONSUMERS) % MV_CONSUMERS;
-            if (MODE == MODE_MATVEC) {
-                if (tile.kind == TILE_SMALL) small_dispatch(tile.k, sa, sc, tile.count, a.v, yt, vcw, lane);
-                else if (tile.kind == TILE_BIG && tile.k <= a.big8_kmax)
-                    big_tile<8>(sa, sc, tile.k, tile.count, a.v, yt, vcw, lane);
-                else if (tile.kind == TILE_BIG) big_tile<4>(sa, sc, tile.k, tile.count, a.v, yt, vcw, lane);
-                else if (vcw == 0) global_block(a, tile.first, ub, yt, lane);
-            } else {
-                const int tid = vcw * 32 + lane;
-                const int64_t r_first = 2LL * tile.cam_off + (tile.kind == TILE_BIG ? tile.r0 : 0);
-                const float* sr = reinterpret_cast<const float*>(smem + L::STAGE_R_OFF + s * MV_STAGE_R) + (r_first & 3);
-                if (tile.kind == TILE_SMALL) precond_blocks(a, tile, sa, sc, sr, tid);
-                else if (tile.kind == TILE_BIG) precond_rows(a, tile, sa, sc, sr, tid);
-                else precond_global(a, tile, tid);
+        // Each consumer warp reads the tile records itself and works only on
+        // the tiles that need it: successive tiles take successive groups of
+        // warps (cyclically), so that the tiles in flight are worked on by
+        // disjoint warps.  The producer arrives on a tile's empty barrier for
+        // the warps the tile does not need, so a stage is released as soon as
+        // its own warps are done.  A warp that skipped tiles first waits until
+        // the producer has armed the stage with its tile (seq), so that the
+        // parity wait on the full barrier that follows is exact.
+        int start = 0;  // first consumer warp of the current tile
+        bool stop = false;
+        for (int base = tb; base < te && !stop; base += 32) {
+            MvTile mine{};
+            if (base + lane < te) mine = a.tiles[base + lane];
+            const int n = min(32, te - base);
+            for (int q = 0; q < n; ++q) {
+                MvTile tile;
+                tile.a_off = __shfl_sync(0xffffffffu, mine.a_off, q);
+                tile.cam_off = __shfl_sync(0xffffffffu, mine.cam_off, q);
+                tile.bytes = __shfl_sync(0xffffffffu, mine.bytes, q);
+                tile.k = (int16_t)__shfl_sync(0xffffffffu, (int)mine.k, q);
+                tile.kind = (int16_t)__shfl_sync(0xffffffffu, (int)mine.kind, q);
+                tile.count = __shfl_sync(0xffffffffu, mine.count, q);
+                tile.r0 = __shfl_sync(0xffffffffu, mine.r0, q);
+                tile.first = __shfl_sync(0xffffffffu, mine.first, q);
+                const int need = tile_warps(tile, MODE, a.big8_kmax);
+                const int vcw = (cw - start + MV_CONSUMERS) % MV_CONSUMERS;
+                start = (start + need) % MV_CONSUMERS;
+                if (vcw >= need) continue;
+                const int i = base + q - tb, s = i % MV_STAGES;
+                if (!seq_wait(seq + s, i, abort_flag, a.err) ||
+                    !mbar_wait(full_bar(s), (i / MV_STAGES) & 1, abort_flag, a.err)) {
+                    stop = true;
+                    break;
+                }
+                const float* sa = reinterpret_cast<const float*>(smem + s * MV_STAGE_A);
+                const int32_t* sc = reinterpret_cast<const int32_t*>(smem + L::STAGE_C_OFF + s * MV_STAGE_C) +
+                                    (tile.cam_off & 3);
+                float* ub = reinterpret_cast<float*>(smem + L::U_OFF) + s * MV_UMAX;
+                if (MODE == MODE_MATVEC) {
+                    if (tile.kind == TILE_SMALL) small_dispatch(tile.k, sa, sc, tile.count, a.v, yt, vcw, lane);
+                    else if (tile.kind == TILE_BIG && tile.k <= a.big8_kmax)
+                        big_tile<8>(sa, sc, tile.k, tile.count, a.v, yt, vcw, lane);
+                    else if (tile.kind == TILE_BIG) big_tile<4>(sa, sc, tile.k, tile.count, a.v, yt, vcw, lane);
+                    else if (vcw == 0) global_block(a, tile.first, ub, yt, lane);
+                } else {
+                    const int tid = vcw * 32 + lane;
+                    const int64_t r_first = 2LL * tile.cam_off + (tile.kind == TILE_BIG ? tile.r0 : 0);
+                    const float* sr = reinterpret_cast<const float*>(smem + L::STAGE_R_OFF + s * MV_STAGE_R) + (r_first & 3);
+                    if (tile.kind == TILE_SMALL) precond_blocks(a, tile, sa, sc, sr, tid);
+                    else if (tile.kind == TILE_BIG) precond_rows(a, tile, sa, sc, sr, tid);
+                    else precond_global(a, tile, tid);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(empty_bar(s));
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(empty_bar(s));
         }
     }
     __syncthreads();

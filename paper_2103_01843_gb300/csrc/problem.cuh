@@ -216,8 +216,7 @@ void build_index(Problem& p, const int32_t* d_obs_cam, const int32_t* d_obs_pt,
                  const double* d_obs_xy, const double* d_cams, const double* d_pts);
 // K1: damping diagonals, linearisation + Householder QR (linearize.cu)
 void launch_frames(Problem& p);   // frames of the current cams
-void launch_camera_diag(Problem& p);
-void launch_linearize(Problem& p);
+void launch_linearize(Problem& p);  // K1 and D_p^2
 void launch_export_jacobians(Problem& p, float* r, float* jp, float* jl);
 // cost and state update (cost.cu)
 void launch_cost(Problem& p, bool candidate);

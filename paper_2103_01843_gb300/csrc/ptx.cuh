@@ -22,6 +22,11 @@ __device__ __forceinline__ void mbar_fence_init() {
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
 }
+// count arrivals at once (on behalf of warps that skip a phase)
+__device__ __forceinline__ void mbar_arrive_cnt(uint32_t bar, uint32_t count) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar), "r"(count)
+                 : "memory");
+}
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
                  "r"(bytes)
@@ -55,6 +60,23 @@ __device__ inline bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* ab
     for (;;) {
         if (mbar_try(bar, parity)) return true;
         if (honour_abort && *abort_flag) return false;
+        if (global_ns() - t0 > WAIT_NS) {
+            *abort_flag = 1;
+            atomicOr(err, ERRBIT_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+// Bounded wait until *p == v (a shared-memory word another warp of the CTA
+// sets); false after WAIT_NS or when another warp has aborted; a timeout
+// raises ERRBIT_TIMEOUT.
+__device__ inline bool seq_wait(volatile int* p, int v, volatile int* abort_flag, uint32_t* err) {
+    if (*p == v) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (*p == v) return true;
+        if (*abort_flag) return false;
         if (global_ns() - t0 > WAIT_NS) {
             *abort_flag = 1;
             atomicOr(err, ERRBIT_TIMEOUT);
