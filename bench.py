@@ -659,7 +659,7 @@ def run_matvec_only(args):
     with sq.Problem.from_scene(scene, stream=torch.cuda.current_stream().cuda_stream) as p:
         p.linearize()
         p.marginalize_qr(1e-4)
-        p.autotune()
+        print(json.dumps({"mode": "matvec", "tuned": p.autotune()}), flush=True)
         v = np.random.default_rng(0).normal(size=9 * scene.n_cam).astype(np.float32)
         for _ in range(args.warmup + args.steps):
             p.matvec(v)

@@ -41,20 +41,21 @@ constexpr int MV_KBIG = 222;        // row ranges, multiples of 4 rows (36k * 4 
 constexpr int MV_UMAX = 45;         // rows of one big tile (multiple of MV_CONSUMERS)
 
 constexpr int MV_STAGE_R = 2048;    // bytes of c_j values per stage (preconditioner mode)
-// Shared-memory layout for NS stages; ACC_OFF starts the per-CTA
-// accumulators (y in matvec mode, the camera blocks in preconditioner mode).
-template <int NS>
+// Shared-memory layout for NS stages (PC = 1: the preconditioner record
+// pass, which also stages c_j values); ACC_OFF starts the matvec's per-CTA
+// copy of y.
+template <int NS, int PC>
 struct Layout {
     static constexpr int STAGE_C_OFF = NS * MV_STAGE_A;
     static constexpr int STAGE_R_OFF = STAGE_C_OFF + NS * MV_STAGE_C;
-    static constexpr int U_OFF = STAGE_R_OFF + NS * MV_STAGE_R;
+    static constexpr int U_OFF = STAGE_R_OFF + (PC ? NS * MV_STAGE_R : 0);
     static constexpr int BAR_OFF = (U_OFF + NS * MV_UMAX * 4 + 7) & ~7;
     static constexpr int FLAG_OFF = BAR_OFF + 2 * NS * 8;
     static constexpr int SEQ_OFF = FLAG_OFF + 16;          // tile index each stage holds
     static constexpr int ACC_OFF = SEQ_OFF + 32;
 };
 constexpr int SMEM_LIMIT = 227 * 1024;
-static_assert(Layout<6>::ACC_OFF <= SMEM_LIMIT, "six stages fit the opt-in shared memory");
+static_assert(Layout<6, 1>::ACC_OFF <= SMEM_LIMIT, "six stages fit the opt-in shared memory");
 
 enum : int16_t { TILE_SMALL = 0, TILE_BIG = 1, TILE_GLOBAL = 2 };
 
@@ -408,7 +409,7 @@ __device__ __forceinline__ int tile_warps(const MvTile& t, int mode, int big8_km
 // MODE_PRECOND: per-observation records (SMEM_ACC false).
 template <int MODE, bool SMEM_ACC, int NS>
 __global__ void __launch_bounds__(MV_THREADS, 1) k_matvec_tiles(MvArgs a) {
-    using L = Layout<NS>;
+    using L = Layout<NS, MODE == MODE_PRECOND ? 1 : 0>;
     constexpr int MV_STAGES = NS;
     extern __shared__ __align__(128) unsigned char smem[];
     if (a.S != nullptr && a.S->done) return;
@@ -578,8 +579,12 @@ __global__ void k_add_damping(int n, const float* __restrict__ dp2, float lam, c
 
 // Pipeline depths built: 4, 5 and 6 stages of 32 KB (the planner's tiles do
 // not depend on the depth; the autotuner picks it per plan).
-int acc_off(int ns) { return ns == 6 ? Layout<6>::ACC_OFF : ns == 5 ? Layout<5>::ACC_OFF : Layout<4>::ACC_OFF; }
-bool y_fits(const Problem& p, int ns) { return acc_off(ns) + 36 * (int64_t)p.n_cam <= SMEM_LIMIT; }
+template <int PC>
+int acc_off_pc(int ns) {
+    return ns == 6 ? Layout<6, PC>::ACC_OFF : ns == 5 ? Layout<5, PC>::ACC_OFF : Layout<4, PC>::ACC_OFF;
+}
+int acc_off(int ns, bool pc) { return pc ? acc_off_pc<1>(ns) : acc_off_pc<0>(ns); }
+bool y_fits(const Problem& p, int ns) { return acc_off(ns, false) + 36 * (int64_t)p.n_cam <= SMEM_LIMIT; }
 // the depth in use: the plan's, unless the options force one
 int depth(const Problem& p, const Problem::TilePlan& plan) {
     return p.opt.pipeline_stages ? p.opt.pipeline_stages : plan.ns;
@@ -587,7 +592,7 @@ int depth(const Problem& p, const Problem::TilePlan& plan) {
 // y is accumulated in shared memory when the plan asks for it and it fits
 bool smem_y(const Problem& p, const Problem::TilePlan& plan) { return plan.y_smem && y_fits(p, depth(p, plan)); }
 size_t smem_bytes(const Problem& p, const Problem::TilePlan& plan, bool pc) {
-    return acc_off(depth(p, plan)) + (!pc && smem_y(p, plan) ? 36 * (size_t)p.n_cam : 0);
+    return acc_off(depth(p, plan), pc) + (!pc && smem_y(p, plan) ? 36 * (size_t)p.n_cam : 0);
 }
 
 using MvKernel = void (*)(MvArgs);

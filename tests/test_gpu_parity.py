@@ -324,12 +324,12 @@ def test_many_cameras_records_path(pkg, from_blocks):
 @pytest.mark.parametrize("stages", [4, 5, 6])
 def test_pipeline_depths(pkg, heavy, stages):
     """Every depth of the K3 / K4 tile pipeline gives the same reduced system:
-    with 700 cameras y is accumulated in shared memory at 4 and 5 stages and
+    with 900 cameras y is accumulated in shared memory at 4 and 5 stages and
     in global memory at 6 (it no longer fits beside six stages)."""
-    many = make_scene("small", 9, n_cam=700, n_pt=2500, p=0.25, cap=40)
+    many = make_scene("small", 9, n_cam=900, n_pt=2500, p=0.25, cap=40)
     for sc, lam in ((heavy, 1e-3), (many, 1e-2)):
         s = Rounded(sc)
-        with pkg.Problem.from_scene(sc, pipeline_stages=stages) as p:
+        with pkg.Problem.from_scene(sc, pipeline_stages=stages, precond_from_blocks=1) as p:
             p.linearize()
             p.marginalize_qr(lam)
             p.pcg_solve()
