@@ -52,10 +52,12 @@ def parse():
     ap.add_argument("--learned-train", type=int, default=32)
     ap.add_argument("--learned-eval", type=int, default=8)
     ap.add_argument("--learned-steps", type=int, default=3000)
-    ap.add_argument("--mode", default="solve", choices=["solve", "matvec", "kernels", "mlp"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "matvec", "kernels", "mlp", "kdeg"],
                     help="kernel-profiling runs that print no bench line: matvec repeats the PCG "
                          "matvec on a linearised, damped problem; kernels runs every kernel of one "
-                         "LM iteration; mlp runs the learned model's forward on 4096 rows")
+                         "LM iteration; mlp runs the learned model's forward on 4096 rows; kdeg "
+                         "times the matvec and K3 on scenes whose landmarks all have k = --k-list")
+    ap.add_argument("--k-list", default="3,6,9,12,16,21,22,32")
     return ap.parse_args()
 
 
@@ -666,8 +668,52 @@ def run_matvec_only(args):
     return 0
 
 
+def run_kdeg(args):
+    """Per landmark degree k: a scene of about 400 MB of blocks whose landmarks
+    all have k observations (each a medium-scene landmark with at least k
+    observations, its first k), timed over ten PCG iterations at two dampings
+    (event timing of the matvec and of K3 with the CG start)."""
+    import numpy as np
+    import torch
+    import paper_2103_01843_gb300 as sq
+    from paper_2103_01843_gb300.synth import make_scene
+    torch.cuda.set_device(0)
+    base = make_scene(args.config, args.seed)
+    rng = np.random.default_rng(0)
+    order = np.argsort(base.obs_pt, kind="stable")
+    off = np.searchsorted(base.obs_pt[order], np.arange(base.n_pt + 1))
+    kk = np.diff(off)
+    for k in [int(x) for x in args.k_list.split(",")]:
+        n_pt = int(400e6 / (72 * k * k))
+        cand = np.nonzero(kk >= k)[0]
+        if cand.size == 0:
+            continue
+        sel = cand[rng.integers(0, cand.size, n_pt)]
+        rows = order[(off[sel][:, None] + np.arange(k)[None, :]).ravel()]
+        oc = base.obs_cam[rows].astype(np.int32)
+        op = np.repeat(np.arange(n_pt), k).astype(np.int32)
+        with sq.Problem(base.cams, base.pts[sel], oc, op, base.obs_xy[rows], cg_eta=1e-12, max_cg_iters=10) as p:
+            p.linearize()
+            p.marginalize_qr(1e-4)
+            t = p.autotune()
+            p.set_profiling(True)
+            for lam in (1e-4, 1e-3):
+                p.marginalize_qr(lam)
+                p.pcg_solve()
+            pr = p.profile()
+        mv = pr["matvec"]["ms"] / max(1, pr["matvec"]["count"]) * 1e3
+        pc = pr["precond"]["ms"] / max(1, pr["precond"]["count"]) * 1e3
+        byt = 72.0 * k * k * n_pt
+        print(json.dumps({"mode": "kdeg", "k": k, "landmarks": n_pt, "block_bytes": byt,
+                          "matvec_us": round(mv, 1), "matvec_gbs": round(byt / mv / 1e3, 1) if mv else None,
+                          "precond_us": round(pc, 1), "tuned": t}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.mode == "kdeg":
+        return run_kdeg(args)
     if args.mode == "matvec":
         return run_matvec_only(args)
     if args.mode == "kernels":
