@@ -4,6 +4,8 @@
 // reads back a few scalars per LM iteration (the PCG scalars, the FP64 model
 // cost and the FP64 candidate cost); everything else stays on the device.
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -18,6 +20,50 @@
 
 namespace sqrtba {
 int linearize_k_limit();
+
+cudaMemPool_t device_pool() {
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    int dev = 0;
+    BA_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    cudaMemPool_t& pool = pools[dev];
+    if (!pool) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        BA_CUDA_TRY(cudaMemPoolCreate(&pool, &props));
+        uint64_t keep = UINT64_MAX;  // never return freed memory to the system on synchronisation
+        BA_CUDA_TRY(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    }
+    return pool;
+}
+
+static std::mutex pinned_mu;
+static std::multimap<size_t, void*> pinned_free;
+
+void* pinned_get(size_t bytes) {
+    {
+        std::lock_guard<std::mutex> lock(pinned_mu);
+        auto it = pinned_free.find(bytes);
+        if (it != pinned_free.end()) {
+            void* ptr = it->second;
+            pinned_free.erase(it);
+            return ptr;
+        }
+    }
+    void* ptr = nullptr;
+    BA_CUDA_TRY(cudaMallocHost(&ptr, bytes));
+    return ptr;
+}
+
+void pinned_put(void* ptr, size_t bytes) {
+    if (!ptr) return;
+    std::lock_guard<std::mutex> lock(pinned_mu);
+    pinned_free.emplace(bytes, ptr);
+}
+
 }  // namespace sqrtba
 
 using namespace sqrtba;
@@ -132,16 +178,16 @@ void free_all(Problem& p) {
     destroy_graph(p);
     for (cudaEvent_t e : p.batch.iter_events) cudaEventDestroy(e);
     p.batch.iter_events.clear();
-    if (p.batch.n_active_host) cudaFreeHost(p.batch.n_active_host);
+    pinned_put(p.batch.n_active_host, sizeof(int32_t));
     p.batch.n_active_host = nullptr;
     for (cudaEvent_t e : p.prof.events) cudaEventDestroy(e);
     for (cudaEvent_t e : p.mv_events) cudaEventDestroy(e);
     p.prof.events.clear();
     p.mv_events.clear();
-    for (void* a : p.allocations) cudaFree(a);
+    for (void* a : p.allocations) cudaFreeAsync(a, p.stream);
     p.allocations.clear();
-    if (p.pcg_host) cudaFreeHost(p.pcg_host);
-    if (p.dsum_host) cudaFreeHost(p.dsum_host);
+    pinned_put(p.pcg_host, sizeof(PcgScalars));
+    pinned_put(p.dsum_host, 4 * sizeof(double));
     p.pcg_host = nullptr;
     p.dsum_host = nullptr;
     if (p.side) cudaStreamDestroy(p.side);
@@ -659,18 +705,18 @@ void create_problem(Problem& p, const double* cams, int32_t n_cam, const double*
     p.err = dalloc<uint32_t>(p, 4);
     p.dsum = dalloc<double>(p, 4);
     p.pcg = dalloc<PcgScalars>(p, 1);
-    BA_CUDA_TRY(cudaMallocHost(&p.pcg_host, sizeof(PcgScalars)));
-    BA_CUDA_TRY(cudaMallocHost(&p.dsum_host, 4 * sizeof(double)));
+    p.pcg_host = static_cast<PcgScalars*>(pinned_get(sizeof(PcgScalars)));
+    p.dsum_host = static_cast<double*>(pinned_get(4 * sizeof(double)));
     std::memset(p.pcg_host, 0, sizeof(PcgScalars));
 
     // stage the FP64 inputs on the device for validation and grouping
     double *d_cams = nullptr, *d_pts = nullptr, *d_xy = nullptr;
     int32_t *d_oc = nullptr, *d_op = nullptr;
-    BA_CUDA_TRY(cudaMallocAsync(&d_cams, sizeof(double) * 9 * n_cam, p.stream));
-    BA_CUDA_TRY(cudaMallocAsync(&d_pts, sizeof(double) * 3 * n_pt, p.stream));
-    BA_CUDA_TRY(cudaMallocAsync(&d_xy, sizeof(double) * 2 * n_obs, p.stream));
-    BA_CUDA_TRY(cudaMallocAsync(&d_oc, sizeof(int32_t) * n_obs, p.stream));
-    BA_CUDA_TRY(cudaMallocAsync(&d_op, sizeof(int32_t) * n_obs, p.stream));
+    BA_CUDA_TRY(cudaMallocFromPoolAsync(&d_cams, sizeof(double) * 9 * n_cam, device_pool(), p.stream));
+    BA_CUDA_TRY(cudaMallocFromPoolAsync(&d_pts, sizeof(double) * 3 * n_pt, device_pool(), p.stream));
+    BA_CUDA_TRY(cudaMallocFromPoolAsync(&d_xy, sizeof(double) * 2 * n_obs, device_pool(), p.stream));
+    BA_CUDA_TRY(cudaMallocFromPoolAsync(&d_oc, sizeof(int32_t) * n_obs, device_pool(), p.stream));
+    BA_CUDA_TRY(cudaMallocFromPoolAsync(&d_op, sizeof(int32_t) * n_obs, device_pool(), p.stream));
     struct StageGuard {
         Problem& p;
         void* b[5];
@@ -809,7 +855,7 @@ void create_batch(ba_batch* bh, const ba_problem_desc* descs, int32_t n, const b
     B.cost_a = dalloc<double>(p, n);
     B.cost_b = dalloc<double>(p, n);
     B.n_active = dalloc<int32_t>(p, 1);
-    BA_CUDA_TRY(cudaMallocHost(&B.n_active_host, sizeof(int32_t)));
+    B.n_active_host = static_cast<int32_t*>(pinned_get(sizeof(int32_t)));
     h2d(p, B.cam_prob, cam_prob.data(), tc);
     h2d(p, B.lm_prob, lm_prob.data(), tp);
     h2d(p, B.prob_cam_off, B.h_cam_off.data(), n + 1);
@@ -1205,9 +1251,9 @@ ba_status ba_debug_export_jacobians(ba_problem* h, float* r, float* jp, float* j
     API_TRY
     Problem& p = h->p;
     float *dr = nullptr, *djp = nullptr, *djl = nullptr;
-    BA_CUDA_TRY(cudaMallocAsync(&dr, sizeof(float) * 2 * p.n_obs, p.stream));
-    BA_CUDA_TRY(cudaMallocAsync(&djp, sizeof(float) * 18 * p.n_obs, p.stream));
-    BA_CUDA_TRY(cudaMallocAsync(&djl, sizeof(float) * 6 * p.n_obs, p.stream));
+    BA_CUDA_TRY(cudaMallocFromPoolAsync(&dr, sizeof(float) * 2 * p.n_obs, device_pool(), p.stream));
+    BA_CUDA_TRY(cudaMallocFromPoolAsync(&djp, sizeof(float) * 18 * p.n_obs, device_pool(), p.stream));
+    BA_CUDA_TRY(cudaMallocFromPoolAsync(&djl, sizeof(float) * 6 * p.n_obs, device_pool(), p.stream));
     launch_export_jacobians(p, dr, djp, djl);
     if (r) d2h(p, r, dr, 2 * p.n_obs);
     if (jp) d2h(p, jp, djp, 18 * p.n_obs);
@@ -1239,8 +1285,8 @@ ba_status ba_debug_matvec(ba_problem* h, const float* v, float* y) {
     require(p.damped, BA_ERR_STATE, "blocks are not marginalised");
     const int64_t n = 9 * (int64_t)p.n_cam;
     float *dv = nullptr, *dy = nullptr;
-    BA_CUDA_TRY(cudaMallocAsync(&dv, sizeof(float) * n, p.stream));
-    BA_CUDA_TRY(cudaMallocAsync(&dy, sizeof(float) * n, p.stream));
+    BA_CUDA_TRY(cudaMallocFromPoolAsync(&dv, sizeof(float) * n, device_pool(), p.stream));
+    BA_CUDA_TRY(cudaMallocFromPoolAsync(&dy, sizeof(float) * n, device_pool(), p.stream));
     h2d(p, dv, v, n);
     launch_matvec(p, dv, dy, true);
     d2h(p, y, dy, n);

@@ -305,7 +305,7 @@ void build_index(Problem& p, const int32_t* d_oc, const int32_t* d_op, const dou
     std::vector<void*> tmps;
     auto tmp_alloc = [&](size_t bytes) {
         void* ptr = nullptr;
-        BA_CUDA_TRY(cudaMallocAsync(&ptr, bytes ? bytes : 1, st));
+        BA_CUDA_TRY(cudaMallocFromPoolAsync(&ptr, bytes ? bytes : 1, device_pool(), st));
         tmps.push_back(ptr);
         return ptr;
     };

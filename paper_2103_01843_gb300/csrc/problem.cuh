@@ -263,12 +263,21 @@ inline void count_launches(Problem& p, int n) {
     if (!p.capturing) p.launches += n;
 }
 
-// device allocation helper that records the pointer for ba_destroy
+// Device memory of every problem comes, in stream order, from one memory
+// pool per device that keeps freed memory for the next problem (creating and
+// destroying problems of similar size then maps no new memory); small pinned
+// host buffers are recycled the same way.
+cudaMemPool_t device_pool();
+void* pinned_get(size_t bytes);
+void pinned_put(void* ptr, size_t bytes);
+
+// device allocation helper (stream-ordered on the problem's stream) that
+// records the pointer for ba_destroy
 template <typename T>
 T* dalloc(Problem& p, int64_t n) {
     void* ptr = nullptr;
     size_t bytes = sizeof(T) * (size_t)(n > 0 ? n : 1);
-    BA_CUDA_TRY(cudaMalloc(&ptr, bytes));
+    BA_CUDA_TRY(cudaMallocFromPoolAsync(&ptr, bytes, device_pool(), p.stream));
     p.allocations.push_back(ptr);
     p.device_bytes += (int64_t)bytes;
     return static_cast<T*>(ptr);
