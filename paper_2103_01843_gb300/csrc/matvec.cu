@@ -95,15 +95,76 @@ struct MvArgs {
 };
 
 // --- consumers ---------------------------------------------------------------------
+// Team width of whole-block tiles of k: narrow teams (fewer shuffles per
+// element) where their lanes hold at most 7 columns, whole warps from k = 12
+// on (measured per k on uniform-k scenes: 8 lanes for k <= 7, 16 for
+// 8 <= k <= 11, 32 above).
+__host__ __device__ constexpr int small_team_width(int k) { return k <= 7 ? 8 : (k <= 11 ? 16 : 32); }
+
 template <int K>
 struct SmallShape {
     static constexpr int NC = 9 * K, NR = 2 * K;
-    static constexpr int W = NC <= 32 ? 8 : (NC <= 64 ? 16 : 32);  // team width (<= 4 columns a lane below k = 8)
-    static constexpr int NM = (NC + W - 1) / W;
+    static constexpr int W = small_team_width(K);
+    static constexpr int NM = (NC + W - 1) / W;         // columns per lane
+    static constexpr int G = NM <= 6 ? 8 : 4;           // rows per group (G x NM values in registers)
     static constexpr int BF = (18 * K * K + 3) & ~3;  // block floats (padded to 16 bytes)
 };
 
+// Rows r0 .. r0 + GR - 1 of one block for a team of W lanes (lane t of the
+// team owns columns t + W m): the GR row sums u_r = A_r v are
+// reduce-scattered (log2 GR halving shuffles over the team's top lane bits
+// leave each lane one row's partial sum, xor shuffles over the remaining
+// bits complete it) and broadcast back, then y += u_r A_r.
+template <int K, int GR>
+__device__ __forceinline__ void small_rows(const float* __restrict__ blk, int r0, const float (&vr)[SmallShape<K>::NM],
+                                           float (&yr)[SmallShape<K>::NM], int t, int lane) {
+    using S = SmallShape<K>;
+    constexpr int W = S::W, NM = S::NM;
+    constexpr int LG = GR == 8 ? 3 : (GR == 4 ? 2 : 1);
+    static_assert(GR == 8 || GR == 4 || GR == 2, "row group");
+    static_assert((GR >> LG) == 1 && GR <= W, "row group within the team");
+    float a[GR][NM], cur[GR];
+#pragma unroll
+    for (int q = 0; q < GR; ++q) {
+        cur[q] = 0.f;
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            const int col = t + W * m;
+            a[q][m] = col < S::NC ? blk[(r0 + q) * S::NC + col] : 0.f;
+            cur[q] += a[q][m] * vr[m];
+        }
+    }
+#pragma unroll
+    for (int st = 0; st < LG; ++st) {
+        const int n = GR >> st, o = W >> (st + 1);
+        const bool b = lane & o;
+#pragma unroll
+        for (int i = 0; i < GR / 2; ++i) {
+            if (i < n / 2) {
+                const float send = b ? cur[i] : cur[i + n / 2], keep = b ? cur[i + n / 2] : cur[i];
+                cur[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        }
+    }
+    float u = cur[0];
+#pragma unroll
+    for (int o = W >> (LG + 1); o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+    const int tbase = lane & ~(W - 1);
+#pragma unroll
+    for (int q = 0; q < GR; ++q) {
+        int src = tbase;
+#pragma unroll
+        for (int st = 0; st < LG; ++st)
+            if ((q >> (LG - 1 - st)) & 1) src += W >> (st + 1);
+        const float uq = __shfl_sync(0xffffffffu, u, src);
+#pragma unroll
+        for (int m = 0; m < NM; ++m) yr[m] += uq * a[q][m];
+    }
+}
+
 // One tile of `count` blocks with k = K; consumer warp cw of MV_CONSUMERS.
+// Each team of W lanes takes one block: full groups of G rows, then the
+// remaining rows in groups of 4 and 2 (2k is even), so no row is padded.
 // Teams past the tile's last block read its first block (finite data) with
 // v = 0, so they add nothing; their y is not written.
 template <int K>
@@ -112,6 +173,9 @@ __device__ __forceinline__ void small_tile(const float* __restrict__ sa, const i
     using S = SmallShape<K>;
     constexpr int TPW = 32 / S::W;
     constexpr int T = MV_CONSUMERS * TPW;
+    constexpr int FULL = (S::NR / S::G) * S::G, REM = S::NR - FULL;
+    constexpr bool R4 = S::G == 8 && REM >= 4;
+    constexpr bool R2 = (REM - (R4 ? 4 : 0)) == 2;
     const int t = lane % S::W;
     for (int base = cw * TPW; base < count; base += T) {
         const int l = base + lane / S::W;
@@ -129,68 +193,10 @@ __device__ __forceinline__ void small_tile(const float* __restrict__ sa, const i
             vr[m] = ok ? __ldg(v + yi[m]) : 0.f;
             yr[m] = 0.f;
         }
-        if constexpr (S::W >= 16) {
-            // teams of 16 or 32 lanes: rows in groups of 8; the 8 row sums
-            // u_r are reduce-scattered (three halving steps over the team's
-            // top lane bits leave each lane one row, summed over 8 lanes; the
-            // remaining steps complete it) and broadcast back: 16-17
-            // shuffles per 8 rows instead of 32-40
-            constexpr int O1 = S::W / 2, O2 = S::W / 4, O3 = S::W / 8;
-            const bool bA = lane & O1, bB = lane & O2, bC = lane & O3;
-            const int tbase = lane & ~(S::W - 1);
 #pragma unroll 1
-            for (int r0 = 0; r0 < S::NR; r0 += 8) {
-                float a[8][S::NM];
-                float pr[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    pr[q] = 0.f;
-#pragma unroll
-                    for (int m = 0; m < S::NM; ++m) {
-                        const int col = t + S::W * m;
-                        a[q][m] = (r0 + q < S::NR && col < S::NC) ? blk[(r0 + q) * S::NC + col] : 0.f;
-                        pr[q] += a[q][m] * vr[m];
-                    }
-                }
-                float h4[4], h2[2];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float send = bA ? pr[i] : pr[i + 4], keep = bA ? pr[i + 4] : pr[i];
-                    h4[i] = keep + __shfl_xor_sync(0xffffffffu, send, O1);
-                }
-#pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const float send = bB ? h4[i] : h4[i + 2], keep = bB ? h4[i + 2] : h4[i];
-                    h2[i] = keep + __shfl_xor_sync(0xffffffffu, send, O2);
-                }
-                float u = (bC ? h2[1] : h2[0]) + __shfl_xor_sync(0xffffffffu, bC ? h2[0] : h2[1], O3);
-#pragma unroll
-                for (int o = O3 / 2; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int src = tbase + ((q >> 2) & 1) * O1 + ((q >> 1) & 1) * O2 + (q & 1) * O3;
-                    const float uq = __shfl_sync(0xffffffffu, u, src);
-#pragma unroll
-                    for (int m = 0; m < S::NM; ++m) yr[m] += uq * a[q][m];
-                }
-            }
-        } else {
-#pragma unroll 4
-            for (int r = 0; r < S::NR; ++r) {
-                float a[S::NM];
-                float part = 0.f;
-#pragma unroll
-                for (int m = 0; m < S::NM; ++m) {
-                    const int col = t + S::W * m;
-                    a[m] = col < S::NC ? blk[r * S::NC + col] : 0.f;
-                    part += a[m] * vr[m];
-                }
-#pragma unroll
-                for (int o = S::W / 2; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-#pragma unroll
-                for (int m = 0; m < S::NM; ++m) yr[m] += part * a[m];
-            }
-        }
+        for (int r0 = 0; r0 < FULL; r0 += S::G) small_rows<K, S::G>(blk, r0, vr, yr, t, lane);
+        if constexpr (R4) small_rows<K, 4>(blk, FULL, vr, yr, t, lane);
+        if constexpr (R2) small_rows<K, 2>(blk, S::NR - 2, vr, yr, t, lane);
 #pragma unroll
         for (int m = 0; m < S::NM; ++m) {
             const int col = t + S::W * m;
@@ -389,8 +395,7 @@ __device__ __forceinline__ int tile_warps(const MvTile& t, int mode, int big8_km
     int w;
     if (mode == MODE_MATVEC) {
         if (t.kind == TILE_SMALL) {
-            const int nc = 9 * t.k;
-            const int tpw = nc <= 32 ? 4 : (nc <= 64 ? 2 : 1);
+            const int tpw = 32 / small_team_width(t.k);
             w = (t.count + tpw - 1) / tpw;
         } else if (t.kind == TILE_BIG) {
             const int rpw = t.k <= big8_kmax ? 8 : 4;
