@@ -358,7 +358,9 @@ void run_autotune(Problem& p, ba_tune_report* rep) {
     require(p.damped, BA_ERR_STATE, "ba_autotune: blocks are not marginalised (call ba_marginalize_qr)");
     const auto t0 = std::chrono::steady_clock::now();
     EventSet es(10);
-    BA_CUDA_TRY(cudaMemsetAsync(p.p, 0, sizeof(float) * 9 * p.n_cam, p.stream));
+    // a non-zero input (D_p^2), so that the timed launches do the work of a
+    // CG iteration (zero contributions skip the flush of y)
+    BA_CUDA_TRY(cudaMemcpyAsync(p.p, p.dp2, sizeof(float) * 9 * p.n_cam, cudaMemcpyDeviceToDevice, p.stream));
     const int ks_opts[3] = {8, 13, 21};
     const int by_opts[3] = {8192, 16384, 32768};
     const Problem::TilePlan dflt{};

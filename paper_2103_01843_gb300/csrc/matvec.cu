@@ -569,7 +569,11 @@ __global__ void __launch_bounds__(MV_THREADS, 1) k_matvec_tiles(MvArgs a) {
     }
     __syncthreads();
     if (MODE == MODE_MATVEC && SMEM_ACC) {
-        for (int i = threadIdx.x; i < acc_n; i += MV_THREADS) {
+        // the CTAs flush at nearly the same time: each starts at its own
+        // offset, so that concurrent atomics go to different addresses
+        const int i0 = (int)(((int64_t)blockIdx.x * acc_n) / gridDim.x);
+        for (int q = threadIdx.x; q < acc_n; q += MV_THREADS) {
+            const int i = q + i0 < acc_n ? q + i0 : q + i0 - acc_n;
             const float val = ys[i];
             if (val != 0.f) atomicAdd(a.y + i, val);
         }
