@@ -235,13 +235,13 @@ void launch_candidate(Problem& p) {
 
 // E at the current state (its frames are recomputed first) or at the
 // candidate (frames written by k_candidate)
-void launch_cost(Problem& p, bool candidate) {
+void launch_cost(Problem& p, bool candidate, int slot) {
     if (!candidate) launch_frames(p);
     count_launches(p, 2);
     k_cost<<<p.red_grid, 256, 0, p.stream>>>(p.n_obs, candidate ? p.cand_frames : p.frames,
                                              candidate ? p.cand_pts : p.pts, p.obs_cam_s, p.obs_pt_s,
                                              p.obs_xy_s, p.partials);
-    k_sum_partials<<<1, 1024, 0, p.stream>>>(p.partials, p.red_grid, p.dsum + 0);
+    k_sum_partials<<<1, 1024, 0, p.stream>>>(p.partials, p.red_grid, p.dsum + slot);
     BA_LAUNCH_CHECK();
 }
 

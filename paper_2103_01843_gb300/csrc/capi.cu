@@ -202,7 +202,9 @@ void free_all(Problem& p) {
 // --- the steps of the hot path ------------------------------------------------
 // K1 (+ D_p^2).  The energy at the linearisation point is evaluated unless
 // the host already knows it (the accepted candidate's cost).
-void do_linearize(Problem& p, bool need_cost = true, double damp_lambda = 0.0) {
+// defer_cost: the energy is left in dsum[2] for the caller's next
+// synchronisation (cost_pending) instead of being read back here.
+void do_linearize(Problem& p, bool need_cost = true, double damp_lambda = 0.0, bool defer_cost = false) {
     PhaseTimer t(p, PROF_LINEARIZE);
     launch_frames(p);
     launch_linearize(p);
@@ -214,12 +216,17 @@ void do_linearize(Problem& p, bool need_cost = true, double damp_lambda = 0.0) {
     }
     if (need_cost || !p.cost_valid) {
         PhaseTimer tc(p, PROF_COST);
-        launch_cost(p, false);
+        launch_cost(p, false, defer_cost ? 2 : 0);
         tc.end();
-        d2h(p, p.dsum_host, p.dsum, 1);
-        sync(p);
-        p.cost = p.dsum_host[0];
-        p.cost_valid = true;
+        if (defer_cost) {
+            p.cost_pending = true;
+            p.cost_valid = false;
+        } else {
+            d2h(p, p.dsum_host, p.dsum, 1);
+            sync(p);
+            p.cost = p.dsum_host[0];
+            p.cost_valid = true;
+        }
     }
     p.linearized = true;
     p.damped = damp_lambda > 0.0;
@@ -585,10 +592,9 @@ void do_lm_step(Problem& p, ba_lm_report* rep) {
     r.iteration = p.iteration;
     const double lam = p.lambda;
     if (!p.linearized) {
-        do_linearize(p, false, lam);
+        do_linearize(p, false, lam, true);  // an unknown energy is read back with the step's scalars
         r.relinearized = 1;
     }
-    const double E = p.cost;
     if (!p.damped || p.lambda_damped != lam) do_marginalize(p, lam);
     // K3-K7 enqueued back to back; one synchronisation for the scalars
     // (the learned mode synchronises once more to judge its CG)
@@ -602,8 +608,14 @@ void do_lm_step(Problem& p, ba_lm_report* rep) {
         launch_backsub_candidate_cost(p);
         tb.end();
     }
-    d2h(p, p.dsum_host, p.dsum, 2);
+    d2h(p, p.dsum_host, p.dsum, 3);
     sync(p);
+    if (p.cost_pending) {
+        p.cost = p.dsum_host[2];
+        p.cost_valid = true;
+        p.cost_pending = false;
+    }
+    const double E = p.cost;
     if (!learned) pcg_judge(p);
     ba_pcg_report pr{};
     fill_pcg_report(p, &pr);
@@ -1112,7 +1124,7 @@ ba_status ba_set_params(ba_problem* h, const double* cams, const double* pts) {
     h2d(p, p.pts, x.data(), (int64_t)x.size());
     sync(p);
     p.linearized = p.damped = p.solved = p.backsubbed = false;
-    p.cost_valid = false;
+    p.cost_valid = p.cost_pending = false;
     p.lambda = p.opt.lambda0;
     p.nu = 2.0;
     p.iteration = 0;

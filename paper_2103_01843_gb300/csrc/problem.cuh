@@ -203,6 +203,7 @@ struct Problem {
     bool stopped = false;
     double cost = 0.0;               // E at the current state
     bool cost_valid = false;         // cost holds E of the current state
+    bool cost_pending = false;       // E of the current state is in dsum[2], not yet read back
     int64_t device_bytes = 0;
     std::vector<void*> allocations;
     std::string last_error;
@@ -219,7 +220,7 @@ void launch_frames(Problem& p);   // frames of the current cams
 void launch_linearize(Problem& p);  // K1 and D_p^2
 void launch_export_jacobians(Problem& p, float* r, float* jp, float* jl);
 // cost and state update (cost.cu)
-void launch_cost(Problem& p, bool candidate);
+void launch_cost(Problem& p, bool candidate, int slot = 0);  // E into dsum[slot]
 void launch_candidate(Problem& p);
 // K2: landmark damping with Givens rotations (damp.cu)
 void launch_damp(Problem& p, bool undo_old, float lambda);
