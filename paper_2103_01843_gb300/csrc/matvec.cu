@@ -695,6 +695,9 @@ void plan_tiles(Problem& p, bool pc) {
                 t.kind = TILE_GLOBAL;
                 t.count = 1;
                 t.first = (int32_t)(pos0 + l);
+                // first observation in storage order: the record pass writes
+                // the block's records there and reads its c_j from there
+                t.cam_off = (int32_t)(p.run_co[b] + l * k);
                 t.bytes = 0;
                 tiles.push_back(t);
             }

@@ -367,6 +367,55 @@ def test_gram_and_block_preconditioners_agree(pkg, heavy, lam):
     assert rel_fro(out[0][0], out[1][0]) < 1e-4
 
 
+@pytest.mark.parametrize("from_blocks", [0, 1])
+def test_long_tracks_read_from_global_memory(pkg, from_blocks):
+    """Landmarks seen by up to 300 cameras (23 of them by more than 222): K1
+    factors them with one CTA each, the matvec reads blocks with k > 222
+    straight from global memory (and the record pass likewise)."""
+    sc = make_scene("small", 13, n_cam=320, n_pt=60, p=0.005, cap=300)
+    assert sc.k_per_point().max() > 222
+    s = Rounded(sc)
+    lam = 1e-3
+    with pkg.Problem.from_scene(sc, precond_from_blocks=from_blocks) as p:
+        p.linearize()
+        p.marginalize_qr(lam)
+        p.pcg_solve()
+        M, g = p.export_rcs_diag()
+        V = np.random.default_rng(9).normal(size=(2, 9 * s.n_cam)).astype(np.float32)
+        Y = np.stack([p.matvec(v) for v in V])
+    Mref, bt = oracle.rcs_diag(s, lam)
+    assert rel_fro(M, Mref) < 1e-4, rel_fro(M, Mref)
+    assert rel_fro(g, -bt) < 1e-4, rel_fro(g, -bt)
+    assert rel_fro(Y, oracle.rcs_matvec(s, lam, V)) < 1e-4
+
+
+def test_camera_without_observations(pkg, tiny):
+    """A camera that observes nothing: its block of the reduced system is
+    lambda D_p^2 with D_p^2 at its lower clamp, its update stays zero, and
+    the LM step matches the oracle."""
+    cams = np.vstack([tiny.cams, tiny.cams[:1] + 0.05])
+    sc = dataclasses.replace(tiny, cams=cams)
+    s = Rounded(sc)
+    lam = 1e-4
+    with pkg.Problem.from_scene(sc) as p:
+        p.linearize()
+        p.marginalize_qr(lam)
+        p.pcg_solve()
+        M, g = p.export_rcs_diag()
+        v = np.random.default_rng(10).normal(size=9 * s.n_cam).astype(np.float32)
+        y = p.matvec(v)
+    Mref, bt = oracle.rcs_diag(s, lam)
+    assert rel_fro(M, Mref) < 1e-4
+    assert rel_fro(g, -bt) < 1e-4
+    assert rel_fro(y, oracle.rcs_matvec(s, lam, v[None])[0]) < 1e-4
+    assert np.all(g[-1] == 0.0)
+    with pkg.Problem.from_scene(sc) as p:
+        rep = p.lm_step()
+    _, _, log = oracle.lm(s, max_iters=1, dense=False)
+    assert rep["accepted"] == int(log[0]["accepted"])
+    assert abs(rep["new_cost"] - log[0]["new_cost"]) <= 1e-3 * log[0]["new_cost"]
+
+
 def test_pcg_solution_and_back_substitution(pkg, tiny):
     s = Rounded(tiny)
     lam = 1e-3
