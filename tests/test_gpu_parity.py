@@ -516,6 +516,23 @@ def test_lm_tiny_matches_oracle(pkg, tiny, use_graph):
     assert reps[-1]["stop"] == 1
 
 
+def test_target_cost_stops_at_the_first_step_below_it(pkg, tiny):
+    """With target_cost the LM stops after the first accepted step whose cost
+    is at or below it (the f_tau stop of the time-to-tolerance benchmark)."""
+    s = Rounded(tiny)
+    _, _, log = oracle.lm(s, max_iters=8, dense=False)
+    acc = [e["new_cost"] for e in log if e["accepted"]]
+    assert len(acc) >= 3
+    target = acc[1] * (1 + 1e-6)
+    with pkg.Problem.from_scene(tiny, target_cost=target, max_lm_iters=30) as p:
+        reps = p.solve()
+    accepted = [r for r in reps if r["accepted"]]
+    assert reps[-1]["stop"] == 1 and reps[-1]["accepted"] == 1
+    assert accepted[-1]["new_cost"] <= target
+    assert all(r["new_cost"] > target for r in accepted[:-1])
+    assert len(reps) < 30
+
+
 def test_lm_noise_free_converges(pkg):
     s = make_scene("tiny", 1, noise_px=0.0)
     with pkg.Problem.from_scene(s, func_tol=0.0, max_lm_iters=30) as p:
