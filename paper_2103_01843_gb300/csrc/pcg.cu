@@ -5,8 +5,9 @@
 //
 //   K3  M_i = sum_j A_ji^T A_ji + lambda D_p,i^2,  g_i = -sum_j A_ji^T c_j,
 //       Cholesky-inverted per camera (the block diagonal of H~, Sec. 6.1):
-//       per-observation records from the tile pipeline (matvec.cu), summed
-//       here per camera in a fixed order
+//       by default each term from the Gram identity (below) per chunk of a
+//       camera's observations; optionally from per-observation records of
+//       the tile pipeline (matvec.cu); summed per camera in a fixed order
 //   K4  y = sum_j P_j^T A_j^T (A_j P_j v) (matvec.cu) + lambda D_p^2 v, the pose
 //       damping added only in the product (Sec. 5.3), inside K5
 //   K5  the CG recursion with the Nash-Sofer stop
