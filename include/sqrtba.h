@@ -281,22 +281,24 @@ SQRTBA_API ba_status ba_eval_cost_noalloc(const float* d_cams, int32_t n_cam, co
 /* The matvec (K4) and the preconditioner's record pass (K3) stream the
  * landmark blocks, stored by decreasing k, as tiles: blocks with k <= ksmall
  * are grouped into tiles of up to small_bytes (specialised code per k),
- * larger blocks are cut into row tiles.  The tuner times each of the two
- * kernels on the current damped blocks for ksmall in {8, 13, 21} and
- * small_bytes in {8192, 16384, 32768} (median of five launches each, CUDA
- * events on the problem's stream), keeps the fastest plan of each, then
- * times that plan with 4, 5 and 6 pipeline stages (the matvec also with y
- * accumulated in global instead of shared memory) and keeps the fastest
- * depth, then (when some blocks are cut into row tiles) the largest k whose
- * row tiles take eight rows a warp.  It reports the choices.  The paper parallelises over landmarks with a parallel-for
- * (Sec. 6.1) and has no tuner.
+ * larger blocks are cut into row tiles.  The tuner times the matvec (and,
+ * with precond_from_blocks = 1, the record pass) on the current damped blocks
+ * for ksmall in {8, 13, 21} and small_bytes in {8192, 16384, 32768} (median
+ * of five launches each, CUDA events on the problem's stream, a non-zero
+ * input), keeps the fastest plan of each, then times that plan with 4, 5 and
+ * 6 pipeline stages (the matvec also with y accumulated in global instead of
+ * shared memory) and keeps the fastest depth, then (when some blocks are cut
+ * into row tiles) the largest k whose row tiles take eight rows a warp.  It
+ * reports the choices; the record pass's fields report its plan in use when
+ * it is not tuned.  The paper parallelises over landmarks with a
+ * parallel-for (Sec. 6.1) and has no tuner.
  * Errors: BA_ERR_STATE if the blocks are not marginalised. */
 typedef struct {
     int32_t ksmall;       /* chosen bucket limit of the matvec */
     int32_t small_bytes;  /* chosen tile size of the matvec's small-block buckets */
     double matvec_ms;     /* its matvec time */
     double default_ms;    /* matvec time of the default plan (21, 32768, 6 stages) */
-    double tune_ms;       /* wall time of the tuning (both kernels) */
+    double tune_ms;       /* wall time of the tuning */
     int32_t pc_ksmall;    /* chosen plan of the preconditioner record pass */
     int32_t pc_small_bytes;
     int32_t ns;           /* chosen pipeline depth of the matvec (4, 5 or 6 stages of 32 KB) */
