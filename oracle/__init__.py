@@ -17,6 +17,10 @@ Functions and the passages of the paper they follow:
                    and back substitution (Eq. backsub_sc)
   rcs_matvec     : products with H~ (block-sparse assembly)
   backsub_given  : back substitution and model cost for a given pose step
+  pcg_dense      : the same block-Jacobi PCG and stop rules on a dense SPD matrix
+                   (Sec. 6.1 forcing sequence, Nash-Sofer reading)
+  lm_decide      : accept/reject and damping update of one LM iteration
+                   (Sec. 6.1, Nielsen's rule as the reading)
   lm             : the Levenberg-Marquardt loop of Sec. 6.1
 """
 from __future__ import annotations
@@ -248,6 +252,31 @@ def linear_step(s, lam, dense=True, max_cg=500, cg_eta=0.1, cams=None, pts=None)
                                  ctypes.byref(cg)), "linear_step")
     return dict(dp=dp.reshape(-1, 9), dl=dl.reshape(-1, 3), model_cost=model.value,
                 cost=E.value, cg_iters=cg.value)
+
+
+def pcg_dense(H, g, max_it=500, eta=0.1):
+    """Block-Jacobi PCG on a dense SPD H (9m square): (x, iterations, Q_0..Q_i, status)."""
+    H, g = _f64(H), _f64(g).ravel()
+    n = g.shape[0]
+    assert n % 9 == 0 and H.shape == (n, n)
+    x = np.zeros(n)
+    Q = np.zeros(max_it + 1)
+    st = ctypes.c_int32()
+    it = lib().orc_pcg_dense(ctypes.c_int32(n // 9), _p(H, _d), _p(g, _d), ctypes.c_int32(max_it),
+                             ctypes.c_double(eta), _p(x, _d), _p(Q, _d), ctypes.byref(st))
+    return x, int(it), Q[: it + 1].copy(), int(st.value)
+
+
+def lm_decide(E, E_new, model, lam, nu, func_tol=1e-6, target_cost=0.0):
+    """One LM decision: dict(accepted, stop, rho, lam, nu) after the update."""
+    lam_c, nu_c = ctypes.c_double(lam), ctypes.c_double(nu)
+    stop, rho = ctypes.c_int32(), ctypes.c_double()
+    acc = lib().orc_lm_decide(ctypes.c_double(E), ctypes.c_double(E_new), ctypes.c_double(model),
+                              ctypes.c_double(func_tol), ctypes.c_double(target_cost),
+                              ctypes.byref(lam_c), ctypes.byref(nu_c), ctypes.byref(stop),
+                              ctypes.byref(rho))
+    return dict(accepted=bool(acc), stop=bool(stop.value), rho=rho.value, lam=lam_c.value,
+                nu=nu_c.value)
 
 
 def lm(s, cams=None, pts=None, **kw):

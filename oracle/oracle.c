@@ -541,44 +541,55 @@ static double dot(int64_t n, const double* a, const double* b) {
     return s;
 }
 
-/* Block-Jacobi PCG on H~ dx = g with g = -b~ (Sec. 5.4 / 6.1).
+/* Products y = H x of the operator a PCG run iterates on. */
+typedef void (*orc_matvec_fn)(const void* ctx, const double* x, double* y);
+
+/* Block-Jacobi PCG on H dx = g (Sec. 5.4 / 6.1) for n_blk blocks of 9 unknowns.
+ * Mblk holds the n_blk diagonal 9x9 blocks of H (row-major), mv applies H.
+ * Stop rules (reading of the "forcing sequence" of Sec. 6.1): the truncated-Newton
+ * test of Nash and Sofer i (Q_i - Q_{i-1}) / Q_i < eta with Q(x) = 1/2 x^T H x - g^T x
+ * evaluated as -1/2 x^T (g + r) and Q_0 = Q(0) = 0; ||r_i|| <= 1e-10 ||g||; i = max_it.
+ * x starts at 0.  Qlog (max_it + 1 entries, or NULL) receives Q_0 .. Q_i.
  * Returns the number of iterations; *status = 0 ok, 1 breakdown. */
-static int rcs_pcg(const orc_lin* L, const double* g, double* x, int max_it, double eta,
-                   int* status) {
-    int64_t n = 9 * (int64_t)L->n_cam;
-    double* Minv = (double*)malloc(sizeof(double) * 81 * L->n_cam);
+static int pcg_block_jacobi(int32_t n_blk, orc_matvec_fn mv, const void* ctx,
+                            const double* Mblk, const double* g, double* x, int max_it,
+                            double eta, int* status, double* Qlog) {
+    int64_t n = 9 * (int64_t)n_blk;
+    double* Minv = (double*)malloc(sizeof(double) * 81 * (n_blk > 0 ? n_blk : 1));
     *status = 0;
-    for (int32_t i = 0; i < L->n_cam; ++i) {
-        memcpy(Minv + 81 * i, L->blk + 81 * find_block(L, i, i), sizeof(double) * 81);
+    for (int32_t i = 0; i < n_blk; ++i) {
+        memcpy(Minv + 81 * i, Mblk + 81 * i, sizeof(double) * 81);
         if (chol(9, Minv + 81 * i)) *status = 1;
     }
-    double *r = (double*)malloc(sizeof(double) * n), *z = (double*)malloc(sizeof(double) * n);
-    double *p = (double*)malloc(sizeof(double) * n), *q = (double*)malloc(sizeof(double) * n);
-    double* tmp = (double*)malloc(sizeof(double) * n);
+    double *r = (double*)malloc(sizeof(double) * (n + 1)), *z = (double*)malloc(sizeof(double) * (n + 1));
+    double *p = (double*)malloc(sizeof(double) * (n + 1)), *q = (double*)malloc(sizeof(double) * (n + 1));
+    double* tmp = (double*)malloc(sizeof(double) * (n + 1));
     memset(x, 0, sizeof(double) * n);
     memcpy(r, g, sizeof(double) * n);
     double gnorm = sqrt(dot(n, g, g));
     int it = 0;
+    if (Qlog) Qlog[0] = 0.0;
     if (*status || gnorm == 0) goto done;
-    for (int32_t i = 0; i < L->n_cam; ++i) {
+    for (int32_t i = 0; i < n_blk; ++i) {
         memcpy(z + 9 * i, r + 9 * i, sizeof(double) * 9);
         chol_solve(9, Minv + 81 * i, z + 9 * i);
     }
     memcpy(p, z, sizeof(double) * n);
     double rho = dot(n, r, z), Q0 = 0.0;
     for (it = 1; it <= max_it; ++it) {
-        rcs_matvec(L, p, q);
+        mv(ctx, p, q);
         double pq = dot(n, p, q);
         if (!(pq > 0)) { *status = 1; it -= 1; break; }
         double alpha = rho / pq;
         for (int64_t i = 0; i < n; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
-        if (sqrt(dot(n, r, r)) <= 1e-10 * gnorm) break;
         for (int64_t i = 0; i < n; ++i) tmp[i] = g[i] + r[i];
         double Q1 = -0.5 * dot(n, x, tmp);
+        if (Qlog) Qlog[it] = Q1;
+        if (sqrt(dot(n, r, r)) <= 1e-10 * gnorm) break;
         if (it * (Q1 - Q0) / Q1 < eta) break;
         Q0 = Q1;
         if (it == max_it) break;
-        for (int32_t i = 0; i < L->n_cam; ++i) {
+        for (int32_t i = 0; i < n_blk; ++i) {
             memcpy(z + 9 * i, r + 9 * i, sizeof(double) * 9);
             chol_solve(9, Minv + 81 * i, z + 9 * i);
         }
@@ -590,6 +601,55 @@ static int rcs_pcg(const orc_lin* L, const double* g, double* x, int max_it, dou
     if (it > max_it) it = max_it;
 done:
     free(Minv); free(r); free(z); free(p); free(q); free(tmp);
+    return it;
+}
+
+static void rcs_matvec_cb(const void* ctx, const double* x, double* y) {
+    rcs_matvec((const orc_lin*)ctx, x, y);
+}
+
+/* Block-Jacobi PCG on the damped RCS H~ dx = g with g = -b~, preconditioned by
+ * the diagonal blocks of H~ (Sec. 5.4). */
+static int rcs_pcg(const orc_lin* L, const double* g, double* x, int max_it, double eta,
+                   int* status) {
+    double* Mblk = (double*)malloc(sizeof(double) * 81 * (L->n_cam > 0 ? L->n_cam : 1));
+    for (int32_t i = 0; i < L->n_cam; ++i)
+        memcpy(Mblk + 81 * i, L->blk + 81 * find_block(L, i, i), sizeof(double) * 81);
+    int it = pcg_block_jacobi(L->n_cam, rcs_matvec_cb, L, Mblk, g, x, max_it, eta, status, NULL);
+    free(Mblk);
+    return it;
+}
+
+typedef struct {
+    int64_t n;
+    const double* H;
+} dense_op;
+
+static void dense_matvec_cb(const void* ctx, const double* x, double* y) {
+    const dense_op* d = (const dense_op*)ctx;
+    for (int64_t i = 0; i < d->n; ++i) {
+        double s = 0;
+        for (int64_t j = 0; j < d->n; ++j) s += d->H[i * d->n + j] * x[j];
+        y[i] = s;
+    }
+}
+
+/* The same PCG on a dense SPD matrix H (9 n_blk square, row-major), block-Jacobi
+ * preconditioned by its 9x9 diagonal blocks.  Exposed so that the stop rule can be
+ * checked on systems whose CG iterates are known independently.  Returns the
+ * iteration count; *status as above; Qlog as above (may be NULL). */
+int orc_pcg_dense(int32_t n_blk, const double* H, const double* g, int32_t max_it, double eta,
+                  double* x, double* Qlog, int32_t* status) {
+    int64_t n = 9 * (int64_t)n_blk;
+    double* Mblk = (double*)malloc(sizeof(double) * 81 * (n_blk > 0 ? n_blk : 1));
+    for (int32_t b = 0; b < n_blk; ++b)
+        for (int u = 0; u < 9; ++u)
+            for (int v = 0; v < 9; ++v) Mblk[81 * b + 9 * u + v] = H[(9 * b + u) * n + 9 * b + v];
+    dense_op d = {n, H};
+    int st = 0;
+    int it = pcg_block_jacobi(n_blk, dense_matvec_cb, &d, Mblk, g, x, max_it, eta, &st, Qlog);
+    *status = st;
+    free(Mblk);
     return it;
 }
 
@@ -808,6 +868,37 @@ typedef struct {
     int32_t accepted;
 } orc_iter;
 
+/* The decision that ends one LM iteration (Sec. 6.1: the step is judged by the
+ * ratio of actual and model cost reduction; the damping update follows Nielsen's
+ * rule, the reading of "in line with Ceres").
+ *   rho = (E - En) / (E - model); accept iff En and rho are finite, E - model > 0
+ *   and rho > 1e-3.
+ *   accept: lambda <- lambda * max(1/3, 1 - (2 rho - 1)^3), nu <- 2, lambda >= 1e-16;
+ *           stop when |E - En| / E < func_tol, or when target_cost > 0 and En <= target_cost.
+ *   reject: lambda <- lambda * nu, nu <- 2 nu; stop when lambda >= 1e32.
+ * Returns 1 if the step is accepted; *stop is set to 1 when the loop ends here. */
+int orc_lm_decide(double E, double En, double model, double func_tol, double target_cost,
+                  double* lambda, double* nu, int32_t* stop, double* rho_out) {
+    double rho = (E - En) / (E - model);
+    int acc = isfinite(En) && isfinite(rho) && (E - model) > 0 && rho > 1e-3;
+    *stop = 0;
+    if (rho_out) *rho_out = rho;
+    if (acc) {
+        double t = 2.0 * rho - 1.0;
+        double f = 1.0 - t * t * t;
+        *lambda *= f > 1.0 / 3.0 ? f : 1.0 / 3.0;
+        *nu = 2.0;
+        if (*lambda < 1e-16) *lambda = 1e-16;
+        if (fabs(E - En) / E < func_tol) *stop = 1;
+        if (target_cost > 0 && En <= target_cost) *stop = 1;
+    } else {
+        *lambda *= *nu;
+        *nu *= 2.0;
+        if (*lambda >= 1e32) *stop = 1;
+    }
+    return acc;
+}
+
 /* Levenberg-Marquardt (Sec. 6.1).  cams/pts are updated in place.
  * log has room for opt->max_iters entries; *n_log receives the count. */
 int orc_lm(int32_t n_cam, double* cams, int32_t n_pt, double* pts, int64_t n_obs,
@@ -829,26 +920,18 @@ int orc_lm(int32_t n_cam, double* cams, int32_t n_pt, double* pts, int64_t n_obs
         if (rc) break;
         orc_apply_update(n_cam, cams, dp, n_pt, pts, dl, cn, pn);
         double En = orc_cost(n_cam, cn, n_pt, pn, n_obs, obs_cam, obs_pt, obs_xy);
-        double rho = (E - En) / (E - model);
-        int acc = isfinite(En) && isfinite(rho) && (E - model) > 0 && rho > 1e-3;
+        double lam_it = lambda, rho = 0;
+        int32_t stop = 0;
+        int acc = orc_lm_decide(E, En, model, opt->func_tol, opt->target_cost, &lambda, &nu,
+                                &stop, &rho);
         orc_iter* lg = log + (*n_log)++;
-        lg->cost = E; lg->new_cost = En; lg->model_cost = model; lg->lambda = lambda;
+        lg->cost = E; lg->new_cost = En; lg->model_cost = model; lg->lambda = lam_it;
         lg->rho = rho; lg->cg_iters = cg; lg->accepted = acc;
         if (acc) {
             memcpy(cams, cn, sizeof(double) * np);
             memcpy(pts, pn, sizeof(double) * nl);
-            double t = 2.0 * rho - 1.0;
-            double f = 1.0 - t * t * t;
-            lambda *= f > 1.0 / 3.0 ? f : 1.0 / 3.0;
-            nu = 2.0;
-            if (lambda < 1e-16) lambda = 1e-16;
-            if (fabs(E - En) / E < opt->func_tol) break;
-            if (opt->target_cost > 0 && En <= opt->target_cost) break;
-        } else {
-            lambda *= nu;
-            nu *= 2.0;
-            if (lambda >= 1e32) break;
         }
+        if (stop) break;
     }
     free(dp); free(dl); free(cn); free(pn);
     return rc;

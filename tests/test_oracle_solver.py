@@ -134,27 +134,22 @@ def test_pcg_iterations_fall_as_eta_grows(small):
     assert all(a >= b for a, b in zip(its, its[1:])), its
 
 
-def _check_lm_log(log, lambda0=1e-4):
-    lam, nu = lambda0, 2.0
+def _check_lm_log(log):
+    """Accepted costs never increase and a rejected step leaves the state (its cost)
+    unchanged; the damping sequence itself is pinned in test_oracle_rules.py."""
     last = None
     for e in log:
-        assert e["lam"] == pytest.approx(lam, rel=1e-12)
         if last is not None:
             assert e["cost"] == pytest.approx(last, rel=1e-12)
         if e["accepted"]:
             assert e["new_cost"] <= e["cost"]
-            lam *= max(1 / 3, 1 - (2 * e["rho"] - 1) ** 3)
-            lam = max(lam, 1e-16)
-            nu = 2.0
             last = e["new_cost"]
         else:
-            lam *= nu
-            nu *= 2
             last = e["cost"]
 
 
 @pytest.mark.parametrize("dense", [True, False])
-def test_lm_monotone_and_nielsen(tiny_scene, dense):
+def test_lm_monotone(tiny_scene, dense):
     _, _, log = oracle.lm(tiny_scene, max_iters=20, dense=dense)
     _check_lm_log(log)
     assert log[-1]["accepted"]
