@@ -57,8 +57,15 @@ typedef enum {
     BA_ERR_OOM = 2,         /* device allocation failed */
     BA_ERR_CUDA = 3,        /* a CUDA runtime call failed */
     BA_ERR_STATE = 4,       /* calls out of order (e.g. PCG before marginalisation) */
-    BA_ERR_NUMERIC = 5,     /* non-finite cost / a preconditioner block not positive definite */
-    BA_ERR_TIMEOUT = 6      /* a bounded device-side wait gave up */
+    BA_ERR_NUMERIC = 5,     /* reserved: no call returns it (a preconditioner block that is not
+                               positive definite is replaced by its diagonal and counted in
+                               ba_pcg_report.precond_fallbacks; a non-finite candidate cost
+                               rejects the LM step) */
+    BA_ERR_TIMEOUT = 6      /* a bounded device-side wait gave up (2 s): the kernel returned
+                               early and the results of the call are invalid.  Kernels record
+                               it in an error word that the library reads back at the call's
+                               synchronisation (or at the next call that synchronises), then
+                               clears, so that the handle stays usable */
 } ba_status;
 
 /* Solver settings (Sec. 6.1 gives lambda0, the iteration limits and the
@@ -80,8 +87,9 @@ typedef struct {
                              <= target_cost (e.g. the f_tau of a tolerance test); default 0 */
     int32_t precond_from_blocks; /* 0 (default): the block-Jacobi blocks and g come from the
                              Gram identity (J_s^T J_s - T_s^T T_s per observation, see
-                             ba_pcg_solve); 1: summed from the stored blocks A_j, as the
-                             matvec reads them */
+                             ba_pcg_solve), except for cameras where that difference would
+                             cancel (then from A_j; counted in ba_pcg_report.precond_exact);
+                             1: summed from the stored blocks A_j, as the matvec reads them */
     int32_t reserved;     /* zero */
 } ba_options;
 
@@ -95,6 +103,11 @@ typedef struct {
     double rhs_norm;      /* ||g|| */
     int32_t learned;      /* 1 if the learned warm start / preconditioner was used */
     int32_t warm_start;   /* 1 if the learned warm start was kept (see ba_set_learned) */
+    int32_t precond_fallbacks; /* block-Jacobi blocks that were not numerically positive
+                             definite in FP32 and were replaced by their diagonal */
+    int32_t precond_exact; /* Gram form only: cameras whose block and g were summed from the
+                             stored blocks A_j because the Gram identity would cancel
+                             (sum_s ||J_s||_F^2 > 64 tr(M_i)) */
 } ba_pcg_report;
 
 typedef struct {
@@ -109,6 +122,8 @@ typedef struct {
     double model_cost;    /* ||r + J dx||^2, undamped Gauss-Newton model */
     double lambda;        /* damping used */
     double rho;           /* (cost - new_cost) / (cost - model_cost) */
+    int32_t precond_fallbacks; /* as in ba_pcg_report, for this iteration's solve */
+    int32_t precond_exact;     /* as in ba_pcg_report, for this iteration's solve */
 } ba_lm_report;
 
 /* Creates a problem from host FP64 arrays (layouts above).  Observations are
@@ -486,6 +501,18 @@ SQRTBA_API ba_status ba_debug_export_rcs_diag(ba_problem* h, float* m, float* g)
 
 /* y = H~ v for a host vector v (9 n_cam) with the current blocks and lambda. */
 SQRTBA_API ba_status ba_debug_matvec(ba_problem* h, const float* v, float* y);
+
+/* Failure test of the bounded waits (no counterpart in the paper; tests only).
+ * tile >= 0: every later matvec launch of this problem (ba_debug_matvec, the
+ * PCG) leaves tile `tile` of the first CTA's tile range and the rest of that
+ * range unissued, and its consumer waits give up after wait_ms milliseconds
+ * (0 < wait_ms <= 2000); the call that synchronises next returns
+ * BA_ERR_TIMEOUT.  No wait is unbounded and no copy is left in flight: the
+ * producer lets the copies it issued land before the CTA exits.  tile < 0
+ * restores normal operation (wait_ms ignored).  A captured PCG graph is
+ * rebuilt on the next solve.  Errors: BA_ERR_INVALID_ARG for wait_ms out of
+ * range. */
+SQRTBA_API ba_status ba_debug_fail_matvec(ba_problem* h, int32_t tile, double wait_ms);
 
 /* The last step: dx_p (9 n_cam) and dx_l (3 n_pt). */
 SQRTBA_API ba_status ba_debug_export_step(ba_problem* h, float* dp, float* dl);

@@ -47,7 +47,8 @@ class Options(ctypes.Structure):
 class PcgReport(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("stop_reason", ctypes.c_int32),
                 ("residual_norm", ctypes.c_double), ("rhs_norm", ctypes.c_double),
-                ("learned", ctypes.c_int32), ("warm_start", ctypes.c_int32)]
+                ("learned", ctypes.c_int32), ("warm_start", ctypes.c_int32),
+                ("precond_fallbacks", ctypes.c_int32), ("precond_exact", ctypes.c_int32)]
 
 
 class LmReport(ctypes.Structure):
@@ -56,7 +57,8 @@ class LmReport(ctypes.Structure):
                 ("stop", ctypes.c_int32), ("pcg_stop_reason", ctypes.c_int32),
                 ("cost", ctypes.c_double), ("new_cost", ctypes.c_double),
                 ("model_cost", ctypes.c_double), ("lambda_", ctypes.c_double),
-                ("rho", ctypes.c_double)]
+                ("rho", ctypes.c_double), ("precond_fallbacks", ctypes.c_int32),
+                ("precond_exact", ctypes.c_int32)]
 
 
 class LmState(ctypes.Structure):
@@ -169,6 +171,7 @@ _SIGS = {
     "ba_debug_export_jacobians": [_P, _f, _f, _f],
     "ba_debug_export_rcs_diag": [_P, _f, _f],
     "ba_debug_matvec": [_P, _f, _f],
+    "ba_debug_fail_matvec": [_P, ctypes.c_int32, ctypes.c_double],
     "ba_debug_export_step": [_P, _f, _f],
 }
 
@@ -424,6 +427,11 @@ class Problem:
         y = np.zeros_like(v)
         self._check(lib().ba_debug_matvec(self.h, _ptr(v, _f), _ptr(y, _f)))
         return y
+
+    def debug_fail_matvec(self, tile, wait_ms=1.0):
+        """Failure test hook: later matvecs leave `tile` of the first CTA
+        unissued and give up waiting after wait_ms (tile < 0 restores)."""
+        self._check(lib().ba_debug_fail_matvec(self.h, int(tile), float(wait_ms)))
 
     def export_step(self):
         dp = np.zeros(9 * self.n_cam, np.float32)

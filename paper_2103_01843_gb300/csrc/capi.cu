@@ -169,6 +169,35 @@ void sync(Problem& p) {
     if (p.prof.on) prof_resolve(p);
 }
 
+// The error words copied back with the last synchronisation (err_host): a
+// bounded device wait that gave up (ERRBIT_TIMEOUT from the matvec / record
+// pass, or from the attached model's tensor-core waits in err_host[3]) fails
+// the call with BA_ERR_TIMEOUT; the counts of preconditioner blocks replaced
+// by their diagonal and of cameras whose blocks were summed from the stored
+// blocks are kept for the reports.  Words that were set are cleared on the
+// device, in stream order, so that the handle stays usable.
+void check_device_errors(Problem& p) {
+    uint32_t* e = p.err_host;
+    p.precond_fallbacks = (int32_t)e[1];
+    p.precond_exact = (int32_t)e[2];
+    const bool timeout = ((e[0] | e[3]) & ERRBIT_TIMEOUT) != 0;
+    if (e[0] || e[1] || e[2]) BA_CUDA_TRY(cudaMemsetAsync(p.err, 0, 3 * sizeof(uint32_t), p.stream));
+    if (e[3] && p.mlp) BA_CUDA_TRY(cudaMemsetAsync(p.mlp->err, 0, sizeof(uint32_t), p.stream));
+    e[0] = e[1] = e[2] = e[3] = 0;
+    if (timeout)
+        throw Error{BA_ERR_TIMEOUT,
+                    "a bounded device-side wait gave up; the kernel returned early and the results of this call "
+                    "are invalid"};
+}
+
+// Synchronises with the error words copied back first, then checks them.
+void sync_checked(Problem& p) {
+    d2h(p, p.err_host, p.err, 3);
+    if (p.mlp && p.learned_active) d2h(p, p.err_host + 3, p.mlp->err, 1);
+    sync(p);
+    check_device_errors(p);
+}
+
 void destroy_graph(Problem& p) {
     if (p.pcg_graph) cudaGraphExecDestroy(p.pcg_graph);
     p.pcg_graph = nullptr;
@@ -187,9 +216,10 @@ void free_all(Problem& p) {
     for (void* a : p.allocations) cudaFreeAsync(a, p.stream);
     p.allocations.clear();
     pinned_put(p.pcg_host, sizeof(PcgScalars));
-    pinned_put(p.dsum_host, 4 * sizeof(double));
+    pinned_put(p.dsum_host, 6 * sizeof(double));
     p.pcg_host = nullptr;
     p.dsum_host = nullptr;
+    p.err_host = nullptr;
     if (p.side) cudaStreamDestroy(p.side);
     for (cudaEvent_t e : {p.ev_fork, p.ev_join})
         if (e) cudaEventDestroy(e);
@@ -223,7 +253,7 @@ void do_linearize(Problem& p, bool need_cost = true, double damp_lambda = 0.0, b
             p.cost_valid = false;
         } else {
             d2h(p, p.dsum_host, p.dsum, 1);
-            sync(p);
+            sync_checked(p);
             p.cost = p.dsum_host[0];
             p.cost_valid = true;
         }
@@ -493,7 +523,7 @@ void pcg_iterate(Problem& p, bool wait) {
         count_launches(p, 2);  // per iteration; the rest is added when the count is known
         p.pending_iteration_launches = true;
         d2h(p, p.pcg_host, p.pcg, 1);
-        if (wait) sync(p);
+        if (wait) sync_checked(p);
         return;
     }
     int launched = 0, it_before = 0;
@@ -506,7 +536,7 @@ void pcg_iterate(Problem& p, bool wait) {
         }
         launched += PCG_CHUNK;
         d2h(p, p.pcg_host, p.pcg, 1);
-        sync(p);
+        sync_checked(p);
         if (p.prof.on) {
             const int real = std::min(PCG_CHUNK, p.pcg_host->it - it_before);
             for (int i = 0; i < real; ++i) {
@@ -551,6 +581,8 @@ void fill_pcg_report(const Problem& p, ba_pcg_report* rep) {
     rep->rhs_norm = p.pcg_host->gnorm;
     rep->learned = p.learned_active ? 1 : 0;
     rep->warm_start = p.learned_active ? p.pcg_host->warm : 0;
+    rep->precond_fallbacks = p.precond_fallbacks;
+    rep->precond_exact = p.precond_exact;
 }
 
 void do_pcg(Problem& p, ba_pcg_report* rep) {
@@ -568,7 +600,7 @@ double do_backsub(Problem& p) {
     launch_backsub(p);
     t.end();
     d2h(p, p.dsum_host + 1, p.dsum + 1, 1);
-    sync(p);
+    sync_checked(p);
     p.backsubbed = true;
     return p.dsum_host[1];
 }
@@ -582,7 +614,7 @@ double do_eval_cost(Problem& p, bool candidate) {
     launch_cost(p, candidate);
     t.end();
     d2h(p, p.dsum_host, p.dsum, 1);
-    sync(p);
+    sync_checked(p);
     return p.dsum_host[0];
 }
 
@@ -608,8 +640,11 @@ void do_lm_step(Problem& p, ba_lm_report* rep) {
         launch_backsub_candidate_cost(p);
         tb.end();
     }
-    d2h(p, p.dsum_host, p.dsum, 3);
+    // the scalars and, behind them in the same allocation, the error words
+    d2h(p, p.dsum_host, p.dsum, 6);
+    if (learned && p.mlp) d2h(p, p.err_host + 3, p.mlp->err, 1);
     sync(p);
+    check_device_errors(p);
     if (p.cost_pending) {
         p.cost = p.dsum_host[2];
         p.cost_valid = true;
@@ -634,6 +669,8 @@ void do_lm_step(Problem& p, ba_lm_report* rep) {
     r.rho = rho;
     r.cg_iters = pr.iterations;
     r.pcg_stop_reason = pr.stop_reason;
+    r.precond_fallbacks = pr.precond_fallbacks;
+    r.precond_exact = pr.precond_exact;
     r.accepted = acc ? 1 : 0;
     if (acc) {
         std::swap(p.cams, p.cand_cams);
@@ -716,11 +753,15 @@ void create_problem(Problem& p, const double* cams, int32_t n_cam, const double*
     p.mv_cam = dalloc<int32_t>(p, n_obs + 8);
     p.c_off = dalloc<int32_t>(p, n_pt + 1);
     p.cam_list_st = dalloc<int32_t>(p, n_obs);
-    p.err = dalloc<uint32_t>(p, 4);
-    p.dsum = dalloc<double>(p, 4);
+    // dsum [0..3] and the error words behind it: one copy brings back both
+    p.dsum = dalloc<double>(p, 6);
+    p.err = reinterpret_cast<uint32_t*>(p.dsum + 4);
     p.pcg = dalloc<PcgScalars>(p, 1);
     p.pcg_host = static_cast<PcgScalars*>(pinned_get(sizeof(PcgScalars)));
-    p.dsum_host = static_cast<double*>(pinned_get(4 * sizeof(double)));
+    p.dsum_host = static_cast<double*>(pinned_get(6 * sizeof(double)));
+    p.err_host = reinterpret_cast<uint32_t*>(p.dsum_host + 4);
+    std::memset(p.dsum_host, 0, 6 * sizeof(double));
+    BA_CUDA_TRY(cudaMemsetAsync(p.dsum, 0, 6 * sizeof(double), p.stream));
     std::memset(p.pcg_host, 0, sizeof(PcgScalars));
 
     // stage the FP64 inputs on the device for validation and grouping
@@ -958,6 +999,19 @@ void do_batch_solve(Problem& p, ba_batch_report* reps, ba_batch_summary* sum) {
         sum->total_ms = t_end[n_it];
         sum->tune_ms = tune_ms;
         sum->kernel_launches = p.launches - launches0;
+    }
+}
+
+// Synchronises the model's stream and reads its error word: a tensor-core
+// wait that gave up fails the call with BA_ERR_TIMEOUT (the word is cleared).
+void mlp_sync_checked(Mlp& m) {
+    uint32_t e = 0;
+    BA_CUDA_TRY(cudaMemcpyAsync(&e, m.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, m.stream));
+    BA_CUDA_TRY(cudaStreamSynchronize(m.stream));
+    if (e) {
+        BA_CUDA_TRY(cudaMemsetAsync(m.err, 0, sizeof(uint32_t), m.stream));
+        if (e & ERRBIT_TIMEOUT)
+            throw Error{BA_ERR_TIMEOUT, "a bounded tensor-core wait of the model gave up; outputs are invalid"};
     }
 }
 
@@ -1306,7 +1360,24 @@ ba_status ba_debug_matvec(ba_problem* h, const float* v, float* y) {
     d2h(p, y, dy, n);
     cudaFreeAsync(dv, p.stream);
     cudaFreeAsync(dy, p.stream);
-    sync(p);
+    sync_checked(p);
+    return BA_OK;
+    API_CATCH(h)
+}
+
+ba_status ba_debug_fail_matvec(ba_problem* h, int32_t tile, double wait_ms) {
+    if (!h) return BA_ERR_INVALID_ARG;
+    API_TRY
+    Problem& p = h->p;
+    if (tile >= 0) {
+        require(wait_ms > 0.0 && wait_ms <= 2000.0, BA_ERR_INVALID_ARG, "wait_ms must be in (0, 2000]");
+        p.dbg_fail_tile = tile;
+        p.dbg_wait_ns = (uint64_t)(wait_ms * 1e6);
+    } else {
+        p.dbg_fail_tile = -1;
+        p.dbg_wait_ns = 0;
+    }
+    destroy_graph(p);  // the captured launches hold the old arguments
     return BA_OK;
     API_CATCH(h)
 }
@@ -1518,7 +1589,7 @@ ba_status ba_mlp_forward(ba_mlp* h, const float* d_feats, int32_t n, float* d_ou
     if (!h || !d_feats || !d_out || n < 1) return BA_ERR_INVALID_ARG;
     MLP_TRY
     mlp_forward(h->m, d_feats, n, d_out);
-    BA_CUDA_TRY(cudaStreamSynchronize(h->m.stream));
+    mlp_sync_checked(h->m);
     return BA_OK;
     MLP_CATCH(h)
 }
@@ -1539,10 +1610,9 @@ ba_status ba_mlp_loss_grad(ba_mlp* h, const float* d_feats, const float* d_aux, 
     MLP_TRY
     const double l = mlp_loss_grad(h->m, d_feats, d_aux, n);
     if (loss) *loss = l;
-    if (grads) {
+    if (grads)
         BA_CUDA_TRY(cudaMemcpyAsync(grads, h->m.grad, sizeof(float) * ML_P, cudaMemcpyDeviceToHost, h->m.stream));
-        BA_CUDA_TRY(cudaStreamSynchronize(h->m.stream));
-    }
+    mlp_sync_checked(h->m);
     return BA_OK;
     MLP_CATCH(h)
 }

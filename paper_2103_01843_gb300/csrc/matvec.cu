@@ -92,6 +92,12 @@ struct MvArgs {
     const float* cpool;  // preconditioner mode: c_j in storage order
     float* rec;          // preconditioner mode: REC floats per observation (storage order)
     int big8_kmax;       // big tiles with k up to this take eight rows a warp (else four)
+    // failure test hooks (defaults WAIT_NS and -1): the limit of the consumer
+    // and empty-stage waits, and a tile of CTA 0 the producer does not issue
+    // (its consumers' waits then run out and the kernel returns with
+    // ERRBIT_TIMEOUT raised).  The producer's final drain keeps WAIT_NS.
+    uint64_t wait_ns;
+    int fail_tile;
 };
 
 // --- consumers ---------------------------------------------------------------------
@@ -465,7 +471,10 @@ __global__ void __launch_bounds__(MV_THREADS, 1) k_matvec_tiles(MvArgs a) {
                 int ok = 1;
                 if (lane == 0) {
                     const int i = base + q - tb, s = i % MV_STAGES;
-                    if (i >= MV_STAGES && !mbar_wait(empty_bar(s), ((i / MV_STAGES) - 1) & 1, abort_flag, a.err)) {
+                    if (i == a.fail_tile && blockIdx.x == 0) {
+                        ok = 0;  // test hook: this tile and the rest of the CTA's range are never issued
+                    } else if (i >= MV_STAGES && !mbar_wait(empty_bar(s), ((i / MV_STAGES) - 1) & 1, abort_flag,
+                                                            a.err, true, a.wait_ns)) {
                         ok = 0;
                     } else {
                         // the consumer warps the tile does not need arrive on
@@ -503,7 +512,7 @@ __global__ void __launch_bounds__(MV_THREADS, 1) k_matvec_tiles(MvArgs a) {
                 }
             }
         }
-        if (lane == 0 && *abort_flag) {
+        if (lane == 0 && (stop || *abort_flag)) {
             // let the copies already issued land before the CTA exits
             for (int i = max(0, issued - MV_STAGES); i < issued; ++i)
                 mbar_wait(full_bar(i % MV_STAGES), (i / MV_STAGES) & 1, abort_flag, a.err, false);
@@ -539,8 +548,8 @@ __global__ void __launch_bounds__(MV_THREADS, 1) k_matvec_tiles(MvArgs a) {
                 start = (start + need) % MV_CONSUMERS;
                 if (vcw >= need) continue;
                 const int i = base + q - tb, s = i % MV_STAGES;
-                if (!seq_wait(seq + s, i, abort_flag, a.err) ||
-                    !mbar_wait(full_bar(s), (i / MV_STAGES) & 1, abort_flag, a.err)) {
+                if (!seq_wait(seq + s, i, abort_flag, a.err, a.wait_ns) ||
+                    !mbar_wait(full_bar(s), (i / MV_STAGES) & 1, abort_flag, a.err, true, a.wait_ns)) {
                     stop = true;
                     break;
                 }
@@ -618,7 +627,8 @@ MvKernel pick_kernel(const Problem& p, const Problem::TilePlan& plan, bool pc) {
 
 MvArgs make_args(Problem& p, const Problem::TilePlan& plan, const float* v, float* y, const PcgScalars* S) {
     return MvArgs{static_cast<const MvTile*>(plan.tiles), plan.begin, p.apool, p.mv_cam, p.lm_by_k, p.pt_off,
-                  p.obs_cam_s, p.a_off, v, y, p.n_cam, S, p.err, p.cpool, p.prec, plan.big8_kmax};
+                  p.obs_cam_s, p.a_off, v, y, p.n_cam, S, p.err, p.cpool, p.prec, plan.big8_kmax,
+                  p.dbg_wait_ns > 0 ? p.dbg_wait_ns : WAIT_NS, &plan == &p.mv_plan ? p.dbg_fail_tile : -1};
 }
 
 }  // namespace

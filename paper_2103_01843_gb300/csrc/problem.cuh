@@ -165,9 +165,21 @@ struct Problem {
     float* dl = nullptr;
     // reductions
     double* partials = nullptr;      // per-block FP64 partial sums
-    double* dsum = nullptr;          // [0] cost, [1] model cost
-    double* dsum_host = nullptr;     // pinned mirror
-    uint32_t* err = nullptr;         // kernel error bits
+    double* dsum = nullptr;          // [0] cost, [1] model cost, [2] deferred cost; err follows at [4]
+    double* dsum_host = nullptr;     // pinned mirror (6 doubles)
+    uint32_t* err = nullptr;         // kernel error words (inside dsum's allocation, so that one copy
+                                     // brings back the scalars and the errors): [0] ERRBIT_* bits,
+                                     // [1] preconditioner blocks replaced by their diagonal,
+                                     // [2] cameras whose Gram-form sums were replaced by sums over
+                                     // the stored blocks (cancellation guard)
+    uint32_t* err_host = nullptr;    // pinned mirror of err[0..3] (inside dsum_host); [3] receives
+                                     // the attached model's error word
+    int32_t precond_fallbacks = 0;   // err[1] at the last synchronisation
+    int32_t precond_exact = 0;       // err[2] at the last synchronisation
+    // failure test hooks of the matvec (ba_debug_fail_matvec): wait limit (0: WAIT_NS)
+    // and a tile of CTA 0 that is never issued (-1: none)
+    uint64_t dbg_wait_ns = 0;
+    int32_t dbg_fail_tile = -1;
     int red_grid = 0;
 
     // CUDA graph of a chunk of PCG iterations

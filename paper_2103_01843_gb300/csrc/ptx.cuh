@@ -51,16 +51,17 @@ __device__ __forceinline__ uint64_t global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// Bounded wait for the phase of `parity`; false after WAIT_NS (2 s) or when
-// another warp has aborted (honour_abort); a timeout raises ERRBIT_TIMEOUT.
+// Bounded wait for the phase of `parity`; false after `limit` ns (WAIT_NS = 2 s
+// unless a test shortens it) or when another warp has aborted (honour_abort);
+// a timeout raises ERRBIT_TIMEOUT.
 __device__ inline bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint32_t* err,
-                          bool honour_abort = true) {
+                          bool honour_abort = true, uint64_t limit = WAIT_NS) {
     if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (;;) {
         if (mbar_try(bar, parity)) return true;
         if (honour_abort && *abort_flag) return false;
-        if (global_ns() - t0 > WAIT_NS) {
+        if (global_ns() - t0 > limit) {
             *abort_flag = 1;
             atomicOr(err, ERRBIT_TIMEOUT);
             return false;
@@ -69,15 +70,16 @@ __device__ inline bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* ab
 }
 
 // Bounded wait until *p == v (a shared-memory word another warp of the CTA
-// sets); false after WAIT_NS or when another warp has aborted; a timeout
+// sets); false after `limit` ns or when another warp has aborted; a timeout
 // raises ERRBIT_TIMEOUT.
-__device__ inline bool seq_wait(volatile int* p, int v, volatile int* abort_flag, uint32_t* err) {
+__device__ inline bool seq_wait(volatile int* p, int v, volatile int* abort_flag, uint32_t* err,
+                                uint64_t limit = WAIT_NS) {
     if (*p == v) return true;
     const uint64_t t0 = global_ns();
     for (;;) {
         if (*p == v) return true;
         if (*abort_flag) return false;
-        if (global_ns() - t0 > WAIT_NS) {
+        if (global_ns() - t0 > limit) {
             *abort_flag = 1;
             atomicOr(err, ERRBIT_TIMEOUT);
             return false;

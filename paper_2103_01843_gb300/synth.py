@@ -119,10 +119,14 @@ def _yaw_frame(yaw):
     return _look_at(np.zeros(3), c)
 
 
-def _intrinsics(rng, n):
-    f = rng.normal(500.0, 20.0, n)
-    k1 = rng.normal(0.0, 1e-3, n)
-    k2 = rng.normal(0.0, 1e-3, n)
+def _intrinsics(rng, n, f_range=None, dist_sigma=1e-3):
+    """f ~ N(500, 20) px (or log-uniform over f_range), k1, k2 ~ N(0, dist_sigma^2)."""
+    if f_range is None:
+        f = rng.normal(500.0, 20.0, n)
+    else:
+        f = np.exp(rng.uniform(np.log(f_range[0]), np.log(f_range[1]), n))
+    k1 = rng.normal(0.0, dist_sigma, n)
+    k2 = rng.normal(0.0, dist_sigma, n)
     return f, k1, k2
 
 
@@ -157,7 +161,7 @@ def _ring_cameras(rng, n_cam, radius, height_sigma, target_sigma):
 
 
 def _gt_ring(rng, n_cam, n_pt, radius, box_half, k_sampler, window=None,
-             height_sigma=0.0, target_sigma=0.0, chunk=20000):
+             height_sigma=0.0, target_sigma=0.0, chunk=20000, f_range=None, dist_sigma=1e-3):
     """Cameras on a ring facing the centre, points uniform in a box.
 
     Each point draws k and then k distinct cameras uniformly from a window
@@ -166,7 +170,7 @@ def _gt_ring(rng, n_cam, n_pt, radius, box_half, k_sampler, window=None,
     chosen views are not all valid is re-drawn (rejection sampling).
     """
     R, t = _ring_cameras(rng, n_cam, radius, height_sigma, target_sigma)
-    f, k1, k2 = _intrinsics(rng, n_cam)
+    f, k1, k2 = _intrinsics(rng, n_cam, f_range, dist_sigma)
     X = rng.uniform(-box_half, box_half, (n_pt, 3))
     win = n_cam if (window is None or window >= n_cam) else window
     obs_cam, obs_pt = [], []
@@ -315,6 +319,80 @@ def _finish(rng, name, seed, R, t, f, k1, k2, X, obs_cam, obs_pt,
 CONFIGS = ("tiny", "medium", "large", "small", "batched_member", "walk")
 
 
+def degenerate_scene(seed=0, n_pt=300, noise_px=1.0):
+    """A small ring scene plus landmarks on which the method's degenerate
+    branches run (no gauge normalisation; the special cameras and landmarks
+    keep their exact ground-truth state).
+
+    Cameras 0..7 form a ring of radius 10 m facing the origin (perturbed
+    initial state).  Camera 8 (axis-angle exactly 0, centre (0, 0, 10)) and
+    camera 9 (axis-angle 0, centre (0, 0, 14)) look down the z axis; camera 10
+    shares camera 8's centre and is tilted by 0.2 rad.  Landmarks:
+      n_pt regular points in a 5 m cube, seen by the cameras that see them;
+      `axis`: (0, 0, 0.5), seen by cameras 8 and 9 only: both project it onto
+        their optical axis (P_x = P_y = 0 exactly), so the depth column of its
+        landmark Jacobian is exactly zero (rank 2, a zero sub-column in the
+        third Householder step);
+      `same_centre`: seen by cameras 8 and 10 only, which share a centre: the
+        ray direction is a null vector of its landmark Jacobian (rank 2 in
+        exact arithmetic);
+      `near`: 0.08 m in front of camera 8 (and seen by camera 9 from 4.08 m):
+        a near-zero depth with Jacobian entries of order f / depth.
+    Returns (scene, dict of the special landmark indices)."""
+    rng = np.random.default_rng(seed)
+    n_ring = 8
+    Rr, tr = _ring_cameras(rng, n_ring, 10.0, 0.3, 0.0)
+    fr, k1r, k2r = _intrinsics(rng, n_ring)
+    tilt = Rotation.from_rotvec([0.2, 0.0, 0.0]).as_matrix()
+    Rs = np.stack([np.eye(3), np.eye(3), tilt])
+    Cs = np.array([[0.0, 0.0, 10.0], [0.0, 0.0, 14.0], [0.0, 0.0, 10.0]])
+    ts = -np.einsum("nij,nj->ni", Rs, Cs)
+    R = np.concatenate([Rr, Rs])
+    t = np.concatenate([tr, ts])
+    f = np.concatenate([fr, [500.0, 520.0, 480.0]])
+    k1 = np.concatenate([k1r, [0.0, 0.0, 0.0]])
+    k2 = np.concatenate([k2r, [0.0, 0.0, 0.0]])
+    n_cam = R.shape[0]
+    X = rng.uniform(-2.5, 2.5, (n_pt, 3))
+    vis = _visible(R[None], t[None], f[None], k1[None], k2[None], X[:, None, :])
+    keep = vis.sum(1) >= 2
+    X, vis = X[keep], vis[keep]
+    obs_pt, obs_cam = np.nonzero(vis)
+    # the direction that camera 10 sees at pixel (40, -30), from the common centre
+    d10 = np.array([40.0 / 480.0, -30.0 / 480.0, -1.0])
+    X_same = Cs[0] + 6.0 * (tilt.T @ d10)
+    special = np.array([[0.0, 0.0, 0.5], X_same, [0.0005, -0.0004, 9.92]])
+    views = [(8, 9), (8, 10), (8, 9)]
+    base = X.shape[0]
+    X = np.concatenate([X, special])
+    for i, cams in enumerate(views):
+        obs_pt = np.concatenate([obs_pt, np.full(len(cams), base + i)])
+        obs_cam = np.concatenate([obs_cam, np.array(cams)])
+    order = np.lexsort((obs_cam, obs_pt))
+    obs_cam = obs_cam[order].astype(np.int32)
+    obs_pt = obs_pt[order].astype(np.int32)
+    pix, depth = _project_mat(R[obs_cam], t[obs_cam], f[obs_cam], k1[obs_cam], k2[obs_cam], X[obs_pt])
+    assert (depth > 0).all()
+    obs_xy = pix + rng.normal(0.0, noise_px, pix.shape)
+    # perturbed initial state of the ring cameras and the regular points only
+    dR = Rotation.from_rotvec(rng.normal(0.0, 0.01, (n_ring, 3))).as_matrix()
+    R0 = R.copy()
+    R0[:n_ring] = np.einsum("nij,njk->nik", dR, R[:n_ring])
+    t0 = t.copy()
+    t0[:n_ring] += rng.normal(0.0, 0.05, (n_ring, 3))
+    X0 = X.copy()
+    X0[:base] += rng.normal(0.0, 0.1, (base, 3))
+
+    def pack(Rm, tv):
+        aa = Rotation.from_matrix(Rm).as_rotvec()
+        aa[n_ring:n_ring + 2] = 0.0  # exactly zero for the axis cameras
+        return np.concatenate([aa, tv, f[:, None], k1[:, None], k2[:, None]], 1)
+
+    sc = Scene(cams=pack(R0, t0), pts=X0, obs_cam=obs_cam, obs_pt=obs_pt, obs_xy=obs_xy,
+               cams_gt=pack(R, t), pts_gt=X, name="degenerate", seed=seed)
+    return sc, dict(axis=base, same_centre=base + 1, near=base + 2, n_cam=n_cam)
+
+
 def make_scene(name="tiny", seed=0, noise_px=1.0, perturb=True, **kw):
     """Build one seeded synthetic scene.
 
@@ -328,7 +406,9 @@ def make_scene(name="tiny", seed=0, noise_px=1.0, perturb=True, **kw):
              k = min(200, 2 + floor(Pareto(1.5))), cameras drawn from a
              window of 600 ring neighbours (heavy-tailed, venice-like).
     small  : tiny-like ring with n_cam / n_pt / p given by keywords
-             (defaults 32 cams, 2000 points, p = 0.3, cap 32).
+             (defaults 32 cams, 2000 points, p = 0.3, cap 32); f_range =
+             (lo, hi) draws focal lengths log-uniformly, dist_sigma sets the
+             spread of k1, k2 (ill-conditioned camera sets).
     batched_member : member `seed` of the 256-problem batch: cams U[8, 64],
              points U[200, 5000], k = 2 + Geom0(0.3) capped at n_cam.
     walk   : medium-shaped (the medium generator and k distribution) with
@@ -349,7 +429,8 @@ def make_scene(name="tiny", seed=0, noise_px=1.0, perturb=True, **kw):
         n_pt = kw.get("n_pt", 2000)
         gt = _gt_ring(rng, n_cam, n_pt, 10.0, 2.5,
                       _geom0(kw.get("p", 0.3), kw.get("cap", 32)),
-                      height_sigma=0.5)
+                      height_sigma=0.5, f_range=kw.get("f_range"),
+                      dist_sigma=kw.get("dist_sigma", 1e-3))
     elif name == "walk":
         gt = _gt_walk(rng, kw.get("n_cam", 100), kw.get("n_pt", 20_000), _geom0(0.2, 64))
     elif name == "batched_member":
