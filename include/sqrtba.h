@@ -90,7 +90,14 @@ typedef struct {
                              ba_pcg_solve), except for cameras where that difference would
                              cancel (then from A_j; counted in ba_pcg_report.precond_exact);
                              1: summed from the stored blocks A_j, as the matvec reads them */
-    int32_t reserved;     /* zero */
+    int32_t implicit_blocks; /* 0 (default): Q2^T J_p is stored per landmark (2k x 9k floats,
+                             Sec. 5.1).  1: the factorisation is stored instead (per
+                             observation J_s and its Householder rows, per landmark the
+                             compact-WY factor and the damping rotations' effect, O(k)
+                             memory, the variant of Table tab:complexities' storage
+                             discussion); products with A_j are formed on the fly in K4.
+                             Same results up to rounding; ba_debug_export_landmark then
+                             exports only the undamped top rows */
 } ba_options;
 
 /* Fills *opt with the defaults above. */

@@ -41,7 +41,7 @@ class Options(ctypes.Structure):
                 ("cg_eta", ctypes.c_double), ("use_graph", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("use_learned", ctypes.c_int32),
                 ("pipeline_stages", ctypes.c_int32), ("target_cost", ctypes.c_double),
-                ("precond_from_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("precond_from_blocks", ctypes.c_int32), ("implicit_blocks", ctypes.c_int32)]
 
 
 class PcgReport(ctypes.Structure):
@@ -390,18 +390,32 @@ class Problem:
                                                 _ptr(cam_off, _i64), _ptr(cam_list, _i32)))
         return perm, pt_off, cam_off, cam_list
 
-    def export_landmark(self, j, k_cap=256):
+    def export_landmark(self, j, k_cap=256, top_only=False):
+        """Landmark j's top rows, A_j, c_j and rotations (top_only: the top
+        rows alone, the only part the implicit storage keeps)."""
         top = np.zeros(3 * (9 * k_cap + 4), np.float32)
-        a = np.zeros(2 * k_cap * 9 * k_cap, np.float32)
+        a = np.zeros(2 * k_cap * 9 * k_cap if not top_only else 1, np.float32)
         c = np.zeros(2 * k_cap, np.float32)
         rot = np.zeros(12, np.float32)
         k = ctypes.c_int32()
-        self._check(lib().ba_debug_export_landmark(self.h, int(j), int(k_cap), _ptr(top, _f), _ptr(a, _f),
-                                                   _ptr(c, _f), _ptr(rot, _f), ctypes.byref(k)))
+        none = ctypes.POINTER(ctypes.c_float)()
+        self._check(lib().ba_debug_export_landmark(
+            self.h, int(j), int(k_cap), _ptr(top, _f), none if top_only else _ptr(a, _f),
+            none if top_only else _ptr(c, _f), none if top_only else _ptr(rot, _f), ctypes.byref(k)))
         k = k.value
         n = 9 * k
-        return dict(k=k, top=top[: 3 * (n + 4)].reshape(3, n + 4), a=a[: 2 * k * n].reshape(2 * k, n),
-                    c=c[: 2 * k], rot=rot.reshape(6, 2))
+        out = dict(k=k, top=top[: 3 * (n + 4)].reshape(3, n + 4))
+        if not top_only:
+            out.update(a=a[: 2 * k * n].reshape(2 * k, n), c=c[: 2 * k], rot=rot.reshape(6, 2))
+        return out
+
+    def set_options(self, **kw):
+        """Change options of the live problem (ba_set_options)."""
+        opt = Options.from_buffer_copy(self.options)
+        for key, val in kw.items():
+            setattr(opt, key, val)
+        self._check(lib().ba_set_options(self.h, ctypes.byref(opt)))
+        self.options = opt
 
     def export_damping(self):
         dp2 = np.zeros(9 * self.n_cam, np.float32)

@@ -24,7 +24,8 @@ constexpr int BS_WARPS = 8;
 // three top rows (coalesced), then the 3x3 triangular solve
 __global__ void __launch_bounds__(32 * BS_WARPS)
 k_backsub_dl(int n_pt, const int32_t* __restrict__ pt_off, const int32_t* __restrict__ obs_cam_s,
-             const float* __restrict__ tpool, const float* __restrict__ dp, float* __restrict__ dl) {
+             const float* __restrict__ tpool, const float* __restrict__ dp, float* __restrict__ dl,
+             const float* __restrict__ lmrec, const int32_t* __restrict__ lm_pos) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int j = blockIdx.x * BS_WARPS + w;
     if (j >= n_pt) return;
@@ -48,6 +49,24 @@ k_backsub_dl(int n_pt, const int32_t* __restrict__ pt_off, const int32_t* __rest
         t0 += R0[3];
         t1 += R1[3];
         t2 += R2[3];
+        if (lmrec) {
+            // implicit storage: undamped top rows; the damped right-hand side is
+            // G_tt times theirs and the damped R is stored with G_tt
+            const float* L = lmrec + 32LL * lm_pos[j];
+            const float* G = L + 16;
+            const float a0 = t0, a1 = t1, a2 = t2;
+            t0 = G[0] * a0 + G[1] * a1 + G[2] * a2;
+            t1 = G[3] * a0 + G[4] * a1 + G[5] * a2;
+            t2 = G[6] * a0 + G[7] * a1 + G[8] * a2;
+            const float r00 = L[25], r01 = L[26], r02 = L[27], r11 = L[28], r12 = L[29], r22 = L[30];
+            const float l2 = -t2 / r22;
+            const float l1 = (-t1 - r12 * l2) / r11;
+            const float l0 = (-t0 - r01 * l1 - r02 * l2) / r00;
+            dl[3 * j] = l0;
+            dl[3 * j + 1] = l1;
+            dl[3 * j + 2] = l2;
+            return;
+        }
         const float l2 = -t2 / R2[2];
         const float l1 = (-t1 - R1[2] * l2) / R1[1];
         const float l0 = (-t0 - R0[1] * l1 - R0[2] * l2) / R0[0];
@@ -194,8 +213,8 @@ __global__ void k_candidate(int n_cam, const float* __restrict__ cams, const flo
 // K6: dl per landmark, then the model cost L(dx) per observation (FP64)
 void launch_backsub(Problem& p) {
     count_launches(p, 3);
-    k_backsub_dl<<<ceil_div(p.n_pt, BS_WARPS), 32 * BS_WARPS, 0, p.stream>>>(p.n_pt, p.pt_off, p.obs_cam_s, p.tpool,
-                                                                             p.x, p.dl);
+    k_backsub_dl<<<ceil_div(p.n_pt, BS_WARPS), 32 * BS_WARPS, 0, p.stream>>>(
+        p.n_pt, p.pt_off, p.obs_cam_s, p.tpool, p.x, p.dl, p.implicit ? p.lmrec : nullptr, p.lm_pos);
     k_model_cost<<<p.red_grid, 256, 0, p.stream>>>(p.n_obs, p.frames, p.pts, p.obs_cam_s, p.obs_pt_s, p.obs_xy_s, p.x,
                                                    p.dl, nullptr, nullptr, p.partials, nullptr);
     k_sum_partials<<<1, 1024, 0, p.stream>>>(p.partials, p.red_grid, p.dsum + 1);
@@ -207,8 +226,8 @@ void launch_backsub(Problem& p) {
 // energy (dsum[0]); a batch gets both per problem (cost_a, cost_b)
 void launch_backsub_candidate_cost(Problem& p) {
     count_launches(p, p.batch.n_prob > 0 ? 2 : 3);
-    k_backsub_dl<<<ceil_div(p.n_pt, BS_WARPS), 32 * BS_WARPS, 0, p.stream>>>(p.n_pt, p.pt_off, p.obs_cam_s, p.tpool,
-                                                                             p.x, p.dl);
+    k_backsub_dl<<<ceil_div(p.n_pt, BS_WARPS), 32 * BS_WARPS, 0, p.stream>>>(
+        p.n_pt, p.pt_off, p.obs_cam_s, p.tpool, p.x, p.dl, p.implicit ? p.lmrec : nullptr, p.lm_pos);
     launch_candidate(p);
     if (p.batch.n_prob > 0) {
         BatchState& B = p.batch;

@@ -393,6 +393,7 @@ double time_plan(Problem& p, bool pc, int ksmall, int bytes, int ns, int y_smem,
 // largest k whose row tiles take eight rows a warp (0, 32, 40, 64, all).
 void run_autotune(Problem& p, ba_tune_report* rep) {
     require(p.damped, BA_ERR_STATE, "ba_autotune: blocks are not marginalised (call ba_marginalize_qr)");
+    require(!p.implicit, BA_ERR_INVALID_ARG, "ba_autotune: the tile plans apply to the stored blocks only");
     const auto t0 = std::chrono::steady_clock::now();
     EventSet es(10);
     // a non-zero input (D_p^2), so that the timed launches do the work of a
@@ -713,8 +714,10 @@ void create_problem(Problem& p, const double* cams, int32_t n_cam, const double*
     ba_default_options(&p.opt);
     if (opt) p.opt = *opt;
     require(p.opt.lambda0 > 0 && p.opt.max_lm_iters >= 1 && p.opt.max_cg_iters >= 1 && p.opt.cg_eta > 0 &&
-            (p.opt.pipeline_stages == 0 || (p.opt.pipeline_stages >= 4 && p.opt.pipeline_stages <= 6)),
+            (p.opt.pipeline_stages == 0 || (p.opt.pipeline_stages >= 4 && p.opt.pipeline_stages <= 6)) &&
+            (p.opt.implicit_blocks == 0 || p.opt.implicit_blocks == 1),
             BA_ERR_INVALID_ARG, "invalid options");
+    p.implicit = p.opt.implicit_blocks != 0;
     p.n_cam = n_cam;
     p.n_pt = n_pt;
     p.n_obs = n_obs;
@@ -788,13 +791,21 @@ void create_problem(Problem& p, const double* cams, int32_t n_cam, const double*
     build_index(p, d_oc, d_op, d_xy, d_cams, d_pts);
     require(p.k_max <= linearize_k_limit(), BA_ERR_INVALID_ARG,
             "a landmark has more observations than the supported maximum (900)");
-    plan_matvec(p);
-
-    p.apool = dalloc<float>(p, p.a_floats);
     p.t_floats = 3 * (9 * n_obs + 4 * (int64_t)n_pt);
     p.tpool = dalloc<float>(p, p.t_floats);
-    p.cpool = dalloc<float>(p, 2 * n_obs + 8);
-    p.rot = dalloc<float>(p, 12 * (int64_t)n_pt);
+    if (p.implicit) {
+        plan_implicit(p);
+        p.ipool = dalloc<float>(p, 24 * n_obs);
+        p.rpool = dalloc<float>(p, 2 * n_obs);
+        p.lmrec = dalloc<float>(p, 32 * (int64_t)n_pt);
+        BA_CUDA_TRY(cudaMemsetAsync(p.lmrec, 0, sizeof(float) * 32 * n_pt, p.stream));
+        p.tuned = true;  // the tile plans of the stored blocks do not apply
+    } else {
+        plan_matvec(p);
+        p.apool = dalloc<float>(p, p.a_floats);
+        p.cpool = dalloc<float>(p, 2 * n_obs + 8);
+        p.rot = dalloc<float>(p, 12 * (int64_t)n_pt);
+    }
     p.dp2 = dalloc<float>(p, 9 * (int64_t)n_cam);
     p.dl2 = dalloc<float>(p, 3 * (int64_t)n_pt);
     const int64_t nv = 9 * (int64_t)n_cam;
@@ -811,7 +822,8 @@ void create_problem(Problem& p, const double* cams, int32_t n_cam, const double*
     BA_CUDA_TRY(cudaMemsetAsync(p.x, 0, sizeof(float) * nv, p.stream));
     BA_CUDA_TRY(cudaMemsetAsync(p.dl, 0, sizeof(float) * 3 * n_pt, p.stream));
     configure_linearize(p);
-    configure_matvec(p);
+    if (p.implicit) configure_implicit(p);
+    else configure_matvec(p);
     sync(p);
 }
 
@@ -1194,6 +1206,8 @@ ba_status ba_set_options(ba_problem* h, const ba_options* opt) {
             (opt->pipeline_stages == 0 || (opt->pipeline_stages >= 4 && opt->pipeline_stages <= 6)),
             BA_ERR_INVALID_ARG, "invalid options");
     Problem& p = h->p;
+    require(opt->implicit_blocks == p.opt.implicit_blocks, BA_ERR_INVALID_ARG,
+            "implicit_blocks is fixed when the problem is created");
     sync(p);
     const bool graph_change = opt->use_graph != p.opt.use_graph || opt->pipeline_stages != p.opt.pipeline_stages;
     p.opt = *opt;
@@ -1293,6 +1307,8 @@ ba_status ba_debug_export_landmark(ba_problem* h, int32_t j, int32_t k_cap, floa
     const int k = off[1] - off[0];
     if (k_out) *k_out = k;
     require(k <= k_cap, BA_ERR_INVALID_ARG, "k exceeds k_cap");
+    require(!p.implicit || (!a && !c && !rot), BA_ERR_INVALID_ARG,
+            "implicit storage: only the (undamped) top rows are stored");
     const int64_t ncol = 9 * (int64_t)k;
     if (top) d2h(p, top, p.tpool + top_offset(off[0], j), 3 * (ncol + 4));
     if (a) d2h(p, a, p.apool + aoff, 2 * (int64_t)k * ncol);

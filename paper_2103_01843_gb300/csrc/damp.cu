@@ -171,10 +171,77 @@ k_damp(int n_pt, const int32_t* __restrict__ pt_off, const int64_t* __restrict__
     }
 }
 
+// The implicit storage keeps the top rows undamped: one thread per landmark
+// (storage position) computes the same six rotations from R1 and
+// sqrt(lambda) D_l, applies them also to [I; 0] (the map from the undamped
+// top rows to the six rotated rows, G[:, 0:3] = [G_tt; G_dt]), and stores
+// S = G_dt^T G_dt, G_tt and the damped R.  No undo is needed: every call
+// starts from the undamped R1.
+__global__ void __launch_bounds__(128)
+k_damp_implicit(int n_pt, const int32_t* __restrict__ lm_by_k, const int32_t* __restrict__ pt_off,
+                const float* __restrict__ tpool, const float* __restrict__ dl2, float* __restrict__ lmrec,
+                float sqrt_lambda, const float* __restrict__ lam_prob, const int32_t* __restrict__ lm_prob) {
+    const int pos = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= n_pt) return;
+    const int j = lm_by_k[pos];
+    const int s0 = pt_off[j], k = pt_off[j + 1] - s0, ncol = 9 * k;
+    const float* top = tpool + top_offset(s0, j);
+    float R[3][3], D[3][3], E[6][3];
+    for (int i = 0; i < 3; ++i)
+        for (int c = 0; c < 3; ++c) {
+            R[i][c] = c >= i ? top[i * (ncol + 4) + ncol + c] : 0.f;
+            D[i][c] = 0.f;
+            E[i][c] = i == c ? 1.f : 0.f;
+            E[3 + i][c] = 0.f;
+        }
+    const float sl = lam_prob ? sqrtf(lam_prob[lm_prob[j]]) : sqrt_lambda;
+    for (int d = 0; d < 3; ++d) D[d][d] = sl * sqrtf(dl2[3 * j + d]);
+    for (int m = 0; m < 6; ++m) {
+        int c, d;
+        givens_pair(m, c, d);
+        const float a = R[c][c], b = D[d][c];
+        const float r2 = a * a + b * b;
+        float cs = 1.f, sn = 0.f;
+        if (r2 > 0.f) {
+            const float inv = rsqrtf(r2);
+            cs = a * inv;
+            sn = b * inv;
+        }
+        for (int col = c; col < 3; ++col) {
+            const float u = R[c][col], v = D[d][col];
+            R[c][col] = cs * u + sn * v;
+            D[d][col] = -sn * u + cs * v;
+        }
+        D[d][c] = 0.f;
+        for (int col = 0; col < 3; ++col) {
+            const float u = E[c][col], v = E[3 + d][col];
+            E[c][col] = cs * u + sn * v;
+            E[3 + d][col] = -sn * u + cs * v;
+        }
+    }
+    float* L = lmrec + 32LL * pos;
+    // S = G_dt^T G_dt (upper: 00 01 02 11 12 22)
+    int q = 6;
+    for (int u = 0; u < 3; ++u)
+        for (int v = u; v < 3; ++v) L[q++] = E[3][u] * E[3][v] + E[4][u] * E[4][v] + E[5][u] * E[5][v];
+    for (int i = 0; i < 3; ++i)
+        for (int c = 0; c < 3; ++c) L[16 + 3 * i + c] = E[i][c];
+    q = 25;
+    for (int i = 0; i < 3; ++i)
+        for (int c = i; c < 3; ++c) L[q++] = R[i][c];
+}
+
 }  // namespace
 
 void launch_damp(Problem& p, bool undo_old, float lambda) {
     count_launches(p, 1);
+    if (p.implicit) {
+        k_damp_implicit<<<ceil_div(p.n_pt, 128), 128, 0, p.stream>>>(p.n_pt, p.lm_by_k, p.pt_off, p.tpool, p.dl2,
+                                                                     p.lmrec, sqrtf(lambda), p.batch.lam,
+                                                                     p.batch.lm_prob);
+        BA_LAUNCH_CHECK();
+        return;
+    }
     k_damp<<<ceil_div(p.n_pt, DB), DT, 0, p.stream>>>(p.n_pt, p.pt_off, p.a_off, p.c_off, p.tpool, p.apool, p.cpool,
                                                       p.dl2, p.rot, sqrtf(lambda), p.batch.lam, p.batch.lm_prob,
                                                       undo_old ? 1 : 0);

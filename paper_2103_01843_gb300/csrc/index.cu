@@ -258,10 +258,11 @@ __global__ void k_storage(int n_pt, const int32_t* __restrict__ order, const int
                           const int64_t* __restrict__ run_co, const int32_t* __restrict__ pt_off,
                           const int32_t* __restrict__ obs_cam_s, int64_t* __restrict__ a_off,
                           int32_t* __restrict__ mv_cam, int32_t* __restrict__ c_off,
-                          int32_t* __restrict__ obs_store) {
+                          int32_t* __restrict__ obs_store, int32_t* __restrict__ lm_pos) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_pt) return;
     const int j = order[i];
+    lm_pos[j] = i;
     const int64_t k = kcount[j];
     const int b = kmax - (int)k;
     const int64_t idx = i - ko[b];
@@ -410,8 +411,10 @@ void build_index(Problem& p, const int32_t* d_oc, const int32_t* d_op, const dou
                                 cudaMemcpyHostToDevice, st));
     BA_CUDA_TRY(cudaMemcpyAsync(p.a_off + p.n_pt, &p.run_off[kmax + 1], sizeof(int64_t), cudaMemcpyHostToDevice, st));
     int32_t* obs_store = (int32_t*)tmp_alloc(sizeof(int32_t) * n);
+    p.lm_pos = dalloc<int32_t>(p, p.n_pt);
     k_storage<<<ceil_div(p.n_pt, 256), 256, 0, st>>>(p.n_pt, p.lm_by_k, kcount, kmax, ko, d_run, d_run + kmax + 2,
-                                                     p.pt_off, p.obs_cam_s, p.a_off, p.mv_cam, p.c_off, obs_store);
+                                                     p.pt_off, p.obs_cam_s, p.a_off, p.mv_cam, p.c_off, obs_store,
+                                                     p.lm_pos);
     k_map_list<<<gsz, TPB, 0, st>>>(n, p.cam_list, obs_store, p.cam_list_st);
     BA_LAUNCH_CHECK();
 

@@ -102,6 +102,12 @@ struct LinArgs {
     float* cpool;
     const int32_t* c_off;
     float* dl2;
+    // implicit storage (null in the explicit form): per observation record
+    // chunks (6 float4 at m n_obs + so), residuals, per storage position Tm
+    float* ipool;
+    float* rpool;
+    float* lmrec;
+    int64_t n_obs;
 };
 
 // Q^T J_p rows of a landmark with K observations, lanes over the columns
@@ -171,8 +177,29 @@ __device__ __forceinline__ void write_rows_dispatch(int k, const float* V, const
 // lanes own the pose columns col = rank + TEAM m, keep their W = Tm^T V^T J_p
 // entries in registers and write Q^T J_p row by row (coalesced), three FMAs
 // per element.  The CTA-wide team (k > 32) goes through shared memory.
+// The top rows of the implicit form: rows 0..2 of Q^T J_p only (lanes over
+// the columns, W entries in registers), three FMAs per element.
+template <int TEAM, int MC>
+__device__ __forceinline__ void write_top_rows(int ncol, const float* __restrict__ V, const float* __restrict__ JP,
+                                               const float (&w0)[MC], const float (&w1)[MC], const float (&w2)[MC],
+                                               float* __restrict__ top, int rank) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float v0 = V[3 * i], v1 = V[3 * i + 1], v2 = V[3 * i + 2];
+        const int base = 9 * (i >> 1);
+#pragma unroll
+        for (int m = 0; m < MC; ++m) {
+            const int col = rank + TEAM * m;
+            if (col >= ncol) break;
+            float out = -(v0 * w0[m] + v1 * w1[m] + v2 * w2[m]);
+            if (col >= base && col < base + 9) out += JP[i * 9 + (col - base)];
+            top[i * (ncol + 4) + col] = out;
+        }
+    }
+}
+
 template <int TEAM, int MC = 1>
-__device__ void marginalize_landmark(const LinArgs& A, int j, float* sm, float* red, bool write = true) {
+__device__ void marginalize_landmark(const LinArgs& A, int j, int pos, float* sm, float* red, bool write = true) {
     using T = Team<TEAM>;
     const int rank = T::rank();
     const int s0 = A.pt_off[j];
@@ -296,7 +323,36 @@ __device__ void marginalize_landmark(const LinArgs& A, int j, float* sm, float* 
 
     const int64_t toff = top_offset(s0, j);
     float* __restrict__ top = A.tpool + toff;
-    float* __restrict__ Aj = A.apool + A.a_off[j];
+    const bool implicit = A.ipool != nullptr;
+    float* __restrict__ Aj = implicit ? nullptr : A.apool + A.a_off[j];
+    if (implicit && write) {
+        // per observation: J_s rows and Householder rows (6 float4 chunks,
+        // coalesced over the team's observations), residuals; per landmark Tm
+        const int64_t so0 = A.c_off[j] >> 1;
+        float4* ip = reinterpret_cast<float4*>(A.ipool);
+        for (int s = rank; s < k; s += TEAM) {
+            float f[24];
+#pragma unroll
+            for (int c = 0; c < 18; ++c) f[c] = JP[18 * s + c];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) f[18 + c] = V[6 * s + c];
+#pragma unroll
+            for (int m = 0; m < 6; ++m)
+                ip[m * A.n_obs + so0 + s] = make_float4(f[4 * m], f[4 * m + 1], f[4 * m + 2], f[4 * m + 3]);
+            A.rpool[2 * (so0 + s)] = RV[2 * s];
+            A.rpool[2 * (so0 + s) + 1] = RV[2 * s + 1];
+        }
+        if (rank == 0) {
+            const float* Tm = misc + 5;
+            float* L = A.lmrec + 32LL * pos;
+            L[0] = Tm[0];
+            L[1] = Tm[1];
+            L[2] = Tm[2];
+            L[3] = Tm[4];
+            L[4] = Tm[5];
+            L[5] = Tm[8];
+        }
+    }
     if constexpr (TEAM <= 32) {
         // 4+5. W for this lane's columns (registers), then Q^T J_p row by row
         const float* Tm = misc + 5;
@@ -315,7 +371,8 @@ __device__ void marginalize_landmark(const LinArgs& A, int j, float* sm, float* 
             w1[m] = T01 * m0 + T11 * m1;
             w2[m] = T02 * m0 + T12 * m1 + T22 * m2;
         }
-        if (write) write_rows_dispatch<TEAM, MC>(k, V, JP, w0, w1, w2, top, Aj, rank);
+        if (write && implicit) write_top_rows<TEAM, MC>(ncol, V, JP, w0, w1, w2, top, rank);
+        else if (write) write_rows_dispatch<TEAM, MC>(k, V, JP, w0, w1, w2, top, Aj, rank);
     } else {
         // 4. W = Tm^T (V^T J_p) for the pose columns (two non-zero rows each)
         {
@@ -333,8 +390,9 @@ __device__ void marginalize_landmark(const LinArgs& A, int j, float* sm, float* 
             }
             T::sync();
         }
-        // 5. write Q^T J_p: rows 0..2 to the top block, rows 3.. to A_j
-        const int64_t total = (int64_t)nr * ncol;
+        // 5. write Q^T J_p: rows 0..2 to the top block, rows 3.. to A_j (the
+        // implicit form keeps the top rows only)
+        const int64_t total = (int64_t)(implicit ? 3 : nr) * ncol;
         int e = rank;
         int i = e / ncol, col = e - i * ncol;
         for (; write && e < total; e += TEAM) {
@@ -362,7 +420,7 @@ __device__ void marginalize_landmark(const LinArgs& A, int j, float* sm, float* 
             row[1] = ii <= 1 ? L[3 * ii + 1] : 0.f;
             row[2] = L[3 * ii + 2];
             row[3] = out;
-        } else {
+        } else if (!implicit) {
             A.cpool[A.c_off[j] + (ii - 3)] = out;
         }
     }
@@ -380,7 +438,8 @@ k_linearize_team(LinArgs A, const int32_t* __restrict__ order, int first, int co
     const int idx = idx0 + tm;
     const bool active = idx < count;
     float* sm = smem + (w * TPW + tm) * lin_smem_floats(KMAX);
-    marginalize_landmark<W, (9 * KMAX + W - 1) / W>(A, order[first + (active ? idx : idx0)], sm, nullptr, active);
+    const int pos = first + (active ? idx : idx0);
+    marginalize_landmark<W, (9 * KMAX + W - 1) / W>(A, order[pos], pos, sm, nullptr, active);
 }
 
 __global__ void __launch_bounds__(BIG_TEAM)
@@ -388,7 +447,7 @@ k_linearize_block(LinArgs A, const int32_t* __restrict__ order, int count) {
     extern __shared__ float smem[];
     __shared__ float red[3 * (BIG_TEAM / 32)];
     if ((int)blockIdx.x >= count) return;
-    marginalize_landmark<BIG_TEAM>(A, order[blockIdx.x], smem, red);
+    marginalize_landmark<BIG_TEAM>(A, order[blockIdx.x], blockIdx.x, smem, red);
 }
 
 // D_p^2 = clamp(diag(J_p^T J_p), 1e-6, 1e32) per camera: one CTA per camera,
@@ -489,8 +548,8 @@ void configure_linearize(Problem& p) {
 // joined back into the problem's stream) beside the team kernels, which run
 // one after the other (run side by side they only contend).
 void launch_linearize(Problem& p) {
-    LinArgs A{p.frames, p.pts, p.obs_cam_s, p.obs_xy_s, p.pt_off, p.a_off,
-              p.apool, p.tpool, p.cpool, p.c_off, p.dl2};
+    LinArgs A{p.frames, p.pts, p.obs_cam_s, p.obs_xy_s, p.pt_off, p.a_off, p.apool, p.tpool, p.cpool, p.c_off,
+              p.dl2, p.implicit ? p.ipool : nullptr, p.rpool, p.lmrec, p.n_obs};
     // segments of lm_by_k: k > 32 | 9..32 | 5..8 | 2..4
     const int n_big = p.n_big, n32 = count_k(p, 8, 32), n16 = count_k(p, 4, 8), n8 = count_k(p, 1, 4);
     BA_CUDA_TRY(cudaEventRecord(p.ev_fork, p.stream));

@@ -763,6 +763,10 @@ void configure_matvec(Problem&) {
 }
 
 void launch_matvec_raw(Problem& p, const float* v, float* y, const PcgScalars* S) {
+    if (p.implicit) {
+        launch_matvec_implicit(p, v, y, S);
+        return;
+    }
     const MvArgs a = make_args(p, p.mv_plan, v, y, S);
     pick_kernel(p, p.mv_plan, false)<<<p.mv_grid, MV_THREADS, smem_bytes(p, p.mv_plan, false), p.stream>>>(a);
     BA_LAUNCH_CHECK();

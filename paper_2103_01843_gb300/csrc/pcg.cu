@@ -176,12 +176,14 @@ k_precond_reduce(int n_cam, const int32_t* __restrict__ cam_off, const int32_t* 
 // (threads over the observations, each summing its own in order, then a
 // fixed-order CTA reduction) writes the chunk's 54 partial sums.
 constexpr int PG_T = 128;
+template <bool IMPLICIT>
 __global__ void __launch_bounds__(PG_T)
 k_precond_gram(const int32_t* __restrict__ chunk_cam, const int32_t* __restrict__ chunk_off,
                const int32_t* __restrict__ cam_off, const int32_t* __restrict__ cam_list,
                const int32_t* __restrict__ obs_pt_s, const float2* __restrict__ obs_xy_s,
                const int32_t* __restrict__ pt_off, const float* __restrict__ frames, const float* __restrict__ pts,
-               const float* __restrict__ tpool, float* __restrict__ part_out) {
+               const float* __restrict__ tpool, float* __restrict__ part_out, const float* __restrict__ lmrec,
+               const int32_t* __restrict__ lm_pos) {
     __shared__ float part[PG_T / 32][REC_SUMS + 1];
     const int ch = blockIdx.x, cam = chunk_cam[ch];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -211,12 +213,33 @@ k_precond_gram(const int32_t* __restrict__ chunk_cam, const int32_t* __restrict_
         }
         const int stride = 9 * k + 4;
         const float* top = tpool + top_offset(s0, j) + 9 * (s - s0);
+        float T3[3][10];  // the camera's 3 x 9 slice of the top rows and the residual column
+#pragma unroll
+        for (int row = 0; row < 3; ++row) {
+#pragma unroll
+            for (int c = 0; c < 9; ++c) T3[row][c] = __ldg(top + row * stride + c);
+            T3[row][9] = __ldg(top + row * stride + 9 * (k - (s - s0)) + 3);
+        }
+        if (IMPLICIT) {
+            // implicit storage: the top rows are undamped; the damped ones are G_tt times them
+            const float* G = lmrec + 32LL * lm_pos[j] + 16;
+            float Gm[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) Gm[q] = __ldg(G + q);
+#pragma unroll
+            for (int c = 0; c < 10; ++c) {
+                const float a0 = T3[0][c], a1 = T3[1][c], a2 = T3[2][c];
+                T3[0][c] = Gm[0] * a0 + Gm[1] * a1 + Gm[2] * a2;
+                T3[1][c] = Gm[3] * a0 + Gm[4] * a1 + Gm[5] * a2;
+                T3[2][c] = Gm[6] * a0 + Gm[7] * a1 + Gm[8] * a2;
+            }
+        }
 #pragma unroll
         for (int row = 0; row < 3; ++row) {
             float T[9];
 #pragma unroll
-            for (int c = 0; c < 9; ++c) T[c] = __ldg(top + row * stride + c);
-            const float t = __ldg(top + row * stride + 9 * (k - (s - s0)) + 3);
+            for (int c = 0; c < 9; ++c) T[c] = T3[row][c];
+            const float t = T3[row][9];
             int q = 0;
 #pragma unroll
             for (int u = 0; u < 9; ++u) {
@@ -291,6 +314,133 @@ __device__ void exact_sums_warp(int cam, const int32_t* __restrict__ cam_off, co
     __syncwarp();
 }
 
+// The 54 sums of one camera in the implicit storage, one warp: for each of
+// its observations s (landmark j, slot q) the columns of A_j for s are formed
+// from the stored factorisation, x_c = Q^T e_c restricted to the landmark's
+// rows with e_c = J_p column c (two non-zeros, rows 2q, 2q+1):
+// x_c[i] = J_p[i][c] - V_i . t_c with t_c = Tm^T (V^T J_p[:, c]), and
+// c_j[i] = r_i - V_i . Tm^T (V^T r); rows >= 3 enter with weight one, the
+// top rows through S (the damping rows keep G_dt times the top entries).
+__device__ void exact_sums_warp_implicit(int cam, const int32_t* __restrict__ cam_off,
+                                         const int32_t* __restrict__ cam_list, const int32_t* __restrict__ obs_pt_s,
+                                         const int32_t* __restrict__ pt_off, const int32_t* __restrict__ c_off,
+                                         const int32_t* __restrict__ lm_pos, const float4* __restrict__ ipool,
+                                         int64_t n_obs, const float* __restrict__ rpool,
+                                         const float* __restrict__ lmrec, float* tot, int lane) {
+    auto rec = [&](int64_t so, float (&f)[24]) {
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+            const float4 c = __ldg(ipool + m * n_obs + so);
+            f[4 * m] = c.x;
+            f[4 * m + 1] = c.y;
+            f[4 * m + 2] = c.z;
+            f[4 * m + 3] = c.w;
+        }
+    };
+    float acc[REC_SUMS];
+#pragma unroll
+    for (int q = 0; q < REC_SUMS; ++q) acc[q] = 0.f;
+    for (int e = cam_off[cam]; e < cam_off[cam + 1]; ++e) {
+        const int s = cam_list[e];
+        const int j = obs_pt_s[s];
+        const int s0 = pt_off[j], k = pt_off[j + 1] - s0, qs = s - s0;
+        const int64_t so0 = c_off[j] >> 1;
+        const float* L = lmrec + 32LL * lm_pos[j];
+        const float T00 = L[0], T01 = L[1], T02 = L[2], T11 = L[3], T12 = L[4], T22 = L[5];
+        const float S[3][3] = {{L[6], L[7], L[8]}, {L[7], L[9], L[10]}, {L[8], L[10], L[11]}};
+        float fq[24];
+        rec(so0 + qs, fq);
+        float tc[9][3];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+            const float a0 = fq[18] * fq[c] + fq[21] * fq[9 + c];
+            const float a1 = fq[19] * fq[c] + fq[22] * fq[9 + c];
+            const float a2 = fq[20] * fq[c] + fq[23] * fq[9 + c];
+            tc[c][0] = T00 * a0;
+            tc[c][1] = T01 * a0 + T11 * a1;
+            tc[c][2] = T02 * a0 + T12 * a1 + T22 * a2;
+        }
+        float p0 = 0.f, p1 = 0.f, p2 = 0.f;
+        for (int t = lane; t < k; t += 32) {
+            float f[24];
+            rec(so0 + t, f);
+            const float r0 = __ldg(rpool + 2 * (so0 + t)), r1 = __ldg(rpool + 2 * (so0 + t) + 1);
+            p0 += f[18] * r0 + f[21] * r1;
+            p1 += f[19] * r0 + f[22] * r1;
+            p2 += f[20] * r0 + f[23] * r1;
+        }
+        p0 = warp_sum(p0);
+        p1 = warp_sum(p1);
+        p2 = warp_sum(p2);
+        const float h0 = T00 * p0, h1 = T01 * p0 + T11 * p1, h2 = T02 * p0 + T12 * p1 + T22 * p2;
+        float xt[2][10];  // this lane's top rows (lane 0: rows 0, 1; lane 1: row 2), columns and c
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+            for (int c = 0; c < 10; ++c) xt[rr][c] = 0.f;
+        for (int t = lane; t < k; t += 32) {
+            float f[24];
+            rec(so0 + t, f);
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr) {
+                const float v0 = f[18 + 3 * rr], v1 = f[19 + 3 * rr], v2 = f[20 + 3 * rr];
+                const float ci = __ldg(rpool + 2 * (so0 + t) + rr) - (v0 * h0 + v1 * h1 + v2 * h2);
+                float x[9];
+#pragma unroll
+                for (int c = 0; c < 9; ++c) {
+                    x[c] = (t == qs ? fq[9 * rr + c] : 0.f) - (v0 * tc[c][0] + v1 * tc[c][1] + v2 * tc[c][2]);
+                }
+                const int i = 2 * t + rr;
+                if (i >= 3) {
+                    int q = 0;
+#pragma unroll
+                    for (int u = 0; u < 9; ++u) {
+                        acc[45 + u] += x[u] * ci;
+#pragma unroll
+                        for (int v = u; v < 9; ++v) acc[q++] += x[u] * x[v];
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) xt[rr][c] = x[c];
+                    xt[rr][9] = ci;
+                }
+            }
+        }
+        // the top rows through S, on lane 0 (row 2 comes from lane 1)
+        float row2[10];
+#pragma unroll
+        for (int c = 0; c < 10; ++c) row2[c] = __shfl_sync(0xffffffffu, xt[0][c], 1);
+        if (lane == 0) {
+            float X[3][10];
+#pragma unroll
+            for (int c = 0; c < 10; ++c) {
+                X[0][c] = xt[0][c];
+                X[1][c] = xt[1][c];
+                X[2][c] = row2[c];
+            }
+            float SX[3][10];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int c = 0; c < 10; ++c) SX[a][c] = S[a][0] * X[0][c] + S[a][1] * X[1][c] + S[a][2] * X[2][c];
+            int q = 0;
+#pragma unroll
+            for (int u = 0; u < 9; ++u) {
+                acc[45 + u] += X[0][u] * SX[0][9] + X[1][u] * SX[1][9] + X[2][u] * SX[2][9];
+#pragma unroll
+                for (int v = u; v < 9; ++v) acc[q++] += X[0][u] * SX[0][v] + X[1][u] * SX[1][v] + X[2][u] * SX[2][v];
+            }
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < REC_SUMS; ++q) {
+        const float v = warp_sum(acc[q]);
+        if (lane == 0) tot[q] = v;
+    }
+    __syncwarp();
+}
+
 // Second pass, one warp per camera: its chunks' sums in chunk order, then
 // the 9 x 9 block as in the record path.
 __global__ void __launch_bounds__(32)
@@ -301,7 +451,9 @@ k_precond_gram_finish(const int32_t* __restrict__ chunk_off, const float* __rest
                       const int32_t* __restrict__ cam_list, const int32_t* __restrict__ obs_pt_s,
                       const int32_t* __restrict__ pt_off, const int64_t* __restrict__ a_off,
                       const int32_t* __restrict__ c_off, const float* __restrict__ apool,
-                      const float* __restrict__ cpool) {
+                      const float* __restrict__ cpool, const int32_t* __restrict__ lm_pos,
+                      const float4* __restrict__ ipool, int64_t n_obs, const float* __restrict__ rpool,
+                      const float* __restrict__ lmrec, int force_exact) {
     __shared__ float tot[56], sM[81], sL[81];
     const int cam = blockIdx.x, lane = threadIdx.x;
     for (int q = lane; q <= REC_SUMS; q += 32) {
@@ -314,8 +466,12 @@ k_precond_gram_finish(const int32_t* __restrict__ chunk_off, const float* __rest
     float trM = 0.f;
 #pragma unroll
     for (int u = 0; u < 9; ++u) trM += tot[9 * u - u * (u - 1) / 2] + lam * dp2[9 * cam + u];
-    if (tot[REC_SUMS] > GRAM_KAPPA_MAX * trM) {
-        exact_sums_warp(cam, cam_off, cam_list, obs_pt_s, pt_off, a_off, c_off, apool, cpool, tot, lane);
+    if (force_exact || tot[REC_SUMS] > GRAM_KAPPA_MAX * trM) {
+        if (lmrec)
+            exact_sums_warp_implicit(cam, cam_off, cam_list, obs_pt_s, pt_off, c_off, lm_pos, ipool, n_obs, rpool,
+                                     lmrec, tot, lane);
+        else
+            exact_sums_warp(cam, cam_off, cam_list, obs_pt_s, pt_off, a_off, c_off, apool, cpool, tot, lane);
         if (lane == 0) atomicAdd(err + 2, 1u);  // cameras summed from the stored blocks (read back by the host)
     }
     finish_block_warp(cam, tot, dp2, lam, mdiag, minv, g, err, sM, sL, lane);
@@ -581,15 +737,20 @@ k_bpcg_update(int n_prob, const int32_t* __restrict__ prob_cam_off, const float*
 }  // namespace
 
 void launch_precond_rhs(Problem& p) {
-    if (!p.opt.precond_from_blocks) {
+    if (!p.opt.precond_from_blocks || p.implicit) {
+        // (implicit storage with precond_from_blocks: every camera's sums from
+        // the factorisation, in the finish kernel)
+        const float* lmrec = p.implicit ? p.lmrec : nullptr;
         count_launches(p, p.pg_chunks > 0 ? 2 : 1);
         if (p.pg_chunks > 0)
-            k_precond_gram<<<p.pg_chunks, PG_T, 0, p.stream>>>(p.pg_chunk_cam, p.pg_chunk_off, p.cam_off, p.cam_list,
-                                                               p.obs_pt_s, p.obs_xy_s, p.pt_off, p.frames, p.pts,
-                                                               p.tpool, p.pg_part);
+            (p.implicit ? k_precond_gram<true> : k_precond_gram<false>)<<<p.pg_chunks, PG_T, 0, p.stream>>>(
+                p.pg_chunk_cam, p.pg_chunk_off, p.cam_off, p.cam_list, p.obs_pt_s, p.obs_xy_s, p.pt_off, p.frames,
+                p.pts, p.tpool, p.pg_part, lmrec, p.lm_pos);
         k_precond_gram_finish<<<p.n_cam, 32, 0, p.stream>>>(
             p.pg_chunk_off, p.pg_part, p.dp2, (float)p.lambda_damped, p.batch.lam, p.batch.cam_prob, p.mdiag, p.minv,
-            p.g, p.err, p.cam_off, p.cam_list, p.obs_pt_s, p.pt_off, p.a_off, p.c_off, p.apool, p.cpool);
+            p.g, p.err, p.cam_off, p.cam_list, p.obs_pt_s, p.pt_off, p.a_off, p.c_off, p.apool, p.cpool, p.lm_pos,
+            reinterpret_cast<const float4*>(p.ipool), p.n_obs, p.rpool, lmrec,
+            p.implicit && p.opt.precond_from_blocks ? 1 : 0);
         BA_LAUNCH_CHECK();
         return;
     }

@@ -154,6 +154,17 @@ struct Problem {
     bool tuned = false;              // the autotuner has chosen the plan
     // blocks
     float *apool = nullptr, *tpool = nullptr, *cpool = nullptr, *rot = nullptr;
+    // implicit storage (ba_options.implicit_blocks): per observation in storage
+    // order 24 floats as 6 float4 chunks (chunk m of observation so at float4
+    // index m n_obs + so): J_s rows (18) and Householder rows (6); residuals
+    // (2 per observation, storage order); per storage position 32 floats:
+    // Tm (6, upper: 00 01 02 11 12 22), S (6, same order), 4 pad, G_tt (9,
+    // row-major), damped R (6, upper), 1 pad; the top block stays undamped
+    bool implicit = false;
+    float *ipool = nullptr, *rpool = nullptr, *lmrec = nullptr;
+    int32_t* lm_pos = nullptr;       // storage position of every landmark
+    void* im_tasks = nullptr;        // matvec tasks (implicit.cu)
+    int im_ntasks = 0;
     float *dp2 = nullptr, *dl2 = nullptr;
     // PCG
     float *g = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
@@ -247,6 +258,10 @@ void launch_pcg_iteration(Problem& p, cudaEvent_t mv_begin = nullptr, cudaEvent_
                           bool in_while = false, cudaGraphConditionalHandle cond = 0);
 void launch_matvec(Problem& p, const float* v, float* y, bool add_damping);
 void launch_matvec_raw(Problem& p, const float* v, float* y, const PcgScalars* S);
+// implicit storage (implicit.cu): task plan, kernel attributes, y += A^T A v
+void plan_implicit(Problem& p);
+void configure_implicit(Problem& p);
+void launch_matvec_implicit(Problem& p, const float* v, float* y, const PcgScalars* S);
 void launch_precond_records(Problem& p);
 int matvec_ctas_per_sm();
 // K6: back substitution + model cost (backsub.cu)
