@@ -273,10 +273,9 @@ SQRTBA_API const char* ba_last_error(const ba_problem* h);
 /* Energy E = sum ||r||^2 (FP64 sum of FP32 residuals) of device-resident
  * FP32 data, without allocating any device memory.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate -
- * code that enqueues work while its stream is being captured into a CUDA
- * graph (cudaMalloc is not permitted there), latency-critical loops in which
- * cudaMalloc / cudaFree would synchronise the device, and programs whose
- * device memory is entirely owned by another allocator.
+ * latency-critical loops in which cudaMalloc / cudaFree would synchronise
+ * the device, and programs whose device memory is entirely owned by another
+ * allocator (a framework's caching allocator, a fixed arena sized at start).
  *   d_cams [9 n_cam], d_pts [3 n_pt], d_obs_cam / d_obs_pt [n_obs],
  *   d_obs_xy [2 n_obs]: device pointers, any observation order, caller-owned.
  *   d_cost: device pointer to one double that receives E.
@@ -287,10 +286,13 @@ SQRTBA_API const char* ba_last_error(const ba_problem* h);
  * limited to 16384 * 1024 = 16,777,216 (larger: BA_ERR_INVALID_ARG with a
  * message in ba_last_error(NULL)).  The first call on a device looks up that
  * array's device address (a one-time set-up per device, with the device
- * current), so make that first call before any stream capture.  All calls
- * share the array: calls that overlap on the GPU (other streams or threads)
- * race and must be serialised by the caller.  An observation index out of
- * range makes the result NaN; no out-of-range access is made. */
+ * current), so make that first call before any stream capture; the address
+ * is kept for the life of the process, so a device reset (cudaDeviceReset)
+ * after the first call is not supported.  cuda_stream must belong to the
+ * current device (else BA_ERR_INVALID_ARG).  All calls share the array:
+ * calls that overlap on the GPU (other streams or threads) race and must be
+ * serialised by the caller.  An observation index out of range makes the
+ * result NaN; no out-of-range access is made. */
 SQRTBA_API ba_status ba_eval_cost_noalloc(const float* d_cams, int32_t n_cam, const float* d_pts,
                                           int32_t n_pt, const int32_t* d_obs_cam,
                                           const int32_t* d_obs_pt, const float* d_obs_xy,

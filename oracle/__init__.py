@@ -63,9 +63,25 @@ def build(force=False):
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"])
+    base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _SRC, "-o", tmp]
+    try:  # OpenMP host threads where the toolchain has them, else one thread
+        subprocess.check_call(base + ["-fopenmp", "-lm"], stderr=subprocess.DEVNULL)
+    except subprocess.CalledProcessError:
+        subprocess.check_call(base + ["-lm"])
     os.replace(tmp, _LIB)
     return _LIB
+
+
+def set_threads(n):
+    """Host threads of the oracle's parallel loops (1 by default); results do
+    not depend on it.  Returns the count in effect."""
+    lib().orc_set_threads(ctypes.c_int32(max(1, int(n))))
+    return max(1, int(n))
+
+
+def max_threads():
+    """Processors OpenMP sees (1 when built without OpenMP)."""
+    return int(lib().orc_max_threads())
 
 
 def lib():
@@ -74,6 +90,7 @@ def lib():
         if _lib is None:
             _lib = ctypes.CDLL(build())
             _lib.orc_cost.restype = ctypes.c_double
+            _lib.orc_max_threads.restype = ctypes.c_int32
     return _lib
 
 

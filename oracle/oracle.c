@@ -37,6 +37,26 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Host threads (OpenMP, when built with it): the independent per-observation
+ * and per-landmark loops run in parallel; every sum keeps the sequential
+ * order (per-item terms are stored, then added in index order, and the
+ * landmark contributions to the reduced system are added in landmark order),
+ * so the results do not depend on the thread count. */
+static int g_threads = 1;
+
+void orc_set_threads(int32_t n) { g_threads = n > 0 ? n : 1; }
+
+int32_t orc_max_threads(void) {
+#ifdef _OPENMP
+    return (int32_t)omp_get_num_procs();
+#else
+    return 1;
+#endif
+}
 
 #define ORC_OK 0
 #define ORC_ERR_ARG 1
@@ -183,12 +203,16 @@ double orc_cost(int32_t n_cam, const double* cams, int32_t n_pt, const double* p
                 const double* obs_xy) {
     (void)n_cam;
     (void)n_pt;
-    double E = 0;
+    double* e = (double*)malloc(sizeof(double) * (n_obs + 1));
+#pragma omp parallel for num_threads(g_threads) schedule(static)
     for (int64_t o = 0; o < n_obs; ++o) {
         double r[2];
         orc_residual(cams + 9 * obs_cam[o], pts + 3 * obs_pt[o], obs_xy + 2 * o, r, NULL, NULL);
-        E += r[0] * r[0] + r[1] * r[1];
+        e[o] = r[0] * r[0] + r[1] * r[1];
     }
+    double E = 0;
+    for (int64_t o = 0; o < n_obs; ++o) E += e[o];
+    free(e);
     return E;
 }
 
@@ -351,10 +375,14 @@ static int lin_setup(orc_lin* L, int32_t n_cam, const double* cams, int32_t n_pt
     L->Jl = (double*)malloc(sizeof(double) * 6 * (n_obs + 1));
     L->Dp2 = (double*)calloc(9 * (size_t)n_cam + 1, sizeof(double));
     L->Dl2 = (double*)calloc(3 * (size_t)n_pt + 1, sizeof(double));
+#pragma omp parallel for num_threads(g_threads) schedule(static)
     for (int64_t s = 0; s < n_obs; ++s) {
         int32_t o = L->perm[s];
         orc_residual(cams + 9 * obs_cam[o], pts + 3 * obs_pt[o], obs_xy + 2 * o,
                      L->r + 2 * s, L->Jp + 18 * s, L->Jl + 6 * s);
+    }
+    for (int64_t s = 0; s < n_obs; ++s) {
+        int32_t o = L->perm[s];
         for (int c = 0; c < 9; ++c)
             L->Dp2[9 * obs_cam[o] + c] += L->Jp[18 * s + c] * L->Jp[18 * s + c] +
                                           L->Jp[18 * s + 9 + c] * L->Jp[18 * s + 9 + c];
@@ -493,30 +521,40 @@ static int lin_build_rcs(orc_lin* L, double lambda) {
         int64_t k = L->pt_off[j + 1] - L->pt_off[j];
         if (k > kmax) kmax = k;
     }
-    double* S = (double*)malloc(sizeof(double) * 81 * kmax * kmax + 8);
-    double* bts = (double*)malloc(sizeof(double) * 9 * kmax + 8);
     int rc = ORC_OK;
-    for (int32_t j = 0; j < L->n_pt; ++j) {
-        int64_t s0 = L->pt_off[j], k = L->pt_off[j + 1] - s0, n = 9 * k;
-        if (landmark_sc(L, j, lambda, S, bts, NULL, NULL)) { rc = ORC_ERR_NUMERIC; break; }
-        for (int64_t s = 0; s < k; ++s) {
-            int32_t a = L->obs_cam[L->perm[s0 + s]];
-            for (int c = 0; c < 9; ++c) L->bt[9 * a + c] += bts[9 * s + c];
-            for (int64_t t = s; t < k; ++t) {
-                int32_t b = L->obs_cam[L->perm[s0 + t]];
-                int64_t bi = find_block(L, a, b);
-                double* B = L->blk + 81 * bi;
-                for (int u = 0; u < 9; ++u)
-                    for (int v = 0; v < 9; ++v) B[u * 9 + v] += S[(9 * s + u) * n + 9 * t + v];
+    /* each landmark's pieces are computed in parallel; they are added to the
+     * blocks in landmark order (ordered region) */
+#pragma omp parallel num_threads(g_threads)
+    {
+        double* S = (double*)malloc(sizeof(double) * 81 * kmax * kmax + 8);
+        double* bts = (double*)malloc(sizeof(double) * 9 * kmax + 8);
+#pragma omp for ordered schedule(dynamic, 1)
+        for (int32_t j = 0; j < L->n_pt; ++j) {
+            int64_t s0 = L->pt_off[j], k = L->pt_off[j + 1] - s0, n = 9 * k;
+            int bad = landmark_sc(L, j, lambda, S, bts, NULL, NULL);
+#pragma omp ordered
+            {
+                if (bad) rc = ORC_ERR_NUMERIC;
+                for (int64_t s = 0; s < k && !bad; ++s) {
+                    int32_t a = L->obs_cam[L->perm[s0 + s]];
+                    for (int c = 0; c < 9; ++c) L->bt[9 * a + c] += bts[9 * s + c];
+                    for (int64_t t = s; t < k; ++t) {
+                        int32_t b = L->obs_cam[L->perm[s0 + t]];
+                        int64_t bi = find_block(L, a, b);
+                        double* B = L->blk + 81 * bi;
+                        for (int u = 0; u < 9; ++u)
+                            for (int v = 0; v < 9; ++v) B[u * 9 + v] += S[(9 * s + u) * n + 9 * t + v];
+                    }
+                }
             }
         }
+        free(S);
+        free(bts);
     }
     for (int32_t i = 0; i < L->n_cam; ++i) {
         double* B = L->blk + 81 * find_block(L, i, i);
         for (int u = 0; u < 9; ++u) B[u * 9 + u] += lambda * L->Dp2[9 * i + u];
     }
-    free(S);
-    free(bts);
     return rc;
 }
 
@@ -672,6 +710,8 @@ static void rcs_dense(const orc_lin* L, double* D) {
 /* Landmark back substitution (Eq. backsub_sc, damped):
  * dl_j = -(H_ll + lambda D_l^2)^-1 (b_l + H_lp dp) */
 static int lin_backsub(const orc_lin* L, const double* dp, double* dl) {
+    int rc = ORC_OK;
+#pragma omp parallel for num_threads(g_threads) schedule(static)
     for (int32_t j = 0; j < L->n_pt; ++j) {
         int64_t s0 = L->pt_off[j], k = L->pt_off[j + 1] - s0;
         double H[9] = {0}, v[3] = {0};
@@ -688,17 +728,22 @@ static int lin_backsub(const orc_lin* L, const double* dp, double* dl) {
             }
         }
         for (int a = 0; a < 3; ++a) H[a * 3 + a] += L->lambda * L->Dl2[3 * j + a];
-        if (chol(3, H)) return ORC_ERR_NUMERIC;
+        if (chol(3, H)) {
+            rc = ORC_ERR_NUMERIC; /* any thread: the same status */
+            continue;
+        }
         chol_solve(3, H, v);
         for (int a = 0; a < 3; ++a) dl[3 * j + a] = -v[a];
     }
-    return ORC_OK;
+    return rc;
 }
 
 /* Model cost L(dx) = ||r + J dx||^2 (undamped). */
 static double lin_model_cost(const orc_lin* L, const double* dp, const double* dl) {
-    double m = 0;
+    double* t = (double*)malloc(sizeof(double) * (L->n_obs + 1));
+#pragma omp parallel for num_threads(g_threads) schedule(static)
     for (int64_t s = 0; s < L->n_obs; ++s) {
+        double m = 0;
         int32_t o = L->perm[s];
         const double* Jp = L->Jp + 18 * s;
         const double* Jl = L->Jl + 6 * s;
@@ -710,7 +755,11 @@ static double lin_model_cost(const orc_lin* L, const double* dp, const double* d
             for (int c = 0; c < 3; ++c) v += Jl[3 * i + c] * e[c];
             m += v * v;
         }
+        t[s] = m;
     }
+    double m = 0;
+    for (int64_t s = 0; s < L->n_obs; ++s) m += t[s];
+    free(t);
     return m;
 }
 

@@ -1,9 +1,8 @@
 // Allocation-free variant of the energy evaluation (K7) for callers that
-// cannot allocate device memory: code that runs while a stream is being
-// captured into a CUDA graph (where cudaMalloc is not allowed), code on a
-// latency-critical path where cudaMalloc/cudaFree would synchronise the
-// device, and hosts whose device memory is entirely owned by another
-// allocator (a framework caching allocator, a fixed arena).
+// cannot allocate device memory: code on a latency-critical path where
+// cudaMalloc/cudaFree would synchronise the device, and hosts whose device
+// memory is entirely owned by another allocator (a framework caching
+// allocator, a fixed arena).
 //
 // The per-block FP64 partial sums live in one file-scope __device__ array of
 // NA_MAX_BLOCKS doubles (128 KiB), which every GPU that loads the library
@@ -91,6 +90,18 @@ extern "C" ba_status ba_eval_cost_noalloc(const float* d_cams, int32_t n_cam, co
     if (e != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) {
         set_create_error(std::string("ba_eval_cost_noalloc: no usable current device: ") + cudaGetErrorString(e));
         return BA_ERR_CUDA;
+    }
+    if (cuda_stream) {
+        // the launches below go to the current device: the stream must be one of its streams
+        int sdev = -1;
+        e = cudaStreamGetDevice((cudaStream_t)cuda_stream, &sdev);
+        if (e != cudaSuccess || sdev != dev) {
+            set_create_error(e != cudaSuccess
+                                 ? std::string("ba_eval_cost_noalloc: invalid stream: ") + cudaGetErrorString(e)
+                                 : std::string("ba_eval_cost_noalloc: the stream belongs to another device than "
+                                               "the current one"));
+            return BA_ERR_INVALID_ARG;
+        }
     }
     double* partials = nullptr;
     {

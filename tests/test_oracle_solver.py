@@ -192,3 +192,17 @@ def test_gauss_newton_model_matches_energy_to_second_order(small):
         c, p = oracle.apply_update(small.cams, t * st["dp"], small.pts, t * st["dl"])
         gaps.append(abs(oracle.cost(small, c, p) - np.sum((r + t * J @ dx) ** 2)))
     assert 3.0 < gaps[0] / gaps[1] < 5.0, gaps
+
+
+def test_results_do_not_depend_on_host_threads(small):
+    """The parallel loops keep every sum in index order: one and several host
+    threads give bit-identical steps, costs and reduced systems."""
+    outs = []
+    for th in (1, 4):
+        oracle.set_threads(th)
+        st = oracle.linear_step(small, 1e-3, dense=False)
+        H, b = oracle.rcs_dense(small, 1e-3)
+        outs.append((st["dp"], st["dl"], st["cost"], st["model_cost"], H, b, oracle.cost(small)))
+    oracle.set_threads(1)
+    for a, b in zip(outs[0], outs[1]):
+        np.testing.assert_array_equal(a, b)
