@@ -98,6 +98,12 @@ typedef struct {
                              discussion); products with A_j are formed on the fly in K4.
                              Same results up to rounding; ba_debug_export_landmark then
                              exports only the undamped top rows */
+    double huber_delta;   /* > 0: robust norm (Sec. 6.2: Huber, 1 px there) by iteratively
+                             reweighted least squares: E = sum rho(||r_ij||^2) with
+                             rho(s) = s (s <= delta^2), 2 delta sqrt(s) - delta^2 (above);
+                             each observation's rows [J | r] are scaled by sqrt(w),
+                             w = min(1, delta / ||r_ij||), and the model cost is
+                             sum rho(s) - w s + w ||r + J dx||^2.  0 (default): squared norm */
 } ba_options;
 
 /* Fills *opt with the defaults above. */

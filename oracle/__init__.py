@@ -98,6 +98,12 @@ def _p(a, t):
     return a.ctypes.data_as(t)
 
 
+def _huber(delta):
+    """Huber parameter of the next call (reading of Sec. 6.2's robust norm as
+    IRLS; 0 = squared norm)."""
+    lib().orc_set_huber(ctypes.c_double(float(delta)))
+
+
 def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
@@ -157,7 +163,8 @@ def apply_update(cams, dcams, pts, dpts):
     return co, po
 
 
-def cost(s, cams=None, pts=None):
+def cost(s, cams=None, pts=None, huber_delta=0.0):
+    _huber(huber_delta)
     c, p, oc, op, xy = _problem(s)
     if cams is not None:
         c = _f64(cams)
@@ -180,7 +187,8 @@ def sort_obs(n_cam, n_pt, obs_cam, obs_pt):
     return rc, perm[:n], pt_off, cam_off, cam_list[:n]
 
 
-def damping_diag(s, cams=None, pts=None):
+def damping_diag(s, cams=None, pts=None, huber_delta=0.0):
+    _huber(huber_delta)
     c, p, oc, op, xy = _problem(s)
     c = c if cams is None else _f64(cams)
     p = p if pts is None else _f64(pts)
@@ -189,8 +197,9 @@ def damping_diag(s, cams=None, pts=None):
     return Dp2.reshape(-1, 9), Dl2.reshape(-1, 3)
 
 
-def rcs_dense(s, lam, cams=None, pts=None):
+def rcs_dense(s, lam, cams=None, pts=None, huber_delta=0.0):
     """Dense damped Schur complement H~ (9 n_cam square) and b~."""
+    _huber(huber_delta)
     c, p, oc, op, xy = _problem(s)
     c = c if cams is None else _f64(cams)
     p = p if pts is None else _f64(pts)
@@ -201,8 +210,9 @@ def rcs_dense(s, lam, cams=None, pts=None):
     return H, bt
 
 
-def rcs_diag(s, lam, cams=None, pts=None):
+def rcs_diag(s, lam, cams=None, pts=None, huber_delta=0.0):
     """Per-camera 9x9 diagonal blocks of H~ and b~ (block-sparse assembly)."""
+    _huber(huber_delta)
     c, p, oc, op, xy = _problem(s)
     c = c if cams is None else _f64(cams)
     p = p if pts is None else _f64(pts)
@@ -212,8 +222,9 @@ def rcs_diag(s, lam, cams=None, pts=None):
     return M, bt.reshape(-1, 9)
 
 
-def landmark_sc(s, lam, j, k_cap=256, cams=None, pts=None):
+def landmark_sc(s, lam, j, k_cap=256, cams=None, pts=None, huber_delta=0.0):
     """Landmark j's damped SC pieces: S (9k, 9k), b~_j (9k), H_ll + lam D_l^2, ||c_j||^2."""
+    _huber(huber_delta)
     c, p, oc, op, xy = _problem(s)
     c = c if cams is None else _f64(cams)
     p = p if pts is None else _f64(pts)
@@ -226,8 +237,9 @@ def landmark_sc(s, lam, j, k_cap=256, cams=None, pts=None):
     return S[: n * n].reshape(n, n), bts[:n], Hll.reshape(3, 3), float(cc[0])
 
 
-def rcs_matvec(s, lam, V, cams=None, pts=None):
+def rcs_matvec(s, lam, V, cams=None, pts=None, huber_delta=0.0):
     """Rows of H~ V^T: y_m = H~ v_m for each row v_m of V (m, 9 n_cam)."""
+    _huber(huber_delta)
     c, p, oc, op, xy = _problem(s)
     c = c if cams is None else _f64(cams)
     p = p if pts is None else _f64(pts)
@@ -238,8 +250,9 @@ def rcs_matvec(s, lam, V, cams=None, pts=None):
     return Y
 
 
-def backsub_given(s, lam, dp, cams=None, pts=None):
+def backsub_given(s, lam, dp, cams=None, pts=None, huber_delta=0.0):
     """Landmark step for a given pose step dp (Eq. backsub_sc) and L(dx)."""
+    _huber(huber_delta)
     c, p, oc, op, xy = _problem(s)
     c = c if cams is None else _f64(cams)
     p = p if pts is None else _f64(pts)
@@ -256,8 +269,9 @@ def options(lambda0=1e-4, max_iters=50, func_tol=1e-6, max_cg=500, cg_eta=0.1, d
     return Options(lambda0, max_iters, func_tol, max_cg, cg_eta, 1 if dense else 0, target_cost)
 
 
-def linear_step(s, lam, dense=True, max_cg=500, cg_eta=0.1, cams=None, pts=None):
+def linear_step(s, lam, dense=True, max_cg=500, cg_eta=0.1, cams=None, pts=None, huber_delta=0.0):
     """One damped step: dict(dp (n_cam,9), dl (n_pt,3), model_cost, cost, cg_iters)."""
+    _huber(huber_delta)
     c, p, oc, op, xy = _problem(s)
     c = c if cams is None else _f64(cams)
     p = p if pts is None else _f64(pts)
@@ -296,8 +310,9 @@ def lm_decide(E, E_new, model, lam, nu, func_tol=1e-6, target_cost=0.0):
                 nu=nu_c.value)
 
 
-def lm(s, cams=None, pts=None, **kw):
+def lm(s, cams=None, pts=None, huber_delta=0.0, **kw):
     """Run the LM loop; returns (cams, pts, log list of dicts)."""
+    _huber(huber_delta)
     c, p, oc, op, xy = _problem(s)
     c = (c if cams is None else _f64(cams)).copy()
     p = (p if pts is None else _f64(pts)).copy()

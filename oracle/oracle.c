@@ -29,6 +29,12 @@
  *   lambda update: Nielsen's rule; accept iff rho > 1e-3, the model decrease
  *     E - L is positive and the new cost is finite.
  *     rho = (E - E_new) / (E - L), L = ||r + J dx||^2 (undamped model).
+ *   robust norm (Huber, Sec. 6.2, as IRLS; off unless orc_set_huber(delta > 0)):
+ *     rho(s) = s for s <= delta^2, 2 delta sqrt(s) - delta^2 above, s = ||r_ij||^2;
+ *     E = sum rho(s); the linearised rows [J | r] of an observation are scaled
+ *     by sqrt(w), w = rho'(s) = min(1, delta / ||r||); the model of the robust
+ *     cost is L = sum rho(s) - w ||r||^2 + w ||r + J dx||^2, so that
+ *     E - L = sum w (||r||^2 - ||r + J dx||^2).
  *   CG stop: Nash-Sofer truncated-Newton test i (Q_i - Q_{i-1}) / Q_i < eta with
  *     Q(x) = 1/2 x^T H x - g^T x evaluated as -1/2 x^T (g + r); or ||r|| <= 1e-10 ||g||;
  *     or the iteration limit.
@@ -47,6 +53,21 @@
  * landmark contributions to the reduced system are added in landmark order),
  * so the results do not depend on the thread count. */
 static int g_threads = 1;
+
+/* Huber parameter of the robust norm (pixels); <= 0: squared norm. */
+static double g_huber = 0.0;
+
+void orc_set_huber(double delta) { g_huber = delta; }
+
+/* rho(s) of the Huber norm for s = ||r||^2, and the IRLS weight w = rho'(s). */
+static double huber_rho(double s) {
+    if (!(g_huber > 0) || s <= g_huber * g_huber) return s;
+    return 2.0 * g_huber * sqrt(s) - g_huber * g_huber;
+}
+static double huber_w(double s) {
+    if (!(g_huber > 0) || s <= g_huber * g_huber) return 1.0;
+    return g_huber / sqrt(s);
+}
 
 void orc_set_threads(int32_t n) { g_threads = n > 0 ? n : 1; }
 
@@ -208,7 +229,7 @@ double orc_cost(int32_t n_cam, const double* cams, int32_t n_pt, const double* p
     for (int64_t o = 0; o < n_obs; ++o) {
         double r[2];
         orc_residual(cams + 9 * obs_cam[o], pts + 3 * obs_pt[o], obs_xy + 2 * o, r, NULL, NULL);
-        e[o] = r[0] * r[0] + r[1] * r[1];
+        e[o] = huber_rho(r[0] * r[0] + r[1] * r[1]);
     }
     double E = 0;
     for (int64_t o = 0; o < n_obs; ++o) E += e[o];
@@ -324,9 +345,10 @@ typedef struct {
     int32_t* perm;       /* sorted order */
     int64_t* pt_off;
     /* per sorted observation */
-    double* r;   /* 2 */
+    double* r;   /* 2 (rows scaled by sqrt(w) under the robust norm) */
     double* Jp;  /* 18 */
     double* Jl;  /* 6 */
+    double* rho; /* rho(||r||^2) of the unscaled residual */
     double* Dp2; /* 9 n_cam */
     double* Dl2; /* 3 n_pt */
     /* block-sparse upper triangle of the RCS, 9x9 blocks */
@@ -354,7 +376,7 @@ static int cmp_i64(const void* a, const void* b) {
 }
 
 static void lin_free(orc_lin* L) {
-    free(L->perm); free(L->pt_off); free(L->r); free(L->Jp); free(L->Jl);
+    free(L->perm); free(L->pt_off); free(L->r); free(L->Jp); free(L->Jl); free(L->rho);
     free(L->Dp2); free(L->Dl2); free(L->row_ptr); free(L->col); free(L->blk); free(L->bt);
     memset(L, 0, sizeof(*L));
 }
@@ -373,6 +395,7 @@ static int lin_setup(orc_lin* L, int32_t n_cam, const double* cams, int32_t n_pt
     L->r = (double*)malloc(sizeof(double) * 2 * (n_obs + 1));
     L->Jp = (double*)malloc(sizeof(double) * 18 * (n_obs + 1));
     L->Jl = (double*)malloc(sizeof(double) * 6 * (n_obs + 1));
+    L->rho = (double*)malloc(sizeof(double) * (n_obs + 1));
     L->Dp2 = (double*)calloc(9 * (size_t)n_cam + 1, sizeof(double));
     L->Dl2 = (double*)calloc(3 * (size_t)n_pt + 1, sizeof(double));
 #pragma omp parallel for num_threads(g_threads) schedule(static)
@@ -380,6 +403,15 @@ static int lin_setup(orc_lin* L, int32_t n_cam, const double* cams, int32_t n_pt
         int32_t o = L->perm[s];
         orc_residual(cams + 9 * obs_cam[o], pts + 3 * obs_pt[o], obs_xy + 2 * o,
                      L->r + 2 * s, L->Jp + 18 * s, L->Jl + 6 * s);
+        /* IRLS: the observation's rows scaled by sqrt(w) */
+        const double sq = L->r[2 * s] * L->r[2 * s] + L->r[2 * s + 1] * L->r[2 * s + 1];
+        L->rho[s] = huber_rho(sq);
+        const double sw = sqrt(huber_w(sq));
+        if (sw != 1.0) {
+            for (int i = 0; i < 2; ++i) L->r[2 * s + i] *= sw;
+            for (int i = 0; i < 18; ++i) L->Jp[18 * s + i] *= sw;
+            for (int i = 0; i < 6; ++i) L->Jl[6 * s + i] *= sw;
+        }
     }
     for (int64_t s = 0; s < n_obs; ++s) {
         int32_t o = L->perm[s];
@@ -755,7 +787,8 @@ static double lin_model_cost(const orc_lin* L, const double* dp, const double* d
             for (int c = 0; c < 3; ++c) v += Jl[3 * i + c] * e[c];
             m += v * v;
         }
-        t[s] = m;
+        /* rho(s) - w ||r||^2 + w ||r + J dx||^2 (the rows are the scaled ones) */
+        t[s] = L->rho[s] - (L->r[2 * s] * L->r[2 * s] + L->r[2 * s + 1] * L->r[2 * s + 1]) + m;
     }
     double m = 0;
     for (int64_t s = 0; s < L->n_obs; ++s) m += t[s];
@@ -900,7 +933,7 @@ int orc_linear_step(int32_t n_cam, const double* cams, int32_t n_pt, const doubl
     if (!rc) {
         *model_cost = lin_model_cost(&L, dp, dl);
         double E = 0;
-        for (int64_t s = 0; s < n_obs; ++s) E += L.r[2 * s] * L.r[2 * s] + L.r[2 * s + 1] * L.r[2 * s + 1];
+        for (int64_t s = 0; s < n_obs; ++s) E += L.rho[s];
         *cost = E;
     }
     lin_free(&L);

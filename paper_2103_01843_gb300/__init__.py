@@ -41,7 +41,8 @@ class Options(ctypes.Structure):
                 ("cg_eta", ctypes.c_double), ("use_graph", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("use_learned", ctypes.c_int32),
                 ("pipeline_stages", ctypes.c_int32), ("target_cost", ctypes.c_double),
-                ("precond_from_blocks", ctypes.c_int32), ("implicit_blocks", ctypes.c_int32)]
+                ("precond_from_blocks", ctypes.c_int32), ("implicit_blocks", ctypes.c_int32),
+                ("huber_delta", ctypes.c_double)]
 
 
 class PcgReport(ctypes.Structure):

@@ -83,25 +83,35 @@ __device__ __forceinline__ void model_cost_obs(int64_t s, const float* __restric
                                                const int32_t* __restrict__ obs_pt_s,
                                                const float2* __restrict__ obs_xy_s, const float* __restrict__ dp,
                                                const float* __restrict__ dl, const float* __restrict__ cand_frames,
-                                               const float* __restrict__ cand_pts, double& m, double& c) {
+                                               const float* __restrict__ cand_pts, float huber, double& m,
+                                               double& c) {
     const int j = obs_pt_s[s], cam = obs_cam_s[s];
     const float2 z = obs_xy_s[s];
     float r[2], Jp[18], Jl[6];
     frame_jacobians(frames + FRAME * cam, pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], z.x, z.y, r, Jp, Jl);
     const float* d = dp + 9 * cam;
     const float l0 = dl[3 * j], l1 = dl[3 * j + 1], l2 = dl[3 * j + 2];
+    // robust norm: rho(s) - w s + w ||r + J dx||^2 (w = 1, rho(s) = s without it)
+    const float w = huber_weight(huber, r[0], r[1]);
+    double mo = 0.0;
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
         float e = r[i] + Jl[3 * i] * l0 + Jl[3 * i + 1] * l1 + Jl[3 * i + 2] * l2;
 #pragma unroll
         for (int q = 0; q < 9; ++q) e += Jp[9 * i + q] * d[q];
-        m += (double)e * (double)e;
+        mo += (double)e * (double)e;
+    }
+    if (w == 1.f) {
+        m += mo;
+    } else {
+        const double s = (double)r[0] * r[0] + (double)r[1] * r[1];
+        m += huber_rho(huber, s) - (double)w * s + (double)w * mo;
     }
     if (cand_frames) {
         float r0, r1;
         frame_residual(cand_frames + FRAME * cam, cand_pts[3 * j], cand_pts[3 * j + 1], cand_pts[3 * j + 2], z.x, z.y,
                        r0, r1);
-        c += (double)r0 * (double)r0 + (double)r1 * (double)r1;
+        c += huber_rho(huber, (double)r0 * (double)r0 + (double)r1 * (double)r1);
     }
 }
 
@@ -112,11 +122,11 @@ k_model_cost(int64_t n_obs, const float* __restrict__ frames, const float* __res
              const int32_t* __restrict__ obs_cam_s, const int32_t* __restrict__ obs_pt_s,
              const float2* __restrict__ obs_xy_s, const float* __restrict__ dp, const float* __restrict__ dl,
              const float* __restrict__ cand_frames, const float* __restrict__ cand_pts, double* __restrict__ part_m,
-             double* __restrict__ part_c) {
+             double* __restrict__ part_c, float huber) {
     __shared__ double red[32];
     double m = 0.0, c = 0.0;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_obs; s += (int64_t)gridDim.x * blockDim.x)
-        model_cost_obs(s, frames, pts, obs_cam_s, obs_pt_s, obs_xy_s, dp, dl, cand_frames, cand_pts, m, c);
+        model_cost_obs(s, frames, pts, obs_cam_s, obs_pt_s, obs_xy_s, dp, dl, cand_frames, cand_pts, huber, m, c);
     m = block_sum_d(m, red);
     if (cand_frames) c = block_sum_d(c, red);
     if (threadIdx.x == 0) {
@@ -131,12 +141,13 @@ k_model_cost_seg(const int64_t* __restrict__ prob_obs_off, const float* __restri
                  const float* __restrict__ pts, const int32_t* __restrict__ obs_cam_s,
                  const int32_t* __restrict__ obs_pt_s, const float2* __restrict__ obs_xy_s,
                  const float* __restrict__ dp, const float* __restrict__ dl, const float* __restrict__ cand_frames,
-                 const float* __restrict__ cand_pts, double* __restrict__ model, double* __restrict__ cost) {
+                 const float* __restrict__ cand_pts, double* __restrict__ model, double* __restrict__ cost,
+                 float huber) {
     __shared__ double red[32];
     const int b = blockIdx.x;
     double m = 0.0, c = 0.0;
     for (int64_t s = prob_obs_off[b] + threadIdx.x; s < prob_obs_off[b + 1]; s += blockDim.x)
-        model_cost_obs(s, frames, pts, obs_cam_s, obs_pt_s, obs_xy_s, dp, dl, cand_frames, cand_pts, m, c);
+        model_cost_obs(s, frames, pts, obs_cam_s, obs_pt_s, obs_xy_s, dp, dl, cand_frames, cand_pts, huber, m, c);
     m = block_sum_d(m, red);
     c = block_sum_d(c, red);
     if (threadIdx.x == 0) {
@@ -148,7 +159,7 @@ k_model_cost_seg(const int64_t* __restrict__ prob_obs_off, const float* __restri
 __global__ void __launch_bounds__(256)
 k_cost(int64_t n_obs, const float* __restrict__ frames, const float* __restrict__ pts,
        const int32_t* __restrict__ obs_cam_s, const int32_t* __restrict__ obs_pt_s,
-       const float2* __restrict__ obs_xy_s, double* __restrict__ partials) {
+       const float2* __restrict__ obs_xy_s, double* __restrict__ partials, float huber) {
     __shared__ double red[32];
     double acc = 0.0;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_obs;
@@ -157,7 +168,7 @@ k_cost(int64_t n_obs, const float* __restrict__ frames, const float* __restrict_
         const float2 z = obs_xy_s[s];
         float r0, r1;
         frame_residual(frames + FRAME * obs_cam_s[s], pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], z.x, z.y, r0, r1);
-        acc += (double)r0 * (double)r0 + (double)r1 * (double)r1;
+        acc += huber_rho(huber, (double)r0 * (double)r0 + (double)r1 * (double)r1);
     }
     acc = block_sum_d(acc, red);
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
@@ -216,7 +227,7 @@ void launch_backsub(Problem& p) {
     k_backsub_dl<<<ceil_div(p.n_pt, BS_WARPS), 32 * BS_WARPS, 0, p.stream>>>(
         p.n_pt, p.pt_off, p.obs_cam_s, p.tpool, p.x, p.dl, p.implicit ? p.lmrec : nullptr, p.lm_pos);
     k_model_cost<<<p.red_grid, 256, 0, p.stream>>>(p.n_obs, p.frames, p.pts, p.obs_cam_s, p.obs_pt_s, p.obs_xy_s, p.x,
-                                                   p.dl, nullptr, nullptr, p.partials, nullptr);
+                                                   p.dl, nullptr, nullptr, p.partials, nullptr, (float)p.opt.huber_delta);
     k_sum_partials<<<1, 1024, 0, p.stream>>>(p.partials, p.red_grid, p.dsum + 1);
     BA_LAUNCH_CHECK();
 }
@@ -233,11 +244,11 @@ void launch_backsub_candidate_cost(Problem& p) {
         BatchState& B = p.batch;
         k_model_cost_seg<<<B.n_prob, 256, 0, p.stream>>>(B.prob_obs_off, p.frames, p.pts, p.obs_cam_s, p.obs_pt_s,
                                                          p.obs_xy_s, p.x, p.dl, p.cand_frames, p.cand_pts, B.cost_b,
-                                                         B.cost_a);
+                                                         B.cost_a, (float)p.opt.huber_delta);
     } else {
         k_model_cost<<<p.red_grid, 256, 0, p.stream>>>(p.n_obs, p.frames, p.pts, p.obs_cam_s, p.obs_pt_s, p.obs_xy_s,
                                                        p.x, p.dl, p.cand_frames, p.cand_pts, p.partials,
-                                                       p.partials + p.red_grid);
+                                                       p.partials + p.red_grid, (float)p.opt.huber_delta);
         k_sum_partials2<<<1, 1024, 0, p.stream>>>(p.partials, p.partials + p.red_grid, p.red_grid, p.dsum + 1,
                                                   p.dsum + 0);
     }
@@ -259,7 +270,7 @@ void launch_cost(Problem& p, bool candidate, int slot) {
     count_launches(p, 2);
     k_cost<<<p.red_grid, 256, 0, p.stream>>>(p.n_obs, candidate ? p.cand_frames : p.frames,
                                              candidate ? p.cand_pts : p.pts, p.obs_cam_s, p.obs_pt_s,
-                                             p.obs_xy_s, p.partials);
+                                             p.obs_xy_s, p.partials, (float)p.opt.huber_delta);
     k_sum_partials<<<1, 1024, 0, p.stream>>>(p.partials, p.red_grid, p.dsum + slot);
     BA_LAUNCH_CHECK();
 }

@@ -25,7 +25,7 @@ constexpr int SEG_T = 256;
 __global__ void __launch_bounds__(SEG_T)
 k_cost_seg(const int64_t* __restrict__ prob_obs_off, const float* __restrict__ frames, const float* __restrict__ pts,
            const int32_t* __restrict__ obs_cam_s, const int32_t* __restrict__ obs_pt_s,
-           const float2* __restrict__ obs_xy_s, double* __restrict__ out) {
+           const float2* __restrict__ obs_xy_s, double* __restrict__ out, float huber) {
     __shared__ double red[32];
     const int b = blockIdx.x;
     double acc = 0.0;
@@ -34,7 +34,7 @@ k_cost_seg(const int64_t* __restrict__ prob_obs_off, const float* __restrict__ f
         const float2 z = obs_xy_s[s];
         float r0, r1;
         frame_residual(frames + FRAME * obs_cam_s[s], pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], z.x, z.y, r0, r1);
-        acc += (double)r0 * (double)r0 + (double)r1 * (double)r1;
+        acc += huber_rho(huber, (double)r0 * (double)r0 + (double)r1 * (double)r1);
     }
     acc = block_sum_d(acc, red);
     if (threadIdx.x == 0) out[b] = acc;
@@ -128,7 +128,7 @@ void launch_batch_cost(Problem& p, bool candidate, double* out) {
     if (!candidate) launch_frames(p);
     k_cost_seg<<<B.n_prob, SEG_T, 0, p.stream>>>(B.prob_obs_off, candidate ? p.cand_frames : p.frames,
                                                  candidate ? p.cand_pts : p.pts, p.obs_cam_s, p.obs_pt_s,
-                                                 p.obs_xy_s, out);
+                                                 p.obs_xy_s, out, (float)p.opt.huber_delta);
     BA_LAUNCH_CHECK();
 }
 

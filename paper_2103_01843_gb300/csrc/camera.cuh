@@ -110,6 +110,30 @@ __device__ __forceinline__ void project_jacobians(const float* __restrict__ cam,
     }
 }
 
+// Robust norm (the Huber norm of Sec. 6.2, read as iteratively reweighted
+// least squares): for s = ||r||^2, rho(s) = s if s <= delta^2, else
+// 2 delta sqrt(s) - delta^2; the linearised rows [J | r] of an observation are
+// scaled by sqrt(w), w = rho'(s) = min(1, delta / ||r||).  delta <= 0: the
+// squared norm (rho(s) = s, w = 1).
+__device__ __forceinline__ float huber_weight(float delta, float r0, float r1) {
+    const float s = r0 * r0 + r1 * r1;
+    return (delta > 0.f && s > delta * delta) ? delta * rsqrtf(s) : 1.f;
+}
+__device__ __forceinline__ double huber_rho(double delta, double s) {
+    return (delta > 0.0 && s > delta * delta) ? 2.0 * delta * sqrt(s) - delta * delta : s;
+}
+__device__ __forceinline__ void huber_scale_rows(float delta, float r[2], float Jp[18], float Jl[6]) {
+    const float w = huber_weight(delta, r[0], r[1]);
+    if (w == 1.f) return;
+    const float sw = sqrtf(w);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) r[i] *= sw;
+#pragma unroll
+    for (int i = 0; i < 18; ++i) Jp[i] *= sw;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) Jl[i] *= sw;
+}
+
 // Camera frames: the rotation matrix evaluated once per camera and state,
 // 16 floats per camera (R row-major, t, f, k1, k2, 0), 16-byte aligned, so
 // that the per-observation kernels skip the trigonometry of R(w).

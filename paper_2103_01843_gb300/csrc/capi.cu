@@ -715,7 +715,8 @@ void create_problem(Problem& p, const double* cams, int32_t n_cam, const double*
     if (opt) p.opt = *opt;
     require(p.opt.lambda0 > 0 && p.opt.max_lm_iters >= 1 && p.opt.max_cg_iters >= 1 && p.opt.cg_eta > 0 &&
             (p.opt.pipeline_stages == 0 || (p.opt.pipeline_stages >= 4 && p.opt.pipeline_stages <= 6)) &&
-            (p.opt.implicit_blocks == 0 || p.opt.implicit_blocks == 1),
+            (p.opt.implicit_blocks == 0 || p.opt.implicit_blocks == 1) &&
+            std::isfinite(p.opt.huber_delta) && p.opt.huber_delta >= 0.0,
             BA_ERR_INVALID_ARG, "invalid options");
     p.implicit = p.opt.implicit_blocks != 0;
     p.n_cam = n_cam;
@@ -1203,13 +1204,19 @@ ba_status ba_set_options(ba_problem* h, const ba_options* opt) {
     if (!h || !opt) return BA_ERR_INVALID_ARG;
     API_TRY
     require(opt->lambda0 > 0 && opt->max_lm_iters >= 1 && opt->max_cg_iters >= 1 && opt->cg_eta > 0 &&
-            (opt->pipeline_stages == 0 || (opt->pipeline_stages >= 4 && opt->pipeline_stages <= 6)),
+            (opt->pipeline_stages == 0 || (opt->pipeline_stages >= 4 && opt->pipeline_stages <= 6)) &&
+            std::isfinite(opt->huber_delta) && opt->huber_delta >= 0.0,
             BA_ERR_INVALID_ARG, "invalid options");
     Problem& p = h->p;
     require(opt->implicit_blocks == p.opt.implicit_blocks, BA_ERR_INVALID_ARG,
             "implicit_blocks is fixed when the problem is created");
     sync(p);
     const bool graph_change = opt->use_graph != p.opt.use_graph || opt->pipeline_stages != p.opt.pipeline_stages;
+    if (opt->huber_delta != p.opt.huber_delta) {
+        // another cost function: the energy and the linearisation are recomputed
+        p.cost_valid = false;
+        p.linearized = p.damped = p.solved = p.backsubbed = false;
+    }
     p.opt = *opt;
     if (graph_change) destroy_graph(p);
     return BA_OK;

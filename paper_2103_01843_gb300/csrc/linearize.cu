@@ -108,6 +108,7 @@ struct LinArgs {
     float* rpool;
     float* lmrec;
     int64_t n_obs;
+    float huber;  // Huber parameter (<= 0: squared norm)
 };
 
 // Q^T J_p rows of a landmark with K observations, lanes over the columns
@@ -219,6 +220,7 @@ __device__ void marginalize_landmark(const LinArgs& A, int j, int pos, float* sm
         const float2 z = A.obs_xy_s[s0 + s];
         float r[2], Jp[18], Jl[6];
         frame_jacobians(A.frames + FRAME * A.obs_cam_s[s0 + s], X0, X1, X2, z.x, z.y, r, Jp, Jl);
+        huber_scale_rows(A.huber, r, Jp, Jl);  // IRLS rows of the robust norm
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             RV[2 * s + i] = r[i];
@@ -458,7 +460,7 @@ __global__ void __launch_bounds__(CD_THREADS)
 k_camera_diag(int n_cam, const float* __restrict__ frames, const float* __restrict__ pts,
               const int32_t* __restrict__ obs_pt_s, const float2* __restrict__ obs_xy_s,
               const int32_t* __restrict__ cam_off, const int32_t* __restrict__ cam_list,
-              float* __restrict__ dp2) {
+              float* __restrict__ dp2, float huber) {
     __shared__ float part[CD_THREADS / 32][9];
     const int cam = blockIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -471,6 +473,7 @@ k_camera_diag(int n_cam, const float* __restrict__ frames, const float* __restri
         const float2 z = obs_xy_s[s];
         float r[2], Jp[18], Jl[6];
         frame_jacobians(frames + FRAME * cam, pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], z.x, z.y, r, Jp, Jl);
+        huber_scale_rows(huber, r, Jp, Jl);
 #pragma unroll
         for (int c = 0; c < 9; ++c) acc[c] += Jp[c] * Jp[c] + Jp[9 + c] * Jp[9 + c];
     }
@@ -490,7 +493,7 @@ k_camera_diag(int n_cam, const float* __restrict__ frames, const float* __restri
 __global__ void k_export_jacobians(int64_t n_obs, const float* __restrict__ frames, const float* __restrict__ pts,
                                    const int32_t* __restrict__ obs_cam_s, const int32_t* __restrict__ obs_pt_s,
                                    const float2* __restrict__ obs_xy_s, float* r_out, float* jp_out,
-                                   float* jl_out) {
+                                   float* jl_out, float huber) {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_obs;
          s += (int64_t)gridDim.x * blockDim.x) {
         const int j = obs_pt_s[s];
@@ -498,6 +501,7 @@ __global__ void k_export_jacobians(int64_t n_obs, const float* __restrict__ fram
         float r[2], Jp[18], Jl[6];
         frame_jacobians(frames + FRAME * obs_cam_s[s], pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], z.x, z.y, r,
                         Jp, Jl);
+        huber_scale_rows(huber, r, Jp, Jl);
         for (int i = 0; i < 2; ++i) r_out[2 * s + i] = r[i];
         for (int i = 0; i < 18; ++i) jp_out[18 * s + i] = Jp[i];
         for (int i = 0; i < 6; ++i) jl_out[6 * s + i] = Jl[i];
@@ -549,14 +553,14 @@ void configure_linearize(Problem& p) {
 // one after the other (run side by side they only contend).
 void launch_linearize(Problem& p) {
     LinArgs A{p.frames, p.pts, p.obs_cam_s, p.obs_xy_s, p.pt_off, p.a_off, p.apool, p.tpool, p.cpool, p.c_off,
-              p.dl2, p.implicit ? p.ipool : nullptr, p.rpool, p.lmrec, p.n_obs};
+              p.dl2, p.implicit ? p.ipool : nullptr, p.rpool, p.lmrec, p.n_obs, (float)p.opt.huber_delta};
     // segments of lm_by_k: k > 32 | 9..32 | 5..8 | 2..4
     const int n_big = p.n_big, n32 = count_k(p, 8, 32), n16 = count_k(p, 4, 8), n8 = count_k(p, 1, 4);
     BA_CUDA_TRY(cudaEventRecord(p.ev_fork, p.stream));
     BA_CUDA_TRY(cudaStreamWaitEvent(p.side, p.ev_fork, 0));
     // side: D_p^2, then the landmarks with k > 32 (one CTA each)
     k_camera_diag<<<p.n_cam, CD_THREADS, 0, p.side>>>(p.n_cam, p.frames, p.pts, p.obs_pt_s, p.obs_xy_s, p.cam_off,
-                                                      p.cam_list, p.dp2);
+                                                      p.cam_list, p.dp2, (float)p.opt.huber_delta);
     count_launches(p, 1);
     if (n_big > 0) {
         const size_t sm = sizeof(float) * lin_smem_floats(p.k_max);
@@ -589,7 +593,7 @@ void launch_linearize(Problem& p) {
 void launch_export_jacobians(Problem& p, float* r, float* jp, float* jl) {
     launch_frames(p);
     k_export_jacobians<<<p.sm_count * 4, 256, 0, p.stream>>>(p.n_obs, p.frames, p.pts, p.obs_cam_s, p.obs_pt_s,
-                                                             p.obs_xy_s, r, jp, jl);
+                                                             p.obs_xy_s, r, jp, jl, (float)p.opt.huber_delta);
     BA_LAUNCH_CHECK();
 }
 

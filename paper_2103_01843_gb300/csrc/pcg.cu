@@ -183,7 +183,7 @@ k_precond_gram(const int32_t* __restrict__ chunk_cam, const int32_t* __restrict_
                const int32_t* __restrict__ obs_pt_s, const float2* __restrict__ obs_xy_s,
                const int32_t* __restrict__ pt_off, const float* __restrict__ frames, const float* __restrict__ pts,
                const float* __restrict__ tpool, float* __restrict__ part_out, const float* __restrict__ lmrec,
-               const int32_t* __restrict__ lm_pos) {
+               const int32_t* __restrict__ lm_pos, float huber) {
     __shared__ float part[PG_T / 32][REC_SUMS + 1];
     const int ch = blockIdx.x, cam = chunk_cam[ch];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -200,6 +200,7 @@ k_precond_gram(const int32_t* __restrict__ chunk_cam, const int32_t* __restrict_
         const float2 z = obs_xy_s[s];
         float r[2], Jp[18], Jl[6];
         frame_jacobians(fr, pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], z.x, z.y, r, Jp, Jl);
+        huber_scale_rows(huber, r, Jp, Jl);  // the rows K1 factored
 #pragma unroll
         for (int u = 0; u < 18; ++u) acc[REC_SUMS] += Jp[u] * Jp[u];
         {
@@ -745,7 +746,7 @@ void launch_precond_rhs(Problem& p) {
         if (p.pg_chunks > 0)
             (p.implicit ? k_precond_gram<true> : k_precond_gram<false>)<<<p.pg_chunks, PG_T, 0, p.stream>>>(
                 p.pg_chunk_cam, p.pg_chunk_off, p.cam_off, p.cam_list, p.obs_pt_s, p.obs_xy_s, p.pt_off, p.frames,
-                p.pts, p.tpool, p.pg_part, lmrec, p.lm_pos);
+                p.pts, p.tpool, p.pg_part, lmrec, p.lm_pos, (float)p.opt.huber_delta);
         k_precond_gram_finish<<<p.n_cam, 32, 0, p.stream>>>(
             p.pg_chunk_off, p.pg_part, p.dp2, (float)p.lambda_damped, p.batch.lam, p.batch.cam_prob, p.mdiag, p.minv,
             p.g, p.err, p.cam_off, p.cam_list, p.obs_pt_s, p.pt_off, p.a_off, p.c_off, p.apool, p.cpool, p.lm_pos,

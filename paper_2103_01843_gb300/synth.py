@@ -257,7 +257,7 @@ def _pareto_floor(alpha, cap):
 # ----------------------------------------------------------------------------
 
 def _finish(rng, name, seed, R, t, f, k1, k2, X, obs_cam, obs_pt,
-            noise_px, perturb):
+            noise_px, perturb, outlier_frac=0.0):
     order = np.lexsort((obs_cam, obs_pt))  # tidy (pt, cam) order; any order is legal input
     obs_cam = obs_cam[order].astype(np.int32)
     obs_pt = obs_pt[order].astype(np.int32)
@@ -265,6 +265,12 @@ def _finish(rng, name, seed, R, t, f, k1, k2, X, obs_cam, obs_pt,
                               k1[obs_cam], k2[obs_cam], X[obs_pt])
     assert (depth > 0).all()
     obs_xy = pix + rng.normal(0.0, noise_px, pix.shape) if noise_px > 0 else pix.copy()
+    if outlier_frac > 0:
+        # gross outliers: a fraction of the measurements replaced by pixels drawn
+        # uniformly over the image (a separate stream, so the inliers are unchanged)
+        orng = np.random.default_rng([seed, 7919])
+        bad = orng.random(obs_xy.shape[0]) < outlier_frac
+        obs_xy[bad] = orng.uniform(-IMAGE_HALF, IMAGE_HALF, (int(bad.sum()), 2))
 
     # perturbed initial state (metres)
     n_cam = R.shape[0]
@@ -393,7 +399,7 @@ def degenerate_scene(seed=0, n_pt=300, noise_px=1.0):
     return sc, dict(axis=base, same_centre=base + 1, near=base + 2, n_cam=n_cam)
 
 
-def make_scene(name="tiny", seed=0, noise_px=1.0, perturb=True, **kw):
+def make_scene(name="tiny", seed=0, noise_px=1.0, perturb=True, outlier_frac=0.0, **kw):
     """Build one seeded synthetic scene.
 
     tiny   : 16 cams on a 10 m circle facing a 5 m cube of 500 points,
@@ -409,6 +415,9 @@ def make_scene(name="tiny", seed=0, noise_px=1.0, perturb=True, **kw):
              (defaults 32 cams, 2000 points, p = 0.3, cap 32); f_range =
              (lo, hi) draws focal lengths log-uniformly, dist_sigma sets the
              spread of k1, k2 (ill-conditioned camera sets).
+    outlier_frac > 0 (any config) replaces that fraction of the pixel
+    measurements by gross outliers uniform over the image (the robust-norm
+    experiments of Sec. 6.2; the BAL data are not available here).
     batched_member : member `seed` of the 256-problem batch: cams U[8, 64],
              points U[200, 5000], k = 2 + Geom0(0.3) capped at n_cam.
     walk   : medium-shaped (the medium generator and k distribution) with
@@ -440,4 +449,4 @@ def make_scene(name="tiny", seed=0, noise_px=1.0, perturb=True, **kw):
                       height_sigma=0.5)
     else:
         raise ValueError(f"unknown scene config {name!r}")
-    return _finish(rng, name, seed, *gt, noise_px=noise_px, perturb=perturb)
+    return _finish(rng, name, seed, *gt, noise_px=noise_px, perturb=perturb, outlier_frac=outlier_frac)
