@@ -59,8 +59,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="medium")
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--storage", default="stored", choices=["stored", "implicit"],
-                    help="landmark blocks: Q2^T J_p stored (Sec. 5.1) or the factorisation kept (implicit_blocks)")
+    ap.add_argument("--storage", default="implicit", choices=["stored", "implicit"],
+                    help="landmark blocks: the factorisation kept (implicit_blocks, default) or Q2^T J_p "
+                         "stored (Sec. 5.1)")
+    ap.add_argument("--no-alt", action="store_true", help="skip timing the other storage form")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--learned-train", type=int, default=32)
@@ -263,8 +265,127 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def kernel_bytes(implicit, info):
+    """Algorithmic bytes per launch of K1, K3 and K4 (the byte models of the
+    measurement section of the design doc restated: what each launch must move)."""
+    sum_k2 = info["sum_k2"]
+    n_obs, n_pt, n_cam = info["n_obs"], info["n_pt"], info["n_cam"]
+    if implicit:
+        return {
+            # K4: per observation its record (J_s and Householder rows, 96 B) and
+            # camera index (4 B), per landmark Tm and S (48 B)
+            "matvec": 100.0 * n_obs + 48.0 * n_pt,
+            # K1: write records (96 B), residuals (8 B) and the top rows (3 x 9 floats
+            # per observation, 3 x 4 per landmark) and Tm (24 B per landmark); read the
+            # observations (12 B), points (12 B) and cameras (36 B)
+            "linearize": (96.0 + 8.0 + 108.0 + 12.0) * n_obs + (48.0 + 24.0 + 12.0) * n_pt + 36.0 * n_cam,
+            # K3 (Gram form) as below plus G_tt (36 B) per landmark
+            "precond": 156.0 * n_obs + 36.0 * n_pt + 4.0 * 196 * n_cam,
+        }
+    return {
+        # K4: every A_j = Q2^T J_p (2k x 9k FP32) streamed once per launch
+        "matvec": 72.0 * sum_k2,
+        # K1: write 4 (2k+3)(9k+4) B per landmark, (2k+3)(9k+4) = 18k^2 + 35k + 12,
+        # read the observations (12 B each), points and cameras
+        "linearize": 4.0 * (18.0 * sum_k2 + 35.0 * n_obs + 12.0 * n_pt) + 12.0 * n_obs + 12.0 * n_pt
+        + 36.0 * n_cam,
+        # K3 (Gram form): per observation its camera-list entry, landmark index,
+        # measurement, landmark offsets and point (36 B) and its 3 x 9 slice and
+        # residual column of the top rows (120 B); per camera its frame and
+        # D_p^2 read, the block, its inverse and g written (4 (16 + 9 + 171) B)
+        "precond": 156.0 * n_obs + 4.0 * 196 * n_cam,
+    }
+
+
+def measure_solves(sq, scene, stream, implicit, args, steps, warmup, world, config, seed, clocks=None):
+    """Solves of `scene` to f_tau in one storage form: untimed solve to the
+    solver's own stop (f0, its best cost), warm-up, `steps` event-timed solves
+    (L2 flushed before each), then profiled solves for the kernel table."""
+    import torch
+    p = sq.Problem.from_scene(scene, stream=stream.cuda_stream, autotune=0 if implicit else 1,
+                              implicit_blocks=1 if implicit else 0)
+    info = p.info()
+    reps = p.solve()
+    f0 = reps[0]["cost"]
+    f_gpu = min([r["new_cost"] for r in reps if r["accepted"]] + [f0])
+    f_star, f_tau, f_src = shared_f_tau(config, seed, f0, lambda: f_gpu)
+    cams0, pts0 = scene.cams, scene.pts
+    p.set_target_cost(f_tau)
+    if clocks:
+        clocks.start()
+    for _ in range(warmup):
+        p.set_params(cams0, pts0)
+        solve_to_tol(p, f_tau)
+    # timed steps without event profiling (the PCG then runs as one graph
+    # launch with a device-side loop); the kernel table comes from a separate
+    # profiled run of the same steps
+    p.set_profiling(False)  # resets the launch and transfer counters
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    step_ms, iters, cgs, reached = [], [], [], True
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MB, twice the L2
+    wall0 = time.perf_counter()
+    for _ in range(steps):
+        p.set_params(cams0, pts0)  # outside the event-timed interval
+        flush.zero_()  # evicts the previous step's data from L2, before the interval
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        it, cg, ok = solve_to_tol(p, f_tau)
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        iters.append(it)
+        cgs.append(cg)
+        reached &= ok
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop() if clocks else None
+    launches = p.profile()["kernel_launches"]
+    p.set_profiling(True)
+    prof_steps = min(steps, 20)
+    for _ in range(prof_steps):
+        p.set_params(cams0, pts0)
+        solve_to_tol(p, f_tau)
+    prof = p.profile()
+    p.close()
+    total_ms = max_over_ranks(sum(step_ms))
+    ms_per_step = total_ms / steps
+    peak, peak_kind = measured_peaks()
+    kb = kernel_bytes(implicit, info)
+    kernels = {}
+    for name in ("linearize", "damp", "precond", "matvec", "backsub", "cost"):
+        e = prof[name]
+        if e["count"]:
+            avg_ms = e["ms"] / e["count"]
+            d = {"launches": e["count"], "total_ms": round(e["ms"], 4), "avg_us": round(avg_ms * 1e3, 3),
+                 "share_of_step": round(e["ms"] / prof_steps / ms_per_step, 4) if ms_per_step else None}
+            if name in kb:
+                d["algorithmic_bytes"] = kb[name]
+                d["achieved_gbs"] = round(kb[name] / (avg_ms * 1e-3) / 1e9, 1)
+            kernels[name] = d
+
+    def roof(name):
+        src = {"matvec": "implicit.cu" if implicit else "matvec.cu", "precond": "pcg.cu",
+               "linearize": "linearize.cu"}[name]
+        return {"kernel": name, "bound": "hbm", "achieved": kernels[name]["achieved_gbs"], "peak": peak,
+                "unit": "GB/s", "frac": round(kernels[name]["achieved_gbs"] / peak, 4),
+                "traffic": recorded_traffic(name + ("_implicit" if implicit else ""), src, config),
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback 6800 GB/s"}
+
+    dom = max((k for k in kernels if k in kb), key=lambda k: kernels[k]["total_ms"])
+    return dict(info=info, f0=f0, f_gpu=f_gpu, f_star=f_star, f_tau=f_tau, f_src=f_src, ms_per_step=ms_per_step,
+                iters=iters, cgs=cgs, reached=reached, wall=wall, clk=clk, launches=launches,
+                kernels=kernels, prof_steps=prof_steps, roofline=roof(dom), matvec_roofline=roof("matvec"),
+                stored_gb=(100.0 * info["n_obs"] + 128.0 * info["n_pt"]) / 1e9 if implicit
+                else 72.0 * info["sum_k2"] / 1e9)
+
+
 def run_ours(args):
-    import numpy as np
     import torch
 
     rank, world, local = rank_env()
@@ -282,120 +403,30 @@ def run_ours(args):
     sq.lib()  # fails loudly when the library is missing
     scene = make_scene(args.config, args.seed)
     stream = torch.cuda.current_stream()
-    implicit = 1 if args.storage == "implicit" else 0
-    # the matvec plan is autotuned during the first (untimed) solve (stored blocks)
-    p = sq.Problem.from_scene(scene, stream=stream.cuda_stream, autotune=1 - implicit, implicit_blocks=implicit)
-    info = p.info()
-
-    # the solver run to its own stopping rule (untimed): f0 and its best cost
-    reps = p.solve()
-    f0 = reps[0]["cost"]
-    f_gpu = min([r["new_cost"] for r in reps if r["accepted"]] + [f0])
-    f_star, f_tau, f_src = shared_f_tau(args.config, args.seed, f0, lambda: f_gpu)
-    cams0, pts0 = scene.cams, scene.pts
-    p.set_target_cost(f_tau)
-
-    clocks = ClockSampler(dev)
-    clocks.start()
-    for _ in range(args.warmup):
-        p.set_params(cams0, pts0)
-        solve_to_tol(p, f_tau)
-
-    # timed steps without event profiling (the PCG then runs as one graph
-    # launch with a device-side loop); the kernel table below comes from a
-    # separate profiled run of the same steps
-    p.set_profiling(False)  # resets the launch and transfer counters
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    step_ms, iters, cgs, reached = [], [], [], True
-    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MB, twice the L2
-    wall0 = time.perf_counter()
-    for _ in range(args.steps):
-        p.set_params(cams0, pts0)  # outside the event-timed interval
-        flush.zero_()  # evicts the previous step's data from L2, before the interval
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        it, cg, ok = solve_to_tol(p, f_tau)
-        ev1.record(stream)
-        ev1.synchronize()
-        step_ms.append(ev0.elapsed_time(ev1))
-        iters.append(it)
-        cgs.append(cg)
-        reached &= ok
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - wall0
-    if world > 1:
-        torch.distributed.barrier()
-    clk = clocks.stop()
-    launches_timed = p.profile()["kernel_launches"]
-    p.set_profiling(True)
-    for _ in range(min(args.steps, 20)):
-        p.set_params(cams0, pts0)
-        solve_to_tol(p, f_tau)
-    prof = p.profile()
-    prof_steps = min(args.steps, 20)
-
-    total_ms = max_over_ranks(sum(step_ms))
-    ms_per_step = total_ms / args.steps
-
-    # roofline of the kernels (algorithmic bytes / event-timed launch durations)
-    sum_k2 = info["sum_k2"]
+    implicit = args.storage == "implicit"
+    m = measure_solves(sq, scene, stream, implicit, args, args.steps, args.warmup, world, args.config, args.seed,
+                       clocks=ClockSampler(dev))
+    info, f_tau = m["info"], m["f_tau"]
     n_obs, n_pt, n_cam = info["n_obs"], info["n_pt"], info["n_cam"]
-    peak, peak_kind = measured_peaks()
-    if implicit:
-        kb = {
-            # K4: per observation its record (J_s and Householder rows, 96 B) and
-            # camera index (4 B), per landmark Tm and S (48 B)
-            "matvec": 100.0 * n_obs + 48.0 * n_pt,
-            # K1: write records (96 B), residuals (8 B) and the top rows (3 x 9 floats
-            # per observation, 3 x 4 per landmark) and Tm (24 B per landmark); read the
-            # observations (12 B), points (12 B) and cameras (36 B)
-            "linearize": (96.0 + 8.0 + 108.0 + 12.0) * n_obs + (48.0 + 24.0 + 12.0) * n_pt + 36.0 * n_cam,
-            # K3 (Gram form) as below plus G_tt (36 B) per landmark
-            "precond": 156.0 * n_obs + 36.0 * n_pt + 4.0 * 196 * n_cam,
-        }
-    else:
-        kb = {
-            # K4: every A_j = Q2^T J_p (2k x 9k FP32) streamed once per launch
-            "matvec": 72.0 * sum_k2,
-            # K1: write 4 (2k+3)(9k+4) B per landmark, (2k+3)(9k+4) = 18k^2 + 35k + 12,
-            # read the observations (12 B each), points and cameras
-            "linearize": 4.0 * (18.0 * sum_k2 + 35.0 * n_obs + 12.0 * n_pt) + 12.0 * n_obs + 12.0 * n_pt
-            + 36.0 * n_cam,
-            # K3 (Gram form): per observation its camera-list entry, landmark index,
-            # measurement, landmark offsets and point (36 B) and its 3 x 9 slice and
-            # residual column of the top rows (120 B); per camera its frame and
-            # D_p^2 read, the block, its inverse and g written (4 (16 + 9 + 171) B)
-            "precond": 156.0 * n_obs + 4.0 * 196 * n_cam,
-        }
-    kernels = {}
-    for name in ("linearize", "damp", "precond", "matvec", "backsub", "cost"):
-        e = prof[name]
-        if e["count"]:
-            avg_ms = e["ms"] / e["count"]
-            d = {"launches": e["count"], "total_ms": round(e["ms"], 4), "avg_us": round(avg_ms * 1e3, 3),
-                 "share_of_step": round(e["ms"] / prof_steps / ms_per_step, 4) if ms_per_step else None}
-            if name in kb:
-                d["algorithmic_bytes"] = kb[name]
-                d["achieved_gbs"] = round(kb[name] / (avg_ms * 1e-3) / 1e9, 1)
-            kernels[name] = d
-    dom = max((k for k in kernels if k in kb), key=lambda k: kernels[k]["total_ms"])
-    src = {"matvec": "implicit.cu" if implicit else "matvec.cu", "precond": "pcg.cu",
-           "linearize": "linearize.cu"}[dom]
-    traffic = recorded_traffic(dom + ("_implicit" if implicit else ""), src, args.config)
-    roofline = {"kernel": dom, "bound": "hbm", "achieved": kernels[dom]["achieved_gbs"], "peak": peak,
-                "unit": "GB/s", "frac": round(kernels[dom]["achieved_gbs"] / peak, 4),
-                "traffic": traffic, "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
-                if peak_kind == "measured" else "fallback 6800 GB/s"}
+    # the other storage form of the same method, same f_tau (context; fewer steps)
+    alt = None
+    if not args.no_alt:
+        a = measure_solves(sq, scene, stream, not implicit, args, min(args.steps, 10), min(args.warmup, 3), world,
+                           args.config, args.seed)
+        alt = {"storage": "stored" if implicit else "implicit", "ms_per_step": a["ms_per_step"],
+               "lm_iters_per_step": statistics.mean(a["iters"]), "pcg_iters_per_step": statistics.mean(a["cgs"]),
+               "reached_tol": a["reached"], "roofline": a["roofline"], "matvec_roofline": a["matvec_roofline"],
+               "kernels": {k: {"avg_us": v["avg_us"], "achieved_gbs": v.get("achieved_gbs")}
+                           for k, v in a["kernels"].items()},
+               "device_bytes": a["info"]["device_bytes"], "steps": min(args.steps, 10)}
 
     # end to end through the C ABI from host buffers
     e2e_times, h2d, d2h = [], [], []
     for _ in range(args.e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        q = sq.Problem.from_scene(scene, stream=stream.cuda_stream, target_cost=f_tau, implicit_blocks=implicit)
+        q = sq.Problem.from_scene(scene, stream=stream.cuda_stream, target_cost=f_tau,
+                                  implicit_blocks=1 if implicit else 0)
         solve_to_tol(q, f_tau)
         q.get_params()
         pr = q.profile()
@@ -404,7 +435,6 @@ def run_ours(args):
         e2e_times.append(time.perf_counter() - t0)
         h2d.append(pr["h2d_bytes"])
         d2h.append(pr["d2h_bytes"])
-    p.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -418,29 +448,30 @@ def run_ours(args):
                          f"solve on one thread"}
 
     if rank == 0:
+        ms_per_step = m["ms_per_step"]
         line = {
             "metric": METRIC, "value": ms_per_step / 1e3, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{args.config}: {n_cam} cams, {n_pt} landmarks, {n_obs} obs, seed {args.seed}",
-                       "tau": TAU, "f0": f0, "f_star": f_star, "f_tau": f_tau, "f_star_source": f_src,
-                       "f_gpu_converged": f_gpu,
-                       "storage": args.storage,
-                       "stored_blocks_gb": round((100.0 * n_obs + 128.0 * n_pt if implicit else 72.0 * sum_k2)
-                                                 / 1e9, 3), "k_max": info["k_max"],
+                       "tau": TAU, "f0": m["f0"], "f_star": m["f_star"], "f_tau": f_tau,
+                       "f_star_source": m["f_src"], "f_gpu_converged": m["f_gpu"], "storage": args.storage,
+                       "stored_blocks_gb": round(m["stored_gb"], 3), "k_max": info["k_max"],
                        "l2": "L2 flushed between timed steps (a 256 MB buffer written outside the timed "
                              "interval)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "lm_iters_per_step": statistics.mean(iters), "pcg_iters_per_step": statistics.mean(cgs),
-            "reached_tol": reached, "wall_s": wall,
-            "roofline": roofline, "kernels": kernels,
-            "gpu_launches": launches_timed,
-            "kernel_table": f"per-kernel times from {prof_steps} further steps with event profiling",
+            "lm_iters_per_step": statistics.mean(m["iters"]), "pcg_iters_per_step": statistics.mean(m["cgs"]),
+            "reached_tol": m["reached"], "wall_s": m["wall"],
+            "roofline": m["roofline"], "matvec_roofline": m["matvec_roofline"], "kernels": m["kernels"],
+            "gpu_launches": m["launches"],
+            "kernel_table": f"per-kernel times from {m['prof_steps']} further steps with event profiling",
             "e2e": {"value": statistics.mean(e2e_times), "unit": UNIT,
                     "h2d_bytes_per_step": int(statistics.mean(h2d)), "d2h_bytes_per_step": int(statistics.mean(d2h))},
-            "clocks": clk,
+            "clocks": m["clk"],
             "device_bytes": info["device_bytes"],
         }
+        if alt:
+            line["other_storage"] = alt
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
