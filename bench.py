@@ -16,6 +16,7 @@ FP64 oracle (explicit Schur complement) on the host cores instead.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
     python bench.py --config batched   # 256 independent problems: problems/s, p50/p99
     python bench.py --config learned --steps 3   # learned vs plain PCG (trains first)
+    python bench.py --config explicit32   # LM backtracking: explicit FP32 Schur complement vs sqrt-32
 """
 from __future__ import annotations
 
@@ -661,6 +662,68 @@ def run_reference_batched(args):
 
 
 # ---------------------------------------------------------------------------
+# explicit-32 vs sqrt-32 (Sec. 6.4): LM backtracking on seeded scenes
+# ---------------------------------------------------------------------------
+EXPLICIT_METRIC = "LM steps rejected, explicit-32 Schur complement vs sqrt-32"
+EXPLICIT_SCENES = [("tiny", s, {}) for s in range(4)] + \
+    [("walk", s, dict(n_cam=100, n_pt=20000, step_sigma=0.05, depth=(20.0, 200.0))) for s in range(2, 4)] + \
+    [("small", s, dict(n_cam=40, n_pt=1500, p=0.35, cap=12, f_range=(60.0, 6000.0), dist_sigma=0.1))
+     for s in range(21, 24)]
+
+
+def run_explicit32(args):
+    """Each scene solved (<= 30 LM iterations, Sec. 6.1 rules) by sqrt-32 and by
+    the explicit FP32 Schur complement on the GPU, and by the FP64 oracle (the
+    explicit Schur complement in double precision, explicit-64) where it is
+    small; counts of rejected LM steps, PCG breakdowns and preconditioner
+    blocks that fail their FP32 Cholesky, and the final costs."""
+    import torch
+    import oracle
+    import paper_2103_01843_gb300 as sq
+    from paper_2103_01843_gb300.synth import make_scene
+    torch.cuda.set_device(0)
+    sq.lib()
+    stream = torch.cuda.current_stream()
+    oracle.set_threads(host_threads())
+    rows, tot = [], {m: dict(rejected=0, breakdowns=0, fallbacks=0, ms=0.0) for m in ("sqrt32", "explicit32")}
+    tot["explicit64"] = dict(rejected=0, scenes=0)
+    for name, seed, kw in EXPLICIT_SCENES:
+        sc = make_scene(name, seed, **kw)
+        row = {"scene": f"{name} seed {seed}", "n_obs": sc.n_obs}
+        for mode, extra in (("sqrt32", {}), ("explicit32", {"schur_explicit": 1})):
+            with sq.Problem.from_scene(sc, stream=stream.cuda_stream, max_lm_iters=30, **extra) as p:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                reps = p.solve()
+                torch.cuda.synchronize()
+                dt = (time.perf_counter() - t0) * 1e3
+            st = dict(rejected=sum(1 for r in reps if not r["accepted"]),
+                      breakdowns=sum(1 for r in reps if r["pcg_stop_reason"] == 3),
+                      fallbacks=sum(r["precond_fallbacks"] for r in reps),
+                      final=min([r["new_cost"] for r in reps if r["accepted"]] + [reps[0]["cost"]]),
+                      lambda_max=max(r["lambda"] for r in reps), iters=len(reps), ms=round(dt, 2))
+            row[mode] = st
+            for key in ("rejected", "breakdowns", "fallbacks", "ms"):
+                tot[mode][key] += st[key]
+        if sc.n_obs < 20000:
+            _, _, log = oracle.lm(sc, max_iters=30, dense=False)
+            row["explicit64"] = dict(rejected=sum(1 for e in log if not e["accepted"]), iters=len(log),
+                                     final=min([e["new_cost"] for e in log if e["accepted"]] + [log[0]["cost"]]))
+            tot["explicit64"]["rejected"] += row["explicit64"]["rejected"]
+            tot["explicit64"]["scenes"] += 1
+        rows.append(row)
+    line = {"metric": EXPLICIT_METRIC, "value": tot["explicit32"]["rejected"], "unit": "rejected LM steps",
+            "higher_is_better": False, "n_gpus": 1, "steps": 1, "warmup": 0, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None,
+            "config": {"workload": f"{len(EXPLICIT_SCENES)} seeded scenes: 4 tiny rings, 2 short-baseline walks "
+                                   f"(100 cams, steps 0.05 m, depth 20-200 m), 3 ill-conditioned camera sets "
+                                   f"(f 60-6000 px, k1, k2 ~ 0.1); <= 30 LM iterations each"},
+            "totals": tot, "scenes": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
 # learned warm start + preconditioner: PCG iterations and time, learned vs plain
 # ---------------------------------------------------------------------------
 LEARNED_METRIC = "PCG iters learned vs plain"
@@ -825,6 +888,12 @@ def main():
         return run_learned(args)
     if args.config == "batched":
         return run_reference_batched(args) if args.impl == "reference" else run_batched(args)
+    if args.config == "explicit32":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the explicit-64 counts are part of the "
+                              "--config explicit32 line itself"}), flush=True)
+            return 0
+        return run_explicit32(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

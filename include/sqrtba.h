@@ -104,6 +104,14 @@ typedef struct {
                              each observation's rows [J | r] are scaled by sqrt(w),
                              w = min(1, delta / ||r_ij||), and the model cost is
                              sum rho(s) - w s + w ||r + J dx||^2.  0 (default): squared norm */
+    int32_t schur_explicit; /* 1: the comparison solver of Sec. 6.4 ("explicit-32"): the reduced
+                             camera system H~ = H_pp - H_pl (H_ll + lambda D_l^2)^-1 H_lp is formed
+                             explicitly in FP32 at every damping (Sec. 4.2, Eq. red_normal_eq) and
+                             solved by the same block-Jacobi PCG; landmarks by Eq. backsub_sc.
+                             Kept to test the paper's claim that this form loses positive
+                             definiteness in FP32 where the square-root form does not.
+                             Excludes implicit_blocks.  0 (default): square root BA */
+    int32_t reserved;     /* zero */
 } ba_options;
 
 /* Fills *opt with the defaults above. */

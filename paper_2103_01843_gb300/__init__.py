@@ -42,7 +42,8 @@ class Options(ctypes.Structure):
                 ("autotune", ctypes.c_int32), ("use_learned", ctypes.c_int32),
                 ("pipeline_stages", ctypes.c_int32), ("target_cost", ctypes.c_double),
                 ("precond_from_blocks", ctypes.c_int32), ("implicit_blocks", ctypes.c_int32),
-                ("huber_delta", ctypes.c_double)]
+                ("huber_delta", ctypes.c_double), ("schur_explicit", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class PcgReport(ctypes.Structure):

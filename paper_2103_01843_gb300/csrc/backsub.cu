@@ -224,8 +224,11 @@ __global__ void k_candidate(int n_cam, const float* __restrict__ cams, const flo
 // K6: dl per landmark, then the model cost L(dx) per observation (FP64)
 void launch_backsub(Problem& p) {
     count_launches(p, 3);
-    k_backsub_dl<<<ceil_div(p.n_pt, BS_WARPS), 32 * BS_WARPS, 0, p.stream>>>(
-        p.n_pt, p.pt_off, p.obs_cam_s, p.tpool, p.x, p.dl, p.implicit ? p.lmrec : nullptr, p.lm_pos);
+    if (p.schur)
+        launch_schur_backsub(p);
+    else
+        k_backsub_dl<<<ceil_div(p.n_pt, BS_WARPS), 32 * BS_WARPS, 0, p.stream>>>(
+            p.n_pt, p.pt_off, p.obs_cam_s, p.tpool, p.x, p.dl, p.implicit ? p.lmrec : nullptr, p.lm_pos);
     k_model_cost<<<p.red_grid, 256, 0, p.stream>>>(p.n_obs, p.frames, p.pts, p.obs_cam_s, p.obs_pt_s, p.obs_xy_s, p.x,
                                                    p.dl, nullptr, nullptr, p.partials, nullptr, (float)p.opt.huber_delta);
     k_sum_partials<<<1, 1024, 0, p.stream>>>(p.partials, p.red_grid, p.dsum + 1);
@@ -237,8 +240,11 @@ void launch_backsub(Problem& p) {
 // energy (dsum[0]); a batch gets both per problem (cost_a, cost_b)
 void launch_backsub_candidate_cost(Problem& p) {
     count_launches(p, p.batch.n_prob > 0 ? 2 : 3);
-    k_backsub_dl<<<ceil_div(p.n_pt, BS_WARPS), 32 * BS_WARPS, 0, p.stream>>>(
-        p.n_pt, p.pt_off, p.obs_cam_s, p.tpool, p.x, p.dl, p.implicit ? p.lmrec : nullptr, p.lm_pos);
+    if (p.schur)
+        launch_schur_backsub(p);
+    else
+        k_backsub_dl<<<ceil_div(p.n_pt, BS_WARPS), 32 * BS_WARPS, 0, p.stream>>>(
+            p.n_pt, p.pt_off, p.obs_cam_s, p.tpool, p.x, p.dl, p.implicit ? p.lmrec : nullptr, p.lm_pos);
     launch_candidate(p);
     if (p.batch.n_prob > 0) {
         BatchState& B = p.batch;

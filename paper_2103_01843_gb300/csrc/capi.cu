@@ -122,6 +122,12 @@ void d2h(Problem& p, T* dst, const T* src, int64_t n) {
     BA_CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(T) * n, cudaMemcpyDeviceToHost, p.stream));
     p.d2h_bytes += (int64_t)sizeof(T) * n;
 }
+// device -> host copy that completes before returning (set-up only)
+template <typename T>
+void d2h_sync_copy(Problem& p, T* dst, const T* src, int64_t n) {
+    BA_CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(T) * n, cudaMemcpyDeviceToHost, p.stream));
+    BA_CUDA_TRY(cudaStreamSynchronize(p.stream));
+}
 
 // --- optional phase timing (CUDA events, resolved at synchronisation points) --
 cudaEvent_t prof_event(Problem& p) {
@@ -716,9 +722,11 @@ void create_problem(Problem& p, const double* cams, int32_t n_cam, const double*
     require(p.opt.lambda0 > 0 && p.opt.max_lm_iters >= 1 && p.opt.max_cg_iters >= 1 && p.opt.cg_eta > 0 &&
             (p.opt.pipeline_stages == 0 || (p.opt.pipeline_stages >= 4 && p.opt.pipeline_stages <= 6)) &&
             (p.opt.implicit_blocks == 0 || p.opt.implicit_blocks == 1) &&
-            std::isfinite(p.opt.huber_delta) && p.opt.huber_delta >= 0.0,
+            std::isfinite(p.opt.huber_delta) && p.opt.huber_delta >= 0.0 &&
+            (p.opt.schur_explicit == 0 || (p.opt.schur_explicit == 1 && p.opt.implicit_blocks == 0)),
             BA_ERR_INVALID_ARG, "invalid options");
     p.implicit = p.opt.implicit_blocks != 0;
+    p.schur = p.opt.schur_explicit != 0;
     p.n_cam = n_cam;
     p.n_pt = n_pt;
     p.n_obs = n_obs;
@@ -792,9 +800,19 @@ void create_problem(Problem& p, const double* cams, int32_t n_cam, const double*
     build_index(p, d_oc, d_op, d_xy, d_cams, d_pts);
     require(p.k_max <= linearize_k_limit(), BA_ERR_INVALID_ARG,
             "a landmark has more observations than the supported maximum (900)");
-    p.t_floats = 3 * (9 * n_obs + 4 * (int64_t)n_pt);
-    p.tpool = dalloc<float>(p, p.t_floats);
-    if (p.implicit) {
+    if (p.schur) {
+        // the explicit Schur complement: its pattern from the sorted observations
+        std::vector<int32_t> h_pt_off(n_pt + 1), h_cam(n_obs);
+        d2h_sync_copy(p, h_pt_off.data(), p.pt_off, n_pt + 1);
+        d2h_sync_copy(p, h_cam.data(), p.obs_cam_s, n_obs);
+        plan_schur(p, h_pt_off, h_cam);
+        p.tuned = true;
+    } else {
+        p.t_floats = 3 * (9 * n_obs + 4 * (int64_t)n_pt);
+        p.tpool = dalloc<float>(p, p.t_floats);
+    }
+    if (p.schur) {
+    } else if (p.implicit) {
         plan_implicit(p);
         p.ipool = dalloc<float>(p, 24 * n_obs);
         p.rpool = dalloc<float>(p, 2 * n_obs);
@@ -824,7 +842,7 @@ void create_problem(Problem& p, const double* cams, int32_t n_cam, const double*
     BA_CUDA_TRY(cudaMemsetAsync(p.dl, 0, sizeof(float) * 3 * n_pt, p.stream));
     configure_linearize(p);
     if (p.implicit) configure_implicit(p);
-    else configure_matvec(p);
+    else if (!p.schur) configure_matvec(p);
     sync(p);
 }
 
@@ -1208,8 +1226,8 @@ ba_status ba_set_options(ba_problem* h, const ba_options* opt) {
             std::isfinite(opt->huber_delta) && opt->huber_delta >= 0.0,
             BA_ERR_INVALID_ARG, "invalid options");
     Problem& p = h->p;
-    require(opt->implicit_blocks == p.opt.implicit_blocks, BA_ERR_INVALID_ARG,
-            "implicit_blocks is fixed when the problem is created");
+    require(opt->implicit_blocks == p.opt.implicit_blocks && opt->schur_explicit == p.opt.schur_explicit,
+            BA_ERR_INVALID_ARG, "implicit_blocks and schur_explicit are fixed when the problem is created");
     sync(p);
     const bool graph_change = opt->use_graph != p.opt.use_graph || opt->pipeline_stages != p.opt.pipeline_stages;
     if (opt->huber_delta != p.opt.huber_delta) {
@@ -1316,6 +1334,7 @@ ba_status ba_debug_export_landmark(ba_problem* h, int32_t j, int32_t k_cap, floa
     require(k <= k_cap, BA_ERR_INVALID_ARG, "k exceeds k_cap");
     require(!p.implicit || (!a && !c && !rot), BA_ERR_INVALID_ARG,
             "implicit storage: only the (undamped) top rows are stored");
+    require(!p.schur, BA_ERR_INVALID_ARG, "the explicit Schur complement stores no landmark blocks");
     const int64_t ncol = 9 * (int64_t)k;
     if (top) d2h(p, top, p.tpool + top_offset(off[0], j), 3 * (ncol + 4));
     if (a) d2h(p, a, p.apool + aoff, 2 * (int64_t)k * ncol);

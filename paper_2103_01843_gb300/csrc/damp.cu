@@ -234,6 +234,10 @@ k_damp_implicit(int n_pt, const int32_t* __restrict__ lm_by_k, const int32_t* __
 }  // namespace
 
 void launch_damp(Problem& p, bool undo_old, float lambda) {
+    if (p.schur) {  // the explicit Schur complement is re-formed at every damping
+        launch_schur_assemble(p, lambda);
+        return;
+    }
     count_launches(p, 1);
     if (p.implicit) {
         k_damp_implicit<<<ceil_div(p.n_pt, 128), 128, 0, p.stream>>>(p.n_pt, p.lm_by_k, p.pt_off, p.tpool, p.dl2,

@@ -552,6 +552,11 @@ void configure_linearize(Problem& p) {
 // joined back into the problem's stream) beside the team kernels, which run
 // one after the other (run side by side they only contend).
 void launch_linearize(Problem& p) {
+    if (p.schur) {  // no factorisation: D_p^2 and D_l^2 only (the Schur complement is formed per damping)
+        launch_camera_diag(p);
+        launch_schur_dl2(p);
+        return;
+    }
     LinArgs A{p.frames, p.pts, p.obs_cam_s, p.obs_xy_s, p.pt_off, p.a_off, p.apool, p.tpool, p.cpool, p.c_off,
               p.dl2, p.implicit ? p.ipool : nullptr, p.rpool, p.lmrec, p.n_obs, (float)p.opt.huber_delta};
     // segments of lm_by_k: k > 32 | 9..32 | 5..8 | 2..4
@@ -588,6 +593,13 @@ void launch_linearize(Problem& p) {
     BA_LAUNCH_CHECK();
     BA_CUDA_TRY(cudaEventRecord(p.ev_join, p.side));
     BA_CUDA_TRY(cudaStreamWaitEvent(p.stream, p.ev_join, 0));
+}
+
+void launch_camera_diag(Problem& p) {
+    count_launches(p, 1);
+    k_camera_diag<<<p.n_cam, CD_THREADS, 0, p.stream>>>(p.n_cam, p.frames, p.pts, p.obs_pt_s, p.obs_xy_s, p.cam_off,
+                                                        p.cam_list, p.dp2, (float)p.opt.huber_delta);
+    BA_LAUNCH_CHECK();
 }
 
 void launch_export_jacobians(Problem& p, float* r, float* jp, float* jl) {

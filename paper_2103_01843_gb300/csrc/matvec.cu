@@ -767,6 +767,10 @@ void launch_matvec_raw(Problem& p, const float* v, float* y, const PcgScalars* S
         launch_matvec_implicit(p, v, y, S);
         return;
     }
+    if (p.schur) {
+        launch_schur_matvec(p, v, y, S);
+        return;
+    }
     const MvArgs a = make_args(p, p.mv_plan, v, y, S);
     pick_kernel(p, p.mv_plan, false)<<<p.mv_grid, MV_THREADS, smem_bytes(p, p.mv_plan, false), p.stream>>>(a);
     BA_LAUNCH_CHECK();

@@ -165,6 +165,13 @@ struct Problem {
     int32_t* lm_pos = nullptr;       // storage position of every landmark
     void* im_tasks = nullptr;        // matvec tasks (implicit.cu)
     int im_ntasks = 0;
+    // explicit Schur complement in FP32 (ba_options.schur_explicit, schur.cu):
+    // block CSR of H~ with both triangles, pair -> blocks map, b~
+    bool schur = false;
+    int32_t *sc_row_ptr = nullptr, *sc_col = nullptr, *sc_diag_blk = nullptr, *sc_pair_blk = nullptr;
+    int64_t* sc_pair_off = nullptr;
+    int64_t sc_nblk = 0;
+    float *sc_blk = nullptr, *sc_bt = nullptr;
     float *dp2 = nullptr, *dl2 = nullptr;
     // PCG
     float *g = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
@@ -260,6 +267,15 @@ void launch_matvec(Problem& p, const float* v, float* y, bool add_damping);
 void launch_matvec_raw(Problem& p, const float* v, float* y, const PcgScalars* S);
 // implicit storage (implicit.cu): task plan, kernel attributes, y += A^T A v
 void plan_implicit(Problem& p);
+// explicit Schur complement (schur.cu): pattern from the sorted observations
+// (host copies), D_l^2, assembly at lambda, preconditioner, matvec, back substitution
+void plan_schur(Problem& p, const std::vector<int32_t>& pt_off, const std::vector<int32_t>& obs_cam_s);
+void launch_schur_dl2(Problem& p);
+void launch_schur_assemble(Problem& p, float lambda);
+void launch_schur_precond(Problem& p);
+void launch_schur_matvec(Problem& p, const float* v, float* y, const PcgScalars* S);
+void launch_schur_backsub(Problem& p);
+void launch_camera_diag(Problem& p);  // D_p^2 alone (linearize.cu)
 void configure_implicit(Problem& p);
 void launch_matvec_implicit(Problem& p, const float* v, float* y, const PcgScalars* S);
 void launch_precond_records(Problem& p);

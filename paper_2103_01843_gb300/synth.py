@@ -198,10 +198,10 @@ def _gt_ring(rng, n_cam, n_pt, radius, box_half, k_sampler, window=None,
     return R, t, f, k1, k2, X, np.concatenate(obs_cam), np.concatenate(obs_pt)
 
 
-def _gt_walk(rng, n_cam, n_pt, k_sampler, window=80):
+def _gt_walk(rng, n_cam, n_pt, k_sampler, window=80, step_sigma=0.5, depth_range=(2.0, 20.0)):
     """Cameras along a random-walk trajectory with drifting heading."""
     yaw = np.cumsum(rng.normal(0.0, 0.05, n_cam))
-    step = rng.normal(0.0, 0.5, (n_cam, 3))
+    step = rng.normal(0.0, step_sigma, (n_cam, 3))
     step[:, 2] *= 0.1
     C = np.cumsum(step, 0)
     R = np.stack([_yaw_frame(y) for y in yaw])
@@ -218,7 +218,7 @@ def _gt_walk(rng, n_cam, n_pt, k_sampler, window=80):
             m = idx.size
             anchor = rng.integers(0, n_cam, m)
             uv = rng.uniform(-0.9 * IMAGE_HALF, 0.9 * IMAGE_HALF, (m, 2))
-            depth = rng.uniform(2.0, 20.0, m)
+            depth = rng.uniform(depth_range[0], depth_range[1], m)
             Pc = np.concatenate([uv / f[anchor, None] * depth[:, None],
                                  -depth[:, None]], 1)
             X[idx] = np.einsum("nji,nj->ni", R[anchor], Pc - t[anchor])
@@ -423,7 +423,9 @@ def make_scene(name="tiny", seed=0, noise_px=1.0, perturb=True, outlier_frac=0.0
     walk   : medium-shaped (the medium generator and k distribution) with
              n_cam / n_pt given by keywords (defaults 100 cams, 20000
              points); the training and evaluation scenes of the learned
-             warm start.
+             warm start.  step_sigma (m) and depth = (lo, hi) (m) set the
+             baselines and point depths (short baselines to far points make
+             the landmark blocks ill-conditioned).
     """
     rng = np.random.default_rng(seed)
     if name == "tiny":
@@ -441,7 +443,8 @@ def make_scene(name="tiny", seed=0, noise_px=1.0, perturb=True, outlier_frac=0.0
                       height_sigma=0.5, f_range=kw.get("f_range"),
                       dist_sigma=kw.get("dist_sigma", 1e-3))
     elif name == "walk":
-        gt = _gt_walk(rng, kw.get("n_cam", 100), kw.get("n_pt", 20_000), _geom0(0.2, 64))
+        gt = _gt_walk(rng, kw.get("n_cam", 100), kw.get("n_pt", 20_000), _geom0(0.2, 64),
+                      step_sigma=kw.get("step_sigma", 0.5), depth_range=kw.get("depth", (2.0, 20.0)))
     elif name == "batched_member":
         n_cam = int(rng.integers(8, 65))
         n_pt = int(rng.integers(200, 5001))
