@@ -20,60 +20,70 @@ namespace {
 
 constexpr int BS_WARPS = 8;
 
-// dl_j for one landmark per warp: lanes over the 9k pose columns of the
-// three top rows (coalesced), then the 3x3 triangular solve
+// dl_j for one landmark per team of BS_TEAM lanes, landmarks in storage order
+// (neighbouring teams have equal or similar k): lane t takes observations
+// t, t + BS_TEAM, ...: its camera's dx_p (9 values) against its 3 x 9 slice of
+// the top rows (three contiguous 36-byte runs), then a team sum of the three
+// partial dot products and the 3x3 triangular solve on the team's first lane.
+constexpr int BS_TEAM = 8;
 __global__ void __launch_bounds__(32 * BS_WARPS)
-k_backsub_dl(int n_pt, const int32_t* __restrict__ pt_off, const int32_t* __restrict__ obs_cam_s,
-             const float* __restrict__ tpool, const float* __restrict__ dp, float* __restrict__ dl,
-             const float* __restrict__ lmrec, const int32_t* __restrict__ lm_pos) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int j = blockIdx.x * BS_WARPS + w;
-    if (j >= n_pt) return;
-    const int s0 = pt_off[j], k = pt_off[j + 1] - s0, ncol = 9 * k;
+k_backsub_dl(int n_pt, const int32_t* __restrict__ lm_by_k, const int32_t* __restrict__ pt_off,
+             const int32_t* __restrict__ obs_cam_s, const float* __restrict__ tpool, const float* __restrict__ dp,
+             float* __restrict__ dl, const float* __restrict__ lmrec) {
+    const int lane = threadIdx.x & 31, rank = lane & (BS_TEAM - 1);
+    const int pos = (blockIdx.x * (32 * BS_WARPS) + threadIdx.x) / BS_TEAM;
+    const bool has = pos < n_pt;
+    const int j = has ? lm_by_k[pos] : 0;
+    const int s0 = has ? pt_off[j] : 0, k = has ? pt_off[j + 1] - s0 : 0, ncol = 9 * k;
     const float* top = tpool + top_offset(s0, j);
     float t0 = 0.f, t1 = 0.f, t2 = 0.f;
-    for (int col = lane; col < ncol; col += 32) {
-        const int s = col / 9;
-        const float d = __ldg(dp + 9 * obs_cam_s[s0 + s] + (col - 9 * s));
-        t0 += top[col] * d;
-        t1 += top[(ncol + 4) + col] * d;
-        t2 += top[2 * (ncol + 4) + col] * d;
-    }
-    t0 = warp_sum(t0);
-    t1 = warp_sum(t1);
-    t2 = warp_sum(t2);
-    if (lane == 0) {
-        const float* R0 = top + ncol;
-        const float* R1 = top + (ncol + 4) + ncol;
-        const float* R2 = top + 2 * (ncol + 4) + ncol;
-        t0 += R0[3];
-        t1 += R1[3];
-        t2 += R2[3];
-        if (lmrec) {
-            // implicit storage: undamped top rows; the damped right-hand side is
-            // G_tt times theirs and the damped R is stored with G_tt
-            const float* L = lmrec + 32LL * lm_pos[j];
-            const float* G = L + 16;
-            const float a0 = t0, a1 = t1, a2 = t2;
-            t0 = G[0] * a0 + G[1] * a1 + G[2] * a2;
-            t1 = G[3] * a0 + G[4] * a1 + G[5] * a2;
-            t2 = G[6] * a0 + G[7] * a1 + G[8] * a2;
-            const float r00 = L[25], r01 = L[26], r02 = L[27], r11 = L[28], r12 = L[29], r22 = L[30];
-            const float l2 = -t2 / r22;
-            const float l1 = (-t1 - r12 * l2) / r11;
-            const float l0 = (-t0 - r01 * l1 - r02 * l2) / r00;
-            dl[3 * j] = l0;
-            dl[3 * j + 1] = l1;
-            dl[3 * j + 2] = l2;
-            return;
+    for (int t = rank; t < k; t += BS_TEAM) {
+        const float* d = dp + 9 * __ldg(obs_cam_s + s0 + t);
+        const float* r0 = top + 9 * t;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+            const float dc = __ldg(d + c);
+            t0 += __ldg(r0 + c) * dc;
+            t1 += __ldg(r0 + (ncol + 4) + c) * dc;
+            t2 += __ldg(r0 + 2 * (ncol + 4) + c) * dc;
         }
-        const float l2 = -t2 / R2[2];
-        const float l1 = (-t1 - R1[2] * l2) / R1[1];
-        const float l0 = (-t0 - R0[1] * l1 - R0[2] * l2) / R0[0];
-        dl[3 * j] = l0;
-        dl[3 * j + 1] = l1;
-        dl[3 * j + 2] = l2;
     }
+#pragma unroll
+    for (int o = BS_TEAM / 2; o > 0; o >>= 1) {
+        t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+        t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+        t2 += __shfl_xor_sync(0xffffffffu, t2, o);
+    }
+    if (!has || rank != 0) return;
+    const float* R0 = top + ncol;
+    const float* R1 = top + (ncol + 4) + ncol;
+    const float* R2 = top + 2 * (ncol + 4) + ncol;
+    t0 += R0[3];
+    t1 += R1[3];
+    t2 += R2[3];
+    float r00 = R0[0], r01 = R0[1], r02 = R0[2], r11 = R1[1], r12 = R1[2], r22 = R2[2];
+    if (lmrec) {
+        // implicit storage: undamped top rows; the damped right-hand side is
+        // G_tt times theirs and the damped R is stored with G_tt
+        const float* L = lmrec + (int64_t)LM_REC * pos;
+        const float* G = L + 16;
+        const float a0 = t0, a1 = t1, a2 = t2;
+        t0 = G[0] * a0 + G[1] * a1 + G[2] * a2;
+        t1 = G[3] * a0 + G[4] * a1 + G[5] * a2;
+        t2 = G[6] * a0 + G[7] * a1 + G[8] * a2;
+        r00 = L[25];
+        r01 = L[26];
+        r02 = L[27];
+        r11 = L[28];
+        r12 = L[29];
+        r22 = L[30];
+    }
+    const float l2 = -t2 / r22;
+    const float l1 = (-t1 - r12 * l2) / r11;
+    const float l0 = (-t0 - r01 * l1 - r02 * l2) / r00;
+    dl[3 * j] = l0;
+    dl[3 * j + 1] = l1;
+    dl[3 * j + 2] = l2;
 }
 
 // One observation: the Gauss-Newton model term ||r + J_p dp + J_l dl||^2 at
@@ -227,8 +237,8 @@ void launch_backsub(Problem& p) {
     if (p.schur)
         launch_schur_backsub(p);
     else
-        k_backsub_dl<<<ceil_div(p.n_pt, BS_WARPS), 32 * BS_WARPS, 0, p.stream>>>(
-            p.n_pt, p.pt_off, p.obs_cam_s, p.tpool, p.x, p.dl, p.implicit ? p.lmrec : nullptr, p.lm_pos);
+        k_backsub_dl<<<ceil_div((int64_t)p.n_pt * BS_TEAM, 32 * BS_WARPS), 32 * BS_WARPS, 0, p.stream>>>(
+            p.n_pt, p.lm_by_k, p.pt_off, p.obs_cam_s, p.tpool, p.x, p.dl, p.implicit ? p.lmrec : nullptr);
     k_model_cost<<<p.red_grid, 256, 0, p.stream>>>(p.n_obs, p.frames, p.pts, p.obs_cam_s, p.obs_pt_s, p.obs_xy_s, p.x,
                                                    p.dl, nullptr, nullptr, p.partials, nullptr, (float)p.opt.huber_delta);
     k_sum_partials<<<1, 1024, 0, p.stream>>>(p.partials, p.red_grid, p.dsum + 1);
@@ -243,8 +253,8 @@ void launch_backsub_candidate_cost(Problem& p) {
     if (p.schur)
         launch_schur_backsub(p);
     else
-        k_backsub_dl<<<ceil_div(p.n_pt, BS_WARPS), 32 * BS_WARPS, 0, p.stream>>>(
-            p.n_pt, p.pt_off, p.obs_cam_s, p.tpool, p.x, p.dl, p.implicit ? p.lmrec : nullptr, p.lm_pos);
+        k_backsub_dl<<<ceil_div((int64_t)p.n_pt * BS_TEAM, 32 * BS_WARPS), 32 * BS_WARPS, 0, p.stream>>>(
+            p.n_pt, p.lm_by_k, p.pt_off, p.obs_cam_s, p.tpool, p.x, p.dl, p.implicit ? p.lmrec : nullptr);
     launch_candidate(p);
     if (p.batch.n_prob > 0) {
         BatchState& B = p.batch;

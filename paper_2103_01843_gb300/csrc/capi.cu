@@ -816,8 +816,8 @@ void create_problem(Problem& p, const double* cams, int32_t n_cam, const double*
         plan_implicit(p);
         p.ipool = dalloc<float>(p, 24 * n_obs);
         p.rpool = dalloc<float>(p, 2 * n_obs);
-        p.lmrec = dalloc<float>(p, 32 * (int64_t)n_pt);
-        BA_CUDA_TRY(cudaMemsetAsync(p.lmrec, 0, sizeof(float) * 32 * n_pt, p.stream));
+        p.lmrec = dalloc<float>(p, LM_REC * (int64_t)n_pt);
+        BA_CUDA_TRY(cudaMemsetAsync(p.lmrec, 0, sizeof(float) * LM_REC * (int64_t)n_pt, p.stream));
         p.tuned = true;  // the tile plans of the stored blocks do not apply
     } else {
         plan_matvec(p);

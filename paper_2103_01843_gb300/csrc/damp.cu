@@ -178,24 +178,26 @@ k_damp(int n_pt, const int32_t* __restrict__ pt_off, const int64_t* __restrict__
 // S = G_dt^T G_dt, G_tt and the damped R.  No undo is needed: every call
 // starts from the undamped R1.
 __global__ void __launch_bounds__(128)
-k_damp_implicit(int n_pt, const int32_t* __restrict__ lm_by_k, const int32_t* __restrict__ pt_off,
-                const float* __restrict__ tpool, const float* __restrict__ dl2, float* __restrict__ lmrec,
-                float sqrt_lambda, const float* __restrict__ lam_prob, const int32_t* __restrict__ lm_prob) {
+k_damp_implicit(int n_pt, float* __restrict__ lmrec, float sqrt_lambda, const int32_t* __restrict__ lm_by_k,
+                const float* __restrict__ lam_prob, const int32_t* __restrict__ lm_prob) {
     const int pos = blockIdx.x * blockDim.x + threadIdx.x;
     if (pos >= n_pt) return;
-    const int j = lm_by_k[pos];
-    const int s0 = pt_off[j], k = pt_off[j + 1] - s0, ncol = 9 * k;
-    const float* top = tpool + top_offset(s0, j);
-    float R[3][3], D[3][3], E[6][3];
+    float* L = lmrec + (int64_t)LM_REC * pos;
+    // R1 (upper) and D_l^2 from the landmark record (K1), 16-byte loads
+    const float4 q0 = *reinterpret_cast<const float4*>(L + 32), q1 = *reinterpret_cast<const float4*>(L + 36);
+    const float q2 = L[40];
+    float R[3][3] = {{q0.x, q0.y, q0.z}, {0.f, q0.w, q1.x}, {0.f, 0.f, q1.y}};
+    const float dl2[3] = {q1.z, q1.w, q2};
+    float D[3][3], E[6][3];
     for (int i = 0; i < 3; ++i)
         for (int c = 0; c < 3; ++c) {
-            R[i][c] = c >= i ? top[i * (ncol + 4) + ncol + c] : 0.f;
             D[i][c] = 0.f;
             E[i][c] = i == c ? 1.f : 0.f;
             E[3 + i][c] = 0.f;
         }
-    const float sl = lam_prob ? sqrtf(lam_prob[lm_prob[j]]) : sqrt_lambda;
-    for (int d = 0; d < 3; ++d) D[d][d] = sl * sqrtf(dl2[3 * j + d]);
+    const float sl = lam_prob ? sqrtf(lam_prob[lm_prob[lm_by_k[pos]]]) : sqrt_lambda;
+    for (int d = 0; d < 3; ++d) D[d][d] = sl * sqrtf(dl2[d]);
+#pragma unroll
     for (int m = 0; m < 6; ++m) {
         int c, d;
         givens_pair(m, c, d);
@@ -207,28 +209,34 @@ k_damp_implicit(int n_pt, const int32_t* __restrict__ lm_by_k, const int32_t* __
             cs = a * inv;
             sn = b * inv;
         }
-        for (int col = c; col < 3; ++col) {
+#pragma unroll
+        for (int col = 0; col < 3; ++col) {
+            if (col < c) continue;
             const float u = R[c][col], v = D[d][col];
             R[c][col] = cs * u + sn * v;
             D[d][col] = -sn * u + cs * v;
         }
         D[d][c] = 0.f;
+#pragma unroll
         for (int col = 0; col < 3; ++col) {
             const float u = E[c][col], v = E[3 + d][col];
             E[c][col] = cs * u + sn * v;
             E[3 + d][col] = -sn * u + cs * v;
         }
     }
-    float* L = lmrec + 32LL * pos;
-    // S = G_dt^T G_dt (upper: 00 01 02 11 12 22)
-    int q = 6;
+    // S = G_dt^T G_dt (upper: 00 01 02 11 12 22), G_tt, damped R (upper): 16-byte stores
+    float S[6];
+    int q = 0;
+#pragma unroll
     for (int u = 0; u < 3; ++u)
-        for (int v = u; v < 3; ++v) L[q++] = E[3][u] * E[3][v] + E[4][u] * E[4][v] + E[5][u] * E[5][v];
-    for (int i = 0; i < 3; ++i)
-        for (int c = 0; c < 3; ++c) L[16 + 3 * i + c] = E[i][c];
-    q = 25;
-    for (int i = 0; i < 3; ++i)
-        for (int c = i; c < 3; ++c) L[q++] = R[i][c];
+#pragma unroll
+        for (int v = u; v < 3; ++v) S[q++] = E[3][u] * E[3][v] + E[4][u] * E[4][v] + E[5][u] * E[5][v];
+    *reinterpret_cast<float2*>(L + 6) = make_float2(S[0], S[1]);
+    *reinterpret_cast<float4*>(L + 8) = make_float4(S[2], S[3], S[4], S[5]);
+    *reinterpret_cast<float4*>(L + 16) = make_float4(E[0][0], E[0][1], E[0][2], E[1][0]);
+    *reinterpret_cast<float4*>(L + 20) = make_float4(E[1][1], E[1][2], E[2][0], E[2][1]);
+    *reinterpret_cast<float4*>(L + 24) = make_float4(E[2][2], R[0][0], R[0][1], R[0][2]);
+    *reinterpret_cast<float4*>(L + 28) = make_float4(R[1][1], R[1][2], R[2][2], 0.f);
 }
 
 }  // namespace
@@ -240,9 +248,8 @@ void launch_damp(Problem& p, bool undo_old, float lambda) {
     }
     count_launches(p, 1);
     if (p.implicit) {
-        k_damp_implicit<<<ceil_div(p.n_pt, 128), 128, 0, p.stream>>>(p.n_pt, p.lm_by_k, p.pt_off, p.tpool, p.dl2,
-                                                                     p.lmrec, sqrtf(lambda), p.batch.lam,
-                                                                     p.batch.lm_prob);
+        k_damp_implicit<<<ceil_div(p.n_pt, 128), 128, 0, p.stream>>>(p.n_pt, p.lmrec, sqrtf(lambda), p.lm_by_k,
+                                                                     p.batch.lam, p.batch.lm_prob);
         BA_LAUNCH_CHECK();
         return;
     }

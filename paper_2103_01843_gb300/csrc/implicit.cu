@@ -95,7 +95,7 @@ struct LmFactors {
 };
 
 __device__ __forceinline__ LmFactors load_factors(const float* lmrec, int pos) {
-    const float4* p = reinterpret_cast<const float4*>(lmrec + 32LL * pos);
+    const float4* p = reinterpret_cast<const float4*>(lmrec + (int64_t)LM_REC * pos);
     const float4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
     return LmFactors{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
 }

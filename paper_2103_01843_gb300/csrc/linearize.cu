@@ -242,9 +242,17 @@ __device__ void marginalize_landmark(const LinArgs& A, int j, int pos, float* sm
         }
         T::sum3(d0, d1, d2, red);
         if (rank == 0 && write) {
-            A.dl2[3 * j] = fminf(fmaxf(d0, 1e-6f), 1e32f);
-            A.dl2[3 * j + 1] = fminf(fmaxf(d1, 1e-6f), 1e32f);
-            A.dl2[3 * j + 2] = fminf(fmaxf(d2, 1e-6f), 1e32f);
+            const float c0 = fminf(fmaxf(d0, 1e-6f), 1e32f), c1 = fminf(fmaxf(d1, 1e-6f), 1e32f),
+                        c2 = fminf(fmaxf(d2, 1e-6f), 1e32f);
+            A.dl2[3 * j] = c0;
+            A.dl2[3 * j + 1] = c1;
+            A.dl2[3 * j + 2] = c2;
+            if (A.lmrec) {  // implicit storage: K2 reads D_l^2 with R1 from the landmark record
+                float* Lr = A.lmrec + (int64_t)LM_REC * pos + 38;
+                Lr[0] = c0;
+                Lr[1] = c1;
+                Lr[2] = c2;
+            }
         }
     }
 
@@ -346,7 +354,7 @@ __device__ void marginalize_landmark(const LinArgs& A, int j, int pos, float* sm
         }
         if (rank == 0) {
             const float* Tm = misc + 5;
-            float* L = A.lmrec + 32LL * pos;
+            float* L = A.lmrec + (int64_t)LM_REC * pos;
             L[0] = Tm[0];
             L[1] = Tm[1];
             L[2] = Tm[2];
@@ -422,6 +430,19 @@ __device__ void marginalize_landmark(const LinArgs& A, int j, int pos, float* sm
             row[1] = ii <= 1 ? L[3 * ii + 1] : 0.f;
             row[2] = L[3 * ii + 2];
             row[3] = out;
+            if (implicit) {  // R1 (upper: 00 01 02 11 12 22) into the landmark record
+                float* Lr = A.lmrec + (int64_t)LM_REC * pos + 32;
+                if (ii == 0) {
+                    Lr[0] = L[0];
+                    Lr[1] = L[1];
+                    Lr[2] = L[2];
+                } else if (ii == 1) {
+                    Lr[3] = L[4];
+                    Lr[4] = L[5];
+                } else {
+                    Lr[5] = L[8];
+                }
+            }
         } else if (!implicit) {
             A.cpool[A.c_off[j] + (ii - 3)] = out;
         }

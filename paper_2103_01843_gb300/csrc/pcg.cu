@@ -155,7 +155,7 @@ k_precond_gram(const int32_t* __restrict__ chunk_cam, const int32_t* __restrict_
         }
         if (IMPLICIT) {
             // implicit storage: the top rows are undamped; the damped ones are G_tt times them
-            const float* G = lmrec + 32LL * lm_pos[j] + 16;
+            const float* G = lmrec + (int64_t)LM_REC * lm_pos[j] + 16;
             float Gm[9];
 #pragma unroll
             for (int q = 0; q < 9; ++q) Gm[q] = __ldg(G + q);
@@ -278,7 +278,7 @@ __device__ void exact_sums_warp_implicit(int cam, const int32_t* __restrict__ ca
         const int j = obs_pt_s[s];
         const int s0 = pt_off[j], k = pt_off[j + 1] - s0, qs = s - s0;
         const int64_t so0 = c_off[j] >> 1;
-        const float* L = lmrec + 32LL * lm_pos[j];
+        const float* L = lmrec + (int64_t)LM_REC * lm_pos[j];
         const float T00 = L[0], T01 = L[1], T02 = L[2], T11 = L[3], T12 = L[4], T22 = L[5];
         const float S[3][3] = {{L[6], L[7], L[8]}, {L[7], L[9], L[10]}, {L[8], L[10], L[11]}};
         float fq[24];

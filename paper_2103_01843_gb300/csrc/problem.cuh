@@ -157,9 +157,11 @@ struct Problem {
     // implicit storage (ba_options.implicit_blocks): per observation in storage
     // order 24 floats as 6 float4 chunks (chunk m of observation so at float4
     // index m n_obs + so): J_s rows (18) and Householder rows (6); residuals
-    // (2 per observation, storage order); per storage position 32 floats:
-    // Tm (6, upper: 00 01 02 11 12 22), S (6, same order), 4 pad, G_tt (9,
-    // row-major), damped R (6, upper), 1 pad; the top block stays undamped
+    // (2 per observation, storage order); per storage position LM_REC floats:
+    // [0..5] Tm (upper: 00 01 02 11 12 22), [6..11] S (same order), [16..24]
+    // G_tt (row-major), [25..30] damped R (upper) (written by K2), [32..37]
+    // undamped R1 (upper), [38..40] D_l^2 (written by K1); the top block stays
+    // undamped
     bool implicit = false;
     float *ipool = nullptr, *rpool = nullptr, *lmrec = nullptr;
     int32_t* lm_pos = nullptr;       // storage position of every landmark
@@ -301,6 +303,7 @@ bool matvec_y_in_smem(const Problem& p);  // the matvec plan in use accumulates 
 int matvec_stage_bytes();
 
 constexpr int PG_CHUNK = 256;  // observations per chunk of the Gram-form K3
+constexpr int LM_REC = 48;     // floats per landmark record of the implicit storage (16-byte aligned)
 
 // kernel launch counter (not counted while a graph is being captured)
 inline void count_launches(Problem& p, int n) {
