@@ -540,6 +540,7 @@ def run_batched(args):
         ev1.synchronize()
         step_ms.append(ev0.elapsed_time(ev1))
         per_problem_ms += [r["solve_ms"] for r in reps]
+        iter_active, iter_ms = b.iterations()
         iters.append(summ["lm_iterations"])
         cgs.append(sum(r["cg_iters"] for r in reps))
         finals = [r["final_cost"] for r in reps]
@@ -622,6 +623,7 @@ def run_batched(args):
                              "too",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "per_problem_ms": {"p50": percentile(per_problem_ms, 50), "p99": percentile(per_problem_ms, 99)},
+            "iterations": {"active_problems": iter_active, "ms": [round(t, 3) for t in iter_ms]},
             "batch_lm_iters_per_step": statistics.mean(iters), "pcg_iters_per_step": statistics.mean(cgs),
             "roofline": roofline, "kernels": kernels, "gpu_launches": launches_timed,
             "kernel_table": f"per-kernel times from {prof_steps} further steps with event profiling",

@@ -424,6 +424,15 @@ SQRTBA_API ba_status ba_batch_set_profiling(ba_batch* b, int32_t enable);
 SQRTBA_API ba_status ba_batch_get_profile(ba_batch* b, ba_profile* out);
 SQRTBA_API ba_status ba_batch_get_info(ba_batch* b, ba_info* info);
 
+/* Per batch LM iteration of the last ba_batch_solve: the number of problems
+ * still iterating when it started (active) and its duration in ms (CUDA events
+ * on the batch's stream).  A stopped problem costs nothing in K2, K3, K6, the
+ * cost passes and the implicit matvec, and a problem whose last step was
+ * rejected is not re-linearised (K2 undoes and redoes its damping), so the
+ * durations follow the active counts.  Writes min(cap, *n) entries; *n gets the
+ * number of iterations.  Any array may be NULL. */
+SQRTBA_API ba_status ba_batch_iterations(ba_batch* b, int32_t cap, int32_t* active, float* ms, int32_t* n);
+
 /* Like ba_last_error for a batch (b = NULL: the last ba_batch_create failure). */
 SQRTBA_API const char* ba_batch_last_error(const ba_batch* b);
 

@@ -158,6 +158,7 @@ _SIGS = {
     "ba_batch_set_profiling": [_P, ctypes.c_int32],
     "ba_batch_get_profile": [_P, ctypes.POINTER(Profile)],
     "ba_batch_get_info": [_P, ctypes.POINTER(Info)],
+    "ba_batch_iterations": [_P, ctypes.c_int32, _i32, _f, _i32],
     "ba_mlp_create": [_f, _P, ctypes.POINTER(_P)],
     "ba_mlp_destroy": [_P],
     "ba_mlp_get_params": [_P, _f],
@@ -533,6 +534,16 @@ class Batch:
         i = Info()
         self._check(lib().ba_batch_get_info(self.h, ctypes.byref(i)))
         return _struct_dict(i)
+
+    def iterations(self):
+        """(active problems at the start, ms) of each LM iteration of the last solve."""
+        n = ctypes.c_int32()
+        self._check(lib().ba_batch_iterations(self.h, 0, None, None, ctypes.byref(n)))
+        m = n.value
+        act = np.zeros(max(m, 1), np.int32)
+        ms = np.zeros(max(m, 1), np.float32)
+        self._check(lib().ba_batch_iterations(self.h, m, _ptr(act, _i32), _ptr(ms, _f), ctypes.byref(n)))
+        return act[:m].tolist(), ms[:m].tolist()
 
     def get_params(self, i):
         nc, npt, _ = self.sizes[i]

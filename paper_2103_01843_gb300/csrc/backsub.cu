@@ -29,11 +29,13 @@ constexpr int BS_TEAM = 8;
 __global__ void __launch_bounds__(32 * BS_WARPS)
 k_backsub_dl(int n_pt, const int32_t* __restrict__ lm_by_k, const int32_t* __restrict__ pt_off,
              const int32_t* __restrict__ obs_cam_s, const float* __restrict__ tpool, const float* __restrict__ dp,
-             float* __restrict__ dl, const float* __restrict__ lmrec) {
+             float* __restrict__ dl, const float* __restrict__ lmrec, const BatchLm* __restrict__ blm,
+             const int32_t* __restrict__ lm_prob) {
     const int lane = threadIdx.x & 31, rank = lane & (BS_TEAM - 1);
     const int pos = (blockIdx.x * (32 * BS_WARPS) + threadIdx.x) / BS_TEAM;
-    const bool has = pos < n_pt;
+    bool has = pos < n_pt;
     const int j = has ? lm_by_k[pos] : 0;
+    if (has && blm && !batch_active(blm, lm_prob[j])) has = false;  // a stopped problem of a batch
     const int s0 = has ? pt_off[j] : 0, k = has ? pt_off[j + 1] - s0 : 0, ncol = 9 * k;
     const float* top = tpool + top_offset(s0, j);
     float t0 = 0.f, t1 = 0.f, t2 = 0.f;
@@ -152,9 +154,13 @@ k_model_cost_seg(const int64_t* __restrict__ prob_obs_off, const float* __restri
                  const int32_t* __restrict__ obs_pt_s, const float2* __restrict__ obs_xy_s,
                  const float* __restrict__ dp, const float* __restrict__ dl, const float* __restrict__ cand_frames,
                  const float* __restrict__ cand_pts, double* __restrict__ model, double* __restrict__ cost,
-                 float huber) {
+                 float huber, const BatchLm* __restrict__ blm) {
     __shared__ double red[32];
     const int b = blockIdx.x;
+    if (blm && !blm[b].active) {  // a stopped problem: its sums are not read
+        if (threadIdx.x == 0) model[b] = cost[b] = 0.0;
+        return;
+    }
     double m = 0.0, c = 0.0;
     for (int64_t s = prob_obs_off[b] + threadIdx.x; s < prob_obs_off[b + 1]; s += blockDim.x)
         model_cost_obs(s, frames, pts, obs_cam_s, obs_pt_s, obs_xy_s, dp, dl, cand_frames, cand_pts, huber, m, c);
@@ -238,7 +244,8 @@ void launch_backsub(Problem& p) {
         launch_schur_backsub(p);
     else
         k_backsub_dl<<<ceil_div((int64_t)p.n_pt * BS_TEAM, 32 * BS_WARPS), 32 * BS_WARPS, 0, p.stream>>>(
-            p.n_pt, p.lm_by_k, p.pt_off, p.obs_cam_s, p.tpool, p.x, p.dl, p.implicit ? p.lmrec : nullptr);
+            p.n_pt, p.lm_by_k, p.pt_off, p.obs_cam_s, p.tpool, p.x, p.dl, p.implicit ? p.lmrec : nullptr,
+            p.batch.n_prob > 0 ? p.batch.lm : nullptr, p.batch.lm_prob);
     k_model_cost<<<p.red_grid, 256, 0, p.stream>>>(p.n_obs, p.frames, p.pts, p.obs_cam_s, p.obs_pt_s, p.obs_xy_s, p.x,
                                                    p.dl, nullptr, nullptr, p.partials, nullptr, (float)p.opt.huber_delta);
     k_sum_partials<<<1, 1024, 0, p.stream>>>(p.partials, p.red_grid, p.dsum + 1);
@@ -254,13 +261,14 @@ void launch_backsub_candidate_cost(Problem& p) {
         launch_schur_backsub(p);
     else
         k_backsub_dl<<<ceil_div((int64_t)p.n_pt * BS_TEAM, 32 * BS_WARPS), 32 * BS_WARPS, 0, p.stream>>>(
-            p.n_pt, p.lm_by_k, p.pt_off, p.obs_cam_s, p.tpool, p.x, p.dl, p.implicit ? p.lmrec : nullptr);
+            p.n_pt, p.lm_by_k, p.pt_off, p.obs_cam_s, p.tpool, p.x, p.dl, p.implicit ? p.lmrec : nullptr,
+            p.batch.n_prob > 0 ? p.batch.lm : nullptr, p.batch.lm_prob);
     launch_candidate(p);
     if (p.batch.n_prob > 0) {
         BatchState& B = p.batch;
         k_model_cost_seg<<<B.n_prob, 256, 0, p.stream>>>(B.prob_obs_off, p.frames, p.pts, p.obs_cam_s, p.obs_pt_s,
                                                          p.obs_xy_s, p.x, p.dl, p.cand_frames, p.cand_pts, B.cost_b,
-                                                         B.cost_a, (float)p.opt.huber_delta);
+                                                         B.cost_a, (float)p.opt.huber_delta, B.lm);
     } else {
         k_model_cost<<<p.red_grid, 256, 0, p.stream>>>(p.n_obs, p.frames, p.pts, p.obs_cam_s, p.obs_pt_s, p.obs_xy_s,
                                                        p.x, p.dl, p.cand_frames, p.cand_pts, p.partials,

@@ -968,10 +968,12 @@ void do_batch_solve(Problem& p, ba_batch_report* reps, ba_batch_summary* sum) {
     int n_it = 0;
     launch_batch_cost(p, false, B.cost_a);
     launch_batch_start(p);  // lambda0 for every problem
+    B.iter_active.assign(1, B.n_prob);
     for (int it = 0; it < max_it; ++it) {
-        // K1 for every problem (a problem whose last step was rejected
-        // recomputes the blocks of its unchanged state), then K2 with each
-        // problem's damping
+        // K1 for the problems that moved (the first iteration: all; a problem
+        // whose last step was rejected keeps its blocks, a stopped one does
+        // nothing), then K2 with each problem's damping (undoing the old one
+        // where the blocks were kept)
         PhaseTimer tl(p, PROF_LINEARIZE);
         launch_frames(p);
         launch_linearize(p);
@@ -997,7 +999,11 @@ void do_batch_solve(Problem& p, ba_batch_report* reps, ba_batch_summary* sum) {
         sync(p);
         n_it = it + 1;
         if (*B.n_active_host == 0) break;
+        B.iter_active.push_back(*B.n_active_host);
     }
+    B.iter_ms.assign(n_it, 0.f);
+    for (int i = 0; i < n_it; ++i)
+        BA_CUDA_TRY(cudaEventElapsedTime(&B.iter_ms[i], B.iter_events[i], B.iter_events[i + 1]));
     p.linearized = p.damped = p.solved = p.backsubbed = false;
     std::vector<BatchLm> lm(B.n_prob);
     d2h(p, lm.data(), B.lm, B.n_prob);
@@ -1551,6 +1557,18 @@ ba_status ba_batch_get_profile(ba_batch* b, ba_profile* out) {
     get_profile_impl(b->p, out);
     return BA_OK;
     BATCH_CATCH(b)
+}
+
+ba_status ba_batch_iterations(ba_batch* b, int32_t cap, int32_t* active, float* ms, int32_t* n) {
+    if (!b || !n || cap < 0) return BA_ERR_INVALID_ARG;
+    const BatchState& B = b->p.batch;
+    const int m = (int)B.iter_ms.size();
+    *n = m;
+    for (int i = 0; i < std::min(m, (int)cap); ++i) {
+        if (active) active[i] = i < (int)B.iter_active.size() ? B.iter_active[i] : 0;
+        if (ms) ms[i] = B.iter_ms[i];
+    }
+    return BA_OK;
 }
 
 ba_status ba_batch_get_info(ba_batch* b, ba_info* info) {

@@ -33,14 +33,21 @@ __global__ void __launch_bounds__(DT)
 k_damp(int n_pt, const int32_t* __restrict__ pt_off, const int64_t* __restrict__ a_off,
        const int32_t* __restrict__ c_off, float* __restrict__ tpool, float* __restrict__ apool,
        float* __restrict__ cpool, const float* __restrict__ dl2, float* __restrict__ rot, float sqrt_lambda,
-       const float* __restrict__ lam_prob, const int32_t* __restrict__ lm_prob, int undo) {
+       const float* __restrict__ lam_prob, const int32_t* __restrict__ lm_prob, int undo_all,
+       const BatchLm* __restrict__ blm) {
     __shared__ float s_rot[DB][24];  // old (12) and new (12) rotations
-    __shared__ int s_k[DB];
+    __shared__ int s_k[DB];          // k, or -1: a stopped problem's landmark (skipped)
+    __shared__ int s_undo[DB];
     __shared__ int64_t s_top[DB], s_damp[DB];
     __shared__ int s_cd[DB];
     const int tid = threadIdx.x;
     const int j = blockIdx.x * DB + tid;
-    if (tid < DB && j < n_pt) {
+    if (tid < DB && j < n_pt && blm && !batch_active(blm, lm_prob[j])) {
+        s_k[tid] = -1;
+    } else if (tid < DB && j < n_pt) {
+        // a batch undoes the damping of the problems that kept their linearisation
+        const int undo = blm ? (batch_relin(blm, lm_prob[j]) ? 0 : 1) : undo_all;
+        s_undo[tid] = undo;
         const int s0 = pt_off[j], k = pt_off[j + 1] - s0;
         const int ncol = 9 * k, nr = 2 * k;
         const int64_t toff = top_offset(s0, j);
@@ -108,6 +115,8 @@ k_damp(int n_pt, const int32_t* __restrict__ pt_off, const int64_t* __restrict__
     const int lane = tid & 31, w = tid >> 5;
     for (int l = w; l < DB; l += DT / 32) {
         if (blockIdx.x * DB + l >= n_pt) break;
+        if (s_k[l] < 0) continue;
+        const int undo = s_undo[l];
         const int ncol = 9 * s_k[l];
         float* __restrict__ top = tpool + s_top[l];
         float* __restrict__ dmp = apool + s_damp[l];
@@ -179,9 +188,11 @@ k_damp(int n_pt, const int32_t* __restrict__ pt_off, const int64_t* __restrict__
 // starts from the undamped R1.
 __global__ void __launch_bounds__(128)
 k_damp_implicit(int n_pt, float* __restrict__ lmrec, float sqrt_lambda, const int32_t* __restrict__ lm_by_k,
-                const float* __restrict__ lam_prob, const int32_t* __restrict__ lm_prob) {
+                const float* __restrict__ lam_prob, const int32_t* __restrict__ lm_prob,
+                const BatchLm* __restrict__ blm) {
     const int pos = blockIdx.x * blockDim.x + threadIdx.x;
     if (pos >= n_pt) return;
+    if (blm && !batch_active(blm, lm_prob[lm_by_k[pos]])) return;
     float* L = lmrec + (int64_t)LM_REC * pos;
     // R1 (upper) and D_l^2 from the landmark record (K1), 16-byte loads
     const float4 q0 = *reinterpret_cast<const float4*>(L + 32), q1 = *reinterpret_cast<const float4*>(L + 36);
@@ -248,14 +259,15 @@ void launch_damp(Problem& p, bool undo_old, float lambda) {
     }
     count_launches(p, 1);
     if (p.implicit) {
-        k_damp_implicit<<<ceil_div(p.n_pt, 128), 128, 0, p.stream>>>(p.n_pt, p.lmrec, sqrtf(lambda), p.lm_by_k,
-                                                                     p.batch.lam, p.batch.lm_prob);
+        k_damp_implicit<<<ceil_div(p.n_pt, 128), 128, 0, p.stream>>>(
+            p.n_pt, p.lmrec, sqrtf(lambda), p.lm_by_k, p.batch.lam, p.batch.lm_prob,
+            p.batch.n_prob > 0 ? p.batch.lm : nullptr);
         BA_LAUNCH_CHECK();
         return;
     }
     k_damp<<<ceil_div(p.n_pt, DB), DT, 0, p.stream>>>(p.n_pt, p.pt_off, p.a_off, p.c_off, p.tpool, p.apool, p.cpool,
                                                       p.dl2, p.rot, sqrtf(lambda), p.batch.lam, p.batch.lm_prob,
-                                                      undo_old ? 1 : 0);
+                                                      undo_old ? 1 : 0, p.batch.n_prob > 0 ? p.batch.lm : nullptr);
     BA_LAUNCH_CHECK();
 }
 

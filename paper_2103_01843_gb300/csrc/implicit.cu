@@ -56,6 +56,9 @@ struct ImArgs {
     float* y;
     int n_cam;
     const PcgScalars* S;
+    const BatchLm* blm;      // batch: per-problem LM state (null for a single problem)
+    const int32_t* lm_prob;  // batch: problem of every landmark
+    const int32_t* lm_by_k;  // landmark at every storage position
 };
 
 __host__ __device__ constexpr int team_width(int k) { return k <= 2 ? 2 : (k <= 4 ? 4 : (k <= 8 ? 8 : (k <= 16 ? 16 : 32))); }
@@ -115,7 +118,8 @@ __device__ void small_task(const ImArgs& a, const ImTask& tk, float* yt, int lan
     const int team = lane / W, t = lane - team * W, base = team * W;
     const int k = tk.k;
     const bool has = team < tk.n;
-    const bool act = has && t < k;
+    // a stopped problem of a batch contributes nothing (its CG has stopped)
+    const bool act = has && t < k && (!a.blm || batch_active(a.blm, a.lm_prob[a.lm_by_k[tk.pos0 + team]]));
     ObsRec r;
     float vv[9];
     int cam = 0;
@@ -172,6 +176,7 @@ __device__ void small_task(const ImArgs& a, const ImTask& tk, float* yt, int lan
 // k > 32: one warp, lanes over the observations in chunks of 32
 __device__ void big_task(const ImArgs& a, const ImTask& tk, float* yt, int lane) {
     const int k = tk.k;
+    if (a.blm && !batch_active(a.blm, a.lm_prob[a.lm_by_k[tk.pos0]])) return;  // whole warp
     const LmFactors F = load_factors(a.lmrec, tk.pos0);
     auto load = [&](int t, ObsRec& r, float (&vv)[9], int& cam) {
         const int64_t so = (int64_t)tk.so0 + t;
@@ -347,7 +352,8 @@ void configure_implicit(Problem&) {
 
 void launch_matvec_implicit(Problem& p, const float* v, float* y, const PcgScalars* S) {
     const ImArgs a{static_cast<const ImTask*>(p.im_tasks), p.im_ntasks, reinterpret_cast<const float4*>(p.ipool),
-                   p.n_obs, p.lmrec, p.mv_cam, v, y, p.n_cam, S};
+                   p.n_obs, p.lmrec, p.mv_cam, v, y, p.n_cam, S,
+                   p.batch.n_prob > 0 ? p.batch.lm : nullptr, p.batch.lm_prob, p.lm_by_k};
     const int grid = p.sm_count * 2;
     if (implicit_smem_y(p))
         k_matvec_implicit<true><<<grid, IM_THREADS, 36 * (size_t)p.n_cam, p.stream>>>(a);

@@ -109,6 +109,8 @@ struct LinArgs {
     float* lmrec;
     int64_t n_obs;
     float huber;  // Huber parameter (<= 0: squared norm)
+    const BatchLm* blm;      // batch: per-problem LM state (null for a single problem)
+    const int32_t* lm_prob;  // batch: problem of every landmark
 };
 
 // Q^T J_p rows of a landmark with K observations, lanes over the columns
@@ -459,7 +461,9 @@ k_linearize_team(LinArgs A, const int32_t* __restrict__ order, int first, int co
     const int idx0 = (blockIdx.x * LIN_WARPS + w) * TPW;
     if (idx0 >= count) return;  // whole warp
     const int idx = idx0 + tm;
-    const bool active = idx < count;
+    // a batch re-linearises only the problems whose last step was accepted
+    const bool active = idx < count && (!A.blm || batch_relin(A.blm, A.lm_prob[order[first + idx]]));
+    if (!__any_sync(0xffffffffu, active)) return;  // whole warp
     float* sm = smem + (w * TPW + tm) * lin_smem_floats(KMAX);
     const int pos = first + (active ? idx : idx0);
     marginalize_landmark<W, (9 * KMAX + W - 1) / W>(A, order[pos], pos, sm, nullptr, active);
@@ -470,6 +474,7 @@ k_linearize_block(LinArgs A, const int32_t* __restrict__ order, int count) {
     extern __shared__ float smem[];
     __shared__ float red[3 * (BIG_TEAM / 32)];
     if ((int)blockIdx.x >= count) return;
+    if (A.blm && !batch_relin(A.blm, A.lm_prob[order[blockIdx.x]])) return;
     marginalize_landmark<BIG_TEAM>(A, order[blockIdx.x], blockIdx.x, smem, red);
 }
 
@@ -481,9 +486,11 @@ __global__ void __launch_bounds__(CD_THREADS)
 k_camera_diag(int n_cam, const float* __restrict__ frames, const float* __restrict__ pts,
               const int32_t* __restrict__ obs_pt_s, const float2* __restrict__ obs_xy_s,
               const int32_t* __restrict__ cam_off, const int32_t* __restrict__ cam_list,
-              float* __restrict__ dp2, float huber) {
+              float* __restrict__ dp2, float huber, const BatchLm* __restrict__ blm,
+              const int32_t* __restrict__ cam_prob) {
     __shared__ float part[CD_THREADS / 32][9];
     const int cam = blockIdx.x;
+    if (blm && !batch_relin(blm, cam_prob[cam])) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float acc[9];
 #pragma unroll
@@ -579,14 +586,16 @@ void launch_linearize(Problem& p) {
         return;
     }
     LinArgs A{p.frames, p.pts, p.obs_cam_s, p.obs_xy_s, p.pt_off, p.a_off, p.apool, p.tpool, p.cpool, p.c_off,
-              p.dl2, p.implicit ? p.ipool : nullptr, p.rpool, p.lmrec, p.n_obs, (float)p.opt.huber_delta};
+              p.dl2, p.implicit ? p.ipool : nullptr, p.rpool, p.lmrec, p.n_obs, (float)p.opt.huber_delta,
+              p.batch.n_prob > 0 ? p.batch.lm : nullptr, p.batch.lm_prob};
     // segments of lm_by_k: k > 32 | 9..32 | 5..8 | 2..4
     const int n_big = p.n_big, n32 = count_k(p, 8, 32), n16 = count_k(p, 4, 8), n8 = count_k(p, 1, 4);
     BA_CUDA_TRY(cudaEventRecord(p.ev_fork, p.stream));
     BA_CUDA_TRY(cudaStreamWaitEvent(p.side, p.ev_fork, 0));
     // side: D_p^2, then the landmarks with k > 32 (one CTA each)
     k_camera_diag<<<p.n_cam, CD_THREADS, 0, p.side>>>(p.n_cam, p.frames, p.pts, p.obs_pt_s, p.obs_xy_s, p.cam_off,
-                                                      p.cam_list, p.dp2, (float)p.opt.huber_delta);
+                                                      p.cam_list, p.dp2, (float)p.opt.huber_delta,
+                                                      p.batch.n_prob > 0 ? p.batch.lm : nullptr, p.batch.cam_prob);
     count_launches(p, 1);
     if (n_big > 0) {
         const size_t sm = sizeof(float) * lin_smem_floats(p.k_max);
@@ -619,7 +628,9 @@ void launch_linearize(Problem& p) {
 void launch_camera_diag(Problem& p) {
     count_launches(p, 1);
     k_camera_diag<<<p.n_cam, CD_THREADS, 0, p.stream>>>(p.n_cam, p.frames, p.pts, p.obs_pt_s, p.obs_xy_s, p.cam_off,
-                                                        p.cam_list, p.dp2, (float)p.opt.huber_delta);
+                                                        p.cam_list, p.dp2, (float)p.opt.huber_delta,
+                                                        p.batch.n_prob > 0 ? p.batch.lm : nullptr,
+                                                        p.batch.cam_prob);
     BA_LAUNCH_CHECK();
 }
 

@@ -115,9 +115,11 @@ k_precond_gram(const int32_t* __restrict__ chunk_cam, const int32_t* __restrict_
                const int32_t* __restrict__ obs_pt_s, const float2* __restrict__ obs_xy_s,
                const int32_t* __restrict__ pt_off, const float* __restrict__ frames, const float* __restrict__ pts,
                const float* __restrict__ tpool, float* __restrict__ part_out, const float* __restrict__ lmrec,
-               const int32_t* __restrict__ lm_pos, float huber) {
+               const int32_t* __restrict__ lm_pos, float huber, const BatchLm* __restrict__ blm,
+               const int32_t* __restrict__ cam_prob) {
     __shared__ float part[PG_T / 32][REC_SUMS + 1];
     const int ch = blockIdx.x, cam = chunk_cam[ch];
+    if (blm && !batch_active(blm, cam_prob[cam])) return;  // a stopped problem of a batch
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int e0 = cam_off[cam] + (ch - chunk_off[cam]) * PG_CHUNK;
     const int e1 = min(cam_off[cam + 1], e0 + PG_CHUNK);
@@ -386,9 +388,10 @@ k_precond_gram_finish(const int32_t* __restrict__ chunk_off, const float* __rest
                       const int32_t* __restrict__ c_off, const float* __restrict__ apool,
                       const float* __restrict__ cpool, const int32_t* __restrict__ lm_pos,
                       const float4* __restrict__ ipool, int64_t n_obs, const float* __restrict__ rpool,
-                      const float* __restrict__ lmrec, int force_exact) {
+                      const float* __restrict__ lmrec, int force_exact, const BatchLm* __restrict__ blm) {
     __shared__ float tot[56], sM[81], sL[81];
     const int cam = blockIdx.x, lane = threadIdx.x;
+    if (blm && !batch_active(blm, cam_prob[cam])) return;  // a stopped problem of a batch
     for (int q = lane; q <= REC_SUMS; q += 32) {
         float v = 0.f;
         for (int c = chunk_off[cam]; c < chunk_off[cam + 1]; ++c) v += part[56LL * c + q];
@@ -682,12 +685,13 @@ void launch_precond_rhs(Problem& p) {
         if (p.pg_chunks > 0)
             (p.implicit ? k_precond_gram<true> : k_precond_gram<false>)<<<p.pg_chunks, PG_T, 0, p.stream>>>(
                 p.pg_chunk_cam, p.pg_chunk_off, p.cam_off, p.cam_list, p.obs_pt_s, p.obs_xy_s, p.pt_off, p.frames,
-                p.pts, p.tpool, p.pg_part, lmrec, p.lm_pos, (float)p.opt.huber_delta);
+                p.pts, p.tpool, p.pg_part, lmrec, p.lm_pos, (float)p.opt.huber_delta,
+                p.batch.n_prob > 0 ? p.batch.lm : nullptr, p.batch.cam_prob);
         k_precond_gram_finish<<<p.n_cam, 32, 0, p.stream>>>(
             p.pg_chunk_off, p.pg_part, p.dp2, (float)p.lambda_damped, p.batch.lam, p.batch.cam_prob, p.mdiag, p.minv,
             p.g, p.err, p.cam_off, p.cam_list, p.obs_pt_s, p.pt_off, p.a_off, p.c_off, p.apool, p.cpool, p.lm_pos,
             reinterpret_cast<const float4*>(p.ipool), p.n_obs, p.rpool, lmrec,
-            p.implicit && p.opt.precond_from_blocks ? 1 : 0);
+            p.implicit && p.opt.precond_from_blocks ? 1 : 0, p.batch.n_prob > 0 ? p.batch.lm : nullptr);
         BA_LAUNCH_CHECK();
         return;
     }

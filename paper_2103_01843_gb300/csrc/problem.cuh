@@ -64,6 +64,14 @@ struct BatchLm {
     int32_t pad;
 };
 
+// Work of a batch iteration per problem (null blm: a single problem, all work):
+// a problem that has stopped does nothing; one whose last step was rejected
+// keeps its linearisation (K1 skipped, K2 undoes and redoes its damping).
+__device__ __forceinline__ bool batch_active(const BatchLm* blm, int b) { return !blm || blm[b].active; }
+__device__ __forceinline__ bool batch_relin(const BatchLm* blm, int b) {
+    return !blm || (blm[b].active && (blm[b].iter == 0 || blm[b].last_acc));
+}
+
 // Index spaces of a batch of independent problems concatenated into one
 // problem (cameras, landmarks and observations of problem b are contiguous).
 struct BatchState {
@@ -81,6 +89,8 @@ struct BatchState {
     std::vector<int32_t> h_cam_off, h_lm_off;
     std::vector<int64_t> h_obs_off;
     std::vector<cudaEvent_t> iter_events;  // one per batch LM iteration (+ start)
+    std::vector<int32_t> iter_active;      // problems iterating at the start of each batch LM iteration
+    std::vector<float> iter_ms;            // duration of each batch LM iteration (events)
 };
 
 // Optional timing of the phases of the hot path with CUDA events.

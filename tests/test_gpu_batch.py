@@ -132,3 +132,28 @@ def test_autotune_single_problem(pkg, members):
         q.marginalize_qr(1e-4)
         y0 = q.matvec(v)
     assert np.linalg.norm(y1 - y0) <= 1e-5 * np.linalg.norm(y0)
+
+
+@pytest.mark.parametrize("implicit", [0, 1])
+def test_stopped_problems_cost_nothing(pkg, implicit):
+    """Problems that have stopped are skipped and rejected steps keep their
+    linearisation: the results still match the oracle per problem, and the
+    late batch iterations, with few problems left, take less time than the
+    first, with all of them."""
+    scenes = [make_scene("batched_member", s) for s in range(16)]
+    iters = 30
+    with pkg.Batch(scenes, max_lm_iters=iters, implicit_blocks=implicit) as b:
+        b.solve()  # warm-up (graphs, pools)
+        b.restart()
+        reps, summ = b.solve()
+        active, ms = b.iterations()
+    assert len(active) == len(ms) == summ["lm_iterations"]
+    assert active[0] == len(scenes)
+    assert all(a >= c for a, c in zip(active, active[1:]))
+    assert abs(sum(ms) - summ["total_ms"]) <= 0.05 * summ["total_ms"] + 0.5
+    late = [t for a, t in zip(active, ms) if a <= len(scenes) // 4]
+    if late:
+        assert np.median(late) < 0.8 * ms[0], (active, ms)
+    for s, r in zip(scenes[:6], reps[:6]):
+        ref, _ = _oracle_final(s, iters)
+        assert abs(r["final_cost"] - ref) <= 1e-3 * ref, (r, ref)
