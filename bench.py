@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--learned-train", type=int, default=32)
     ap.add_argument("--learned-eval", type=int, default=8)
     ap.add_argument("--learned-steps", type=int, default=3000)
+    ap.add_argument("--learned-scene", default="walk", choices=["walk", "medium"],
+                    help="learned: walk scenes of 100 cameras (quick) or the medium shape (500 cameras, 100k "
+                         "landmarks; the configured experiment: --learned-train 2000 --learned-eval 50)")
     ap.add_argument("--mode", default="solve", choices=["solve", "matvec", "kernels", "mlp", "kdeg"],
                     help="kernel-profiling runs that print no bench line: matvec repeats the PCG "
                          "matvec on a linearised, damped problem; kernels runs every kernel of one "
@@ -267,8 +270,8 @@ def run_reference(args):
 # our arm
 # ---------------------------------------------------------------------------
 def kernel_bytes(implicit, info):
-    """Algorithmic bytes per launch of K1, K3 and K4 (the byte models of the
-    measurement section of the design doc restated: what each launch must move)."""
+    """Algorithmic bytes per launch of K1, K3 and K4: what each launch must
+    move, per observation, landmark and camera."""
     sum_k2 = info["sum_k2"]
     n_obs, n_pt, n_cam = info["n_obs"], info["n_pt"], info["n_cam"]
     if implicit:
@@ -735,37 +738,63 @@ def run_explicit32(args):
 LEARNED_METRIC = "PCG iters learned vs plain"
 
 
+def _learned_scene(args_tuple):
+    """Worker of the scene pool (numpy only): one seeded training or
+    evaluation scene of the learned experiment."""
+    kind, seed = args_tuple
+    from paper_2103_01843_gb300.synth import make_scene
+    return make_scene("medium", seed) if kind == "medium" else make_scene("walk", seed)
+
+
+def _scene_stream(kind, seeds, procs):
+    """Seeded scenes in order, generated by a pool of `procs` processes
+    (started with spawn: this process already uses the GPU)."""
+    if procs <= 1:
+        for sd in seeds:
+            yield _learned_scene((kind, sd))
+        return
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        for sc in pool.imap(_learned_scene, [(kind, sd) for sd in seeds], chunksize=2):
+            yield sc
+
+
 def run_learned(args):
     import numpy as np
     import torch
     torch.cuda.set_device(0)
     import paper_2103_01843_gb300 as sq
     from paper_2103_01843_gb300 import learned
-    from paper_2103_01843_gb300.synth import make_scene
     sq.lib()
-    n_train, n_eval = args.learned_train, args.learned_eval
+    n_train, n_eval, kind = args.learned_train, args.learned_eval, args.learned_scene
+    procs = min(16, os.cpu_count() or 1) if kind == "medium" else 1
     t0 = time.perf_counter()
-    samples = [learned.solver_samples(make_scene("walk", s)) for s in range(1000, 1000 + n_train)]
+    samples = [learned.solver_samples(sc) for sc in _scene_stream(kind, range(1000, 1000 + n_train), procs)]
     t_data = time.perf_counter() - t0
     t0 = time.perf_counter()
     model, losses = learned.train(samples, steps=args.learned_steps, lr=1e-3, seed=0)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    res = [learned.compare(make_scene("walk", s), model, repeats=max(1, args.steps))
-           for s in range(100000, 100000 + n_eval)]
+    n_samples = int(sum(x["g"].shape[0] for x in samples))
+    del samples
+    res = [learned.compare(sc, model, repeats=max(1, args.steps))
+           for sc in _scene_stream(kind, range(100000, 100000 + n_eval), procs)]
     def agg(name, key):
         return float(np.mean([r[name][key] for r in res]))
     pcg_p = agg("plain", "pcg_iters") / max(agg("plain", "lm_iters"), 1e-9)
     pcg_l = agg("learned", "pcg_iters") / max(agg("learned", "lm_iters"), 1e-9)
     rel_cost = max(abs(r["learned"]["final_cost"] - r["plain"]["final_cost"]) / r["plain"]["final_cost"] for r in res)
+    shape = ("medium (500 cams, 100000 landmarks, k = 2 + Geom0(0.2) capped at 64)" if kind == "medium"
+             else "medium-shaped walk (100 cams, 20000 landmarks)")
     line = {
         "metric": LEARNED_METRIC, "value": pcg_l / pcg_p, "unit": "ratio (PCG iterations per LM iteration)",
         "n_gpus": 1, "steps": args.steps, "warmup": 0, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16 MLP / f32 solver", "data": "synthetic",
-        "config": {"workload": f"learned: trained on {n_train} medium-shaped walk scenes (100 cams, 20000 "
-                               f"landmarks, seeds 1000..), evaluated on {n_eval} held-out seeds (100000..)",
-                   "train_samples": int(sum(x["g"].shape[0] for x in samples)), "train_steps": args.learned_steps,
-                   "data_gen_s": t_data, "train_s": t_train,
+        "config": {"workload": f"learned: trained on {n_train} {shape} scenes (seeds 1000..), evaluated on "
+                               f"{n_eval} held-out seeds (100000..)",
+                   "train_samples": n_samples, "train_steps": args.learned_steps,
+                   "data_gen_s": t_data, "train_s": t_train, "scene_procs": procs,
                    "loss_first": losses[0], "loss_last50": float(np.mean(losses[-50:]))},
         "pcg_iters_per_lm_iter": {"plain": pcg_p, "learned": pcg_l},
         "time_to_tol_s": {"plain": agg("plain", "seconds"), "learned": agg("learned", "seconds")},

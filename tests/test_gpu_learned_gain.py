@@ -1,4 +1,8 @@
-"""What the trained network gains over the method without it.
+"""The trained network against the method without it (a small-scale check:
+12 training and 2 held-out walk scenes of 60 cameras; the configured
+experiment - 2000 medium-shaped training scenes, 50 held out - is
+`bench.py --config learned --learned-scene medium --learned-train 2000
+--learned-eval 50`).
 
 The model is trained on the GPU with the library's own kernels on data the
 solver generates (medium-shaped walk scenes, one tight solve per LM iteration
@@ -12,9 +16,11 @@ block Jacobi with the block-Jacobi solution as warm start):
     (the warm start costs one);
   * the held-out loss of the trained and the untrained model and both
     solvers' iteration counts and times are printed (pytest -s) for the
-    record: on these scenes the loss gain is within the run-to-run noise
-    (about +-3 %; the per-camera features carry little of the inter-camera
-    coupling that decides x*), so it is reported, not asserted."""
+    record.  No gain in the held-out loss or in wall time is asserted: none
+    was measured (the loss gain is within the run-to-run noise, about +-3 %,
+    the per-camera features carry little of the inter-camera coupling that
+    decides x*, and the network and the warm start's extra product cost more
+    than the PCG iteration they save)."""
 import json
 
 import numpy as np
@@ -52,7 +58,7 @@ def _held_loss(pkg, learned, torch, model, samples):
     return model.loss_grad(f, a, with_grads=False)[0]
 
 
-def test_trained_network_gain(env):
+def test_trained_network_is_stable_and_no_worse(env):
     pkg, learned, torch = env
     train = [learned.solver_samples(_scene(s)) for s in range(2000, 2012)]
     held = [learned.solver_samples(_scene(s)) for s in range(200000, 200002)]
