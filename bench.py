@@ -773,7 +773,11 @@ def run_learned(args):
     samples = [learned.solver_samples(sc) for sc in _scene_stream(kind, range(1000, 1000 + n_train), procs)]
     t_data = time.perf_counter() - t0
     t0 = time.perf_counter()
-    model, losses = learned.train(samples, steps=args.learned_steps, lr=1e-3, seed=0)
+    kept = {}
+    if n_train > 0:
+        model, losses = learned.train(samples, steps=args.learned_steps, lr=1e-3, seed=0, stats=kept)
+    else:  # the untrained model: zero output layer, i.e. block Jacobi warm-started at M^-1 g
+        model, losses = sq.Mlp(learned.init_params(0)), []
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     n_samples = int(sum(x["g"].shape[0] for x in samples))
@@ -791,11 +795,13 @@ def run_learned(args):
         "metric": LEARNED_METRIC, "value": pcg_l / pcg_p, "unit": "ratio (PCG iterations per LM iteration)",
         "n_gpus": 1, "steps": args.steps, "warmup": 0, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16 MLP / f32 solver", "data": "synthetic",
-        "config": {"workload": f"learned: trained on {n_train} {shape} scenes (seeds 1000..), evaluated on "
-                               f"{n_eval} held-out seeds (100000..)",
-                   "train_samples": n_samples, "train_steps": args.learned_steps,
+        "config": {"workload": (f"learned: trained on {n_train} {shape} scenes (seeds 1000..)" if n_train > 0
+                                else f"learned, untrained model (block-Jacobi warm start), {shape} scenes")
+                               + f", evaluated on {n_eval} held-out seeds (100000..)",
+                   "train_samples": n_samples, "sample_filter": kept, "train_steps": args.learned_steps,
                    "data_gen_s": t_data, "train_s": t_train, "scene_procs": procs,
-                   "loss_first": losses[0], "loss_last50": float(np.mean(losses[-50:]))},
+                   "loss_first": losses[0] if n_train > 0 else None,
+                   "loss_last50": float(np.mean(losses[-50:])) if n_train > 0 else None},
         "pcg_iters_per_lm_iter": {"plain": pcg_p, "learned": pcg_l},
         "time_to_tol_s": {"plain": agg("plain", "seconds"), "learned": agg("learned", "seconds")},
         "lm_iters_to_tol": {"plain": agg("plain", "lm_iters"), "learned": agg("learned", "lm_iters")},

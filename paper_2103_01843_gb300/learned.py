@@ -62,11 +62,64 @@ def _merge(samples):
     return {k: np.concatenate([s[k] for s in samples]) for k in samples[0]}
 
 
-def train(samples, params=None, steps=1500, batch=2048, lr=1e-3, seed=0, stream=None):
+def clean_samples(data, max_ratio=1e6, chunk=1 << 20):
+    """Drops the samples the normalised loss cannot use; returns (data, counts).
+
+    The loss of one sample is divided by ||L^T x*||^2 (L the Cholesky factor
+    of its block M), so a sample is kept only if its entries are finite, M is
+    positive definite (in FP64), x* is non-zero in the M-norm, and the
+    block-Jacobi term ||L^-1 g||^2 is at most `max_ratio` times that norm (a
+    sample beyond it would dominate a minibatch's mean loss by itself)."""
+    n = data["g"].shape[0]
+    keep = np.zeros(n, bool)
+    counts = dict(total=int(n), non_finite=0, not_pd=0, zero_target=0, ratio=0)
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        M = data["M"][a:b].reshape(-1, 9, 9).astype(np.float64)
+        g = data["g"][a:b].astype(np.float64)
+        x = data["xstar"][a:b].astype(np.float64)
+        fin = np.isfinite(M).all(axis=(1, 2)) & np.isfinite(g).all(axis=1) & np.isfinite(x).all(axis=1)
+        M = np.where(fin[:, None, None], M, np.eye(9))
+        g = np.where(fin[:, None], g, 0.0)
+        x = np.where(fin[:, None], x, 0.0)
+        L = np.zeros_like(M)
+        pd = np.ones(b - a, bool)
+        for j in range(9):  # column-by-column Cholesky over the whole chunk
+            d = M[:, j, j] - np.einsum("nk,nk->n", L[:, j, :j], L[:, j, :j])
+            pd &= d > 0
+            L[:, j, j] = np.sqrt(np.where(d > 0, d, 1.0))
+            for i in range(j + 1, 9):
+                L[:, i, j] = (M[:, i, j] - np.einsum("nk,nk->n", L[:, i, :j], L[:, j, :j])) / L[:, j, j]
+        w = np.zeros_like(g)
+        for i in range(9):
+            w[:, i] = (g[:, i] - np.einsum("nk,nk->n", L[:, i, :i], w[:, :i])) / L[:, i, i]
+        z2 = np.einsum("nij,ni->nj", L, x)
+        z2 = np.einsum("nj,nj->n", z2, z2)
+        w2 = np.einsum("ni,ni->n", w, w)
+        ok_fin, ok_pd = fin, fin & pd
+        ok_z = ok_pd & (z2 > 0)
+        ok = ok_z & (w2 <= max_ratio * z2)
+        counts["non_finite"] += int((~ok_fin).sum())
+        counts["not_pd"] += int((ok_fin & ~ok_pd).sum())
+        counts["zero_target"] += int((ok_pd & ~ok_z).sum())
+        counts["ratio"] += int((ok_z & ~ok).sum())
+        keep[a:b] = ok
+    counts["kept"] = int(keep.sum())
+    return {k: v[keep] for k, v in data.items()}, counts
+
+
+def train(samples, params=None, steps=1500, batch=2048, lr=1e-3, seed=0, stream=None, stats=None):
     """Trains a model on solver samples (a dict or a list of dicts) on the
-    GPU; returns (Mlp, list of losses)."""
+    GPU; returns (Mlp, list of losses).  The samples pass through
+    clean_samples first; its counts go into `stats` (a dict) if given.
+    Raises FloatingPointError at the first non-finite minibatch loss."""
     import torch
     data = _merge(samples) if isinstance(samples, (list, tuple)) else samples
+    data, counts = clean_samples(data)
+    if stats is not None:
+        stats.update(counts)
+    if counts["kept"] == 0:
+        raise ValueError(f"no usable training sample: {counts}")
     dev = torch.device("cuda")
     n = data["g"].shape[0]
     model = Mlp(params if params is not None else init_params(seed), stream=stream)
@@ -81,6 +134,9 @@ def train(samples, params=None, steps=1500, batch=2048, lr=1e-3, seed=0, stream=
     for _ in range(steps):
         idx = torch.randint(0, n, (min(batch, n),), device=dev, generator=gen)
         losses.append(model.train_step(feats[idx].contiguous(), aux[idx].contiguous(), lr))
+        if not np.isfinite(losses[-1]):
+            model.close()
+            raise FloatingPointError(f"non-finite minibatch loss at step {len(losses) - 1}")
     return model, losses
 
 
