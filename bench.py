@@ -279,12 +279,15 @@ def kernel_bytes(implicit, info):
             # K4: per observation its record (J_s and Householder rows, 96 B) and
             # camera index (4 B), per landmark Tm and S (48 B)
             "matvec": 100.0 * n_obs + 48.0 * n_pt,
-            # K1: write records (96 B), residuals (8 B) and the top rows (3 x 9 floats
-            # per observation, 3 x 4 per landmark) and Tm (24 B per landmark); read the
-            # observations (12 B), points (12 B) and cameras (36 B)
-            "linearize": (96.0 + 8.0 + 108.0 + 12.0) * n_obs + (48.0 + 24.0 + 12.0) * n_pt + 36.0 * n_cam,
-            # K3 (Gram form) as below plus G_tt (36 B) per landmark
-            "precond": 156.0 * n_obs + 36.0 * n_pt + 4.0 * 196 * n_cam,
+            # K1: write records (96 B) and residuals (8 B) per observation, per
+            # landmark Tm, P, R1, Q1^T r and D_l^2 (twice: record and vector), 120 B;
+            # read the observations (12 B), points (12 B) and cameras (36 B)
+            "linearize": (96.0 + 8.0 + 12.0) * n_obs + (120.0 + 12.0) * n_pt + 36.0 * n_cam,
+            # K3 (Gram form, top rows rebuilt): per observation the 36 B of the
+            # stored form's list entry, landmark index, measurement, offsets and
+            # point, its two Householder rows (32 B), c_off and lm_pos (8 B); per
+            # landmark G_tt P, G_tt t and G_tt (84 B); per camera as below
+            "precond": 76.0 * n_obs + 84.0 * n_pt + 4.0 * 196 * n_cam,
         }
     return {
         # K4: every A_j = Q2^T J_p (2k x 9k FP32) streamed once per launch
@@ -822,7 +825,9 @@ def run_kernels_only(args):
     from paper_2103_01843_gb300.synth import make_scene
     torch.cuda.set_device(0)
     scene = make_scene(args.config, args.seed)
-    with sq.Problem.from_scene(scene, stream=torch.cuda.current_stream().cuda_stream, autotune=1) as p:
+    implicit = 1 if args.storage == "implicit" else 0
+    with sq.Problem.from_scene(scene, stream=torch.cuda.current_stream().cuda_stream, autotune=1 - implicit,
+                               implicit_blocks=implicit) as p:
         for _ in range(args.warmup + args.steps):
             p.linearize()
             p.marginalize_qr(1e-4)
@@ -859,10 +864,12 @@ def run_matvec_only(args):
     from paper_2103_01843_gb300.synth import make_scene
     torch.cuda.set_device(0)
     scene = make_scene(args.config, args.seed)
-    with sq.Problem.from_scene(scene, stream=torch.cuda.current_stream().cuda_stream) as p:
+    implicit = 1 if args.storage == "implicit" else 0
+    with sq.Problem.from_scene(scene, stream=torch.cuda.current_stream().cuda_stream, implicit_blocks=implicit) as p:
         p.linearize()
         p.marginalize_qr(1e-4)
-        print(json.dumps({"mode": "matvec", "tuned": p.autotune()}), flush=True)
+        print(json.dumps({"mode": "matvec", "storage": args.storage,
+                          "tuned": None if implicit else p.autotune()}), flush=True)
         v = np.random.default_rng(0).normal(size=9 * scene.n_cam).astype(np.float32)
         for _ in range(args.warmup + args.steps):
             p.matvec(v)

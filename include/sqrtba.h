@@ -93,11 +93,12 @@ typedef struct {
     int32_t implicit_blocks; /* 0 (default): Q2^T J_p is stored per landmark (2k x 9k floats,
                              Sec. 5.1).  1: the factorisation is stored instead (per
                              observation J_s and its Householder rows, per landmark the
-                             compact-WY factor and the damping rotations' effect, O(k)
-                             memory, the variant of Table tab:complexities' storage
-                             discussion); products with A_j are formed on the fly in K4.
+                             compact-WY factor, R1, Q1^T r, P = V[0:3, :] Tm^T and the
+                             damping rotations' effect, O(k) memory, the variant of
+                             Table tab:complexities' storage discussion); products with
+                             A_j are formed on the fly in K4, the top rows in K3 and K6.
                              Same results up to rounding; ba_debug_export_landmark then
-                             exports only the undamped top rows */
+                             exports only the undamped top rows, rebuilt from the records */
     double huber_delta;   /* > 0: robust norm (Sec. 6.2: Huber, 1 px there) by iteratively
                              reweighted least squares: E = sum rho(||r_ij||^2) with
                              rho(s) = s (s <= delta^2), 2 delta sqrt(s) - delta^2 (above);
@@ -192,8 +193,10 @@ SQRTBA_API ba_status ba_marginalize_qr(ba_problem* h, double lambda);
  * equals J_s^T J_s - T_s^T T_s (and J_s^T r_s - T_s^T t) with J_s, r_s the
  * observation's Jacobian rows and residuals and T_s, t its columns of the
  * damped top rows [Q1^T J_p | R1 | Q1^T r]; by default the blocks are formed
- * that way (30 floats read per observation), with precond_from_blocks = 1
- * from the stored A_j and c_j (18 k floats per observation).
+ * that way (30 floats read per observation; in the implicit storage T_s is
+ * rebuilt from the observation's Householder rows and its landmark's record),
+ * with precond_from_blocks = 1 from the stored A_j and c_j (18 k floats per
+ * observation).
  * Errors: BA_ERR_STATE if not marginalised. */
 SQRTBA_API ba_status ba_pcg_solve(ba_problem* h, ba_pcg_report* report);
 

@@ -395,7 +395,8 @@ class Problem:
 
     def export_landmark(self, j, k_cap=256, top_only=False):
         """Landmark j's top rows, A_j, c_j and rotations (top_only: the top
-        rows alone, the only part the implicit storage keeps)."""
+        rows alone, the only part the implicit storage exports: it rebuilds
+        them from its records)."""
         top = np.zeros(3 * (9 * k_cap + 4), np.float32)
         a = np.zeros(2 * k_cap * 9 * k_cap if not top_only else 1, np.float32)
         c = np.zeros(2 * k_cap, np.float32)

@@ -29,8 +29,7 @@ constexpr int BS_TEAM = 8;
 __global__ void __launch_bounds__(32 * BS_WARPS)
 k_backsub_dl(int n_pt, const int32_t* __restrict__ lm_by_k, const int32_t* __restrict__ pt_off,
              const int32_t* __restrict__ obs_cam_s, const float* __restrict__ tpool, const float* __restrict__ dp,
-             float* __restrict__ dl, const float* __restrict__ lmrec, const BatchLm* __restrict__ blm,
-             const int32_t* __restrict__ lm_prob) {
+             float* __restrict__ dl, const BatchLm* __restrict__ blm, const int32_t* __restrict__ lm_prob) {
     const int lane = threadIdx.x & 31, rank = lane & (BS_TEAM - 1);
     const int pos = (blockIdx.x * (32 * BS_WARPS) + threadIdx.x) / BS_TEAM;
     bool has = pos < n_pt;
@@ -63,26 +62,88 @@ k_backsub_dl(int n_pt, const int32_t* __restrict__ lm_by_k, const int32_t* __res
     t0 += R0[3];
     t1 += R1[3];
     t2 += R2[3];
-    float r00 = R0[0], r01 = R0[1], r02 = R0[2], r11 = R1[1], r12 = R1[2], r22 = R2[2];
-    if (lmrec) {
-        // implicit storage: undamped top rows; the damped right-hand side is
-        // G_tt times theirs and the damped R is stored with G_tt
-        const float* L = lmrec + (int64_t)LM_REC * pos;
-        const float* G = L + 16;
-        const float a0 = t0, a1 = t1, a2 = t2;
-        t0 = G[0] * a0 + G[1] * a1 + G[2] * a2;
-        t1 = G[3] * a0 + G[4] * a1 + G[5] * a2;
-        t2 = G[6] * a0 + G[7] * a1 + G[8] * a2;
-        r00 = L[25];
-        r01 = L[26];
-        r02 = L[27];
-        r11 = L[28];
-        r12 = L[29];
-        r22 = L[30];
-    }
+    const float r00 = R0[0], r01 = R0[1], r02 = R0[2], r11 = R1[1], r12 = R1[2], r22 = R2[2];
     const float l2 = -t2 / r22;
     const float l1 = (-t1 - r12 * l2) / r11;
     const float l0 = (-t0 - r01 * l1 - r02 * l2) / r00;
+    dl[3 * j] = l0;
+    dl[3 * j + 1] = l1;
+    dl[3 * j + 2] = l2;
+}
+
+// The same in the implicit storage, which keeps no top rows: with
+// u_s = V_s^T (J_s dx_p) (the observation's two Householder rows against its
+// two linearised residual rows) the undamped top rows give
+//   Q1^T J_p dx_p = sum_s D_s dx_p - P sum_s u_s
+// (D_s dx_p is (J_s dx_p, 0) for slot 0 and (0, 0, first row) for slot 1),
+// and the damped right-hand side is G_tt t + G_tt sum D_s dx_p - (G_tt P)
+// sum u_s.  Lane t of a team reads observation t's record (6 float4, in
+// storage order: coalesced over the team).
+__global__ void __launch_bounds__(32 * BS_WARPS)
+k_backsub_dl_implicit(int n_pt, const int32_t* __restrict__ lm_by_k, const int32_t* __restrict__ pt_off,
+                      const int32_t* __restrict__ c_off, const int32_t* __restrict__ obs_cam_s,
+                      const float4* __restrict__ ipool, int64_t n_obs, const float* __restrict__ dp,
+                      float* __restrict__ dl, const float* __restrict__ lmrec, const BatchLm* __restrict__ blm,
+                      const int32_t* __restrict__ lm_prob) {
+    const int lane = threadIdx.x & 31, rank = lane & (BS_TEAM - 1);
+    const int pos = (blockIdx.x * (32 * BS_WARPS) + threadIdx.x) / BS_TEAM;
+    bool has = pos < n_pt;
+    const int j = has ? lm_by_k[pos] : 0;
+    if (has && blm && !batch_active(blm, lm_prob[j])) has = false;  // a stopped problem of a batch
+    const int s0 = has ? pt_off[j] : 0, k = has ? pt_off[j + 1] - s0 : 0;
+    const int64_t so0 = has ? (c_off[j] >> 1) : 0;
+    float u0 = 0.f, u1 = 0.f, u2 = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
+    for (int t = rank; t < k; t += BS_TEAM) {
+        float f[24];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+            const float4 c = __ldg(ipool + m * n_obs + so0 + t);
+            f[4 * m] = c.x;
+            f[4 * m + 1] = c.y;
+            f[4 * m + 2] = c.z;
+            f[4 * m + 3] = c.w;
+        }
+        const float* d = dp + 9 * __ldg(obs_cam_s + s0 + t);
+        float e0 = 0.f, e1 = 0.f;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+            const float dc = __ldg(d + c);
+            e0 += f[c] * dc;
+            e1 += f[9 + c] * dc;
+        }
+        u0 += f[18] * e0 + f[21] * e1;
+        u1 += f[19] * e0 + f[22] * e1;
+        u2 += f[20] * e0 + f[23] * e1;
+        if (t == 0) {
+            d0 = e0;
+            d1 = e1;
+        } else if (t == 1) {
+            d2 = e0;
+        }
+    }
+#pragma unroll
+    for (int o = BS_TEAM / 2; o > 0; o >>= 1) {
+        u0 += __shfl_xor_sync(0xffffffffu, u0, o);
+        u1 += __shfl_xor_sync(0xffffffffu, u1, o);
+        u2 += __shfl_xor_sync(0xffffffffu, u2, o);
+        d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+        d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+        d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+    }
+    if (!has || rank != 0) return;
+    const float* L = lmrec + (int64_t)LM_REC * pos;
+    const float* GP = L + LR_GP;
+    const float* Gt = L + LR_GT;
+    const float* G = L + LR_G;
+    const float* R = L + LR_RD;
+    float a[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        a[i] = Gt[i] + G[3 * i] * d0 + G[3 * i + 1] * d1 + G[3 * i + 2] * d2 -
+               (GP[3 * i] * u0 + GP[3 * i + 1] * u1 + GP[3 * i + 2] * u2);
+    const float l2 = -a[2] / R[5];
+    const float l1 = (-a[1] - R[4] * l2) / R[3];
+    const float l0 = (-a[0] - R[1] * l1 - R[2] * l2) / R[0];
     dl[3 * j] = l0;
     dl[3 * j + 1] = l1;
     dl[3 * j + 2] = l2;
@@ -237,15 +298,26 @@ __global__ void k_candidate(int n_cam, const float* __restrict__ cams, const flo
 
 }  // namespace
 
+// K6: dl per landmark (the stored top rows, or the implicit storage's records)
+static void launch_backsub_dl(Problem& p) {
+    const int grid = (int)ceil_div((int64_t)p.n_pt * BS_TEAM, 32 * BS_WARPS);
+    const BatchLm* blm = p.batch.n_prob > 0 ? p.batch.lm : nullptr;
+    if (p.implicit)
+        k_backsub_dl_implicit<<<grid, 32 * BS_WARPS, 0, p.stream>>>(
+            p.n_pt, p.lm_by_k, p.pt_off, p.c_off, p.obs_cam_s, reinterpret_cast<const float4*>(p.ipool), p.n_obs,
+            p.x, p.dl, p.lmrec, blm, p.batch.lm_prob);
+    else
+        k_backsub_dl<<<grid, 32 * BS_WARPS, 0, p.stream>>>(p.n_pt, p.lm_by_k, p.pt_off, p.obs_cam_s, p.tpool, p.x,
+                                                          p.dl, blm, p.batch.lm_prob);
+}
+
 // K6: dl per landmark, then the model cost L(dx) per observation (FP64)
 void launch_backsub(Problem& p) {
     count_launches(p, 3);
     if (p.schur)
         launch_schur_backsub(p);
     else
-        k_backsub_dl<<<ceil_div((int64_t)p.n_pt * BS_TEAM, 32 * BS_WARPS), 32 * BS_WARPS, 0, p.stream>>>(
-            p.n_pt, p.lm_by_k, p.pt_off, p.obs_cam_s, p.tpool, p.x, p.dl, p.implicit ? p.lmrec : nullptr,
-            p.batch.n_prob > 0 ? p.batch.lm : nullptr, p.batch.lm_prob);
+        launch_backsub_dl(p);
     k_model_cost<<<p.red_grid, 256, 0, p.stream>>>(p.n_obs, p.frames, p.pts, p.obs_cam_s, p.obs_pt_s, p.obs_xy_s, p.x,
                                                    p.dl, nullptr, nullptr, p.partials, nullptr, (float)p.opt.huber_delta);
     k_sum_partials<<<1, 1024, 0, p.stream>>>(p.partials, p.red_grid, p.dsum + 1);
@@ -260,9 +332,7 @@ void launch_backsub_candidate_cost(Problem& p) {
     if (p.schur)
         launch_schur_backsub(p);
     else
-        k_backsub_dl<<<ceil_div((int64_t)p.n_pt * BS_TEAM, 32 * BS_WARPS), 32 * BS_WARPS, 0, p.stream>>>(
-            p.n_pt, p.lm_by_k, p.pt_off, p.obs_cam_s, p.tpool, p.x, p.dl, p.implicit ? p.lmrec : nullptr,
-            p.batch.n_prob > 0 ? p.batch.lm : nullptr, p.batch.lm_prob);
+        launch_backsub_dl(p);
     launch_candidate(p);
     if (p.batch.n_prob > 0) {
         BatchState& B = p.batch;

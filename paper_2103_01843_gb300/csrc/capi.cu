@@ -12,6 +12,7 @@
 #include <new>
 #include <string>
 #include <utility>
+#include <memory>
 #include <vector>
 
 #include "camera.cuh"
@@ -807,7 +808,7 @@ void create_problem(Problem& p, const double* cams, int32_t n_cam, const double*
         d2h_sync_copy(p, h_cam.data(), p.obs_cam_s, n_obs);
         plan_schur(p, h_pt_off, h_cam);
         p.tuned = true;
-    } else {
+    } else if (!p.implicit) {  // the implicit storage keeps no top rows (landmark records instead)
         p.t_floats = 3 * (9 * n_obs + 4 * (int64_t)n_pt);
         p.tpool = dalloc<float>(p, p.t_floats);
     }
@@ -1339,10 +1340,19 @@ ba_status ba_debug_export_landmark(ba_problem* h, int32_t j, int32_t k_cap, floa
     if (k_out) *k_out = k;
     require(k <= k_cap, BA_ERR_INVALID_ARG, "k exceeds k_cap");
     require(!p.implicit || (!a && !c && !rot), BA_ERR_INVALID_ARG,
-            "implicit storage: only the (undamped) top rows are stored");
+            "implicit storage: only the (undamped) top rows can be exported");
     require(!p.schur, BA_ERR_INVALID_ARG, "the explicit Schur complement stores no landmark blocks");
     const int64_t ncol = 9 * (int64_t)k;
-    if (top) d2h(p, top, p.tpool + top_offset(off[0], j), 3 * (ncol + 4));
+    if (top && p.implicit) {  // rebuilt from the records (the implicit storage keeps no top rows)
+        float* d_top = nullptr;
+        BA_CUDA_TRY(cudaMalloc(&d_top, sizeof(float) * 3 * (ncol + 4)));
+        std::unique_ptr<float, decltype(&cudaFree)> hold(d_top, &cudaFree);
+        launch_implicit_top_rows(p, j, k, d_top);
+        d2h(p, top, d_top, 3 * (ncol + 4));
+        sync(p);
+    } else if (top) {
+        d2h(p, top, p.tpool + top_offset(off[0], j), 3 * (ncol + 4));
+    }
     if (a) d2h(p, a, p.apool + aoff, 2 * (int64_t)k * ncol);
     if (c) d2h(p, c, p.cpool + coff, 2 * (int64_t)k);
     if (rot) d2h(p, rot, p.rot + 12 * (int64_t)j, 12);

@@ -180,12 +180,13 @@ k_damp(int n_pt, const int32_t* __restrict__ pt_off, const int64_t* __restrict__
     }
 }
 
-// The implicit storage keeps the top rows undamped: one thread per landmark
-// (storage position) computes the same six rotations from R1 and
-// sqrt(lambda) D_l, applies them also to [I; 0] (the map from the undamped
-// top rows to the six rotated rows, G[:, 0:3] = [G_tt; G_dt]), and stores
-// S = G_dt^T G_dt, G_tt and the damped R.  No undo is needed: every call
-// starts from the undamped R1.
+// The implicit storage keeps no top rows; its landmark record holds the
+// undamped R1, Q1^T r = t and P (K1).  One thread per landmark (storage
+// position) computes the same six rotations from R1 and sqrt(lambda) D_l,
+// applies them also to [I; 0] (the map from the undamped top rows to the six
+// rotated rows, G[:, 0:3] = [G_tt; G_dt]), and stores S = G_dt^T G_dt, G_tt,
+// G_tt P, G_tt t and the damped R.  No undo is needed: every call starts from
+// the undamped R1.
 __global__ void __launch_bounds__(128)
 k_damp_implicit(int n_pt, float* __restrict__ lmrec, float sqrt_lambda, const int32_t* __restrict__ lm_by_k,
                 const float* __restrict__ lam_prob, const int32_t* __restrict__ lm_prob,
@@ -194,11 +195,16 @@ k_damp_implicit(int n_pt, float* __restrict__ lmrec, float sqrt_lambda, const in
     if (pos >= n_pt) return;
     if (blm && !batch_active(blm, lm_prob[lm_by_k[pos]])) return;
     float* L = lmrec + (int64_t)LM_REC * pos;
-    // R1 (upper) and D_l^2 from the landmark record (K1), 16-byte loads
-    const float4 q0 = *reinterpret_cast<const float4*>(L + 32), q1 = *reinterpret_cast<const float4*>(L + 36);
-    const float q2 = L[40];
+    // R1 (upper), D_l^2, t and P from the landmark record (K1), 16-byte loads
+    static_assert(LR_DL2 == LR_R1 + 6 && LR_T == LR_R1 + 9 && LR_P == LR_R1 + 12 && LR_R1 % 4 == 0, "record");
+    const float4 q0 = *reinterpret_cast<const float4*>(L + LR_R1), q1 = *reinterpret_cast<const float4*>(L + LR_R1 + 4),
+                 q2 = *reinterpret_cast<const float4*>(L + LR_R1 + 8), p0 = *reinterpret_cast<const float4*>(L + LR_P),
+                 p1 = *reinterpret_cast<const float4*>(L + LR_P + 4);
+    const float p8 = L[LR_P + 8];
     float R[3][3] = {{q0.x, q0.y, q0.z}, {0.f, q0.w, q1.x}, {0.f, 0.f, q1.y}};
-    const float dl2[3] = {q1.z, q1.w, q2};
+    const float dl2[3] = {q1.z, q1.w, q2.x};
+    const float t[3] = {q2.y, q2.z, q2.w};
+    const float P[3][3] = {{p0.x, p0.y, p0.z}, {p0.w, p1.x, p1.y}, {p1.z, p1.w, p8}};
     float D[3][3], E[6][3];
     for (int i = 0; i < 3; ++i)
         for (int c = 0; c < 3; ++c) {
@@ -235,19 +241,30 @@ k_damp_implicit(int n_pt, float* __restrict__ lmrec, float sqrt_lambda, const in
             E[3 + d][col] = -sn * u + cs * v;
         }
     }
-    // S = G_dt^T G_dt (upper: 00 01 02 11 12 22), G_tt, damped R (upper): 16-byte stores
-    float S[6];
+    // S = G_dt^T G_dt (upper: 00 01 02 11 12 22), G_tt P, G_tt t, G_tt, damped R
+    // (upper): 16-byte stores
+    float S[6], GP[9], Gt[3];
     int q = 0;
 #pragma unroll
     for (int u = 0; u < 3; ++u)
 #pragma unroll
         for (int v = u; v < 3; ++v) S[q++] = E[3][u] * E[3][v] + E[4][u] * E[4][v] + E[5][u] * E[5][v];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        Gt[i] = E[i][0] * t[0] + E[i][1] * t[1] + E[i][2] * t[2];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) GP[3 * i + b] = E[i][0] * P[0][b] + E[i][1] * P[1][b] + E[i][2] * P[2][b];
+    }
+    static_assert(LR_S == 6 && LR_GP == 12 && LR_GT == 21 && LR_G == 24 && LR_RD == 33, "record");
     *reinterpret_cast<float2*>(L + 6) = make_float2(S[0], S[1]);
     *reinterpret_cast<float4*>(L + 8) = make_float4(S[2], S[3], S[4], S[5]);
-    *reinterpret_cast<float4*>(L + 16) = make_float4(E[0][0], E[0][1], E[0][2], E[1][0]);
-    *reinterpret_cast<float4*>(L + 20) = make_float4(E[1][1], E[1][2], E[2][0], E[2][1]);
-    *reinterpret_cast<float4*>(L + 24) = make_float4(E[2][2], R[0][0], R[0][1], R[0][2]);
-    *reinterpret_cast<float4*>(L + 28) = make_float4(R[1][1], R[1][2], R[2][2], 0.f);
+    *reinterpret_cast<float4*>(L + 12) = make_float4(GP[0], GP[1], GP[2], GP[3]);
+    *reinterpret_cast<float4*>(L + 16) = make_float4(GP[4], GP[5], GP[6], GP[7]);
+    *reinterpret_cast<float4*>(L + 20) = make_float4(GP[8], Gt[0], Gt[1], Gt[2]);
+    *reinterpret_cast<float4*>(L + 24) = make_float4(E[0][0], E[0][1], E[0][2], E[1][0]);
+    *reinterpret_cast<float4*>(L + 28) = make_float4(E[1][1], E[1][2], E[2][0], E[2][1]);
+    *reinterpret_cast<float4*>(L + 32) = make_float4(E[2][2], R[0][0], R[0][1], R[0][2]);
+    *reinterpret_cast<float4*>(L + 36) = make_float4(R[1][1], R[1][2], R[2][2], 0.f);
 }
 
 }  // namespace

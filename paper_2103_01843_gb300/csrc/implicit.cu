@@ -313,7 +313,53 @@ __global__ void __launch_bounds__(IM_THREADS, 2) k_matvec_implicit(ImArgs a) {
 
 bool implicit_smem_y(const Problem& p) { return 36LL * p.n_cam <= IM_SMEM_Y_MAX; }
 
+// The undamped top rows [Q1^T J_p | R1 | Q1^T r] of landmark j (3 rows of
+// 9 k + 4, the stored form's layout) rebuilt from the records, one thread per
+// element: camera s's column c of row i is D_s[i][c] - sum_b P[i][b] u_s[b][c],
+// u_s = V_s^T J_s (export only; the solver's readers fold this into their sums).
+__global__ void k_implicit_top_rows(int j, const int32_t* __restrict__ pt_off, const int32_t* __restrict__ c_off,
+                                    const int32_t* __restrict__ lm_pos, const float4* __restrict__ ipool,
+                                    int64_t n_obs, const float* __restrict__ lmrec, float* __restrict__ top) {
+    const int s0 = pt_off[j], k = pt_off[j + 1] - s0, ncol = 9 * k;
+    const int64_t so0 = c_off[j] >> 1;
+    const float* L = lmrec + (int64_t)LM_REC * lm_pos[j];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 3 * (ncol + 4); e += gridDim.x * blockDim.x) {
+        const int i = e / (ncol + 4), col = e - i * (ncol + 4);
+        float out;
+        if (col < ncol) {
+            const int q = col / 9, c = col - 9 * q;
+            float f[24];
+#pragma unroll
+            for (int m = 0; m < 6; ++m) {
+                const float4 v = ipool[m * n_obs + so0 + q];
+                f[4 * m] = v.x;
+                f[4 * m + 1] = v.y;
+                f[4 * m + 2] = v.z;
+                f[4 * m + 3] = v.w;
+            }
+            out = 0.f;
+            if (q == 0 && i < 2) out = f[9 * i + c];
+            if (q == 1 && i == 2) out = f[c];
+#pragma unroll
+            for (int b = 0; b < 3; ++b) out -= L[LR_P + 3 * i + b] * (f[18 + b] * f[c] + f[21 + b] * f[9 + c]);
+        } else if (col < ncol + 3) {
+            const int c = col - ncol;  // R1, upper (00 01 02 11 12 22)
+            const int idx[3][3] = {{0, 1, 2}, {-1, 3, 4}, {-1, -1, 5}};
+            out = idx[i][c] < 0 ? 0.f : L[LR_R1 + idx[i][c]];
+        } else {
+            out = L[LR_T + i];
+        }
+        top[e] = out;
+    }
+}
+
 }  // namespace
+
+void launch_implicit_top_rows(Problem& p, int j, int k, float* top) {
+    k_implicit_top_rows<<<ceil_div(3 * (9 * (int64_t)k + 4), 256), 256, 0, p.stream>>>(
+        j, p.pt_off, p.c_off, p.lm_pos, reinterpret_cast<const float4*>(p.ipool), p.n_obs, p.lmrec, top);
+    BA_LAUNCH_CHECK();
+}
 
 // Tasks in storage order (decreasing k): k <= 32, the landmarks of one warp
 // (32 / W teams); k > 32, one landmark each.

@@ -10,6 +10,9 @@
 // W = T^T (V^T M) with M = [J_p | r].  Rows 0..2 are the R1 rows
 // (Q1^T J_p, R1, Q1^T r, used by back substitution, Eq. backsub_nm); rows
 // 3..2k-1 are Q2^T J_p and Q2^T r (Eq. reduced).  Q is never stored.
+// The implicit storage writes no rows at all: per observation J_s and the
+// two Householder rows, per landmark Tm, P = V[0:3, :] Tm^T, R1, Q1^T r and
+// D_l^2; its readers rebuild camera s's top slice as D_s - P (V_s^T J_s).
 //
 // One warp handles a landmark with k <= 32 (2k rows fit one row per lane for
 // the reductions); a 256-thread CTA handles larger k.  Work is taken from
@@ -180,27 +183,6 @@ __device__ __forceinline__ void write_rows_dispatch(int k, const float* V, const
 // lanes own the pose columns col = rank + TEAM m, keep their W = Tm^T V^T J_p
 // entries in registers and write Q^T J_p row by row (coalesced), three FMAs
 // per element.  The CTA-wide team (k > 32) goes through shared memory.
-// The top rows of the implicit form: rows 0..2 of Q^T J_p only (lanes over
-// the columns, W entries in registers), three FMAs per element.
-template <int TEAM, int MC>
-__device__ __forceinline__ void write_top_rows(int ncol, const float* __restrict__ V, const float* __restrict__ JP,
-                                               const float (&w0)[MC], const float (&w1)[MC], const float (&w2)[MC],
-                                               float* __restrict__ top, int rank) {
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const float v0 = V[3 * i], v1 = V[3 * i + 1], v2 = V[3 * i + 2];
-        const int base = 9 * (i >> 1);
-#pragma unroll
-        for (int m = 0; m < MC; ++m) {
-            const int col = rank + TEAM * m;
-            if (col >= ncol) break;
-            float out = -(v0 * w0[m] + v1 * w1[m] + v2 * w2[m]);
-            if (col >= base && col < base + 9) out += JP[i * 9 + (col - base)];
-            top[i * (ncol + 4) + col] = out;
-        }
-    }
-}
-
 template <int TEAM, int MC = 1>
 __device__ void marginalize_landmark(const LinArgs& A, int j, int pos, float* sm, float* red, bool write = true) {
     using T = Team<TEAM>;
@@ -250,7 +232,7 @@ __device__ void marginalize_landmark(const LinArgs& A, int j, int pos, float* sm
             A.dl2[3 * j + 1] = c1;
             A.dl2[3 * j + 2] = c2;
             if (A.lmrec) {  // implicit storage: K2 reads D_l^2 with R1 from the landmark record
-                float* Lr = A.lmrec + (int64_t)LM_REC * pos + 38;
+                float* Lr = A.lmrec + (int64_t)LM_REC * pos + LR_DL2;
                 Lr[0] = c0;
                 Lr[1] = c1;
                 Lr[2] = c2;
@@ -333,9 +315,8 @@ __device__ void marginalize_landmark(const LinArgs& A, int j, int pos, float* sm
         T::sync();
     }
 
-    const int64_t toff = top_offset(s0, j);
-    float* __restrict__ top = A.tpool + toff;
     const bool implicit = A.ipool != nullptr;
+    float* __restrict__ top = implicit ? nullptr : A.tpool + top_offset(s0, j);
     float* __restrict__ Aj = implicit ? nullptr : A.apool + A.a_off[j];
     if (implicit && write) {
         // per observation: J_s rows and Householder rows (6 float4 chunks,
@@ -355,17 +336,26 @@ __device__ void marginalize_landmark(const LinArgs& A, int j, int pos, float* sm
             A.rpool[2 * (so0 + s) + 1] = RV[2 * s + 1];
         }
         if (rank == 0) {
+            // Tm and P = V[0:3, :] Tm^T (the top rows are rebuilt from P by
+            // their readers: rows 0..2 of Q^T M are M[0:3] - P (V^T M))
             const float* Tm = misc + 5;
             float* L = A.lmrec + (int64_t)LM_REC * pos;
-            L[0] = Tm[0];
-            L[1] = Tm[1];
-            L[2] = Tm[2];
-            L[3] = Tm[4];
-            L[4] = Tm[5];
-            L[5] = Tm[8];
+            L[LR_TM] = Tm[0];
+            L[LR_TM + 1] = Tm[1];
+            L[LR_TM + 2] = Tm[2];
+            L[LR_TM + 3] = Tm[4];
+            L[LR_TM + 4] = Tm[5];
+            L[LR_TM + 5] = Tm[8];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int b = 0; b < 3; ++b)
+                    L[LR_P + 3 * i + b] = V[3 * i] * Tm[3 * b] + V[3 * i + 1] * Tm[3 * b + 1] + V[3 * i + 2] * Tm[3 * b + 2];
         }
     }
-    if constexpr (TEAM <= 32) {
+    if (implicit) {
+        // nothing more per column: the readers rebuild the top rows
+    } else if constexpr (TEAM <= 32) {
         // 4+5. W for this lane's columns (registers), then Q^T J_p row by row
         const float* Tm = misc + 5;
         const float T00 = Tm[0], T01 = Tm[1], T02 = Tm[2], T11 = Tm[4], T12 = Tm[5], T22 = Tm[8];
@@ -383,8 +373,7 @@ __device__ void marginalize_landmark(const LinArgs& A, int j, int pos, float* sm
             w1[m] = T01 * m0 + T11 * m1;
             w2[m] = T02 * m0 + T12 * m1 + T22 * m2;
         }
-        if (write && implicit) write_top_rows<TEAM, MC>(ncol, V, JP, w0, w1, w2, top, rank);
-        else if (write) write_rows_dispatch<TEAM, MC>(k, V, JP, w0, w1, w2, top, Aj, rank);
+        if (write) write_rows_dispatch<TEAM, MC>(k, V, JP, w0, w1, w2, top, Aj, rank);
     } else {
         // 4. W = Tm^T (V^T J_p) for the pose columns (two non-zero rows each)
         {
@@ -402,9 +391,8 @@ __device__ void marginalize_landmark(const LinArgs& A, int j, int pos, float* sm
             }
             T::sync();
         }
-        // 5. write Q^T J_p: rows 0..2 to the top block, rows 3.. to A_j (the
-        // implicit form keeps the top rows only)
-        const int64_t total = (int64_t)(implicit ? 3 : nr) * ncol;
+        // 5. write Q^T J_p: rows 0..2 to the top block, rows 3.. to A_j
+        const int64_t total = (int64_t)nr * ncol;
         int e = rank;
         int i = e / ncol, col = e - i * ncol;
         for (; write && e < total; e += TEAM) {
@@ -426,25 +414,26 @@ __device__ void marginalize_landmark(const LinArgs& A, int j, int pos, float* sm
     // residual column and R1
     for (int ii = rank; write && ii < nr; ii += TEAM) {
         const float out = RV[ii] - (V[3 * ii] * wr0 + V[3 * ii + 1] * wr1 + V[3 * ii + 2] * wr2);
-        if (ii < 3) {
+        if (ii < 3 && implicit) {
+            // R1 (upper: 00 01 02 11 12 22) and t = Q1^T r into the landmark record
+            float* Lr = A.lmrec + (int64_t)LM_REC * pos;
+            Lr[LR_T + ii] = out;
+            if (ii == 0) {
+                Lr[LR_R1] = L[0];
+                Lr[LR_R1 + 1] = L[1];
+                Lr[LR_R1 + 2] = L[2];
+            } else if (ii == 1) {
+                Lr[LR_R1 + 3] = L[4];
+                Lr[LR_R1 + 4] = L[5];
+            } else {
+                Lr[LR_R1 + 5] = L[8];
+            }
+        } else if (ii < 3) {
             float* row = top + ii * (ncol + 4) + ncol;
             row[0] = ii <= 0 ? L[3 * ii] : 0.f;
             row[1] = ii <= 1 ? L[3 * ii + 1] : 0.f;
             row[2] = L[3 * ii + 2];
             row[3] = out;
-            if (implicit) {  // R1 (upper: 00 01 02 11 12 22) into the landmark record
-                float* Lr = A.lmrec + (int64_t)LM_REC * pos + 32;
-                if (ii == 0) {
-                    Lr[0] = L[0];
-                    Lr[1] = L[1];
-                    Lr[2] = L[2];
-                } else if (ii == 1) {
-                    Lr[3] = L[4];
-                    Lr[4] = L[5];
-                } else {
-                    Lr[5] = L[8];
-                }
-            }
         } else if (!implicit) {
             A.cpool[A.c_off[j] + (ii - 3)] = out;
         }
@@ -467,6 +456,144 @@ k_linearize_team(LinArgs A, const int32_t* __restrict__ order, int first, int co
     float* sm = smem + (w * TPW + tm) * lin_smem_floats(KMAX);
     const int pos = first + (active ? idx : idx0);
     marginalize_landmark<W, (9 * KMAX + W - 1) / W>(A, order[pos], pos, sm, nullptr, active);
+}
+
+// The implicit storage for k <= THR_KMAX: one thread per landmark, the whole
+// 2k x 4 block [J_l | r] in registers.  The record's J_s part is written as
+// each observation is linearised; Householder QR in place (R1 on and above the
+// diagonal, v_a below it with v_a[a] = 1 implied) with the reflectors applied
+// to r directly (Q^T r = H_3 H_2 H_1 r); then Tm, P, R1, Q1^T r and D_l^2 as
+// 16-byte stores and the records' Householder part.  No team reductions and
+// no shared memory: a warp factors 32 landmarks of equal k side by side
+// (landmarks are in decreasing-k order).
+constexpr int THR_KMAX = 8;
+
+template <int K>
+__device__ __forceinline__ void linearize_thread(const LinArgs& A, int j, int pos) {
+    constexpr int NR = 2 * K;
+    const int s0 = A.pt_off[j];
+    const int64_t so0 = A.c_off[j] >> 1, n = A.n_obs;
+    const float X0 = __ldg(A.pts + 3 * j), X1 = __ldg(A.pts + 3 * j + 1), X2 = __ldg(A.pts + 3 * j + 2);
+    float4* __restrict__ ip = reinterpret_cast<float4*>(A.ipool);
+    float B[NR][4];  // [J_l | r] -> [R1 and v_1..v_3 | Q^T r]
+    float jt[K][2];  // J_s entries 16 and 17 (record chunk 4, with the Householder rows)
+    float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+        const float2 z = A.obs_xy_s[s0 + s];
+        float r[2], Jp[18], Jl[6];
+        frame_jacobians(A.frames + FRAME * A.obs_cam_s[s0 + s], X0, X1, X2, z.x, z.y, r, Jp, Jl);
+        huber_scale_rows(A.huber, r, Jp, Jl);
+        const int64_t so = so0 + s;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) ip[m * n + so] = make_float4(Jp[4 * m], Jp[4 * m + 1], Jp[4 * m + 2], Jp[4 * m + 3]);
+        reinterpret_cast<float2*>(A.rpool)[so] = make_float2(r[0], r[1]);
+        jt[s][0] = Jp[16];
+        jt[s][1] = Jp[17];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            B[2 * s + i][0] = Jl[3 * i];
+            B[2 * s + i][1] = Jl[3 * i + 1];
+            B[2 * s + i][2] = Jl[3 * i + 2];
+            B[2 * s + i][3] = r[i];
+            d0 += Jl[3 * i] * Jl[3 * i];
+            d1 += Jl[3 * i + 1] * Jl[3 * i + 1];
+            d2 += Jl[3 * i + 2] * Jl[3 * i + 2];
+        }
+    }
+    const float c0 = fminf(fmaxf(d0, 1e-6f), 1e32f), c1 = fminf(fmaxf(d1, 1e-6f), 1e32f),
+                c2 = fminf(fmaxf(d2, 1e-6f), 1e32f);
+    A.dl2[3 * j] = c0;
+    A.dl2[3 * j + 1] = c1;
+    A.dl2[3 * j + 2] = c2;
+    // Householder QR: reflector a acts on rows a..2k-1
+    float tau[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float sg = 0.f;
+#pragma unroll
+        for (int i = a + 1; i < NR; ++i) sg += B[i][a] * B[i][a];
+        const float alpha = B[a][a];
+        float t = 0.f, beta = alpha, v0 = 1.f;
+        if (sg > 0.f) {
+            const float mu = sqrtf(alpha * alpha + sg);
+            beta = alpha > 0.f ? -mu : mu;
+            v0 = alpha - beta;
+            t = (beta - alpha) / beta;
+        }
+        tau[a] = t;
+        const float iv = 1.0f / v0;
+#pragma unroll
+        for (int i = a + 1; i < NR; ++i) B[i][a] = t == 0.f ? 0.f : B[i][a] * iv;
+        B[a][a] = beta;
+#pragma unroll
+        for (int c = a + 1; c < 4; ++c) {
+            float w = B[a][c];
+#pragma unroll
+            for (int i = a + 1; i < NR; ++i) w += B[i][a] * B[i][c];
+            w *= t;
+            B[a][c] -= w;
+#pragma unroll
+            for (int i = a + 1; i < NR; ++i) B[i][c] -= w * B[i][a];
+        }
+    }
+    // compact WY: H_1 H_2 H_3 = I - V Tm V^T (V(i, a) = 1 at i = a, 0 above)
+    auto V = [&](int i, int a) { return i == a ? 1.f : (i > a ? B[i][a] : 0.f); };
+    float d01 = 0.f, d02 = 0.f, d12 = 0.f;
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+        d01 += V(i, 0) * V(i, 1);
+        d02 += V(i, 0) * V(i, 2);
+        d12 += V(i, 1) * V(i, 2);
+    }
+    float Tm[3][3];
+    Tm[0][0] = tau[0];
+    Tm[1][1] = tau[1];
+    Tm[2][2] = tau[2];
+    Tm[1][0] = Tm[2][0] = Tm[2][1] = 0.f;
+    Tm[0][1] = -tau[0] * tau[1] * d01;
+    Tm[1][2] = -tau[2] * (tau[1] * d12);
+    Tm[0][2] = -tau[2] * (tau[0] * d02 + Tm[0][1] * d12);
+    float P[3][3];  // P = V[0:3, :] Tm^T
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) P[i][b] = V(i, 0) * Tm[b][0] + V(i, 1) * Tm[b][1] + V(i, 2) * Tm[b][2];
+    static_assert(LR_TM == 0 && LR_R1 == 40 && LR_DL2 == 46 && LR_T == 49 && LR_P == 52, "record");
+    float4* L4 = reinterpret_cast<float4*>(A.lmrec + (int64_t)LM_REC * pos);
+    L4[0] = make_float4(Tm[0][0], Tm[0][1], Tm[0][2], Tm[1][1]);
+    *reinterpret_cast<float2*>(L4 + 1) = make_float2(Tm[1][2], Tm[2][2]);
+    L4[10] = make_float4(B[0][0], B[0][1], B[0][2], B[1][1]);
+    L4[11] = make_float4(B[1][2], B[2][2], c0, c1);
+    L4[12] = make_float4(c2, B[0][3], B[1][3], B[2][3]);
+    L4[13] = make_float4(P[0][0], P[0][1], P[0][2], P[1][0]);
+    L4[14] = make_float4(P[1][1], P[1][2], P[2][0], P[2][1]);
+    L4[15] = make_float4(P[2][2], 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+        const int i = 2 * s;
+        ip[4 * n + so0 + s] = make_float4(jt[s][0], jt[s][1], V(i, 0), V(i, 1));
+        ip[5 * n + so0 + s] = make_float4(V(i, 2), V(i + 1, 0), V(i + 1, 1), V(i + 1, 2));
+    }
+}
+
+// landmarks order[first .. first + count) with 2 <= k <= THR_KMAX, one thread each
+__global__ void __launch_bounds__(128)
+k_linearize_thread(LinArgs A, const int32_t* __restrict__ order, int first, int count) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= count) return;
+    const int pos = first + idx, j = order[pos];
+    if (A.blm && !batch_relin(A.blm, A.lm_prob[j])) return;
+    switch (A.pt_off[j + 1] - A.pt_off[j]) {
+        case 2: linearize_thread<2>(A, j, pos); break;
+        case 3: linearize_thread<3>(A, j, pos); break;
+        case 4: linearize_thread<4>(A, j, pos); break;
+        case 5: linearize_thread<5>(A, j, pos); break;
+        case 6: linearize_thread<6>(A, j, pos); break;
+        case 7: linearize_thread<7>(A, j, pos); break;
+        case 8: linearize_thread<8>(A, j, pos); break;
+        default: break;
+    }
 }
 
 __global__ void __launch_bounds__(BIG_TEAM)
@@ -589,7 +716,8 @@ void launch_linearize(Problem& p) {
               p.dl2, p.implicit ? p.ipool : nullptr, p.rpool, p.lmrec, p.n_obs, (float)p.opt.huber_delta,
               p.batch.n_prob > 0 ? p.batch.lm : nullptr, p.batch.lm_prob};
     // segments of lm_by_k: k > 32 | 9..32 | 5..8 | 2..4
-    const int n_big = p.n_big, n32 = count_k(p, 8, 32), n16 = count_k(p, 4, 8), n8 = count_k(p, 1, 4);
+    const int n_big = p.n_big, n32 = count_k(p, 8, 32);
+    int n16 = count_k(p, 4, 8), n8 = count_k(p, 1, 4);
     BA_CUDA_TRY(cudaEventRecord(p.ev_fork, p.stream));
     BA_CUDA_TRY(cudaStreamWaitEvent(p.side, p.ev_fork, 0));
     // side: D_p^2, then the landmarks with k > 32 (one CTA each)
@@ -609,6 +737,12 @@ void launch_linearize(Problem& p) {
         count_launches(p, 1);
     }
     first += n32;
+    if (p.implicit && n16 + n8 > 0) {  // k <= 8: a thread per landmark
+        static_assert(THR_KMAX == 8, "segments");
+        k_linearize_thread<<<ceil_div(n16 + n8, 128), 128, 0, p.stream>>>(A, p.lm_by_k, first, n16 + n8);
+        count_launches(p, 1);
+        n16 = n8 = 0;
+    }
     if (n16 > 0) {
         k_linearize_team<16, 8><<<ceil_div(n16, 2 * LIN_WARPS), 32 * LIN_WARPS, team_smem_bytes<16, 8>(), p.stream>>>(
             A, p.lm_by_k, first, n16);

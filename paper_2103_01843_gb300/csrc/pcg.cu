@@ -103,7 +103,12 @@ k_precond_reduce(int n_cam, const int32_t* __restrict__ cam_off, const int32_t* 
 // with J_s, r_s the observation's two Jacobian rows and residuals (recomputed
 // here) and T_s, t the camera's 3 x 9 slice and the residual column of the
 // landmark's damped top rows [Q1^T J_p | R1 | Q1^T r]: 30 floats read per
-// observation instead of the 18 k floats of its columns of A_j.
+// observation instead of the 18 k floats of its columns of A_j.  The implicit
+// storage keeps no top rows: there T_s = C_s J_s with the 3 x 2 matrix
+// C_s = G_tt D'_s - (G_tt P) V_s^T (V_s the observation's two Householder
+// rows, 8 floats read; G_tt P and G_tt t from the landmark record, 12 floats,
+// G_tt too for the slots 0 and 1, whose D'_s is non-zero), and the two sums
+// become J_s^T (I - C_s^T C_s) J_s and J_s^T (r_s - C_s^T G_tt t).
 // First pass: one CTA per chunk of up to PG_CHUNK observations of one camera
 // (threads over the observations, each summing its own in order, then a
 // fixed-order CTA reduction) writes the chunk's 54 partial sums.
@@ -115,7 +120,8 @@ k_precond_gram(const int32_t* __restrict__ chunk_cam, const int32_t* __restrict_
                const int32_t* __restrict__ obs_pt_s, const float2* __restrict__ obs_xy_s,
                const int32_t* __restrict__ pt_off, const float* __restrict__ frames, const float* __restrict__ pts,
                const float* __restrict__ tpool, float* __restrict__ part_out, const float* __restrict__ lmrec,
-               const int32_t* __restrict__ lm_pos, float huber, const BatchLm* __restrict__ blm,
+               const int32_t* __restrict__ lm_pos, const int32_t* __restrict__ c_off,
+               const float4* __restrict__ ipool, int64_t n_obs, float huber, const BatchLm* __restrict__ blm,
                const int32_t* __restrict__ cam_prob) {
     __shared__ float part[PG_T / 32][REC_SUMS + 1];
     const int ch = blockIdx.x, cam = chunk_cam[ch];
@@ -137,7 +143,54 @@ k_precond_gram(const int32_t* __restrict__ chunk_cam, const int32_t* __restrict_
         huber_scale_rows(huber, r, Jp, Jl);  // the rows K1 factored
 #pragma unroll
         for (int u = 0; u < 18; ++u) acc[REC_SUMS] += Jp[u] * Jp[u];
-        {
+        if constexpr (IMPLICIT) {
+            // T_s = C J_s with C = G_tt D'_s - (G_tt P) V_s^T (3 x 2; D'_s picks
+            // J_s's rows 0, 1 into top rows 0, 1 for slot 0, row 0 into top row 2
+            // for slot 1), so J_s^T J_s - T_s^T T_s = J_s^T W J_s, W = I - C^T C,
+            // and J_s^T r_s - T_s^T t = J_s^T (r_s - C^T G_tt t)
+            const int slot = s - s0;
+            const int64_t so = (int64_t)(c_off[j] >> 1) + slot;
+            const float4 c4 = __ldg(ipool + 4 * n_obs + so), c5 = __ldg(ipool + 5 * n_obs + so);
+            const float va[3] = {c4.z, c4.w, c5.x}, vb[3] = {c5.y, c5.z, c5.w};  // V rows 2 slot, 2 slot + 1
+            const float4* Lr = reinterpret_cast<const float4*>(lmrec + (int64_t)LM_REC * lm_pos[j]);
+            static_assert(LR_GP == 12 && LR_GT == 21 && LR_G == 24, "record");
+            const float4 g0 = __ldg(Lr + 3), g1 = __ldg(Lr + 4), g2 = __ldg(Lr + 5);
+            const float GP[9] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g2.x};
+            const float Gt[3] = {g2.y, g2.z, g2.w};
+            float C[3][2];
+#pragma unroll
+            for (int row = 0; row < 3; ++row) {
+                C[row][0] = -(GP[3 * row] * va[0] + GP[3 * row + 1] * va[1] + GP[3 * row + 2] * va[2]);
+                C[row][1] = -(GP[3 * row] * vb[0] + GP[3 * row + 1] * vb[1] + GP[3 * row + 2] * vb[2]);
+            }
+            if (slot < 2) {
+                const float4 h0 = __ldg(Lr + 6), h1 = __ldg(Lr + 7), h2 = __ldg(Lr + 8);
+                const float G[9] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w, h2.x};
+#pragma unroll
+                for (int row = 0; row < 3; ++row) {
+                    C[row][0] += slot == 0 ? G[3 * row] : G[3 * row + 2];
+                    C[row][1] += slot == 0 ? G[3 * row + 1] : 0.f;
+                }
+            }
+            const float w00 = 1.f - (C[0][0] * C[0][0] + C[1][0] * C[1][0] + C[2][0] * C[2][0]);
+            const float w01 = -(C[0][0] * C[0][1] + C[1][0] * C[1][1] + C[2][0] * C[2][1]);
+            const float w11 = 1.f - (C[0][1] * C[0][1] + C[1][1] * C[1][1] + C[2][1] * C[2][1]);
+            const float q0 = r[0] - (C[0][0] * Gt[0] + C[1][0] * Gt[1] + C[2][0] * Gt[2]);
+            const float q1 = r[1] - (C[0][1] * Gt[0] + C[1][1] * Gt[1] + C[2][1] * Gt[2]);
+            float y0[9], y1[9];  // W J_s
+#pragma unroll
+            for (int c = 0; c < 9; ++c) {
+                y0[c] = w00 * Jp[c] + w01 * Jp[9 + c];
+                y1[c] = w01 * Jp[c] + w11 * Jp[9 + c];
+            }
+            int q = 0;
+#pragma unroll
+            for (int u = 0; u < 9; ++u) {
+                acc[45 + u] += Jp[u] * q0 + Jp[9 + u] * q1;
+#pragma unroll
+                for (int v = u; v < 9; ++v) acc[q++] += Jp[u] * y0[v] + Jp[9 + u] * y1[v];
+            }
+        } else {
             int q = 0;
 #pragma unroll
             for (int u = 0; u < 9; ++u) {
@@ -145,42 +198,22 @@ k_precond_gram(const int32_t* __restrict__ chunk_cam, const int32_t* __restrict_
 #pragma unroll
                 for (int v = u; v < 9; ++v) acc[q++] += Jp[u] * Jp[v] + Jp[9 + u] * Jp[9 + v];
             }
-        }
-        const int stride = 9 * k + 4;
-        const float* top = tpool + top_offset(s0, j) + 9 * (s - s0);
-        float T3[3][10];  // the camera's 3 x 9 slice of the top rows and the residual column
+            // the camera's 3 x 9 slice of the damped top rows and the residual column
+            const int stride = 9 * k + 4;
+            const float* top = tpool + top_offset(s0, j) + 9 * (s - s0);
 #pragma unroll
-        for (int row = 0; row < 3; ++row) {
+            for (int row = 0; row < 3; ++row) {
+                float T[9];
 #pragma unroll
-            for (int c = 0; c < 9; ++c) T3[row][c] = __ldg(top + row * stride + c);
-            T3[row][9] = __ldg(top + row * stride + 9 * (k - (s - s0)) + 3);
-        }
-        if (IMPLICIT) {
-            // implicit storage: the top rows are undamped; the damped ones are G_tt times them
-            const float* G = lmrec + (int64_t)LM_REC * lm_pos[j] + 16;
-            float Gm[9];
+                for (int c = 0; c < 9; ++c) T[c] = __ldg(top + row * stride + c);
+                const float t = __ldg(top + row * stride + 9 * (k - (s - s0)) + 3);
+                q = 0;
 #pragma unroll
-            for (int q = 0; q < 9; ++q) Gm[q] = __ldg(G + q);
+                for (int u = 0; u < 9; ++u) {
+                    acc[45 + u] -= T[u] * t;
 #pragma unroll
-            for (int c = 0; c < 10; ++c) {
-                const float a0 = T3[0][c], a1 = T3[1][c], a2 = T3[2][c];
-                T3[0][c] = Gm[0] * a0 + Gm[1] * a1 + Gm[2] * a2;
-                T3[1][c] = Gm[3] * a0 + Gm[4] * a1 + Gm[5] * a2;
-                T3[2][c] = Gm[6] * a0 + Gm[7] * a1 + Gm[8] * a2;
-            }
-        }
-#pragma unroll
-        for (int row = 0; row < 3; ++row) {
-            float T[9];
-#pragma unroll
-            for (int c = 0; c < 9; ++c) T[c] = T3[row][c];
-            const float t = T3[row][9];
-            int q = 0;
-#pragma unroll
-            for (int u = 0; u < 9; ++u) {
-                acc[45 + u] -= T[u] * t;
-#pragma unroll
-                for (int v = u; v < 9; ++v) acc[q++] -= T[u] * T[v];
+                    for (int v = u; v < 9; ++v) acc[q++] -= T[u] * T[v];
+                }
             }
         }
     }
@@ -685,8 +718,8 @@ void launch_precond_rhs(Problem& p) {
         if (p.pg_chunks > 0)
             (p.implicit ? k_precond_gram<true> : k_precond_gram<false>)<<<p.pg_chunks, PG_T, 0, p.stream>>>(
                 p.pg_chunk_cam, p.pg_chunk_off, p.cam_off, p.cam_list, p.obs_pt_s, p.obs_xy_s, p.pt_off, p.frames,
-                p.pts, p.tpool, p.pg_part, lmrec, p.lm_pos, (float)p.opt.huber_delta,
-                p.batch.n_prob > 0 ? p.batch.lm : nullptr, p.batch.cam_prob);
+                p.pts, p.tpool, p.pg_part, lmrec, p.lm_pos, p.c_off, reinterpret_cast<const float4*>(p.ipool),
+                p.n_obs, (float)p.opt.huber_delta, p.batch.n_prob > 0 ? p.batch.lm : nullptr, p.batch.cam_prob);
         k_precond_gram_finish<<<p.n_cam, 32, 0, p.stream>>>(
             p.pg_chunk_off, p.pg_part, p.dp2, (float)p.lambda_damped, p.batch.lam, p.batch.cam_prob, p.mdiag, p.minv,
             p.g, p.err, p.cam_off, p.cam_list, p.obs_pt_s, p.pt_off, p.a_off, p.c_off, p.apool, p.cpool, p.lm_pos,

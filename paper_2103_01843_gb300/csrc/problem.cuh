@@ -167,11 +167,11 @@ struct Problem {
     // implicit storage (ba_options.implicit_blocks): per observation in storage
     // order 24 floats as 6 float4 chunks (chunk m of observation so at float4
     // index m n_obs + so): J_s rows (18) and Householder rows (6); residuals
-    // (2 per observation, storage order); per storage position LM_REC floats:
-    // [0..5] Tm (upper: 00 01 02 11 12 22), [6..11] S (same order), [16..24]
-    // G_tt (row-major), [25..30] damped R (upper) (written by K2), [32..37]
-    // undamped R1 (upper), [38..40] D_l^2 (written by K1); the top block stays
-    // undamped
+    // (2 per observation, storage order); per storage position LM_REC floats
+    // (the LR_* offsets below).  The top rows [Q1^T J_p | R1 | Q1^T r] are not
+    // stored: camera s's 3 x 9 slice is D_s - P (V_s^T J_s), with D_s the
+    // rows 0..2 of J_p in its columns (J_s itself for slot 0, J_s's first row
+    // in row 2 for slot 1, zero otherwise) and P = V[0:3, :] Tm^T
     bool implicit = false;
     float *ipool = nullptr, *rpool = nullptr, *lmrec = nullptr;
     int32_t* lm_pos = nullptr;       // storage position of every landmark
@@ -290,6 +290,7 @@ void launch_schur_backsub(Problem& p);
 void launch_camera_diag(Problem& p);  // D_p^2 alone (linearize.cu)
 void configure_implicit(Problem& p);
 void launch_matvec_implicit(Problem& p, const float* v, float* y, const PcgScalars* S);
+void launch_implicit_top_rows(Problem& p, int j, int k, float* top);  // export: landmark j's undamped top rows
 void launch_precond_records(Problem& p);
 int matvec_ctas_per_sm();
 // K6: back substitution + model cost (backsub.cu)
@@ -313,7 +314,18 @@ bool matvec_y_in_smem(const Problem& p);  // the matvec plan in use accumulates 
 int matvec_stage_bytes();
 
 constexpr int PG_CHUNK = 256;  // observations per chunk of the Gram-form K3
-constexpr int LM_REC = 48;     // floats per landmark record of the implicit storage (16-byte aligned)
+// landmark record of the implicit storage (16-byte aligned groups)
+constexpr int LM_REC = 64;     // floats per landmark
+constexpr int LR_TM = 0;       // Tm, upper (00 01 02 11 12 22)                      K1
+constexpr int LR_S = 6;        // S = G_dt^T G_dt, same order                          K2
+constexpr int LR_GP = 12;      // G_tt P, row-major                                   K2
+constexpr int LR_GT = 21;      // G_tt t (the damped Q1^T r)                          K2
+constexpr int LR_G = 24;       // G_tt, row-major (undamped -> damped top rows)      K2
+constexpr int LR_RD = 33;      // damped R, upper                                     K2
+constexpr int LR_R1 = 40;      // undamped R1, upper                                  K1
+constexpr int LR_DL2 = 46;     // D_l^2                                               K1
+constexpr int LR_T = 49;       // t = Q1^T r (undamped)                               K1
+constexpr int LR_P = 52;       // P = V[0:3, :] Tm^T, row-major                       K1
 
 // kernel launch counter (not counted while a graph is being captured)
 inline void count_launches(Problem& p, int n) {

@@ -11,6 +11,8 @@ through the C ABI, against the FP64 oracle.
   the block-Jacobi blocks matches the oracle, and where its subtraction would
   cancel the camera's block is summed from the stored square-root blocks
   (reported in precond_exact); no block falls back to its diagonal.
+* The same landmarks in the implicit storage (top rows rebuilt from the
+  records).
 * Bounded device waits that run out reach the caller as BA_ERR_TIMEOUT, and
   the handle then solves cleanly.
 """
@@ -99,6 +101,50 @@ def test_degenerate_back_substitution_and_lm(pkg, degen):
     with pkg.Problem.from_scene(s, max_lm_iters=10) as p:
         reps = p.solve()
     assert abs(_final(reps) - _final(ref)) <= 1e-3 * _final(ref), (_final(reps), _final(ref))
+
+
+@pytest.mark.parametrize("lam", [1e-4, 1e-8])
+def test_degenerate_landmarks_in_the_implicit_storage(pkg, degen, lam):
+    """The same degenerate landmarks through the implicit storage (K1 with a
+    thread per landmark for k <= 8, the top rows rebuilt from the records):
+    the undamped top rows against the stored form's (the zero depth column
+    stays exactly zero), the reduced system, blocks and back substitution
+    against the oracle, the cancellation guard taken, no diagonal fallback."""
+    s, sp = degen
+    sr = Rounded(s)
+    with pkg.Problem.from_scene(s, implicit_blocks=1, cg_eta=1e-6) as p, pkg.Problem.from_scene(s) as q:
+        p.linearize()
+        q.linearize()
+        for name in ("axis", "same_centre", "near"):
+            a = p.export_landmark(sp[name], top_only=True)
+            b = q.export_landmark(sp[name])
+            assert rel_fro(a["top"], b["top"]) < 1e-5, name
+        k = p.export_landmark(sp["axis"], top_only=True)["k"]
+        R = p.export_landmark(sp["axis"], top_only=True)["top"][:, 9 * k:9 * k + 3]
+        assert np.all(R[:, 2] == 0.0)
+        p.marginalize_qr(lam)
+        rep = p.pcg_solve()
+        M, g = p.export_rcs_diag()
+        V = np.random.default_rng(4).normal(size=(3, 9 * s.n_cam)).astype(np.float32)
+        Y = np.stack([p.matvec(v) for v in V])
+        p.backsubstitute()
+        dp, dl = p.export_step()
+    H_ref, bt_ref = oracle.rcs_dense(sr, lam)
+    assert rel_fro(Y, V.astype(np.float64) @ H_ref.T) < 1e-4
+    assert rel_fro(g.ravel(), -bt_ref) < 1e-4
+    for i in range(s.n_cam):
+        assert rel_fro(M[i], H_ref[9 * i:9 * i + 9, 9 * i:9 * i + 9]) < 1e-4, i
+    assert rep["precond_fallbacks"] == 0 and rep["precond_exact"] >= 1
+    dl_ref, _ = oracle.backsub_given(sr, lam, dp.astype(np.float64))
+    # at lambda = 1e-8 a rank-deficient landmark's dl along its null direction
+    # is fixed by the damping alone (condition ~ 1 / (sqrt(lambda) D_l)): FP32
+    # rounding is amplified ~1e4 there, so those three are compared at 1e-4 only
+    keep = np.ones(s.n_pt, bool)
+    if lam < 1e-4:
+        keep[[sp["axis"], sp["same_centre"], sp["near"]]] = False
+    err = np.linalg.norm(dl - dl_ref, axis=1)
+    worst = int(np.argmax(np.where(keep, err, 0.0)))
+    assert rel_fro(dl[keep], dl_ref[keep]) < 1e-4, (worst, dl[worst], dl_ref[worst], sp)
 
 
 @pytest.mark.parametrize("lam", [1e-8, 1e-4])

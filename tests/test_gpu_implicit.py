@@ -184,6 +184,24 @@ def test_many_cameras_y_in_global_memory(pkg):
     assert rel_fro(Y, oracle.rcs_matvec(s, lam, V)) < 1e-4
 
 
+def test_rebuilt_top_rows_match_the_stored_form(pkg, scene):
+    """The implicit storage keeps no top rows [Q1^T J_p | R1 | Q1^T r]; the
+    export rebuilds them from the records (D_s - P V_s^T J_s, R1, Q1^T r),
+    the way K3 and the back substitution do.  Against the stored form's rows
+    (the same Householder reflections), undamped, on landmarks of every k."""
+    name, sc = scene
+    with pkg.Problem.from_scene(sc, implicit_blocks=1) as p, pkg.Problem.from_scene(sc) as q:
+        p.linearize()
+        q.linearize()
+        ks = np.bincount(sc.obs_pt, minlength=sc.n_pt)  # observations per landmark
+        js = sorted({int(np.argmax(ks))} | {int(np.flatnonzero(ks == k)[0]) for k in np.unique(ks)[:12]})
+        for j in js:
+            a = p.export_landmark(j, k_cap=int(ks.max()), top_only=True)["top"]
+            b = q.export_landmark(j, k_cap=int(ks.max()))["top"]
+            assert a.shape == b.shape and a.size == 3 * (9 * ks[j] + 4)
+            assert rel_fro(a, b) < 1e-5, (name, j, int(ks[j]), rel_fro(a, b))
+
+
 def test_option_is_fixed_at_create(pkg):
     tiny = make_scene("tiny", 0)
     with pkg.Problem.from_scene(tiny, implicit_blocks=1) as p:
