@@ -458,62 +458,102 @@ k_linearize_team(LinArgs A, const int32_t* __restrict__ order, int first, int co
     marginalize_landmark<W, (9 * KMAX + W - 1) / W>(A, order[pos], pos, sm, nullptr, active);
 }
 
-// The implicit storage for k <= THR_KMAX: one thread per landmark, the whole
-// 2k x 4 block [J_l | r] in registers.  The record's J_s part is written as
-// each observation is linearised; Householder QR in place (R1 on and above the
-// diagonal, v_a below it with v_a[a] = 1 implied) with the reflectors applied
-// to r directly (Q^T r = H_3 H_2 H_1 r); then Tm, P, R1, Q1^T r and D_l^2 as
-// 16-byte stores and the records' Householder part.  No team reductions and
-// no shared memory: a warp factors 32 landmarks of equal k side by side
-// (landmarks are in decreasing-k order).
-constexpr int THR_KMAX = 8;
+// The implicit storage for k <= 32: register-resident teams of T lanes per
+// landmark (T = 1, 2, 4, 8 for k <= 4, 8, 16, 32), lane r holding the rows of
+// observations s = r, r + T, ... (at most four), so that the whole 2k x 4
+// block [J_l | r] stays in registers.  The record's J_s part is written as each
+// observation is linearised; Householder QR in place (R1 on and above the
+// diagonal, v_a below it with v_a[a] = 1 implied), the reflectors applied to r
+// directly (Q^T r = H_3 H_2 H_1 r); the team sums take log2 T shuffles, the
+// pivot rows come from their owner lane.  A warp's teams all use the k of its
+// first landmark (the largest: landmarks are in decreasing-k order); a shorter
+// landmark's missing observations are zero rows, which leave R1, V's real
+// rows and Q^T r unchanged and write nothing.  Then Tm, P, R1, Q1^T r and D_l^2
+// as 16-byte stores and the records' Householder part.
+template <int T>
+__device__ __forceinline__ float team_sum(float v) {
+#pragma unroll
+    for (int o = T / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 
-template <int K>
-__device__ __forceinline__ void linearize_thread(const LinArgs& A, int j, int pos) {
-    constexpr int NR = 2 * K;
-    const int s0 = A.pt_off[j];
-    const int64_t so0 = A.c_off[j] >> 1, n = A.n_obs;
-    const float X0 = __ldg(A.pts + 3 * j), X1 = __ldg(A.pts + 3 * j + 1), X2 = __ldg(A.pts + 3 * j + 2);
+template <int T, int K>
+__device__ __forceinline__ void linearize_regteam(const LinArgs& A, int j, int pos, bool act) {
+    constexpr int MO = (K + T - 1) / T;  // observations per lane
+    constexpr int MR = 2 * MO;           // rows per lane: local row 2m + e is global row 2 (r + T m) + e
+    const int lane = threadIdx.x & 31, r = lane & (T - 1), base = lane & ~(T - 1);
+    int s0 = 0, k = 0;
+    int64_t so0 = 0;
+    float X0 = 0.f, X1 = 0.f, X2 = 0.f;
+    if (act) {
+        s0 = A.pt_off[j];
+        k = A.pt_off[j + 1] - s0;
+        so0 = A.c_off[j] >> 1;
+        X0 = __ldg(A.pts + 3 * j);
+        X1 = __ldg(A.pts + 3 * j + 1);
+        X2 = __ldg(A.pts + 3 * j + 2);
+    }
+    const int64_t n = A.n_obs;
     float4* __restrict__ ip = reinterpret_cast<float4*>(A.ipool);
-    float B[NR][4];  // [J_l | r] -> [R1 and v_1..v_3 | Q^T r]
-    float jt[K][2];  // J_s entries 16 and 17 (record chunk 4, with the Householder rows)
+    float B[MR][4];  // [J_l | r] -> [R1 and v_1..v_3 | Q^T r], this lane's rows
+    float jt[MO][2];  // J_s entries 16 and 17 (record chunk 4, with the Householder rows)
     float d0 = 0.f, d1 = 0.f, d2 = 0.f;
 #pragma unroll
-    for (int s = 0; s < K; ++s) {
-        const float2 z = A.obs_xy_s[s0 + s];
-        float r[2], Jp[18], Jl[6];
-        frame_jacobians(A.frames + FRAME * A.obs_cam_s[s0 + s], X0, X1, X2, z.x, z.y, r, Jp, Jl);
-        huber_scale_rows(A.huber, r, Jp, Jl);
-        const int64_t so = so0 + s;
+    for (int m = 0; m < MO; ++m) {
+        const int s = r + T * m;
+        if (s < k) {
+            const float2 z = A.obs_xy_s[s0 + s];
+            float rr[2], Jp[18], Jl[6];
+            frame_jacobians(A.frames + FRAME * A.obs_cam_s[s0 + s], X0, X1, X2, z.x, z.y, rr, Jp, Jl);
+            huber_scale_rows(A.huber, rr, Jp, Jl);
+            const int64_t so = so0 + s;
 #pragma unroll
-        for (int m = 0; m < 4; ++m) ip[m * n + so] = make_float4(Jp[4 * m], Jp[4 * m + 1], Jp[4 * m + 2], Jp[4 * m + 3]);
-        reinterpret_cast<float2*>(A.rpool)[so] = make_float2(r[0], r[1]);
-        jt[s][0] = Jp[16];
-        jt[s][1] = Jp[17];
+            for (int q = 0; q < 4; ++q)
+                ip[q * n + so] = make_float4(Jp[4 * q], Jp[4 * q + 1], Jp[4 * q + 2], Jp[4 * q + 3]);
+            reinterpret_cast<float2*>(A.rpool)[so] = make_float2(rr[0], rr[1]);
+            jt[m][0] = Jp[16];
+            jt[m][1] = Jp[17];
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            B[2 * s + i][0] = Jl[3 * i];
-            B[2 * s + i][1] = Jl[3 * i + 1];
-            B[2 * s + i][2] = Jl[3 * i + 2];
-            B[2 * s + i][3] = r[i];
-            d0 += Jl[3 * i] * Jl[3 * i];
-            d1 += Jl[3 * i + 1] * Jl[3 * i + 1];
-            d2 += Jl[3 * i + 2] * Jl[3 * i + 2];
+            for (int e = 0; e < 2; ++e) {
+                B[2 * m + e][0] = Jl[3 * e];
+                B[2 * m + e][1] = Jl[3 * e + 1];
+                B[2 * m + e][2] = Jl[3 * e + 2];
+                B[2 * m + e][3] = rr[e];
+                d0 += Jl[3 * e] * Jl[3 * e];
+                d1 += Jl[3 * e + 1] * Jl[3 * e + 1];
+                d2 += Jl[3 * e + 2] * Jl[3 * e + 2];
+            }
+        } else {
+            jt[m][0] = jt[m][1] = 0.f;
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) B[2 * m + e][c] = 0.f;
         }
     }
+    d0 = team_sum<T>(d0);
+    d1 = team_sum<T>(d1);
+    d2 = team_sum<T>(d2);
     const float c0 = fminf(fmaxf(d0, 1e-6f), 1e32f), c1 = fminf(fmaxf(d1, 1e-6f), 1e32f),
                 c2 = fminf(fmaxf(d2, 1e-6f), 1e32f);
-    A.dl2[3 * j] = c0;
-    A.dl2[3 * j + 1] = c1;
-    A.dl2[3 * j + 2] = c2;
-    // Householder QR: reflector a acts on rows a..2k-1
+    if (act && r == 0) {
+        A.dl2[3 * j] = c0;
+        A.dl2[3 * j + 1] = c1;
+        A.dl2[3 * j + 2] = c2;
+    }
+    auto grow = [&](int lr) { return 2 * (r + T * (lr >> 1)) + (lr & 1); };  // global row of local row lr
+    // Householder QR: reflector a acts on global rows a..2k-1; pivot row a is
+    // local row pl of lane (a / 2) % T
     float tau[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
+        const int own = (a >> 1) % T, pl = 2 * ((a >> 1) / T) + (a & 1);
         float sg = 0.f;
 #pragma unroll
-        for (int i = a + 1; i < NR; ++i) sg += B[i][a] * B[i][a];
-        const float alpha = B[a][a];
+        for (int lr = 0; lr < MR; ++lr)
+            if (grow(lr) > a) sg += B[lr][a] * B[lr][a];
+        sg = team_sum<T>(sg);
+        const float alpha = __shfl_sync(0xffffffffu, B[pl][a], base + own);
         float t = 0.f, beta = alpha, v0 = 1.f;
         if (sg > 0.f) {
             const float mu = sqrtf(alpha * alpha + sg);
@@ -524,28 +564,43 @@ __device__ __forceinline__ void linearize_thread(const LinArgs& A, int j, int po
         tau[a] = t;
         const float iv = 1.0f / v0;
 #pragma unroll
-        for (int i = a + 1; i < NR; ++i) B[i][a] = t == 0.f ? 0.f : B[i][a] * iv;
-        B[a][a] = beta;
+        for (int lr = 0; lr < MR; ++lr)
+            if (grow(lr) > a) B[lr][a] = t == 0.f ? 0.f : B[lr][a] * iv;
+        if (r == own) B[pl][a] = beta;
+        // w_c = B[a][c] + sum_{i > a} v_i B[i][c] for the columns c > a (and r)
+        float w[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int c = a + 1; c < 4; ++c) {
-            float w = B[a][c];
 #pragma unroll
-            for (int i = a + 1; i < NR; ++i) w += B[i][a] * B[i][c];
-            w *= t;
-            B[a][c] -= w;
+            for (int lr = 0; lr < MR; ++lr)
+                if (grow(lr) > a) w[c - a - 1] += B[lr][a] * B[lr][c];
+            w[c - a - 1] = team_sum<T>(w[c - a - 1]);
+            w[c - a - 1] = t * (w[c - a - 1] + __shfl_sync(0xffffffffu, B[pl][c], base + own));
+        }
 #pragma unroll
-            for (int i = a + 1; i < NR; ++i) B[i][c] -= w * B[i][a];
+        for (int c = a + 1; c < 4; ++c) {
+            const float wc = w[c - a - 1];
+#pragma unroll
+            for (int lr = 0; lr < MR; ++lr)
+                if (grow(lr) > a) B[lr][c] -= wc * B[lr][a];
+            if (r == own) B[pl][c] -= wc;
         }
     }
     // compact WY: H_1 H_2 H_3 = I - V Tm V^T (V(i, a) = 1 at i = a, 0 above)
-    auto V = [&](int i, int a) { return i == a ? 1.f : (i > a ? B[i][a] : 0.f); };
+    auto V = [&](int lr, int a) {
+        const int i = grow(lr);
+        return i == a ? 1.f : (i > a ? B[lr][a] : 0.f);
+    };
     float d01 = 0.f, d02 = 0.f, d12 = 0.f;
 #pragma unroll
-    for (int i = 0; i < NR; ++i) {
-        d01 += V(i, 0) * V(i, 1);
-        d02 += V(i, 0) * V(i, 2);
-        d12 += V(i, 1) * V(i, 2);
+    for (int lr = 0; lr < MR; ++lr) {
+        d01 += V(lr, 0) * V(lr, 1);
+        d02 += V(lr, 0) * V(lr, 2);
+        d12 += V(lr, 1) * V(lr, 2);
     }
+    d01 = team_sum<T>(d01);
+    d02 = team_sum<T>(d02);
+    d12 = team_sum<T>(d12);
     float Tm[3][3];
     Tm[0][0] = tau[0];
     Tm[1][1] = tau[1];
@@ -554,46 +609,66 @@ __device__ __forceinline__ void linearize_thread(const LinArgs& A, int j, int po
     Tm[0][1] = -tau[0] * tau[1] * d01;
     Tm[1][2] = -tau[2] * (tau[1] * d12);
     Tm[0][2] = -tau[2] * (tau[0] * d02 + Tm[0][1] * d12);
-    float P[3][3];  // P = V[0:3, :] Tm^T
+    // rows 0 and 1 live on lane 0 (local rows 0, 1), row 2 on lane 1 % T (local row 2 (1 / T))
+    constexpr int own2 = 1 % T, pl2 = 2 * (1 / T);
+    const float b20 = __shfl_sync(0xffffffffu, B[pl2][0], base + own2);
+    const float b21 = __shfl_sync(0xffffffffu, B[pl2][1], base + own2);
+    const float b22 = __shfl_sync(0xffffffffu, B[pl2][2], base + own2);
+    const float b23 = __shfl_sync(0xffffffffu, B[pl2][3], base + own2);
+    if (act && r == 0) {
+        const float Vt[3][3] = {{1.f, 0.f, 0.f}, {B[1][0], 1.f, 0.f}, {b20, b21, 1.f}};
+        float P[3][3];  // P = V[0:3, :] Tm^T
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) P[i][b] = V(i, 0) * Tm[b][0] + V(i, 1) * Tm[b][1] + V(i, 2) * Tm[b][2];
-    static_assert(LR_TM == 0 && LR_R1 == 40 && LR_DL2 == 46 && LR_T == 49 && LR_P == 52, "record");
-    float4* L4 = reinterpret_cast<float4*>(A.lmrec + (int64_t)LM_REC * pos);
-    L4[0] = make_float4(Tm[0][0], Tm[0][1], Tm[0][2], Tm[1][1]);
-    *reinterpret_cast<float2*>(L4 + 1) = make_float2(Tm[1][2], Tm[2][2]);
-    L4[10] = make_float4(B[0][0], B[0][1], B[0][2], B[1][1]);
-    L4[11] = make_float4(B[1][2], B[2][2], c0, c1);
-    L4[12] = make_float4(c2, B[0][3], B[1][3], B[2][3]);
-    L4[13] = make_float4(P[0][0], P[0][1], P[0][2], P[1][0]);
-    L4[14] = make_float4(P[1][1], P[1][2], P[2][0], P[2][1]);
-    L4[15] = make_float4(P[2][2], 0.f, 0.f, 0.f);
+            for (int b = 0; b < 3; ++b) P[i][b] = Vt[i][0] * Tm[b][0] + Vt[i][1] * Tm[b][1] + Vt[i][2] * Tm[b][2];
+        static_assert(LR_TM == 0 && LR_R1 == 40 && LR_DL2 == 46 && LR_T == 49 && LR_P == 52, "record");
+        float4* L4 = reinterpret_cast<float4*>(A.lmrec + (int64_t)LM_REC * pos);
+        L4[0] = make_float4(Tm[0][0], Tm[0][1], Tm[0][2], Tm[1][1]);
+        *reinterpret_cast<float2*>(L4 + 1) = make_float2(Tm[1][2], Tm[2][2]);
+        L4[10] = make_float4(B[0][0], B[0][1], B[0][2], B[1][1]);
+        L4[11] = make_float4(B[1][2], b22, c0, c1);
+        L4[12] = make_float4(c2, B[0][3], B[1][3], b23);
+        L4[13] = make_float4(P[0][0], P[0][1], P[0][2], P[1][0]);
+        L4[14] = make_float4(P[1][1], P[1][2], P[2][0], P[2][1]);
+        L4[15] = make_float4(P[2][2], 0.f, 0.f, 0.f);
+    }
 #pragma unroll
-    for (int s = 0; s < K; ++s) {
-        const int i = 2 * s;
-        ip[4 * n + so0 + s] = make_float4(jt[s][0], jt[s][1], V(i, 0), V(i, 1));
-        ip[5 * n + so0 + s] = make_float4(V(i, 2), V(i + 1, 0), V(i + 1, 1), V(i + 1, 2));
+    for (int m = 0; m < MO; ++m) {
+        const int s = r + T * m;
+        if (s < k) {
+            const int lr = 2 * m;
+            ip[4 * n + so0 + s] = make_float4(jt[m][0], jt[m][1], V(lr, 0), V(lr, 1));
+            ip[5 * n + so0 + s] = make_float4(V(lr, 2), V(lr + 1, 0), V(lr + 1, 1), V(lr + 1, 2));
+        }
     }
 }
 
-// landmarks order[first .. first + count) with 2 <= k <= THR_KMAX, one thread each
-__global__ void __launch_bounds__(128)
-k_linearize_thread(LinArgs A, const int32_t* __restrict__ order, int first, int count) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= count) return;
-    const int pos = first + idx, j = order[pos];
-    if (A.blm && !batch_relin(A.blm, A.lm_prob[j])) return;
-    switch (A.pt_off[j + 1] - A.pt_off[j]) {
-        case 2: linearize_thread<2>(A, j, pos); break;
-        case 3: linearize_thread<3>(A, j, pos); break;
-        case 4: linearize_thread<4>(A, j, pos); break;
-        case 5: linearize_thread<5>(A, j, pos); break;
-        case 6: linearize_thread<6>(A, j, pos); break;
-        case 7: linearize_thread<7>(A, j, pos); break;
-        case 8: linearize_thread<8>(A, j, pos); break;
-        default: break;
+template <int T, int KLO, int KHI>
+__device__ __forceinline__ void linearize_regteam_k(int kw, const LinArgs& A, int j, int pos, bool act) {
+    if constexpr (KLO <= KHI) {
+        if (kw == KLO) linearize_regteam<T, KLO>(A, j, pos, act);
+        else linearize_regteam_k<T, KLO + 1, KHI>(kw, A, j, pos, act);
     }
+}
+
+// landmarks order[first .. first + count) with KLO <= k <= KHI, teams of T lanes
+template <int T, int KLO, int KHI>
+__global__ void __launch_bounds__(128)
+k_linearize_reg(LinArgs A, const int32_t* __restrict__ order, int first, int count) {
+    constexpr int TPW = 32 / T;
+    const int lane = threadIdx.x & 31;
+    const int idx0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * TPW;
+    if (idx0 >= count) return;  // whole warp
+    const int idx = idx0 + lane / T;
+    bool act = idx < count;
+    const int pos = first + (act ? idx : idx0);
+    const int j = order[pos];
+    // a batch re-linearises only the problems whose last step was accepted
+    if (act && A.blm && !batch_relin(A.blm, A.lm_prob[j])) act = false;
+    const int j0 = order[first + idx0];  // the warp's largest k (uniform over the warp)
+    const int kw = A.pt_off[j0 + 1] - A.pt_off[j0];
+    linearize_regteam_k<T, KLO, KHI>(kw, A, j, pos, act);
 }
 
 __global__ void __launch_bounds__(BIG_TEAM)
@@ -716,8 +791,7 @@ void launch_linearize(Problem& p) {
               p.dl2, p.implicit ? p.ipool : nullptr, p.rpool, p.lmrec, p.n_obs, (float)p.opt.huber_delta,
               p.batch.n_prob > 0 ? p.batch.lm : nullptr, p.batch.lm_prob};
     // segments of lm_by_k: k > 32 | 9..32 | 5..8 | 2..4
-    const int n_big = p.n_big, n32 = count_k(p, 8, 32);
-    int n16 = count_k(p, 4, 8), n8 = count_k(p, 1, 4);
+    const int n_big = p.n_big, n32 = count_k(p, 8, 32), n16 = count_k(p, 4, 8), n8 = count_k(p, 1, 4);
     BA_CUDA_TRY(cudaEventRecord(p.ev_fork, p.stream));
     BA_CUDA_TRY(cudaStreamWaitEvent(p.side, p.ev_fork, 0));
     // side: D_p^2, then the landmarks with k > 32 (one CTA each)
@@ -730,29 +804,38 @@ void launch_linearize(Problem& p) {
         k_linearize_block<<<n_big, BIG_TEAM, sm, p.side>>>(A, p.lm_by_k, n_big);
         count_launches(p, 1);
     }
-    int first = n_big;
-    if (n32 > 0) {
-        k_linearize_team<32, 32><<<ceil_div(n32, LIN_WARPS), 32 * LIN_WARPS, team_smem_bytes<32, 32>(), p.stream>>>(
-            A, p.lm_by_k, first, n32);
-        count_launches(p, 1);
-    }
-    first += n32;
-    if (p.implicit && n16 + n8 > 0) {  // k <= 8: a thread per landmark
-        static_assert(THR_KMAX == 8, "segments");
-        k_linearize_thread<<<ceil_div(n16 + n8, 128), 128, 0, p.stream>>>(A, p.lm_by_k, first, n16 + n8);
-        count_launches(p, 1);
-        n16 = n8 = 0;
-    }
-    if (n16 > 0) {
-        k_linearize_team<16, 8><<<ceil_div(n16, 2 * LIN_WARPS), 32 * LIN_WARPS, team_smem_bytes<16, 8>(), p.stream>>>(
-            A, p.lm_by_k, first, n16);
-        count_launches(p, 1);
-    }
-    first += n16;
-    if (n8 > 0) {
-        k_linearize_team<8, 4><<<ceil_div(n8, 4 * LIN_WARPS), 32 * LIN_WARPS, team_smem_bytes<8, 4>(), p.stream>>>(
-            A, p.lm_by_k, first, n8);
-        count_launches(p, 1);
+    if (p.implicit) {
+        // register-resident teams of 8, 4, 2 and 1 lanes: k 17..32, 9..16, 5..8, 2..4
+        const int c17 = count_k(p, 16, 32), c9 = count_k(p, 8, 16), c5 = count_k(p, 4, 8), c2 = count_k(p, 1, 4);
+        auto grid = [](int cnt, int t) { return ceil_div((int64_t)cnt * t, 128); };
+        int f = n_big;
+        if (c17 > 0) k_linearize_reg<8, 17, 32><<<grid(c17, 8), 128, 0, p.stream>>>(A, p.lm_by_k, f, c17);
+        f += c17;
+        if (c9 > 0) k_linearize_reg<4, 9, 16><<<grid(c9, 4), 128, 0, p.stream>>>(A, p.lm_by_k, f, c9);
+        f += c9;
+        if (c5 > 0) k_linearize_reg<2, 5, 8><<<grid(c5, 2), 128, 0, p.stream>>>(A, p.lm_by_k, f, c5);
+        f += c5;
+        if (c2 > 0) k_linearize_reg<1, 2, 4><<<grid(c2, 1), 128, 0, p.stream>>>(A, p.lm_by_k, f, c2);
+        count_launches(p, (c17 > 0) + (c9 > 0) + (c5 > 0) + (c2 > 0));
+    } else {
+        int first = n_big;
+        if (n32 > 0) {
+            k_linearize_team<32, 32><<<ceil_div(n32, LIN_WARPS), 32 * LIN_WARPS, team_smem_bytes<32, 32>(),
+                                       p.stream>>>(A, p.lm_by_k, first, n32);
+            count_launches(p, 1);
+        }
+        first += n32;
+        if (n16 > 0) {
+            k_linearize_team<16, 8><<<ceil_div(n16, 2 * LIN_WARPS), 32 * LIN_WARPS, team_smem_bytes<16, 8>(),
+                                      p.stream>>>(A, p.lm_by_k, first, n16);
+            count_launches(p, 1);
+        }
+        first += n16;
+        if (n8 > 0) {
+            k_linearize_team<8, 4><<<ceil_div(n8, 4 * LIN_WARPS), 32 * LIN_WARPS, team_smem_bytes<8, 4>(),
+                                     p.stream>>>(A, p.lm_by_k, first, n8);
+            count_launches(p, 1);
+        }
     }
     BA_LAUNCH_CHECK();
     BA_CUDA_TRY(cudaEventRecord(p.ev_join, p.side));
