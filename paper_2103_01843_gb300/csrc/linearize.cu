@@ -652,13 +652,14 @@ __device__ __forceinline__ void linearize_regteam_k(int kw, const LinArgs& A, in
     }
 }
 
-// landmarks order[first .. first + count) with KLO <= k <= KHI, teams of T lanes
+// landmarks order[first .. first + count) with KLO <= k <= KHI, teams of T
+// lanes; `cta` is the CTA's index within its segment
 template <int T, int KLO, int KHI>
-__global__ void __launch_bounds__(128)
-k_linearize_reg(LinArgs A, const int32_t* __restrict__ order, int first, int count) {
+__device__ __forceinline__ void linearize_reg_segment(const LinArgs& A, const int32_t* __restrict__ order, int first,
+                                                      int count, int cta) {
     constexpr int TPW = 32 / T;
     const int lane = threadIdx.x & 31;
-    const int idx0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * TPW;
+    const int idx0 = ((cta * blockDim.x + threadIdx.x) >> 5) * TPW;
     if (idx0 >= count) return;  // whole warp
     const int idx = idx0 + lane / T;
     bool act = idx < count;
@@ -669,6 +670,22 @@ k_linearize_reg(LinArgs A, const int32_t* __restrict__ order, int first, int cou
     const int j0 = order[first + idx0];  // the warp's largest k (uniform over the warp)
     const int kw = A.pt_off[j0 + 1] - A.pt_off[j0];
     linearize_regteam_k<T, KLO, KHI>(kw, A, j, pos, act);
+}
+
+// The four segments k 17..32, 9..16, 5..8, 2..4 (teams of 8, 4, 2, 1 lanes) in
+// one grid, longest k first, so that their per-warp latencies overlap: a
+// CTA's segment is fixed by its index (uniform over the CTA).
+struct RegSegments {
+    int first[4], count[4], cta_end[4];
+};
+
+__global__ void __launch_bounds__(128)
+k_linearize_reg(LinArgs A, const int32_t* __restrict__ order, RegSegments g) {
+    const int b = blockIdx.x;
+    if (b < g.cta_end[0]) linearize_reg_segment<8, 17, 32>(A, order, g.first[0], g.count[0], b);
+    else if (b < g.cta_end[1]) linearize_reg_segment<4, 9, 16>(A, order, g.first[1], g.count[1], b - g.cta_end[0]);
+    else if (b < g.cta_end[2]) linearize_reg_segment<2, 5, 8>(A, order, g.first[2], g.count[2], b - g.cta_end[1]);
+    else linearize_reg_segment<1, 2, 4>(A, order, g.first[3], g.count[3], b - g.cta_end[2]);
 }
 
 __global__ void __launch_bounds__(BIG_TEAM)
@@ -805,18 +822,22 @@ void launch_linearize(Problem& p) {
         count_launches(p, 1);
     }
     if (p.implicit) {
-        // register-resident teams of 8, 4, 2 and 1 lanes: k 17..32, 9..16, 5..8, 2..4
-        const int c17 = count_k(p, 16, 32), c9 = count_k(p, 8, 16), c5 = count_k(p, 4, 8), c2 = count_k(p, 1, 4);
-        auto grid = [](int cnt, int t) { return ceil_div((int64_t)cnt * t, 128); };
-        int f = n_big;
-        if (c17 > 0) k_linearize_reg<8, 17, 32><<<grid(c17, 8), 128, 0, p.stream>>>(A, p.lm_by_k, f, c17);
-        f += c17;
-        if (c9 > 0) k_linearize_reg<4, 9, 16><<<grid(c9, 4), 128, 0, p.stream>>>(A, p.lm_by_k, f, c9);
-        f += c9;
-        if (c5 > 0) k_linearize_reg<2, 5, 8><<<grid(c5, 2), 128, 0, p.stream>>>(A, p.lm_by_k, f, c5);
-        f += c5;
-        if (c2 > 0) k_linearize_reg<1, 2, 4><<<grid(c2, 1), 128, 0, p.stream>>>(A, p.lm_by_k, f, c2);
-        count_launches(p, (c17 > 0) + (c9 > 0) + (c5 > 0) + (c2 > 0));
+        // register-resident teams of 8, 4, 2 and 1 lanes: k 17..32, 9..16, 5..8, 2..4, one grid
+        RegSegments g{};
+        const int cnt[4] = {count_k(p, 16, 32), count_k(p, 8, 16), count_k(p, 4, 8), count_k(p, 1, 4)};
+        const int lanes[4] = {8, 4, 2, 1};
+        int f = n_big, ctas = 0;
+        for (int q = 0; q < 4; ++q) {
+            g.first[q] = f;
+            g.count[q] = cnt[q];
+            f += cnt[q];
+            ctas += ceil_div((int64_t)cnt[q] * lanes[q], 128);
+            g.cta_end[q] = ctas;
+        }
+        if (ctas > 0) {
+            k_linearize_reg<<<ctas, 128, 0, p.stream>>>(A, p.lm_by_k, g);
+            count_launches(p, 1);
+        }
     } else {
         int first = n_big;
         if (n32 > 0) {
