@@ -251,25 +251,26 @@ k_cost(int64_t n_obs, const float* __restrict__ frames, const float* __restrict_
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
-__global__ void __launch_bounds__(1024)
+// Fixed-order FP64 sums of the per-CTA partials by one warp: lane l adds
+// partials l, l + 32, ... in order, then a fixed butterfly (deterministic; one
+// warp keeps the FP64 instruction count and the latency chain short).
+__global__ void __launch_bounds__(32)
 k_sum_partials(const double* __restrict__ partials, int n, double* out) {
-    __shared__ double red[32];
     double acc = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partials[i];
-    acc = block_sum_d(acc, red);
+    for (int i = threadIdx.x; i < n; i += 32) acc += partials[i];
+    acc = warp_sum_d(acc);
     if (threadIdx.x == 0) *out = acc;
 }
 
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(32)
 k_sum_partials2(const double* __restrict__ a, const double* __restrict__ b, int n, double* out_a, double* out_b) {
-    __shared__ double red[32];
     double sa = 0.0, sb = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int i = threadIdx.x; i < n; i += 32) {
         sa += a[i];
         sb += b[i];
     }
-    sa = block_sum_d(sa, red);
-    sb = block_sum_d(sb, red);
+    sa = warp_sum_d(sa);
+    sb = warp_sum_d(sb);
     if (threadIdx.x == 0) {
         *out_a = sa;
         *out_b = sb;
@@ -320,7 +321,7 @@ void launch_backsub(Problem& p) {
         launch_backsub_dl(p);
     k_model_cost<<<p.red_grid, 256, 0, p.stream>>>(p.n_obs, p.frames, p.pts, p.obs_cam_s, p.obs_pt_s, p.obs_xy_s, p.x,
                                                    p.dl, nullptr, nullptr, p.partials, nullptr, (float)p.opt.huber_delta);
-    k_sum_partials<<<1, 1024, 0, p.stream>>>(p.partials, p.red_grid, p.dsum + 1);
+    k_sum_partials<<<1, 32, 0, p.stream>>>(p.partials, p.red_grid, p.dsum + 1);
     BA_LAUNCH_CHECK();
 }
 
@@ -343,7 +344,7 @@ void launch_backsub_candidate_cost(Problem& p) {
         k_model_cost<<<p.red_grid, 256, 0, p.stream>>>(p.n_obs, p.frames, p.pts, p.obs_cam_s, p.obs_pt_s, p.obs_xy_s,
                                                        p.x, p.dl, p.cand_frames, p.cand_pts, p.partials,
                                                        p.partials + p.red_grid, (float)p.opt.huber_delta);
-        k_sum_partials2<<<1, 1024, 0, p.stream>>>(p.partials, p.partials + p.red_grid, p.red_grid, p.dsum + 1,
+        k_sum_partials2<<<1, 32, 0, p.stream>>>(p.partials, p.partials + p.red_grid, p.red_grid, p.dsum + 1,
                                                   p.dsum + 0);
     }
     BA_LAUNCH_CHECK();
@@ -365,7 +366,7 @@ void launch_cost(Problem& p, bool candidate, int slot) {
     k_cost<<<p.red_grid, 256, 0, p.stream>>>(p.n_obs, candidate ? p.cand_frames : p.frames,
                                              candidate ? p.cand_pts : p.pts, p.obs_cam_s, p.obs_pt_s,
                                              p.obs_xy_s, p.partials, (float)p.opt.huber_delta);
-    k_sum_partials<<<1, 1024, 0, p.stream>>>(p.partials, p.red_grid, p.dsum + slot);
+    k_sum_partials<<<1, 32, 0, p.stream>>>(p.partials, p.red_grid, p.dsum + slot);
     BA_LAUNCH_CHECK();
 }
 

@@ -505,10 +505,10 @@ void pcg_start(Problem& p) {
     require(!learned || p.batch.n_prob == 0, BA_ERR_INVALID_ARG, "the learned mode solves single problems");
     if (p.opt.autotune && !p.tuned) run_autotune(p, nullptr);
     PhaseTimer t(p, PROF_PRECOND);
-    launch_precond_rhs(p);
+    const bool fused = launch_precond_rhs(p, !learned);
     p.learned_active = learned;
     if (learned) start_learned(p);
-    else launch_pcg_init(p);
+    else if (!fused) launch_pcg_init(p);
     t.end();
 }
 

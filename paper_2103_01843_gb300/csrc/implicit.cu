@@ -2,11 +2,12 @@
 // tab:complexities that keeps the factorisation of each landmark block
 // instead of Q2^T J_p.  Per observation (storage order, 24 floats): its two
 // pose Jacobian rows J_s (2 x 9) and its two rows of the Householder vectors
-// V (2 x 3); per landmark (storage position, 32 floats): the compact-WY
+// V (2 x 3); per landmark (storage position, LM_REC floats): the compact-WY
 // factor Tm (Q^T = I - V Tm^T V^T, upper triangular) and, after the landmark
 // damping, S = G_dt^T G_dt, G_tt and the damped R (the 6 Givens rotations G of
 // Sec. 5.3 act on the 3 top rows and the 3 damping rows; G_tt / G_dt are the
 // blocks of G that map the undamped top rows to the new top / damping rows).
+// The matvec reads Tm and S (48 bytes) of the record.
 //
 // Products with A_j = the rows of Q^ T [J_p; 0] below the top rows:
 //     A_j^T A_j v = J_p^T Q diag(S, I) Q^T J_p v
@@ -14,15 +15,16 @@
 // after the rotations the top rows are dropped (Eq. reduced), the damping rows
 // keep G_dt times the top entries, so the top three entries of Q^T u enter
 // through S and all others unchanged.  Per landmark: u = J_p v (2k), two
-// reductions over its rows (V^T u, V^T z), no block is formed.  Reads 96 bytes
-// per observation and 64 per landmark instead of 72 k bytes per observation.
+// reductions over its rows (V^T u, V^T z), no block is formed.  Reads 100 bytes
+// per observation and 48 per landmark instead of 72 k bytes per observation.
 //
 // Work: warps over tasks of landmarks of equal k in storage order (decreasing
 // k); k <= 32: teams of W = 2, 4, 8, 16 or 32 lanes (W >= k), one landmark per
 // team and one observation per lane; k > 32: one warp per landmark, lanes over
 // its observations in chunks of 32 (three passes over the records).  y is
 // accumulated in shared memory when it fits (9 n_cam floats), flushed once per
-// CTA; else in global memory.
+// CTA, else in global memory; v is staged in shared memory beside it when both
+// fit (see implicit_mode).
 #include <algorithm>
 #include <vector>
 
@@ -114,7 +116,7 @@ __device__ __forceinline__ void accumulate_y(float* yt, int cam, const ObsRec& r
 
 // k <= 32: teams of W lanes, lane t of a team holds observation t (rows 2t, 2t+1)
 template <int W>
-__device__ void small_task(const ImArgs& a, const ImTask& tk, float* yt, int lane) {
+__device__ void small_task(const ImArgs& a, const ImTask& tk, const float* vt, float* yt, int lane) {
     const int team = lane / W, t = lane - team * W, base = team * W;
     const int k = tk.k;
     const bool has = team < tk.n;
@@ -128,7 +130,7 @@ __device__ void small_task(const ImArgs& a, const ImTask& tk, float* yt, int lan
         load_rec(a, so, r);
         cam = __ldg(a.mv_cam + so);
 #pragma unroll
-        for (int c = 0; c < 9; ++c) vv[c] = __ldg(a.v + 9 * cam + c);
+        for (int c = 0; c < 9; ++c) vv[c] = vt[9 * cam + c];
     } else {
 #pragma unroll
         for (int i = 0; i < 18; ++i) r.J[i] = 0.f;
@@ -174,7 +176,7 @@ __device__ void small_task(const ImArgs& a, const ImTask& tk, float* yt, int lan
 }
 
 // k > 32: one warp, lanes over the observations in chunks of 32
-__device__ void big_task(const ImArgs& a, const ImTask& tk, float* yt, int lane) {
+__device__ void big_task(const ImArgs& a, const ImTask& tk, const float* vt, float* yt, int lane) {
     const int k = tk.k;
     if (a.blm && !batch_active(a.blm, a.lm_prob[a.lm_by_k[tk.pos0]])) return;  // whole warp
     const LmFactors F = load_factors(a.lmrec, tk.pos0);
@@ -183,7 +185,7 @@ __device__ void big_task(const ImArgs& a, const ImTask& tk, float* yt, int lane)
         load_rec(a, so, r);
         cam = __ldg(a.mv_cam + so);
 #pragma unroll
-        for (int c = 0; c < 9; ++c) vv[c] = __ldg(a.v + 9 * cam + c);
+        for (int c = 0; c < 9; ++c) vv[c] = vt[9 * cam + c];
     };
     // pass 1: V^T u
     float p0 = 0.f, p1 = 0.f, p2 = 0.f;
@@ -277,33 +279,39 @@ __device__ void big_task(const ImArgs& a, const ImTask& tk, float* yt, int lane)
     }
 }
 
-template <bool SMEM_Y>
-__global__ void __launch_bounds__(IM_THREADS, 2) k_matvec_implicit(ImArgs a) {
-    extern __shared__ float ys[];
-    if (a.S != nullptr && a.S->done) return;
+// SMEM_Y: y accumulated in shared memory (flushed once per CTA); SMEM_V: v
+// staged in shared memory too (one coalesced copy per CTA: the nine gathers of
+// an observation's camera then hit shared memory, not 32-sector L1 requests).
+// NT threads per CTA: 512 (two CTAs per SM) or 1024 (one, when y and v do
+// not fit twice).
+template <bool SMEM_Y, bool SMEM_V, int NT>
+__device__ __forceinline__ void matvec_body(const ImArgs& a, float* ys) {
     const int acc_n = 9 * a.n_cam;
-    if (SMEM_Y) {
-        for (int i = threadIdx.x; i < acc_n; i += IM_THREADS) ys[i] = 0.f;
-        __syncthreads();
-    }
+    float* vs = ys + (SMEM_Y ? acc_n : 0);
+    if (SMEM_Y)
+        for (int i = threadIdx.x; i < acc_n; i += NT) ys[i] = 0.f;
+    if (SMEM_V)
+        for (int i = threadIdx.x; i < acc_n; i += NT) vs[i] = __ldg(a.v + i);
+    if (SMEM_Y || SMEM_V) __syncthreads();
     float* yt = SMEM_Y ? ys : a.y;
+    const float* vt = SMEM_V ? vs : a.v;
     const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * IM_WARPS + (threadIdx.x >> 5), nw = gridDim.x * IM_WARPS;
+    const int gw = blockIdx.x * (NT / 32) + (threadIdx.x >> 5), nw = gridDim.x * (NT / 32);
     for (int ti = gw; ti < a.n_tasks; ti += nw) {
         const ImTask tk = a.tasks[ti];
         switch (team_width(tk.k) * (tk.k <= 32 ? 1 : 0)) {
-            case 2: small_task<2>(a, tk, yt, lane); break;
-            case 4: small_task<4>(a, tk, yt, lane); break;
-            case 8: small_task<8>(a, tk, yt, lane); break;
-            case 16: small_task<16>(a, tk, yt, lane); break;
-            case 32: small_task<32>(a, tk, yt, lane); break;
-            default: big_task(a, tk, yt, lane); break;
+            case 2: small_task<2>(a, tk, vt, yt, lane); break;
+            case 4: small_task<4>(a, tk, vt, yt, lane); break;
+            case 8: small_task<8>(a, tk, vt, yt, lane); break;
+            case 16: small_task<16>(a, tk, vt, yt, lane); break;
+            case 32: small_task<32>(a, tk, vt, yt, lane); break;
+            default: big_task(a, tk, vt, yt, lane); break;
         }
     }
     if (SMEM_Y) {
         __syncthreads();
         const int i0 = (int)(((int64_t)blockIdx.x * acc_n) / gridDim.x);
-        for (int q = threadIdx.x; q < acc_n; q += IM_THREADS) {
+        for (int q = threadIdx.x; q < acc_n; q += NT) {
             const int i = q + i0 < acc_n ? q + i0 : q + i0 - acc_n;
             const float val = ys[i];
             if (val != 0.f) atomicAdd(a.y + i, val);
@@ -311,7 +319,32 @@ __global__ void __launch_bounds__(IM_THREADS, 2) k_matvec_implicit(ImArgs a) {
     }
 }
 
-bool implicit_smem_y(const Problem& p) { return 36LL * p.n_cam <= IM_SMEM_Y_MAX; }
+// SMEM_Y: y accumulated in shared memory (flushed once per CTA); SMEM_V: v
+// staged in shared memory too (one coalesced copy per CTA: the nine gathers of
+// an observation's camera then hit shared memory, not 32-sector L1 requests).
+// NT threads per CTA: 512 (two CTAs per SM) or 1024 (one, when y and v do
+// not fit twice).
+template <bool SMEM_Y, bool SMEM_V, int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_matvec_implicit(ImArgs a) {
+    extern __shared__ float ys[];
+    if (a.S != nullptr && a.S->done) return;
+    matvec_body<SMEM_Y, SMEM_V, NT>(a, ys);
+}
+
+// shared-memory plan of the matvec: y and v in shared memory at two CTAs of
+// 512 threads per SM when both fit twice, else at one CTA of 1024 threads;
+// then y alone (v from global memory); else neither
+enum ImMode { IM_YV2, IM_YV1, IM_Y2, IM_NONE };
+constexpr int64_t IM_SMEM_SM = 220 * 1024;  // shared memory used per SM at most
+
+ImMode implicit_mode(const Problem& p) {
+    const int64_t b = 36LL * p.n_cam;
+    if (2 * b <= IM_SMEM_SM / 2) return IM_YV2;
+    if (2 * b <= IM_SMEM_SM) return IM_YV1;
+    if (b <= IM_SMEM_Y_MAX) return IM_Y2;
+    return IM_NONE;
+}
+
 
 // The undamped top rows [Q1^T J_p | R1 | Q1^T r] of landmark j (3 rows of
 // 9 k + 4, the stored form's layout) rebuilt from the records, one thread per
@@ -392,19 +425,33 @@ void plan_implicit(Problem& p) {
 }
 
 void configure_implicit(Problem&) {
-    BA_CUDA_TRY(cudaFuncSetAttribute(k_matvec_implicit<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     IM_SMEM_Y_MAX));
+    BA_CUDA_TRY(cudaFuncSetAttribute(k_matvec_implicit<true, true, IM_THREADS>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(IM_SMEM_SM / 2)));
+    BA_CUDA_TRY(cudaFuncSetAttribute(k_matvec_implicit<true, true, 2 * IM_THREADS>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)IM_SMEM_SM));
+    BA_CUDA_TRY(cudaFuncSetAttribute(k_matvec_implicit<true, false, IM_THREADS>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, IM_SMEM_Y_MAX));
 }
 
 void launch_matvec_implicit(Problem& p, const float* v, float* y, const PcgScalars* S) {
     const ImArgs a{static_cast<const ImTask*>(p.im_tasks), p.im_ntasks, reinterpret_cast<const float4*>(p.ipool),
                    p.n_obs, p.lmrec, p.mv_cam, v, y, p.n_cam, S,
                    p.batch.n_prob > 0 ? p.batch.lm : nullptr, p.batch.lm_prob, p.lm_by_k};
-    const int grid = p.sm_count * 2;
-    if (implicit_smem_y(p))
-        k_matvec_implicit<true><<<grid, IM_THREADS, 36 * (size_t)p.n_cam, p.stream>>>(a);
-    else
-        k_matvec_implicit<false><<<grid, IM_THREADS, 0, p.stream>>>(a);
+    const size_t b = 36 * (size_t)p.n_cam;
+    switch (implicit_mode(p)) {
+        case IM_YV2:
+            k_matvec_implicit<true, true, IM_THREADS><<<p.sm_count * 2, IM_THREADS, 2 * b, p.stream>>>(a);
+            break;
+        case IM_YV1:
+            k_matvec_implicit<true, true, 2 * IM_THREADS><<<p.sm_count, 2 * IM_THREADS, 2 * b, p.stream>>>(a);
+            break;
+        case IM_Y2:
+            k_matvec_implicit<true, false, IM_THREADS><<<p.sm_count * 2, IM_THREADS, b, p.stream>>>(a);
+            break;
+        default:
+            k_matvec_implicit<false, false, IM_THREADS><<<p.sm_count * 2, IM_THREADS, 0, p.stream>>>(a);
+            break;
+    }
     BA_LAUNCH_CHECK();
 }
 

@@ -409,6 +409,75 @@ __device__ void exact_sums_warp_implicit(int cam, const int32_t* __restrict__ ca
     __syncwarp();
 }
 
+// The CG start folded into the finish (a single problem without the learned
+// correction): each camera's warp writes x = 0, r = g, q = 0 and p = z = M^-1 g
+// for its camera and its partials of g^T g and r^T z; the last warp to finish
+// (an atomic ticket) sums the partials in camera order (deterministic) and
+// sets the CG scalars as k_pcg_init does.
+struct PcgInit {
+    PcgScalars* S;      // null: no fused start
+    float *x, *r, *z, *p, *q;
+    float* part;        // 2 per camera
+    uint32_t* ticket;   // zero between calls (the last warp resets it)
+    float eta;
+    int max_it;
+};
+
+__device__ void pcg_init_fused(int cam, int n_cam, const float* __restrict__ minv, const float* g, const PcgInit& in,
+                               float lam, int lane) {
+    __syncwarp();  // minv and g of this camera, written by the warp's lanes
+    float gg = 0.f, rz = 0.f;
+    if (lane < 9) {
+        const int64_t o = 9LL * cam;
+        const float* M = minv + 81LL * cam + 9 * lane;
+        float zi = 0.f;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) zi += M[c] * g[o + c];
+        const float gi = g[o + lane];
+        in.x[o + lane] = 0.f;
+        in.r[o + lane] = gi;
+        in.q[o + lane] = 0.f;
+        in.z[o + lane] = zi;
+        in.p[o + lane] = zi;
+        gg = gi * gi;
+        rz = gi * zi;
+    }
+    gg = warp_sum(gg);
+    rz = warp_sum(rz);
+    unsigned last = 0;
+    if (lane == 0) {
+        in.part[2 * cam] = gg;
+        in.part[2 * cam + 1] = rz;
+        __threadfence();
+        last = atomicAdd(in.ticket, 1u) == (unsigned)(n_cam - 1);
+    }
+    if (!__shfl_sync(0xffffffffu, last, 0)) return;
+    __threadfence();
+    float sg = 0.f, sr = 0.f;
+    for (int c = lane; c < n_cam; c += 32) {
+        sg += __ldcg(in.part + 2 * c);
+        sr += __ldcg(in.part + 2 * c + 1);
+    }
+    sg = warp_sum(sg);
+    sr = warp_sum(sr);
+    if (lane == 0) {
+        const bool done = !(sg > 0.f && sr > 0.f);
+        PcgScalars* S = in.S;
+        S->rho = sr;
+        S->q_prev = 0.f;
+        S->gnorm = sqrtf(sg);
+        S->rnorm = sqrtf(sg);
+        S->lambda = lam;
+        S->eta = in.eta;
+        S->it = 0;
+        S->max_it = in.max_it;
+        S->done = done ? 1 : 0;
+        S->stop = done ? 4 : -1;
+        S->warm = 0;
+        *in.ticket = 0u;
+    }
+}
+
 // Second pass, one warp per camera: its chunks' sums in chunk order, then
 // the 9 x 9 block as in the record path.
 __global__ void __launch_bounds__(32)
@@ -421,7 +490,8 @@ k_precond_gram_finish(const int32_t* __restrict__ chunk_off, const float* __rest
                       const int32_t* __restrict__ c_off, const float* __restrict__ apool,
                       const float* __restrict__ cpool, const int32_t* __restrict__ lm_pos,
                       const float4* __restrict__ ipool, int64_t n_obs, const float* __restrict__ rpool,
-                      const float* __restrict__ lmrec, int force_exact, const BatchLm* __restrict__ blm) {
+                      const float* __restrict__ lmrec, int force_exact, const BatchLm* __restrict__ blm,
+                      PcgInit init) {
     __shared__ float tot[56], sM[81], sL[81];
     const int cam = blockIdx.x, lane = threadIdx.x;
     if (blm && !batch_active(blm, cam_prob[cam])) return;  // a stopped problem of a batch
@@ -444,6 +514,7 @@ k_precond_gram_finish(const int32_t* __restrict__ chunk_off, const float* __rest
         if (lane == 0) atomicAdd(err + 2, 1u);  // cameras summed from the stored blocks (read back by the host)
     }
     precond_finish_warp(cam, tot, dp2, lam, mdiag, minv, g, err, sM, sL, lane);
+    if (init.S) pcg_init_fused(cam, gridDim.x, minv, g, init, lam, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -705,10 +776,10 @@ k_bpcg_update(int n_prob, const int32_t* __restrict__ prob_cam_off, const float*
 
 }  // namespace
 
-void launch_precond_rhs(Problem& p) {
+bool launch_precond_rhs(Problem& p, bool fuse_init) {
     if (p.schur) {
         launch_schur_precond(p);
-        return;
+        return false;
     }
     if (!p.opt.precond_from_blocks || p.implicit) {
         // (implicit storage with precond_from_blocks: every camera's sums from
@@ -720,13 +791,21 @@ void launch_precond_rhs(Problem& p) {
                 p.pg_chunk_cam, p.pg_chunk_off, p.cam_off, p.cam_list, p.obs_pt_s, p.obs_xy_s, p.pt_off, p.frames,
                 p.pts, p.tpool, p.pg_part, lmrec, p.lm_pos, p.c_off, reinterpret_cast<const float4*>(p.ipool),
                 p.n_obs, (float)p.opt.huber_delta, p.batch.n_prob > 0 ? p.batch.lm : nullptr, p.batch.cam_prob);
+        const bool fuse = fuse_init && p.batch.n_prob == 0;
+        if (fuse && !p.init_part) {
+            p.init_part = dalloc<float>(p, 2LL * p.n_cam);
+            p.init_ticket = dalloc<uint32_t>(p, 1);
+        }
+        if (fuse) BA_CUDA_TRY(cudaMemsetAsync(p.init_ticket, 0, sizeof(uint32_t), p.stream));
+        const PcgInit init{fuse ? p.pcg : nullptr, p.x, p.r, p.z, p.p, p.q, p.init_part, p.init_ticket,
+                           (float)p.opt.cg_eta, p.opt.max_cg_iters};
         k_precond_gram_finish<<<p.n_cam, 32, 0, p.stream>>>(
             p.pg_chunk_off, p.pg_part, p.dp2, (float)p.lambda_damped, p.batch.lam, p.batch.cam_prob, p.mdiag, p.minv,
             p.g, p.err, p.cam_off, p.cam_list, p.obs_pt_s, p.pt_off, p.a_off, p.c_off, p.apool, p.cpool, p.lm_pos,
             reinterpret_cast<const float4*>(p.ipool), p.n_obs, p.rpool, lmrec,
-            p.implicit && p.opt.precond_from_blocks ? 1 : 0, p.batch.n_prob > 0 ? p.batch.lm : nullptr);
+            p.implicit && p.opt.precond_from_blocks ? 1 : 0, p.batch.n_prob > 0 ? p.batch.lm : nullptr, init);
         BA_LAUNCH_CHECK();
-        return;
+        return fuse;
     }
     launch_precond_records(p);
     count_launches(p, 2 + (p.pc_plan.n_obs_split > 0 ? 1 : 0));
@@ -734,6 +813,7 @@ void launch_precond_rhs(Problem& p) {
                                                              (float)p.lambda_damped, p.batch.lam, p.batch.cam_prob,
                                                              p.mdiag, p.minv, p.g, p.err);
     BA_LAUNCH_CHECK();
+    return false;
 }
 
 // the block inverses the CG applies: plain block Jacobi, or the learned

@@ -175,6 +175,8 @@ struct Problem {
     bool implicit = false;
     float *ipool = nullptr, *rpool = nullptr, *lmrec = nullptr;
     int32_t* lm_pos = nullptr;       // storage position of every landmark
+    float* init_part = nullptr;      // CG start folded into K3: per-camera partials of g^T g, r^T z
+    uint32_t* init_ticket = nullptr; // and the finish kernel's completion count
     void* im_tasks = nullptr;        // matvec tasks (implicit.cu)
     int im_ntasks = 0;
     // explicit Schur complement in FP32 (ba_options.schur_explicit, schur.cu):
@@ -267,7 +269,9 @@ void launch_candidate(Problem& p);
 // K2: landmark damping with Givens rotations (damp.cu)
 void launch_damp(Problem& p, bool undo_old, float lambda);
 // K3, K5: preconditioner and PCG (pcg.cu); K4: matvec (matvec.cu)
-void launch_precond_rhs(Problem& p);
+// K3; with fuse_init (a single problem) the CG start is folded into its finish
+// kernel: returns true if it was (no k_pcg_init needed)
+bool launch_precond_rhs(Problem& p, bool fuse_init = false);
 void launch_pcg_init(Problem& p);
 void launch_pcg_init_warm(Problem& p);
 const float* active_minv(const Problem& p);
