@@ -50,6 +50,8 @@ static_assert(sizeof(ImTask) == 16, "task record");
 struct ImArgs {
     const ImTask* tasks;
     int n_tasks;
+    int n_big;             // tasks [0, n_big) have k > 32 (one landmark each), taken dynamically
+    unsigned* ctr;         // [0] next big task, [32] CTAs done (both zero between launches)
     const float4* ipool;   // 6 float4 chunks per observation, chunk m at m * n_obs
     int64_t n_obs;
     const float* lmrec;    // 32 floats per storage position
@@ -297,15 +299,33 @@ __device__ __forceinline__ void matvec_body(const ImArgs& a, float* ys) {
     const float* vt = SMEM_V ? vs : a.v;
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * (NT / 32) + (threadIdx.x >> 5), nw = gridDim.x * (NT / 32);
-    for (int ti = gw; ti < a.n_tasks; ti += nw) {
+    // the k <= 32 tasks statically, round robin over the warps ...
+    for (int ti = a.n_big + gw; ti < a.n_tasks; ti += nw) {
         const ImTask tk = a.tasks[ti];
-        switch (team_width(tk.k) * (tk.k <= 32 ? 1 : 0)) {
+        switch (team_width(tk.k)) {
             case 2: small_task<2>(a, tk, vt, yt, lane); break;
             case 4: small_task<4>(a, tk, vt, yt, lane); break;
             case 8: small_task<8>(a, tk, vt, yt, lane); break;
             case 16: small_task<16>(a, tk, vt, yt, lane); break;
-            case 32: small_task<32>(a, tk, vt, yt, lane); break;
-            default: big_task(a, tk, vt, yt, lane); break;
+            default: small_task<32>(a, tk, vt, yt, lane); break;
+        }
+    }
+    // ... then the k > 32 ones (three passes each, up to k = 900) one at a time
+    // to whichever warp asks next, so that they do not set the kernel's tail
+    for (;;) {
+        unsigned ti = 0;
+        if (lane == 0) ti = atomicAdd(a.ctr, 1u);
+        ti = __shfl_sync(0xffffffffu, ti, 0);
+        if (ti >= (unsigned)a.n_big) break;
+        big_task(a, a.tasks[ti], vt, yt, lane);
+    }
+    // the last CTA to finish resets the counters for the next launch
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(a.ctr + 32, 1u) == gridDim.x - 1) {
+            atomicExch(a.ctr, 0u);
+            atomicExch(a.ctr + 32, 0u);
         }
     }
     if (SMEM_Y) {
@@ -417,6 +437,10 @@ void plan_implicit(Problem& p) {
         pos += cnt;
     }
     p.im_ntasks = (int)tasks.size();
+    p.im_nbig = 0;
+    while (p.im_nbig < p.im_ntasks && tasks[p.im_nbig].k > 32) ++p.im_nbig;
+    p.im_ctr = dalloc<uint32_t>(p, 64);
+    BA_CUDA_TRY(cudaMemsetAsync(p.im_ctr, 0, 64 * sizeof(uint32_t), p.stream));
     p.im_tasks = dalloc<ImTask>(p, std::max<int64_t>(1, (int64_t)tasks.size()));
     if (!tasks.empty())
         BA_CUDA_TRY(cudaMemcpyAsync(p.im_tasks, tasks.data(), sizeof(ImTask) * tasks.size(), cudaMemcpyHostToDevice,
@@ -434,7 +458,8 @@ void configure_implicit(Problem&) {
 }
 
 void launch_matvec_implicit(Problem& p, const float* v, float* y, const PcgScalars* S) {
-    const ImArgs a{static_cast<const ImTask*>(p.im_tasks), p.im_ntasks, reinterpret_cast<const float4*>(p.ipool),
+    const ImArgs a{static_cast<const ImTask*>(p.im_tasks), p.im_ntasks, p.im_nbig, p.im_ctr,
+                   reinterpret_cast<const float4*>(p.ipool),
                    p.n_obs, p.lmrec, p.mv_cam, v, y, p.n_cam, S,
                    p.batch.n_prob > 0 ? p.batch.lm : nullptr, p.batch.lm_prob, p.lm_by_k};
     const size_t b = 36 * (size_t)p.n_cam;

@@ -179,6 +179,8 @@ struct Problem {
     uint32_t* init_ticket = nullptr; // and the finish kernel's completion count
     void* im_tasks = nullptr;        // matvec tasks (implicit.cu)
     int im_ntasks = 0;
+    int im_nbig = 0;                 // matvec tasks with k > 32 (the first ones), handed out dynamically
+    uint32_t* im_ctr = nullptr;      // their counter [0] and the CTAs-done count [32]
     // explicit Schur complement in FP32 (ba_options.schur_explicit, schur.cu):
     // block CSR of H~ with both triangles, pair -> blocks map, b~
     bool schur = false;
