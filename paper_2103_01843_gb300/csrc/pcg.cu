@@ -121,7 +121,8 @@ k_precond_gram(const int32_t* __restrict__ chunk_cam, const int32_t* __restrict_
                const int32_t* __restrict__ pt_off, const float* __restrict__ frames, const float* __restrict__ pts,
                const float* __restrict__ tpool, float* __restrict__ part_out, const float* __restrict__ lmrec,
                const int32_t* __restrict__ lm_pos, const int32_t* __restrict__ c_off,
-               const float4* __restrict__ ipool, int64_t n_obs, float huber, const BatchLm* __restrict__ blm,
+               const float4* __restrict__ ipool, int64_t n_obs, const int4* __restrict__ k3rec,
+               const float2* __restrict__ k3xy, float huber, const BatchLm* __restrict__ blm,
                const int32_t* __restrict__ cam_prob) {
     __shared__ float part[PG_T / 32][REC_SUMS + 1];
     const int ch = blockIdx.x, cam = chunk_cam[ch];
@@ -132,12 +133,22 @@ k_precond_gram(const int32_t* __restrict__ chunk_cam, const int32_t* __restrict_
     float acc[REC_SUMS + 1];  // + sum of ||J_s||_F^2 (the cancellation guard of the finish)
 #pragma unroll
     for (int q = 0; q <= REC_SUMS; ++q) acc[q] = 0.f;
-    const float* fr = frames + FRAME * cam;
+    const float* fr = frames + FRAME * cam;  // global (load_frame reads it with __ldg)
     for (int e = e0 + threadIdx.x; e < e1; e += PG_T) {
-        const int s = cam_list[e];
-        const int j = obs_pt_s[s];
-        const int s0 = pt_off[j], k = pt_off[j + 1] - s0;
-        const float2 z = obs_xy_s[s];
+        int s = 0, j, s0 = 0, k = 0;
+        float2 z;
+        int4 rec = make_int4(0, 0, 0, 0);
+        if constexpr (IMPLICIT) {  // the camera-ordered record: landmark, storage index, position | slot
+            rec = __ldg(k3rec + e);
+            z = __ldg(k3xy + e);
+            j = rec.x;
+        } else {
+            s = cam_list[e];
+            j = obs_pt_s[s];
+            s0 = pt_off[j];
+            k = pt_off[j + 1] - s0;
+            z = obs_xy_s[s];
+        }
         float r[2], Jp[18], Jl[6];
         frame_jacobians(fr, pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], z.x, z.y, r, Jp, Jl);
         huber_scale_rows(huber, r, Jp, Jl);  // the rows K1 factored
@@ -148,11 +159,12 @@ k_precond_gram(const int32_t* __restrict__ chunk_cam, const int32_t* __restrict_
             // J_s's rows 0, 1 into top rows 0, 1 for slot 0, row 0 into top row 2
             // for slot 1), so J_s^T J_s - T_s^T T_s = J_s^T W J_s, W = I - C^T C,
             // and J_s^T r_s - T_s^T t = J_s^T (r_s - C^T G_tt t)
-            const int slot = s - s0;
-            const int64_t so = (int64_t)(c_off[j] >> 1) + slot;
+            const int slot = (int)((unsigned)rec.z >> 30);     // 0, 1 or 2 (>= 2)
+            const int64_t so = (int64_t)(unsigned)rec.y;
+            const int pos = rec.z & 0x3fffffff;
             const float4 c4 = __ldg(ipool + 4 * n_obs + so), c5 = __ldg(ipool + 5 * n_obs + so);
             const float va[3] = {c4.z, c4.w, c5.x}, vb[3] = {c5.y, c5.z, c5.w};  // V rows 2 slot, 2 slot + 1
-            const float4* Lr = reinterpret_cast<const float4*>(lmrec + (int64_t)LM_REC * lm_pos[j]);
+            const float4* Lr = reinterpret_cast<const float4*>(lmrec + (int64_t)LM_REC * pos);
             static_assert(LR_GP == 12 && LR_GT == 21 && LR_G == 24, "record");
             const float4 g0 = __ldg(Lr + 3), g1 = __ldg(Lr + 4), g2 = __ldg(Lr + 5);
             const float GP[9] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g2.x};
@@ -228,6 +240,24 @@ k_precond_gram(const int32_t* __restrict__ chunk_cam, const int32_t* __restrict_
 #pragma unroll
         for (int m = 0; m < PG_T / 32; ++m) v += part[m][threadIdx.x];
         part_out[56LL * ch + threadIdx.x] = v;
+    }
+}
+
+// The camera-ordered record of every observation (entry e of the camera
+// lists) for the implicit K3: landmark, storage index, landmark storage
+// position with the slot (0, 1, or 2 for any later slot) in its top two bits,
+// and the measurement.  Static per problem (built at create).
+__global__ void k_k3_records(int64_t n_obs, const int32_t* __restrict__ cam_list, const int32_t* __restrict__ obs_pt_s,
+                             const int32_t* __restrict__ pt_off, const int32_t* __restrict__ c_off,
+                             const int32_t* __restrict__ lm_pos, const float2* __restrict__ obs_xy_s,
+                             int4* __restrict__ rec, float2* __restrict__ xy) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_obs; e += (int64_t)gridDim.x * blockDim.x) {
+        const int s = cam_list[e];
+        const int j = obs_pt_s[s];
+        const int slot = s - pt_off[j];
+        const int so = (c_off[j] >> 1) + slot;
+        rec[e] = make_int4(j, so, (int)((unsigned)lm_pos[j] | ((unsigned)min(slot, 2) << 30)), 0);
+        xy[e] = obs_xy_s[s];
     }
 }
 
@@ -776,6 +806,15 @@ k_bpcg_update(int n_prob, const int32_t* __restrict__ prob_cam_off, const float*
 
 }  // namespace
 
+void build_k3_records(Problem& p) {
+    p.k3rec = dalloc<int4>(p, std::max<int64_t>(1, p.n_obs));
+    p.k3xy = dalloc<float2>(p, std::max<int64_t>(1, p.n_obs));
+    if (p.n_obs > 0)
+        k_k3_records<<<p.sm_count * 8, 256, 0, p.stream>>>(p.n_obs, p.cam_list, p.obs_pt_s, p.pt_off, p.c_off, p.lm_pos,
+                                                          p.obs_xy_s, p.k3rec, p.k3xy);
+    BA_LAUNCH_CHECK();
+}
+
 bool launch_precond_rhs(Problem& p, bool fuse_init) {
     if (p.schur) {
         launch_schur_precond(p);
@@ -790,7 +829,8 @@ bool launch_precond_rhs(Problem& p, bool fuse_init) {
             (p.implicit ? k_precond_gram<true> : k_precond_gram<false>)<<<p.pg_chunks, PG_T, 0, p.stream>>>(
                 p.pg_chunk_cam, p.pg_chunk_off, p.cam_off, p.cam_list, p.obs_pt_s, p.obs_xy_s, p.pt_off, p.frames,
                 p.pts, p.tpool, p.pg_part, lmrec, p.lm_pos, p.c_off, reinterpret_cast<const float4*>(p.ipool),
-                p.n_obs, (float)p.opt.huber_delta, p.batch.n_prob > 0 ? p.batch.lm : nullptr, p.batch.cam_prob);
+                p.n_obs, p.k3rec, p.k3xy, (float)p.opt.huber_delta, p.batch.n_prob > 0 ? p.batch.lm : nullptr,
+                p.batch.cam_prob);
         const bool fuse = fuse_init && p.batch.n_prob == 0;
         if (fuse && !p.init_part) {
             p.init_part = dalloc<float>(p, 2LL * p.n_cam);

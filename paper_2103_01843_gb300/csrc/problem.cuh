@@ -175,6 +175,8 @@ struct Problem {
     bool implicit = false;
     float *ipool = nullptr, *rpool = nullptr, *lmrec = nullptr;
     int32_t* lm_pos = nullptr;       // storage position of every landmark
+    int4* k3rec = nullptr;           // K3's camera-ordered records (landmark, storage index, position | slot)
+    float2* k3xy = nullptr;          // and measurements, per camera-list entry
     float* init_part = nullptr;      // CG start folded into K3: per-camera partials of g^T g, r^T z
     uint32_t* init_ticket = nullptr; // and the finish kernel's completion count
     void* im_tasks = nullptr;        // matvec tasks (implicit.cu)
@@ -274,6 +276,7 @@ void launch_damp(Problem& p, bool undo_old, float lambda);
 // K3; with fuse_init (a single problem) the CG start is folded into its finish
 // kernel: returns true if it was (no k_pcg_init needed)
 bool launch_precond_rhs(Problem& p, bool fuse_init = false);
+void build_k3_records(Problem& p);  // implicit storage: K3's camera-ordered records (at create)
 void launch_pcg_init(Problem& p);
 void launch_pcg_init_warm(Problem& p);
 const float* active_minv(const Problem& p);
