@@ -117,7 +117,14 @@ __device__ __forceinline__ void accumulate_y(float* yt, int cam, const ObsRec& r
 }
 
 // k <= 32: teams of W lanes, lane t of a team holds observation t (rows 2t, 2t+1)
-template <int W>
+// v element i: shared memory (SV) or the read-only global path
+template <bool SV>
+__device__ __forceinline__ float load_v(const float* vt, int i) {
+    if constexpr (SV) return vt[i];
+    else return __ldg(vt + i);
+}
+
+template <int W, bool SV>
 __device__ void small_task(const ImArgs& a, const ImTask& tk, const float* vt, float* yt, int lane) {
     const int team = lane / W, t = lane - team * W, base = team * W;
     const int k = tk.k;
@@ -132,7 +139,7 @@ __device__ void small_task(const ImArgs& a, const ImTask& tk, const float* vt, f
         load_rec(a, so, r);
         cam = __ldg(a.mv_cam + so);
 #pragma unroll
-        for (int c = 0; c < 9; ++c) vv[c] = vt[9 * cam + c];
+        for (int c = 0; c < 9; ++c) vv[c] = load_v<SV>(vt, 9 * cam + c);
     } else {
 #pragma unroll
         for (int i = 0; i < 18; ++i) r.J[i] = 0.f;
@@ -178,6 +185,7 @@ __device__ void small_task(const ImArgs& a, const ImTask& tk, const float* vt, f
 }
 
 // k > 32: one warp, lanes over the observations in chunks of 32
+template <bool SV>
 __device__ void big_task(const ImArgs& a, const ImTask& tk, const float* vt, float* yt, int lane) {
     const int k = tk.k;
     if (a.blm && !batch_active(a.blm, a.lm_prob[a.lm_by_k[tk.pos0]])) return;  // whole warp
@@ -187,7 +195,7 @@ __device__ void big_task(const ImArgs& a, const ImTask& tk, const float* vt, flo
         load_rec(a, so, r);
         cam = __ldg(a.mv_cam + so);
 #pragma unroll
-        for (int c = 0; c < 9; ++c) vv[c] = vt[9 * cam + c];
+        for (int c = 0; c < 9; ++c) vv[c] = load_v<SV>(vt, 9 * cam + c);
     };
     // pass 1: V^T u
     float p0 = 0.f, p1 = 0.f, p2 = 0.f;
@@ -303,29 +311,32 @@ __device__ __forceinline__ void matvec_body(const ImArgs& a, float* ys) {
     for (int ti = a.n_big + gw; ti < a.n_tasks; ti += nw) {
         const ImTask tk = a.tasks[ti];
         switch (team_width(tk.k)) {
-            case 2: small_task<2>(a, tk, vt, yt, lane); break;
-            case 4: small_task<4>(a, tk, vt, yt, lane); break;
-            case 8: small_task<8>(a, tk, vt, yt, lane); break;
-            case 16: small_task<16>(a, tk, vt, yt, lane); break;
-            default: small_task<32>(a, tk, vt, yt, lane); break;
+            case 2: small_task<2, SMEM_V>(a, tk, vt, yt, lane); break;
+            case 4: small_task<4, SMEM_V>(a, tk, vt, yt, lane); break;
+            case 8: small_task<8, SMEM_V>(a, tk, vt, yt, lane); break;
+            case 16: small_task<16, SMEM_V>(a, tk, vt, yt, lane); break;
+            default: small_task<32, SMEM_V>(a, tk, vt, yt, lane); break;
         }
     }
     // ... then the k > 32 ones (three passes each, up to k = 900) one at a time
     // to whichever warp asks next, so that they do not set the kernel's tail
-    for (;;) {
-        unsigned ti = 0;
-        if (lane == 0) ti = atomicAdd(a.ctr, 1u);
-        ti = __shfl_sync(0xffffffffu, ti, 0);
-        if (ti >= (unsigned)a.n_big) break;
-        big_task(a, a.tasks[ti], vt, yt, lane);
-    }
-    // the last CTA to finish resets the counters for the next launch
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(a.ctr + 32, 1u) == gridDim.x - 1) {
-            atomicExch(a.ctr, 0u);
-            atomicExch(a.ctr + 32, 0u);
+    // (a plain read first: once they are gone no warp queues on the atomic)
+    if (a.n_big > 0) {
+        for (;;) {
+            unsigned ti = (unsigned)a.n_big;
+            if (lane == 0 && *(volatile unsigned*)a.ctr < (unsigned)a.n_big) ti = atomicAdd(a.ctr, 1u);
+            ti = __shfl_sync(0xffffffffu, ti, 0);
+            if (ti >= (unsigned)a.n_big) break;
+            big_task<SMEM_V>(a, a.tasks[ti], vt, yt, lane);
+        }
+        // the last CTA to finish resets the counters for the next launch
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(a.ctr + 32, 1u) == gridDim.x - 1) {
+                atomicExch(a.ctr, 0u);
+                atomicExch(a.ctr + 32, 0u);
+            }
         }
     }
     if (SMEM_Y) {

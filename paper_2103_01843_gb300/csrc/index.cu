@@ -136,54 +136,87 @@ __global__ void k_validate_count(const int32_t* __restrict__ oc, const int32_t* 
     }
 }
 
-__global__ void k_scatter_pt(const int32_t* __restrict__ op, int64_t n,
-                             const int32_t* __restrict__ pt_off, int32_t* cursor,
-                             int32_t* __restrict__ tmp) {
+// observation o into its landmark's segment as the key (camera << 32 | o):
+// the segment sorts then compare one contiguous array (camera first, the
+// observation index breaks ties, so every key is unique)
+__global__ void k_scatter_pt(const int32_t* __restrict__ op, const int32_t* __restrict__ oc, int64_t n,
+                             const int32_t* __restrict__ pt_off, int32_t* cursor, uint64_t* __restrict__ kv) {
     for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n;
          o += (int64_t)gridDim.x * blockDim.x) {
         const int j = op[o];
         const int pos = pt_off[j] + atomicAdd(&cursor[j], 1);
-        tmp[pos] = (int32_t)o;
+        kv[pos] = ((uint64_t)(uint32_t)oc[o] << 32) | (uint64_t)(uint32_t)o;
     }
 }
 
-// One thread per landmark: order its observations by camera (insertion
-// sort; the keys are unique for valid input), reject k < 2 and duplicates,
-// and write the sorted observation arrays.
-__global__ void k_sort_segments(int n_pt, const int32_t* __restrict__ pt_off, int32_t* tmp,
-                                const int32_t* __restrict__ oc, const double* __restrict__ xy,
-                                int32_t* __restrict__ perm, int32_t* __restrict__ obs_cam_s,
-                                int32_t* __restrict__ obs_pt_s, float2* __restrict__ obs_xy_s,
-                                int32_t* __restrict__ kcount, int32_t* kmax, int32_t* nbig,
-                                uint32_t* err) {
+__device__ __forceinline__ void write_sorted(int i, int j, uint64_t key, const double* __restrict__ xy,
+                                             int32_t* __restrict__ perm, int32_t* __restrict__ obs_cam_s,
+                                             int32_t* __restrict__ obs_pt_s, float2* __restrict__ obs_xy_s) {
+    const int o = (int)(uint32_t)key;
+    perm[i] = o;
+    obs_cam_s[i] = (int)(key >> 32);
+    obs_pt_s[i] = j;
+    obs_xy_s[i] = make_float2((float)xy[2 * o], (float)xy[2 * o + 1]);
+}
+
+// One thread per landmark: its size, the checks (k < 2), and for k <= 32 the
+// order of its observations by camera (insertion sort of the keys), the
+// duplicate check and the sorted observation arrays; k > 32 is left to
+// k_sort_segments_big.
+__global__ void k_sort_segments(int n_pt, const int32_t* __restrict__ pt_off, uint64_t* kv,
+                                const double* __restrict__ xy, int32_t* __restrict__ perm,
+                                int32_t* __restrict__ obs_cam_s, int32_t* __restrict__ obs_pt_s,
+                                float2* __restrict__ obs_xy_s, int32_t* __restrict__ kcount, int32_t* kmax,
+                                int32_t* nbig, uint32_t* err) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_pt) return;
     const int a = pt_off[j], b = pt_off[j + 1], k = b - a;
     kcount[j] = k;
     atomicMax(kmax, k);
-    if (k > 32) atomicAdd(nbig, 1);
+    if (k > 32) {
+        atomicAdd(nbig, 1);
+        return;
+    }
     if (k < 2) atomicOr(err, ERRBIT_FEWOBS);
     for (int i = a + 1; i < b; ++i) {
-        const int v = tmp[i];
-        const int key = oc[v];
+        const uint64_t v = kv[i];
         int m = i - 1;
-        while (m >= a && oc[tmp[m]] > key) {
-            tmp[m + 1] = tmp[m];
+        while (m >= a && kv[m] > v) {
+            kv[m + 1] = kv[m];
             --m;
         }
-        tmp[m + 1] = v;
+        kv[m + 1] = v;
     }
-    int prev = -1;
+    uint64_t prev = ~0ull;
     for (int i = a; i < b; ++i) {
-        const int o = tmp[i];
-        const int c = oc[o];
-        if (c == prev) atomicOr(err, ERRBIT_DUPLICATE);
-        prev = c;
-        perm[i] = o;
-        obs_cam_s[i] = c;
-        obs_pt_s[i] = j;
-        obs_xy_s[i] = make_float2((float)xy[2 * o], (float)xy[2 * o + 1]);
+        const uint64_t key = kv[i];
+        if ((key >> 32) == (prev >> 32)) atomicOr(err, ERRBIT_DUPLICATE);
+        prev = key;
+        write_sorted(i, j, key, xy, perm, obs_cam_s, obs_pt_s, obs_xy_s);
     }
+}
+
+// k > 32: one warp per landmark, each key placed at its rank among the
+// segment's keys (the keys are unique), then the duplicate check against the
+// neighbour in the sorted order.
+__global__ void k_sort_segments_big(int n_pt, const int32_t* __restrict__ pt_off, const uint64_t* __restrict__ kv,
+                                    const double* __restrict__ xy, int32_t* __restrict__ perm,
+                                    int32_t* __restrict__ obs_cam_s, int32_t* __restrict__ obs_pt_s,
+                                    float2* __restrict__ obs_xy_s, uint32_t* err) {
+    const int lane = threadIdx.x & 31;
+    const int j = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (j >= n_pt) return;
+    const int a = pt_off[j], k = pt_off[j + 1] - a;
+    if (k <= 32) return;  // whole warp
+    for (int i = lane; i < k; i += 32) {
+        const uint64_t key = kv[a + i];
+        int rank = 0;
+        for (int m = 0; m < k; ++m) rank += kv[a + m] < key ? 1 : 0;
+        write_sorted(a + rank, j, key, xy, perm, obs_cam_s, obs_pt_s, obs_xy_s);
+    }
+    __syncwarp();
+    for (int i = a + 1 + lane; i < a + k; i += 32)
+        if (obs_cam_s[i] == obs_cam_s[i - 1]) atomicOr(err, ERRBIT_DUPLICATE);
 }
 
 // --- camera lists: a stable counting sort by camera over tiles --------------
@@ -194,15 +227,25 @@ __global__ void k_tile_hist(const int32_t* __restrict__ cam_s, int64_t n, int n_
         atomicAdd(&hist[(s / tile) * n_cam + cam_s[s]], 1);
 }
 
+// One warp per camera: its counts over the tiles turned into the tiles'
+// running bases (an exclusive scan in tile order, 32 tiles per step)
 __global__ void k_tile_base(int32_t* hist, int n_tiles, int n_cam, const int32_t* __restrict__ cam_off) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n_cam) return;
+    const int lane = threadIdx.x & 31;
+    const int c = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (c >= n_cam) return;  // whole warp
     int run = cam_off[c];
-    for (int t = 0; t < n_tiles; ++t) {
+    for (int t0 = 0; t0 < n_tiles; t0 += 32) {
+        const int t = t0 + lane;
         const int64_t i = (int64_t)t * n_cam + c;
-        const int h = hist[i];
-        hist[i] = run;  // becomes the tile's running base for this camera
-        run += h;
+        const int h = t < n_tiles ? hist[i] : 0;
+        int inc = h;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        if (t < n_tiles) hist[i] = run + inc - h;
+        run += __shfl_sync(0xffffffffu, inc, 31);
     }
 }
 
@@ -340,14 +383,17 @@ void build_index(Problem& p, const int32_t* d_oc, const int32_t* d_op, const dou
 
     int32_t* cursor = cnt_pt;  // reuse as scatter cursors
     BA_CUDA_TRY(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (p.n_pt + 1), st));
-    int32_t* tmp_idx = (int32_t*)tmp_alloc(sizeof(int32_t) * n);
-    k_scatter_pt<<<gsz, TPB, 0, st>>>(d_op, n, p.pt_off, cursor, tmp_idx);
+    uint64_t* kv = (uint64_t*)tmp_alloc(sizeof(uint64_t) * n);
+    k_scatter_pt<<<gsz, TPB, 0, st>>>(d_op, d_oc, n, p.pt_off, cursor, kv);
     int32_t* kcount = (int32_t*)tmp_alloc(sizeof(int32_t) * (p.n_pt + 1));
     int32_t* kmax_d = (int32_t*)tmp_alloc(2 * sizeof(int32_t));
     BA_CUDA_TRY(cudaMemsetAsync(kmax_d, 0, 2 * sizeof(int32_t), st));
-    k_sort_segments<<<ceil_div(p.n_pt, 128), 128, 0, st>>>(p.n_pt, p.pt_off, tmp_idx, d_oc, d_xy, p.perm,
-                                                           p.obs_cam_s, p.obs_pt_s, p.obs_xy_s, kcount,
-                                                           kmax_d, kmax_d + 1, p.err);
+    k_sort_segments<<<ceil_div(p.n_pt, 128), 128, 0, st>>>(p.n_pt, p.pt_off, kv, d_xy, p.perm, p.obs_cam_s,
+                                                           p.obs_pt_s, p.obs_xy_s, kcount, kmax_d, kmax_d + 1,
+                                                           p.err);
+    k_sort_segments_big<<<ceil_div((int64_t)p.n_pt * 32, 128), 128, 0, st>>>(p.n_pt, p.pt_off, kv, d_xy, p.perm,
+                                                                              p.obs_cam_s, p.obs_pt_s,
+                                                                              p.obs_xy_s, p.err);
     BA_LAUNCH_CHECK();
 
     // camera lists
@@ -357,7 +403,7 @@ void build_index(Problem& p, const int32_t* d_oc, const int32_t* d_op, const dou
     int32_t* hist = (int32_t*)tmp_alloc(sizeof(int32_t) * n_tiles * p.n_cam);
     BA_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(int32_t) * n_tiles * p.n_cam, st));
     k_tile_hist<<<gsz, TPB, 0, st>>>(p.obs_cam_s, n, p.n_cam, (int)tile, hist);
-    k_tile_base<<<ceil_div(p.n_cam, 128), 128, 0, st>>>(hist, (int)n_tiles, p.n_cam, p.cam_off);
+    k_tile_base<<<ceil_div((int64_t)p.n_cam * 32, 128), 128, 0, st>>>(hist, (int)n_tiles, p.n_cam, p.cam_off);
     k_tile_place<<<ceil_div(n_tiles * 32, 128), 128, 0, st>>>(p.obs_cam_s, n, p.n_cam, (int)tile,
                                                               (int)n_tiles, hist, p.cam_list);
     BA_LAUNCH_CHECK();
