@@ -477,9 +477,11 @@ __device__ __forceinline__ float team_sum(float v) {
     return v;
 }
 
-template <int T, int K>
+// MO: observations per lane (ceil(k / T) for the warp's largest k); the code
+// depends on k only through MO (fewer rows are zero), so one instantiation
+// serves every k with the same MO
+template <int T, int MO>
 __device__ __forceinline__ void linearize_regteam(const LinArgs& A, int j, int pos, bool act) {
-    constexpr int MO = (K + T - 1) / T;  // observations per lane
     constexpr int MR = 2 * MO;           // rows per lane: local row 2m + e is global row 2 (r + T m) + e
     const int lane = threadIdx.x & 31, r = lane & (T - 1), base = lane & ~(T - 1);
     int s0 = 0, k = 0;
@@ -644,11 +646,11 @@ __device__ __forceinline__ void linearize_regteam(const LinArgs& A, int j, int p
     }
 }
 
-template <int T, int KLO, int KHI>
-__device__ __forceinline__ void linearize_regteam_k(int kw, const LinArgs& A, int j, int pos, bool act) {
-    if constexpr (KLO <= KHI) {
-        if (kw == KLO) linearize_regteam<T, KLO>(A, j, pos, act);
-        else linearize_regteam_k<T, KLO + 1, KHI>(kw, A, j, pos, act);
+template <int T, int MLO, int MHI>
+__device__ __forceinline__ void linearize_regteam_m(int mo, const LinArgs& A, int j, int pos, bool act) {
+    if constexpr (MLO <= MHI) {
+        if (mo == MLO) linearize_regteam<T, MLO>(A, j, pos, act);
+        else linearize_regteam_m<T, MLO + 1, MHI>(mo, A, j, pos, act);
     }
 }
 
@@ -669,7 +671,8 @@ __device__ __forceinline__ void linearize_reg_segment(const LinArgs& A, const in
     if (act && A.blm && !batch_relin(A.blm, A.lm_prob[j])) act = false;
     const int j0 = order[first + idx0];  // the warp's largest k (uniform over the warp)
     const int kw = A.pt_off[j0 + 1] - A.pt_off[j0];
-    linearize_regteam_k<T, KLO, KHI>(kw, A, j, pos, act);
+    if (kw >= KLO && kw <= KHI)
+        linearize_regteam_m<T, (KLO + T - 1) / T, (KHI + T - 1) / T>((kw + T - 1) / T, A, j, pos, act);
 }
 
 // The four segments k 17..32, 9..16, 5..8, 2..4 (teams of 8, 4, 2, 1 lanes) in
