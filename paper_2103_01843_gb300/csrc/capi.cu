@@ -820,6 +820,7 @@ void create_problem(Problem& p, const double* cams, int32_t n_cam, const double*
         p.lmrec = dalloc<float>(p, LM_REC * (int64_t)n_pt);
         BA_CUDA_TRY(cudaMemsetAsync(p.lmrec, 0, sizeof(float) * LM_REC * (int64_t)n_pt, p.stream));
         require(n_pt < (1 << 30), BA_ERR_INVALID_ARG, "the implicit storage supports fewer than 2^30 landmarks");
+        p.pq_part = dalloc<float>(p, 2LL * p.sm_count);
         build_k3_records(p);
         p.tuned = true;  // the tile plans of the stored blocks do not apply
     } else {

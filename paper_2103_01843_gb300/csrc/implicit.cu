@@ -52,6 +52,7 @@ struct ImArgs {
     int n_tasks;
     int n_big;             // tasks [0, n_big) have k > 32 (one landmark each), taken dynamically
     unsigned* ctr;         // [0] next big task, [32] CTAs done (both zero between launches)
+    float* pq_part;        // non-null: per-CTA sums of ||A_j v||^2 (the CG's p^T A^T A p as a sum of squares)
     const float4* ipool;   // 6 float4 chunks per observation, chunk m at m * n_obs
     int64_t n_obs;
     const float* lmrec;    // 32 floats per storage position
@@ -125,7 +126,7 @@ __device__ __forceinline__ float load_v(const float* vt, int i) {
 }
 
 template <int W, bool SV>
-__device__ void small_task(const ImArgs& a, const ImTask& tk, const float* vt, float* yt, int lane) {
+__device__ void small_task(const ImArgs& a, const ImTask& tk, const float* vt, float* yt, int lane, float& pqa) {
     const int team = lane / W, t = lane - team * W, base = team * W;
     const int k = tk.k;
     const bool has = team < tk.n;
@@ -164,12 +165,16 @@ __device__ void small_task(const ImArgs& a, const ImTask& tk, const float* vt, f
     const float h0 = F.T00 * p0, h1 = F.T01 * p0 + F.T11 * p1, h2 = F.T02 * p0 + F.T12 * p1 + F.T22 * p2;
     float z0 = u0 - (r.V[0] * h0 + r.V[1] * h1 + r.V[2] * h2);
     float z1 = u1 - (r.V[3] * h0 + r.V[4] * h1 + r.V[5] * h2);
+    // ||A_j v||^2: the rows below the top three, squared, ...
+    if (act) pqa += t >= 2 ? z0 * z0 + z1 * z1 : (t == 1 ? z1 * z1 : 0.f);
     // top rows 0, 1 (lane t = 0) and 2 (lane t = 1) enter through S
     const float zt0 = __shfl_sync(0xffffffffu, z0, base), zt1 = __shfl_sync(0xffffffffu, z1, base);
     const float zt2 = __shfl_sync(0xffffffffu, z0, base + 1);
     if (t == 0) {
         z0 = F.S00 * zt0 + F.S01 * zt1 + F.S02 * zt2;
         z1 = F.S01 * zt0 + F.S11 * zt1 + F.S12 * zt2;
+        // ... and the top entries through S
+        if (act) pqa += zt0 * z0 + zt1 * z1 + zt2 * (F.S02 * zt0 + F.S12 * zt1 + F.S22 * zt2);
     } else if (t == 1) {
         z0 = F.S02 * zt0 + F.S12 * zt1 + F.S22 * zt2;
     }
@@ -186,7 +191,7 @@ __device__ void small_task(const ImArgs& a, const ImTask& tk, const float* vt, f
 
 // k > 32: one warp, lanes over the observations in chunks of 32
 template <bool SV>
-__device__ void big_task(const ImArgs& a, const ImTask& tk, const float* vt, float* yt, int lane) {
+__device__ void big_task(const ImArgs& a, const ImTask& tk, const float* vt, float* yt, int lane, float& pqa) {
     const int k = tk.k;
     if (a.blm && !batch_active(a.blm, a.lm_prob[a.lm_by_k[tk.pos0]])) return;  // whole warp
     const LmFactors F = load_factors(a.lmrec, tk.pos0);
@@ -246,6 +251,7 @@ __device__ void big_task(const ImArgs& a, const ImTask& tk, const float* vt, flo
     const float s0 = F.S00 * zt0 + F.S01 * zt1 + F.S02 * zt2;
     const float s1 = F.S01 * zt0 + F.S11 * zt1 + F.S12 * zt2;
     const float s2 = F.S02 * zt0 + F.S12 * zt1 + F.S22 * zt2;
+    if (lane == 0) pqa += zt0 * s0 + zt1 * s1 + zt2 * s2;  // ||A_j v||^2: the top entries through S
     // pass 2: V^T z with the top entries replaced
     float q0 = 0.f, q1 = 0.f, q2 = 0.f;
     for (int t = lane; t < k; t += 32) {
@@ -255,6 +261,7 @@ __device__ void big_task(const ImArgs& a, const ImTask& tk, const float* vt, flo
         load(t, r, vv, cam);
         float z0, z1;
         zrows(r, vv, z0, z1);
+        pqa += t >= 2 ? z0 * z0 + z1 * z1 : (t == 1 ? z1 * z1 : 0.f);  // and the rows below them
         if (t == 0) {
             z0 = s0;
             z1 = s1;
@@ -307,15 +314,16 @@ __device__ __forceinline__ void matvec_body(const ImArgs& a, float* ys) {
     const float* vt = SMEM_V ? vs : a.v;
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * (NT / 32) + (threadIdx.x >> 5), nw = gridDim.x * (NT / 32);
+    float pqa = 0.f;
     // the k <= 32 tasks statically, round robin over the warps ...
     for (int ti = a.n_big + gw; ti < a.n_tasks; ti += nw) {
         const ImTask tk = a.tasks[ti];
         switch (team_width(tk.k)) {
-            case 2: small_task<2, SMEM_V>(a, tk, vt, yt, lane); break;
-            case 4: small_task<4, SMEM_V>(a, tk, vt, yt, lane); break;
-            case 8: small_task<8, SMEM_V>(a, tk, vt, yt, lane); break;
-            case 16: small_task<16, SMEM_V>(a, tk, vt, yt, lane); break;
-            default: small_task<32, SMEM_V>(a, tk, vt, yt, lane); break;
+            case 2: small_task<2, SMEM_V>(a, tk, vt, yt, lane, pqa); break;
+            case 4: small_task<4, SMEM_V>(a, tk, vt, yt, lane, pqa); break;
+            case 8: small_task<8, SMEM_V>(a, tk, vt, yt, lane, pqa); break;
+            case 16: small_task<16, SMEM_V>(a, tk, vt, yt, lane, pqa); break;
+            default: small_task<32, SMEM_V>(a, tk, vt, yt, lane, pqa); break;
         }
     }
     // ... then the k > 32 ones (three passes each, up to k = 900) one at a time
@@ -327,7 +335,7 @@ __device__ __forceinline__ void matvec_body(const ImArgs& a, float* ys) {
             if (lane == 0 && *(volatile unsigned*)a.ctr < (unsigned)a.n_big) ti = atomicAdd(a.ctr, 1u);
             ti = __shfl_sync(0xffffffffu, ti, 0);
             if (ti >= (unsigned)a.n_big) break;
-            big_task<SMEM_V>(a, a.tasks[ti], vt, yt, lane);
+            big_task<SMEM_V>(a, a.tasks[ti], vt, yt, lane, pqa);
         }
         // the last CTA to finish resets the counters for the next launch
         __syncthreads();
@@ -338,6 +346,11 @@ __device__ __forceinline__ void matvec_body(const ImArgs& a, float* ys) {
                 atomicExch(a.ctr + 32, 0u);
             }
         }
+    }
+    if (a.pq_part) {  // this CTA's share of p^T A^T A p (summed by the CG update in CTA order)
+        __shared__ float red[32];
+        pqa = block_sum(pqa, red);
+        if (threadIdx.x == 0) a.pq_part[blockIdx.x] = pqa;
     }
     if (SMEM_Y) {
         __syncthreads();
@@ -468,8 +481,10 @@ void configure_implicit(Problem&) {
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, IM_SMEM_Y_MAX));
 }
 
-void launch_matvec_implicit(Problem& p, const float* v, float* y, const PcgScalars* S) {
-    const ImArgs a{static_cast<const ImTask*>(p.im_tasks), p.im_ntasks, p.im_nbig, p.im_ctr,
+int implicit_matvec_grid(const Problem& p) { return implicit_mode(p) == IM_YV1 ? p.sm_count : 2 * p.sm_count; }
+
+void launch_matvec_implicit(Problem& p, const float* v, float* y, const PcgScalars* S, float* pq_part) {
+    const ImArgs a{static_cast<const ImTask*>(p.im_tasks), p.im_ntasks, p.im_nbig, p.im_ctr, pq_part,
                    reinterpret_cast<const float4*>(p.ipool),
                    p.n_obs, p.lmrec, p.mv_cam, v, y, p.n_cam, S,
                    p.batch.n_prob > 0 ? p.batch.lm : nullptr, p.batch.lm_prob, p.lm_by_k};

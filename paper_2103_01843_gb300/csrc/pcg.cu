@@ -612,18 +612,25 @@ __device__ bool pcg_init_range(int c0, int c1, const float* __restrict__ g, cons
 
 // one CG iteration after q = A^T A p (the matvec); adds the pose damping
 // lambda D_p^2 p to q.  Returns true if a stop rule fired in this call.
+// pq_part (non-null, n_part of them): the matvec's per-CTA sums of
+// ||A_j p||^2, so that p^T (A^T A + lambda D_p^2) p is formed as a sum of
+// squares (positive unless p = 0), not as p^T q from the rounded product
 template <int T>
 __device__ bool pcg_update_range(int c0, int c1, const float* __restrict__ g, const float* __restrict__ dp2,
                                  const float* __restrict__ minv, float* x, float* r, float* z, float* p, float* q,
-                                 PcgScalars* S, float* red) {
+                                 PcgScalars* S, float* red, const float* __restrict__ pq_part = nullptr,
+                                 int n_part = 0) {
     const float lam = S->lambda;
     const float rho = S->rho;
     float pq = 0.f;
     for (int i = 9 * c0 + threadIdx.x; i < 9 * c1; i += T) {
-        const float qi = q[i] + lam * dp2[i] * p[i];
+        const float di = lam * dp2[i] * p[i];
+        const float qi = q[i] + di;
         q[i] = qi;
-        pq += p[i] * qi;
+        pq += pq_part ? p[i] * di : p[i] * qi;
     }
+    if (pq_part)
+        for (int c = threadIdx.x; c < n_part; c += T) pq += pq_part[c];
     pq = block_sum(pq, red);
     if (!(pq > 0.f)) {
         if (threadIdx.x == 0) {
@@ -749,13 +756,14 @@ k_pcg_init(int n_cam, const float* __restrict__ g, const float* __restrict__ min
 __global__ void __launch_bounds__(PCG_T)
 k_pcg_update(int n_cam, const float* __restrict__ g, const float* __restrict__ dp2,
              const float* __restrict__ minv, float* x, float* r, float* z, float* p, float* q,
-             PcgScalars* S, cudaGraphConditionalHandle cond, int cond_on) {
+             PcgScalars* S, cudaGraphConditionalHandle cond, int cond_on, const float* __restrict__ pq_part,
+             int n_part) {
     __shared__ float red[32];
     if (S->done) {
         if (cond_on && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
         return;
     }
-    const bool fin = pcg_update_range<PCG_T>(0, n_cam, g, dp2, minv, x, r, z, p, q, S, red);
+    const bool fin = pcg_update_range<PCG_T>(0, n_cam, g, dp2, minv, x, r, z, p, q, S, red, pq_part, n_part);
     if (fin && cond_on && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
 }
 
@@ -894,8 +902,11 @@ void launch_pcg_iteration(Problem& p, cudaEvent_t mv_begin, cudaEvent_t mv_end, 
         if (p.capturing) BA_CUDA_TRY(cudaEventRecordWithFlags(ev, p.stream, cudaEventRecordExternal));
         else BA_CUDA_TRY(cudaEventRecord(ev, p.stream));
     };
+    // the implicit storage's matvec also forms p^T A^T A p as a sum of squares (a single problem)
+    const bool sq = p.implicit && p.batch.n_prob == 0;
     record(mv_begin);
-    launch_matvec_raw(p, p.p, p.q, p.pcg);
+    if (sq) launch_matvec_implicit(p, p.p, p.q, p.pcg, p.pq_part);
+    else launch_matvec_raw(p, p.p, p.q, p.pcg);
     record(mv_end);
     if (p.batch.n_prob > 0) {
         BatchState& B = p.batch;
@@ -903,7 +914,8 @@ void launch_pcg_iteration(Problem& p, cudaEvent_t mv_begin, cudaEvent_t mv_end, 
                                                         p.p, p.q, B.pcg, p.pcg, B.n_done, cond, in_while ? 1 : 0);
     } else {
         k_pcg_update<<<1, PCG_T, 0, p.stream>>>(p.n_cam, p.g, p.dp2, active_minv(p), p.x, p.r, p.z, p.p, p.q,
-                                                p.pcg, cond, in_while ? 1 : 0);
+                                                p.pcg, cond, in_while ? 1 : 0, sq ? p.pq_part : nullptr,
+                                                sq ? implicit_matvec_grid(p) : 0);
     }
     BA_LAUNCH_CHECK();
 }

@@ -175,6 +175,7 @@ struct Problem {
     bool implicit = false;
     float *ipool = nullptr, *rpool = nullptr, *lmrec = nullptr;
     int32_t* lm_pos = nullptr;       // storage position of every landmark
+    float* pq_part = nullptr;        // implicit storage: the matvec's per-CTA sums of ||A_j p||^2 (CG)
     int4* k3rec = nullptr;           // K3's camera-ordered records (landmark, storage index, position | slot)
     float2* k3xy = nullptr;          // and measurements, per camera-list entry
     float* init_part = nullptr;      // CG start folded into K3: per-camera partials of g^T g, r^T z
@@ -298,7 +299,9 @@ void launch_schur_matvec(Problem& p, const float* v, float* y, const PcgScalars*
 void launch_schur_backsub(Problem& p);
 void launch_camera_diag(Problem& p);  // D_p^2 alone (linearize.cu)
 void configure_implicit(Problem& p);
-void launch_matvec_implicit(Problem& p, const float* v, float* y, const PcgScalars* S);
+// pq_part (non-null): per-CTA sums of ||A_j v||^2, implicit_matvec_grid(p) of them
+void launch_matvec_implicit(Problem& p, const float* v, float* y, const PcgScalars* S, float* pq_part = nullptr);
+int implicit_matvec_grid(const Problem& p);
 void launch_implicit_top_rows(Problem& p, int j, int k, float* top);  // export: landmark j's undamped top rows
 void launch_precond_records(Problem& p);
 int matvec_ctas_per_sm();
