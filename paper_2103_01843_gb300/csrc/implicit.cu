@@ -55,7 +55,7 @@ struct ImArgs {
     float* pq_part;        // non-null: per-CTA sums of ||A_j v||^2 (the CG's p^T A^T A p as a sum of squares)
     const float4* ipool;   // 6 float4 chunks per observation, chunk m at m * n_obs
     int64_t n_obs;
-    const float* lmrec;    // 32 floats per storage position
+    const float* lmrec;    // LM_REC floats per storage position (Tm and S read here)
     const int32_t* mv_cam;
     const float* v;
     float* y;
@@ -117,7 +117,6 @@ __device__ __forceinline__ void accumulate_y(float* yt, int cam, const ObsRec& r
     }
 }
 
-// k <= 32: teams of W lanes, lane t of a team holds observation t (rows 2t, 2t+1)
 // v element i: shared memory (SV) or the read-only global path
 template <bool SV>
 __device__ __forceinline__ float load_v(const float* vt, int i) {
@@ -125,6 +124,7 @@ __device__ __forceinline__ float load_v(const float* vt, int i) {
     else return __ldg(vt + i);
 }
 
+// k <= 32: teams of W lanes, lane t of a team holds observation t (rows 2t, 2t+1)
 template <int W, bool SV>
 __device__ void small_task(const ImArgs& a, const ImTask& tk, const float* vt, float* yt, int lane, float& pqa) {
     const int team = lane / W, t = lane - team * W, base = team * W;
