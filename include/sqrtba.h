@@ -224,7 +224,9 @@ SQRTBA_API ba_status ba_solve(ba_problem* h, ba_lm_report* reports, int32_t max_
                    int32_t* n_reports);
 
 /* Copies the current state to host FP64 arrays (cams: 9 n_cam, pts: 3 n_pt);
- * either pointer may be NULL. */
+ * either pointer may be NULL.  The FP32 state is copied through one
+ * process-wide page-locked staging buffer (grown to the largest state read,
+ * kept for the life of the process; concurrent calls take turns). */
 SQRTBA_API ba_status ba_get_params(ba_problem* h, double* cams, double* pts);
 
 /* Replaces the state (host FP64 arrays, same layout), resets lambda to

@@ -333,8 +333,8 @@ class Problem:
 
     # --- state ------------------------------------------------------------------
     def get_params(self):
-        c = np.zeros((self.n_cam, 9))
-        p = np.zeros((self.n_pt, 3))
+        c = np.empty((self.n_cam, 9))  # every element is written by the call
+        p = np.empty((self.n_pt, 3))
         self._check(lib().ba_get_params(self.h, _ptr(c, _d), _ptr(p, _d)))
         return c, p
 

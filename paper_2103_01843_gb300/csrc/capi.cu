@@ -1186,18 +1186,44 @@ ba_status ba_solve(ba_problem* h, ba_lm_report* reps, int32_t max_reports, int32
     API_CATCH(h)
 }
 
+// A process-wide page-locked staging buffer for reading the state back
+// (grow-only; one caller at a time): the device-to-host copy then runs at the
+// link's speed instead of through the driver's pageable bounce buffers, and a
+// problem created per solve does not pay for page-locking each time.
+struct HostStage {
+    std::mutex mu;
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+HostStage& host_stage() {
+    static HostStage s;
+    return s;
+}
+
 ba_status ba_get_params(ba_problem* h, double* cams, double* pts) {
     if (!h) return BA_ERR_INVALID_ARG;
     API_TRY
     Problem& p = h->p;
-    std::vector<float> c(9 * (size_t)p.n_cam), x(3 * (size_t)p.n_pt);
-    if (cams) d2h(p, c.data(), p.cams, (int64_t)c.size());
-    if (pts) d2h(p, x.data(), p.pts, (int64_t)x.size());
+    const size_t nc = 9 * (size_t)p.n_cam, nx = 3 * (size_t)p.n_pt;
+    HostStage& hs = host_stage();
+    std::lock_guard<std::mutex> lock(hs.mu);
+    const size_t need = sizeof(float) * (nc + nx);
+    if (hs.bytes < need) {
+        if (hs.ptr) cudaFreeHost(hs.ptr);
+        hs.ptr = nullptr;
+        hs.bytes = 0;
+        BA_CUDA_TRY(cudaMallocHost(&hs.ptr, need));
+        hs.bytes = need;
+    }
+    float* c = static_cast<float*>(hs.ptr);
+    float* x = c + nc;
+    if (cams) d2h(p, c, p.cams, (int64_t)nc);
+    if (pts) d2h(p, x, p.pts, (int64_t)nx);
     sync(p);
     if (cams)
-        for (size_t i = 0; i < c.size(); ++i) cams[i] = c[i];
+        for (size_t i = 0; i < nc; ++i) cams[i] = c[i];
     if (pts)
-        for (size_t i = 0; i < x.size(); ++i) pts[i] = x[i];
+        for (size_t i = 0; i < nx; ++i) pts[i] = x[i];
     return BA_OK;
     API_CATCH(h)
 }
