@@ -181,90 +181,119 @@ k_damp(int n_pt, const int32_t* __restrict__ pt_off, const int64_t* __restrict__
 }
 
 // The implicit storage keeps no top rows; its landmark record holds the
-// undamped R1, Q1^T r = t and P (K1).  One thread per landmark (storage
+// undamped R1, Q1^T r = t and P (K1).  One lane per landmark (storage
 // position) computes the same six rotations from R1 and sqrt(lambda) D_l,
 // applies them also to [I; 0] (the map from the undamped top rows to the six
 // rotated rows, G[:, 0:3] = [G_tt; G_dt]), and stores S = G_dt^T G_dt, G_tt,
 // G_tt P, G_tt t and the damped R.  No undo is needed: every call starts from
-// the undamped R1.
-__global__ void __launch_bounds__(128)
+// the undamped R1.  A warp takes 32 consecutive 256-byte records: their input
+// fields (floats 40..63) are loaded and their outputs (floats 6..39) stored
+// cooperatively through shared memory, so that consecutive lanes touch
+// consecutive 16-byte words instead of one word per record each.
+constexpr int DI_WARPS = 4;
+constexpr int DI_OUT = 37;  // shared floats per record for floats 6..39 (odd stride)
+
+__global__ void __launch_bounds__(32 * DI_WARPS)
 k_damp_implicit(int n_pt, float* __restrict__ lmrec, float sqrt_lambda, const int32_t* __restrict__ lm_by_k,
                 const float* __restrict__ lam_prob, const int32_t* __restrict__ lm_prob,
                 const BatchLm* __restrict__ blm) {
-    const int pos = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pos >= n_pt) return;
-    if (blm && !batch_active(blm, lm_prob[lm_by_k[pos]])) return;
-    float* L = lmrec + (int64_t)LM_REC * pos;
-    // R1 (upper), D_l^2, t and P from the landmark record (K1), 16-byte loads
-    static_assert(LR_DL2 == LR_R1 + 6 && LR_T == LR_R1 + 9 && LR_P == LR_R1 + 12 && LR_R1 % 4 == 0, "record");
-    const float4 q0 = *reinterpret_cast<const float4*>(L + LR_R1), q1 = *reinterpret_cast<const float4*>(L + LR_R1 + 4),
-                 q2 = *reinterpret_cast<const float4*>(L + LR_R1 + 8), p0 = *reinterpret_cast<const float4*>(L + LR_P),
-                 p1 = *reinterpret_cast<const float4*>(L + LR_P + 4);
-    const float p8 = L[LR_P + 8];
-    float R[3][3] = {{q0.x, q0.y, q0.z}, {0.f, q0.w, q1.x}, {0.f, 0.f, q1.y}};
-    const float dl2[3] = {q1.z, q1.w, q2.x};
-    const float t[3] = {q2.y, q2.z, q2.w};
-    const float P[3][3] = {{p0.x, p0.y, p0.z}, {p0.w, p1.x, p1.y}, {p1.z, p1.w, p8}};
-    float D[3][3], E[6][3];
-    for (int i = 0; i < 3; ++i)
-        for (int c = 0; c < 3; ++c) {
-            D[i][c] = 0.f;
-            E[i][c] = i == c ? 1.f : 0.f;
-            E[3 + i][c] = 0.f;
-        }
-    const float sl = lam_prob ? sqrtf(lam_prob[lm_prob[lm_by_k[pos]]]) : sqrt_lambda;
-    for (int d = 0; d < 3; ++d) D[d][d] = sl * sqrtf(dl2[d]);
-#pragma unroll
-    for (int m = 0; m < 6; ++m) {
-        int c, d;
-        givens_pair(m, c, d);
-        const float a = R[c][c], b = D[d][c];
-        const float r2 = a * a + b * b;
-        float cs = 1.f, sn = 0.f;
-        if (r2 > 0.f) {
-            const float inv = rsqrtf(r2);
-            cs = a * inv;
-            sn = b * inv;
-        }
-#pragma unroll
-        for (int col = 0; col < 3; ++col) {
-            if (col < c) continue;
-            const float u = R[c][col], v = D[d][col];
-            R[c][col] = cs * u + sn * v;
-            D[d][col] = -sn * u + cs * v;
-        }
-        D[d][c] = 0.f;
-#pragma unroll
-        for (int col = 0; col < 3; ++col) {
-            const float u = E[c][col], v = E[3 + d][col];
-            E[c][col] = cs * u + sn * v;
-            E[3 + d][col] = -sn * u + cs * v;
-        }
+    __shared__ float4 sin[DI_WARPS][32 * 6];
+    __shared__ float sout[DI_WARPS][32 * DI_OUT];
+    __shared__ int sact[DI_WARPS][32];
+    static_assert(LR_R1 == 40 && LR_DL2 == 46 && LR_T == 49 && LR_P == 52, "input fields: float4s 10..15");
+    static_assert(LR_S == 6 && LR_GP == 12 && LR_GT == 21 && LR_G == 24 && LR_RD == 33, "outputs: floats 6..39");
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int pos0 = (blockIdx.x * DI_WARPS + w) * 32;
+    if (pos0 >= n_pt) return;  // whole warp
+    const int nrec = min(32, n_pt - pos0);
+    float4* L4 = reinterpret_cast<float4*>(lmrec + (int64_t)LM_REC * pos0);
+    for (int q = lane; q < nrec * 6; q += 32) {
+        const int r = q / 6;
+        sin[w][q] = L4[16 * r + 10 + (q - 6 * r)];
     }
-    // S = G_dt^T G_dt (upper: 00 01 02 11 12 22), G_tt P, G_tt t, G_tt, damped R
-    // (upper): 16-byte stores
-    float S[6], GP[9], Gt[3];
-    int q = 0;
+    const int pos = pos0 + lane;
+    const bool act = lane < nrec && (!blm || batch_active(blm, lm_prob[lm_by_k[pos]]));
+    sact[w][lane] = act ? 1 : 0;
+    __syncwarp();
+    if (act) {
+        const float4* in = &sin[w][6 * lane];
+        const float4 q0 = in[0], q1 = in[1], q2 = in[2], p0 = in[3], p1 = in[4], p2 = in[5];
+        float R[3][3] = {{q0.x, q0.y, q0.z}, {0.f, q0.w, q1.x}, {0.f, 0.f, q1.y}};
+        const float dl2[3] = {q1.z, q1.w, q2.x};
+        const float t[3] = {q2.y, q2.z, q2.w};
+        const float P[3][3] = {{p0.x, p0.y, p0.z}, {p0.w, p1.x, p1.y}, {p1.z, p1.w, p2.x}};
+        float D[3][3], E[6][3];
+        for (int i = 0; i < 3; ++i)
+            for (int c = 0; c < 3; ++c) {
+                D[i][c] = 0.f;
+                E[i][c] = i == c ? 1.f : 0.f;
+                E[3 + i][c] = 0.f;
+            }
+        const float sl = lam_prob ? sqrtf(lam_prob[lm_prob[lm_by_k[pos]]]) : sqrt_lambda;
+        for (int d = 0; d < 3; ++d) D[d][d] = sl * sqrtf(dl2[d]);
 #pragma unroll
-    for (int u = 0; u < 3; ++u)
+        for (int m = 0; m < 6; ++m) {
+            int c, d;
+            givens_pair(m, c, d);
+            const float a = R[c][c], b = D[d][c];
+            const float r2 = a * a + b * b;
+            float cs = 1.f, sn = 0.f;
+            if (r2 > 0.f) {
+                const float inv = rsqrtf(r2);
+                cs = a * inv;
+                sn = b * inv;
+            }
 #pragma unroll
-        for (int v = u; v < 3; ++v) S[q++] = E[3][u] * E[3][v] + E[4][u] * E[4][v] + E[5][u] * E[5][v];
+            for (int col = 0; col < 3; ++col) {
+                if (col < c) continue;
+                const float u = R[c][col], v = D[d][col];
+                R[c][col] = cs * u + sn * v;
+                D[d][col] = -sn * u + cs * v;
+            }
+            D[d][c] = 0.f;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        Gt[i] = E[i][0] * t[0] + E[i][1] * t[1] + E[i][2] * t[2];
+            for (int col = 0; col < 3; ++col) {
+                const float u = E[c][col], v = E[3 + d][col];
+                E[c][col] = cs * u + sn * v;
+                E[3 + d][col] = -sn * u + cs * v;
+            }
+        }
+        // floats 6..39 of the record: S (6), G_tt P (9), G_tt t (3), G_tt (9), damped R (6), pad
+        float* o = &sout[w][DI_OUT * lane];
+        int q = 0;
 #pragma unroll
-        for (int b = 0; b < 3; ++b) GP[3 * i + b] = E[i][0] * P[0][b] + E[i][1] * P[1][b] + E[i][2] * P[2][b];
+        for (int u = 0; u < 3; ++u)
+#pragma unroll
+            for (int v = u; v < 3; ++v) o[q++] = E[3][u] * E[3][v] + E[4][u] * E[4][v] + E[5][u] * E[5][v];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) o[6 + 3 * i + b] = E[i][0] * P[0][b] + E[i][1] * P[1][b] + E[i][2] * P[2][b];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) o[15 + i] = E[i][0] * t[0] + E[i][1] * t[1] + E[i][2] * t[2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) o[18 + 3 * i + c] = E[i][c];
+        o[27] = R[0][0];
+        o[28] = R[0][1];
+        o[29] = R[0][2];
+        o[30] = R[1][1];
+        o[31] = R[1][2];
+        o[32] = R[2][2];
+        o[33] = 0.f;
     }
-    static_assert(LR_S == 6 && LR_GP == 12 && LR_GT == 21 && LR_G == 24 && LR_RD == 33, "record");
-    *reinterpret_cast<float2*>(L + 6) = make_float2(S[0], S[1]);
-    *reinterpret_cast<float4*>(L + 8) = make_float4(S[2], S[3], S[4], S[5]);
-    *reinterpret_cast<float4*>(L + 12) = make_float4(GP[0], GP[1], GP[2], GP[3]);
-    *reinterpret_cast<float4*>(L + 16) = make_float4(GP[4], GP[5], GP[6], GP[7]);
-    *reinterpret_cast<float4*>(L + 20) = make_float4(GP[8], Gt[0], Gt[1], Gt[2]);
-    *reinterpret_cast<float4*>(L + 24) = make_float4(E[0][0], E[0][1], E[0][2], E[1][0]);
-    *reinterpret_cast<float4*>(L + 28) = make_float4(E[1][1], E[1][2], E[2][0], E[2][1]);
-    *reinterpret_cast<float4*>(L + 32) = make_float4(E[2][2], R[0][0], R[0][1], R[0][2]);
-    *reinterpret_cast<float4*>(L + 36) = make_float4(R[1][1], R[1][2], R[2][2], 0.f);
+    __syncwarp();
+    // floats 8..39 as 8 float4 per record, floats 6..7 as one float2
+    for (int q = lane; q < nrec * 8; q += 32) {
+        const int r = q >> 3, m = q & 7;
+        if (!sact[w][r]) continue;
+        const float* o = &sout[w][DI_OUT * r + 2 + 4 * m];
+        L4[16 * r + 2 + m] = make_float4(o[0], o[1], o[2], o[3]);
+    }
+    if (act)
+        *reinterpret_cast<float2*>(lmrec + (int64_t)LM_REC * pos + LR_S) =
+            make_float2(sout[w][DI_OUT * lane], sout[w][DI_OUT * lane + 1]);
 }
 
 }  // namespace
@@ -276,7 +305,7 @@ void launch_damp(Problem& p, bool undo_old, float lambda) {
     }
     count_launches(p, 1);
     if (p.implicit) {
-        k_damp_implicit<<<ceil_div(p.n_pt, 128), 128, 0, p.stream>>>(
+        k_damp_implicit<<<ceil_div(p.n_pt, 32 * DI_WARPS), 32 * DI_WARPS, 0, p.stream>>>(
             p.n_pt, p.lmrec, sqrtf(lambda), p.lm_by_k, p.batch.lam, p.batch.lm_prob,
             p.batch.n_prob > 0 ? p.batch.lm : nullptr);
         BA_LAUNCH_CHECK();
