@@ -3,12 +3,12 @@
 // from the three top rows of each landmark block (one warp per landmark),
 // followed by the Gauss-Newton model cost L(dx) = ||r + J_p dx_p + J_l dx_l||^2
 // (undamped) evaluated per observation (one thread each) from the camera
-// model and summed in FP64.
+// model, each observation's term in FP32, the sum in FP64.
 //
 // K7 (same file): candidate state x (+) dx (rotation Exp(dw) R, everything
-// else additive) and the energy E = sum ||r||^2 (Eq. ba_energy) with FP32
-// residuals accumulated in FP64.  All FP64 sums are deterministic: fixed
-// per-block partials reduced in a fixed order.
+// else additive) and the energy E = sum ||r||^2 (Eq. ba_energy), FP32 terms
+// accumulated in FP64.  All FP64 sums are deterministic: fixed per-block
+// partials reduced in a fixed order.
 #include <algorithm>
 
 #include "camera.cuh"
@@ -164,27 +164,28 @@ __device__ __forceinline__ void model_cost_obs(int64_t s, const float* __restric
     frame_jacobians(frames + FRAME * cam, pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], z.x, z.y, r, Jp, Jl);
     const float* d = dp + 9 * cam;
     const float l0 = dl[3 * j], l1 = dl[3 * j + 1], l2 = dl[3 * j + 2];
-    // robust norm: rho(s) - w s + w ||r + J dx||^2 (w = 1, rho(s) = s without it)
+    // robust norm: rho(s) - w s + w ||r + J dx||^2 (w = 1, rho(s) = s without
+    // it); the observation's terms in FP32, their sums in FP64 (energy_term)
     const float w = huber_weight(huber, r[0], r[1]);
-    double mo = 0.0;
+    float e[2];
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-        float e = r[i] + Jl[3 * i] * l0 + Jl[3 * i + 1] * l1 + Jl[3 * i + 2] * l2;
+        e[i] = r[i] + Jl[3 * i] * l0 + Jl[3 * i + 1] * l1 + Jl[3 * i + 2] * l2;
 #pragma unroll
-        for (int q = 0; q < 9; ++q) e += Jp[9 * i + q] * d[q];
-        mo += (double)e * (double)e;
+        for (int q = 0; q < 9; ++q) e[i] += Jp[9 * i + q] * d[q];
     }
+    const float mo = e[0] * e[0] + e[1] * e[1];
     if (w == 1.f) {
-        m += mo;
+        m += (double)mo;
     } else {
-        const double s = (double)r[0] * r[0] + (double)r[1] * r[1];
-        m += huber_rho(huber, s) - (double)w * s + (double)w * mo;
+        const double s = (double)(r[0] * r[0] + r[1] * r[1]);
+        m += huber_rho(huber, s) - (double)w * s + (double)w * (double)mo;
     }
     if (cand_frames) {
         float r0, r1;
         frame_residual(cand_frames + FRAME * cam, cand_pts[3 * j], cand_pts[3 * j + 1], cand_pts[3 * j + 2], z.x, z.y,
                        r0, r1);
-        c += huber_rho(huber, (double)r0 * (double)r0 + (double)r1 * (double)r1);
+        c += energy_term(huber, r0, r1);
     }
 }
 
@@ -245,7 +246,7 @@ k_cost(int64_t n_obs, const float* __restrict__ frames, const float* __restrict_
         const float2 z = obs_xy_s[s];
         float r0, r1;
         frame_residual(frames + FRAME * obs_cam_s[s], pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], z.x, z.y, r0, r1);
-        acc += huber_rho(huber, (double)r0 * (double)r0 + (double)r1 * (double)r1);
+        acc += energy_term(huber, r0, r1);
     }
     acc = block_sum_d(acc, red);
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
@@ -362,11 +363,16 @@ void launch_candidate(Problem& p) {
 // candidate (frames written by k_candidate)
 void launch_cost(Problem& p, bool candidate, int slot) {
     if (!candidate) launch_frames(p);
+    launch_cost_on(p, candidate ? p.cand_frames : p.frames, candidate ? p.cand_pts : p.pts, slot, p.stream);
+}
+
+// E from the given frames and points into dsum[slot] on stream st (the
+// per-CTA partials, then their fixed-order sum)
+void launch_cost_on(Problem& p, const float* frames, const float* pts, int slot, cudaStream_t st) {
     count_launches(p, 2);
-    k_cost<<<p.red_grid, 256, 0, p.stream>>>(p.n_obs, candidate ? p.cand_frames : p.frames,
-                                             candidate ? p.cand_pts : p.pts, p.obs_cam_s, p.obs_pt_s,
-                                             p.obs_xy_s, p.partials, (float)p.opt.huber_delta);
-    k_sum_partials<<<1, 32, 0, p.stream>>>(p.partials, p.red_grid, p.dsum + slot);
+    k_cost<<<p.red_grid, 256, 0, st>>>(p.n_obs, frames, pts, p.obs_cam_s, p.obs_pt_s, p.obs_xy_s, p.partials,
+                                       (float)p.opt.huber_delta);
+    k_sum_partials<<<1, 32, 0, st>>>(p.partials, p.red_grid, p.dsum + slot);
     BA_LAUNCH_CHECK();
 }
 

@@ -34,7 +34,7 @@ k_cost_seg(const int64_t* __restrict__ prob_obs_off, const float* __restrict__ f
         const float2 z = obs_xy_s[s];
         float r0, r1;
         frame_residual(frames + FRAME * obs_cam_s[s], pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], z.x, z.y, r0, r1);
-        acc += huber_rho(huber, (double)r0 * (double)r0 + (double)r1 * (double)r1);
+        acc += energy_term(huber, r0, r1);
     }
     acc = block_sum_d(acc, red);
     if (threadIdx.x == 0) out[b] = acc;

@@ -122,6 +122,15 @@ __device__ __forceinline__ float huber_weight(float delta, float r0, float r1) {
 __device__ __forceinline__ double huber_rho(double delta, double s) {
     return (delta > 0.0 && s > delta * delta) ? 2.0 * delta * sqrt(s) - delta * delta : s;
 }
+// One observation's energy term rho(r0^2 + r1^2) from FP32 residuals, for an
+// FP64 sum: the square in FP32 (relative error 2^-23 at most, below that of
+// the FP32 residual itself), then one conversion; FP64 arithmetic only on the
+// robust branch.  GB300 issues FP64 at a small fraction of its FP32 rate, and
+// the squares in FP64 made the per-observation sums FP64-bound.
+__device__ __forceinline__ double energy_term(float delta, float r0, float r1) {
+    const float s = r0 * r0 + r1 * r1;
+    return (delta > 0.f && s > delta * delta) ? huber_rho((double)delta, (double)s) : (double)s;
+}
 __device__ __forceinline__ void huber_scale_rows(float delta, float r[2], float Jp[18], float Jl[6]) {
     const float w = huber_weight(delta, r[0], r[1]);
     if (w == 1.f) return;

@@ -242,19 +242,17 @@ void free_all(Problem& p) {
 // defer_cost: the energy is left in dsum[2] for the caller's next
 // synchronisation (cost_pending) instead of being read back here.
 void do_linearize(Problem& p, bool need_cost = true, double damp_lambda = 0.0, bool defer_cost = false) {
+    const bool want_cost = need_cost || !p.cost_valid;
     PhaseTimer t(p, PROF_LINEARIZE);
     launch_frames(p);
-    launch_linearize(p);
+    launch_linearize(p, want_cost ? (defer_cost ? 2 : 0) : -1);  // the energy beside K1
     t.end();
     if (damp_lambda > 0.0) {
         PhaseTimer td(p, PROF_DAMP);
         launch_damp(p, false, (float)damp_lambda);
         td.end();
     }
-    if (need_cost || !p.cost_valid) {
-        PhaseTimer tc(p, PROF_COST);
-        launch_cost(p, false, defer_cost ? 2 : 0);
-        tc.end();
+    if (want_cost) {
         if (defer_cost) {
             p.cost_pending = true;
             p.cost_valid = false;

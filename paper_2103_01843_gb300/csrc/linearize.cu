@@ -800,11 +800,14 @@ void configure_linearize(Problem& p) {
 // The K1 kernels work on disjoint landmarks and D_p^2 only reads: D_p^2 and
 // the few long k > 32 factorisations run on a side stream (forked from and
 // joined back into the problem's stream) beside the team kernels, which run
-// one after the other (run side by side they only contend).
-void launch_linearize(Problem& p) {
+// one after the other (run side by side they only contend).  The energy at
+// the linearisation point, which only reads too, follows them on the side
+// stream: K1's kernels are latency-bound at low occupancy and leave room.
+void launch_linearize(Problem& p, int cost_slot) {
     if (p.schur) {  // no factorisation: D_p^2 and D_l^2 only (the Schur complement is formed per damping)
         launch_camera_diag(p);
         launch_schur_dl2(p);
+        if (cost_slot >= 0) launch_cost_on(p, p.frames, p.pts, cost_slot, p.stream);
         return;
     }
     LinArgs A{p.frames, p.pts, p.obs_cam_s, p.obs_xy_s, p.pt_off, p.a_off, p.apool, p.tpool, p.cpool, p.c_off,
@@ -824,6 +827,7 @@ void launch_linearize(Problem& p) {
         k_linearize_block<<<n_big, BIG_TEAM, sm, p.side>>>(A, p.lm_by_k, n_big);
         count_launches(p, 1);
     }
+    if (cost_slot >= 0) launch_cost_on(p, p.frames, p.pts, cost_slot, p.side);
     if (p.implicit) {
         // register-resident teams of 8, 4, 2 and 1 lanes: k 17..32, 9..16, 5..8, 2..4, one grid
         RegSegments g{};

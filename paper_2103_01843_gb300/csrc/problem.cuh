@@ -266,10 +266,13 @@ void build_index(Problem& p, const int32_t* d_obs_cam, const int32_t* d_obs_pt,
                  const double* d_obs_xy, const double* d_cams, const double* d_pts);
 // K1: damping diagonals, linearisation + Householder QR (linearize.cu)
 void launch_frames(Problem& p);   // frames of the current cams
-void launch_linearize(Problem& p);  // K1 and D_p^2
+// K1 and D_p^2; cost_slot >= 0 adds the energy at the linearisation point
+// (frames already computed) into dsum[cost_slot], run beside K1
+void launch_linearize(Problem& p, int cost_slot = -1);
 void launch_export_jacobians(Problem& p, float* r, float* jp, float* jl);
 // cost and state update (cost.cu)
 void launch_cost(Problem& p, bool candidate, int slot = 0);  // E into dsum[slot]
+void launch_cost_on(Problem& p, const float* frames, const float* pts, int slot, cudaStream_t st);
 void launch_candidate(Problem& p);
 // K2: landmark damping with Givens rotations (damp.cu)
 void launch_damp(Problem& p, bool undo_old, float lambda);

@@ -138,8 +138,12 @@ def test_autotune_single_problem(pkg, members):
 def test_stopped_problems_cost_nothing(pkg, implicit):
     """Problems that have stopped are skipped and rejected steps keep their
     linearisation: the results still match the oracle per problem, and the
-    late batch iterations, with few problems left, take less time than the
-    first, with all of them."""
+    late batch iterations, with a quarter of the problems or fewer left, take
+    less time than the iterations with all of them.  On these small members a
+    fixed part of every iteration (launches, the host round trip, the CG loop
+    of the slowest problem left) does not shrink with the active count, so the
+    margin asked for is 10 %; a batch that kept working on stopped problems
+    would take as long late as early."""
     scenes = [make_scene("batched_member", s) for s in range(16)]
     iters = 30
     with pkg.Batch(scenes, max_lm_iters=iters, implicit_blocks=implicit) as b:
@@ -152,8 +156,9 @@ def test_stopped_problems_cost_nothing(pkg, implicit):
     assert all(a >= c for a, c in zip(active, active[1:]))
     assert abs(sum(ms) - summ["total_ms"]) <= 0.05 * summ["total_ms"] + 0.5
     late = [t for a, t in zip(active, ms) if a <= len(scenes) // 4]
+    full = [t for a, t in zip(active, ms) if a == len(scenes)]
     if late:
-        assert np.median(late) < 0.8 * ms[0], (active, ms)
+        assert np.median(late) < 0.9 * np.median(full), (active, ms)
     for s, r in zip(scenes[:6], reps[:6]):
         ref, _ = _oracle_final(s, iters)
         assert abs(r["final_cost"] - ref) <= 1e-3 * ref, (r, ref)
