@@ -15,7 +15,8 @@
  * Q2^T J_p blocks (Sec. 5.4, Eq. cg_mult); landmarks are then recovered by
  * back substitution (Eq. backsub_nm).  All marginalisation and PCG arithmetic
  * is FP32 (Sec. 6.1, "sqrt BA-32"); the global cost sum, the model cost and
- * the LM gain ratio are accumulated in FP64.
+ * the LM gain ratio are accumulated in FP64 (each observation's term is formed
+ * in FP32 and added to the FP64 sum).
  *
  * Conventions for every call
  *   - Camera layout (BAL, Sec. 6.2): 9 doubles per camera, row-major:
@@ -205,7 +206,7 @@ SQRTBA_API ba_status ba_pcg_solve(ba_problem* h, ba_pcg_report* report);
  * Errors: BA_ERR_STATE if no PCG solution is present. */
 SQRTBA_API ba_status ba_backsubstitute(ba_problem* h, double* model_cost);
 
-/* *cost = E (Eq. ba_energy, FP64 sum of FP32 residuals) at the current state
+/* *cost = E (Eq. ba_energy, FP64 sum of the FP32 terms ||r||^2) at the current state
  * (candidate = 0) or at the candidate x (+) dx (candidate = 1; rotation
  * updated as Exp(dw) R, everything else additively).
  * Errors: BA_ERR_STATE for candidate = 1 without a back-substituted step. */
